@@ -1,0 +1,202 @@
+/*
+ * vfd.h -- C ABI of the GB300 (sm_103a) library for the linear-complexity
+ * finite element operator of variable-order fractional diffusion
+ * (Lei, Turkiyyah & Knio, arXiv 2302.02863).
+ *
+ * Problem (Sec. 2, eqs. e:strong, e:weak-d): on a simplicial mesh of
+ * Omega = Omega_i U Omega_e, find the P1 function U, zero on Omega_e, with
+ *     A(U, V) = int_{Omega_i} f V   for all P1 V zero on Omega_e,
+ *     A(u, v) = int int (u(x)-u(y)) (v(x)-v(y)) gamma(x,y) dy dx,
+ *     gamma(x,y) = sqrt(kappa(x) kappa(y)) / |x-y|^(d + s(x) + s(y)).
+ * The stiffness matrix is assembled as A = B + K + M (Sec. 3, eq. e:decomp):
+ * B the singular near field (Sec. 4), K the H^2 matrix of the separated
+ * interior pairs (Sec. 5), M the weighted mass matrix whose density rho is
+ * computed by an H^2 (fast-multipole type) sweep (Sec. 6), plus the exterior
+ * tail of Sec. 7.1.1 when Omega_e is all of R^d outside the mesh.
+ *
+ * Conventions for every entry point:
+ *  - No exception crosses the ABI; a failing call returns a status and sets
+ *    a message readable with vfd_last_error() (thread-local).
+ *  - The caller owns every data pointer.  Handles own their device memory
+ *    until vfd_free_*.  "device" pointers are CUDA device (or managed)
+ *    memory of the current device; entry points that say "host or device"
+ *    accept either and copy host memory through the library.
+ *  - Vectors indexed by DoF use the library's DoF numbering (cluster-tree
+ *    order), available from vfd_mesh_dofs.  Multi-RHS blocks are
+ *    column-major: entry (i, r) at ptr[i + r*ld], ld >= n_dof.
+ *  - Work is enqueued on the given cudaStream_t (passed as void*; NULL is the
+ *    legacy default stream) and is asynchronous unless the call returns
+ *    host values (vfd_solve's iteration counts and residuals, vfd_assemble's
+ *    field check).  One handle must not be used from two streams at once.
+ *  - Nothing falls back to the CPU: without a CUDA device every call that
+ *    computes returns VFD_ECUDA.
+ */
+#ifndef VFD_H
+#define VFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VFD_OK = 0,
+    VFD_EINVAL = 1,        /* bad argument, bad mesh, field outside 0 <= s <= s_bar < 1 */
+    VFD_ENOMEM = 2,        /* device or host allocation failed */
+    VFD_ECUDA = 3,         /* CUDA runtime error, or no CUDA device */
+    VFD_ENOCONV = 4,       /* solver hit max_it; the last iterate is returned */
+    VFD_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    VFD_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} vfd_status;
+
+typedef struct vfd_mesh_s *vfd_mesh_t;
+typedef struct vfd_op_s *vfd_op_t;
+
+/* Precision of the assembled operator (argument `precision`). */
+enum {
+    VFD_FP64 = 0,   /* every part in FP64 */
+    VFD_FP32 = 1    /* K (near blocks, coupling, bases, transfers) stored and
+                       applied in FP32 with FP32 accumulation; B, M, the
+                       density rho and all solver vectors stay FP64 */
+};
+
+/* Parts of the operator for vfd_apply_parts (bit mask). */
+enum {
+    VFD_PART_B = 1,       /* singular near field B (Sec. 4) */
+    VFD_PART_M = 2,       /* weighted mass matrix M incl. exterior tail (Sec. 6, 7.1.1) */
+    VFD_PART_KNEAR = 4,   /* dense inadmissible leaf blocks of K (Sec. 5.2) */
+    VFD_PART_KFAR = 8,    /* low-rank admissible blocks of K (Sec. 5.3) */
+    VFD_PART_ALL = 15
+};
+
+/* Flags of vfd_assemble. */
+enum {
+    VFD_ASSEMBLE_UNCHECKED = 1  /* skip the check 0 <= s <= s_bar < 1 (lets the
+                                   tests use polynomial kernels, e.g. s = -2) */
+};
+
+/* Mesh-level options (geometry only; fixed for the life of the mesh handle). */
+typedef struct {
+    int leaf_m;         /* max DoFs per leaf of the K cluster tree (Sec. 5.1, m); default 64 */
+    int cheb_p;         /* Chebyshev nodes per dimension; rank k = p^d (Sec. 5.3); default 4 */
+    double lambda;      /* admissibility lambda ||C-C'|| >= (D+D')/2 on the support-extended
+                           boxes (Sec. 7, first paragraph); default 0.75; 0 = no low-rank block */
+    int n_sing;         /* Gauss points per direction in the singular rules (Sec. 4, n); default 3 */
+    int tail_mode;      /* 0: Omega_e is the meshed exterior; 1: Omega_e = R^d minus the mesh,
+                           whose outer boundary is the sphere |x| = tail_R (Sec. 7.1.1) */
+    double tail_R;      /* radius of that sphere; default 1.1 */
+    int rho_leaf_m;     /* max points per leaf of the density cluster trees (Sec. 6.2); default 64 */
+    double rho_lambda;  /* admissibility of the density sweep on plain point boxes, with the
+                           extra condition dist > 2 h_max (Sec. 6.2); default 0.75; 0 = direct */
+} vfd_mesh_opts;
+
+/* Scalar field on R^d: value = squash(c0 + sum of terms), or a P1 field.
+ * fourier rows (k1,k2,k3 integers, amp, phase): amp cos(pi k.x + phase)
+ * gauss rows   (x0,y0,z0, amp, c):              amp exp(-c |x-x0|^2)
+ * tbump rows   (x0,y0,z0, amp, ell):            amp prod_i exp(-1/(1-r_i^2)), r_i = 2(x_i-x0_i)/ell, |r_i|<1
+ * squash = 1: lo + (hi-lo)/(1+exp(-v)).
+ * Row arrays are host memory, read during the call.  kind = VFD_FIELD_NODAL
+ * takes `nodal`, values at the n_vert mesh vertices (host or device); it is
+ * supported only when the operator has no low-rank part (lambda = 0 and
+ * rho_lambda = 0), where every evaluation point lies in a known cell. */
+enum { VFD_FIELD_ANALYTIC = 0, VFD_FIELD_NODAL = 1 };
+typedef struct {
+    int kind;
+    double c0;
+    int n_fourier;
+    const double *fourier;
+    int n_gauss;
+    const double *gauss;
+    int n_tbump;
+    const double *tbump;
+    int squash;
+    double lo, hi;
+    const double *nodal;
+} vfd_field;
+
+/* Fill *opts with the defaults listed above. */
+void vfd_default_mesh_opts(vfd_mesh_opts *opts);
+
+/* Build the mesh handle: topology (interior DoFs are the vertices of no
+ * exterior cell, Sec. 2.3), touching element pairs with their type
+ * (identical / edge / vertex, Sec. 4), the element quadrature cloud Q
+ * (3 points per triangle / interval, Sec. 6.1 and Sec. 7), the KD cluster tree
+ * on the DoFs with support-extended boxes, the admissible and inadmissible
+ * block lists, leaf bases and transfer matrices (Sec. 5), the point cluster
+ * trees of the density sweep (Sec. 6.2), and uploads them to the device.
+ *   d: 1 or 2.  coords: host, n_vert*d (row-major).  cells: host,
+ *   n_cell*(d+1) vertex ids.  cell_is_interior: host, n_cell flags.
+ *   opts: may be NULL for the defaults.
+ * Errors: VFD_EINVAL (d, degenerate cells, no interior DoF, bad options),
+ * VFD_ENOMEM, VFD_ECUDA. */
+vfd_status vfd_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell, const int32_t *cells,
+                    const uint8_t *cell_is_interior, const vfd_mesh_opts *opts, vfd_mesh_t *out);
+
+/* dof_of_vertex: host, n_vert entries, the DoF index of each vertex or -1.
+ * n_dof: host.  Either pointer may be NULL. */
+vfd_status vfd_mesh_dofs(vfd_mesh_t mesh, int32_t *dof_of_vertex, int64_t *n_dof);
+
+/* Structure counts (host int64 array of n_info entries, in this order):
+ * [0] n_dof  [1] n_vert  [2] n_cell  [3] touching pairs  [4] nnz(B+M)
+ * [5] tree levels  [6] tree nodes  [7] rank k  [8] admissible blocks of K
+ * [9] inadmissible leaf blocks of K  [10] dense near entries of K
+ * [11] quadrature points  [12] interior quadrature points
+ * [13] admissible blocks of the density sweep  [14] near point pairs of the
+ * density sweep. */
+vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info);
+
+/* Assemble the operator for the fields s and log kappa (Algorithm 1):
+ * field values, coupling blocks S = -2 gamma(xi_a, xi_b) (Sec. 5.3, eq.
+ * eq:triple_product), dense inadmissible blocks (Sec. 5.2), singular B
+ * (Sec. 4), density rho (Sec. 6.2) plus tail, and M (eq. e:m).
+ *   s_bar: quadrature parameter of the singular rules (Sec. 4), 0 <= s <= s_bar < 1
+ *          must hold at every evaluation point unless VFD_ASSEMBLE_UNCHECKED.
+ *   precision: VFD_FP64 or VFD_FP32.  stream: cudaStream_t.
+ * Blocks the host once to read the field check.
+ * Errors: VFD_EINVAL (field out of range, bad s_bar), VFD_EUNSUPPORTED
+ * (nodal field with a low-rank part; tail with non-constant fields),
+ * VFD_ENOMEM, VFD_ECUDA. */
+vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *log_kappa, double s_bar,
+                        int precision, int flags, void *stream, vfd_op_t *out);
+
+/* Y = A X for nrhs columns (X, Y: host or device, n_dof x nrhs, leading
+ * dimension ld).  X and Y must not overlap. */
+vfd_status vfd_apply(vfd_op_t op, const double *X, double *Y, int64_t nrhs, int64_t ld, void *stream);
+
+/* Y = (sum of the selected parts) X; parts is a mask of VFD_PART_*. */
+vfd_status vfd_apply_parts(vfd_op_t op, int parts, const double *X, double *Y, int64_t nrhs, int64_t ld,
+                           void *stream);
+
+/* Solve A U = F by conjugate gradients (Sec. 7: "conjugate gradient
+ * solver"), every iteration on the device, column by column for nrhs > 1.
+ * F, U: host or device, n_dof x nrhs, leading dimension ld; U holds the
+ * initial guess on entry.  Converged when ||F - A U|| <= rtol ||F||.
+ * iters, relres: host arrays of nrhs entries (may be NULL).  For a
+ * VFD_FP32 operator the solve is iterative refinement: an FP64 residual with
+ * the FP64 parts and the FP32 K, and inner CG sweeps on the same operator.
+ * Returns VFD_ENOCONV when some column did not converge in max_it. */
+vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int64_t ld, double rtol,
+                     int max_it, int *iters, double *relres, void *stream);
+
+/* P1 load F = M0 f (exact P1 mass matrix of the interior cells times the
+ * nodal values f at all n_vert vertices).  f_nodal, F: host or device. */
+vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *stream);
+
+/* Density rho (incl. tail) at the interior quadrature points, ordered by
+ * interior cell (increasing cell id) then element-rule point (triangle:
+ * the point nearest to stored vertex 0, 1, 2; interval: Gauss points left
+ * to right in the stored orientation).  rho: host or device, n_qint doubles. */
+vfd_status vfd_op_rho(vfd_op_t op, double *rho, void *stream);
+
+void vfd_free_op(vfd_op_t op);
+void vfd_free_mesh(vfd_mesh_t mesh);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *vfd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VFD_H */

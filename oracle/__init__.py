@@ -63,6 +63,8 @@ def lib():
         L.oracle_gamma.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
         L.oracle_gamma.restype = C.c_double
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_cg.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_int]
+        L.oracle_cg.restype = C.c_int
         _lib = L
     return _lib
 
@@ -189,6 +191,15 @@ def cholesky_solve(A, F):
     if rc != 0:
         raise np.linalg.LinAlgError(f"matrix not positive definite at pivot {rc - 1}")
     return U
+
+
+def cg(A, F, rtol=1e-10, max_it=100000):
+    """Plain dense CG (the paper's solver) from zero; returns (U, iterations)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    U = np.zeros_like(F)
+    it = lib().oracle_cg(A.shape[0], _dp(A), _dp(F), _dp(U), float(rtol), int(max_it))
+    return U, it
 
 
 def field(d, f, x):

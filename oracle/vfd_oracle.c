@@ -866,3 +866,33 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* plain conjugate gradients on the dense matrix (the paper's solver, Sec. 7),
+ * for the CPU timing baseline: A U = F from U = 0 until ||F - A U|| <= rtol ||F||.
+ * Returns the number of iterations (matrix-vector products). */
+int oracle_cg(int N, const double *A, const double *F, double *U, double rtol, int max_it)
+{
+    double *r = malloc(sizeof(double) * N), *p = malloc(sizeof(double) * N), *q = malloc(sizeof(double) * N);
+    double bb = 0.0, rr = 0.0;
+    for (int i = 0; i < N; ++i) { U[i] = 0.0; r[i] = F[i]; p[i] = F[i]; bb += F[i] * F[i]; }
+    rr = bb;
+    int it = 0;
+    while (it < max_it && rr > rtol * rtol * bb) {
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < N; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < N; ++j) v += A[(size_t)i * N + j] * p[j];
+            q[i] = v;
+        }
+        double pq = 0.0;
+        for (int i = 0; i < N; ++i) pq += p[i] * q[i];
+        double alpha = rr / pq, rn = 0.0;
+        for (int i = 0; i < N; ++i) { U[i] += alpha * p[i]; r[i] -= alpha * q[i]; rn += r[i] * r[i]; }
+        double beta = rn / rr;
+        rr = rn;
+        for (int i = 0; i < N; ++i) p[i] = r[i] + beta * p[i];
+        ++it;
+    }
+    free(r); free(p); free(q);
+    return it;
+}

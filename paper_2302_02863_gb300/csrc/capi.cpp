@@ -1,0 +1,369 @@
+// C ABI of the vfd library (declared in include/vfd.h): argument checks,
+// host/device staging, handle lifetimes and error reporting.  All
+// computation happens in the CUDA kernels of assemble.cu / apply.cu / solve.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "vfd_internal.h"
+
+struct vfd_mesh_s {
+    vfd::MeshData *m;
+};
+struct vfd_op_s {
+    vfd::OpData *op;
+};
+
+namespace vfd {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+}  // namespace vfd
+
+using namespace vfd;
+
+#define VFD_API_BEGIN try {
+#define VFD_API_END                                                                \
+    }                                                                              \
+    catch (const vfd::Error &e) {                                                  \
+        vfd::set_error(e.msg);                                                     \
+        return e.st;                                                               \
+    }                                                                              \
+    catch (const std::bad_alloc &) {                                               \
+        vfd::set_error("host allocation failed");                                  \
+        return VFD_ENOMEM;                                                         \
+    }                                                                              \
+    catch (const std::exception &e) {                                              \
+        vfd::set_error(e.what());                                                  \
+        return VFD_EINVAL;                                                         \
+    }
+
+namespace {
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void require_device()
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        throw vfd::Error{VFD_ECUDA, "no CUDA device available (this library has no CPU path)"};
+    }
+}
+
+// upload a field descriptor; Fourier rows become (k, amp cos(phase), amp sin(phase))
+void upload_field(const vfd_field *f, int n_vert, DBuf<double> &rows, DBuf<double> &vals, DField &out)
+{
+    VFD_REQUIRE(f, VFD_EINVAL, "null field");
+    out = DField{};
+    out.c0 = f->c0;
+    out.squash = f->squash;
+    out.lo = f->lo;
+    out.hi = f->hi;
+    if (f->kind == VFD_FIELD_NODAL) {
+        VFD_REQUIRE(f->nodal, VFD_EINVAL, "nodal field without values");
+        out.nodal = 1;
+        vals.alloc(n_vert);
+        VFD_CUDA(cudaMemcpy(vals.p, f->nodal, sizeof(double) * n_vert, cudaMemcpyDefault));
+        out.vals = vals.p;
+        rows.alloc(0);
+        return;
+    }
+    VFD_REQUIRE(f->kind == VFD_FIELD_ANALYTIC, VFD_EINVAL, "unknown field kind");
+    VFD_REQUIRE(f->n_fourier >= 0 && f->n_gauss >= 0 && f->n_tbump >= 0, VFD_EINVAL, "negative term count");
+    VFD_REQUIRE((f->n_fourier == 0 || f->fourier) && (f->n_gauss == 0 || f->gauss) && (f->n_tbump == 0 || f->tbump),
+                VFD_EINVAL, "missing field rows");
+    std::vector<double> h;
+    int kmax = 0;
+    for (int t = 0; t < f->n_fourier; ++t) {
+        const double *r = f->fourier + 5 * t;
+        for (int j = 0; j < 3; ++j) {
+            if (r[j] != std::floor(r[j])) kmax = 99;           // non-integer: general path
+            kmax = std::max(kmax, (int)std::min(99.0, std::fabs(r[j])));
+            h.push_back(r[j]);
+        }
+        h.push_back(r[3] * std::cos(r[4]));
+        h.push_back(r[3] * std::sin(r[4]));
+    }
+    for (int t = 0; t < 5 * f->n_gauss; ++t) h.push_back(f->gauss[t]);
+    for (int t = 0; t < 5 * f->n_tbump; ++t) h.push_back(f->tbump[t]);
+    rows.upload(h);
+    out.nF = f->n_fourier;
+    out.nG = f->n_gauss;
+    out.nT = f->n_tbump;
+    out.kmax = kmax;
+    out.rows = rows.p;
+}
+
+bool field_is_const(const vfd_field *f)
+{
+    return f->kind == VFD_FIELD_ANALYTIC && f->n_fourier == 0 && f->n_gauss == 0 && f->n_tbump == 0 && !f->squash;
+}
+
+// stage a possibly-host input block into device memory
+const double *stage_in(const double *X, int64_t n, int64_t nrhs, int64_t ld, DBuf<double> &buf, cudaStream_t st)
+{
+    if (is_device_ptr(X)) return X;
+    size_t need = (size_t)ld * nrhs;
+    if (buf.n < need) buf.alloc(need);
+    VFD_CUDA(cudaMemcpyAsync(buf.p, X, sizeof(double) * ((size_t)ld * (nrhs - 1) + n), cudaMemcpyHostToDevice, st));
+    return buf.p;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vfd_default_mesh_opts(vfd_mesh_opts *o)
+{
+    if (!o) return;
+    o->leaf_m = 64;
+    o->cheb_p = 4;
+    o->lambda = 0.75;
+    o->n_sing = 3;
+    o->tail_mode = 0;
+    o->tail_R = 1.1;
+    o->rho_leaf_m = 64;
+    o->rho_lambda = 0.75;
+}
+
+const char *vfd_last_error(void) { return vfd::g_err.c_str(); }
+
+vfd_status vfd_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell, const int32_t *cells,
+                    const uint8_t *cell_is_interior, const vfd_mesh_opts *opts, vfd_mesh_t *out)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(out && coords && cells && cell_is_interior, VFD_EINVAL, "null argument");
+    *out = nullptr;
+    require_device();
+    vfd_mesh_opts o;
+    vfd_default_mesh_opts(&o);
+    if (opts) o = *opts;
+    MeshData *m = build_mesh(d, n_vert, coords, n_cell, cells, cell_is_interior, o);
+    *out = new vfd_mesh_s{m};
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_mesh_dofs(vfd_mesh_t mesh, int32_t *dof_of_vertex, int64_t *n_dof)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(mesh, VFD_EINVAL, "null mesh");
+    if (dof_of_vertex) std::memcpy(dof_of_vertex, mesh->m->dof_of_vertex.data(), sizeof(int32_t) * mesh->m->M);
+    if (n_dof) *n_dof = mesh->m->N;
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(mesh && info && n_info >= 0, VFD_EINVAL, "bad argument");
+    const MeshData &m = *mesh->m;
+    int64_t v[15] = {m.N,        m.M,          m.C,       m.npairs, m.nnz,    m.kt.L,        m.kt.nnode, m.k,
+                     m.nfar,     m.nnear,      m.near_entries, m.nQ, m.nQint, m.nrfar, m.rnear_pairs};
+    for (int i = 0; i < n_info && i < 15; ++i) info[i] = v[i];
+    for (int i = 15; i < n_info; ++i) info[i] = 0;
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *log_kappa, double s_bar,
+                        int precision, int flags, void *stream, vfd_op_t *out)
+{
+    OpData *op = nullptr;
+    VFD_API_BEGIN
+    VFD_REQUIRE(mesh && s && log_kappa && out, VFD_EINVAL, "null argument");
+    *out = nullptr;
+    require_device();
+    const MeshData &m = *mesh->m;
+    cudaStream_t st = (cudaStream_t)stream;
+    VFD_REQUIRE(precision == VFD_FP64 || precision == VFD_FP32, VFD_EINVAL, "unknown precision");
+    VFD_REQUIRE(s_bar < 1.0 && ((flags & VFD_ASSEMBLE_UNCHECKED) || s_bar >= 0.0), VFD_EINVAL,
+                "s_bar must satisfy 0 <= s_bar < 1");
+    bool nodal = s->kind == VFD_FIELD_NODAL || log_kappa->kind == VFD_FIELD_NODAL;
+    VFD_REQUIRE(!nodal || (m.nfar == 0 && m.nrfar == 0), VFD_EUNSUPPORTED,
+                "P1 (nodal) fields need an operator without low-rank blocks (lambda = rho_lambda = 0)");
+    VFD_REQUIRE(m.opts.tail_mode == 0 || (field_is_const(s) && field_is_const(log_kappa)), VFD_EUNSUPPORTED,
+                "the exterior tail needs constant s and kappa");
+    op = new OpData();
+    op->m = mesh->m;
+    op->precision = precision;
+    op->s_bar = s_bar;
+    op->check_fields = !(flags & VFD_ASSEMBLE_UNCHECKED);
+    upload_field(s, m.M, op->f_rows_s, op->f_vals_s, op->fs);
+    upload_field(log_kappa, m.M, op->f_rows_k, op->f_vals_k, op->fk);
+    op->errflag.alloc(2);
+    op->errflag.zero(st);
+    // a2: field values; check 0 <= s <= s_bar at every evaluation point (Sec. 2, i:s)
+    launch_field_points(m, *op, st);
+    int herr[2] = {0, 0};
+    VFD_CUDA(cudaMemcpyAsync(herr, op->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VFD_CUDA(cudaStreamSynchronize(st));
+    VFD_REQUIRE(herr[0] == 0, VFD_EINVAL, "s(x) outside [0, s_bar] at some evaluation point");
+    // a3: coupling blocks; a4: dense inadmissible leaves
+    launch_coupling_build(m, *op, st);
+    launch_near_build(m, *op, st);
+    // a6: density by the H^2 sweep + tail
+    launch_density(m, *op, st);
+    // a5: singular near field
+    {
+        DBuf<double> Lbuf;
+        launch_singular_B(m, *op, Lbuf, st);
+        launch_gather_B(m, *op, Lbuf, st);
+        VFD_CUDA(cudaStreamSynchronize(st));
+    }
+    // a7: weighted mass (and B + M for the apply)
+    launch_gather_M(m, *op, st);
+    if (precision == VFD_FP32) launch_convert_fp32(m, *op, st);
+    VFD_CUDA(cudaStreamSynchronize(st));
+    *out = new vfd_op_s{op};
+    return VFD_OK;
+    }
+    catch (const vfd::Error &e) {
+        delete op;
+        vfd::set_error(e.msg);
+        return e.st;
+    }
+    catch (const std::bad_alloc &) {
+        delete op;
+        vfd::set_error("host allocation failed");
+        return VFD_ENOMEM;
+    }
+}
+
+static vfd_status apply_common(vfd_op_t h, int parts, const double *X, double *Y, int64_t nrhs, int64_t ld,
+                               void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && X && Y, VFD_EINVAL, "null argument");
+    OpData &op = *h->op;
+    const MeshData &m = *op.m;
+    VFD_REQUIRE(nrhs >= 1 && nrhs <= 65535 && ld >= m.N, VFD_EINVAL, "bad nrhs or ld");
+    VFD_REQUIRE((parts & ~VFD_PART_ALL) == 0, VFD_EINVAL, "bad parts mask");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *dx = stage_in(X, m.N, nrhs, ld, op.xin, st);
+    bool ydev = is_device_ptr(Y);
+    double *dy = Y;
+    if (!ydev) {
+        size_t need = (size_t)ld * nrhs;
+        if (op.yout.n < need) op.yout.alloc(need);
+        dy = op.yout.p;
+    }
+    apply_parts(m, op, parts, dx, dy, (int)nrhs, ld, st);
+    if (!ydev) {
+        VFD_CUDA(cudaMemcpyAsync(Y, dy, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaStreamSynchronize(st));
+    }
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_apply(vfd_op_t op, const double *X, double *Y, int64_t nrhs, int64_t ld, void *stream)
+{
+    return apply_common(op, VFD_PART_ALL, X, Y, nrhs, ld, stream);
+}
+
+vfd_status vfd_apply_parts(vfd_op_t op, int parts, const double *X, double *Y, int64_t nrhs, int64_t ld,
+                           void *stream)
+{
+    return apply_common(op, parts, X, Y, nrhs, ld, stream);
+}
+
+vfd_status vfd_solve(vfd_op_t h, const double *F, double *U, int64_t nrhs, int64_t ld, double rtol, int max_it,
+                     int *iters, double *relres, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && F && U, VFD_EINVAL, "null argument");
+    OpData &op = *h->op;
+    const MeshData &m = *op.m;
+    VFD_REQUIRE(nrhs >= 1 && ld >= m.N && rtol > 0.0 && max_it >= 0, VFD_EINVAL, "bad solver arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *df = stage_in(F, m.N, nrhs, ld, op.xin, st);
+    bool udev = is_device_ptr(U);
+    double *du = U;
+    if (!udev) {
+        size_t need = (size_t)ld * nrhs;
+        if (op.yout.n < need) op.yout.alloc(need);
+        du = op.yout.p;
+        VFD_CUDA(cudaMemcpyAsync(du, U, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyHostToDevice, st));
+    }
+    vfd_status rs = cg_solve(m, op, df, du, (int)nrhs, ld, rtol, max_it, iters, relres, st);
+    if (!udev) {
+        VFD_CUDA(cudaMemcpyAsync(U, du, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyDeviceToHost, st));
+    }
+    VFD_CUDA(cudaStreamSynchronize(st));
+    if (rs != VFD_OK) vfd::set_error("CG did not reach rtol within max_it");
+    return rs;
+    VFD_API_END
+}
+
+vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(mesh && f_nodal && F, VFD_EINVAL, "null argument");
+    require_device();
+    const MeshData &m = *mesh->m;
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf<double> fin, fout;
+    const double *df = f_nodal;
+    if (!is_device_ptr(f_nodal)) {
+        fin.alloc(m.M);
+        VFD_CUDA(cudaMemcpyAsync(fin.p, f_nodal, sizeof(double) * m.M, cudaMemcpyHostToDevice, st));
+        df = fin.p;
+    }
+    bool fdev = is_device_ptr(F);
+    double *dF = F;
+    if (!fdev) {
+        fout.alloc(m.N);
+        dF = fout.p;
+    }
+    launch_load(m, df, dF, st);
+    if (!fdev) VFD_CUDA(cudaMemcpyAsync(F, dF, sizeof(double) * m.N, cudaMemcpyDeviceToHost, st));
+    VFD_CUDA(cudaStreamSynchronize(st));
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_op_rho(vfd_op_t h, double *rho, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && rho, VFD_EINVAL, "null argument");
+    OpData &op = *h->op;
+    cudaStream_t st = (cudaStream_t)stream;
+    VFD_CUDA(cudaMemcpyAsync(rho, op.rho.p, sizeof(double) * op.m->nQint, cudaMemcpyDefault, st));
+    VFD_CUDA(cudaStreamSynchronize(st));
+    return VFD_OK;
+    VFD_API_END
+}
+
+void vfd_free_op(vfd_op_t h)
+{
+    if (!h) return;
+    release_graphs(*h->op);
+    delete h->op;
+    delete h;
+}
+
+void vfd_free_mesh(vfd_mesh_t h)
+{
+    if (!h) return;
+    delete h->m;
+    delete h;
+}
+
+}  // extern "C"

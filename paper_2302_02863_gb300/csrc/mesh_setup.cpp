@@ -1,0 +1,830 @@
+// Host-side, geometry-only setup of the mesh handle (built once per mesh):
+// interior DoFs (Sec. 2.3), touching element pairs and their type (Sec. 4),
+// the element quadrature cloud (Sec. 6.1), the B/M sparsity with
+// deterministic gather lists, the KD cluster trees with support-extended
+// boxes, the admissible / inadmissible block lists, leaf bases and transfer
+// matrices of the interpolation H^2 matrix (Sec. 5), and the point trees,
+// lists and source moments of the density sweep (Sec. 6.2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "vfd_internal.h"
+
+namespace vfd {
+
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    // Golub-Welsch would need an eigen-solver; Newton on the three-term
+    // recurrence of P_n is enough for n <= 64.
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1.0, pc = z;
+            for (int k = 2; k <= n; ++k) {
+                double pn = ((2.0 * k - 1.0) * z * pc - (k - 1.0) * pm) / k;
+                pm = pc;
+                pc = pn;
+            }
+            if (n == 1) { pc = z; pm = 1.0; }
+            dp = n * (z * pc - pm) / (z * z - 1.0);
+            double dz = pc / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double pm = 1.0, pc = z;
+        for (int k = 2; k <= n; ++k) {
+            double pn = ((2.0 * k - 1.0) * z * pc - (k - 1.0) * pm) / k;
+            pm = pc;
+            pc = pn;
+        }
+        if (n == 1) { pc = z; pm = 1.0; }
+        dp = n * (z * pc - pm) / (z * z - 1.0);
+        x[n - 1 - i] = 0.5 * (1.0 + z);
+        w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void cheb_nodes_1d(int p, double lo, double hi, double *out)
+{
+    // first-kind Chebyshev points of [lo, hi] (Sec. 5.3; reading: Chebyshev,
+    // not the Legendre basis named in Sec. 7)
+    double c = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+    for (int i = 0; i < p; ++i) out[i] = c + h * std::cos((2.0 * i + 1.0) * M_PI / (2.0 * p));
+}
+
+namespace {
+
+// tensor Lagrange basis on a box: values l_alpha(x), alpha = a0 + p*a1 (+p^2 a2)
+void lagrange_box(int d, int p, const double *lo, const double *hi, const double *x, double *out)
+{
+    double nodes[PMAX], l1[3][PMAX];
+    for (int i = 0; i < d; ++i) {
+        cheb_nodes_1d(p, lo[i], hi[i], nodes);
+        for (int a = 0; a < p; ++a) {
+            double v = 1.0;
+            for (int b = 0; b < p; ++b)
+                if (b != a) v *= (x[i] - nodes[b]) / (nodes[a] - nodes[b]);
+            l1[i][a] = v;
+        }
+    }
+    int k = 1;
+    for (int i = 0; i < d; ++i) k *= p;
+    for (int al = 0; al < k; ++al) {
+        int r = al;
+        double v = 1.0;
+        for (int i = 0; i < d; ++i) {
+            v *= l1[i][r % p];
+            r /= p;
+        }
+        out[al] = v;
+    }
+}
+
+void cheb_box(int d, int p, const double *lo, const double *hi, double *pts /* k*d */)
+{
+    double nodes[3][PMAX];
+    for (int i = 0; i < d; ++i) cheb_nodes_1d(p, lo[i], hi[i], nodes[i]);
+    int k = 1;
+    for (int i = 0; i < d; ++i) k *= p;
+    for (int al = 0; al < k; ++al) {
+        int r = al;
+        for (int i = 0; i < d; ++i) {
+            pts[al * d + i] = nodes[i][r % p];
+            r /= p;
+        }
+    }
+}
+
+// complete binary KD tree: median splits along the longest box side (Sec. 5.1)
+Tree build_kdtree(int d, const std::vector<double> &P /* n*d */, int n, int leaf_m)
+{
+    Tree t;
+    int L = 0;
+    while (n > leaf_m * (1 << L)) ++L;
+    t.L = L;
+    t.nnode = (1 << (L + 1)) - 1;
+    t.nleaf = 1 << L;
+    t.begin.assign(t.nnode, 0);
+    t.end.assign(t.nnode, 0);
+    t.perm.resize(n);
+    std::iota(t.perm.begin(), t.perm.end(), 0);
+    t.lo.assign((size_t)t.nnode * d, 0.0);
+    t.hi.assign((size_t)t.nnode * d, 0.0);
+    t.begin[0] = 0;
+    t.end[0] = n;
+    for (int node = 0; node < t.nnode; ++node) {
+        int b = t.begin[node], e = t.end[node];
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int i = b; i < e; ++i)
+            for (int c = 0; c < d; ++c) {
+                double v = P[(size_t)t.perm[i] * d + c];
+                lo[c] = std::min(lo[c], v);
+                hi[c] = std::max(hi[c], v);
+            }
+        for (int c = 0; c < d; ++c) {
+            t.lo[(size_t)node * d + c] = (e > b) ? lo[c] : 0.0;
+            t.hi[(size_t)node * d + c] = (e > b) ? hi[c] : 0.0;
+        }
+        if (t.is_leaf(node)) continue;
+        int dim = 0;
+        for (int c = 1; c < d; ++c)
+            if (hi[c] - lo[c] > hi[dim] - lo[dim]) dim = c;
+        std::sort(t.perm.begin() + b, t.perm.begin() + e, [&](int u, int v) {
+            double a = P[(size_t)u * d + dim], bb = P[(size_t)v * d + dim];
+            return a < bb || (a == bb && u < v);
+        });
+        int mid = b + (e - b) / 2;
+        t.begin[2 * node + 1] = b;
+        t.end[2 * node + 1] = mid;
+        t.begin[2 * node + 2] = mid;
+        t.end[2 * node + 2] = e;
+    }
+    return t;
+}
+
+double box_diam(int d, const double *lo, const double *hi)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) s += (hi[i] - lo[i]) * (hi[i] - lo[i]);
+    return std::sqrt(s);
+}
+
+double box_dist(int d, const double *alo, const double *ahi, const double *blo, const double *bhi)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double g = std::max(0.0, std::max(alo[i] - bhi[i], blo[i] - ahi[i]));
+        s += g * g;
+    }
+    return std::sqrt(s);
+}
+
+// admissibility as used in the paper's experiments (Sec. 7):
+// lambda ||C - C'|| >= (D + D')/2, with strictly separated boxes
+bool admissible(int d, double lambda, const double *alo, const double *ahi, const double *blo, const double *bhi,
+                double min_dist)
+{
+    if (lambda <= 0.0) return false;
+    double cc = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double c = 0.5 * (alo[i] + ahi[i]) - 0.5 * (blo[i] + bhi[i]);
+        cc += c * c;
+    }
+    double D = box_diam(d, alo, ahi), Dp = box_diam(d, blo, bhi);
+    if (lambda * std::sqrt(cc) < 0.5 * (D + Dp)) return false;
+    return box_dist(d, alo, ahi, blo, bhi) > min_dist;
+}
+
+void pad_boxes(Tree &t, int d)
+{
+    // keep Chebyshev nodes distinct on (nearly) flat boxes
+    const double root = box_diam(d, &t.lo[0], &t.hi[0]);
+    for (int n = 0; n < t.nnode; ++n) {
+        double diam = box_diam(d, &t.lo[(size_t)n * d], &t.hi[(size_t)n * d]);
+        for (int i = 0; i < d; ++i) {
+            double w = t.hi[(size_t)n * d + i] - t.lo[(size_t)n * d + i];
+            double need = 1e-9 * std::max(diam, 1e-6 * root);
+            if (w < need) {
+                t.lo[(size_t)n * d + i] -= 0.5 * need;
+                t.hi[(size_t)n * d + i] += 0.5 * need;
+            }
+        }
+    }
+}
+
+template <class T>
+void csr_from_lists(const std::vector<std::vector<T>> &lists, std::vector<int> &ptr, std::vector<T> &val)
+{
+    ptr.assign(lists.size() + 1, 0);
+    for (size_t i = 0; i < lists.size(); ++i) ptr[i + 1] = ptr[i] + (int)lists[i].size();
+    val.clear();
+    val.reserve(ptr.back());
+    for (auto &l : lists) val.insert(val.end(), l.begin(), l.end());
+}
+
+}  // namespace
+
+MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell, const int32_t *cells,
+                     const uint8_t *inter, const vfd_mesh_opts &opts)
+{
+    VFD_REQUIRE(d == 1 || d == 2, VFD_EINVAL, "d must be 1 or 2");
+    VFD_REQUIRE(n_vert > 0 && n_cell > 0 && n_vert < (1LL << 30) && n_cell < (1LL << 28), VFD_EINVAL,
+                "bad mesh size");
+    VFD_REQUIRE(opts.leaf_m >= 2 && opts.leaf_m <= 256, VFD_EINVAL, "leaf_m must be in [2,256]");
+    VFD_REQUIRE(opts.rho_leaf_m >= 2 && opts.rho_leaf_m <= 1024, VFD_EINVAL, "rho_leaf_m must be in [2,1024]");
+    VFD_REQUIRE(opts.cheb_p >= 1 && opts.cheb_p <= PMAX, VFD_EINVAL, "cheb_p must be in [1,8]");
+    VFD_REQUIRE(opts.n_sing >= 1 && opts.n_sing <= NSMAX, VFD_EINVAL, "n_sing must be in [1,16]");
+    VFD_REQUIRE(opts.lambda >= 0.0 && opts.rho_lambda >= 0.0, VFD_EINVAL, "lambda must be >= 0");
+    VFD_REQUIRE(opts.tail_mode == 0 || (opts.tail_mode == 1 && opts.tail_R > 0.0), VFD_EINVAL, "bad tail options");
+    int kk = 1;
+    for (int i = 0; i < d; ++i) kk *= opts.cheb_p;
+    VFD_REQUIRE(kk <= KMAX, VFD_EINVAL, "rank p^d too large");
+
+    auto *m = new MeshData();
+    try {
+        m->d = d;
+        m->M = (int)n_vert;
+        m->C = (int)n_cell;
+        m->opts = opts;
+        m->p = opts.cheb_p;
+        m->k = kk;
+        const int nv = d + 1, M = m->M, C = m->C;
+        m->X.assign(coords, coords + (size_t)M * d);
+        m->T.assign(cells, cells + (size_t)C * nv);
+        m->inter.assign(inter, inter + C);
+        for (int i = 0; i < C * nv; ++i)
+            VFD_REQUIRE(m->T[i] >= 0 && m->T[i] < M, VFD_EINVAL, "cell vertex id out of range");
+
+        // ---- cell measures, h_max
+        std::vector<double> meas(C);
+        for (int c = 0; c < C; ++c) {
+            const int *t = &m->T[(size_t)c * nv];
+            double mu, diam = 0.0;
+            if (d == 1) {
+                mu = std::fabs(m->X[t[1]] - m->X[t[0]]);
+                diam = mu;
+            } else {
+                const double *a = &m->X[2 * t[0]], *b = &m->X[2 * t[1]], *e = &m->X[2 * t[2]];
+                mu = 0.5 * std::fabs((b[0] - a[0]) * (e[1] - a[1]) - (b[1] - a[1]) * (e[0] - a[0]));
+                for (int u = 0; u < 3; ++u)
+                    for (int v = u + 1; v < 3; ++v) {
+                        double dx = m->X[2 * t[u]] - m->X[2 * t[v]], dy = m->X[2 * t[u] + 1] - m->X[2 * t[v] + 1];
+                        diam = std::max(diam, std::sqrt(dx * dx + dy * dy));
+                    }
+            }
+            VFD_REQUIRE(mu > 0.0, VFD_EINVAL, "degenerate cell " + std::to_string(c));
+            meas[c] = mu;
+            m->h_max = std::max(m->h_max, diam);
+        }
+
+        // ---- DoFs: vertices of no exterior cell (Sec. 2.3)
+        std::vector<char> used(M, 0), ext(M, 0);
+        for (int c = 0; c < C; ++c)
+            for (int a = 0; a < nv; ++a) {
+                used[m->T[(size_t)c * nv + a]] = 1;
+                if (!m->inter[c]) ext[m->T[(size_t)c * nv + a]] = 1;
+            }
+        std::vector<int> dofv;
+        for (int v = 0; v < M; ++v)
+            if (used[v] && !ext[v]) dofv.push_back(v);
+        m->N = (int)dofv.size();
+        VFD_REQUIRE(m->N > 0, VFD_EINVAL, "mesh has no interior DoF");
+        const int N = m->N;
+
+        // ---- K cluster tree on the DoF positions; DoF numbering = tree order
+        {
+            std::vector<double> P((size_t)N * d);
+            for (int i = 0; i < N; ++i)
+                for (int c = 0; c < d; ++c) P[(size_t)i * d + c] = m->X[(size_t)dofv[i] * d + c];
+            m->kt = build_kdtree(d, P, N, opts.leaf_m);
+            m->vertex_of_dof.resize(N);
+            m->dof_of_vertex.assign(M, -1);
+            for (int i = 0; i < N; ++i) {
+                int v = dofv[m->kt.perm[i]];
+                m->vertex_of_dof[i] = v;
+                m->dof_of_vertex[v] = i;
+            }
+        }
+
+        // ---- vertex -> cells
+        std::vector<int> vc_ptr(M + 1, 0), vc;
+        for (int c = 0; c < C; ++c)
+            for (int a = 0; a < nv; ++a) vc_ptr[m->T[(size_t)c * nv + a] + 1]++;
+        for (int v = 0; v < M; ++v) vc_ptr[v + 1] += vc_ptr[v];
+        vc.resize(vc_ptr[M]);
+        {
+            std::vector<int> fill(M, 0);
+            for (int c = 0; c < C; ++c)
+                for (int a = 0; a < nv; ++a) {
+                    int v = m->T[(size_t)c * nv + a];
+                    vc[vc_ptr[v] + fill[v]++] = c;
+                }
+        }
+
+        // ---- quadrature cloud: interior cells first (increasing id), then exterior;
+        // element rule R3: triangle points with barycentric weight 2/3 on vertex q,
+        // interval 3-point Gauss (left to right from stored vertex 0).
+        std::vector<int> cell_order;
+        for (int c = 0; c < C; ++c)
+            if (m->inter[c]) cell_order.push_back(c);
+        int nint = (int)cell_order.size();
+        for (int c = 0; c < C; ++c)
+            if (!m->inter[c]) cell_order.push_back(c);
+        std::vector<int> cell_slot(C);
+        for (int i = 0; i < C; ++i) cell_slot[cell_order[i]] = i;
+        double bq[3][3], wq[3];
+        if (d == 2) {
+            for (int q = 0; q < 3; ++q) {
+                for (int a = 0; a < 3; ++a) bq[q][a] = (a == q) ? 2.0 / 3.0 : 1.0 / 6.0;
+                wq[q] = 1.0 / 3.0;
+            }
+        } else {
+            double g = 0.5 * std::sqrt(0.6);
+            double tt[3] = {0.5 - g, 0.5, 0.5 + g}, ww[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+            for (int q = 0; q < 3; ++q) {
+                bq[q][0] = 1.0 - tt[q];
+                bq[q][1] = tt[q];
+                bq[q][2] = 0.0;
+                wq[q] = ww[q];
+            }
+        }
+        m->nQ = C * NQ;
+        m->nQint = nint * NQ;
+        const int nQ = m->nQ;
+        std::vector<double> qx((size_t)nQ * d), qw(nQ), qb((size_t)nQ * 3);
+        m->qcell_host.resize(nQ);
+        for (int i = 0; i < C; ++i) {
+            int c = cell_order[i];
+            const int *t = &m->T[(size_t)c * nv];
+            for (int q = 0; q < NQ; ++q) {
+                int id = i * NQ + q;
+                for (int dim = 0; dim < d; ++dim) {
+                    double v = 0.0;
+                    for (int a = 0; a < nv; ++a) v += bq[q][a] * m->X[(size_t)t[a] * d + dim];
+                    qx[(size_t)dim * nQ + id] = v;
+                }
+                qw[id] = wq[q] * meas[c];
+                m->qcell_host[id] = c;
+                for (int a = 0; a < 3; ++a) qb[(size_t)id * 3 + a] = bq[q][a];
+            }
+        }
+        auto qpos = [&](int id, int dim) { return qx[(size_t)dim * nQ + id]; };
+
+        // ---- touching unordered pairs with >= 1 interior cell (canonical orientation R1')
+        struct Pair {
+            int type, w, pv[3], qv[3], loc[5], nl;
+        };
+        std::vector<Pair> pairs;
+        {
+            std::vector<int> mark(C, -1);
+            for (int c = 0; c < C; ++c) {
+                const int *t = &m->T[(size_t)c * nv];
+                std::vector<int> nb;
+                for (int a = 0; a < nv; ++a)
+                    for (int k2 = vc_ptr[t[a]]; k2 < vc_ptr[t[a] + 1]; ++k2) {
+                        int c2 = vc[k2];
+                        if (mark[c2] != c) {
+                            mark[c2] = c;
+                            nb.push_back(c2);
+                        }
+                    }
+                std::sort(nb.begin(), nb.end());
+                for (int c2 : nb) {
+                    if (c2 < c) continue;
+                    if (!m->inter[c] && !m->inter[c2]) continue;
+                    int first = c, second = c2;
+                    if (c != c2 && m->inter[c] != m->inter[c2]) {
+                        first = m->inter[c] ? c : c2;
+                        second = m->inter[c] ? c2 : c;
+                    }
+                    const int *u1 = &m->T[(size_t)first * nv], *u2 = &m->T[(size_t)second * nv];
+                    Pair pr{};
+                    pr.w = (first == second) ? 1 : 2;
+                    for (int a = 0; a < 3; ++a) pr.pv[a] = pr.qv[a] = -1;
+                    if (first == second) {
+                        pr.type = 3;
+                        for (int a = 0; a < nv; ++a) pr.pv[a] = pr.qv[a] = u1[a];
+                    } else {
+                        int shared[3], ns = 0;
+                        for (int a = 0; a < nv; ++a)
+                            for (int b = 0; b < nv; ++b)
+                                if (u1[a] == u2[b]) shared[ns++] = u1[a];
+                        if (ns == 1) {
+                            pr.type = 1;
+                            int k1 = 1, k3 = 1;
+                            pr.pv[0] = pr.qv[0] = shared[0];
+                            for (int a = 0; a < nv; ++a) {
+                                if (u1[a] != shared[0]) pr.pv[k1++] = u1[a];
+                                if (u2[a] != shared[0]) pr.qv[k3++] = u2[a];
+                            }
+                        } else {
+                            VFD_REQUIRE(d == 2 && ns == 2, VFD_EINVAL, "non-conforming cells " + std::to_string(c));
+                            pr.type = 2;
+                            // shared edge in the first cell's order, apexes last
+                            pr.pv[0] = shared[0];
+                            pr.pv[1] = shared[1];
+                            for (int a = 0; a < 3; ++a)
+                                if (u1[a] != shared[0] && u1[a] != shared[1]) pr.pv[2] = u1[a];
+                            pr.qv[0] = shared[0];
+                            pr.qv[1] = shared[1];
+                            for (int a = 0; a < 3; ++a)
+                                if (u2[a] != shared[0] && u2[a] != shared[1]) pr.qv[2] = u2[a];
+                        }
+                    }
+                    // local DoF list
+                    if (d == 2) {
+                        if (pr.type == 3) { pr.nl = 3; for (int a = 0; a < 3; ++a) pr.loc[a] = pr.pv[a]; }
+                        else if (pr.type == 2) { pr.nl = 4; pr.loc[0] = pr.pv[0]; pr.loc[1] = pr.pv[1]; pr.loc[2] = pr.pv[2]; pr.loc[3] = pr.qv[2]; }
+                        else { pr.nl = 5; pr.loc[0] = pr.pv[0]; pr.loc[1] = pr.pv[1]; pr.loc[2] = pr.pv[2]; pr.loc[3] = pr.qv[1]; pr.loc[4] = pr.qv[2]; }
+                    } else {
+                        if (pr.type == 3) { pr.nl = 2; pr.loc[0] = pr.pv[0]; pr.loc[1] = pr.pv[1]; }
+                        else { pr.nl = 3; pr.loc[0] = pr.pv[0]; pr.loc[1] = pr.pv[1]; pr.loc[2] = pr.qv[1]; }
+                    }
+                    pairs.push_back(pr);
+                }
+            }
+        }
+        m->npairs = (int)pairs.size();
+
+        // ---- B/M sparsity over DoFs and deterministic gather lists
+        std::vector<std::vector<int>> rows(N);
+        for (auto &pr : pairs)
+            for (int i = 0; i < pr.nl; ++i) {
+                int di = m->dof_of_vertex[pr.loc[i]];
+                if (di < 0) continue;
+                for (int j = 0; j < pr.nl; ++j) {
+                    int dj = m->dof_of_vertex[pr.loc[j]];
+                    if (dj >= 0) rows[di].push_back(dj);
+                }
+            }
+        std::vector<int> rowptr(N + 1, 0), colidx;
+        for (int i = 0; i < N; ++i) {
+            auto &r = rows[i];
+            std::sort(r.begin(), r.end());
+            r.erase(std::unique(r.begin(), r.end()), r.end());
+            rowptr[i + 1] = rowptr[i] + (int)r.size();
+        }
+        colidx.reserve(rowptr[N]);
+        for (auto &r : rows) colidx.insert(colidx.end(), r.begin(), r.end());
+        m->nnz = rowptr[N];
+        auto entry = [&](int i, int j) {
+            auto b = colidx.begin() + rowptr[i], e = colidx.begin() + rowptr[i + 1];
+            return (int)(std::lower_bound(b, e, j) - colidx.begin());
+        };
+        {
+            std::vector<int> cnt(m->nnz + 1, 0);
+            std::vector<std::pair<int, int>> cont;  // (entry, idx)
+            for (int p = 0; p < m->npairs; ++p) {
+                auto &pr = pairs[p];
+                for (int i = 0; i < pr.nl; ++i) {
+                    int di = m->dof_of_vertex[pr.loc[i]];
+                    if (di < 0) continue;
+                    for (int j = 0; j < pr.nl; ++j) {
+                        int dj = m->dof_of_vertex[pr.loc[j]];
+                        if (dj < 0) continue;
+                        cont.push_back({entry(di, dj), p * 25 + i * 5 + j});
+                    }
+                }
+            }
+            std::stable_sort(cont.begin(), cont.end(),
+                             [](const std::pair<int, int> &a, const std::pair<int, int> &b) { return a.first < b.first; });
+            std::vector<int> ptr(m->nnz + 1, 0), idx(cont.size());
+            for (size_t k2 = 0; k2 < cont.size(); ++k2) {
+                ptr[cont[k2].first + 1]++;
+                idx[k2] = cont[k2].second;
+            }
+            for (int e = 0; e < m->nnz; ++e) ptr[e + 1] += ptr[e];
+            m->ncontribB = (int64_t)cont.size();
+            m->cB_ptr.upload(ptr);
+            m->cB_idx.upload(idx);
+        }
+        {
+            // mass: entry(i,j) += 2 w_q lam_a(q) lam_b(q) rho(q) over interior cells (eq. e:m)
+            struct MC {
+                int e, q;
+                double c;
+            };
+            std::vector<MC> cont;
+            for (int i = 0; i < nint; ++i) {
+                int c = cell_order[i];
+                const int *t = &m->T[(size_t)c * nv];
+                for (int a = 0; a < nv; ++a) {
+                    int di = m->dof_of_vertex[t[a]];
+                    if (di < 0) continue;
+                    for (int b = 0; b < nv; ++b) {
+                        int dj = m->dof_of_vertex[t[b]];
+                        if (dj < 0) continue;
+                        int e = entry(di, dj);
+                        for (int q = 0; q < NQ; ++q) {
+                            int id = i * NQ + q;
+                            cont.push_back({e, id, 2.0 * qw[id] * qb[(size_t)id * 3 + a] * qb[(size_t)id * 3 + b]});
+                        }
+                    }
+                }
+            }
+            std::stable_sort(cont.begin(), cont.end(), [](const MC &a, const MC &b) { return a.e < b.e; });
+            std::vector<int> ptr(m->nnz + 1, 0), qi(cont.size());
+            std::vector<double> cf(cont.size());
+            for (size_t k2 = 0; k2 < cont.size(); ++k2) {
+                ptr[cont[k2].e + 1]++;
+                qi[k2] = cont[k2].q;
+                cf[k2] = cont[k2].c;
+            }
+            for (int e = 0; e < m->nnz; ++e) ptr[e + 1] += ptr[e];
+            m->ncontribM = (int64_t)cont.size();
+            m->cM_ptr.upload(ptr);
+            m->cM_q.upload(qi);
+            m->cM_coef.upload(cf);
+        }
+        m->rowptr.upload(rowptr);
+        m->colidx.upload(colidx);
+        {
+            std::vector<int> pinfo((size_t)m->npairs * 8);
+            for (int p = 0; p < m->npairs; ++p) {
+                auto &pr = pairs[p];
+                pinfo[(size_t)p * 8 + 0] = pr.type;
+                pinfo[(size_t)p * 8 + 1] = pr.w;
+                for (int a = 0; a < 3; ++a) {
+                    pinfo[(size_t)p * 8 + 2 + a] = pr.pv[a];
+                    pinfo[(size_t)p * 8 + 5 + a] = pr.qv[a];
+                }
+            }
+            m->pair_info.upload(pinfo);
+        }
+
+        // ---- K tree: support-extended boxes (Sec. 5.1, omega^e), Chebyshev nodes
+        Tree &kt = m->kt;
+        const int k = m->k, p = m->p, nnode = kt.nnode, nleaf = kt.nleaf, fl = kt.first_leaf();
+        for (int lf = 0; lf < nleaf; ++lf) {
+            int node = fl + lf;
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+            for (int i = kt.begin[node]; i < kt.end[node]; ++i) {
+                int v = m->vertex_of_dof[i];
+                for (int k2 = vc_ptr[v]; k2 < vc_ptr[v + 1]; ++k2) {
+                    const int *t = &m->T[(size_t)vc[k2] * nv];
+                    for (int a = 0; a < nv; ++a)
+                        for (int c = 0; c < d; ++c) {
+                            lo[c] = std::min(lo[c], m->X[(size_t)t[a] * d + c]);
+                            hi[c] = std::max(hi[c], m->X[(size_t)t[a] * d + c]);
+                        }
+                }
+            }
+            for (int c = 0; c < d; ++c) {
+                kt.lo[(size_t)node * d + c] = lo[c];
+                kt.hi[(size_t)node * d + c] = hi[c];
+            }
+        }
+        for (int node = fl - 1; node >= 0; --node)
+            for (int c = 0; c < d; ++c) {
+                kt.lo[(size_t)node * d + c] = std::min(kt.lo[(size_t)(2 * node + 1) * d + c], kt.lo[(size_t)(2 * node + 2) * d + c]);
+                kt.hi[(size_t)node * d + c] = std::max(kt.hi[(size_t)(2 * node + 1) * d + c], kt.hi[(size_t)(2 * node + 2) * d + c]);
+            }
+        pad_boxes(kt, d);
+        std::vector<double> kcheb((size_t)nnode * k * d);
+        for (int n = 0; n < nnode; ++n) cheb_box(d, p, &kt.lo[(size_t)n * d], &kt.hi[(size_t)n * d], &kcheb[(size_t)n * k * d]);
+        m->kt_cheb.upload(kcheb);
+        m->kt_begin.upload(kt.begin);
+        m->kt_end.upload(kt.end);
+
+        // ---- dual traversal: admissible (far) and inadmissible leaf (near) pairs
+        {
+            std::vector<std::vector<int>> farl(nnode), nearl(nleaf);
+            std::vector<std::pair<int, int>> stack{{0, 0}};
+            while (!stack.empty()) {
+                auto [a, b] = stack.back();
+                stack.pop_back();
+                const double *alo = &kt.lo[(size_t)a * d], *ahi = &kt.hi[(size_t)a * d];
+                const double *blo = &kt.lo[(size_t)b * d], *bhi = &kt.hi[(size_t)b * d];
+                if (admissible(d, opts.lambda, alo, ahi, blo, bhi, 0.0)) {
+                    farl[a].push_back(b);
+                } else if (kt.is_leaf(a)) {
+                    nearl[a - fl].push_back(b - fl);
+                } else {
+                    for (int ca = 2 * a + 1; ca <= 2 * a + 2; ++ca)
+                        for (int cb = 2 * b + 1; cb <= 2 * b + 2; ++cb) stack.push_back({ca, cb});
+                }
+            }
+            for (auto &l : farl) std::sort(l.begin(), l.end());
+            for (auto &l : nearl) std::sort(l.begin(), l.end());
+            csr_from_lists(farl, m->far_ptr_h, m->far_col_h);
+            csr_from_lists(nearl, m->near_ptr_h, m->near_col_h);
+            m->nfar = (int)m->far_col_h.size();
+            m->nnear = (int)m->near_col_h.size();
+            m->near_off_h.assign(m->nnear + 1, 0);
+            std::vector<int> src(m->nnear, -1), prow(m->nnear);
+            for (int a = 0; a < nleaf; ++a)
+                for (int e = m->near_ptr_h[a]; e < m->near_ptr_h[a + 1]; ++e) {
+                    int b = m->near_col_h[e];
+                    prow[e] = a;
+                    int na = kt.end[fl + a] - kt.begin[fl + a], nb = kt.end[fl + b] - kt.begin[fl + b];
+                    m->near_off_h[e + 1] = m->near_off_h[e] + (int64_t)na * nb;
+                    if (a > b) {
+                        auto bb = m->near_col_h.begin() + m->near_ptr_h[b], ee = m->near_col_h.begin() + m->near_ptr_h[b + 1];
+                        auto it = std::lower_bound(bb, ee, a);
+                        VFD_REQUIRE(it != ee && *it == a, VFD_ECUDA, "near list not symmetric");
+                        src[e] = (int)(it - m->near_col_h.begin());
+                    }
+                }
+            m->near_entries = m->near_off_h[m->nnear];
+            m->far_ptr.upload(m->far_ptr_h);
+            m->far_col.upload(m->far_col_h);
+            m->near_ptr.upload(m->near_ptr_h);
+            m->near_col.upload(m->near_col_h);
+            m->near_off.upload(m->near_off_h);
+            m->near_src.upload(src);
+            m->near_pair_row.upload(prow);
+        }
+
+        // ---- per-leaf point sets and DoF supports; leaf bases U (Sec. 5.3, R5)
+        {
+            std::vector<int> lp_ptr(nleaf + 1, 0), lp_pts;
+            std::vector<std::vector<std::pair<int, double>>> supp(N);
+            std::vector<double> U;
+            std::vector<int> Uoff(nleaf);
+            std::vector<int> mark(C, -1);
+            std::vector<double> lag(k);
+            for (int lf = 0; lf < nleaf; ++lf) {
+                int node = fl + lf;
+                std::vector<int> lc;
+                for (int i = kt.begin[node]; i < kt.end[node]; ++i) {
+                    int v = m->vertex_of_dof[i];
+                    for (int k2 = vc_ptr[v]; k2 < vc_ptr[v + 1]; ++k2)
+                        if (mark[vc[k2]] != lf) {
+                            mark[vc[k2]] = lf;
+                            lc.push_back(vc[k2]);
+                        }
+                }
+                std::sort(lc.begin(), lc.end());
+                std::vector<int> cpos(lc.size());
+                int base = (int)lp_pts.size();
+                for (size_t j = 0; j < lc.size(); ++j)
+                    for (int q = 0; q < NQ; ++q) lp_pts.push_back(cell_slot[lc[j]] * NQ + q);
+                lp_ptr[lf + 1] = (int)lp_pts.size();
+                m->max_leaf_pts = std::max(m->max_leaf_pts, lp_ptr[lf + 1] - lp_ptr[lf]);
+                m->max_leaf_size = std::max(m->max_leaf_size, kt.end[node] - kt.begin[node]);
+                Uoff[lf] = (int)U.size();
+                for (int i = kt.begin[node]; i < kt.end[node]; ++i) {
+                    int v = m->vertex_of_dof[i];
+                    for (int k2 = vc_ptr[v]; k2 < vc_ptr[v + 1]; ++k2) {
+                        int c = vc[k2];
+                        int j = (int)(std::lower_bound(lc.begin(), lc.end(), c) - lc.begin());
+                        const int *t = &m->T[(size_t)c * nv];
+                        int a = 0;
+                        while (t[a] != v) ++a;
+                        for (int q = 0; q < NQ; ++q) {
+                            int id = cell_slot[c] * NQ + q;
+                            supp[i].push_back({j * NQ + q, qw[id] * qb[(size_t)id * 3 + a]});
+                        }
+                    }
+                    m->max_supp = std::max(m->max_supp, (int)supp[i].size());
+                    // U_{i,alpha} = sum_{q in supp(i)} w_q psi_i(q) l_alpha(q)
+                    std::vector<double> row(k, 0.0);
+                    for (auto &sc : supp[i]) {
+                        int id = lp_pts[base + sc.first];
+                        double x[3];
+                        for (int c = 0; c < d; ++c) x[c] = qpos(id, c);
+                        lagrange_box(d, p, &kt.lo[(size_t)node * d], &kt.hi[(size_t)node * d], x, lag.data());
+                        for (int al = 0; al < k; ++al) row[al] += sc.second * lag[al];
+                    }
+                    U.insert(U.end(), row.begin(), row.end());
+                }
+            }
+            std::vector<int> sp(N + 1, 0), sl;
+            std::vector<double> sc;
+            for (int i = 0; i < N; ++i) {
+                sp[i + 1] = sp[i] + (int)supp[i].size();
+                for (auto &e : supp[i]) {
+                    sl.push_back(e.first);
+                    sc.push_back(e.second);
+                }
+            }
+            m->lp_ptr.upload(lp_ptr);
+            m->lp_pts.upload(lp_pts);
+            m->supp_ptr.upload(sp);
+            m->supp_loc.upload(sl);
+            m->supp_coef.upload(sc);
+            m->U64.upload(U);
+            m->kt_Uoff.upload(Uoff);
+        }
+        // transfers E_c[beta][alpha] = l^parent_alpha(xi^c_beta)
+        {
+            std::vector<double> E((size_t)nnode * k * k, 0.0), lag(k);
+            for (int c = 1; c < nnode; ++c) {
+                int par = (c - 1) / 2;
+                for (int be = 0; be < k; ++be) {
+                    lagrange_box(d, p, &kt.lo[(size_t)par * d], &kt.hi[(size_t)par * d], &kcheb[((size_t)c * k + be) * d], lag.data());
+                    for (int al = 0; al < k; ++al) E[((size_t)c * k + be) * k + al] = lag[al];
+                }
+            }
+            m->E64.upload(E);
+        }
+
+        // ---- density sweep trees (Sec. 6.2): targets = interior points, sources = all points
+        {
+            std::vector<double> Pt((size_t)m->nQint * d), Ps((size_t)nQ * d);
+            for (int i = 0; i < nQ; ++i)
+                for (int c = 0; c < d; ++c) {
+                    Ps[(size_t)i * d + c] = qpos(i, c);
+                    if (i < m->nQint) Pt[(size_t)i * d + c] = qpos(i, c);
+                }
+            m->tt = build_kdtree(d, Pt, m->nQint, opts.rho_leaf_m);
+            m->st = build_kdtree(d, Ps, nQ, opts.rho_leaf_m);
+            pad_boxes(m->tt, d);
+            pad_boxes(m->st, d);
+            Tree &tt = m->tt, &st = m->st;
+            std::vector<double> tch((size_t)tt.nnode * k * d), sch((size_t)st.nnode * k * d);
+            for (int n = 0; n < tt.nnode; ++n) cheb_box(d, p, &tt.lo[(size_t)n * d], &tt.hi[(size_t)n * d], &tch[(size_t)n * k * d]);
+            for (int n = 0; n < st.nnode; ++n) cheb_box(d, p, &st.lo[(size_t)n * d], &st.hi[(size_t)n * d], &sch[(size_t)n * k * d]);
+            // source moments xhat_s[beta] = sum_{q in s} l_beta(q) w_q (geometry only)
+            std::vector<double> xs((size_t)st.nnode * k, 0.0), lag(k);
+            for (int n = 0; n < st.nnode; ++n)
+                for (int i = st.begin[n]; i < st.end[n]; ++i) {
+                    int id = st.perm[i];
+                    double x[3];
+                    for (int c = 0; c < d; ++c) x[c] = qpos(id, c);
+                    lagrange_box(d, p, &st.lo[(size_t)n * d], &st.hi[(size_t)n * d], x, lag.data());
+                    for (int b = 0; b < k; ++b) xs[(size_t)n * k + b] += lag[b] * qw[id];
+                }
+            // rectangular dual traversal
+            std::vector<std::vector<int>> farl(tt.nnode), nearl(tt.nleaf);
+            std::vector<std::pair<int, int>> stack{{0, 0}};
+            const double mind = 2.0 * m->h_max;
+            while (!stack.empty()) {
+                auto [a, b] = stack.back();
+                stack.pop_back();
+                const double *alo = &tt.lo[(size_t)a * d], *ahi = &tt.hi[(size_t)a * d];
+                const double *blo = &st.lo[(size_t)b * d], *bhi = &st.hi[(size_t)b * d];
+                bool la = tt.is_leaf(a), lb = st.is_leaf(b);
+                if (admissible(d, opts.rho_lambda, alo, ahi, blo, bhi, mind)) {
+                    farl[a].push_back(b);
+                } else if (la && lb) {
+                    nearl[a - tt.first_leaf()].push_back(b);
+                } else if (la) {
+                    stack.push_back({a, 2 * b + 1});
+                    stack.push_back({a, 2 * b + 2});
+                } else if (lb) {
+                    stack.push_back({2 * a + 1, b});
+                    stack.push_back({2 * a + 2, b});
+                } else {
+                    for (int ca = 2 * a + 1; ca <= 2 * a + 2; ++ca)
+                        for (int cb = 2 * b + 1; cb <= 2 * b + 2; ++cb) stack.push_back({ca, cb});
+                }
+            }
+            for (auto &l : farl) std::sort(l.begin(), l.end());
+            for (auto &l : nearl) std::sort(l.begin(), l.end());
+            std::vector<int> fp, fc, np_, nc;
+            csr_from_lists(farl, fp, fc);
+            csr_from_lists(nearl, np_, nc);
+            m->nrfar = (int)fc.size();
+            m->nrnear = (int)nc.size();
+            m->rnear_pairs = 0;
+            for (int a = 0; a < tt.nleaf; ++a)
+                for (int e = np_[a]; e < np_[a + 1]; ++e) {
+                    int ta = tt.first_leaf() + a, sb = nc[e];
+                    m->rnear_pairs += (int64_t)(tt.end[ta] - tt.begin[ta]) * (st.end[sb] - st.begin[sb]);
+                }
+            m->rfar_ptr.upload(fp);
+            m->rfar_col.upload(fc);
+            m->rnear_ptr.upload(np_);
+            m->rnear_col.upload(nc);
+            m->tt_begin.upload(tt.begin);
+            m->tt_end.upload(tt.end);
+            m->tt_perm.upload(tt.perm);
+            m->st_begin.upload(st.begin);
+            m->st_end.upload(st.end);
+            m->st_perm.upload(st.perm);
+            m->tt_lo.upload(tt.lo);
+            m->tt_hi.upload(tt.hi);
+            m->tt_cheb.upload(tch);
+            m->st_cheb.upload(sch);
+            m->st_xhat.upload(xs);
+        }
+
+        // ---- load-vector gather lists: DoF -> (cell, local vertex) of interior cells
+        {
+            std::vector<std::vector<int>> l(N);
+            for (int c = 0; c < C; ++c) {
+                if (!m->inter[c]) continue;
+                for (int a = 0; a < nv; ++a) {
+                    int di = m->dof_of_vertex[m->T[(size_t)c * nv + a]];
+                    if (di >= 0) l[di].push_back(c * nv + a);
+                }
+            }
+            std::vector<int> ptr, idx;
+            csr_from_lists(l, ptr, idx);
+            m->ld_ptr.upload(ptr);
+            m->ld_idx.upload(idx);
+        }
+
+        // ---- device geometry
+        {
+            std::vector<double> vx((size_t)M * d);
+            for (int v = 0; v < M; ++v)
+                for (int c = 0; c < d; ++c) vx[(size_t)c * M + v] = m->X[(size_t)v * d + c];
+            m->vx.upload(vx);
+            m->cells.upload(m->T);
+            m->vdof.upload(m->dof_of_vertex);
+            m->qx.upload(qx);
+            m->qw.upload(qw);
+            m->qcell.upload(m->qcell_host);
+            m->qbary.upload(qb);
+            std::vector<double> gx, gw;
+            gauss_legendre01(opts.n_sing, gx, gw);
+            m->gl_x.upload(gx);
+            m->gl_w.upload(gw);
+            gauss_legendre01(9, gx, gw);
+            m->gl9_x.upload(gx);
+            m->gl9_w.upload(gw);
+        }
+    } catch (...) {
+        delete m;
+        throw;
+    }
+    return m;
+}
+
+}  // namespace vfd

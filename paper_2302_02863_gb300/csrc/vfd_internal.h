@@ -1,0 +1,242 @@
+// Internal declarations of the vfd library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/vfd.h"
+
+namespace vfd {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+
+struct Error {
+    vfd_status st;
+    std::string msg;
+};
+
+#define VFD_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            throw ::vfd::Error{e_ == cudaErrorMemoryAllocation ? VFD_ENOMEM : VFD_ECUDA,        \
+                               std::string(#call) + ": " + cudaGetErrorString(e_)};            \
+    } while (0)
+
+#define VFD_REQUIRE(cond, st, msg)                                                             \
+    do {                                                                                       \
+        if (!(cond)) throw ::vfd::Error{st, msg};                                              \
+    } while (0)
+
+// device buffer (RAII, cudaMalloc/cudaFree)
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) VFD_CUDA(cudaMalloc(&p, sizeof(T) * count));
+    }
+    void upload(const std::vector<T> &h) {
+        alloc(h.size());
+        if (!h.empty()) VFD_CUDA(cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    }
+    void zero(cudaStream_t st) {
+        if (n) VFD_CUDA(cudaMemsetAsync(p, 0, sizeof(T) * n, st));
+    }
+    size_t bytes() const { return sizeof(T) * n; }
+};
+
+constexpr int KMAX = 64;       // max rank p^d handled by the kernels
+constexpr int PMAX = 8;        // max Chebyshev nodes per dimension
+constexpr int NSMAX = 16;      // max Gauss points per direction of the singular rules
+constexpr int NQ = 3;          // element-rule points per cell (triangle and interval)
+
+// ---------------------------------------------------------------------------
+// device view of a field descriptor
+// ---------------------------------------------------------------------------
+struct DField {
+    int nodal;          // 1: P1 values at vertices (vals)
+    int nF, nG, nT;     // term counts
+    int squash;
+    int kmax;           // max |k_i| of the Fourier rows (fast path when <= 4)
+    double c0, lo, hi;
+    const double *rows; // device, (nF + nG + nT) * 5
+    const double *vals; // device, n_vert (nodal)
+};
+
+// ---------------------------------------------------------------------------
+// cluster tree (complete binary, heap numbering: children of n are 2n+1, 2n+2)
+// ---------------------------------------------------------------------------
+struct Tree {
+    int L = 0;                     // leaf level; levels 0..L
+    int nnode = 0, nleaf = 0;
+    std::vector<int> begin, end;   // index range in tree order, per node
+    std::vector<int> perm;         // tree position -> original item
+    std::vector<double> lo, hi;    // boxes, nnode * d
+    int first_leaf() const { return (1 << L) - 1; }
+    bool is_leaf(int n) const { return n >= first_leaf(); }
+};
+
+// ---------------------------------------------------------------------------
+// mesh handle: geometry-only data, built once per mesh
+// ---------------------------------------------------------------------------
+struct MeshData {
+    int d = 2, M = 0, C = 0, N = 0;
+    int nQ = 0, nQint = 0;
+    vfd_mesh_opts opts{};
+    double h_max = 0.0;
+    int k = 16, p = 4;
+
+    std::vector<double> X;           // host coords M*d
+    std::vector<int> T;              // host cells C*(d+1)
+    std::vector<uint8_t> inter;      // host
+    std::vector<int> dof_of_vertex;  // host
+    std::vector<int> vertex_of_dof;  // host
+    std::vector<int> qcell_host;     // host, point -> cell (interior cells first)
+
+    // device geometry
+    DBuf<double> vx;       // M*d, SoA: vx[i*M + v]
+    DBuf<int> cells;       // C*(d+1)
+    DBuf<int> vdof;        // M: dof of vertex or -1
+    DBuf<double> qx;       // nQ*d SoA
+    DBuf<double> qw;       // nQ
+    DBuf<int> qcell;       // nQ
+    DBuf<double> qbary;    // nQ*3
+
+    // touching pairs (unordered, canonical orientation)
+    int npairs = 0;
+    DBuf<int> pair_info;   // npairs * 8: type, w(1|2), pv0..2, qv0..2
+    // B/M sparsity (DoF CSR) and deterministic gather lists
+    int nnz = 0;
+    DBuf<int> rowptr, colidx;
+    DBuf<int> cB_ptr, cB_idx;             // entry -> list of pair*25 + li*5 + lj
+    DBuf<int> cM_ptr, cM_q;               // entry -> list of interior point ids
+    DBuf<double> cM_coef;                 //   with coefficient 2 w lam_i lam_j
+    int64_t ncontribB = 0, ncontribM = 0;
+
+    // K tree (over DoFs; DoF index = tree position)
+    Tree kt;
+    DBuf<int> kt_begin, kt_end;
+    DBuf<double> kt_cheb;      // nnode * k * d (node-major, point, dim)
+    DBuf<double> U64;          // per leaf: (end-begin) x k row-major, offsets kt_Uoff
+    DBuf<int> kt_Uoff;         // nleaf
+    DBuf<double> E64;          // nnode * k * k (E_c[beta][alpha]); root unused
+    // admissible blocks (both orders), CSR by row node
+    int nfar = 0;
+    std::vector<int> far_ptr_h, far_col_h;
+    DBuf<int> far_ptr, far_col;
+    // inadmissible leaf pairs (both orders), CSR by row leaf
+    int nnear = 0;
+    int64_t near_entries = 0;
+    std::vector<int> near_ptr_h, near_col_h;
+    std::vector<int64_t> near_off_h;
+    DBuf<int> near_ptr, near_col;
+    DBuf<int64_t> near_off;    // offset of block (row-major |sigma| x |sigma'|)
+    DBuf<int> near_src;        // per block: index of the computed block it is the transpose of, or -1
+    DBuf<int> near_pair_row;   // per block: row leaf (for launch over blocks)
+    // per-leaf point sets for the near-block build
+    DBuf<int> lp_ptr, lp_pts;          // leaf -> element-rule points of the cells in its supports
+    DBuf<int> supp_ptr, supp_loc;      // DoF -> (index into its leaf's point list, coefficient)
+    DBuf<double> supp_coef;
+    int max_leaf_pts = 0, max_leaf_size = 0, max_supp = 0;
+
+    // density sweep: target tree (interior points) and source tree (all points)
+    Tree tt, st;
+    DBuf<int> tt_begin, tt_end, tt_perm, st_begin, st_end, st_perm;
+    DBuf<double> tt_lo, tt_hi;          // target boxes (for the downsweep basis)
+    DBuf<double> tt_cheb, st_cheb;      // nnode * k * d
+    DBuf<double> st_xhat;               // source node moments sum_q l_b(q) w_q, nnode_s * k
+    int nrfar = 0;
+    DBuf<int> rfar_ptr, rfar_col;       // by target node
+    int nrnear = 0;
+    int64_t rnear_pairs = 0;
+    DBuf<int> rnear_ptr, rnear_col;     // by target leaf
+    DBuf<double> gl_x, gl_w;            // Gauss-Legendre on [0,1], n_sing points
+    DBuf<double> gl9_x, gl9_w;          // 9-point rule for the tail
+
+    // load assembly (exact P1 mass)
+    DBuf<int> ld_ptr, ld_idx;           // DoF -> list of cell*(d+1)+a contributions
+};
+
+// ---------------------------------------------------------------------------
+// operator handle: per-field data
+// ---------------------------------------------------------------------------
+struct OpData {
+    MeshData *m = nullptr;
+    int precision = VFD_FP64;
+    double s_bar = 0.9;
+    bool check_fields = true;
+    DField fs{}, fk{};
+    DBuf<double> f_rows_s, f_rows_k, f_vals_s, f_vals_k;
+    DBuf<double> q_s, q_lk;            // at all quadrature points
+    DBuf<double> kc_s, kc_lk;          // at K-tree Chebyshev nodes
+    DBuf<double> tc_s, tc_lk, sc_s, sc_lk;  // density trees' Chebyshev nodes
+    DBuf<double> valB, valM, valBM;    // CSR values
+    DBuf<double> rho;                  // interior points, canonical order
+    DBuf<double> S64;                  // nfar * k * k
+    DBuf<double> D64;                  // near entries
+    DBuf<float> S32, D32, U32, E32;    // FP32 copies (VFD_FP32)
+    // apply workspace
+    int ws_nrhs = 0;
+    DBuf<double> xhat, yhat;           // nnode * k * ws_nrhs
+    DBuf<float> xhat32, yhat32;
+    DBuf<double> xin, yout;            // staging for host pointers
+    // solver workspace
+    DBuf<double> cg_r, cg_p, cg_q, cg_x, cg_b, cg_z;
+    DBuf<double> cg_red;               // reduction partials
+    DBuf<double> cg_scal;              // device scalars
+    DBuf<int> cg_flag;
+    DBuf<int> errflag;
+    cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};   // captured CG chunks (FP64 K, FP32 K)
+    const void *cg_key[2] = {nullptr, nullptr};
+};
+
+// ---------------------------------------------------------------------------
+// host setup (mesh_setup.cpp)
+// ---------------------------------------------------------------------------
+MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell, const int32_t *cells,
+                     const uint8_t *inter, const vfd_mesh_opts &opts);
+void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w);
+void cheb_nodes_1d(int p, double lo, double hi, double *out);
+
+// ---------------------------------------------------------------------------
+// kernels (launch wrappers)
+// ---------------------------------------------------------------------------
+// assemble.cu
+void launch_field_points(const MeshData &m, OpData &op, cudaStream_t st);
+void launch_singular_B(const MeshData &m, OpData &op, DBuf<double> &Lbuf, cudaStream_t st);
+void launch_gather_B(const MeshData &m, OpData &op, const DBuf<double> &Lbuf, cudaStream_t st);
+void launch_density(const MeshData &m, OpData &op, cudaStream_t st);
+void launch_gather_M(const MeshData &m, OpData &op, cudaStream_t st);
+void launch_coupling_build(const MeshData &m, OpData &op, cudaStream_t st);
+void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st);
+void launch_convert_fp32(const MeshData &m, OpData &op, cudaStream_t st);
+void launch_load(const MeshData &m, const double *f, double *F, cudaStream_t st);
+// apply.cu
+void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
+                    bool lowp, cudaStream_t st, const int *skip);
+void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
+                 cudaStream_t st);
+// solve.cu
+void release_graphs(OpData &op);
+vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
+                    int max_it, int *iters, double *relres, cudaStream_t st);
+
+}  // namespace vfd

@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Exact mode (lambda = rho_lambda = 0: every K block dense, rho by the direct
+masked sum) must match the oracle to rounding (<= 1e-11 relative); with the
+H^2 parts on, polynomial kernels (gamma = |x-y|^2, exactly interpolated by
+Chebyshev degree 3) must match to rounding, and real kernels within the
+interpolation error the test states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2302_02863_gb300 import vfd  # noqa: E402
+
+
+def _maps(mesh_gpu, ref):
+    dof, n = vfd.vfd_mesh_dofs(mesh_gpu)
+    assert n == ref.N
+    sel = dof >= 0
+    assert np.array_equal(sel, ref.dof >= 0)
+    return dof[sel], ref.dof[sel]          # GPU index, oracle index (same vertices)
+
+
+def _gpu_matrix(op, n, parts=vfd.VFD_PART_ALL):
+    """A[:, j] for all j by applying the operator to the identity (nrhs = n)."""
+    X = torch.eye(n, dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    vfd.vfd_apply_parts(op, parts, X, Y)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy().T.copy()        # row r of Y is A e_r = column r
+
+
+def _to_oracle(Ag, gi, oi):
+    n = len(gi)
+    A = np.zeros((n, n))
+    A[np.ix_(oi, oi)] = Ag[np.ix_(gi, gi)]
+    return A
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.fixture(scope="module")
+def small_disk():
+    m = synth.disk_mesh(7, R=1.3, jitter=0.2, seed=11)
+    s = synth.config2_s_field()
+    k = synth.random_fourier_field(21, 0.5)
+    ref = oracle.assemble(m, s, k, s_bar=0.9, n_sing=3)
+    return m, s, k, ref
+
+
+def test_exact_mode_parts_and_rho(small_disk):
+    m, s, k, ref = small_disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16, lam=0.0, rho_lambda=0.0)
+    op = vfd.vfd_assemble(mesh, s, k, 0.9)
+    gi, oi = _maps(mesh, ref)
+    n = ref.N
+    for part, R in ((vfd.VFD_PART_B, ref.B), (vfd.VFD_PART_M, ref.M), (vfd.VFD_PART_KNEAR, ref.K)):
+        A = _to_oracle(_gpu_matrix(op, n, part), gi, oi)
+        assert _rel(A, R) < 1e-12, (part, _rel(A, R))
+    A = _to_oracle(_gpu_matrix(op, n), gi, oi)
+    assert _rel(A, ref.A) < 1e-12
+    rho = torch.empty(mesh.info["n_qint"], dtype=torch.float64, device="cuda")
+    vfd.vfd_op_rho(op, rho)
+    assert _rel(rho.cpu().numpy(), ref.rho) < 1e-12
+
+
+def test_polynomial_kernel_h2_is_exact():
+    """s = -2: gamma = |x-y|^2 is a polynomial of degree 2 per variable, so the
+    Chebyshev interpolant with p = 4 is exact and the H^2 operator (tree,
+    admissible lists, bases, transfers, sweeps, point-level density sweep)
+    must reproduce the dense oracle to rounding."""
+    m = synth.disk_mesh(12, R=1.3, jitter=0.2, seed=5)
+    s = synth.const_field(-2.0)
+    k = synth.fourier_field(0.0, [[1, 1, 0, 0.0, 0.0]])
+    ref = oracle.assemble(m, s, k, s_bar=2.0 / 3.0, n_sing=3)
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=8, cheb_p=4, lam=0.75, rho_leaf_m=16,
+                        rho_lambda=0.75)
+    assert mesh.info["far_blocks"] > 0 and mesh.info["rho_far_blocks"] > 0
+    op = vfd.vfd_assemble(mesh, s, k, 2.0 / 3.0, flags=vfd.VFD_ASSEMBLE_UNCHECKED)
+    gi, oi = _maps(mesh, ref)
+    n = ref.N
+    Kg = _to_oracle(_gpu_matrix(op, n, vfd.VFD_PART_KNEAR | vfd.VFD_PART_KFAR), gi, oi)
+    assert _rel(Kg, ref.K) < 1e-11
+    rho = torch.empty(mesh.info["n_qint"], dtype=torch.float64, device="cuda")
+    vfd.vfd_op_rho(op, rho)
+    assert _rel(rho.cpu().numpy(), ref.rho) < 1e-11
+    A = _to_oracle(_gpu_matrix(op, n), gi, oi)
+    assert _rel(A, ref.A) < 1e-11
+
+
+@pytest.mark.parametrize("p,tol", [(4, 5e-4), (6, 2e-5)])
+def test_h2_matvec_error(p, tol):
+    """Real kernel: relative matvec error of the full operator (H^2 for K and
+    for rho) against the dense oracle, for random vectors."""
+    m = synth.disk_mesh(14, R=1.1, jitter=0.2, seed=9)
+    s = synth.config2_s_field()
+    k = synth.random_fourier_field(31, 0.5)
+    ref = oracle.assemble(m, s, k, s_bar=0.9, n_sing=3)
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16, cheb_p=p, lam=0.75, rho_leaf_m=32,
+                        rho_lambda=0.75)
+    assert mesh.info["far_blocks"] > 0
+    op = vfd.vfd_assemble(mesh, s, k, 0.9)
+    gi, oi = _maps(mesh, ref)
+    rng = np.random.default_rng(1)
+    Xo = rng.standard_normal((4, ref.N))
+    Xg = np.zeros_like(Xo)
+    Xg[:, gi] = Xo[:, oi]
+    X = torch.tensor(Xg, device="cuda")
+    Y = torch.empty_like(X)
+    vfd.vfd_apply(op, X, Y)
+    torch.cuda.synchronize()
+    Yg = Y.cpu().numpy()
+    Yo = (ref.A @ Xo.T).T
+    err = np.linalg.norm(Yg[:, gi] - Yo[:, oi]) / np.linalg.norm(Yo)
+    assert err < tol, err
+
+
+def test_solve_exact_mode(small_disk):
+    m, s, k, ref = small_disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16, lam=0.0, rho_lambda=0.0)
+    op = vfd.vfd_assemble(mesh, s, k, 0.9)
+    gi, oi = _maps(mesh, ref)
+    F_or = oracle.load(m, np.ones(m.n_vert))
+    U_or = oracle.cholesky_solve(ref.A, F_or)
+    F = torch.zeros(ref.N, dtype=torch.float64, device="cuda")
+    vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device="cuda"), F)
+    Fg = F.cpu().numpy()
+    assert _rel(Fg[gi], F_or[oi]) < 1e-14
+    U = torch.zeros_like(F)
+    st, it, rel = vfd.vfd_solve(op, F, U, rtol=1e-13, max_it=5000)
+    assert st == vfd.VFD_OK and rel[0] < 1e-12
+    Ug = U.cpu().numpy()
+    assert np.linalg.norm(Ug[gi] - U_or[oi]) / np.linalg.norm(U_or) < 1e-8
+
+
+def test_interval_closed_form_problem():
+    """1D, s = 0.3, a = C_{1,0.3}/2, tail (Omega_e = R minus (-1,1)): exact mode
+    parity and the same solution as the oracle."""
+    s0 = 0.3
+    m = synth.interval_mesh(63, R=1.1)
+    s = synth.const_field(s0)
+    k = synth.const_field(math.log(synth.frac_laplacian_const(1, s0) / 2))
+    ref = oracle.assemble(m, s, k, s_bar=s0, n_sing=3, tail=1, R=1.1)
+    mesh = vfd.vfd_mesh(1, m.coords, m.cells, m.cell_is_interior, leaf_m=16, lam=0.0, rho_lambda=0.0, tail_mode=1,
+                        tail_R=1.1)
+    op = vfd.vfd_assemble(mesh, s, k, s0)
+    gi, oi = _maps(mesh, ref)
+    A = _to_oracle(_gpu_matrix(op, ref.N), gi, oi)
+    assert _rel(A, ref.A) < 1e-12
+    F = torch.zeros(ref.N, dtype=torch.float64, device="cuda")
+    vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device="cuda"), F)
+    U = torch.zeros_like(F)
+    st, it, rel = vfd.vfd_solve(op, F, U, rtol=1e-13, max_it=5000)
+    U_or = oracle.cholesky_solve(ref.A, oracle.load(m, np.ones(m.n_vert)))
+    Ug = U.cpu().numpy()
+    assert np.linalg.norm(Ug[gi] - U_or[oi]) / np.linalg.norm(U_or) < 1e-9
+
+
+def test_fp32_operator_refinement(small_disk):
+    """VFD_FP32: K in FP32 for the inner CG, FP64 residuals: the refined
+    solution reaches the FP64 operator's solution."""
+    m, s, k, ref = small_disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16, lam=0.0, rho_lambda=0.0)
+    op64 = vfd.vfd_assemble(mesh, s, k, 0.9)
+    op32 = vfd.vfd_assemble(mesh, s, k, 0.9, precision=vfd.VFD_FP32)
+    n = ref.N
+    F = torch.ones(n, dtype=torch.float64, device="cuda")
+    U64 = torch.zeros_like(F)
+    U32 = torch.zeros_like(F)
+    vfd.vfd_solve(op64, F, U64, rtol=1e-12, max_it=5000)
+    st, it, rel = vfd.vfd_solve(op32, F, U32, rtol=1e-10, max_it=5000)
+    assert st == vfd.VFD_OK and rel[0] <= 1e-10
+    a, b = U32.cpu().numpy(), U64.cpu().numpy()
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-8
+    # the FP32 operator itself differs from FP64 only at FP32 rounding of K
+    X = torch.randn(n, dtype=torch.float64, device="cuda")
+    Y1, Y2 = torch.empty_like(X), torch.empty_like(X)
+    vfd.vfd_apply(op64, X, Y1)
+    vfd.vfd_apply(op32, X, Y2)
+    d = (torch.linalg.norm(Y1 - Y2) / torch.linalg.norm(Y1)).item()
+    assert d < 1e-5
+
+
+def test_host_pointers_roundtrip(small_disk):
+    """Host (numpy) buffers through the same entry points give the same result."""
+    m, s, k, ref = small_disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16, lam=0.0, rho_lambda=0.0)
+    op = vfd.vfd_assemble(mesh, s, k, 0.9)
+    n = ref.N
+    x = np.random.default_rng(3).standard_normal(n)
+    yh = np.zeros(n)
+    vfd.vfd_apply(op, x, yh)
+    X = torch.tensor(x, device="cuda")
+    Y = torch.empty_like(X)
+    vfd.vfd_apply(op, X, Y)
+    torch.cuda.synchronize()
+    assert np.array_equal(yh, Y.cpu().numpy())
+
+
+def test_field_range_is_checked():
+    m = synth.disk_mesh(4, R=1.3, jitter=0.0, seed=1)
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16)
+    with pytest.raises(vfd.VfdError) as e:
+        vfd.vfd_assemble(mesh, synth.const_field(0.95), synth.const_field(0.0), 0.9)
+    assert e.value.status == vfd.VFD_EINVAL
