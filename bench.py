@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the variable-order fractional FE operator on GB300.
+
+Metric: H^2 stiffness matvec DOF*RHS/s (with the CG time to tolerance).
+Workload (default 'disk33k'): the 2D unit disk + annulus to R = 1.1, 96 rings
+(34,027 vertices, 27,361 interior DoFs), s = 0.25 + 0.5(0.5 + 0.5 sin 2 pi x1
+cos 2 pi x2), log a a seeded 16-mode Fourier field (sigma 0.5), s_bar = 0.9,
+leaf size 64, tensor Chebyshev rank 16, lambda = 0.75, FP64, 1 RHS, CG to
+1e-10, f = 1.
+
+One step = one pass of the whole hot path on device-resident inputs:
+vfd_assemble (field values, coupling blocks, dense near blocks, singular
+near field, density sweep, weighted mass) followed by vfd_solve (CG to
+rtol).  value = n_dof * nrhs * (operator applications in the step) / step
+time, i.e. matvec throughput delivered inside the full assemble + solve step;
+ms_per_step is the time to a 1e-10 solution from the fields.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py --impl reference ...     (the CPU oracle on a bounded sample)
+
+Multi-GPU: replicas only (the method has no data-parallel exchange step at
+one mesh); each rank solves its own replica, value sums the ranks, time is
+the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H^2 stiffness matvec DOF*RHS/s and CG time-to-tolerance (assemble + solve step)"
+UNIT = "DOF*RHS/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--workload", default="disk33k")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--rtol", type=float, default=1e-10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg (bounded sample of the same workload)
+# ----------------------------------------------------------------------------
+def oracle_step_value(K=24, rtol=1e-10):
+    """The oracle as it stands (dense FP64 assembly + plain CG) on a smaller
+    disk of the same workload family; returns (value, seconds, n_dof, iters)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    m = synth.disk_mesh(K, R=1.1, jitter=0.2, seed=2000 + K)
+    s = synth.config2_s_field()
+    k = synth.random_fourier_field(2001, 0.5)
+    t0 = time.perf_counter()
+    A = oracle.assemble(m, s, k, s_bar=0.9, n_sing=3)
+    F = oracle.load(m, np.ones(m.n_vert))
+    U, it = oracle.cg(A.A, F, rtol)
+    t = time.perf_counter() - t0
+    return A.N * (it + 1) / t, t, A.N, it
+
+
+def reference_arm(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    K = 20
+    for _ in range(args.warmup):
+        oracle_step_value(K, args.rtol)
+    vals, secs, n, its = [], [], 0, []
+    for _ in range(args.steps):
+        v, t, n, it = oracle_step_value(K, args.rtol)
+        vals.append(v)
+        secs.append(t)
+        its.append(it)
+    tot = sum(secs)
+    value = n * sum(i + 1 for i in its) / tot
+    cores = oracle.num_threads()
+    sample = f"disk K={K} ({n} DoFs): dense FP64 oracle assembly + CG to {args.rtol:g}, per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2302_02863_gb300 import vfd
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    vfd.load()
+    m, s, k, prm = synth.workload(args.workload)
+    prec = vfd.VFD_FP64 if args.precision == "fp64" else vfd.VFD_FP32
+    mesh = vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"],
+                        lam=0.75, rho_lambda=0.75, tail_mode=prm["tail"], tail_R=prm["R"])
+    info = mesh.info
+    n = mesh.n_dof
+    stream = torch.cuda.current_stream()
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device="cuda"), F)
+    U = torch.zeros_like(F)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def step(timed=False):
+        op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec,
+                              flags=vfd.VFD_ASSEMBLE_TIMED if timed else 0)
+        U.zero_()
+        st, it, rel = vfd.vfd_solve(op, F, U, rtol=args.rtol, max_it=100000)
+        return op, st, int(it[0]), float(rel[0])
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, iters, rels, phases = [], [], [], []
+    for _ in range(args.steps):
+        flush.zero_()                        # L2 flush between timed steps (not timed)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        op, st, it, rel = step(timed=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1000.0)
+        iters.append(it)
+        rels.append(rel)
+        phases.append(vfd.vfd_op_timings(op))
+        del op
+    clk = clocks.stop()
+    tot = sum(times)
+    n_apply = sum(i + 2 for i in iters)          # CG iterations + initial and final residual
+    if dist:
+        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    value = world * n * n_apply / tot
+
+    # ---- e2e: the same step through the C ABI with HOST buffers (copies timed)
+    Fh = F.cpu().numpy().copy()
+    Uh = np.zeros(n)
+    for _ in range(2):
+        op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec)
+        Uh[:] = 0
+        vfd.vfd_solve(op, Fh, Uh, rtol=args.rtol, max_it=100000, stream=0)
+        del op
+    torch.cuda.synchronize()
+    e2e_t, e2e_apply = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec, stream=0)
+        Uh[:] = 0
+        st, it, rel = vfd.vfd_solve(op, Fh, Uh, rtol=args.rtol, max_it=100000, stream=0)
+        e2e_t += time.perf_counter() - t0
+        e2e_apply += int(it[0]) + 2
+        del op
+    e2e_value = world * n * e2e_apply / e2e_t
+
+    # ---- dominant-kernel roofline, measured live on the launching stream
+    op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec, flags=vfd.VFD_ASSEMBLE_TIMED)
+    ph = {key: statistics.mean(p[key] for p in phases) for key in phases[0]}
+    X = torch.randn(n, dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    parts_near = vfd.VFD_PART_B | vfd.VFD_PART_M | vfd.VFD_PART_KNEAR   # one kernel: fused leaf/near/CSR rows
+    for _ in range(5):
+        vfd.vfd_apply_parts(op, parts_near, X, Y)
+    R = 50
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(R):
+        vfd.vfd_apply_parts(op, parts_near, X, Y)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_leaf = ev[0].elapsed_time(ev[1]) / R / 1000.0
+    ev[0].record(stream)
+    for _ in range(R):
+        vfd.vfd_apply(op, X, Y)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_apply = ev[0].elapsed_time(ev[1]) / R / 1000.0
+    wbytes = 8 if prec == vfd.VFD_FP64 else 4
+    leaf_bytes = info["near_entries"] * wbytes + info["nnz"] * 12 + (n + 1) * 4 + 2 * n * 8
+    leaf_flops = 2.0 * (info["near_entries"] + info["nnz"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    if prec == vfd.VFD_FP64:
+        # FP64 FMA rate bounds this kernel on GB300 (1 FMA per 8 bytes of the
+        # streamed matrix > 1.25 TFLOP/s / 6.8 TB/s); nominal FP64 peak
+        roof = {"bound": "alu", "achieved": leaf_flops / t_leaf / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": leaf_flops / t_leaf / 1e12 / 1.25, "traffic": None,
+                "kernel": "k_near_csr<double,double> (near panels + B+M CSR rows)", "peak_source": "nominal FP64 1.25 TFLOP/s",
+                "hbm_frac": leaf_bytes / t_leaf / 1e9 / hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": leaf_bytes / t_leaf / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": leaf_bytes / t_leaf / 1e9 / hbm, "traffic": None,
+                "kernel": "k_near_csr<float,float> (near panels + B+M CSR rows)", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    roof["algorithmic_bytes"] = leaf_bytes
+    roof["launch_us"] = t_leaf * 1e6
+    roof["traffic"] = _traffic_from_profile(args.workload, args.precision)
+
+    # apply: far projections, node sums, coupling, row kernel, far expansion
+    apply_kernels = 5 if info["far_blocks"] > 0 else 1
+    mean_it = statistics.mean(iters)
+    replays = math.ceil(mean_it / 8)
+    per_solve = apply_kernels + 4 + replays * 8 * (apply_kernels + 3) + apply_kernels + 2
+    per_assemble = 4 + 1 + 2 + 2 + 1 + 1 + 1 + (4 if prec == vfd.VFD_FP32 else 0)
+    gpu_launches = args.steps * (per_assemble + per_solve)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        v, t, ns, it = oracle_step_value(24, args.rtol)
+        cpu = {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"disk K=24 ({ns} DoFs, same fields): dense FP64 oracle assembly + plain CG to "
+                         f"{args.rtol:g}, one step, {t:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == vfd.VFD_FP64 else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_dof": n, "nrhs": 1, "precision": args.precision,
+                       "rtol": args.rtol, "leaf": prm["leaf"], "rank": info["rank"], "lambda": 0.75,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "cg_iters": iters[0], "relres": rels[0],
+            "assemble_ms": ph["total"], "phases_ms": {k2: round(v2, 3) for k2, v2 in ph.items()},
+            "solve_ms": 1000 * tot / args.steps - ph["total"], "apply_us": t_apply * 1e6,
+            "apply_dof_rhs_per_s": n / t_apply,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
+            "gpu_launches": gpu_launches, "clocks": clk, "mesh": info,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _traffic_from_profile(workload, precision):
+    """DRAM bytes per launch of the roofline kernel from the committed ncu
+    summary, if one exists for this workload and precision (else null)."""
+    p = os.path.join(ROOT, "profiles", f"k_near_csr_{workload}_{precision}.json")
+    try:
+        return json.load(open(p)).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+if __name__ == "__main__":
+    main()

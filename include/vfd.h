@@ -72,8 +72,22 @@ enum {
 
 /* Flags of vfd_assemble. */
 enum {
-    VFD_ASSEMBLE_UNCHECKED = 1  /* skip the check 0 <= s <= s_bar < 1 (lets the
+    VFD_ASSEMBLE_UNCHECKED = 1, /* skip the check 0 <= s <= s_bar < 1 (lets the
                                    tests use polynomial kernels, e.g. s = -2) */
+    VFD_ASSEMBLE_TIMED = 2      /* record CUDA events around every assembly phase
+                                   (read back with vfd_op_timings) */
+};
+
+/* Phases reported by vfd_op_timings (milliseconds of device time). */
+enum {
+    VFD_T_FIELDS = 0,    /* field values at element points and Chebyshev nodes */
+    VFD_T_COUPLING = 1,  /* coupling blocks S of K (Sec. 5.3) */
+    VFD_T_NEAR = 2,      /* dense inadmissible leaf blocks of K (Sec. 5.2) */
+    VFD_T_DENSITY = 3,   /* density rho, H^2 sweep + tail (Sec. 6.2, 7.1.1) */
+    VFD_T_SINGULAR = 4,  /* singular near field B, local matrices (Sec. 4) */
+    VFD_T_GATHER = 5,    /* CSR gathers of B and M (and the FP32 copies) */
+    VFD_T_TOTAL = 6,
+    VFD_T_COUNT = 7
 };
 
 /* Mesh-level options (geometry only; fixed for the life of the mesh handle). */
@@ -143,7 +157,7 @@ vfd_status vfd_mesh_dofs(vfd_mesh_t mesh, int32_t *dof_of_vertex, int64_t *n_dof
  * [9] inadmissible leaf blocks of K  [10] dense near entries of K
  * [11] quadrature points  [12] interior quadrature points
  * [13] admissible blocks of the density sweep  [14] near point pairs of the
- * density sweep. */
+ * density sweep  [15] stored near entries (row panels, padded to 4 columns). */
 vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info);
 
 /* Assemble the operator for the fields s and log kappa (Algorithm 1):
@@ -188,6 +202,18 @@ vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *str
  * the point nearest to stored vertex 0, 1, 2; interval: Gauss points left
  * to right in the stored orientation).  rho: host or device, n_qint doubles. */
 vfd_status vfd_op_rho(vfd_op_t op, double *rho, void *stream);
+
+/* Device time per assembly phase (VFD_T_* order) of the vfd_assemble call
+ * that created op, if it was given VFD_ASSEMBLE_TIMED; ms: host, n entries
+ * (at most VFD_T_COUNT are written).  Returns VFD_EINVAL if not recorded. */
+vfd_status vfd_op_timings(vfd_op_t op, double *ms, int n);
+
+/* Self-test of the library's table-driven FP64 logarithm / exponential used
+ * for the kernel evaluations (Tang's table-driven method): out[i] =
+ * log(x[i]) (which = 0) or exp(x[i]) (which = 1), computed on the device.
+ * x, out: device pointers, n entries.  Needs a mesh handle for the tables.
+ * Valid inputs: x > 0 normal (log), |x| < 700 (exp). */
+vfd_status vfd_selftest_math(vfd_mesh_t mesh, int which, int64_t n, const double *x, double *out, void *stream);
 
 void vfd_free_op(vfd_op_t op);
 void vfd_free_mesh(vfd_mesh_t mesh);

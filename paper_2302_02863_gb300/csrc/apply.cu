@@ -1,187 +1,362 @@
-// Operator apply Y = A X = (B + M) X + K_near X + K_far X (Sec. 3, eq. e:decomp):
-//   K_far by the H^2 product (Sec. 5.3, eq. eq:triple_product_factored with
-//   nested bases): leaf upsweep xhat = U^T x, transfer upsweep, coupling
-//   yhat = S xhat over the admissible list, transfer downsweep, leaf
-//   expansion U yhat;  K_near by the dense inadmissible leaf blocks;  B + M by
-//   CSR.  The last kernel fuses the leaf expansion, the near blocks and the
-//   CSR rows, writing each output row once.
+// Operator apply Y = A X = (B + M) X + K_near X + K_far X (Sec. 3, eq. e:decomp).
+//
+// K_far is the H^2 product of Sec. 5.3 (eq. eq:triple_product_factored):
+// y_sigma += U_sigma (sum_{sigma'} S_{sigma sigma'} U_{sigma'}^T x_sigma').  The
+// bases of all levels are the nested ones (U E ... E); the apply uses them
+// flattened per level (Ul^(l), precomputed at setup from U and the transfer
+// matrices), which turns the level-by-level transfer chain into independent
+// work:
+//   1. k_far_proj:   per (leaf, level) the projection Ul^(l)_leaf^T x_leaf
+//   2. k_far_sum:    per node, xhat = sum of its leaves' projections
+//   3. k_far_couple: per node, yhat = sum_e S_e xhat[col e] (CTA per node)
+//   4. k_near_csr:   per row, the near panel row and the B + M CSR row
+//                    (concurrently with 1-3, which run on a high-priority
+//                    side stream)
+//   5. k_far_expand: after the join, Y[i] += sum_l Ul^(l)[i] . yhat[ancestor]
 // Tree order is the DoF order, so every leaf's x and y are contiguous.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace vfd {
 
-// xhat[r][leaf][a] = sum_i U[i][a] x[i]    (thread per (leaf, a))
-template <class T, class A>
-__global__ void k_up_leaf(int k, int nleaf, int fl, const int *__restrict__ kb, const int *__restrict__ ke,
-                          const int *__restrict__ Uoff, const T *__restrict__ U, const double *__restrict__ X,
-                          int64_t ld, A *__restrict__ xhat, int64_t hstride, const int *skip)
+template <class T>
+struct Vec;
+template <>
+struct Vec<double> {
+    using V = double2;
+    static constexpr int W = 2;
+};
+template <>
+struct Vec<float> {
+    using V = float4;
+    static constexpr int W = 4;
+};
+
+__device__ __forceinline__ void fma_v(const double2 a, const double2 x, double &s0, double &s1)
 {
+    s0 = fma(a.x, x.x, s0);
+    s1 = fma(a.y, x.y, s1);
+}
+__device__ __forceinline__ void fma_v(const float4 a, const float4 x, float &s0, float &s1)
+{
+    s0 = fmaf(a.x, x.x, s0);
+    s1 = fmaf(a.y, x.y, s1);
+    s0 = fmaf(a.z, x.z, s0);
+    s1 = fmaf(a.w, x.w, s1);
+}
+
+struct FarView {
+    int use;         // apply K_far
+    int lmin, L, nlev, k, N;
+};
+
+// ---------------------------------------------------------------------------
+// 1. leaf-level projections  part[r][lv][leaf][a] = sum_{i in leaf} Ul^(lmin+lv)[i][a] x[i]
+// ---------------------------------------------------------------------------
+template <class T, class A>
+__global__ void __launch_bounds__(128)
+k_far_proj(FarView F, int fl, int nleaf, const int *__restrict__ kb, const int *__restrict__ ke,
+           const T *__restrict__ Ul, const double *__restrict__ X, int64_t ld, A *__restrict__ part, const int *skip)
+{
+    __shared__ A red[128];
     if (skip && *skip) return;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nleaf * k) return;
-    int lf = t / k, al = t - lf * k, r = blockIdx.y;
-    int b = kb[fl + lf], e = ke[fl + lf];
-    const T *u = U + Uoff[lf] + al;
+    const int leaf = blockIdx.x, lv = blockIdx.y, r = blockIdx.z, k = F.k;
+    const int b = kb[fl + leaf], e = ke[fl + leaf];
+    const int kk = min(k, (int)blockDim.x);
+    const int parts = blockDim.x / kk;
+    const int al = threadIdx.x % kk, pt = threadIdx.x / kk;
+    const T *u = Ul + ((size_t)lv * F.N) * k;
     const double *x = X + (size_t)r * ld;
-    A acc = 0;
-    for (int i = b; i < e; ++i) acc += (A)u[(size_t)(i - b) * k] * (A)x[i];
-    xhat[(size_t)r * hstride + (size_t)(fl + lf) * k + al] = acc;
-}
-
-// xhat[parent][a] = sum_children sum_b E_c[b][a] xhat[c][b]  (level l)
-template <class T, class A>
-__global__ void k_up_level(int k, int first, int count, const T *__restrict__ E, A *__restrict__ xhat,
-                           int64_t hstride, const int *skip)
-{
-    if (skip && *skip) return;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count * k) return;
-    int n = first + t / k, al = t % k;
-    A *xh = xhat + (size_t)blockIdx.y * hstride;
-    A acc = 0;
-    for (int c = 2 * n + 1; c <= 2 * n + 2; ++c) {
-        const T *Ec = E + (size_t)c * k * k + al;
-        const A *xc = xh + (size_t)c * k;
-        for (int be = 0; be < k; ++be) acc += (A)Ec[(size_t)be * k] * xc[be];
+    for (int a0 = 0; a0 < k; a0 += kk) {
+        A acc = 0;
+        if (pt < parts)
+            for (int i = b + pt; i < e; i += parts) acc += (A)u[(size_t)i * k + a0 + al] * (A)x[i];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < kk) {
+            A s = 0;
+            for (int q = 0; q < parts; ++q) s += red[q * kk + threadIdx.x];
+            part[(((size_t)r * F.nlev + lv) * nleaf + leaf) * k + a0 + threadIdx.x] = s;
+        }
+        __syncthreads();
     }
-    xh[(size_t)n * k + al] = acc;
 }
 
-// yhat[n][a] = sum_{blocks e of row n} sum_b S_e[a][b] xhat[col e][b]; S stored [b][a]
-template <class T, class A>
-__global__ void k_couple(int k, int nnode, const int *__restrict__ fptr, const int *__restrict__ fcol,
-                         const T *__restrict__ S, const A *__restrict__ xhat, A *__restrict__ yhat, int64_t hstride,
-                         const int *skip)
+// ---------------------------------------------------------------------------
+// 2. node sums  xhat[r][node][a] = sum over the node's leaves of part  (levels
+//    lmin..L); one CTA per node, threads (a, part) over the leaves, reduced
+//    in shared memory
+// ---------------------------------------------------------------------------
+template <class A>
+__global__ void __launch_bounds__(128)
+k_far_sum(FarView F, int nleaf, const A *__restrict__ part, A *__restrict__ xhat, int64_t hs, const int *skip)
 {
+    __shared__ A red[128];
     if (skip && *skip) return;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nnode * k) return;
-    int n = t / k, al = t % k;
-    const A *xh = xhat + (size_t)blockIdx.y * hstride;
-    A acc = 0;
-    for (int e = fptr[n]; e < fptr[n + 1]; ++e) {
-        const T *s = S + (size_t)e * k * k + al;
-        const A *xc = xh + (size_t)fcol[e] * k;
-        for (int be = 0; be < k; ++be) acc += (A)s[(size_t)be * k] * xc[be];
+    const int k = F.k, node = (1 << F.lmin) - 1 + blockIdx.x, r = blockIdx.y;
+    int l = 0;
+    while ((2 << l) - 1 <= node) ++l;
+    const int lv = l - F.lmin, span = 1 << (F.L - l);
+    const int leaf0 = ((node + 1) << (F.L - l)) - 1 - ((1 << F.L) - 1);
+    const int kk = min(k, (int)blockDim.x), parts = blockDim.x / kk;
+    const int al = threadIdx.x % kk, pt = threadIdx.x / kk;
+    const A *p = part + (((size_t)r * F.nlev + lv) * nleaf + leaf0) * k;
+    for (int a0 = 0; a0 < k; a0 += kk) {
+        A s = 0;
+        if (pt < parts)
+            for (int j = pt; j < span; j += parts) s += p[(size_t)j * k + a0 + al];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        if (threadIdx.x < kk) {
+            A t = 0;
+            for (int q = 0; q < parts; ++q) t += red[q * kk + threadIdx.x];
+            xhat[(size_t)r * hs + (size_t)node * k + a0 + threadIdx.x] = t;
+        }
+        __syncthreads();
     }
-    yhat[(size_t)blockIdx.y * hstride + (size_t)n * k + al] = acc;
 }
 
-// yhat[c][b] += sum_a E_c[b][a] yhat[parent][a]  (level l, parents already final)
-template <class T, class A>
-__global__ void k_down_level(int k, int first, int count, const T *__restrict__ E, A *__restrict__ yhat,
-                             int64_t hstride, const int *skip)
-{
-    if (skip && *skip) return;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count * k) return;
-    int c = first + t / k, be = t % k;
-    A *yh = yhat + (size_t)blockIdx.y * hstride;
-    const T *Ec = E + ((size_t)c * k + be) * k;
-    const A *yp = yh + (size_t)((c - 1) / 2) * k;
-    A acc = 0;
-    for (int al = 0; al < k; ++al) acc += (A)Ec[al] * yp[al];
-    yh[(size_t)c * k + be] += acc;
-}
-
-// Y[i] = [U yhat]_i + sum_near D x + sum_csr val x ; block per leaf, warp per row
+// ---------------------------------------------------------------------------
+// 3. coupling  yhat[node][a] = sum_{e in row node} sum_b S_e[b][a] xhat[col e][b]
+//    (S stored [b][a]); one CTA per node: every (block e, a) partial in its own
+//    thread, then a shared-memory sum over the node's blocks
+// ---------------------------------------------------------------------------
 template <class T, class A>
 __global__ void __launch_bounds__(256)
-k_leaf_out(int k, int fl, const int *__restrict__ kb, const int *__restrict__ ke, const int *__restrict__ Uoff,
-           const T *__restrict__ U, const A *__restrict__ yhat, int64_t hstride, int use_far,
-           const int *__restrict__ nptr, const int *__restrict__ ncol, const int64_t *__restrict__ noff,
-           const T *__restrict__ D, int use_near, const int *__restrict__ rowptr, const int *__restrict__ colidx,
-           const double *__restrict__ val, const double *__restrict__ X, int64_t ld, double *__restrict__ Y,
+k_far_couple(FarView F, const int *__restrict__ fptr, const int *__restrict__ fcol, const T *__restrict__ S,
+             const A *__restrict__ xhat, A *__restrict__ yhat, int64_t hs, const int *skip)
+{
+    __shared__ A red[256];
+    if (skip && *skip) return;
+    const int node = blockIdx.x, r = blockIdx.y, k = F.k;
+    const int e0 = fptr[node], ne = fptr[node + 1] - e0;
+    const A *xh = xhat + (size_t)r * hs;
+    const int kk = min(k, (int)blockDim.x), per = blockDim.x / kk;   // blocks handled per pass
+    for (int a0 = 0; a0 < k; a0 += kk) {
+        const int al = threadIdx.x % kk, g = threadIdx.x / kk;
+        A tot = 0;   // meaningful in threads g == 0
+        for (int eb = 0; eb < ne; eb += per) {
+            A acc = 0;
+            const int e = eb + g;
+            if (g < per && e < ne) {
+                const T *sp = S + (size_t)(e0 + e) * k * k + a0 + al;
+                const A *xc = xh + (size_t)fcol[e0 + e] * k;
+                for (int be = 0; be < k; ++be) acc += (A)sp[(size_t)be * k] * xc[be];
+            }
+            red[threadIdx.x] = acc;
+            __syncthreads();
+            if (g == 0)
+                for (int q = 0; q < per && eb + q < ne; ++q) tot += red[q * kk + al];
+            __syncthreads();
+        }
+        if (g == 0) yhat[(size_t)r * hs + (size_t)node * k + a0 + al] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4. rows: one CTA per (leaf, slice of NR rows): the partners' x gathered in
+//    shared memory, warp per row over the contiguous panel entries, the CSR
+//    row, and the far expansion over the levels lmin..L
+// ---------------------------------------------------------------------------
+template <class T, class A>
+__global__ void __launch_bounds__(128)
+k_near_csr(int fl, int NR, const int *__restrict__ kb, const int *__restrict__ ke, const int *__restrict__ nptr,
+           const int *__restrict__ ncol, const int64_t *__restrict__ noff, const int *__restrict__ pw,
+           const int64_t *__restrict__ poff, const int *__restrict__ gcol, const int *__restrict__ goff,
+           const T *__restrict__ D, int use_near, const int *__restrict__ rowptr,
+           const int *__restrict__ colidx, const double *__restrict__ val, FarView F, const T *__restrict__ Ul,
+           const A *__restrict__ yhat, int64_t hs, const double *__restrict__ X, int64_t ld, double *__restrict__ Y,
            const int *skip)
 {
+    using V = typename Vec<T>::V;
+    constexpr int VW = Vec<T>::W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *xg = (T *)smraw;
     if (skip && *skip) return;
-    const int lf = blockIdx.x, r = blockIdx.y;
-    const int b = kb[fl + lf], e = ke[fl + lf];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int lf = blockIdx.x, r = blockIdx.z;
+    const int b_leaf = kb[fl + lf];
+    const int b = b_leaf + blockIdx.y * NR, e = min(ke[fl + lf], b + NR);
+    if (b >= e) return;
     const double *x = X + (size_t)r * ld;
-    const A *yh = yhat + (size_t)r * hstride + (size_t)(fl + lf) * k;
-    for (int i = b + warp; i < e; i += nw) {
-        const int il = i - b;
-        A kacc = 0;
-        if (use_far) {
-            const T *u = U + Uoff[lf] + (size_t)il * k;
-            for (int al = lane; al < k; al += 32) kacc += (A)u[al] * yh[al];
+    const int W = use_near ? pw[lf] : 0;
+    const int64_t P0 = use_near ? poff[lf] : 0;
+    if (use_near) {
+        const int *gc = gcol + goff[lf];
+        for (int t = threadIdx.x; t < W; t += blockDim.x) {
+            int j = gc[t];
+            xg[t] = j >= 0 ? (T)x[j] : (T)0;
         }
+        __syncthreads();
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const A *yh = yhat + (size_t)r * hs;
+    for (int i = b + warp; i < e; i += nw) {
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
         if (use_near) {
-            for (int ne = nptr[lf]; ne < nptr[lf + 1]; ++ne) {
-                int c = ncol[ne];
-                int cb = kb[fl + c], nb = ke[fl + c] - cb;
-                const T *drow = D + noff[ne] + (size_t)il * nb;
-                const double *xc = x + cb;
-                for (int j = lane; j < nb; j += 32) kacc += (A)drow[j] * (A)xc[j];
+            const V *row = (const V *)(D + P0 + (size_t)(i - b_leaf) * W);
+            const V *xv = (const V *)xg;
+            const int nv = W / VW;
+            int c = lane;
+            for (; c + 96 < nv; c += 128) {
+                V a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
+                fma_v(a0, xv[c], s0, s1);
+                fma_v(a1, xv[c + 32], s2, s3);
+                fma_v(a2, xv[c + 64], s0, s1);
+                fma_v(a3, xv[c + 96], s2, s3);
+            }
+            for (; c < nv; c += 32) fma_v(row[c], xv[c], s0, s1);
+        }
+        A fa = 0;
+        if (F.use) {
+            // lanes cover (level, alpha) pairs: 32/k levels per instruction when k <= 32
+            const int per = F.k <= 32 ? 32 / F.k : 1;
+            const int kk = F.k <= 32 ? F.k : 32;
+            for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
+                const int l = l0 + lane / kk;
+                if (lane / kk < per && l <= F.L) {
+                    const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
+                    const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
+                    const A *y = yh + (size_t)node * F.k;
+                    for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
+                }
             }
         }
-        double acc = (double)kacc;
-        if (val) {
-            for (int c = rowptr[i] + lane; c < rowptr[i + 1]; c += 32) acc += val[c] * x[colidx[c]];
-        }
+        double acc = (double)((s0 + s1) + (s2 + s3)) + (double)fa;
+        if (val)
+            for (int c = rowptr[i] + lane; c < rowptr[i + 1]; c += 32) acc = fma(val[c], x[colidx[c]], acc);
         acc = warp_sum(acc);
         if (lane == 0) Y[(size_t)r * ld + i] = acc;
     }
 }
 
+// ---------------------------------------------------------------------------
+// 5. far expansion after the join: Y[i] += sum_l Ul^(l)[i] . yhat[ancestor_l(i)]
+//    (warp per row, lanes over (level, alpha))
+// ---------------------------------------------------------------------------
+template <class T, class A>
+__global__ void __launch_bounds__(128)
+k_far_expand(FarView F, int fl, const int *__restrict__ leaf_of, const T *__restrict__ Ul, const A *__restrict__ yhat,
+             int64_t hs, double *__restrict__ Y, int64_t ld, const int *skip)
+{
+    if (skip && *skip) return;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, r = blockIdx.y;
+    if (i >= F.N) return;
+    const int lf = leaf_of[i];
+    const A *yh = yhat + (size_t)r * hs;
+    const int per = F.k <= 32 ? 32 / F.k : 1;
+    const int kk = F.k <= 32 ? F.k : 32;
+    A fa = 0;
+    for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
+        const int l = l0 + lane / kk;
+        if (lane / kk < per && l <= F.L) {
+            const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
+            const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
+            const A *y = yh + (size_t)node * F.k;
+            for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
+        }
+    }
+    double v = warp_sum((double)fa);
+    if (lane == 0) Y[(size_t)r * ld + i] += v;
+}
+
+// ---------------------------------------------------------------------------
 template <class T, class A>
 static void apply_impl(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
-                       const T *U, const T *E, const T *S, const T *D, A *xhat, A *yhat, cudaStream_t st,
+                       const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, cudaStream_t st,
                        const int *skip)
 {
     const int k = m.k, fl = m.kt.first_leaf(), L = m.kt.L, nnode = m.kt.nnode;
     const int64_t hs = (int64_t)nnode * k;
-    const bool far = (parts & VFD_PART_KFAR) && m.nfar > 0;
+    FarView F;
+    F.use = ((parts & VFD_PART_KFAR) && m.nfar > 0) ? 1 : 0;
+    F.lmin = m.far_lmin;
+    F.L = L;
+    F.nlev = F.use ? L - m.far_lmin + 1 : 0;
+    F.k = k;
+    F.N = m.N;
     const bool near = (parts & VFD_PART_KNEAR) && m.nnear > 0;
     const double *val = nullptr;
     if ((parts & VFD_PART_B) && (parts & VFD_PART_M)) val = op.valBM.p;
     else if (parts & VFD_PART_B) val = op.valB.p;
     else if (parts & VFD_PART_M) val = op.valM.p;
-    const int TB = 128;
-    if (far) {
-        dim3 g(cdiv((long long)m.kt.nleaf * k, TB), nrhs);
-        k_up_leaf<T, A><<<g, TB, 0, st>>>(k, m.kt.nleaf, fl, m.kt_begin.p, m.kt_end.p, m.kt_Uoff.p, U, X, ld, xhat, hs,
-                                          skip);
-        for (int l = L - 1; l >= 0; --l) {
-            int first = (1 << l) - 1, count = 1 << l;
-            dim3 gl(cdiv((long long)count * k, TB), nrhs);
-            k_up_level<T, A><<<gl, TB, 0, st>>>(k, first, count, E, xhat, hs, skip);
-        }
-        dim3 gc(cdiv((long long)nnode * k, TB), nrhs);
-        k_couple<T, A><<<gc, TB, 0, st>>>(k, nnode, m.far_ptr.p, m.far_col.p, S, xhat, yhat, hs, skip);
-        for (int l = 1; l <= L; ++l) {
-            int first = (1 << l) - 1, count = 1 << l;
-            dim3 gl(cdiv((long long)count * k, TB), nrhs);
-            k_down_level<T, A><<<gl, TB, 0, st>>>(k, first, count, E, yhat, hs, skip);
-        }
+    FarView Fn = F;
+    Fn.use = 0;   // the expansion runs after the join (k_far_expand)
+    if (F.use) {
+        // far chain on the high-priority side stream, concurrent with the rows
+        VFD_CUDA(cudaEventRecord(op.ev_fork, st));
+        VFD_CUDA(cudaStreamWaitEvent(op.side, op.ev_fork, 0));
+        dim3 gp(m.kt.nleaf, F.nlev, nrhs);
+        k_far_proj<T, A><<<gp, 128, 0, op.side>>>(F, fl, m.kt.nleaf, m.kt_begin.p, m.kt_end.p, Ul, X, ld, part, skip);
+        const int nn = nnode - ((1 << F.lmin) - 1);
+        dim3 gs(nn, nrhs);
+        k_far_sum<A><<<gs, 128, 0, op.side>>>(F, m.kt.nleaf, part, xhat, hs, skip);
+        dim3 gc(nnode, nrhs);
+        k_far_couple<T, A><<<gc, 256, 0, op.side>>>(F, m.far_ptr.p, m.far_col.p, S, xhat, yhat, hs, skip);
     }
-    dim3 go(m.kt.nleaf, nrhs);
-    k_leaf_out<T, A><<<go, 256, 0, st>>>(k, fl, m.kt_begin.p, m.kt_end.p, m.kt_Uoff.p, U, yhat, hs, far ? 1 : 0,
-                                         m.near_ptr.p, m.near_col.p, m.near_off.p, D, near ? 1 : 0, m.rowptr.p,
-                                         m.colidx.p, val, X, ld, Y, skip);
+    const int NR = 16;
+    dim3 go(m.kt.nleaf, cdiv(m.max_leaf_size, NR), nrhs);
+    size_t shm = near ? (size_t)m.max_panel_w * sizeof(T) : 0;
+    k_near_csr<T, A><<<go, 128, shm, st>>>(fl, NR, m.kt_begin.p, m.kt_end.p, m.near_ptr.p, m.near_col.p, m.near_off.p,
+                                           m.panel_w.p, m.panel_off.p, m.gcol.p, m.gcol_off.p, D, near ? 1 : 0,
+                                           m.rowptr.p, m.colidx.p, val, Fn, Ul, yhat, hs, X, ld, Y, skip);
+    if (F.use) {
+        VFD_CUDA(cudaEventRecord(op.ev_join, op.side));
+        VFD_CUDA(cudaStreamWaitEvent(st, op.ev_join, 0));
+        dim3 ge(cdiv(m.N, 4), nrhs);
+        k_far_expand<T, A><<<ge, 128, 0, st>>>(F, fl, m.vleaf.p, Ul, yhat, hs, Y, ld, skip);
+    }
     VFD_CUDA(cudaGetLastError());
+}
+
+static void ensure_streams(OpData &op)
+{
+    if (!op.side) {
+        // the far chain is a short sequence of small launches: give it priority
+        // so its CTAs are not queued behind the row kernel
+        int lo = 0, hi = 0;
+        VFD_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        VFD_CUDA(cudaStreamCreateWithPriority(&op.side, cudaStreamNonBlocking, hi));
+        VFD_CUDA(cudaEventCreateWithFlags(&op.ev_fork, cudaEventDisableTiming));
+        VFD_CUDA(cudaEventCreateWithFlags(&op.ev_join, cudaEventDisableTiming));
+    }
+}
+
+void release_streams(OpData &op)
+{
+    if (op.side) {
+        cudaStreamSynchronize(op.side);
+        cudaStreamDestroy(op.side);
+        cudaEventDestroy(op.ev_fork);
+        cudaEventDestroy(op.ev_join);
+        op.side = nullptr;
+    }
 }
 
 // parts: VFD_PART_* mask; lowp: use the FP32 copies of K (VFD_FP32 operators)
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                     bool lowp, cudaStream_t st, const int *skip)
 {
+    ensure_streams(op);
+    const int nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
     const size_t need = (size_t)m.kt.nnode * m.k * nrhs;
+    const size_t needp = (size_t)std::max(nlev, 1) * m.kt.nleaf * m.k * nrhs;
     if (lowp) {
         if (op.xhat32.n < need) {
             op.xhat32.alloc(need);
             op.yhat32.alloc(need);
         }
-        apply_impl<float, float>(m, op, parts, X, Y, nrhs, ld, op.U32.p, op.E32.p, op.S32.p, op.D32.p, op.xhat32.p,
-                                 op.yhat32.p, st, skip);
+        if (op.P32.n < needp) op.P32.alloc(needp);
+        apply_impl<float, float>(m, op, parts, X, Y, nrhs, ld, op.Ul32.p, op.S32.p, op.D32.p, op.xhat32.p, op.yhat32.p,
+                                 op.P32.p, st, skip);
     } else {
         if (op.xhat.n < need) {
             op.xhat.alloc(need);
             op.yhat.alloc(need);
         }
-        apply_impl<double, double>(m, op, parts, X, Y, nrhs, ld, m.U64.p, m.E64.p, op.S64.p, op.D64.p, op.xhat.p,
-                                   op.yhat.p, st, skip);
+        if (op.P64.n < needp) op.P64.alloc(needp);
+        apply_impl<double, double>(m, op, parts, X, Y, nrhs, ld, m.Ul64.p, op.S64.p, op.D64.p, op.xhat.p, op.yhat.p,
+                                   op.P64.p, st, skip);
     }
 }
 

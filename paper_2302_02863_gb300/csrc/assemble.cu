@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_singular(SingParams P, double *__restri
     }
 }
 
-void launch_singular_B(const MeshData &m, OpData &op, DBuf<double> &Lbuf, cudaStream_t st)
+void launch_singular_B_generic(const MeshData &m, OpData &op, DBuf<double> &Lbuf, cudaStream_t st)
 {
     Lbuf.alloc((size_t)m.npairs * 25);
     if (!m.npairs) return;
@@ -345,7 +345,7 @@ __global__ void k_rho_coupling(int d, int k, int nnode_t, const int *__restrict_
                                const double *__restrict__ tch, const double *__restrict__ ts,
                                const double *__restrict__ tlk, const double *__restrict__ sch,
                                const double *__restrict__ ss, const double *__restrict__ slk,
-                               const double *__restrict__ xs, double *__restrict__ yt)
+                               const double *__restrict__ xs, const double *__restrict__ mt, double *__restrict__ yt)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nnode_t * k) return;
@@ -361,7 +361,7 @@ __global__ void k_rho_coupling(int d, int k, int nnode_t, const int *__restrict_
                 double dd = xa[c] - sch[(size_t)j * d + c];
                 r2 += dd * dd;
             }
-            acc += gamma_r2(d, r2, sa, ss[j], la, slk[j]) * xs[j];
+            acc += gamma_r2t(mt, d, r2, sa, ss[j], la, slk[j]) * xs[j];
         }
     }
     yt[i] = acc;
@@ -377,6 +377,7 @@ struct RhoParams {
     int tail;
     double R;
     const double *g9x, *g9w;
+    const double *mt;
     double *rho;
 };
 
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
                             double dd = x[c] - sx[t * d + c];
                             r2 += dd * dd;
                         }
-                        acc += gamma_r2(d, r2, s_, ss[t], l_, sl[t]) * sw[t];
+                        acc += gamma_r2t(P.mt, d, r2, s_, ss[t], l_, sl[t]) * sw[t];
                     }
             }
         }
@@ -505,7 +506,7 @@ void launch_density(const MeshData &m, OpData &op, cudaStream_t st)
         int n = m.tt.nnode * k;
         k_rho_coupling<<<cdiv(n, 128), 128, 0, st>>>(d, k, m.tt.nnode, m.rfar_ptr.p, m.rfar_col.p, m.tt_cheb.p,
                                                       op.tc_s.p, op.tc_lk.p, m.st_cheb.p, op.sc_s.p, op.sc_lk.p,
-                                                      m.st_xhat.p, yt.p);
+                                                      m.st_xhat.p, m.mtab.p, yt.p);
         VFD_CUDA(cudaGetLastError());
     }
     RhoParams P;
@@ -536,6 +537,7 @@ void launch_density(const MeshData &m, OpData &op, cudaStream_t st)
     P.R = m.opts.tail_R;
     P.g9x = m.gl9_x.p;
     P.g9w = m.gl9_w.p;
+    P.mt = m.mtab.p;
     P.rho = op.rho.p;
     size_t shm = 128 * (d + 3) * sizeof(double) + 128 * 3 * sizeof(int);
     k_rho_points<<<m.tt.nleaf, 128, shm, st>>>(P);
@@ -549,7 +551,7 @@ void launch_density(const MeshData &m, OpData &op, cudaStream_t st)
 // ---------------------------------------------------------------------------
 __global__ void k_coupling(int d, int k, int nnode, const int *__restrict__ fptr, const int *__restrict__ fcol,
                            const double *__restrict__ ch, const double *__restrict__ cs,
-                           const double *__restrict__ clk, double *__restrict__ S)
+                           const double *__restrict__ clk, const double *__restrict__ mt, double *__restrict__ S)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long kk = (long long)k * k;
@@ -570,7 +572,7 @@ __global__ void k_coupling(int d, int k, int nnode, const int *__restrict__ fptr
         double dd = ch[(size_t)ia * d + c] - ch[(size_t)ib * d + c];
         r2 += dd * dd;
     }
-    S[i] = -2.0 * gamma_r2(d, r2, cs[ia], cs[ib], clk[ia], clk[ib]);
+    S[i] = -2.0 * gamma_r2t(mt, d, r2, cs[ia], cs[ib], clk[ia], clk[ib]);
 }
 
 void launch_coupling_build(const MeshData &m, OpData &op, cudaStream_t st)
@@ -579,7 +581,7 @@ void launch_coupling_build(const MeshData &m, OpData &op, cudaStream_t st)
     op.S64.alloc(n);
     if (!n) return;
     k_coupling<<<cdiv(n, 256), 256, 0, st>>>(m.d, m.k, m.kt.nnode, m.far_ptr.p, m.far_col.p, m.kt_cheb.p, op.kc_s.p,
-                                             op.kc_lk.p, op.S64.p);
+                                             op.kc_lk.p, m.mtab.p, op.S64.p);
     VFD_CUDA(cudaGetLastError());
 }
 
@@ -595,11 +597,13 @@ struct NearParams {
     int d, nv, nQ, fl, TQ, maxpts, maxleaf;
     const int *near_ptr, *near_col, *near_src, *prow;
     const int64_t *near_off;
+    const int *panel_w;
     const int *kt_begin, *kt_end;
     const int *lp_ptr, *lp_pts, *supp_ptr, *supp_loc;
     const double *supp_coef;
     const double *qx, *qs, *qlk;
     const int *qcell, *cells;
+    const double *mt;
     double *D;
 };
 
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
                     double dd = P.qx[(size_t)c * P.nQ + id] - bx[l * d + c];
                     r2 += dd * dd;
                 }
-                g = gamma_r2(d, r2, P.qs[id], bs[l], P.qlk[id], bl[l]);
+                g = gamma_r2t(P.mt, d, r2, P.qs[id], bs[l], P.qlk[id], bl[l]);
             }
             G[(size_t)tq * npb + l] = g;
         }
@@ -678,24 +682,31 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
         }
         __syncthreads();
     }
+    // write into the row panel of leaf a (row stride panel_w[a])
     double *out = P.D + P.near_off[e];
-    for (int t = threadIdx.x; t < na * nb; t += blockDim.x) out[t] = -2.0 * Dacc[t];
+    const int W = P.panel_w[a];
+    for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
+        int i = t / nb, j = t - i * nb;
+        out[(size_t)i * W + j] = -2.0 * Dacc[t];
+    }
 }
 
 __global__ void k_near_transpose(int nnear, const int *__restrict__ src, const int *__restrict__ prow,
                                  const int *__restrict__ ncol, const int *__restrict__ kb, const int *__restrict__ ke,
-                                 int fl, const int64_t *__restrict__ off, double *__restrict__ D)
+                                 int fl, const int64_t *__restrict__ off, const int *__restrict__ pw,
+                                 double *__restrict__ D)
 {
     int e = blockIdx.x;
     int s = src[e];
     if (s < 0) return;
     int a = prow[e], b = ncol[e];
     int na = ke[fl + a] - kb[fl + a], nb = ke[fl + b] - kb[fl + b];
-    const double *in = D + off[s];   // nb x na
-    double *out = D + off[e];        // na x nb
+    const int Wa = pw[a], Wb = pw[b];
+    const double *in = D + off[s];   // block (b, a): nb rows, stride Wb
+    double *out = D + off[e];        // block (a, b): na rows, stride Wa
     for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
         int i = t / nb, j = t % nb;
-        out[t] = in[(size_t)j * na + i];
+        out[(size_t)i * Wa + j] = in[(size_t)j * Wb + i];
     }
 }
 
@@ -703,6 +714,7 @@ void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st)
 {
     op.D64.alloc(m.near_entries);
     if (!m.nnear) return;
+    op.D64.zero(st);   // panel padding columns stay zero
     NearParams P;
     P.d = m.d;
     P.nv = m.d + 1;
@@ -715,6 +727,7 @@ void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st)
     P.near_src = m.near_src.p;
     P.prow = m.near_pair_row.p;
     P.near_off = m.near_off.p;
+    P.panel_w = m.panel_w.p;
     P.kt_begin = m.kt_begin.p;
     P.kt_end = m.kt_end.p;
     P.lp_ptr = m.lp_ptr.p;
@@ -727,6 +740,7 @@ void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st)
     P.qlk = op.q_lk.p;
     P.qcell = m.qcell.p;
     P.cells = m.cells.p;
+    P.mt = m.mtab.p;
     P.D = op.D64.p;
     auto shm_for = [&](int TQ) {
         return (size_t)TQ * P.maxpts * 8 + (size_t)TQ * P.maxleaf * 8 + (size_t)P.maxleaf * P.maxleaf * 8 +
@@ -741,7 +755,7 @@ void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st)
     k_near_build<<<m.nnear, 256, shm, st>>>(P);
     VFD_CUDA(cudaGetLastError());
     k_near_transpose<<<m.nnear, 256, 0, st>>>(m.nnear, m.near_src.p, m.near_pair_row.p, m.near_col.p, m.kt_begin.p,
-                                              m.kt_end.p, P.fl, m.near_off.p, op.D64.p);
+                                              m.kt_end.p, P.fl, m.near_off.p, m.panel_w.p, op.D64.p);
     VFD_CUDA(cudaGetLastError());
 }
 
@@ -765,8 +779,7 @@ void launch_convert_fp32(const MeshData &m, OpData &op, cudaStream_t st)
 {
     to32(op.S64, op.S32, st);
     to32(op.D64, op.D32, st);
-    to32(m.U64, op.U32, st);
-    to32(m.E64, op.E32, st);
+    to32(m.Ul64, op.Ul32, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -794,6 +807,20 @@ __global__ void k_load(int N, int d, int M, const int *__restrict__ ptr, const i
         for (int bb = 0; bb < nv; ++bb) acc += meas * (a == bb ? 2.0 : 1.0) / den * f[t[bb]];
     }
     F[i] = acc;
+}
+
+__global__ void k_selftest_math(int which, long long n, const double *__restrict__ mt, const double *__restrict__ x,
+                                double *__restrict__ out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = which == 0 ? fast_log(mt, x[i]) : fast_exp(mt, x[i]);
+}
+
+void launch_selftest_math(const MeshData &m, int which, long long n, const double *x, double *out, cudaStream_t st)
+{
+    if (n > 0) k_selftest_math<<<cdiv(n, 256), 256, 0, st>>>(which, n, m.mtab.p, x, out);
+    VFD_CUDA(cudaGetLastError());
 }
 
 void launch_load(const MeshData &m, const double *f, double *F, cudaStream_t st)

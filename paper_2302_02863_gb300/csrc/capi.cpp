@@ -174,10 +174,10 @@ vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info)
     VFD_API_BEGIN
     VFD_REQUIRE(mesh && info && n_info >= 0, VFD_EINVAL, "bad argument");
     const MeshData &m = *mesh->m;
-    int64_t v[15] = {m.N,        m.M,          m.C,       m.npairs, m.nnz,    m.kt.L,        m.kt.nnode, m.k,
-                     m.nfar,     m.nnear,      m.near_entries, m.nQ, m.nQint, m.nrfar, m.rnear_pairs};
-    for (int i = 0; i < n_info && i < 15; ++i) info[i] = v[i];
-    for (int i = 15; i < n_info; ++i) info[i] = 0;
+    int64_t v[16] = {m.N,    m.M,     m.C,      m.npairs, m.nnz,   m.kt.L,      m.kt.nnode,  m.k,
+                     m.nfar, m.nnear, m.near_entries_alg, m.nQ, m.nQint, m.nrfar, m.rnear_pairs, m.near_entries};
+    for (int i = 0; i < n_info && i < 16; ++i) info[i] = v[i];
+    for (int i = 16; i < n_info; ++i) info[i] = 0;
     return VFD_OK;
     VFD_API_END
 }
@@ -209,28 +209,57 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
     upload_field(log_kappa, m.M, op->f_rows_k, op->f_vals_k, op->fk);
     op->errflag.alloc(2);
     op->errflag.zero(st);
+    op->timed = (flags & VFD_ASSEMBLE_TIMED) != 0;
+    cudaEvent_t ev[VFD_T_COUNT];
+    int nev = 0;
+    auto mark = [&]() {
+        if (!op->timed) return;
+        VFD_CUDA(cudaEventCreate(&ev[nev]));
+        VFD_CUDA(cudaEventRecord(ev[nev], st));
+        ++nev;
+    };
+    mark();
     // a2: field values; check 0 <= s <= s_bar at every evaluation point (Sec. 2, i:s)
     launch_field_points(m, *op, st);
+    mark();
     int herr[2] = {0, 0};
     VFD_CUDA(cudaMemcpyAsync(herr, op->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     VFD_CUDA(cudaStreamSynchronize(st));
     VFD_REQUIRE(herr[0] == 0, VFD_EINVAL, "s(x) outside [0, s_bar] at some evaluation point");
-    // a3: coupling blocks; a4: dense inadmissible leaves
+    // a3: coupling blocks
     launch_coupling_build(m, *op, st);
+    mark();
+    // a4: dense inadmissible leaves
     launch_near_build(m, *op, st);
+    mark();
     // a6: density by the H^2 sweep + tail
     launch_density(m, *op, st);
+    mark();
     // a5: singular near field
     {
         DBuf<double> Lbuf;
         launch_singular_B(m, *op, Lbuf, st);
+        mark();
         launch_gather_B(m, *op, Lbuf, st);
         VFD_CUDA(cudaStreamSynchronize(st));
     }
     // a7: weighted mass (and B + M for the apply)
     launch_gather_M(m, *op, st);
     if (precision == VFD_FP32) launch_convert_fp32(m, *op, st);
+    mark();
     VFD_CUDA(cudaStreamSynchronize(st));
+    if (op->timed) {
+        // events: 0 start, 1 fields, 2 coupling, 3 near, 4 density, 5 singular, 6 gathers
+        for (int i = 0; i + 1 < nev && i < 6; ++i) {
+            float ms = 0.f;
+            VFD_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+            op->phase_ms[i] = ms;
+        }
+        float tot = 0.f;
+        VFD_CUDA(cudaEventElapsedTime(&tot, ev[0], ev[nev - 1]));
+        op->phase_ms[VFD_T_TOTAL] = tot;
+        for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+    }
     *out = new vfd_op_s{op};
     return VFD_OK;
     }
@@ -351,10 +380,33 @@ vfd_status vfd_op_rho(vfd_op_t h, double *rho, void *stream)
     VFD_API_END
 }
 
+vfd_status vfd_selftest_math(vfd_mesh_t mesh, int which, int64_t n, const double *x, double *out, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(mesh && x && out && n >= 0 && (which == 0 || which == 1), VFD_EINVAL, "bad argument");
+    VFD_REQUIRE(is_device_ptr(x) && is_device_ptr(out), VFD_EINVAL, "x and out must be device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_selftest_math(*mesh->m, which, n, x, out, st);
+    VFD_CUDA(cudaStreamSynchronize(st));
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_op_timings(vfd_op_t h, double *ms, int n)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && ms && n >= 0, VFD_EINVAL, "bad argument");
+    VFD_REQUIRE(h->op->timed, VFD_EINVAL, "the operator was assembled without VFD_ASSEMBLE_TIMED");
+    for (int i = 0; i < n && i < VFD_T_COUNT; ++i) ms[i] = h->op->phase_ms[i];
+    return VFD_OK;
+    VFD_API_END
+}
+
 void vfd_free_op(vfd_op_t h)
 {
     if (!h) return;
     release_graphs(*h->op);
+    release_streams(*h->op);
     delete h->op;
     delete h;
 }

@@ -109,3 +109,66 @@ __device__ __forceinline__ double warp_sum(double v)
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace vfd
+
+namespace vfd {
+
+// ---------------------------------------------------------------------------
+// Table-driven FP64 logarithm and exponential (P. T. P. Tang, "Table-driven
+// implementation of the logarithm function in IEEE floating-point
+// arithmetic", ACM TOMS 16(4) 1990, and "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2)
+// 1989), used for the kernel evaluations gamma on GB300, whose FP64 pipe is
+// 1/58 of FP32.  Table layout (built on the host by make_math_tables):
+//   [0..128]   c_j = 1/F_j, F_j = 1 + j/128
+//   [129..257] log F_j
+//   [258..321] 2^(j/64)
+//   [322..325] ln2_hi, ln2_lo, ln2/64 hi, ln2/64 lo   (Cody-Waite splits)
+// Valid for normal positive x (log) and |y| < 700 (exp); relative error of a
+// few ulp (tests/test_gpu_math.py).
+// ---------------------------------------------------------------------------
+constexpr int MT_C = 0, MT_LOGF = 129, MT_EXP2 = 258, MT_CONST = 322, MT_SIZE = 326;
+
+__device__ __forceinline__ double fast_log(const double *__restrict__ mt, double x)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const int j = (int)(((bits >> 44) & 0xff) + 1) >> 1;   // nearest j/128 to m - 1
+    const double r = fma(m, __ldg(mt + MT_C + j), -1.0);   // |r| <= 2^-8
+    double q = 1.0 / 7.0;
+    q = fma(q, r, -1.0 / 6.0);
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    q = fma(q, r, 1.0);
+    const double ed = (double)e;
+    return fma(ed, __ldg(mt + MT_CONST), __ldg(mt + MT_LOGF + j) + fma(ed, __ldg(mt + MT_CONST + 1), q * r));
+}
+
+__device__ __forceinline__ double fast_exp(const double *__restrict__ mt, double y)
+{
+    y = fmin(fmax(y, -700.0), 700.0);
+    const double kf = rint(y * 92.33248261689366);   // 64 / ln 2
+    const long long ki = (long long)kf;
+    double r = fma(-kf, __ldg(mt + MT_CONST + 2), y);
+    r = fma(-kf, __ldg(mt + MT_CONST + 3), r);        // |r| <= ln2/128
+    double q = 1.0 / 720.0;
+    q = fma(q, r, 1.0 / 120.0);
+    q = fma(q, r, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    q = fma(q, r, 1.0);
+    const double s = __ldg(mt + MT_EXP2 + (int)(ki & 63));
+    const double v = fma(s, q * r, s);
+    return __longlong_as_double(__double_as_longlong(v) + ((ki >> 6) << 52));
+}
+
+// gamma from r^2 with the table-driven log/exp
+__device__ __forceinline__ double gamma_r2t(const double *__restrict__ mt, int d, double r2, double sx, double sy,
+                                            double lkx, double lky)
+{
+    return fast_exp(mt, 0.5 * (lkx + lky) - 0.5 * (d + sx + sy) * fast_log(mt, r2));
+}
+
+}  // namespace vfd

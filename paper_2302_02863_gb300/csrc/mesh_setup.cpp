@@ -48,6 +48,31 @@ void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w)
     }
 }
 
+std::vector<double> make_math_tables()
+{
+    // tables of the table-driven log/exp (layout in device_common.cuh),
+    // computed with the host C library in extended precision
+    std::vector<double> t(326, 0.0);
+    for (int j = 0; j <= 128; ++j) {
+        double c = 1.0 / (1.0 + j / 128.0);
+        t[j] = c;
+        t[129 + j] = (double)(-std::log((long double)c));
+    }
+    for (int j = 0; j < 64; ++j) t[258 + j] = (double)std::exp2((long double)j / 64.0L);
+    const long double ln2 = std::log(2.0L);
+    double hi = (double)ln2;
+    long long b;
+    std::memcpy(&b, &hi, 8);
+    b &= ~((1LL << 28) - 1);   // 25 significant bits: e*hi and k*hi/64 are exact
+    std::memcpy(&hi, &b, 8);
+    double lo = (double)(ln2 - (long double)hi);
+    t[322] = hi;
+    t[323] = lo;
+    t[324] = hi / 64.0;
+    t[325] = lo / 64.0;
+    return t;
+}
+
 void cheb_nodes_1d(int p, double lo, double hi, double *out)
 {
     // first-kind Chebyshev points of [lo, hi] (Sec. 5.3; reading: Chebyshev,
@@ -594,14 +619,22 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             csr_from_lists(nearl, m->near_ptr_h, m->near_col_h);
             m->nfar = (int)m->far_col_h.size();
             m->nnear = (int)m->near_col_h.size();
+            // Near blocks of one row leaf form a row panel (row stride W_a = the
+            // partners' column counts, padded to a multiple of 4), so that a row's
+            // near entries are contiguous; block e starts at near_off[e].
             m->near_off_h.assign(m->nnear + 1, 0);
-            std::vector<int> src(m->nnear, -1), prow(m->nnear);
-            for (int a = 0; a < nleaf; ++a)
+            std::vector<int> src(m->nnear, -1), prow(m->nnear), pw(nleaf, 0);
+            std::vector<int64_t> poff(nleaf + 1, 0);
+            m->near_entries_alg = 0;
+            for (int a = 0; a < nleaf; ++a) {
+                int na = kt.end[fl + a] - kt.begin[fl + a], w = 0;
                 for (int e = m->near_ptr_h[a]; e < m->near_ptr_h[a + 1]; ++e) {
                     int b = m->near_col_h[e];
                     prow[e] = a;
-                    int na = kt.end[fl + a] - kt.begin[fl + a], nb = kt.end[fl + b] - kt.begin[fl + b];
-                    m->near_off_h[e + 1] = m->near_off_h[e] + (int64_t)na * nb;
+                    int nb = kt.end[fl + b] - kt.begin[fl + b];
+                    m->near_off_h[e] = poff[a] + w;
+                    w += nb;
+                    m->near_entries_alg += (int64_t)na * nb;
                     if (a > b) {
                         auto bb = m->near_col_h.begin() + m->near_ptr_h[b], ee = m->near_col_h.begin() + m->near_ptr_h[b + 1];
                         auto it = std::lower_bound(bb, ee, a);
@@ -609,7 +642,33 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                         src[e] = (int)(it - m->near_col_h.begin());
                     }
                 }
-            m->near_entries = m->near_off_h[m->nnear];
+                w = (w + 3) & ~3;
+                pw[a] = w;
+                m->max_panel_w = std::max(m->max_panel_w, w);
+                poff[a + 1] = poff[a] + (int64_t)na * w;
+            }
+            m->near_entries = poff[nleaf];
+            m->near_off_h[m->nnear] = m->near_entries;
+            m->panel_w.upload(pw);
+            m->panel_off.upload(poff);
+            // flat gather index of every panel column: the DoF whose x it takes
+            // (-1 for the padding); panel a's columns start at gcol_off[a]
+            std::vector<int> gcol, goff(nleaf + 1, 0);
+            for (int a = 0; a < nleaf; ++a) {
+                goff[a] = (int)gcol.size();
+                for (int e = m->near_ptr_h[a]; e < m->near_ptr_h[a + 1]; ++e) {
+                    int b = m->near_col_h[e];
+                    for (int j = kt.begin[fl + b]; j < kt.end[fl + b]; ++j) gcol.push_back(j);
+                }
+                while ((int)gcol.size() - goff[a] < pw[a]) gcol.push_back(-1);
+            }
+            goff[nleaf] = (int)gcol.size();
+            m->gcol.upload(gcol);
+            m->gcol_off.upload(goff);
+            std::vector<int> vl(N);
+            for (int a = 0; a < nleaf; ++a)
+                for (int j = kt.begin[fl + a]; j < kt.end[fl + a]; ++j) vl[j] = a;
+            m->vleaf.upload(vl);
             m->far_ptr.upload(m->far_ptr_h);
             m->far_col.upload(m->far_col_h);
             m->near_ptr.upload(m->near_ptr_h);
@@ -620,6 +679,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
         }
 
         // ---- per-leaf point sets and DoF supports; leaf bases U (Sec. 5.3, R5)
+        std::vector<double> Uh;   // N x k, tree order
         {
             std::vector<int> lp_ptr(nleaf + 1, 0), lp_pts;
             std::vector<std::vector<std::pair<int, double>>> supp(N);
@@ -687,10 +747,16 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             m->supp_ptr.upload(sp);
             m->supp_loc.upload(sl);
             m->supp_coef.upload(sc);
-            m->U64.upload(U);
+            Uh = U;
             m->kt_Uoff.upload(Uoff);
         }
-        // transfers E_c[beta][alpha] = l^parent_alpha(xi^c_beta)
+        // transfers E_c[beta][alpha] = l^parent_alpha(xi^c_beta) (nested bases,
+        // Sec. 5.3 last paragraph), and the per-level bases they generate:
+        // Ul^(l)[i] = U[i] E_{c_L} ... E_{c_(l+1)} along the path from the leaf
+        // of DoF i to its level-(l+1) ancestor, so that the basis of a node at
+        // level l is the stack of its rows (used by the apply to avoid a
+        // level-by-level transfer chain; stored for the levels with
+        // admissible blocks only).
         {
             std::vector<double> E((size_t)nnode * k * k, 0.0), lag(k);
             for (int c = 1; c < nnode; ++c) {
@@ -700,7 +766,34 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                     for (int al = 0; al < k; ++al) E[((size_t)c * k + be) * k + al] = lag[al];
                 }
             }
-            m->E64.upload(E);
+            int lmin = kt.L + 1;
+            for (int a = 0; a < nnode; ++a)
+                if (m->far_ptr_h[a + 1] > m->far_ptr_h[a]) {
+                    int lev = 0;
+                    while ((2 << lev) - 1 <= a) ++lev;
+                    lmin = std::min(lmin, lev);
+                }
+            m->far_lmin = lmin;
+            const int nlev = (lmin <= kt.L) ? kt.L - lmin + 1 : 0;
+            std::vector<double> Ul((size_t)nlev * N * k, 0.0);
+            if (nlev) {
+                for (size_t t = 0; t < (size_t)N * k; ++t) Ul[(size_t)(kt.L - lmin) * N * k + t] = Uh[t];
+                for (int l = kt.L - 1; l >= lmin; --l)
+                    for (int lf = 0; lf < nleaf; ++lf) {
+                        int c = ((fl + lf + 1) >> (kt.L - (l + 1))) - 1;   // level-(l+1) ancestor
+                        const double *Ec = &E[(size_t)c * k * k];
+                        for (int i = kt.begin[fl + lf]; i < kt.end[fl + lf]; ++i) {
+                            const double *src = &Ul[((size_t)(l + 1 - lmin) * N + i) * k];
+                            double *dst = &Ul[((size_t)(l - lmin) * N + i) * k];
+                            for (int al = 0; al < k; ++al) {
+                                double v = 0.0;
+                                for (int be = 0; be < k; ++be) v += src[be] * Ec[(size_t)be * k + al];
+                                dst[al] = v;
+                            }
+                        }
+                    }
+            }
+            m->Ul64.upload(Ul);
         }
 
         // ---- density sweep trees (Sec. 6.2): targets = interior points, sources = all points
@@ -819,6 +912,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             gauss_legendre01(9, gx, gw);
             m->gl9_x.upload(gx);
             m->gl9_w.upload(gw);
+            m->mtab.upload(make_math_tables());
         }
     } catch (...) {
         delete m;

@@ -193,7 +193,7 @@ static int run_cg(const MeshData &m, OpData &op, bool lowp, double rtol, int max
         }
         VFD_CUDA(cudaStreamEndCapture(cs, &graph));
         cudaStreamDestroy(cs);
-        cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+        cudaError_t ie = cudaGraphInstantiate(&gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(graph);
         VFD_CUDA(ie);
         gkey = op.cg_p.p;
@@ -254,14 +254,19 @@ vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, i
         if (op.precision != VFD_FP32) {
             VFD_CUDA(cudaMemcpyAsync(op.cg_b.p, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
             VFD_CUDA(cudaMemcpyAsync(op.cg_x.p, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-            double rr, bb;
-            total = run_cg(m, op, false, rtol, max_it, st, &rr, &bb);
+            // CG; when the recursive residual has converged but the true
+            // residual of the iterate has not, restart from the iterate
+            // (residual replacement), at most a few times
+            for (int restart = 0; restart < 4; ++restart) {
+                double rr, bb;
+                total += run_cg(m, op, false, rtol, max_it - total, st, &rr, &bb);
+                apply_parts_ex(m, op, VFD_PART_ALL, op.cg_x.p, op.cg_q.p, 1, n, false, st, nullptr);
+                k_sub<<<VB, RB, 0, st>>>(n, f, op.cg_q.p, op.cg_r.p);
+                double res2 = dev_dot(m, op, op.cg_r.p, op.cg_r.p, st);
+                rel = (bb > 0.0) ? std::sqrt(res2 / bb) : std::sqrt(res2);
+                if (rel <= rtol || total >= max_it) break;
+            }
             VFD_CUDA(cudaMemcpyAsync(u, op.cg_x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-            // true residual of the returned iterate
-            apply_parts_ex(m, op, VFD_PART_ALL, u, op.cg_q.p, 1, n, false, st, nullptr);
-            k_sub<<<VB, RB, 0, st>>>(n, f, op.cg_q.p, op.cg_r.p);
-            double res2 = dev_dot(m, op, op.cg_r.p, op.cg_r.p, st);
-            rel = (bb > 0.0) ? std::sqrt(res2 / bb) : std::sqrt(res2);
         } else {
             // iterative refinement: outer FP64 residual, inner CG with FP32 K
             double bb = dev_dot(m, op, f, f, st);

@@ -135,9 +135,9 @@ struct MeshData {
     Tree kt;
     DBuf<int> kt_begin, kt_end;
     DBuf<double> kt_cheb;      // nnode * k * d (node-major, point, dim)
-    DBuf<double> U64;          // per leaf: (end-begin) x k row-major, offsets kt_Uoff
     DBuf<int> kt_Uoff;         // nleaf
-    DBuf<double> E64;          // nnode * k * k (E_c[beta][alpha]); root unused
+    int far_lmin = 0;          // first level with admissible blocks
+    DBuf<double> Ul64;         // per-level bases, (L - far_lmin + 1) x N x k
     // admissible blocks (both orders), CSR by row node
     int nfar = 0;
     std::vector<int> far_ptr_h, far_col_h;
@@ -148,7 +148,13 @@ struct MeshData {
     std::vector<int> near_ptr_h, near_col_h;
     std::vector<int64_t> near_off_h;
     DBuf<int> near_ptr, near_col;
-    DBuf<int64_t> near_off;    // offset of block (row-major |sigma| x |sigma'|)
+    DBuf<int64_t> near_off;    // offset of block e's (0,0) entry in its row leaf's panel
+    DBuf<int> panel_w;         // per row leaf: panel row stride (padded to 4)
+    DBuf<int64_t> panel_off;   // per row leaf: panel start (nleaf + 1)
+    int64_t near_entries_alg = 0;   // sum |sigma||sigma'| over near blocks (no padding)
+    DBuf<int> gcol, gcol_off;  // per panel column the DoF of its x entry (-1: padding)
+    DBuf<int> vleaf;           // leaf of every DoF
+    int max_panel_w = 0;
     DBuf<int> near_src;        // per block: index of the computed block it is the transpose of, or -1
     DBuf<int> near_pair_row;   // per block: row leaf (for launch over blocks)
     // per-leaf point sets for the near-block build
@@ -170,6 +176,7 @@ struct MeshData {
     DBuf<int> rnear_ptr, rnear_col;     // by target leaf
     DBuf<double> gl_x, gl_w;            // Gauss-Legendre on [0,1], n_sing points
     DBuf<double> gl9_x, gl9_w;          // 9-point rule for the tail
+    DBuf<double> mtab;                  // tables of the table-driven FP64 log/exp
 
     // load assembly (exact P1 mass)
     DBuf<int> ld_ptr, ld_idx;           // DoF -> list of cell*(d+1)+a contributions
@@ -192,11 +199,15 @@ struct OpData {
     DBuf<double> rho;                  // interior points, canonical order
     DBuf<double> S64;                  // nfar * k * k
     DBuf<double> D64;                  // near entries
-    DBuf<float> S32, D32, U32, E32;    // FP32 copies (VFD_FP32)
+    DBuf<float> S32, D32, Ul32;        // FP32 copies (VFD_FP32)
     // apply workspace
     int ws_nrhs = 0;
     DBuf<double> xhat, yhat;           // nnode * k * ws_nrhs
     DBuf<float> xhat32, yhat32;
+    DBuf<double> P64;                  // leaf-level projections nlev * nleaf * k * nrhs
+    DBuf<float> P32;
+    cudaStream_t side = nullptr;       // far-field branch of the apply
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DBuf<double> xin, yout;            // staging for host pointers
     // solver workspace
     DBuf<double> cg_r, cg_p, cg_q, cg_x, cg_b, cg_z;
@@ -204,6 +215,8 @@ struct OpData {
     DBuf<double> cg_scal;              // device scalars
     DBuf<int> cg_flag;
     DBuf<int> errflag;
+    double phase_ms[VFD_T_COUNT] = {0};
+    bool timed = false;
     cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};   // captured CG chunks (FP64 K, FP32 K)
     const void *cg_key[2] = {nullptr, nullptr};
 };
@@ -214,6 +227,7 @@ struct OpData {
 MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell, const int32_t *cells,
                      const uint8_t *inter, const vfd_mesh_opts &opts);
 void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w);
+std::vector<double> make_math_tables();
 void cheb_nodes_1d(int p, double lo, double hi, double *out);
 
 // ---------------------------------------------------------------------------
@@ -229,6 +243,7 @@ void launch_coupling_build(const MeshData &m, OpData &op, cudaStream_t st);
 void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st);
 void launch_convert_fp32(const MeshData &m, OpData &op, cudaStream_t st);
 void launch_load(const MeshData &m, const double *f, double *F, cudaStream_t st);
+void launch_selftest_math(const MeshData &m, int which, long long n, const double *x, double *out, cudaStream_t st);
 // apply.cu
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                     bool lowp, cudaStream_t st, const int *skip);
@@ -236,6 +251,7 @@ void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, doub
                  cudaStream_t st);
 // solve.cu
 void release_graphs(OpData &op);
+void release_streams(OpData &op);
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st);
 

@@ -23,14 +23,16 @@ VFD_OK, VFD_EINVAL, VFD_ENOMEM, VFD_ECUDA, VFD_ENOCONV, VFD_ETIMEOUT, VFD_EUNSUP
 VFD_FP64, VFD_FP32 = 0, 1
 VFD_PART_B, VFD_PART_M, VFD_PART_KNEAR, VFD_PART_KFAR, VFD_PART_ALL = 1, 2, 4, 8, 15
 VFD_ASSEMBLE_UNCHECKED = 1
+VFD_ASSEMBLE_TIMED = 2
+TIMING_KEYS = ["fields", "coupling", "near", "density", "singular", "gather", "total"]
 VFD_FIELD_ANALYTIC, VFD_FIELD_NODAL = 0, 1
 INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "nodes", "rank",
              "far_blocks", "near_blocks", "near_entries", "n_q", "n_qint", "rho_far_blocks",
-             "rho_near_pairs"]
+             "rho_near_pairs", "near_storage"]
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
-           "vfd_apply", "vfd_apply_parts", "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_free_op",
-           "vfd_free_mesh", "vfd_last_error"]
+           "vfd_apply", "vfd_apply_parts", "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings",
+           "vfd_selftest_math", "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
 
 
 class VfdError(RuntimeError):
@@ -80,13 +82,15 @@ def load():
                             dp, vp]
     L.vfd_load.argtypes = [vp, vp, vp, vp]
     L.vfd_op_rho.argtypes = [vp, vp, vp]
+    L.vfd_op_timings.argtypes = [vp, dp, C.c_int]
+    L.vfd_selftest_math.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp]
     L.vfd_free_op.argtypes = [vp]
     L.vfd_free_op.restype = None
     L.vfd_free_mesh.argtypes = [vp]
     L.vfd_free_mesh.restype = None
     L.vfd_last_error.restype = C.c_char_p
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
-              "vfd_solve", "vfd_load", "vfd_op_rho"]:
+              "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -260,6 +264,20 @@ def vfd_load(mesh, f_nodal, F, stream=None):
 def vfd_op_rho(op, rho, stream=None):
     _check(load().vfd_op_rho(op.handle, _ptr(rho), _stream(stream)))
     return rho
+
+
+def vfd_op_timings(op):
+    """Device milliseconds per assembly phase (needs flags=VFD_ASSEMBLE_TIMED)."""
+    a = np.zeros(len(TIMING_KEYS))
+    _check(load().vfd_op_timings(op.handle, a.ctypes.data_as(C.POINTER(C.c_double)), len(a)))
+    return dict(zip(TIMING_KEYS, a.tolist()))
+
+
+def vfd_selftest_math(mesh, which, x, out, stream=None):
+    """out = log(x) (which=0) or exp(x) (which=1) by the library's table-driven
+    FP64 routines (device tensors)."""
+    _check(load().vfd_selftest_math(mesh.handle, int(which), x.numel(), _ptr(x), _ptr(out), _stream(stream)))
+    return out
 
 
 def vfd_free_op(op):
