@@ -50,6 +50,9 @@ def _args():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--rtol", type=float, default=1e-10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mode", default="step", choices=["step", "apply"],
+                   help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
+    p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
     return p.parse_args()
 
 
@@ -186,6 +189,8 @@ def main():
                         lam=0.75, rho_lambda=0.75, tail_mode=prm["tail"], tail_R=prm["R"])
     info = mesh.info
     n = mesh.n_dof
+    if args.mode == "apply":
+        return apply_mode(args, mesh, s, k, prm, prec, torch, vfd)
     stream = torch.cuda.current_stream()
     F = torch.zeros(n, dtype=torch.float64, device="cuda")
     vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device="cuda"), F)
@@ -334,6 +339,24 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def apply_mode(args, mesh, s, k, prm, prec, torch, vfd):
+    """Bounded run for profilers: one assembly, then --warmup + --steps applies."""
+    op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec)
+    X = torch.randn(mesh.n_dof, dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    for _ in range(args.warmup):
+        vfd.vfd_apply_parts(op, args.parts, X, Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        vfd.vfd_apply_parts(op, args.parts, X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "apply", "parts": args.parts, "precision": args.precision,
+                      "us_per_apply": 1000 * e0.elapsed_time(e1) / args.steps}), flush=True)
 
 
 def _traffic_from_profile(workload, precision):

@@ -56,9 +56,11 @@ typedef struct vfd_op_s *vfd_op_t;
 /* Precision of the assembled operator (argument `precision`). */
 enum {
     VFD_FP64 = 0,   /* every part in FP64 */
-    VFD_FP32 = 1    /* K (near blocks, coupling, bases, transfers) stored and
-                       applied in FP32 with FP32 accumulation; B, M, the
-                       density rho and all solver vectors stay FP64 */
+    VFD_FP32 = 1,   /* K (near blocks, coupling, bases) stored and applied in
+                       FP32 (single RHS) or TF32 tensor-core products (batched
+                       solves) with FP32 accumulation; B, M, the density rho
+                       and the refinement residuals stay FP64 */
+    VFD_BF16 = 2    /* as VFD_FP32 with K in BF16 for the batched solves */
 };
 
 /* Parts of the operator for vfd_apply_parts (bit mask). */
@@ -175,7 +177,12 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
                         int precision, int flags, void *stream, vfd_op_t *out);
 
 /* Y = A X for nrhs columns (X, Y: host or device, n_dof x nrhs, leading
- * dimension ld).  X and Y must not overlap. */
+ * dimension ld).  X and Y must not overlap.  VFD_FP64 operators apply the
+ * FP64 operator.  VFD_FP32 / VFD_BF16 operators apply the low-precision
+ * operator of the refinement: with nrhs a multiple of 64 (and leaves of at
+ * most 64 DoFs) the batched path -- near panels on the tensor cores in TF32
+ * (VFD_FP32) or BF16 (VFD_BF16), B + M and the far field in FP32 -- else
+ * column by column with K in FP32 and B + M in FP64. */
 vfd_status vfd_apply(vfd_op_t op, const double *X, double *Y, int64_t nrhs, int64_t ld, void *stream);
 
 /* Y = (sum of the selected parts) X; parts is a mask of VFD_PART_*. */
@@ -186,9 +193,13 @@ vfd_status vfd_apply_parts(vfd_op_t op, int parts, const double *X, double *Y, i
  * solver"), every iteration on the device, column by column for nrhs > 1.
  * F, U: host or device, n_dof x nrhs, leading dimension ld; U holds the
  * initial guess on entry.  Converged when ||F - A U|| <= rtol ||F||.
- * iters, relres: host arrays of nrhs entries (may be NULL).  For a
- * VFD_FP32 operator the solve is iterative refinement: an FP64 residual with
- * the FP64 parts and the FP32 K, and inner CG sweeps on the same operator.
+ * iters, relres: host arrays of nrhs entries (may be NULL).
+ * VFD_FP64 operators: FP64 CG, column by column.  VFD_FP32 / VFD_BF16
+ * operators: iterative refinement, the residual F - A U in FP64 with the FP64
+ * operator; with nrhs = 1 the inner CG uses FP32 K; with nrhs > 1 all columns
+ * are solved together by a batched inner CG in FP32 vectors whose near-field
+ * products run on the tensor cores (TF32 or BF16) -- this needs leaves of at
+ * most 64 DoFs.  iters reports the inner CG iterations.
  * Returns VFD_ENOCONV when some column did not converge in max_it. */
 vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int64_t ld, double rtol,
                      int max_it, int *iters, double *relres, void *stream);

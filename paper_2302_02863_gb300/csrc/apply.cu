@@ -342,19 +342,21 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
     const size_t need = (size_t)m.kt.nnode * m.k * nrhs;
     const size_t needp = (size_t)std::max(nlev, 1) * m.kt.nleaf * m.k * nrhs;
     if (lowp) {
-        if (op.xhat32.n < need) {
+        if (op.xhat32.n < need || op.P32.n < needp) {
+            release_graphs(op);   // captured solves refer to the old workspace
             op.xhat32.alloc(need);
             op.yhat32.alloc(need);
+            op.P32.alloc(needp);
         }
-        if (op.P32.n < needp) op.P32.alloc(needp);
         apply_impl<float, float>(m, op, parts, X, Y, nrhs, ld, op.Ul32.p, op.S32.p, op.D32.p, op.xhat32.p, op.yhat32.p,
                                  op.P32.p, st, skip);
     } else {
-        if (op.xhat.n < need) {
+        if (op.xhat.n < need || op.P64.n < needp) {
+            release_graphs(op);
             op.xhat.alloc(need);
             op.yhat.alloc(need);
+            op.P64.alloc(needp);
         }
-        if (op.P64.n < needp) op.P64.alloc(needp);
         apply_impl<double, double>(m, op, parts, X, Y, nrhs, ld, m.Ul64.p, op.S64.p, op.D64.p, op.xhat.p, op.yhat.p,
                                    op.P64.p, st, skip);
     }

@@ -192,7 +192,8 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
     require_device();
     const MeshData &m = *mesh->m;
     cudaStream_t st = (cudaStream_t)stream;
-    VFD_REQUIRE(precision == VFD_FP64 || precision == VFD_FP32, VFD_EINVAL, "unknown precision");
+    VFD_REQUIRE(precision == VFD_FP64 || precision == VFD_FP32 || precision == VFD_BF16, VFD_EINVAL,
+                "unknown precision");
     VFD_REQUIRE(s_bar < 1.0 && ((flags & VFD_ASSEMBLE_UNCHECKED) || s_bar >= 0.0), VFD_EINVAL,
                 "s_bar must satisfy 0 <= s_bar < 1");
     bool nodal = s->kind == VFD_FIELD_NODAL || log_kappa->kind == VFD_FIELD_NODAL;
@@ -245,7 +246,11 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
     }
     // a7: weighted mass (and B + M for the apply)
     launch_gather_M(m, *op, st);
-    if (precision == VFD_FP32) launch_convert_fp32(m, *op, st);
+    if (precision != VFD_FP64) {
+        launch_convert_fp32(m, *op, st);
+        launch_lowp_csr(m, *op, st);
+    }
+    if (precision == VFD_BF16) launch_convert_bf16(m, *op, st);
     mark();
     VFD_CUDA(cudaStreamSynchronize(st));
     if (op->timed) {
@@ -293,7 +298,10 @@ static vfd_status apply_common(vfd_op_t h, int parts, const double *X, double *Y
         if (op.yout.n < need) op.yout.alloc(need);
         dy = op.yout.p;
     }
-    apply_parts(m, op, parts, dx, dy, (int)nrhs, ld, st);
+    if (parts == VFD_PART_ALL && op.precision != VFD_FP64 && nrhs % 64 == 0 && m.max_leaf_size <= 64)
+        mr_apply_colmajor(m, op, dx, dy, (int)nrhs, ld, st);   // batched tensor-core path
+    else
+        apply_parts(m, op, parts, dx, dy, (int)nrhs, ld, st);
     if (!ydev) {
         VFD_CUDA(cudaMemcpyAsync(Y, dy, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyDeviceToHost, st));
         VFD_CUDA(cudaStreamSynchronize(st));
@@ -331,7 +339,9 @@ vfd_status vfd_solve(vfd_op_t h, const double *F, double *U, int64_t nrhs, int64
         du = op.yout.p;
         VFD_CUDA(cudaMemcpyAsync(du, U, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyHostToDevice, st));
     }
-    vfd_status rs = cg_solve(m, op, df, du, (int)nrhs, ld, rtol, max_it, iters, relres, st);
+    vfd_status rs = (nrhs > 1 && op.precision != VFD_FP64)
+                        ? batched_solve(m, op, df, du, (int)nrhs, ld, rtol, max_it, iters, relres, st)
+                        : cg_solve(m, op, df, du, (int)nrhs, ld, rtol, max_it, iters, relres, st);
     if (!udev) {
         VFD_CUDA(cudaMemcpyAsync(U, du, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyDeviceToHost, st));
     }
@@ -406,6 +416,7 @@ void vfd_free_op(vfd_op_t h)
 {
     if (!h) return;
     release_graphs(*h->op);
+    release_bgraph(*h->op);
     release_streams(*h->op);
     delete h->op;
     delete h;

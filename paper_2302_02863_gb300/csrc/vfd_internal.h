@@ -200,6 +200,15 @@ struct OpData {
     DBuf<double> S64;                  // nfar * k * k
     DBuf<double> D64;                  // near entries
     DBuf<float> S32, D32, Ul32;        // FP32 copies (VFD_FP32)
+    DBuf<unsigned short> S16, D16, Ul16;   // BF16 copies (VFD_BF16)
+    DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
+    // batched (multi-RHS) low-precision apply and solve workspaces
+    DBuf<float> mr_part, mr_xh, mr_yh, mr_xi, mr_yi;
+    DBuf<float> mb_x, mb_r, mb_p, mb_q, mb_b, mb_part, mb_sc;
+    DBuf<int> mb_flag;
+    cudaGraphExec_t mb_exec = nullptr;
+    const void *mb_key = nullptr;
+    int mb_R = 0;
     // apply workspace
     int ws_nrhs = 0;
     DBuf<double> xhat, yhat;           // nnode * k * ws_nrhs
@@ -252,6 +261,14 @@ void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, doub
 // solve.cu
 void release_graphs(OpData &op);
 void release_streams(OpData &op);
+void release_bgraph(OpData &op);
+void launch_convert_bf16(const MeshData &m, OpData &op, cudaStream_t st);
+void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st);
+void mr_apply(const MeshData &m, OpData &op, const float *X, float *Y, int R, cudaStream_t st, const int *skip);
+void mr_apply_colmajor(const MeshData &m, OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
+                       cudaStream_t st);
+vfd_status batched_solve(const MeshData &m, OpData &op, const double *F, double *U, int R, int64_t ld, double rtol,
+                         int max_it, int *iters, double *relres, cudaStream_t st);
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st);
 

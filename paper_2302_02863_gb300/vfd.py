@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libvfd.so")
 
 VFD_OK, VFD_EINVAL, VFD_ENOMEM, VFD_ECUDA, VFD_ENOCONV, VFD_ETIMEOUT, VFD_EUNSUPPORTED = range(7)
-VFD_FP64, VFD_FP32 = 0, 1
+VFD_FP64, VFD_FP32, VFD_BF16 = 0, 1, 2
 VFD_PART_B, VFD_PART_M, VFD_PART_KNEAR, VFD_PART_KFAR, VFD_PART_ALL = 1, 2, 4, 8, 15
 VFD_ASSEMBLE_UNCHECKED = 1
 VFD_ASSEMBLE_TIMED = 2

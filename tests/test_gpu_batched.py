@@ -1,0 +1,75 @@
+"""Batched mixed-precision path (64 RHS at once) through the C ABI.
+
+* the batched apply of a VFD_FP32 (TF32 tensor cores) / VFD_BF16 operator
+  against the FP64 operator on the same 64 random vectors: the error is the
+  rounding of the K data and of x to TF32 (2^-11) or BF16 (2^-8) -- the
+  tolerances below are a few units of that, relative to ||A x||;
+* the batched refinement solve (FP64 residual, inner batched CG) against
+  the FP64 oracle's Cholesky solution, column by column, to 1e-8.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2302_02863_gb300 import vfd  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def disk():
+    m = synth.disk_mesh(14, R=1.1, jitter=0.2, seed=9)
+    s = synth.config2_s_field()
+    k = synth.random_fourier_field(31, 0.5)
+    return m, s, k
+
+
+@pytest.mark.parametrize("prec,tol", [(vfd.VFD_FP32, 2e-3), (vfd.VFD_BF16, 2e-2)])
+def test_batched_apply_matches_fp64_operator(disk, prec, tol):
+    m, s, k = disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=32, lam=0.75, rho_lambda=0.75)
+    assert mesh.info["far_blocks"] > 0 and mesh.info["near_blocks"] > 0
+    op64 = vfd.vfd_assemble(mesh, s, k, 0.9)
+    opl = vfd.vfd_assemble(mesh, s, k, 0.9, precision=prec)
+    n = mesh.n_dof
+    X = torch.randn(64, n, dtype=torch.float64, device="cuda")
+    Y64 = torch.empty_like(X)
+    Yl = torch.empty_like(X)
+    vfd.vfd_apply(op64, X, Y64)
+    vfd.vfd_apply(opl, X, Yl)
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(Yl - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)).max().item()
+    assert err < tol, err
+    # K alone carries the low-precision error; B + M (FP32) is far more accurate,
+    # so the K part must also be close in its own norm
+    K64 = torch.empty_like(X)
+    vfd.vfd_apply_parts(op64, vfd.VFD_PART_KNEAR | vfd.VFD_PART_KFAR, X, K64)
+    torch.cuda.synchronize()
+    assert (torch.linalg.norm(Yl - Y64) / torch.linalg.norm(K64)).item() < 5 * tol
+
+
+@pytest.mark.parametrize("prec", [vfd.VFD_FP32, vfd.VFD_BF16])
+def test_batched_refinement_solve(disk, prec):
+    m, s, k = disk
+    ref = oracle.assemble(m, s, k, s_bar=0.9, n_sing=3)
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=32, lam=0.0, rho_lambda=0.0)
+    op = vfd.vfd_assemble(mesh, s, k, 0.9, precision=prec)
+    dof, n = vfd.vfd_mesh_dofs(mesh)
+    sel = dof >= 0
+    gi, oi = dof[sel], ref.dof[sel]
+    rng = np.random.default_rng(7)
+    Fo = rng.standard_normal((64, n))
+    Fg = np.zeros_like(Fo)
+    Fg[:, gi] = Fo[:, oi]
+    F = torch.tensor(Fg, device="cuda")
+    U = torch.zeros_like(F)
+    st, it, rel = vfd.vfd_solve(op, F, U, rtol=1e-10, max_it=20000)
+    assert st == vfd.VFD_OK and np.all(rel <= 1e-10), (st, it[0], rel.max())
+    Ug = U.cpu().numpy()
+    L = np.linalg.cholesky(ref.A)
+    Uo = np.linalg.solve(L.T, np.linalg.solve(L, Fo.T)).T
+    err = np.linalg.norm(Ug[:, gi] - Uo[:, oi], axis=1) / np.linalg.norm(Uo, axis=1)
+    assert err.max() < 1e-8, err.max()
