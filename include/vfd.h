@@ -189,6 +189,46 @@ vfd_status vfd_apply(vfd_op_t op, const double *X, double *Y, int64_t nrhs, int6
 vfd_status vfd_apply_parts(vfd_op_t op, int parts, const double *X, double *Y, int64_t nrhs, int64_t ld,
                            void *stream);
 
+/* Size of the fixed device scratch used by vfd_apply_noalloc (8 MiB per device). */
+#define VFD_APPLY_NOALLOC_SCRATCH_BYTES 8388608
+
+/* Y = A X for nrhs columns, as vfd_apply computes it column by column, but
+ * without allocating anything during the call.  The paper has no counterpart:
+ * this is a library convenience.
+ *
+ * Who needs it: callers that must not allocate device memory while they run,
+ * e.g. a solver loop whose device memory is reserved in advance by another
+ * framework's memory pool (a cudaMalloc could fail or make the pool give back
+ * cached blocks), or code on a latency-critical path where cudaFree would wait
+ * for the whole device.  vfd_apply may allocate on its first call and whenever
+ * nrhs grows (operator workspaces, a side stream for the far field), and it
+ * copies host arguments through device buffers.
+ *
+ * What differs from vfd_apply:
+ *  - X and Y must be device pointers (n_dof x nrhs, leading dimension ld);
+ *    host pointers are rejected with VFD_EINVAL.
+ *  - The far-field scratch lives in one file-scope device array of
+ *    VFD_APPLY_NOALLOC_SCRATCH_BYTES bytes per device.  An operator and nrhs
+ *    whose scratch, 8 or 4 bytes (VFD_FP64 or VFD_FP32 operators) times
+ *    nrhs x (2 x tree nodes x rank + far levels x leaves x rank), rounded up
+ *    to 256-byte pieces, exceeds that size is rejected with VFD_EINVAL and a
+ *    message that gives both sizes; nothing is launched then.
+ *  - Nothing in the scratch has to start at zero: every entry read is written
+ *    earlier in the same call.
+ *  - All kernels run in order on `stream`; the far field is not overlapped
+ *    with the near field (so it can be slower than vfd_apply).
+ *  - Low-precision operators always take the column-by-column path (K in
+ *    FP32, B + M in FP64), never the batched tensor-core path.
+ *  - Setup: the first call on each device (with that device current) looks up
+ *    the device address of the scratch array once (cudaGetSymbolAddress);
+ *    make that first call before any stream capture begins.
+ *  - Calls that overlap in time on the same device (other streams or host
+ *    threads) share the one scratch array and race; order them, e.g. on one
+ *    stream.  X and Y must not overlap.
+ * Errors: VFD_EINVAL (null or host pointers, bad nrhs / ld, scratch too
+ * small), VFD_EUNSUPPORTED (device ordinal >= 64), VFD_ECUDA. */
+vfd_status vfd_apply_noalloc(vfd_op_t op, const double *X, double *Y, int64_t nrhs, int64_t ld, void *stream);
+
 /* Solve A U = F by conjugate gradients (Sec. 7: "conjugate gradient
  * solver"), every iteration on the device, column by column for nrhs > 1.
  * F, U: host or device, n_dof x nrhs, leading dimension ld; U holds the

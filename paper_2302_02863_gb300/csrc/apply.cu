@@ -15,6 +15,7 @@
 //   5. k_far_expand: after the join, Y[i] += sum_l Ul^(l)[i] . yhat[ancestor]
 // Tree order is the DoF order, so every leaf's x and y are contiguous.
 #include <algorithm>
+#include <mutex>
 
 #include "device_common.cuh"
 
@@ -366,6 +367,108 @@ void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, doub
                  cudaStream_t st)
 {
     apply_parts_ex(m, op, parts, X, Y, nrhs, ld, op.precision == VFD_FP32, st, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Apply without any allocation (vfd_apply_noalloc).  The far-field scratch
+// (node sums xhat, node results yhat, per-level leaf projections) lives in a
+// fixed file-scope device array instead of operator workspaces, and the whole
+// sequence runs on the caller's stream (no side stream, no events).  Every
+// word of the scratch that a kernel reads has been written earlier in the
+// same call, so nothing in it has to start at zero.  Two calls in flight at
+// once on one device share the array and race.
+// ---------------------------------------------------------------------------
+static_assert(VFD_APPLY_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VFD_APPLY_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// the scratch address on the current device, looked up once per device
+void *noalloc_scratch()
+{
+    int dev = -1;
+    VFD_CUDA(cudaGetDevice(&dev));
+    VFD_REQUIRE(dev >= 0 && dev < NOALLOC_MAX_DEVICES, VFD_EUNSUPPORTED, "vfd_apply_noalloc: device ordinal >= 64");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        VFD_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        VFD_REQUIRE(p != nullptr, VFD_ECUDA, "vfd_apply_noalloc: no address for the static scratch");
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+// the launches of apply_impl, in order, on one stream
+template <class T, class A>
+void apply_one_stream(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
+                      const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, cudaStream_t st)
+{
+    const int k = m.k, fl = m.kt.first_leaf(), L = m.kt.L, nnode = m.kt.nnode;
+    const int64_t hs = (int64_t)nnode * k;
+    FarView F;
+    F.use = m.nfar > 0 ? 1 : 0;
+    F.lmin = m.far_lmin;
+    F.L = L;
+    F.nlev = F.use ? L - m.far_lmin + 1 : 0;
+    F.k = k;
+    F.N = m.N;
+    const bool near = m.nnear > 0;
+    FarView Fn = F;
+    Fn.use = 0;
+    if (F.use) {
+        dim3 gp(m.kt.nleaf, F.nlev, nrhs);
+        k_far_proj<T, A><<<gp, 128, 0, st>>>(F, fl, m.kt.nleaf, m.kt_begin.p, m.kt_end.p, Ul, X, ld, part, nullptr);
+        const int nn = nnode - ((1 << F.lmin) - 1);
+        dim3 gs(nn, nrhs);
+        k_far_sum<A><<<gs, 128, 0, st>>>(F, m.kt.nleaf, part, xhat, hs, nullptr);
+        dim3 gc(nnode, nrhs);
+        k_far_couple<T, A><<<gc, 256, 0, st>>>(F, m.far_ptr.p, m.far_col.p, S, xhat, yhat, hs, nullptr);
+    }
+    const int NR = 16;
+    dim3 go(m.kt.nleaf, cdiv(m.max_leaf_size, NR), nrhs);
+    size_t shm = near ? (size_t)m.max_panel_w * sizeof(T) : 0;
+    k_near_csr<T, A><<<go, 128, shm, st>>>(fl, NR, m.kt_begin.p, m.kt_end.p, m.near_ptr.p, m.near_col.p, m.near_off.p,
+                                           m.panel_w.p, m.panel_off.p, m.gcol.p, m.gcol_off.p, D, near ? 1 : 0,
+                                           m.rowptr.p, m.colidx.p, op.valBM.p, Fn, Ul, yhat, hs, X, ld, Y, nullptr);
+    if (F.use) {
+        dim3 ge(cdiv(m.N, 4), nrhs);
+        k_far_expand<T, A><<<ge, 128, 0, st>>>(F, fl, m.vleaf.p, Ul, yhat, hs, Y, ld, nullptr);
+    }
+    VFD_CUDA(cudaGetLastError());
+}
+}  // namespace
+
+// Y = A X (all parts) as apply_parts computes it, scratch in g_noalloc_scratch
+void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
+                   cudaStream_t st)
+{
+    const bool lowp = op.precision == VFD_FP32;
+    const size_t es = lowp ? sizeof(float) : sizeof(double);
+    const int nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
+    const size_t nh = (size_t)m.kt.nnode * m.k * nrhs;
+    const size_t np = (size_t)std::max(nlev, 1) * m.kt.nleaf * m.k * nrhs;
+    const size_t bh = round256(nh * es), need = 2 * bh + round256(np * es);
+    if (need > (size_t)VFD_APPLY_NOALLOC_SCRATCH_BYTES) {
+        char msg[256];
+        snprintf(msg, sizeof msg,
+                 "vfd_apply_noalloc: this operator and nrhs = %d need %zu bytes of far-field scratch; the static "
+                 "scratch holds %zu bytes (use vfd_apply, or fewer columns per call)",
+                 nrhs, need, (size_t)VFD_APPLY_NOALLOC_SCRATCH_BYTES);
+        throw Error{VFD_EINVAL, msg};
+    }
+    unsigned char *base = (unsigned char *)noalloc_scratch();
+    if (lowp)
+        apply_one_stream<float, float>(m, op, X, Y, nrhs, ld, op.Ul32.p, op.S32.p, op.D32.p, (float *)base,
+                                       (float *)(base + bh), (float *)(base + 2 * bh), st);
+    else
+        apply_one_stream<double, double>(m, op, X, Y, nrhs, ld, m.Ul64.p, op.S64.p, op.D64.p, (double *)base,
+                                         (double *)(base + bh), (double *)(base + 2 * bh), st);
 }
 
 }  // namespace vfd

@@ -321,6 +321,20 @@ vfd_status vfd_apply_parts(vfd_op_t op, int parts, const double *X, double *Y, i
     return apply_common(op, parts, X, Y, nrhs, ld, stream);
 }
 
+vfd_status vfd_apply_noalloc(vfd_op_t h, const double *X, double *Y, int64_t nrhs, int64_t ld, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && X && Y, VFD_EINVAL, "null argument");
+    const OpData &op = *h->op;
+    const MeshData &m = *op.m;
+    VFD_REQUIRE(nrhs >= 1 && nrhs <= 65535 && ld >= m.N, VFD_EINVAL, "bad nrhs or ld");
+    VFD_REQUIRE(is_device_ptr(X) && is_device_ptr(Y), VFD_EINVAL,
+                "vfd_apply_noalloc: X and Y must be device pointers (host copies would need device buffers)");
+    apply_noalloc(m, op, X, Y, (int)nrhs, ld, (cudaStream_t)stream);
+    return VFD_OK;
+    VFD_API_END
+}
+
 vfd_status vfd_solve(vfd_op_t h, const double *F, double *U, int64_t nrhs, int64_t ld, double rtol, int max_it,
                      int *iters, double *relres, void *stream)
 {

@@ -258,6 +258,8 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
                     bool lowp, cudaStream_t st, const int *skip);
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                  cudaStream_t st);
+void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
+                   cudaStream_t st);
 // solve.cu
 void release_graphs(OpData &op);
 void release_streams(OpData &op);

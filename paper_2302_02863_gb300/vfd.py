@@ -24,6 +24,7 @@ VFD_FP64, VFD_FP32, VFD_BF16 = 0, 1, 2
 VFD_PART_B, VFD_PART_M, VFD_PART_KNEAR, VFD_PART_KFAR, VFD_PART_ALL = 1, 2, 4, 8, 15
 VFD_ASSEMBLE_UNCHECKED = 1
 VFD_ASSEMBLE_TIMED = 2
+VFD_APPLY_NOALLOC_SCRATCH_BYTES = 8388608   # static scratch of vfd_apply_noalloc, per device
 TIMING_KEYS = ["fields", "coupling", "near", "density", "singular", "gather", "total"]
 VFD_FIELD_ANALYTIC, VFD_FIELD_NODAL = 0, 1
 INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "nodes", "rank",
@@ -31,7 +32,7 @@ INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "no
              "rho_near_pairs", "near_storage"]
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
-           "vfd_apply", "vfd_apply_parts", "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings",
+           "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings",
            "vfd_selftest_math", "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
 
 
@@ -78,6 +79,7 @@ def load():
                                C.c_int, vp, C.POINTER(vp)]
     L.vfd_apply.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp]
     L.vfd_apply_parts.argtypes = [vp, C.c_int, vp, vp, C.c_int64, C.c_int64, vp]
+    L.vfd_apply_noalloc.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp]
     L.vfd_solve.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, C.c_double, C.c_int, C.POINTER(C.c_int),
                             dp, vp]
     L.vfd_load.argtypes = [vp, vp, vp, vp]
@@ -90,6 +92,7 @@ def load():
     L.vfd_free_mesh.restype = None
     L.vfd_last_error.restype = C.c_char_p
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
+              "vfd_apply_noalloc",
               "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -241,6 +244,13 @@ def vfd_apply(op, X, Y, stream=None):
 def vfd_apply_parts(op, parts, X, Y, stream=None):
     nrhs, ld = _nrhs_ld(X, op.mesh.n_dof)
     _check(load().vfd_apply_parts(op.handle, int(parts), _ptr(X), _ptr(Y), nrhs, ld, _stream(stream)))
+    return Y
+
+
+def vfd_apply_noalloc(op, X, Y, stream=None):
+    """Y = A X with no allocation inside the call (X, Y on the device)."""
+    nrhs, ld = _nrhs_ld(X, op.mesh.n_dof)
+    _check(load().vfd_apply_noalloc(op.handle, _ptr(X), _ptr(Y), nrhs, ld, _stream(stream)))
     return Y
 
 
