@@ -18,14 +18,14 @@ void mr_apply(const MeshData &m, OpData &op, const float *X, float *Y, int R, cu
 namespace {
 
 constexpr int BCHUNK = 8;
-constexpr int BNB = 256;   // reduction blocks
+constexpr int BT = 1024;   // threads of the reduction kernels (one block per SM)
 // per-column scalars (float arrays of Rp): rr, pq, alpha, beta, tol2
 enum { C_RR = 0, C_PQ = 1, C_AL = 2, C_BE = 3, C_TOL = 4, C_N = 5 };
 // flags (int): [0] all done, [1] iterations, [2] max_it, [3] counter
 enum { BF_DONE = 0, BF_IT = 1, BF_MAX = 2, BF_CNT = 3 };
 
-// Per-column sums over the rows of f(i, c); block = 256 threads = (256 / Rc)
-// row lanes x Rc columns with Rc = min(Rp, 256).  f may also update the
+// Per-column sums over the rows of f(i, c); block = BT threads = (BT / Rc)
+// row lanes x Rc columns with Rc = min(Rp, BT).  f may also update the
 // vectors at (i, c): each block visits the same (i, c) set in every kernel
 // that uses this helper, and reads only what it wrote itself.  The last block
 // reduces the block partials in fixed order and calls fin(c, total); returns
@@ -34,13 +34,14 @@ template <class Elem, class Fin>
 __device__ bool col_reduce(int N, int Rp, Elem f, float *part, unsigned *cnt, Fin fin)
 {
     __shared__ bool am_last;
-    __shared__ float sh[256];
+    __shared__ float sh[BT];
     const int Rc = min(Rp, (int)blockDim.x), lanes = blockDim.x / Rc;
     for (int c0 = 0; c0 < Rp; c0 += Rc) {
         const int cl = threadIdx.x % Rc, c = c0 + cl, rl = threadIdx.x / Rc;
         const bool ok = rl < lanes && c < Rp;
         float v = 0.f;
         if (ok)
+#pragma unroll 4
             for (int i = blockIdx.x * lanes + rl; i < N; i += gridDim.x * lanes) v += f((size_t)i * Rp + c);
         // fixed-order reduction over the row lanes of this block
         sh[threadIdx.x] = v;
@@ -60,15 +61,26 @@ __device__ bool col_reduce(int N, int Rp, Elem f, float *part, unsigned *cnt, Fi
     __syncthreads();
     if (!am_last) return false;
     __threadfence();
-    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+    // fixed-order reduction of the block partials: lane l of column c sums the
+    // blocks l, l + lanes, ... ; the lanes are then summed in order
+    for (int c0 = 0; c0 < Rp; c0 += Rc) {
+        const int cl = threadIdx.x % Rc, c = c0 + cl, rl = threadIdx.x / Rc;
         float s = 0.f;
-        for (int bI = 0; bI < (int)gridDim.x; ++bI) s += ((volatile float *)part)[(size_t)bI * Rp + c];
-        fin(c, s);
+        if (rl < lanes && c < Rp)
+            for (int bI = rl; bI < (int)gridDim.x; bI += lanes) s += __ldcg(part + (size_t)bI * Rp + c);
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        if (rl == 0 && c < Rp) {
+            float tot = 0.f;
+            for (int q = 0; q < lanes; ++q) tot += sh[q * Rc + cl];
+            fin(c, tot);
+        }
+        __syncthreads();
     }
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_b_init(int N, int Rp, const float *__restrict__ b, float *__restrict__ x,
+__global__ void __launch_bounds__(BT) k_b_init(int N, int Rp, const float *__restrict__ b, float *__restrict__ x,
                                                 float *__restrict__ r, float *__restrict__ p, float *part,
                                                 unsigned *cnt, float *sc, int *flag, float tol, int max_it)
 {
@@ -95,7 +107,7 @@ __global__ void __launch_bounds__(256) k_b_init(int N, int Rp, const float *__re
 }
 
 // pq = p.q per column; alpha = rr / pq (0 for converged columns)
-__global__ void __launch_bounds__(256) k_b_pq(int N, int Rp, const float *__restrict__ p, const float *__restrict__ q,
+__global__ void __launch_bounds__(BT) k_b_pq(int N, int Rp, const float *__restrict__ p, const float *__restrict__ q,
                                               float *part, unsigned *cnt, float *sc, const int *flag)
 {
     if (flag[BF_DONE]) return;
@@ -110,7 +122,7 @@ __global__ void __launch_bounds__(256) k_b_pq(int N, int Rp, const float *__rest
 }
 
 // x += alpha p; r -= alpha q; rr_new; beta; convergence of every column
-__global__ void __launch_bounds__(256) k_b_xr(int N, int Rp, float *__restrict__ x, float *__restrict__ r,
+__global__ void __launch_bounds__(BT) k_b_xr(int N, int Rp, float *__restrict__ x, float *__restrict__ r,
                                               const float *__restrict__ p, const float *__restrict__ q, float *part,
                                               unsigned *cnt, float *sc, int *flag)
 {
@@ -215,13 +227,22 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
 
 void release_bgraph(OpData &op);
 
+// blocks of the column reductions: one per SM of the current device
+static int nb_reduce()
+{
+    int dev = 0, nsm = 0;
+    VFD_CUDA(cudaGetDevice(&dev));
+    VFD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    return std::max(1, nsm);
+}
+
 // inner batched CG: z ~ A_low^-1 b on op.mb_b (interleaved [N][Rp]); returns iterations
 static int run_bcg(const MeshData &m, OpData &op, int Rp, float tol, int max_it, cudaStream_t st)
 {
     const int N = m.N;
     const int VB = std::max(1, std::min(cdiv((long long)N * Rp, 256), 2048));
     unsigned *cnt = (unsigned *)(op.mb_flag.p + BF_CNT);
-    k_b_init<<<BNB, 256, 0, st>>>(N, Rp, op.mb_b.p, op.mb_x.p, op.mb_r.p, op.mb_p.p, op.mb_part.p, cnt, op.mb_sc.p,
+    k_b_init<<<nb_reduce(), BT, 0, st>>>(N, Rp, op.mb_b.p, op.mb_x.p, op.mb_r.p, op.mb_p.p, op.mb_part.p, cnt, op.mb_sc.p,
                                   op.mb_flag.p, tol, max_it);
     VFD_CUDA(cudaGetLastError());
     // eager apply first: allocates the apply workspace outside the capture
@@ -236,8 +257,8 @@ static int run_bcg(const MeshData &m, OpData &op, int Rp, float tol, int max_it,
         try {
             for (int it = 0; it < BCHUNK; ++it) {
                 mr_apply(m, op, op.mb_p.p, op.mb_q.p, Rp, cs, op.mb_flag.p);
-                k_b_pq<<<BNB, 256, 0, cs>>>(N, Rp, op.mb_p.p, op.mb_q.p, op.mb_part.p, cnt, op.mb_sc.p, op.mb_flag.p);
-                k_b_xr<<<BNB, 256, 0, cs>>>(N, Rp, op.mb_x.p, op.mb_r.p, op.mb_p.p, op.mb_q.p, op.mb_part.p, cnt,
+                k_b_pq<<<nb_reduce(), BT, 0, cs>>>(N, Rp, op.mb_p.p, op.mb_q.p, op.mb_part.p, cnt, op.mb_sc.p, op.mb_flag.p);
+                k_b_xr<<<nb_reduce(), BT, 0, cs>>>(N, Rp, op.mb_x.p, op.mb_r.p, op.mb_p.p, op.mb_q.p, op.mb_part.p, cnt,
                                             op.mb_sc.p, op.mb_flag.p);
                 k_b_p<<<VB, 256, 0, cs>>>(N, Rp, op.mb_r.p, op.mb_p.p, op.mb_sc.p, op.mb_flag.p);
             }
@@ -277,7 +298,7 @@ vfd_status batched_solve(const MeshData &m, OpData &op, const double *F, double 
         op.mb_p.alloc(nv);
         op.mb_q.alloc(nv);
         op.mb_b.alloc(nv);
-        op.mb_part.alloc((size_t)BNB * Rp);
+        op.mb_part.alloc((size_t)nb_reduce() * Rp);
         op.mb_sc.alloc((size_t)C_N * Rp);
     }
     if (op.mb_flag.n < 8) {

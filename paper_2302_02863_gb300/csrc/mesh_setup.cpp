@@ -620,7 +620,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             m->nfar = (int)m->far_col_h.size();
             m->nnear = (int)m->near_col_h.size();
             // Near blocks of one row leaf form a row panel (row stride W_a = the
-            // partners' column counts, padded to a multiple of 4), so that a row's
+            // partners' column counts, padded to a multiple of 8), so that a row's
             // near entries are contiguous; block e starts at near_off[e].
             m->near_off_h.assign(m->nnear + 1, 0);
             std::vector<int> src(m->nnear, -1), prow(m->nnear), pw(nleaf, 0);
@@ -642,7 +642,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                         src[e] = (int)(it - m->near_col_h.begin());
                     }
                 }
-                w = (w + 3) & ~3;
+                w = (w + 7) & ~7;   // rows start on 16 bytes in FP64, FP32 and BF16
                 pw[a] = w;
                 m->max_panel_w = std::max(m->max_panel_w, w);
                 poff[a + 1] = poff[a] + (int64_t)na * w;

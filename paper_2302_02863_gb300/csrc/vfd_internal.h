@@ -149,7 +149,7 @@ struct MeshData {
     std::vector<int64_t> near_off_h;
     DBuf<int> near_ptr, near_col;
     DBuf<int64_t> near_off;    // offset of block e's (0,0) entry in its row leaf's panel
-    DBuf<int> panel_w;         // per row leaf: panel row stride (padded to 4)
+    DBuf<int> panel_w;         // per row leaf: panel row stride (padded to 8)
     DBuf<int64_t> panel_off;   // per row leaf: panel start (nleaf + 1)
     int64_t near_entries_alg = 0;   // sum |sigma||sigma'| over near blocks (no padding)
     DBuf<int> gcol, gcol_off;  // per panel column the DoF of its x entry (-1: padding)
@@ -203,7 +203,7 @@ struct OpData {
     DBuf<unsigned short> S16, D16, Ul16;   // BF16 copies (VFD_BF16)
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
     // batched (multi-RHS) low-precision apply and solve workspaces
-    DBuf<float> mr_part, mr_xh, mr_yh, mr_xi, mr_yi;
+    DBuf<float> mr_part, mr_xh, mr_yh, mr_xi, mr_yi, mr_y2;
     DBuf<float> mb_x, mb_r, mb_p, mb_q, mb_b, mb_part, mb_sc;
     DBuf<int> mb_flag;
     cudaGraphExec_t mb_exec = nullptr;
