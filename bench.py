@@ -15,6 +15,11 @@ rtol).  value = n_dof * nrhs * (operator applications in the step) / step
 time, i.e. matvec throughput delivered inside the full assemble + solve step;
 ms_per_step is the time to a 1e-10 solution from the fields.
 
+After the timed steps (outside the timed region) the line also carries
+"batched_mixed_precision": 64 seeded load vectors on the same fields, the
+batched apply and the iterative-refinement solve to 1e-8 with TF32 and with
+BF16 near panels, against FP64 column-by-column CG on the same GPU.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
   python bench.py --impl reference ...     (the CPU oracle on a bounded sample)
 
@@ -50,6 +55,7 @@ def _args():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--rtol", type=float, default=1e-10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the 64-RHS mixed-precision leg")
     p.add_argument("--mode", default="step", choices=["step", "apply"],
                    help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
     p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
@@ -311,6 +317,10 @@ def main():
     per_assemble = 4 + 1 + 2 + 2 + 1 + 1 + 1 + (4 if prec == vfd.VFD_FP32 else 0)
     gpu_launches = args.steps * (per_assemble + per_solve)
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(mesh, s, k, prm, torch, vfd, hbm=hbm)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -334,11 +344,77 @@ def main():
             "apply_dof_rhs_per_s": n / t_apply,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
-            "gpu_launches": gpu_launches, "clocks": clk, "mesh": info,
+            "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "batched_mixed_precision": batched,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def batched_leg(mesh, s, k, prm, torch, vfd, nrhs=64, rtol=1e-8, fp64_cols=8, hbm=6800.0):
+    """The mixed-precision batched path against the plain FP64 path on the same
+    operator fields: 64 seeded N(0,1) load vectors, batched apply throughput
+    (device-resident FP64 column-major X, as the C ABI takes it) and the
+    refinement solve to rtol (TF32 and BF16 near panels, FP64 residual); FP64
+    CG column by column on the first fp64_cols columns, per-column time x nrhs
+    as the FP64 estimate for all columns."""
+    n = mesh.n_dof
+    g = torch.Generator(device="cuda").manual_seed(3000)
+    F = torch.randn(nrhs, n, dtype=torch.float64, device="cuda", generator=g)
+    X = torch.randn(nrhs, n, dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.empty_like(X)
+    info = mesh.info
+    out = {"nrhs": nrhs, "rtol": rtol, "rhs": "seeded N(0,1)"}
+
+    def ev_time(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1000.0
+
+    op64 = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=vfd.VFD_FP64)
+    U64 = torch.zeros(fp64_cols, n, dtype=torch.float64, device="cuda")
+    vfd.vfd_apply(op64, X, Y)
+    Y64 = Y.clone()
+    torch.cuda.synchronize()
+    t64 = ev_time(lambda: vfd.vfd_solve(op64, F[:fp64_cols].contiguous(), U64.zero_(), rtol=rtol, max_it=100000), 1)
+    st, it64, rel64 = vfd.vfd_solve(op64, F[:fp64_cols].contiguous(), U64.zero_(), rtol=rtol, max_it=100000)
+    ta64 = ev_time(lambda: vfd.vfd_apply(op64, X, Y), 3)
+    out["fp64"] = {"apply_us": ta64 * 1e6, "apply_dof_rhs_per_s": n * nrhs / ta64,
+                   "solve_ms_per_col": 1000 * t64 / fp64_cols, "solve_ms_est_all_cols": 1000 * t64 / fp64_cols * nrhs,
+                   "cg_iters_mean": float(sum(it64) / len(it64)), "cols_timed": fp64_cols}
+    for name, prec, wbytes in (("tf32", vfd.VFD_FP32, 4), ("bf16", vfd.VFD_BF16, 2)):
+        op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec)
+        for _ in range(3):
+            vfd.vfd_apply(op, X, Y)
+        ta = ev_time(lambda: vfd.vfd_apply(op, X, Y), 20)
+        err_apply = (torch.linalg.norm(Y - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)).max().item()
+        U = torch.zeros_like(F)
+        vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)   # warm-up (graph capture)
+        U.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, it, rel = vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)
+        e1.record()
+        torch.cuda.synchronize()
+        ts = e0.elapsed_time(e1) / 1000.0
+        err_sol = (torch.linalg.norm(U[:fp64_cols] - U64, dim=1) / torch.linalg.norm(U64, dim=1)).max().item()
+        near_bytes = info["near_storage"] * wbytes + n * nrhs * 4 * 2 + info["nnz"] * 8
+        out[name] = {"apply_us": ta * 1e6, "apply_dof_rhs_per_s": n * nrhs / ta,
+                     "apply_rel_err_vs_fp64": err_apply, "solve_ms": ts * 1000, "status": int(st),
+                     "inner_iters": int(it[0]), "relres_max": float(rel.max()),
+                     "solution_rel_err_vs_fp64_cg": err_sol,
+                     "speedup_vs_fp64_solve": (t64 / fp64_cols * nrhs) / ts,
+                     "apply_near_bytes": near_bytes,
+                     "apply_near_bytes_over_time_gbs": near_bytes / ta / 1e9,
+                     "apply_near_bytes_frac_of_hbm": near_bytes / ta / 1e9 / hbm}
+        del op
+    del op64
+    return out
 
 
 def apply_mode(args, mesh, s, k, prm, prec, torch, vfd):
