@@ -65,6 +65,8 @@ def lib():
         L.oracle_num_threads.restype = C.c_int
         L.oracle_cg.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_int]
         L.oracle_cg.restype = C.c_int
+        L.oracle_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, ip, up, dp, dp, dp, C.c_int, dp, dp, dp, dp]
+        L.oracle_grad.restype = C.c_int
         _lib = L
     return _lib
 
@@ -145,6 +147,29 @@ def assemble(mesh, s, logk, s_bar=0.9, n_sing=3, tail=0, R=1.1, want_full=False)
     if n != N:
         raise RuntimeError("oracle_assemble failed")
     return Assembled(B=B, K=K, M=Mw, rho=rho, Afull=Af, dof=dof, N=N, seconds=t1 - t0)
+
+
+def grad(mesh, s_nodal, logk_nodal, U, Lam, s_bar=0.9, n_sing=3):
+    """g_s, g_logk (one entry per vertex) = -sum_r Lam_r^T (dA/dtheta) U_r for
+    P1 (nodal) s and log kappa: the derivative of the route-2 matrix B + K + M
+    term by term (kernel derivatives -ln|x-y| gamma and gamma/2 times the
+    basis functions at both points), bounded exterior (no tail).  U, Lam:
+    (N,) or (nrhs, N) in the DoF order of dofs()."""
+    X = np.ascontiguousarray(mesh.coords, dtype=np.float64)
+    T = np.ascontiguousarray(mesh.cells, dtype=np.int32)
+    inn = np.ascontiguousarray(mesh.cell_is_interior, dtype=np.uint8)
+    sn = np.ascontiguousarray(s_nodal, dtype=np.float64)
+    kn = np.ascontiguousarray(logk_nodal, dtype=np.float64)
+    U2 = np.ascontiguousarray(np.atleast_2d(U), dtype=np.float64)
+    L2 = np.ascontiguousarray(np.atleast_2d(Lam), dtype=np.float64)
+    gs = np.zeros(mesh.n_vert)
+    gk = np.zeros(mesh.n_vert)
+    params = np.array([s_bar, n_sing, 0, 0.0], dtype=np.float64)
+    n = lib().oracle_grad(mesh.d, mesh.n_vert, mesh.n_cell, _dp(X), _ip(T), _up(inn), _dp(sn), _dp(kn),
+                          _dp(params), U2.shape[0], _dp(U2), _dp(L2), _dp(gs), _dp(gk))
+    if n < 0 or U2.shape[1] != n:
+        raise ValueError("oracle_grad: bad input")
+    return gs, gk
 
 
 def pair_local(d, typ, P, Q, s, logk, s_bar, n_sing, pv=None, qv=None):

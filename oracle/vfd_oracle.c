@@ -793,6 +793,301 @@ int oracle_assemble(int d, int M, int C, const double *X, const int *T, const un
     return N;
 }
 
+/* ------------------------------------------------------------------------ */
+/* gradient of J = Lam^T U(theta) through the adjoint: g = -Lam^T (dA/dtheta) U */
+/* ------------------------------------------------------------------------ */
+/* The paper has no gradients; this is the derivative of the discrete matrix
+ * A = B + K + M assembled above (same quadrature, s_bar and rules held
+ * fixed) with respect to the nodal values of s and of log kappa (P1 fields).
+ * Every quadrature term carries gamma(x,y) = a(x,y) |x-y|^-(d+s(x)+s(y)), so
+ *   d gamma / d s_k      = -ln|x-y| (psi_k(x) + psi_k(y)) gamma,
+ *   d gamma / d logk_k   = 1/2      (psi_k(x) + psi_k(y)) gamma,
+ * and each term of B, K and M is differentiated where it is formed. */
+
+/* pair_fields plus the barycentric coordinates of the mapped points (in the
+ * pv / qv order of the pair) */
+static void pair_fields_b(const opair *pp, const ofield *fs, const ofield *fk, const double *xh, const double *yh,
+                          double *S, double *a, double *bx, double *by)
+{
+    double x[2], y[2];
+    if (pp->d == 2) {
+        ref_to_phys2(pp->P, xh, x); ref_to_phys2(pp->Q, yh, y);
+        bary2(xh, bx); bary2(yh, by);
+    } else {
+        x[0] = pp->P[0][0] + (pp->P[1][0] - pp->P[0][0]) * xh[0];
+        y[0] = pp->Q[0][0] + (pp->Q[1][0] - pp->Q[0][0]) * yh[0];
+        bx[0] = 1.0 - xh[0]; bx[1] = xh[0]; bx[2] = 0.0;
+        by[0] = 1.0 - yh[0]; by[1] = yh[0]; by[2] = 0.0;
+    }
+    double sx = field_eval(fs, pp->d, x, pp->pv, bx), sy = field_eval(fs, pp->d, y, pp->qv, by);
+    double kx = field_eval(fk, pp->d, x, pp->pv, bx), ky = field_eval(fk, pp->d, y, pp->qv, by);
+    *S = sx + sy;
+    *a = sqrt(exp(kx) * exp(ky));
+}
+
+/* one rule point of a touching pair: weight w (as in pair_singular), the
+ * local basis differences f[0..nl), dlw = d(log w)/dS (= -ln|x-y|, read off
+ * the factors of w that depend on S), barycentrics bx, by.  Accumulates
+ *   gs[a] (a < 3: vertex pv[a]; a >= 3: qv[a-3]) -= c dlw (bx | by),
+ *   gk[a] -= c/2 (bx | by),  c = w sum_r (U_r . f)(Lam_r . f). */
+static void grad_point(int nl, int nrhs, const double *Ul, const double *Ll, double w, const double *f, double dlw,
+                       const double *bx, const double *by, double *gs, double *gk)
+{
+    double ul = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+        double u = 0.0, l = 0.0;
+        for (int i = 0; i < nl; ++i) { u += Ul[r * nl + i] * f[i]; l += Ll[r * nl + i] * f[i]; }
+        ul += u * l;
+    }
+    double c = w * ul;
+    for (int a = 0; a < 3; ++a) {
+        gs[a] -= c * dlw * bx[a]; gs[3 + a] -= c * dlw * by[a];
+        gk[a] -= 0.5 * c * bx[a]; gk[3 + a] -= 0.5 * c * by[a];
+    }
+}
+
+/* gradient contributions of one touching pair (the loops of pair_singular) */
+static void pair_singular_grad(const opair *pp, const ofield *fs, const ofield *fk, double sbar, int ns,
+                               const double *gx, const double *gw, int nl, int nrhs, const double *Ul,
+                               const double *Ll, double *gs, double *gk)
+{
+    int d = pp->d;
+    double phi[5], a[2], b[2], bx[3], by[3];
+    if (d == 2 && (pp->type == 1 || pp->type == 2)) {
+        double c = 4.0 - 2.0 * sbar;
+        double pre = (2.0 * pp->measP) * (2.0 * pp->measQ) / c;
+        int nreg = pp->type == 1 ? 2 : 5;
+        for (int k = 0; k < nreg; ++k)
+            for (int iz = 0; iz < ns; ++iz)
+                for (int i1 = 0; i1 < ns; ++i1)
+                    for (int i2 = 0; i2 < ns; ++i2)
+                        for (int i3 = 0; i3 < ns; ++i3) {
+                            double eta[3] = {gx[i1], gx[i2], gx[i3]}, jac;
+                            if (pp->type == 1) region_vertex(k, eta, a, b, phi, &jac);
+                            else region_edge(k, eta, a, b, phi, &jac);
+                            double zeta = gx[iz], xi = pow(zeta, 1.0 / c);
+                            double xh[2] = {xi * a[0], xi * a[1]}, yh[2] = {xi * b[0], xi * b[1]};
+                            double S, aa;
+                            pair_fields_b(pp, fs, fk, xh, yh, &S, &aa, bx, by);
+                            double ja[2], jb[2];
+                            J_apply2(pp->P, a, ja); J_apply2(pp->Q, b, jb);
+                            double D = hypot(ja[0] - jb[0], ja[1] - jb[1]);
+                            double w = gw[iz] * gw[i1] * gw[i2] * gw[i3] * pre
+                                     * pow(zeta, (2.0 * sbar - S) / c) * jac * aa / pow(D, 2.0 + S);
+                            double dlw = -log(zeta) / c - log(D);
+                            grad_point(nl, nrhs, Ul, Ll, w, phi, dlw, bx, by, gs, gk);
+                        }
+    } else if (d == 2) {
+        double c = 4.0 - 2.0 * sbar, c2 = 2.0 - 2.0 * sbar;
+        double J2 = (2.0 * pp->measP) * (2.0 * pp->measP);
+        double pre = 2.0 * J2 / (c * c2);
+        double dref[2];
+        for (int k = 0; k < 3; ++k)
+            for (int iz = 0; iz < ns; ++iz)
+                for (int i1 = 0; i1 < ns; ++i1)
+                    for (int it = 0; it < ns; ++it)
+                        for (int i3 = 0; i3 < ns; ++i3) {
+                            double zeta = gx[iz], t = gx[it];
+                            double xi = pow(zeta, 1.0 / c), e1 = gx[i1], e2 = pow(t, 1.0 / c2), e3 = gx[i3];
+                            region_identical(k, e1, e2, e3, a, b, dref, phi);
+                            double xh[2] = {xi * a[0], xi * a[1]}, yh[2] = {xi * b[0], xi * b[1]};
+                            double S, aa;
+                            pair_fields_b(pp, fs, fk, xh, yh, &S, &aa, bx, by);
+                            double jd[2];
+                            J_apply2(pp->P, dref, jd);
+                            double D = hypot(jd[0], jd[1]);
+                            double w = gw[iz] * gw[i1] * gw[it] * gw[i3] * pre
+                                     * pow(zeta, (2.0 * sbar - S) / c) * pow(e1, 2.0 - S)
+                                     * pow(t, (2.0 * sbar - S) / c2) * aa / pow(D, 2.0 + S);
+                            double dlw = -log(zeta) / c - log(e1) - log(t) / c2 - log(D);
+                            grad_point(nl, nrhs, Ul, Ll, w, phi, dlw, bx, by, gs, gk);
+                        }
+    } else if (pp->type == 3) {
+        double c = 2.0 - 2.0 * sbar, h = pp->measP;
+        double pre = 2.0 * h * h / c;
+        for (int iz = 0; iz < ns; ++iz)
+            for (int it = 0; it < ns; ++it) {
+                double zeta = gx[iz], t = gx[it], z = pow(zeta, 1.0 / c);
+                double yh = (1.0 - z) * t, xh = yh + z;
+                double S, aa;
+                pair_fields_b(pp, fs, fk, &xh, &yh, &S, &aa, bx, by);
+                double psi[2] = {-1.0, 1.0};
+                double w = gw[iz] * gw[it] * pre * pow(zeta, (2.0 * sbar - S) / c) * (1.0 - z) * aa / pow(h, 1.0 + S);
+                double dlw = -log(zeta) / c - log(h);
+                grad_point(nl, nrhs, Ul, Ll, w, psi, dlw, bx, by, gs, gk);
+            }
+    } else {
+        double c = 3.0 - 2.0 * sbar;
+        double pre = pp->measP * pp->measQ / c;
+        double JP = pp->P[1][0] - pp->P[0][0], JQ = pp->Q[1][0] - pp->Q[0][0];
+        for (int k = 0; k < 2; ++k)
+            for (int iz = 0; iz < ns; ++iz)
+                for (int ie = 0; ie < ns; ++ie) {
+                    double zeta = gx[iz], eta = gx[ie], xi = pow(zeta, 1.0 / c);
+                    double av = k == 0 ? 1.0 : eta, bv = k == 0 ? eta : 1.0;
+                    double xh = xi * av, yh = xi * bv;
+                    double S, aa;
+                    pair_fields_b(pp, fs, fk, &xh, &yh, &S, &aa, bx, by);
+                    double D = fabs(JP * av - JQ * bv);
+                    double f[3] = {bv - av, av, -bv};
+                    double w = gw[iz] * gw[ie] * pre * pow(zeta, (2.0 * sbar - S) / c) * aa / pow(D, 1.0 + S);
+                    double dlw = -log(zeta) / c - log(D);
+                    grad_point(nl, nrhs, Ul, Ll, w, f, dlw, bx, by, gs, gk);
+                }
+    }
+}
+
+/* g_s[k] = -sum_r Lam_r^T (dA/ds_k) U_r and g_lk[k] likewise for log kappa,
+ * for P1 (nodal) s and log kappa given at all M vertices; A = B + K + M as in
+ * oracle_assemble (route 2; bounded exterior only: tail_mode must be 0).
+ * U, Lam: nrhs x N (row r contiguous, DoF order of oracle_dofs).  g_s, g_lk:
+ * M entries each, overwritten.  Returns N, or -1 on bad input. */
+int oracle_grad(int d, int M, int C, const double *X, const int *T, const unsigned char *in,
+                const double *snodal, const double *knodal, const double *params, int nrhs,
+                const double *U, const double *Lam, double *g_s, double *g_lk)
+{
+    omesh m = {d, M, C, X, T, in};
+    ofield fs = {NULL, snodal}, fk = {NULL, knodal};
+    double sbar = params[0];
+    int ns = (int)params[1], tail = (int)params[2];
+    int nv = d + 1;
+    if (!snodal || !knodal || tail != 0 || ns < 1 || ns > 64 || nrhs < 1) return -1;
+    int *dof = malloc(sizeof(int) * M);
+    int N = oracle_dofs(d, M, C, T, in, dof);
+    double gx[64], gw[64];
+    oracle_gauss01(ns, gx, gw);
+    oquad Q;
+    build_quad(&m, &fs, &fk, &Q);
+    int nq = Q.n / C;
+
+    /* U and Lam at the quadrature points (zero on exterior cells) */
+    double *Uq = calloc((size_t)nrhs * Q.n, sizeof(double)), *Lq = calloc((size_t)nrhs * Q.n, sizeof(double));
+    for (int r = 0; r < nrhs; ++r)
+        for (int iq = 0; iq < Q.n; ++iq) {
+            const int *t = T + Q.cell[iq] * nv;
+            double u = 0.0, l = 0.0;
+            for (int a = 0; a < nv; ++a) {
+                int i = dof[t[a]];
+                if (i >= 0) { u += Q.bary[iq * 3 + a] * U[(size_t)r * N + i]; l += Q.bary[iq * 3 + a] * Lam[(size_t)r * N + i]; }
+            }
+            Uq[(size_t)r * Q.n + iq] = u;
+            Lq[(size_t)r * Q.n + iq] = l;
+        }
+
+    int *vdeg = calloc(M + 1, sizeof(int));
+    for (int c = 0; c < C; ++c) for (int a = 0; a < nv; ++a) vdeg[T[c * nv + a] + 1]++;
+    for (int v = 0; v < M; ++v) vdeg[v + 1] += vdeg[v];
+    int *vcell = malloc(sizeof(int) * vdeg[M]);
+    int *fill = calloc(M, sizeof(int));
+    for (int c = 0; c < C; ++c) for (int a = 0; a < nv; ++a) { int v = T[c * nv + a]; vcell[vdeg[v] + fill[v]++] = c; }
+    free(fill);
+
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    double *acc = calloc((size_t)nth * 2 * M, sizeof(double));   /* per thread: g_s, g_lk */
+
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *gS = acc + (size_t)tid * 2 * M, *gK = gS + M;
+        char *mark = calloc(C, 1);
+        int *list = malloc(sizeof(int) * C);
+        double *Ul = malloc(sizeof(double) * nrhs * 5), *Ll = malloc(sizeof(double) * nrhs * 5);
+
+        /* ---- B: touching pairs (Sec. 4 rules), both orders by R1 / R1' ---- */
+#pragma omp for schedule(static)
+        for (int c = 0; c < C; ++c) {
+            int nl_ = 0;
+            for (int a = 0; a < nv; ++a) {
+                int v = T[c * nv + a];
+                for (int k = vdeg[v]; k < vdeg[v + 1]; ++k) {
+                    int c2 = vcell[k];
+                    if (!mark[c2]) { mark[c2] = 1; list[nl_++] = c2; }
+                }
+            }
+            for (int k = 0; k < nl_; ++k) {
+                int c2 = list[k];
+                mark[c2] = 0;
+                if (c2 < c) continue;
+                if (!in[c] && !in[c2]) continue;
+                opair pp; int loc[5];
+                int nl = make_pair(&m, c, c2, &pp, loc);
+                for (int r = 0; r < nrhs; ++r)
+                    for (int i = 0; i < nl; ++i) {
+                        int j = dof[loc[i]];
+                        Ul[r * nl + i] = j >= 0 ? U[(size_t)r * N + j] : 0.0;
+                        Ll[r * nl + i] = j >= 0 ? Lam[(size_t)r * N + j] : 0.0;
+                    }
+                double gs[6] = {0, 0, 0, 0, 0, 0}, gk[6] = {0, 0, 0, 0, 0, 0};
+                pair_singular_grad(&pp, &fs, &fk, sbar, ns, gx, gw, nl, nrhs, Ul, Ll, gs, gk);
+                double wgt = (c == c2) ? 1.0 : 2.0;
+                for (int a = 0; a < nv; ++a) {
+                    gS[pp.pv[a]] += wgt * gs[a]; gS[pp.qv[a]] += wgt * gs[3 + a];
+                    gK[pp.pv[a]] += wgt * gk[a]; gK[pp.qv[a]] += wgt * gk[3 + a];
+                }
+            }
+        }
+
+        /* ---- K (e:k, interior separated pairs) and M (e:m with rho of
+         * e:tgt-sum over all separated source points) ----
+         * per point pair (q in interior c, q' in c2 not touching c):
+         *   K: -2 w w' gamma Lam(q) U(q')   (c2 interior)
+         *   M:  2 w w' gamma Lam(q) U(q)    (the rho(q) sum)
+         * differentiated in gamma and contracted with -1. */
+#pragma omp for schedule(static)
+        for (int c = 0; c < C; ++c) {
+            if (!in[c]) continue;
+            const int *t = T + c * nv;
+            for (int a = 0; a < nv; ++a) {
+                int v = t[a];
+                for (int k = vdeg[v]; k < vdeg[v + 1]; ++k) mark[vcell[k]] = 1;
+            }
+            for (int c2 = 0; c2 < C; ++c2) {
+                if (mark[c2]) continue;
+                const int *u = T + c2 * nv;
+                for (int q = 0; q < nq; ++q)
+                    for (int q2 = 0; q2 < nq; ++q2) {
+                        int iq = c * nq + q, jq = c2 * nq + q2;
+                        double r = qdist(d, Q.x + iq * d, Q.x + jq * d);
+                        double G = kernel_gamma(d, r, Q.s[iq], Q.s[jq], Q.lk[iq], Q.lk[jq]) * Q.w[iq] * Q.w[jq];
+                        double lu = 0.0, mu = 0.0;
+                        for (int rr = 0; rr < nrhs; ++rr) {
+                            mu += Lq[(size_t)rr * Q.n + iq] * Uq[(size_t)rr * Q.n + iq];
+                            if (in[c2]) lu += Lq[(size_t)rr * Q.n + iq] * Uq[(size_t)rr * Q.n + jq];
+                        }
+                        /* g = -(dK + dM) contracted: dgamma_s = -ln r (...) gamma, dgamma_lk = (...) gamma / 2 */
+                        double ts = 2.0 * G * log(r) * (mu - lu);
+                        double tk = G * (lu - mu);
+                        for (int a = 0; a < nv; ++a) {
+                            double bq = Q.bary[iq * 3 + a], bq2 = Q.bary[jq * 3 + a];
+                            gS[t[a]] += ts * bq; gS[u[a]] += ts * bq2;
+                            gK[t[a]] += tk * bq; gK[u[a]] += tk * bq2;
+                        }
+                    }
+            }
+            for (int a = 0; a < nv; ++a) {
+                int v = t[a];
+                for (int k = vdeg[v]; k < vdeg[v + 1]; ++k) mark[vcell[k]] = 0;
+            }
+        }
+        free(mark); free(list); free(Ul); free(Ll);
+    }
+    for (int v = 0; v < M; ++v) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int th = 0; th < nth; ++th) { a1 += acc[(size_t)th * 2 * M + v]; a2 += acc[(size_t)th * 2 * M + M + v]; }
+        g_s[v] = a1;
+        g_lk[v] = a2;
+    }
+    free(acc); free(Uq); free(Lq); free(vdeg); free(vcell); free(dof);
+    free_quad(&Q);
+    return N;
+}
+
 /* P1 load vector F_i = int f_h psi_i over interior cells (exact P1 mass
  * matrix times nodal f), DoF order of oracle_dofs. */
 int oracle_load(int d, int M, int C, const double *X, const int *T, const unsigned char *in,
