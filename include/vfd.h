@@ -248,6 +248,25 @@ vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int6
  * nodal values f at all n_vert vertices).  f_nodal, F: host or device. */
 vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *stream);
 
+/* Adjoint gradient (the paper has no gradients; derivative of the discrete
+ * operator A = B + K + M of Sec. 3 with every quadrature rule and s_bar held
+ * fixed):
+ *   g_s[k]        = -sum_r Lam_r^T (dA/ds_k) U_r,
+ *   g_logkappa[k] = -sum_r Lam_r^T (dA/dlogkappa_k) U_r,
+ * for P1 (nodal) fields s and log kappa, k over all n_vert vertices.  With
+ * A Lam = dJ/dU this is dJ/dtheta of any J(U(theta)).  The kernel
+ * derivatives are -ln|x-y| gamma (psi_k(x) + psi_k(y)) and
+ * gamma (psi_k(x) + psi_k(y)) / 2; touching pairs go through the singular
+ * rules of Sec. 4, separated pairs through the element rules.
+ * U, Lam: device, n_dof x nrhs, leading dimension ld.  g_s, g_logkappa:
+ * device, n_vert doubles each, overwritten.  The operator's fields must be
+ * VFD_FIELD_NODAL (such operators have no low-rank part) and the mesh must
+ * have tail_mode 0.  The separated pairs are summed directly: O(n_q^2) work.
+ * Errors: VFD_EINVAL (null or host pointers, bad nrhs / ld), VFD_EUNSUPPORTED
+ * (analytic fields, exterior tail), VFD_ECUDA. */
+vfd_status vfd_grad(vfd_op_t op, const double *U, const double *Lam, int64_t nrhs, int64_t ld, double *g_s,
+                    double *g_logkappa, void *stream);
+
 /* Density rho (incl. tail) at the interior quadrature points, ordered by
  * interior cell (increasing cell id) then element-rule point (triangle:
  * the point nearest to stored vertex 0, 1, 2; interval: Gauss points left

@@ -392,6 +392,23 @@ vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *str
     VFD_API_END
 }
 
+vfd_status vfd_grad(vfd_op_t h, const double *U, const double *Lam, int64_t nrhs, int64_t ld, double *g_s,
+                    double *g_logkappa, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && U && Lam && g_s && g_logkappa, VFD_EINVAL, "null argument");
+    OpData &op = *h->op;
+    MeshData &m = *op.m;
+    VFD_REQUIRE(op.fs.nodal && op.fk.nodal, VFD_EUNSUPPORTED, "vfd_grad needs P1 (nodal) s and log kappa");
+    VFD_REQUIRE(m.opts.tail_mode == 0, VFD_EUNSUPPORTED, "vfd_grad needs a bounded exterior (tail_mode 0)");
+    VFD_REQUIRE(nrhs >= 1 && ld >= m.N, VFD_EINVAL, "bad nrhs or ld");
+    VFD_REQUIRE(is_device_ptr(U) && is_device_ptr(Lam) && is_device_ptr(g_s) && is_device_ptr(g_logkappa),
+                VFD_EINVAL, "vfd_grad: U, Lam, g_s and g_logkappa must be device pointers");
+    grad_exact(m, op, U, Lam, (int)nrhs, ld, g_s, g_logkappa, (cudaStream_t)stream);
+    return VFD_OK;
+    VFD_API_END
+}
+
 vfd_status vfd_op_rho(vfd_op_t h, double *rho, void *stream)
 {
     VFD_API_BEGIN

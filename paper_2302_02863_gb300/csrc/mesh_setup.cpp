@@ -559,6 +559,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                 }
             }
             m->pair_info.upload(pinfo);
+            m->pair_info_h = pinfo;
         }
 
         // ---- K tree: support-extended boxes (Sec. 5.1, omega^e), Chebyshev nodes

@@ -123,6 +123,10 @@ struct MeshData {
     // touching pairs (unordered, canonical orientation)
     int npairs = 0;
     DBuf<int> pair_info;   // npairs * 8: type, w(1|2), pv0..2, qv0..2
+    std::vector<int> pair_info_h;   // host copy
+    // gradient gather lists (built on the first vfd_grad): vertex -> point*3 + slot, vertex -> pair*6 + slot
+    bool grad_lists = false;
+    DBuf<int> gq_ptr, gq_idx, gp_ptr, gp_idx;
     // B/M sparsity (DoF CSR) and deterministic gather lists
     int nnz = 0;
     DBuf<int> rowptr, colidx;
@@ -204,6 +208,8 @@ struct OpData {
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
     // batched (multi-RHS) low-precision apply and solve workspaces
     DBuf<float> mr_part, mr_xh, mr_yh, mr_xi, mr_yi, mr_y2;
+    // adjoint gradient workspaces
+    DBuf<double> gr_uq, gr_lq, gr_hs, gr_h1, gr_pg;
     DBuf<float> mb_x, mb_r, mb_p, mb_q, mb_b, mb_part, mb_sc;
     DBuf<int> mb_flag;
     cudaGraphExec_t mb_exec = nullptr;
@@ -258,6 +264,8 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
                     bool lowp, cudaStream_t st, const int *skip);
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                  cudaStream_t st);
+void grad_exact(MeshData &m, OpData &op, const double *U, const double *Lam, int nrhs, int64_t ld, double *g_s,
+                double *g_lk, cudaStream_t st);
 void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
                    cudaStream_t st);
 // solve.cu

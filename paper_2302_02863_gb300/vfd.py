@@ -32,7 +32,7 @@ INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "no
              "rho_near_pairs", "near_storage"]
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
-           "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings",
+           "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_grad", "vfd_load", "vfd_op_rho", "vfd_op_timings",
            "vfd_selftest_math", "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
 
 
@@ -80,6 +80,7 @@ def load():
     L.vfd_apply.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp]
     L.vfd_apply_parts.argtypes = [vp, C.c_int, vp, vp, C.c_int64, C.c_int64, vp]
     L.vfd_apply_noalloc.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp]
+    L.vfd_grad.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp, vp, vp]
     L.vfd_solve.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, C.c_double, C.c_int, C.POINTER(C.c_int),
                             dp, vp]
     L.vfd_load.argtypes = [vp, vp, vp, vp]
@@ -92,7 +93,7 @@ def load():
     L.vfd_free_mesh.restype = None
     L.vfd_last_error.restype = C.c_char_p
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
-              "vfd_apply_noalloc",
+              "vfd_apply_noalloc", "vfd_grad",
               "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -252,6 +253,13 @@ def vfd_apply_noalloc(op, X, Y, stream=None):
     nrhs, ld = _nrhs_ld(X, op.mesh.n_dof)
     _check(load().vfd_apply_noalloc(op.handle, _ptr(X), _ptr(Y), nrhs, ld, _stream(stream)))
     return Y
+
+
+def vfd_grad(op, U, Lam, g_s, g_logk, stream=None):
+    """g_s, g_logk (device, n_vert) = -sum_r Lam_r^T (dA/dtheta) U_r for nodal fields."""
+    nrhs, ld = _nrhs_ld(U, op.mesh.n_dof)
+    _check(load().vfd_grad(op.handle, _ptr(U), _ptr(Lam), nrhs, ld, _ptr(g_s), _ptr(g_logk), _stream(stream)))
+    return g_s, g_logk
 
 
 def vfd_solve(op, F, U, rtol=1e-10, max_it=10000, stream=None, raise_on_noconv=False):
