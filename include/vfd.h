@@ -52,6 +52,7 @@ typedef enum {
 
 typedef struct vfd_mesh_s *vfd_mesh_t;
 typedef struct vfd_op_s *vfd_op_t;
+typedef struct vfd_batch_s *vfd_batch_t;
 
 /* Precision of the assembled operator (argument `precision`). */
 enum {
@@ -247,6 +248,37 @@ vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int6
 /* P1 load F = M0 f (exact P1 mass matrix of the interior cells times the
  * nodal values f at all n_vert vertices).  f_nodal, F: host or device. */
 vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *stream);
+
+/* Batch of operators (meshes) for the batched low-precision path: one
+ * launch per stage over a global queue of work items of all meshes, and one
+ * batched refinement solve with scalars per (mesh, column).  The paper solves
+ * one mesh at a time; the batch is a throughput construction on top of the
+ * per-mesh operators of Sec. 5-7.
+ * ops: nops operators, all VFD_FP32 or all VFD_BF16, leaves of at most 64
+ * DoFs; they must outlive the batch (not owned).  Errors: VFD_EINVAL,
+ * VFD_EUNSUPPORTED, VFD_ENOMEM. */
+vfd_status vfd_batch_create(const vfd_op_t *ops, int nops, vfd_batch_t *out);
+
+/* Y_m = A_low,m X_m for every mesh m of the batch: the batched apply of
+ * vfd_apply (near panels on the tensor cores in TF32 or BF16, B + M and the
+ * far field in FP32) for all meshes at once.  X, Y: host arrays of nops
+ * device pointers, block m n_dof(m) x nrhs, leading dimension ld[m];
+ * nrhs a multiple of 64. */
+vfd_status vfd_batch_apply(vfd_batch_t batch, const double *const *X, double *const *Y, const int64_t *ld,
+                           int64_t nrhs, void *stream);
+
+/* Solve A_m U_m = F_m for every mesh (nrhs columns each) by iterative
+ * refinement: FP64 residuals with each mesh's FP64 operator, inner batched
+ * CG on the low-precision operators of all meshes at once (per-(mesh,
+ * column) scalars, inner tolerance 1e-4), until ||F - A U|| <= rtol ||F||
+ * for every column of every mesh.  F, U: host arrays of nops device
+ * pointers (U holds the initial guess).  iters, relres: host, nops x nrhs
+ * (mesh-major), may be NULL.  VFD_ENOCONV when max_it inner iterations did
+ * not suffice (U holds the last iterate). */
+vfd_status vfd_batch_solve(vfd_batch_t batch, const double *const *F, double *const *U, const int64_t *ld,
+                           int64_t nrhs, double rtol, int max_it, int *iters, double *relres, void *stream);
+
+void vfd_batch_free(vfd_batch_t batch);
 
 /* Adjoint gradient (the paper has no gradients; derivative of the discrete
  * operator A = B + K + M of Sec. 3 with every quadrature rule and s_bar held

@@ -1,7 +1,12 @@
 // Batched multi-RHS apply of the low-precision operator (the inner operator
-// of iterative refinement) for R right-hand sides at once, R a multiple of 64.
+// of iterative refinement) for R right-hand sides at once, R a multiple of 64,
+// over a batch of operators (meshes) in one launch per stage: every kernel
+// walks a global queue of work items (mesh, leaf) or (mesh, node) and reads
+// the mesh's pointers and sizes from a device table of descriptors.  A
+// single operator is a batch of one.
 // Vectors are FP32 in the interleaved layout X[i][r] (DoF-major, RHS
-// contiguous), so every gather of one DoF's entries is one contiguous read.
+// contiguous; the meshes' rows one after another), so every gather of one
+// DoF's entries is one contiguous read.
 //
 //   near panels: per (leaf, 64-RHS tile) a dense product Y = D_panel Xg on the
 //     tensor cores (mma.sync m16n8k16 BF16 or m16n8k8 TF32, FP32 accumulate):
@@ -13,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "device_common.cuh"
 
@@ -21,6 +27,21 @@ namespace vfd {
 namespace {
 
 constexpr int RT = 64;   // RHS per tile
+
+}  // namespace
+
+// one operator of a batch, as the kernels see it (device-resident table)
+struct MrMesh {
+    int N, fl, k, L, lmin, nlev, nleaf, nnode, has_near, has_far;
+    long long xoff;   // first row of this mesh in the batch vectors
+    const int *kb, *ke, *pw, *gcol, *goff, *rowptr, *colidx, *fptr, *fcol;
+    const int64_t *poff;
+    const void *D, *Ul, *S;   // near panels, level bases, coupling blocks (FP32 or BF16)
+    const float *val;         // B + M in FP32 (CSR)
+    float *part, *xhat, *yhat;   // far-field workspaces of this mesh
+};
+
+namespace {
 
 template <class T>
 struct MmaTraits;
@@ -132,20 +153,26 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 
 template <class T>
 __global__ void __launch_bounds__(NEAR_THREADS)
-k_mr_near(int fl, int R, const int *__restrict__ kb, const int *__restrict__ ke, const int *__restrict__ pw,
-          const int64_t *__restrict__ poff, const int *__restrict__ gcol, const int *__restrict__ goff,
-          const T *__restrict__ D, const float *__restrict__ X, float *__restrict__ Y, float *__restrict__ Y2,
-          const int *skip)
+k_mr_near(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
+          float *__restrict__ Yall, float *__restrict__ Y2all, const int *skip)
 {
     using TT = NearTile<T>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (skip && *skip) return;
-    const int lf = blockIdx.x, rt = blockIdx.y * RT;
-    const int b0 = kb[fl + lf], na = ke[fl + lf] - b0;
-    const int W = pw[lf];   // multiple of 8
-    const T *Dp = D + poff[lf];
+    const int2 item = items[blockIdx.x];
+    const MrMesh &Ms = ms[item.x];
+    const int lf = item.y, rt = blockIdx.y * RT, fl = Ms.fl;
+    const size_t xo = (size_t)Ms.xoff * R;
+    const float *__restrict__ X = Xall + xo;
+    float *__restrict__ Y = Yall + xo;
+    float *__restrict__ Y2 = Y2all + xo;
+    const T *__restrict__ D = (const T *)Ms.D;
+    const int b0 = Ms.kb[fl + lf], na = Ms.ke[fl + lf] - b0;
+    const int W = Ms.pw[lf];   // multiple of 8
+    const T *Dp = D + Ms.poff[lf];
     int *gs = (int *)(smem + NSTAGE * TT::STAGE_BYTES);
-    for (int c = threadIdx.x; c < W; c += NEAR_THREADS) gs[c] = gcol[goff[lf] + c];
+    const int *gcol = Ms.gcol + Ms.goff[lf];
+    for (int c = threadIdx.x; c < W; c += NEAR_THREADS) gs[c] = gcol[c];
     __syncthreads();
 
     auto load_stage = [&](int slot, int chunk) {
@@ -227,26 +254,41 @@ k_mr_near(int fl, int R, const int *__restrict__ kb, const int *__restrict__ ke,
 }
 
 template <class T>
-static size_t near_smem_bytes(const MeshData &m)
+static size_t near_smem_bytes(int max_panel_w)
 {
-    return (size_t)NSTAGE * NearTile<T>::STAGE_BYTES + (size_t)m.max_panel_w * sizeof(int);
+    return (size_t)NSTAGE * NearTile<T>::STAGE_BYTES + (size_t)max_panel_w * sizeof(int);
 }
 
 // Y[i][r..r+3] = (Y + Y2)[i][r..r+3] + sum_c val[c] X[col c][r..r+3]   (B + M
 // in FP32 added to the two partial near products; thread per (row, 4 RHS);
 // accumulate = 0: no near products)
-__global__ void k_mr_csr(int N, int R, int accumulate, const int *__restrict__ rowptr, const int *__restrict__ colidx,
-                         const float *__restrict__ val, const float *__restrict__ X, float *__restrict__ Y,
-                         const float *__restrict__ Y2, const int *skip)
+__global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restrict__ row_off, int nmesh,
+                         long long ntot, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
+                         const float *__restrict__ Y2all, const int *skip)
 {
     if (skip && *skip) return;
     const int R4 = R >> 2;
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)N * R4) return;
+    long long tg = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tg >= ntot * R4) return;
+    const long long ig = tg / R4;
+    int lo = 0, hi = nmesh - 1;   // the mesh holding row ig: row_off[mesh] <= ig < row_off[mesh + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= ig) lo = mid;
+        else hi = mid - 1;
+    }
+    const MrMesh &Ms = ms[lo];
+    const size_t xo = (size_t)Ms.xoff * R;
+    const float *__restrict__ X = Xall + xo;
+    float *__restrict__ Y = Yall + xo;
+    const float *__restrict__ Y2 = Y2all + xo;
+    const int *__restrict__ rowptr = Ms.rowptr, *__restrict__ colidx = Ms.colidx;
+    const float *__restrict__ val = Ms.val;
+    const long long t = tg - Ms.xoff * R4;
     const int i = (int)(t / R4), q = (int)(t % R4);
     const float4 *X4 = (const float4 *)X;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (accumulate) {
+    if (Ms.has_near) {
         const float4 a = ((const float4 *)Y)[t], b = ((const float4 *)Y2)[t];
         acc = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
     }
@@ -279,15 +321,20 @@ __device__ __forceinline__ void fma4(float4 &acc, float u, const float4 x)
 // by chunk.
 template <class T>
 __global__ void __launch_bounds__(256)
-k_mr_far_proj(int fl, int k, int nlev, int N, int R, const int *__restrict__ kb, const int *__restrict__ ke,
-              const T *__restrict__ Ul, const float *__restrict__ X, float *__restrict__ part, int nleaf,
+k_mr_far_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
               const int *skip)
 {
     __shared__ float4 Xs[64][RT / 4];
     extern __shared__ float Us[];   // [n][nlev * k]
     if (skip && *skip) return;
-    const int leaf = blockIdx.x, rt = blockIdx.y * RT;
-    const int b = kb[fl + leaf], n = ke[fl + leaf] - b;
+    const int2 item = items[blockIdx.x];
+    const MrMesh &Ms = ms[item.x];
+    const int leaf = item.y, rt = blockIdx.y * RT;
+    const int fl = Ms.fl, k = Ms.k, nlev = Ms.nlev, N = Ms.N, nleaf = Ms.nleaf;
+    const float *__restrict__ X = Xall + (size_t)Ms.xoff * R;
+    const T *__restrict__ Ul = (const T *)Ms.Ul;
+    float *__restrict__ part = Ms.part;
+    const int b = Ms.kb[fl + leaf], n = Ms.ke[fl + leaf] - b;
     const int R4 = R >> 2, NL = nlev * k;
     for (int e = threadIdx.x; e < n * (RT / 4); e += blockDim.x) {
         const int i = e / (RT / 4), q = e % (RT / 4);
@@ -323,11 +370,14 @@ k_mr_far_proj(int fl, int k, int nlev, int N, int R, const int *__restrict__ kb,
 }
 
 // xhat[node][a][r] = sum over the node's leaves of part (levels lmin..L)
-__global__ void k_mr_far_sum(int lmin, int L, int k, int R, int nleaf, const float *__restrict__ part,
-                             float *__restrict__ xhat, const int *skip)
+__global__ void k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip)
 {
     if (skip && *skip) return;
-    const int node = (1 << lmin) - 1 + blockIdx.x;
+    const int2 item = items[blockIdx.x];
+    const MrMesh &Ms = ms[item.x];
+    const int node = item.y, lmin = Ms.lmin, L = Ms.L, k = Ms.k, nleaf = Ms.nleaf;
+    const float *__restrict__ part = Ms.part;
+    float *__restrict__ xhat = Ms.xhat;
     const int t = blockIdx.y * blockDim.x + threadIdx.x;
     if (t >= k * R / 4) return;
     int l = 0;
@@ -373,12 +423,17 @@ __host__ __device__ constexpr int couple_sbytes(int k)
 
 template <class T>
 __global__ void __launch_bounds__(64)
-k_mr_far_couple(int k, int R, const int *__restrict__ fptr, const int *__restrict__ fcol, const T *__restrict__ S,
-                const float *__restrict__ xhat, float *__restrict__ yhat, const int *skip)
+k_mr_far_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip)
 {
     extern __shared__ __align__(16) unsigned char csm[];
     if (skip && *skip) return;
-    const int node = blockIdx.x, rt = blockIdx.y * RT;
+    const int2 item = items[blockIdx.x];
+    const MrMesh &Ms = ms[item.x];
+    const int node = item.y, rt = blockIdx.y * RT, k = Ms.k;
+    const int *__restrict__ fptr = Ms.fptr, *__restrict__ fcol = Ms.fcol;
+    const T *__restrict__ S = (const T *)Ms.S;
+    const float *__restrict__ xhat = Ms.xhat;
+    float *__restrict__ yhat = Ms.yhat;
     const int rq = threadIdx.x & 15, g = threadIdx.x >> 4;
     const int R4 = R >> 2;
     const int sbytes = couple_sbytes<T>(k), xbytes = k * RT * 4, slot_bytes = EPS * (sbytes + xbytes);
@@ -441,13 +496,19 @@ k_mr_far_couple(int k, int R, const int *__restrict__ fptr, const int *__restric
 // memory; thread (r-quad = t % 16, g = t / 16) owns rows g + 16 q (q < 4).
 template <class T>
 __global__ void __launch_bounds__(256)
-k_mr_far_expand(int fl, int lmin, int L, int k, int N, int R, const int *__restrict__ kb, const int *__restrict__ ke,
-                const T *__restrict__ Ul, const float *__restrict__ yhat, float *__restrict__ Y, const int *skip)
+k_mr_far_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
+                const int *skip)
 {
     extern __shared__ float4 Ys[];   // [nlev * k][16], then Us[nlev * k][64] (floats)
     if (skip && *skip) return;
-    const int leaf = blockIdx.x, rt = blockIdx.y * RT;
-    const int b = kb[fl + leaf], n = ke[fl + leaf] - b;
+    const int2 item = items[blockIdx.x];
+    const MrMesh &Ms = ms[item.x];
+    const int leaf = item.y, rt = blockIdx.y * RT;
+    const int fl = Ms.fl, lmin = Ms.lmin, L = Ms.L, k = Ms.k, N = Ms.N;
+    const T *__restrict__ Ul = (const T *)Ms.Ul;
+    const float *__restrict__ yhat = Ms.yhat;
+    float *__restrict__ Y = Yall + (size_t)Ms.xoff * R;
+    const int b = Ms.kb[fl + leaf], n = Ms.ke[fl + leaf] - b;
     const int nlev = L - lmin + 1, NL = nlev * k, R4 = R >> 2;
     float *Us = (float *)(Ys + NL * 16);
     for (int e = threadIdx.x; e < NL * 16; e += blockDim.x) {
@@ -485,75 +546,191 @@ k_mr_far_expand(int fl, int lmin, int L, int k, int N, int R, const int *__restr
 }
 
 // ---------------------------------------------------------------------------
-void release_bgraph(OpData &op);
+// host side: descriptors, work items, workspaces, launches
+// ---------------------------------------------------------------------------
+BatchData::~BatchData() { release_bgraph(*this); }
+
+void release_bgraph(BatchData &b)
+{
+    if (b.exec) {
+        cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+    }
+}
+
+BatchData *op_batch(OpData &op)
+{
+    if (!op.self) {
+        BatchData *b = new BatchData();
+        b->ops.push_back(&op);
+        b->nmesh = 1;
+        b->precision = op.precision;
+        b->ntot = op.m->N;
+        b->xoff = {0, (int64_t)op.m->N};
+        op.self = b;
+    }
+    return op.self;
+}
+
+static void upload_items(DBuf<int> &buf, const std::vector<int> &v)
+{
+    buf.upload(v.empty() ? std::vector<int>{0, 0} : v);
+}
+
+// descriptors, item queues and workspaces for R columns (allocates: call
+// outside stream capture; a captured solve is released when they change)
+static void ensure_batch(BatchData &b, int R)
+{
+    if (b.R == R) return;
+    release_bgraph(b);
+    const bool bf = b.precision == VFD_BF16;
+    size_t np = 0, nh = 0;
+    b.max_panel_w = b.max_k = b.max_nlev = b.max_leaf = 0;
+    b.any_far = false;
+    for (OpData *op : b.ops) {
+        const MeshData &m = *op->m;
+        VFD_REQUIRE(op->precision == b.precision, VFD_EINVAL, "batched apply: operators of different precision");
+        VFD_REQUIRE(op->precision != VFD_FP64, VFD_EINVAL, "batched apply needs VFD_FP32 or VFD_BF16 operators");
+        VFD_REQUIRE(m.max_leaf_size <= 64, VFD_EUNSUPPORTED, "batched apply needs leaves of at most 64 DoFs");
+        const int nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
+        if (m.nfar > 0) {
+            np += (size_t)nlev * m.kt.nleaf * m.k * R;
+            nh += (size_t)m.kt.nnode * m.k * R;
+            b.any_far = true;
+            b.max_nlev = std::max(b.max_nlev, nlev);
+        }
+        b.max_panel_w = std::max(b.max_panel_w, m.max_panel_w);
+        b.max_k = std::max(b.max_k, m.k);
+        b.max_leaf = std::max(b.max_leaf, m.max_leaf_size);
+    }
+    VFD_REQUIRE(near_smem_bytes<float>(b.max_panel_w) <= 227 * 1024, VFD_EUNSUPPORTED,
+                "batched apply: near panel too wide");
+    VFD_REQUIRE(2 * EPS * ((size_t)couple_sbytes<float>(b.max_k) + (size_t)b.max_k * RT * sizeof(float)) <= 227 * 1024,
+                VFD_EUNSUPPORTED, "batched apply: rank too large for the coupling tile");
+    VFD_REQUIRE(!b.any_far || (size_t)b.max_nlev * b.max_k * (RT + 64) * sizeof(float) <= 227 * 1024,
+                VFD_EUNSUPPORTED, "batched apply: too many far levels x rank for the expansion tile");
+    VFD_REQUIRE(!b.any_far || (size_t)b.max_leaf * b.max_nlev * b.max_k * sizeof(float) + 64 * RT * sizeof(float) <=
+                                  227 * 1024,
+                VFD_EUNSUPPORTED, "batched apply: too many far levels x rank for the projection tile");
+    b.part.alloc(std::max<size_t>(np, 1));
+    b.xhat.alloc(std::max<size_t>(nh, 1));
+    b.yhat.alloc(std::max<size_t>(nh, 1));
+    b.y2.alloc((size_t)b.ntot * R);
+    std::vector<MrMesh> d(b.nmesh);
+    std::vector<int> li, si, ni, nri;
+    size_t po = 0, ho = 0;
+    for (int i = 0; i < b.nmesh; ++i) {
+        const OpData &op = *b.ops[i];
+        const MeshData &m = *op.m;
+        MrMesh &e = d[i];
+        e.N = m.N;
+        e.fl = m.kt.first_leaf();
+        e.k = m.k;
+        e.L = m.kt.L;
+        e.lmin = m.far_lmin;
+        e.nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
+        e.nleaf = m.kt.nleaf;
+        e.nnode = m.kt.nnode;
+        e.has_near = m.nnear > 0;
+        e.has_far = m.nfar > 0;
+        e.xoff = b.xoff[i];
+        e.kb = m.kt_begin.p;
+        e.ke = m.kt_end.p;
+        e.pw = m.panel_w.p;
+        e.gcol = m.gcol.p;
+        e.goff = m.gcol_off.p;
+        e.rowptr = m.rowptr.p;
+        e.colidx = m.colidx.p;
+        e.fptr = m.far_ptr.p;
+        e.fcol = m.far_col.p;
+        e.poff = m.panel_off.p;
+        e.D = bf ? (const void *)op.D16.p : (const void *)op.D32.p;
+        e.Ul = bf ? (const void *)op.Ul16.p : (const void *)op.Ul32.p;
+        e.S = bf ? (const void *)op.S16.p : (const void *)op.S32.p;
+        e.val = op.valBM32.p;
+        e.part = b.part.p + po;
+        e.xhat = b.xhat.p + ho;
+        e.yhat = b.yhat.p + ho;
+        if (m.nfar > 0) {
+            po += (size_t)e.nlev * m.kt.nleaf * m.k * R;
+            ho += (size_t)m.kt.nnode * m.k * R;
+        }
+        for (int lf = 0; lf < m.kt.nleaf; ++lf) {
+            if (m.nnear > 0) {
+                nri.push_back(i);
+                nri.push_back(lf);
+            }
+            if (m.nfar > 0) {
+                li.push_back(i);
+                li.push_back(lf);
+            }
+        }
+        if (m.nfar > 0) {
+            for (int nd = (1 << m.far_lmin) - 1; nd < m.kt.nnode; ++nd) {
+                si.push_back(i);
+                si.push_back(nd);
+            }
+            for (int nd = 0; nd < m.kt.nnode; ++nd) {
+                ni.push_back(i);
+                ni.push_back(nd);
+            }
+        }
+    }
+    std::vector<unsigned char> bytes(sizeof(MrMesh) * d.size());
+    memcpy(bytes.data(), d.data(), bytes.size());
+    b.desc.upload(bytes);
+    upload_items(b.leaf_items, li);
+    upload_items(b.sum_items, si);
+    upload_items(b.node_items, ni);
+    upload_items(b.near_items, nri);
+    b.n_leaf_items = (int)li.size() / 2;
+    b.n_sum_items = (int)si.size() / 2;
+    b.n_node_items = (int)ni.size() / 2;
+    b.n_near_items = (int)nri.size() / 2;
+    std::vector<long long> ro(b.xoff.begin(), b.xoff.end());
+    b.row_off.upload(ro);
+    b.R = R;
+}
 
 template <class T>
-static void mr_apply_impl(const MeshData &m, OpData &op, const float *X, float *Y, int R, const T *D, const T *Ul,
-                          const T *S, cudaStream_t st, const int *skip)
+static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip)
 {
-    const int fl = m.kt.first_leaf(), k = m.k, N = m.N;
-    const bool far = m.nfar > 0;
-    const int nlev = far ? m.kt.L - m.far_lmin + 1 : 0;
-    if (m.nnear > 0) {
-        if (op.mr_y2.n < (size_t)N * R) {
-            release_bgraph(op);   // a captured solve refers to the old workspace
-            op.mr_y2.alloc((size_t)N * R);
-        }
-        const size_t shm = near_smem_bytes<T>(m);
+    const MrMesh *ms = (const MrMesh *)b.desc.p;
+    if (b.n_near_items > 0) {
+        const size_t shm = near_smem_bytes<T>(b.max_panel_w);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        dim3 g(m.kt.nleaf, R / RT, KSPLIT);
-        k_mr_near<T><<<g, NEAR_THREADS, shm, st>>>(fl, R, m.kt_begin.p, m.kt_end.p, m.panel_w.p, m.panel_off.p,
-                                                   m.gcol.p, m.gcol_off.p, D, X, Y, op.mr_y2.p, skip);
+        dim3 g(b.n_near_items, R / RT, KSPLIT);
+        k_mr_near<T><<<g, NEAR_THREADS, shm, st>>>(ms, (const int2 *)b.near_items.p, R, X, Y, b.y2.p, skip);
     }
-    k_mr_csr<<<cdiv((long long)N * (R / 4), 256), 256, 0, st>>>(N, R, m.nnear > 0 ? 1 : 0, m.rowptr.p, m.colidx.p,
-                                                                 op.valBM32.p, X, Y, op.mr_y2.p, skip);
-    if (far) {
-        const size_t need_p = (size_t)nlev * m.kt.nleaf * k * R, need_h = (size_t)m.kt.nnode * k * R;
-        if (op.mr_part.n < need_p || op.mr_xh.n < need_h) {
-            release_bgraph(op);   // a captured solve refers to the old workspace
-            op.mr_part.alloc(need_p);
-            op.mr_xh.alloc(need_h);
-            op.mr_yh.alloc(need_h);
-        }
-        dim3 gp(m.kt.nleaf, R / RT);
-        const size_t pshm = (size_t)m.max_leaf_size * nlev * k * sizeof(float);
+    k_mr_csr<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R, X,
+                                                                      Y, b.y2.p, skip);
+    if (b.any_far) {
+        const int k = b.max_k, nlev = b.max_nlev;
+        dim3 gp(b.n_leaf_items, R / RT);
+        const size_t pshm = (size_t)b.max_leaf * nlev * k * sizeof(float);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-        k_mr_far_proj<T><<<gp, 256, pshm, st>>>(fl, k, nlev, N, R, m.kt_begin.p, m.kt_end.p, Ul, X, op.mr_part.p,
-                                                m.kt.nleaf, skip);
-        const int nn = m.kt.nnode - ((1 << m.far_lmin) - 1);
-        dim3 gs(nn, cdiv(k * R / 4, 128));
-        k_mr_far_sum<<<gs, 128, 0, st>>>(m.far_lmin, m.kt.L, k, R, m.kt.nleaf, op.mr_part.p, op.mr_xh.p, skip);
-        dim3 gc(m.kt.nnode, R / RT);
+        k_mr_far_proj<T><<<gp, 256, pshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip);
+        dim3 gs(b.n_sum_items, cdiv(k * R / 4, 128));
+        k_mr_far_sum<<<gs, 128, 0, st>>>(ms, (const int2 *)b.sum_items.p, R, skip);
+        dim3 gc(b.n_node_items, R / RT);
         const size_t cshm = 2 * EPS * ((size_t)couple_sbytes<T>(k) + (size_t)k * RT * sizeof(float));
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
-        k_mr_far_couple<T><<<gc, 64, cshm, st>>>(k, R, m.far_ptr.p, m.far_col.p, S, op.mr_xh.p, op.mr_yh.p, skip);
+        k_mr_far_couple<T><<<gc, 64, cshm, st>>>(ms, (const int2 *)b.node_items.p, R, skip);
         const size_t eshm = (size_t)nlev * k * (RT + 64) * sizeof(float);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eshm));
-        dim3 ge(m.kt.nleaf, R / RT);
-        k_mr_far_expand<T><<<ge, 256, eshm, st>>>(fl, m.far_lmin, m.kt.L, k, N, R, m.kt_begin.p, m.kt_end.p, Ul,
-                                                  op.mr_yh.p, Y, skip);
+        dim3 ge(b.n_leaf_items, R / RT);
+        k_mr_far_expand<T><<<ge, 256, eshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip);
     }
     VFD_CUDA(cudaGetLastError());
 }
 
-// Y = A_low X for R (multiple of 64) interleaved FP32 columns
-void mr_apply(const MeshData &m, OpData &op, const float *X, float *Y, int R, cudaStream_t st, const int *skip)
+// Y = A_low X for R (multiple of 64) interleaved FP32 columns over all meshes
+void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip)
 {
-    VFD_REQUIRE(R % RT == 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
-    VFD_REQUIRE(m.max_leaf_size <= 64, VFD_EUNSUPPORTED, "batched apply needs leaves of at most 64 DoFs");
-    VFD_REQUIRE(near_smem_bytes<float>(m) <= 227 * 1024, VFD_EUNSUPPORTED, "batched apply: near panel too wide");
-    VFD_REQUIRE(2 * EPS * ((size_t)couple_sbytes<float>(m.k) + (size_t)m.k * RT * sizeof(float)) <= 227 * 1024,
-                VFD_EUNSUPPORTED, "batched apply: rank too large for the coupling tile");
-    VFD_REQUIRE(m.nfar == 0 || (size_t)(m.kt.L - m.far_lmin + 1) * m.k * (RT + 64) * sizeof(float) <= 227 * 1024,
-                VFD_EUNSUPPORTED, "batched apply: too many far levels x rank for the expansion tile");
-    VFD_REQUIRE(m.nfar == 0 || (size_t)m.max_leaf_size * (m.kt.L - m.far_lmin + 1) * m.k * sizeof(float) +
-                                       64 * RT * sizeof(float) <= 227 * 1024,
-                VFD_EUNSUPPORTED, "batched apply: too many far levels x rank for the projection tile");
-    if (op.precision == VFD_BF16)
-        mr_apply_impl<__nv_bfloat16>(m, op, X, Y, R, (const __nv_bfloat16 *)op.D16.p,
-                                     (const __nv_bfloat16 *)op.Ul16.p, (const __nv_bfloat16 *)op.S16.p, st, skip);
-    else
-        mr_apply_impl<float>(m, op, X, Y, R, op.D32.p, op.Ul32.p, op.S32.p, st, skip);
+    VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
+    ensure_batch(b, R);
+    if (b.precision == VFD_BF16) batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip);
+    else batch_apply_impl<float>(b, X, Y, R, st, skip);
 }
 
 // column-major FP64 <-> interleaved FP32
@@ -573,18 +750,26 @@ __global__ void k_il_to_cm(int N, int R, int64_t ld, const float *__restrict__ Y
     Y[(size_t)r * ld + i] = (double)Yi[(size_t)i * R + r];
 }
 
-// Y = A_low X for column-major FP64 blocks (nrhs a multiple of 64)
-void mr_apply_colmajor(const MeshData &m, OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
-                       cudaStream_t st)
+// Y_m = A_low,m X_m for every mesh m (column-major FP64 blocks, nrhs a multiple of 64)
+void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,
+                          cudaStream_t st)
 {
-    const size_t n = (size_t)m.N * nrhs;
-    if (op.mr_xi.n < n) {
-        op.mr_xi.alloc(n);
-        op.mr_yi.alloc(n);
+    const size_t n = (size_t)b.ntot * nrhs;
+    if (b.xi.n < n) {
+        b.xi.alloc(n);
+        b.yi.alloc(n);
     }
-    k_cm_to_il<<<cdiv((long long)n, 256), 256, 0, st>>>(m.N, nrhs, ld, X, op.mr_xi.p);
-    mr_apply(m, op, op.mr_xi.p, op.mr_yi.p, nrhs, st, nullptr);
-    k_il_to_cm<<<cdiv((long long)n, 256), 256, 0, st>>>(m.N, nrhs, ld, op.mr_yi.p, Y);
+    for (int i = 0; i < b.nmesh; ++i) {
+        const int N = b.ops[i]->m->N;
+        k_cm_to_il<<<cdiv((long long)N * nrhs, 256), 256, 0, st>>>(N, nrhs, ld[i], X[i],
+                                                                   b.xi.p + (size_t)b.xoff[i] * nrhs);
+    }
+    batch_apply(b, b.xi.p, b.yi.p, nrhs, st, nullptr);
+    for (int i = 0; i < b.nmesh; ++i) {
+        const int N = b.ops[i]->m->N;
+        k_il_to_cm<<<cdiv((long long)N * nrhs, 256), 256, 0, st>>>(N, nrhs, ld[i], b.yi.p + (size_t)b.xoff[i] * nrhs,
+                                                                   Y[i]);
+    }
     VFD_CUDA(cudaGetLastError());
 }
 

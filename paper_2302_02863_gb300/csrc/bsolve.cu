@@ -1,11 +1,13 @@
-// Batched mixed-precision solve of A U = F for R right-hand sides (the CG of
-// the paper's Sec. 7 run on all columns at once): iterative refinement with
-// an FP64 residual F - A U from the FP64 operator, and an inner batched CG on
-// the low-precision operator (K in TF32 or BF16 on the tensor cores, B + M in
-// FP32) in FP32 vectors of interleaved layout [N][Rp] (Rp = R rounded up to
-// 64).  Per-column scalars; deterministic per-column reductions (block
-// partials summed in a fixed order by the last block); a device flag ends a
-// captured chunk of iterations once every column has converged.
+// Batched mixed-precision solve of A_m U_m = F_m for a batch of operators
+// (meshes) m with R right-hand sides each (the CG of the paper's Sec. 7 run
+// on all columns of all meshes at once): iterative refinement with an FP64
+// residual F - A U from each mesh's FP64 operator, and an inner batched CG on
+// the low-precision operators (K in TF32 or BF16 on the tensor cores, B + M in
+// FP32) in FP32 vectors of interleaved layout [sum N_m][Rp] (Rp = R rounded
+// up to 64).  Scalars per (mesh, column); deterministic segmented reductions
+// (every reduction block works inside one mesh; the last block of a mesh sums
+// that mesh's block partials in a fixed order); a device flag ends a captured
+// chunk of iterations once every column of every mesh has converged.
 #include <algorithm>
 #include <cmath>
 
@@ -13,158 +15,183 @@
 
 namespace vfd {
 
-void mr_apply(const MeshData &m, OpData &op, const float *X, float *Y, int R, cudaStream_t st, const int *skip);
-
 namespace {
 
 constexpr int BCHUNK = 8;
-constexpr int BT = 1024;   // threads of the reduction kernels (one block per SM)
-// per-column scalars (float arrays of Rp): rr, pq, alpha, beta, tol2
+constexpr int BT = 1024;   // threads of the reduction kernels
+// per (mesh, column) scalars, arrays of nmesh * Rp floats: rr, pq, alpha, beta, tol2
 enum { C_RR = 0, C_PQ = 1, C_AL = 2, C_BE = 3, C_TOL = 4, C_N = 5 };
-// flags (int): [0] all done, [1] iterations, [2] max_it, [3] counter
-enum { BF_DONE = 0, BF_IT = 1, BF_MAX = 2, BF_CNT = 3 };
+// flags (int): [0] all done, [1] iterations, [2] max_it, [3] mesh-finish counter,
+// then per mesh: a block counter (FL_CNT + m) and its live-column count (FL_CNT + nmesh + m)
+enum { BF_DONE = 0, BF_IT = 1, BF_MAX = 2, BF_GCNT = 3, FL_CNT = 4 };
 
-// Per-column sums over the rows of f(i, c); block = BT threads = (BT / Rc)
-// row lanes x Rc columns with Rc = min(Rp, BT).  f may also update the
-// vectors at (i, c): each block visits the same (i, c) set in every kernel
-// that uses this helper, and reads only what it wrote itself.  The last block
-// reduces the block partials in fixed order and calls fin(c, total); returns
-// true in that block.
+struct Seg {
+    int nmesh, Rp;
+    const int *items;        // per block: mesh, index of the block inside the mesh
+    const int *mesh;         // per mesh: first block, blocks, rows, first row
+    float *red;              // block partials, nred x Rp
+    int *flag;
+    float *sc;               // C_N x (nmesh * Rp)
+};
+
+__device__ __forceinline__ float &scal(const Seg &S, int kind, int m, int c)
+{
+    return S.sc[(size_t)kind * S.nmesh * S.Rp + (size_t)m * S.Rp + c];
+}
+
+// Per-(mesh, column) sums over the mesh's rows of f(global element index).
+// Block = BT threads = (BT / Rc) row lanes x Rc columns, Rc = min(Rp, BT); the
+// blocks of a mesh stride over its rows.  f may also update the vectors at
+// its element: every kernel using this helper visits the same elements in
+// the same block, and a block reads only what it wrote itself.  The last
+// block of the mesh reduces the mesh's partials in a fixed order and calls
+// fin(mesh, c, total); returns the mesh in that block, else -1.
 template <class Elem, class Fin>
-__device__ bool col_reduce(int N, int Rp, Elem f, float *part, unsigned *cnt, Fin fin)
+__device__ int seg_reduce(const Seg &S, Elem f, Fin fin)
 {
     __shared__ bool am_last;
     __shared__ float sh[BT];
-    const int Rc = min(Rp, (int)blockDim.x), lanes = blockDim.x / Rc;
+    const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
+    const int b0 = S.mesh[4 * m], nb = S.mesh[4 * m + 1], N = S.mesh[4 * m + 2], r0 = S.mesh[4 * m + 3];
+    const int Rp = S.Rp, Rc = min(Rp, (int)blockDim.x), lanes = blockDim.x / Rc;
     for (int c0 = 0; c0 < Rp; c0 += Rc) {
         const int cl = threadIdx.x % Rc, c = c0 + cl, rl = threadIdx.x / Rc;
-        const bool ok = rl < lanes && c < Rp;
         float v = 0.f;
-        if (ok)
+        if (rl < lanes && c < Rp)
 #pragma unroll 4
-            for (int i = blockIdx.x * lanes + rl; i < N; i += gridDim.x * lanes) v += f((size_t)i * Rp + c);
-        // fixed-order reduction over the row lanes of this block
+            for (int i = j * lanes + rl; i < N; i += nb * lanes) v += f((size_t)(r0 + i) * Rp + c, m, c);
         sh[threadIdx.x] = v;
         __syncthreads();
         if (rl == 0 && c < Rp) {
             float s = 0.f;
             for (int q = 0; q < lanes; ++q) s += sh[q * Rc + cl];
-            part[(size_t)blockIdx.x * Rp + c] = s;
+            S.red[(size_t)blockIdx.x * Rp + c] = s;
         }
         __syncthreads();
     }
     __threadfence();
     if (threadIdx.x == 0) {
-        unsigned v = atomicInc(cnt, gridDim.x - 1);
-        am_last = (v == gridDim.x - 1);
+        unsigned v = atomicInc((unsigned *)&S.flag[FL_CNT + m], nb - 1);
+        am_last = (v == (unsigned)(nb - 1));
     }
     __syncthreads();
-    if (!am_last) return false;
+    if (!am_last) return -1;
     __threadfence();
-    // fixed-order reduction of the block partials: lane l of column c sums the
-    // blocks l, l + lanes, ... ; the lanes are then summed in order
     for (int c0 = 0; c0 < Rp; c0 += Rc) {
         const int cl = threadIdx.x % Rc, c = c0 + cl, rl = threadIdx.x / Rc;
         float s = 0.f;
         if (rl < lanes && c < Rp)
-            for (int bI = rl; bI < (int)gridDim.x; bI += lanes) s += __ldcg(part + (size_t)bI * Rp + c);
+            for (int bI = rl; bI < nb; bI += lanes) s += __ldcg(S.red + (size_t)(b0 + bI) * Rp + c);
         sh[threadIdx.x] = s;
         __syncthreads();
         if (rl == 0 && c < Rp) {
             float tot = 0.f;
             for (int q = 0; q < lanes; ++q) tot += sh[q * Rc + cl];
-            fin(c, tot);
+            fin(m, c, tot);
         }
         __syncthreads();
     }
-    return true;
+    return m;
 }
 
-__global__ void __launch_bounds__(BT) k_b_init(int N, int Rp, const float *__restrict__ b, float *__restrict__ x,
-                                                float *__restrict__ r, float *__restrict__ p, float *part,
-                                                unsigned *cnt, float *sc, int *flag, float tol, int max_it)
+__global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ b, float *__restrict__ x,
+                                               float *__restrict__ r, float *__restrict__ p, float tol, int max_it)
 {
-    col_reduce(
-        N, Rp,
-        [&](size_t t) {
+    seg_reduce(
+        S,
+        [&](size_t t, int, int) {
             const float v = b[t];
             x[t] = 0.f;
             r[t] = v;
             p[t] = v;
             return v * v;
         },
-        part, cnt, [&](int c, float s) {
-            sc[C_RR * Rp + c] = s;
-            sc[C_TOL * Rp + c] = tol * tol * s;
-            sc[C_AL * Rp + c] = 0.f;
-            sc[C_BE * Rp + c] = 0.f;
+        [&](int m, int c, float s) {
+            scal(S, C_RR, m, c) = s;
+            scal(S, C_TOL, m, c) = tol * tol * s;
+            scal(S, C_AL, m, c) = 0.f;
+            scal(S, C_BE, m, c) = 0.f;
         });
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        flag[BF_IT] = 0;
-        flag[BF_MAX] = max_it;
-        flag[BF_DONE] = max_it <= 0 ? 1 : 0;
+        S.flag[BF_IT] = 0;
+        S.flag[BF_MAX] = max_it;
+        S.flag[BF_DONE] = max_it <= 0 ? 1 : 0;
     }
 }
 
-// pq = p.q per column; alpha = rr / pq (0 for converged columns)
-__global__ void __launch_bounds__(BT) k_b_pq(int N, int Rp, const float *__restrict__ p, const float *__restrict__ q,
-                                              float *part, unsigned *cnt, float *sc, const int *flag)
+// pq = p.q per (mesh, column); alpha = rr / pq (0 for converged columns)
+__global__ void __launch_bounds__(BT) k_b_pq(Seg S, const float *__restrict__ p, const float *__restrict__ q)
 {
-    if (flag[BF_DONE]) return;
-    col_reduce(
-        N, Rp, [&](size_t t) { return p[t] * q[t]; }, part, cnt,
-        [&](int c, float s) {
-            float rr = sc[C_RR * Rp + c];
-            bool live = rr > sc[C_TOL * Rp + c] && s > 0.f;
-            sc[C_PQ * Rp + c] = s;
-            sc[C_AL * Rp + c] = live ? rr / s : 0.f;
+    if (S.flag[BF_DONE]) return;
+    seg_reduce(
+        S, [&](size_t t, int, int) { return p[t] * q[t]; },
+        [&](int m, int c, float s) {
+            const float rr = scal(S, C_RR, m, c);
+            const bool live = rr > scal(S, C_TOL, m, c) && s > 0.f;
+            scal(S, C_PQ, m, c) = s;
+            scal(S, C_AL, m, c) = live ? rr / s : 0.f;
         });
 }
 
 // x += alpha p; r -= alpha q; rr_new; beta; convergence of every column
-__global__ void __launch_bounds__(BT) k_b_xr(int N, int Rp, float *__restrict__ x, float *__restrict__ r,
-                                              const float *__restrict__ p, const float *__restrict__ q, float *part,
-                                              unsigned *cnt, float *sc, int *flag)
+__global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float *__restrict__ r,
+                                             const float *__restrict__ p, const float *__restrict__ q)
 {
-    if (flag[BF_DONE]) return;
+    if (S.flag[BF_DONE]) return;
     __shared__ int live;
+    __shared__ bool all_last;
     if (threadIdx.x == 0) live = 0;
     __syncthreads();
-    const bool last = col_reduce(
-        N, Rp,
-        [&](size_t t) {
-            const float al = sc[C_AL * Rp + (int)(t % Rp)];
+    const int m = seg_reduce(
+        S,
+        [&](size_t t, int mm, int c) {
+            const float al = scal(S, C_AL, mm, c);
             x[t] = fmaf(al, p[t], x[t]);
             const float rn = fmaf(-al, q[t], r[t]);
             r[t] = rn;
             return rn * rn;
         },
-        part, cnt, [&](int c, float s) {
-            float rr = sc[C_RR * Rp + c];
-            bool was_live = sc[C_AL * Rp + c] != 0.f;
-            if (was_live) {
-                sc[C_BE * Rp + c] = rr > 0.f ? s / rr : 0.f;
-                sc[C_RR * Rp + c] = s;
-                if (s > sc[C_TOL * Rp + c]) atomicAdd(&live, 1);
+        [&](int mm, int c, float s) {
+            const float rr = scal(S, C_RR, mm, c);
+            if (scal(S, C_AL, mm, c) != 0.f) {
+                scal(S, C_BE, mm, c) = rr > 0.f ? s / rr : 0.f;
+                scal(S, C_RR, mm, c) = s;
+                if (s > scal(S, C_TOL, mm, c)) atomicAdd(&live, 1);
             } else {
-                sc[C_BE * Rp + c] = 0.f;
+                scal(S, C_BE, mm, c) = 0.f;
             }
         });
-    if (!last) return;
+    if (m < 0) return;
     __syncthreads();
+    // the last mesh to finish decides for the whole batch
     if (threadIdx.x == 0) {
-        int it = flag[BF_IT] + 1;
-        flag[BF_IT] = it;
-        if (live == 0 || it >= flag[BF_MAX]) flag[BF_DONE] = 1;
+        S.flag[FL_CNT + S.nmesh + m] = live;
+        __threadfence();
+        unsigned v = atomicInc((unsigned *)&S.flag[BF_GCNT], S.nmesh - 1);
+        all_last = (v == (unsigned)(S.nmesh - 1));
     }
+    __syncthreads();
+    if (!all_last || threadIdx.x != 0) return;
+    __threadfence();
+    int tot = 0;
+    for (int mm = 0; mm < S.nmesh; ++mm) tot += __ldcg(S.flag + FL_CNT + S.nmesh + mm);
+    const int it = S.flag[BF_IT] + 1;
+    S.flag[BF_IT] = it;
+    if (tot == 0 || it >= S.flag[BF_MAX]) S.flag[BF_DONE] = 1;
 }
 
-__global__ void k_b_p(int N, int Rp, const float *__restrict__ r, float *__restrict__ p, const float *sc,
-                      const int *flag)
+// p = r + beta p (same block decomposition as the reductions)
+__global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, float *__restrict__ p)
 {
-    if (flag[BF_DONE]) return;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)N * Rp; t += gridDim.x * blockDim.x)
-        p[t] = fmaf(sc[C_BE * Rp + (int)(t % Rp)], p[t], r[t]);
+    if (S.flag[BF_DONE]) return;
+    const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
+    const int nb = S.mesh[4 * m + 1], N = S.mesh[4 * m + 2], r0 = S.mesh[4 * m + 3];
+    const int Rp = S.Rp;
+    const size_t base = (size_t)r0 * Rp, n = (size_t)N * Rp;
+    for (size_t e = (size_t)j * blockDim.x + threadIdx.x; e < n; e += (size_t)nb * blockDim.x) {
+        const int c = (int)(e % Rp);
+        p[base + e] = fmaf(scal(S, C_BE, m, c), p[base + e], r[base + e]);
+    }
 }
 
 // residual scaling between the FP64 column-major and the FP32 interleaved layouts
@@ -219,48 +246,85 @@ __global__ void k_b_resid(int N, int64_t ld, const double *__restrict__ F, const
     }
 }
 
-
 }  // namespace
 
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                     bool lowp, cudaStream_t st, const int *skip);
 
-void release_bgraph(OpData &op);
-
-// blocks of the column reductions: one per SM of the current device
-static int nb_reduce()
+// reduction blocks: per mesh a share of one block per SM proportional to its
+// rows (at least one); vectors, partials, scalars and flags for Rp columns
+static void ensure_solve(BatchData &b, int Rp)
 {
+    if (b.sR == Rp) return;
+    release_bgraph(b);   // the captured chunk refers to these buffers
     int dev = 0, nsm = 0;
     VFD_CUDA(cudaGetDevice(&dev));
     VFD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    return std::max(1, nsm);
+    const int target = std::max(1, nsm);
+    std::vector<int> items, mesh(4 * (size_t)b.nmesh);
+    int nred = 0;
+    for (int i = 0; i < b.nmesh; ++i) {
+        const int N = b.ops[i]->m->N;
+        int nb = (int)std::llround((double)target * N / (double)std::max<int64_t>(b.ntot, 1));
+        nb = std::max(1, std::min(nb, std::max(1, N)));
+        mesh[4 * i] = nred;
+        mesh[4 * i + 1] = nb;
+        mesh[4 * i + 2] = N;
+        mesh[4 * i + 3] = (int)b.xoff[i];
+        for (int j = 0; j < nb; ++j) {
+            items.push_back(i);
+            items.push_back(j);
+        }
+        nred += nb;
+    }
+    b.nred = nred;
+    b.red_items.upload(items);
+    b.red_mesh.upload(mesh);
+    const size_t nv = (size_t)b.ntot * Rp;
+    b.x.alloc(nv);
+    b.r.alloc(nv);
+    b.p.alloc(nv);
+    b.q.alloc(nv);
+    b.b.alloc(nv);
+    b.red.alloc((size_t)nred * Rp);
+    b.sc.alloc((size_t)C_N * b.nmesh * Rp);
+    b.flag.alloc(FL_CNT + 2 * (size_t)b.nmesh);
+    VFD_CUDA(cudaMemset(b.flag.p, 0, b.flag.bytes()));
+    b.sR = Rp;
 }
 
-// inner batched CG: z ~ A_low^-1 b on op.mb_b (interleaved [N][Rp]); returns iterations
-static int run_bcg(const MeshData &m, OpData &op, int Rp, float tol, int max_it, cudaStream_t st)
+static Seg make_seg(BatchData &b, int Rp)
 {
-    const int N = m.N;
-    const int VB = std::max(1, std::min(cdiv((long long)N * Rp, 256), 2048));
-    unsigned *cnt = (unsigned *)(op.mb_flag.p + BF_CNT);
-    k_b_init<<<nb_reduce(), BT, 0, st>>>(N, Rp, op.mb_b.p, op.mb_x.p, op.mb_r.p, op.mb_p.p, op.mb_part.p, cnt, op.mb_sc.p,
-                                  op.mb_flag.p, tol, max_it);
+    Seg S;
+    S.nmesh = b.nmesh;
+    S.Rp = Rp;
+    S.items = b.red_items.p;
+    S.mesh = b.red_mesh.p;
+    S.red = b.red.p;
+    S.flag = b.flag.p;
+    S.sc = b.sc.p;
+    return S;
+}
+
+// inner batched CG: z ~ A_low^-1 b on b.b (interleaved [ntot][Rp]); returns iterations
+static int run_bcg(BatchData &b, int Rp, float tol, int max_it, cudaStream_t st)
+{
+    const Seg S = make_seg(b, Rp);
+    k_b_init<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, tol, max_it);
     VFD_CUDA(cudaGetLastError());
-    // eager apply first: allocates the apply workspace outside the capture
-    mr_apply(m, op, op.mb_p.p, op.mb_q.p, Rp, st, nullptr);
-    if (!op.mb_exec || op.mb_key != (const void *)op.mb_p.p || op.mb_R != Rp) {
-        if (op.mb_exec) cudaGraphExecDestroy(op.mb_exec);
-        op.mb_exec = nullptr;
+    // eager apply first: builds the apply's descriptors and workspaces outside the capture
+    batch_apply(b, b.p.p, b.q.p, Rp, st, nullptr);
+    if (!b.exec) {
         cudaStream_t cs;
         VFD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t graph;
         VFD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         try {
             for (int it = 0; it < BCHUNK; ++it) {
-                mr_apply(m, op, op.mb_p.p, op.mb_q.p, Rp, cs, op.mb_flag.p);
-                k_b_pq<<<nb_reduce(), BT, 0, cs>>>(N, Rp, op.mb_p.p, op.mb_q.p, op.mb_part.p, cnt, op.mb_sc.p, op.mb_flag.p);
-                k_b_xr<<<nb_reduce(), BT, 0, cs>>>(N, Rp, op.mb_x.p, op.mb_r.p, op.mb_p.p, op.mb_q.p, op.mb_part.p, cnt,
-                                            op.mb_sc.p, op.mb_flag.p);
-                k_b_p<<<VB, 256, 0, cs>>>(N, Rp, op.mb_r.p, op.mb_p.p, op.mb_sc.p, op.mb_flag.p);
+                batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p);
+                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
+                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p);
+                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p);
             }
         } catch (...) {
             cudaStreamEndCapture(cs, &graph);
@@ -269,64 +333,55 @@ static int run_bcg(const MeshData &m, OpData &op, int Rp, float tol, int max_it,
         }
         VFD_CUDA(cudaStreamEndCapture(cs, &graph));
         cudaStreamDestroy(cs);
-        cudaError_t ie = cudaGraphInstantiate(&op.mb_exec, graph, 0);
+        cudaError_t ie = cudaGraphInstantiate(&b.exec, graph, 0);
         cudaGraphDestroy(graph);
         VFD_CUDA(ie);
-        op.mb_key = op.mb_p.p;
-        op.mb_R = Rp;
     }
     int hf[3] = {0, 0, 0};
     while (true) {
-        VFD_CUDA(cudaGraphLaunch(op.mb_exec, st));
-        VFD_CUDA(cudaMemcpyAsync(hf, op.mb_flag.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaGraphLaunch(b.exec, st));
+        VFD_CUDA(cudaMemcpyAsync(hf, b.flag.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
         VFD_CUDA(cudaStreamSynchronize(st));
         if (hf[BF_DONE]) break;
     }
     return hf[BF_IT];
 }
 
-// R columns of F, U (FP64, column-major, leading dimension ld, device)
-vfd_status batched_solve(const MeshData &m, OpData &op, const double *F, double *U, int R, int64_t ld, double rtol,
-                         int max_it, int *iters, double *relres, cudaStream_t st)
+// R columns per mesh of F_m, U_m (FP64, column-major, leading dimension ld_m,
+// device); relres and iters: nmesh x R, mesh-major (may be null)
+vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
+                       int max_it, int *iters, double *relres, cudaStream_t st)
 {
-    const int N = m.N, Rp = ((R + 63) / 64) * 64;
-    const size_t nv = (size_t)N * Rp;
-    if (op.mb_x.n != nv || op.mb_sc.n != (size_t)C_N * Rp) {
-        release_bgraph(op);   // the captured chunk refers to these buffers
-        op.mb_x.alloc(nv);
-        op.mb_r.alloc(nv);
-        op.mb_p.alloc(nv);
-        op.mb_q.alloc(nv);
-        op.mb_b.alloc(nv);
-        op.mb_part.alloc((size_t)nb_reduce() * Rp);
-        op.mb_sc.alloc((size_t)C_N * Rp);
+    const int Rp = ((R + 63) / 64) * 64, nm = b.nmesh;
+    ensure_solve(b, Rp);
+    std::vector<DBuf<double>> AU(nm), res(nm);
+    DBuf<double> n2, f2, scale;
+    for (int i = 0; i < nm; ++i) {
+        AU[i].alloc((size_t)ld[i] * R);
+        res[i].alloc((size_t)ld[i] * R);
     }
-    if (op.mb_flag.n < 8) {
-        op.mb_flag.alloc(8);
-        VFD_CUDA(cudaMemsetAsync(op.mb_flag.p, 0, 8 * sizeof(int), st));
-    }
-    DBuf<double> AU, res, n2, f2, scale;
-    AU.alloc((size_t)ld * R);
-    res.alloc((size_t)ld * R);
-    n2.alloc(R);
-    f2.alloc(R);
-    scale.alloc(R);
-    std::vector<double> hn(R), hf(R);
+    n2.alloc((size_t)nm * R);
+    f2.alloc((size_t)nm * R);
+    scale.alloc((size_t)nm * R);
+    std::vector<double> hn((size_t)nm * R), hf((size_t)nm * R), sc((size_t)nm * R);
     int total = 0;
     const float inner_tol = 1e-4f;
     vfd_status status = VFD_ENOCONV;   // until every column meets rtol
     for (int outer = 0; outer < 100; ++outer) {
-        // FP64 residual with the FP64 operator
-        apply_parts_ex(m, op, VFD_PART_ALL, U, AU.p, R, ld, false, st, nullptr);
-        k_b_resid<<<R, 256, 0, st>>>(N, ld, F, AU.p, res.p, n2.p, f2.p);
-        VFD_CUDA(cudaGetLastError());
-        VFD_CUDA(cudaMemcpyAsync(hn.data(), n2.p, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-        VFD_CUDA(cudaMemcpyAsync(hf.data(), f2.p, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        // FP64 residuals with the FP64 operators
+        for (int i = 0; i < nm; ++i) {
+            OpData &op = *b.ops[i];
+            apply_parts_ex(*op.m, op, VFD_PART_ALL, U[i], AU[i].p, R, ld[i], false, st, nullptr);
+            k_b_resid<<<R, 256, 0, st>>>(op.m->N, ld[i], F[i], AU[i].p, res[i].p, n2.p + (size_t)i * R,
+                                         f2.p + (size_t)i * R);
+            VFD_CUDA(cudaGetLastError());
+        }
+        VFD_CUDA(cudaMemcpyAsync(hn.data(), n2.p, sizeof(double) * nm * R, cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaMemcpyAsync(hf.data(), f2.p, sizeof(double) * nm * R, cudaMemcpyDeviceToHost, st));
         VFD_CUDA(cudaStreamSynchronize(st));
         bool all = true;
-        std::vector<double> sc(R);
-        for (int c = 0; c < R; ++c) {
-            double rel = hf[c] > 0.0 ? std::sqrt(hn[c] / hf[c]) : std::sqrt(hn[c]);
+        for (size_t c = 0; c < (size_t)nm * R; ++c) {
+            const double rel = hf[c] > 0.0 ? std::sqrt(hn[c] / hf[c]) : std::sqrt(hn[c]);
             if (relres) relres[c] = rel;
             // converged columns get scale 0: no correction, zero inner RHS
             sc[c] = (rel > rtol) ? std::sqrt(hn[c]) : 0.0;
@@ -337,24 +392,27 @@ vfd_status batched_solve(const MeshData &m, OpData &op, const double *F, double 
             break;
         }
         if (total >= max_it) break;
-        VFD_CUDA(cudaMemcpyAsync(scale.p, sc.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
-        k_b_to_inner<<<cdiv((long long)N * Rp, 256), 256, 0, st>>>(N, R, Rp, ld, res.p, scale.p, op.mb_b.p);
-        total += run_bcg(m, op, Rp, inner_tol, std::max(1, max_it - total), st);
-        k_b_from_inner<<<cdiv((long long)N * R, 256), 256, 0, st>>>(N, R, Rp, ld, op.mb_x.p, scale.p, U);
+        VFD_CUDA(cudaMemcpyAsync(scale.p, sc.data(), sizeof(double) * nm * R, cudaMemcpyHostToDevice, st));
+        for (int i = 0; i < nm; ++i) {
+            const int N = b.ops[i]->m->N;
+            k_b_to_inner<<<cdiv((long long)N * Rp, 256), 256, 0, st>>>(N, R, Rp, ld[i], res[i].p,
+                                                                       scale.p + (size_t)i * R,
+                                                                       b.b.p + (size_t)b.xoff[i] * Rp);
+        }
+        VFD_CUDA(cudaGetLastError());
+        total += run_bcg(b, Rp, inner_tol, std::max(1, max_it - total), st);
+        for (int i = 0; i < nm; ++i) {
+            const int N = b.ops[i]->m->N;
+            k_b_from_inner<<<cdiv((long long)N * R, 256), 256, 0, st>>>(N, R, Rp, ld[i],
+                                                                        b.x.p + (size_t)b.xoff[i] * Rp,
+                                                                        scale.p + (size_t)i * R, U[i]);
+        }
         VFD_CUDA(cudaGetLastError());
     }
     VFD_CUDA(cudaStreamSynchronize(st));
     if (iters)
-        for (int c = 0; c < R; ++c) iters[c] = total;
+        for (size_t c = 0; c < (size_t)nm * R; ++c) iters[c] = total;
     return status;
-}
-
-void release_bgraph(OpData &op)
-{
-    if (op.mb_exec) {
-        cudaGraphExecDestroy(op.mb_exec);
-        op.mb_exec = nullptr;
-    }
 }
 
 }  // namespace vfd

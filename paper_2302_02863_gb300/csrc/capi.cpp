@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 
 #include "vfd_internal.h"
@@ -13,6 +14,9 @@ struct vfd_mesh_s {
 };
 struct vfd_op_s {
     vfd::OpData *op;
+};
+struct vfd_batch_s {
+    vfd::BatchData *b;
 };
 
 namespace vfd {
@@ -299,7 +303,7 @@ static vfd_status apply_common(vfd_op_t h, int parts, const double *X, double *Y
         dy = op.yout.p;
     }
     if (parts == VFD_PART_ALL && op.precision != VFD_FP64 && nrhs % 64 == 0 && m.max_leaf_size <= 64)
-        mr_apply_colmajor(m, op, dx, dy, (int)nrhs, ld, st);   // batched tensor-core path
+        batch_apply_colmajor(*op_batch(op), &dx, &dy, &ld, (int)nrhs, st);   // batched tensor-core path
     else
         apply_parts(m, op, parts, dx, dy, (int)nrhs, ld, st);
     if (!ydev) {
@@ -354,7 +358,7 @@ vfd_status vfd_solve(vfd_op_t h, const double *F, double *U, int64_t nrhs, int64
         VFD_CUDA(cudaMemcpyAsync(du, U, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyHostToDevice, st));
     }
     vfd_status rs = (nrhs > 1 && op.precision != VFD_FP64)
-                        ? batched_solve(m, op, df, du, (int)nrhs, ld, rtol, max_it, iters, relres, st)
+                        ? batch_solve(*op_batch(op), &df, &du, &ld, (int)nrhs, rtol, max_it, iters, relres, st)
                         : cg_solve(m, op, df, du, (int)nrhs, ld, rtol, max_it, iters, relres, st);
     if (!udev) {
         VFD_CUDA(cudaMemcpyAsync(U, du, sizeof(double) * ((size_t)ld * (nrhs - 1) + m.N), cudaMemcpyDeviceToHost, st));
@@ -443,11 +447,79 @@ vfd_status vfd_op_timings(vfd_op_t h, double *ms, int n)
     VFD_API_END
 }
 
+vfd_status vfd_batch_create(const vfd_op_t *ops, int nops, vfd_batch_t *out)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(ops && out && nops >= 1, VFD_EINVAL, "null argument or empty batch");
+    *out = nullptr;
+    std::unique_ptr<BatchData> b(new BatchData());
+    for (int i = 0; i < nops; ++i) {
+        VFD_REQUIRE(ops[i], VFD_EINVAL, "null operator in the batch");
+        OpData *op = ops[i]->op;
+        VFD_REQUIRE(op->precision == VFD_FP32 || op->precision == VFD_BF16, VFD_EINVAL,
+                    "a batch takes VFD_FP32 or VFD_BF16 operators");
+        VFD_REQUIRE(op->precision == ops[0]->op->precision, VFD_EINVAL, "a batch takes operators of one precision");
+        VFD_REQUIRE(op->m->max_leaf_size <= 64, VFD_EUNSUPPORTED, "a batch needs leaves of at most 64 DoFs");
+        b->ops.push_back(op);
+    }
+    b->nmesh = nops;
+    b->precision = ops[0]->op->precision;
+    b->xoff.assign(1, 0);
+    for (int i = 0; i < nops; ++i) b->xoff.push_back(b->xoff.back() + b->ops[i]->m->N);
+    b->ntot = b->xoff.back();
+    *out = new vfd_batch_s{b.release()};
+    return VFD_OK;
+    VFD_API_END
+}
+
+static void batch_args(vfd::BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int64_t nrhs)
+{
+    VFD_REQUIRE(X && Y && ld, VFD_EINVAL, "null argument");
+    VFD_REQUIRE(nrhs >= 1 && nrhs <= 65535, VFD_EINVAL, "bad nrhs");
+    for (int i = 0; i < b.nmesh; ++i) {
+        VFD_REQUIRE(X[i] && Y[i] && ld[i] >= b.ops[i]->m->N, VFD_EINVAL, "bad block or leading dimension");
+        VFD_REQUIRE(is_device_ptr(X[i]) && is_device_ptr(Y[i]), VFD_EINVAL, "batch blocks must be device pointers");
+    }
+}
+
+vfd_status vfd_batch_apply(vfd_batch_t h, const double *const *X, double *const *Y, const int64_t *ld, int64_t nrhs,
+                           void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h, VFD_EINVAL, "null batch");
+    batch_args(*h->b, X, Y, ld, nrhs);
+    VFD_REQUIRE(nrhs % 64 == 0, VFD_EINVAL, "vfd_batch_apply needs a multiple of 64 columns");
+    batch_apply_colmajor(*h->b, X, Y, ld, (int)nrhs, (cudaStream_t)stream);
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_batch_solve(vfd_batch_t h, const double *const *F, double *const *U, const int64_t *ld, int64_t nrhs,
+                           double rtol, int max_it, int *iters, double *relres, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h, VFD_EINVAL, "null batch");
+    batch_args(*h->b, F, U, ld, nrhs);
+    VFD_REQUIRE(rtol > 0.0 && max_it >= 0, VFD_EINVAL, "bad solver arguments");
+    vfd_status rs = batch_solve(*h->b, F, U, ld, (int)nrhs, rtol, max_it, iters, relres, (cudaStream_t)stream);
+    if (rs != VFD_OK) vfd::set_error("batched refinement did not reach rtol within max_it");
+    return rs;
+    VFD_API_END
+}
+
+void vfd_batch_free(vfd_batch_t h)
+{
+    if (!h) return;
+    delete h->b;
+    delete h;
+}
+
 void vfd_free_op(vfd_op_t h)
 {
     if (!h) return;
     release_graphs(*h->op);
-    release_bgraph(*h->op);
+    delete h->op->self;
+    h->op->self = nullptr;
     release_streams(*h->op);
     delete h->op;
     delete h;

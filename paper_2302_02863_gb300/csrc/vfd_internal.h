@@ -206,15 +206,10 @@ struct OpData {
     DBuf<float> S32, D32, Ul32;        // FP32 copies (VFD_FP32)
     DBuf<unsigned short> S16, D16, Ul16;   // BF16 copies (VFD_BF16)
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
-    // batched (multi-RHS) low-precision apply and solve workspaces
-    DBuf<float> mr_part, mr_xh, mr_yh, mr_xi, mr_yi, mr_y2;
+    // the batch of one used by the batched (multi-RHS) low-precision apply / solve
+    struct BatchData *self = nullptr;
     // adjoint gradient workspaces
     DBuf<double> gr_uq, gr_lq, gr_hs, gr_h1, gr_pg;
-    DBuf<float> mb_x, mb_r, mb_p, mb_q, mb_b, mb_part, mb_sc;
-    DBuf<int> mb_flag;
-    cudaGraphExec_t mb_exec = nullptr;
-    const void *mb_key = nullptr;
-    int mb_R = 0;
     // apply workspace
     int ws_nrhs = 0;
     DBuf<double> xhat, yhat;           // nnode * k * ws_nrhs
@@ -234,6 +229,33 @@ struct OpData {
     bool timed = false;
     cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};   // captured CG chunks (FP64 K, FP32 K)
     const void *cg_key[2] = {nullptr, nullptr};
+};
+
+// ---------------------------------------------------------------------------
+// batch of low-precision operators (one mesh each) for the batched apply and
+// the batched refinement solve: the kernels walk global work-item queues
+// over all meshes (batched.cu, bsolve.cu)
+// ---------------------------------------------------------------------------
+struct BatchData {
+    std::vector<OpData *> ops;          // not owned
+    int nmesh = 0, precision = VFD_FP32;
+    int64_t ntot = 0;                   // sum of the meshes' DoFs
+    std::vector<int64_t> xoff;          // first row of each mesh (nmesh + 1)
+    int R = 0;                          // columns the workspaces below are built for (0: not built)
+    DBuf<unsigned char> desc;           // nmesh descriptors (MrMesh)
+    DBuf<int> leaf_items, sum_items, node_items, near_items;   // (mesh, index) pairs
+    int n_leaf_items = 0, n_sum_items = 0, n_node_items = 0, n_near_items = 0;
+    DBuf<long long> row_off;            // xoff on the device
+    int max_panel_w = 0, max_k = 0, max_nlev = 0, max_leaf = 0;
+    bool any_far = false;
+    DBuf<float> part, xhat, yhat, y2;   // far-field workspaces (all meshes), second near partial
+    DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
+    // batched refinement solve
+    DBuf<float> x, r, p, q, b, red, sc;
+    DBuf<int> flag, red_items, red_mesh;
+    int nred = 0, sR = 0;
+    cudaGraphExec_t exec = nullptr;
+    ~BatchData();
 };
 
 // ---------------------------------------------------------------------------
@@ -271,14 +293,15 @@ void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double 
 // solve.cu
 void release_graphs(OpData &op);
 void release_streams(OpData &op);
-void release_bgraph(OpData &op);
+void release_bgraph(BatchData &b);
+BatchData *op_batch(OpData &op);   // the op's batch of one (created on first use)
+void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip);
+void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,
+                          cudaStream_t st);
+vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
+                       int max_it, int *iters, double *relres, cudaStream_t st);
 void launch_convert_bf16(const MeshData &m, OpData &op, cudaStream_t st);
 void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st);
-void mr_apply(const MeshData &m, OpData &op, const float *X, float *Y, int R, cudaStream_t st, const int *skip);
-void mr_apply_colmajor(const MeshData &m, OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
-                       cudaStream_t st);
-vfd_status batched_solve(const MeshData &m, OpData &op, const double *F, double *U, int R, int64_t ld, double rtol,
-                         int max_it, int *iters, double *relres, cudaStream_t st);
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st);
 

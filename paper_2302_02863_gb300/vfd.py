@@ -33,7 +33,8 @@ INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "no
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
            "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_grad", "vfd_load", "vfd_op_rho", "vfd_op_timings",
-           "vfd_selftest_math", "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
+           "vfd_selftest_math", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve", "vfd_batch_free",
+           "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
 
 
 class VfdError(RuntimeError):
@@ -87,13 +88,19 @@ def load():
     L.vfd_op_rho.argtypes = [vp, vp, vp]
     L.vfd_op_timings.argtypes = [vp, dp, C.c_int]
     L.vfd_selftest_math.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp]
+    L.vfd_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
+    L.vfd_batch_apply.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int64), C.c_int64, vp]
+    L.vfd_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int64), C.c_int64, C.c_double,
+                                  C.c_int, C.POINTER(C.c_int), dp, vp]
+    L.vfd_batch_free.argtypes = [vp]
+    L.vfd_batch_free.restype = None
     L.vfd_free_op.argtypes = [vp]
     L.vfd_free_op.restype = None
     L.vfd_free_mesh.argtypes = [vp]
     L.vfd_free_mesh.restype = None
     L.vfd_last_error.restype = C.c_char_p
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
-              "vfd_apply_noalloc", "vfd_grad",
+              "vfd_apply_noalloc", "vfd_grad", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve",
               "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -272,6 +279,61 @@ def vfd_solve(op, F, U, rtol=1e-10, max_it=10000, stream=None, raise_on_noconv=F
     if st not in (VFD_OK, VFD_ENOCONV) or (raise_on_noconv and st != VFD_OK):
         _check(st)
     return st, np.array(list(it)), rr
+
+
+class Batch:
+    """A batch of VFD_FP32 / VFD_BF16 operators (keeps them alive)."""
+
+    def __init__(self, handle, ops):
+        self.handle = handle
+        self.ops = list(ops)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                load().vfd_batch_free(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def vfd_batch_create(ops):
+    arr = (C.c_void_p * len(ops))(*[op.handle for op in ops])
+    h = C.c_void_p()
+    _check(load().vfd_batch_create(arr, len(ops), C.byref(h)))
+    return Batch(h, ops)
+
+
+def _blocks(batch, Xs):
+    ptrs = (C.c_void_p * len(Xs))(*[a.data_ptr() for a in Xs])
+    lds = (C.c_int64 * len(Xs))(*[int(a.shape[1]) for a in Xs])
+    nrhs = int(Xs[0].shape[0])
+    for a, op in zip(Xs, batch.ops):
+        if a.ndim != 2 or a.shape[0] != nrhs or a.shape[1] != op.mesh.n_dof:
+            raise ValueError("batch blocks must be (nrhs, n_dof) tensors, one per operator")
+    return ptrs, lds, nrhs
+
+
+def vfd_batch_apply(batch, Xs, Ys, stream=None):
+    """Ys[m] = A_low,m Xs[m]; Xs, Ys: lists of (nrhs, n_dof(m)) float64 CUDA tensors, nrhs % 64 == 0."""
+    xp, lds, nrhs = _blocks(batch, Xs)
+    yp, _, _ = _blocks(batch, Ys)
+    _check(load().vfd_batch_apply(batch.handle, xp, yp, lds, nrhs, _stream(stream)))
+    return Ys
+
+
+def vfd_batch_solve(batch, Fs, Us, rtol=1e-8, max_it=100000, stream=None, raise_on_noconv=False):
+    """Batched refinement solve; returns (status, iters (nmesh, nrhs), relres (nmesh, nrhs))."""
+    fp, lds, nrhs = _blocks(batch, Fs)
+    up, _, _ = _blocks(batch, Us)
+    n = len(Fs) * nrhs
+    it = (C.c_int * n)()
+    rr = np.zeros(n)
+    st = load().vfd_batch_solve(batch.handle, fp, up, lds, nrhs, float(rtol), int(max_it), it,
+                                rr.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream))
+    if st not in (VFD_OK, VFD_ENOCONV) or (raise_on_noconv and st != VFD_OK):
+        _check(st)
+    return st, np.array(list(it)).reshape(len(Fs), nrhs), rr.reshape(len(Fs), nrhs)
 
 
 def vfd_load(mesh, f_nodal, F, stream=None):
