@@ -154,12 +154,13 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 template <class T>
 __global__ void __launch_bounds__(NEAR_THREADS)
 k_mr_near(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
-          float *__restrict__ Yall, float *__restrict__ Y2all, const int *skip)
+          float *__restrict__ Yall, float *__restrict__ Y2all, const int *skip, const int *mdone)
 {
     using TT = NearTile<T>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
+    if (mdone && mdone[item.x]) return;
     const MrMesh &Ms = ms[item.x];
     const int lf = item.y, rt = blockIdx.y * RT, fl = Ms.fl;
     const size_t xo = (size_t)Ms.xoff * R;
@@ -264,7 +265,7 @@ static size_t near_smem_bytes(int max_panel_w)
 // accumulate = 0: no near products)
 __global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restrict__ row_off, int nmesh,
                          long long ntot, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
-                         const float *__restrict__ Y2all, const int *skip)
+                         const float *__restrict__ Y2all, const int *skip, const int *mdone)
 {
     if (skip && *skip) return;
     const int R4 = R >> 2;
@@ -277,6 +278,7 @@ __global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restr
         if (row_off[mid] <= ig) lo = mid;
         else hi = mid - 1;
     }
+    if (mdone && mdone[lo]) return;
     const MrMesh &Ms = ms[lo];
     const size_t xo = (size_t)Ms.xoff * R;
     const float *__restrict__ X = Xall + xo;
@@ -322,12 +324,13 @@ __device__ __forceinline__ void fma4(float4 &acc, float u, const float4 x)
 template <class T>
 __global__ void __launch_bounds__(256)
 k_mr_far_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
-              const int *skip)
+              const int *skip, const int *mdone)
 {
     __shared__ float4 Xs[64][RT / 4];
     extern __shared__ float Us[];   // [n][nlev * k]
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
+    if (mdone && mdone[item.x]) return;
     const MrMesh &Ms = ms[item.x];
     const int leaf = item.y, rt = blockIdx.y * RT;
     const int fl = Ms.fl, k = Ms.k, nlev = Ms.nlev, N = Ms.N, nleaf = Ms.nleaf;
@@ -370,10 +373,12 @@ k_mr_far_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int
 }
 
 // xhat[node][a][r] = sum over the node's leaves of part (levels lmin..L)
-__global__ void k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip)
+__global__ void k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip,
+                             const int *mdone)
 {
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
+    if (mdone && mdone[item.x]) return;
     const MrMesh &Ms = ms[item.x];
     const int node = item.y, lmin = Ms.lmin, L = Ms.L, k = Ms.k, nleaf = Ms.nleaf;
     const float *__restrict__ part = Ms.part;
@@ -423,11 +428,13 @@ __host__ __device__ constexpr int couple_sbytes(int k)
 
 template <class T>
 __global__ void __launch_bounds__(64)
-k_mr_far_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip)
+k_mr_far_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip,
+                const int *mdone)
 {
     extern __shared__ __align__(16) unsigned char csm[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
+    if (mdone && mdone[item.x]) return;
     const MrMesh &Ms = ms[item.x];
     const int node = item.y, rt = blockIdx.y * RT, k = Ms.k;
     const int *__restrict__ fptr = Ms.fptr, *__restrict__ fcol = Ms.fcol;
@@ -497,11 +504,12 @@ k_mr_far_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, i
 template <class T>
 __global__ void __launch_bounds__(256)
 k_mr_far_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
-                const int *skip)
+                const int *skip, const int *mdone)
 {
     extern __shared__ float4 Ys[];   // [nlev * k][16], then Us[nlev * k][64] (floats)
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
+    if (mdone && mdone[item.x]) return;
     const MrMesh &Ms = ms[item.x];
     const int leaf = item.y, rt = blockIdx.y * RT;
     const int fl = Ms.fl, lmin = Ms.lmin, L = Ms.L, k = Ms.k, N = Ms.N;
@@ -693,44 +701,47 @@ static void ensure_batch(BatchData &b, int R)
 }
 
 template <class T>
-static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip)
+static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
+                             const int *mdone)
 {
     const MrMesh *ms = (const MrMesh *)b.desc.p;
     if (b.n_near_items > 0) {
         const size_t shm = near_smem_bytes<T>(b.max_panel_w);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         dim3 g(b.n_near_items, R / RT, KSPLIT);
-        k_mr_near<T><<<g, NEAR_THREADS, shm, st>>>(ms, (const int2 *)b.near_items.p, R, X, Y, b.y2.p, skip);
+        k_mr_near<T><<<g, NEAR_THREADS, shm, st>>>(ms, (const int2 *)b.near_items.p, R, X, Y, b.y2.p, skip, mdone);
     }
     k_mr_csr<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R, X,
-                                                                      Y, b.y2.p, skip);
+                                                                      Y, b.y2.p, skip, mdone);
     if (b.any_far) {
         const int k = b.max_k, nlev = b.max_nlev;
         dim3 gp(b.n_leaf_items, R / RT);
         const size_t pshm = (size_t)b.max_leaf * nlev * k * sizeof(float);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-        k_mr_far_proj<T><<<gp, 256, pshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip);
+        k_mr_far_proj<T><<<gp, 256, pshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
         dim3 gs(b.n_sum_items, cdiv(k * R / 4, 128));
-        k_mr_far_sum<<<gs, 128, 0, st>>>(ms, (const int2 *)b.sum_items.p, R, skip);
+        k_mr_far_sum<<<gs, 128, 0, st>>>(ms, (const int2 *)b.sum_items.p, R, skip, mdone);
         dim3 gc(b.n_node_items, R / RT);
         const size_t cshm = 2 * EPS * ((size_t)couple_sbytes<T>(k) + (size_t)k * RT * sizeof(float));
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
-        k_mr_far_couple<T><<<gc, 64, cshm, st>>>(ms, (const int2 *)b.node_items.p, R, skip);
+        k_mr_far_couple<T><<<gc, 64, cshm, st>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
         const size_t eshm = (size_t)nlev * k * (RT + 64) * sizeof(float);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eshm));
         dim3 ge(b.n_leaf_items, R / RT);
-        k_mr_far_expand<T><<<ge, 256, eshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip);
+        k_mr_far_expand<T><<<ge, 256, eshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
     }
     VFD_CUDA(cudaGetLastError());
 }
 
-// Y = A_low X for R (multiple of 64) interleaved FP32 columns over all meshes
-void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip)
+// Y = A_low X for R (multiple of 64) interleaved FP32 columns over all meshes;
+// skip: device flag, nonzero = launch nothing; mdone: per-mesh device flags,
+// nonzero = leave that mesh's rows of Y alone (both may be null)
+void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip, const int *mdone)
 {
     VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
     ensure_batch(b, R);
-    if (b.precision == VFD_BF16) batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip);
-    else batch_apply_impl<float>(b, X, Y, R, st, skip);
+    if (b.precision == VFD_BF16) batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
+    else batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
 }
 
 // column-major FP64 <-> interleaved FP32
@@ -764,7 +775,7 @@ void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y
         k_cm_to_il<<<cdiv((long long)N * nrhs, 256), 256, 0, st>>>(N, nrhs, ld[i], X[i],
                                                                    b.xi.p + (size_t)b.xoff[i] * nrhs);
     }
-    batch_apply(b, b.xi.p, b.yi.p, nrhs, st, nullptr);
+    batch_apply(b, b.xi.p, b.yi.p, nrhs, st, nullptr, nullptr);
     for (int i = 0; i < b.nmesh; ++i) {
         const int N = b.ops[i]->m->N;
         k_il_to_cm<<<cdiv((long long)N * nrhs, 256), 256, 0, st>>>(N, nrhs, ld[i], b.yi.p + (size_t)b.xoff[i] * nrhs,

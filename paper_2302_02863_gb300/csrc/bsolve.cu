@@ -22,7 +22,9 @@ constexpr int BT = 1024;   // threads of the reduction kernels
 // per (mesh, column) scalars, arrays of nmesh * Rp floats: rr, pq, alpha, beta, tol2
 enum { C_RR = 0, C_PQ = 1, C_AL = 2, C_BE = 3, C_TOL = 4, C_N = 5 };
 // flags (int): [0] all done, [1] iterations, [2] max_it, [3] mesh-finish counter,
-// then per mesh: a block counter (FL_CNT + m) and its live-column count (FL_CNT + nmesh + m)
+// then per mesh: a block counter (FL_CNT + m), its live-column count
+// (FL_CNT + nmesh + m) and its done flag (FL_CNT + 2 nmesh + m: every column
+// converged; its blocks then skip all element work and the apply skips it)
 enum { BF_DONE = 0, BF_IT = 1, BF_MAX = 2, BF_GCNT = 3, FL_CNT = 4 };
 
 struct Seg {
@@ -32,6 +34,7 @@ struct Seg {
     float *red;              // block partials, nred x Rp
     int *flag;
     float *sc;               // C_N x (nmesh * Rp)
+    __device__ int *mdone() const { return flag + FL_CNT + 2 * nmesh; }
 };
 
 __device__ __forceinline__ float &scal(const Seg &S, int kind, int m, int c)
@@ -45,19 +48,22 @@ __device__ __forceinline__ float &scal(const Seg &S, int kind, int m, int c)
 // its element: every kernel using this helper visits the same elements in
 // the same block, and a block reads only what it wrote itself.  The last
 // block of the mesh reduces the mesh's partials in a fixed order and calls
-// fin(mesh, c, total); returns the mesh in that block, else -1.
-template <class Elem, class Fin>
+// fin(mesh, c, total); returns the mesh in that block, else -1.  With
+// check_done, a mesh whose done flag is set does no element work and no fin
+// (its blocks still take part in the counting).
+template <bool check_done, class Elem, class Fin>
 __device__ int seg_reduce(const Seg &S, Elem f, Fin fin)
 {
     __shared__ bool am_last;
     __shared__ float sh[BT];
     const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
+    const bool work = !check_done || !S.mdone()[m];
     const int b0 = S.mesh[4 * m], nb = S.mesh[4 * m + 1], N = S.mesh[4 * m + 2], r0 = S.mesh[4 * m + 3];
     const int Rp = S.Rp, Rc = min(Rp, (int)blockDim.x), lanes = blockDim.x / Rc;
     for (int c0 = 0; c0 < Rp; c0 += Rc) {
         const int cl = threadIdx.x % Rc, c = c0 + cl, rl = threadIdx.x / Rc;
         float v = 0.f;
-        if (rl < lanes && c < Rp)
+        if (work && rl < lanes && c < Rp)
 #pragma unroll 4
             for (int i = j * lanes + rl; i < N; i += nb * lanes) v += f((size_t)(r0 + i) * Rp + c, m, c);
         sh[threadIdx.x] = v;
@@ -84,7 +90,7 @@ __device__ int seg_reduce(const Seg &S, Elem f, Fin fin)
             for (int bI = rl; bI < nb; bI += lanes) s += __ldcg(S.red + (size_t)(b0 + bI) * Rp + c);
         sh[threadIdx.x] = s;
         __syncthreads();
-        if (rl == 0 && c < Rp) {
+        if (work && rl == 0 && c < Rp) {
             float tot = 0.f;
             for (int q = 0; q < lanes; ++q) tot += sh[q * Rc + cl];
             fin(m, c, tot);
@@ -97,7 +103,10 @@ __device__ int seg_reduce(const Seg &S, Elem f, Fin fin)
 __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ b, float *__restrict__ x,
                                                float *__restrict__ r, float *__restrict__ p, float tol, int max_it)
 {
-    seg_reduce(
+    __shared__ int live;
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    const int m = seg_reduce<false>(
         S,
         [&](size_t t, int, int) {
             const float v = b[t];
@@ -111,7 +120,12 @@ __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ 
             scal(S, C_TOL, m, c) = tol * tol * s;
             scal(S, C_AL, m, c) = 0.f;
             scal(S, C_BE, m, c) = 0.f;
+            if (s > 0.f) atomicAdd(&live, 1);
         });
+    if (m >= 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) S.mdone()[m] = live == 0 ? 1 : 0;   // a mesh with zero right-hand sides is done
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         S.flag[BF_IT] = 0;
         S.flag[BF_MAX] = max_it;
@@ -123,7 +137,7 @@ __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ 
 __global__ void __launch_bounds__(BT) k_b_pq(Seg S, const float *__restrict__ p, const float *__restrict__ q)
 {
     if (S.flag[BF_DONE]) return;
-    seg_reduce(
+    seg_reduce<true>(
         S, [&](size_t t, int, int) { return p[t] * q[t]; },
         [&](int m, int c, float s) {
             const float rr = scal(S, C_RR, m, c);
@@ -142,7 +156,8 @@ __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float
     __shared__ bool all_last;
     if (threadIdx.x == 0) live = 0;
     __syncthreads();
-    const int m = seg_reduce(
+    const bool was_done = S.mdone()[S.items[2 * blockIdx.x]];
+    const int m = seg_reduce<true>(
         S,
         [&](size_t t, int mm, int c) {
             const float al = scal(S, C_AL, mm, c);
@@ -166,6 +181,7 @@ __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float
     // the last mesh to finish decides for the whole batch
     if (threadIdx.x == 0) {
         S.flag[FL_CNT + S.nmesh + m] = live;
+        if (!was_done && live == 0) S.mdone()[m] = 1;
         __threadfence();
         unsigned v = atomicInc((unsigned *)&S.flag[BF_GCNT], S.nmesh - 1);
         all_last = (v == (unsigned)(S.nmesh - 1));
@@ -185,6 +201,7 @@ __global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, 
 {
     if (S.flag[BF_DONE]) return;
     const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
+    if (S.mdone()[m]) return;
     const int nb = S.mesh[4 * m + 1], N = S.mesh[4 * m + 2], r0 = S.mesh[4 * m + 3];
     const int Rp = S.Rp;
     const size_t base = (size_t)r0 * Rp, n = (size_t)N * Rp;
@@ -288,7 +305,7 @@ static void ensure_solve(BatchData &b, int Rp)
     b.b.alloc(nv);
     b.red.alloc((size_t)nred * Rp);
     b.sc.alloc((size_t)C_N * b.nmesh * Rp);
-    b.flag.alloc(FL_CNT + 2 * (size_t)b.nmesh);
+    b.flag.alloc(FL_CNT + 3 * (size_t)b.nmesh);
     VFD_CUDA(cudaMemset(b.flag.p, 0, b.flag.bytes()));
     b.sR = Rp;
 }
@@ -313,7 +330,7 @@ static int run_bcg(BatchData &b, int Rp, float tol, int max_it, cudaStream_t st)
     k_b_init<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, tol, max_it);
     VFD_CUDA(cudaGetLastError());
     // eager apply first: builds the apply's descriptors and workspaces outside the capture
-    batch_apply(b, b.p.p, b.q.p, Rp, st, nullptr);
+    batch_apply(b, b.p.p, b.q.p, Rp, st, nullptr, nullptr);
     if (!b.exec) {
         cudaStream_t cs;
         VFD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -321,7 +338,7 @@ static int run_bcg(BatchData &b, int Rp, float tol, int max_it, cudaStream_t st)
         VFD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         try {
             for (int it = 0; it < BCHUNK; ++it) {
-                batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p);
+                batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh);
                 k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
                 k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p);
                 k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p);

@@ -295,7 +295,8 @@ void release_graphs(OpData &op);
 void release_streams(OpData &op);
 void release_bgraph(BatchData &b);
 BatchData *op_batch(OpData &op);   // the op's batch of one (created on first use)
-void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip);
+void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
+                 const int *mdone);
 void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,
                           cudaStream_t st);
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,

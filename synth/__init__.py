@@ -329,6 +329,26 @@ def rhs_vectors(n: int, nrhs: int, seed: int) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------
+def batch_workload(n_mesh: int = 24, n_min: int = 2000, ratio: float = 65.0, seed0: int = 3000):
+    """Many meshes of uneven size: mesh i (i = 0..n_mesh-1) targets
+    round(n_min * ratio^(i/(n_mesh-1))) interior DoFs (log-uniform sizes, 2k to
+    130k for the defaults); even i: the square (-1,1)^2 inside (-2,2)^2, odd i:
+    the unit disk with an annulus to R = 1.1; jitter 0.2 of the local spacing.
+    Fields per mesh: s = 0.1 + 0.8 sigmoid(F_a) with F_a a seeded 16-mode
+    Fourier field (sigma 1), log kappa a seeded Fourier field (sigma 0.5).
+    Returns a list of (mesh, s_field, logkappa_field, target_dofs)."""
+    out = []
+    for i in range(n_mesh):
+        n = int(round(n_min * ratio ** (i / max(n_mesh - 1, 1))))
+        seed = seed0 + i
+        m = square_mesh_for_dofs(n, jitter=0.2, seed=seed) if i % 2 == 0 else \
+            disk_mesh_for_dofs(n, R=1.1, jitter=0.2, seed=seed)
+        s = sigmoid_field(random_fourier_field(seed + 100, 1.0), 0.1, 0.9)
+        k = random_fourier_field(seed + 200, 0.5)
+        out.append((m, s, k, n))
+    return out
+
+
 def workload(name: str):
     """Named synthetic workloads: returns (mesh, s_field, logkappa_field, params).
 
