@@ -18,7 +18,11 @@ ms_per_step is the time to a 1e-10 solution from the fields.
 After the timed steps (outside the timed region) the line also carries
 "batched_mixed_precision": 64 seeded load vectors on the same fields, the
 batched apply and the iterative-refinement solve to 1e-8 with TF32 and with
-BF16 near panels, against FP64 column-by-column CG on the same GPU.
+BF16 near panels, against FP64 column-by-column CG on the same GPU; and
+"batch_24_meshes": 24 squares and disks of 2k to 130k DoFs (773,540 DoFs in
+all, each mesh its own fields), 64 load vectors per mesh, one batched
+refinement solve to 1e-8 over all meshes, against the per-mesh batched solves
+one after another.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
   python bench.py --impl reference ...     (the CPU oracle on a bounded sample)
@@ -56,6 +60,7 @@ def _args():
     p.add_argument("--rtol", type=float, default=1e-10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-RHS mixed-precision leg")
+    p.add_argument("--no-batch24", action="store_true", help="skip the 24-mesh batched leg")
     p.add_argument("--mode", default="step", choices=["step", "apply"],
                    help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
     p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
@@ -320,6 +325,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_leg(mesh, s, k, prm, torch, vfd, hbm=hbm)
+    batch24 = None
+    if not args.no_batch24:
+        batch24 = batch24_leg(torch, vfd, hbm=hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -345,6 +353,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "batched_mixed_precision": batched,
+            "batch_24_meshes": batch24,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -414,6 +423,72 @@ def batched_leg(mesh, s, k, prm, torch, vfd, nrhs=64, rtol=1e-8, fp64_cols=8, hb
                      "apply_near_bytes_frac_of_hbm": near_bytes / ta / 1e9 / hbm}
         del op
     del op64
+    return out
+
+
+def batch24_leg(torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
+    """Many meshes at once: the 24 squares and disks of synth.batch_workload
+    (2k to 130k DoFs, 773,540 in all, each with its own fields), 64 seeded
+    N(0,1) load vectors per mesh, one batched refinement solve to rtol over
+    all meshes (TF32 and BF16 near panels), and the batch apply throughput;
+    against the same per-mesh batched solves run one mesh after another."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import synth
+    W = synth.batch_workload()
+    t0 = time.perf_counter()
+
+    def mk(w):
+        m = w[0]
+        return vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=64, cheb_p=4, lam=0.75,
+                            rho_lambda=0.75)
+
+    with ThreadPoolExecutor(16) as ex:
+        meshes = list(ex.map(mk, W))
+    t_setup = time.perf_counter() - t0
+    ntot = sum(mm.n_dof for mm in meshes)
+    out = {"meshes": len(meshes), "n_dof_total": ntot, "n_dof_min": min(mm.n_dof for mm in meshes),
+           "n_dof_max": max(mm.n_dof for mm in meshes), "nrhs": nrhs, "rtol": rtol,
+           "mesh_setup_s_host": t_setup, "rhs": "seeded N(0,1)"}
+    g = torch.Generator(device="cuda").manual_seed(4000)
+    Fs = [torch.randn(nrhs, mm.n_dof, dtype=torch.float64, device="cuda", generator=g) for mm in meshes]
+    for name, prec in (("tf32", vfd.VFD_FP32), ("bf16", vfd.VFD_BF16)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ops = [vfd.vfd_assemble(mesh, w[1], w[2], 0.9, precision=prec) for mesh, w in zip(meshes, W)]
+        e1.record()
+        torch.cuda.synchronize()
+        t_asm = e0.elapsed_time(e1) / 1000.0
+        batch = vfd.vfd_batch_create(ops)
+        Ys = [torch.empty_like(f) for f in Fs]
+        for _ in range(2):
+            vfd.vfd_batch_apply(batch, Fs, Ys)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            vfd.vfd_batch_apply(batch, Fs, Ys)
+        e1.record()
+        torch.cuda.synchronize()
+        ta = e0.elapsed_time(e1) / 5 / 1000.0
+        Us = [torch.zeros_like(f) for f in Fs]
+        e0.record()
+        st, it, rel = vfd.vfd_batch_solve(batch, Fs, Us, rtol=rtol, max_it=200000)
+        e1.record()
+        torch.cuda.synchronize()
+        ts = e0.elapsed_time(e1) / 1000.0
+        Us2 = [torch.zeros_like(f) for f in Fs]
+        e0.record()
+        for op, F, U in zip(ops, Fs, Us2):
+            vfd.vfd_solve(op, F, U, rtol=rtol, max_it=200000)
+        e1.record()
+        torch.cuda.synchronize()
+        tseq = e0.elapsed_time(e1) / 1000.0
+        out[name] = {"assemble_s": t_asm, "apply_ms": ta * 1000, "apply_dof_rhs_per_s": ntot * nrhs / ta,
+                     "solve_s": ts, "status": int(st), "inner_iters_max": int(it.max()),
+                     "relres_max": float(rel.max()), "solved_dof_rhs_per_s": ntot * nrhs / ts,
+                     "sequential_per_mesh_solves_s": tseq}
+        del batch, ops
     return out
 
 
