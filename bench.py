@@ -56,12 +56,13 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--workload", default="disk33k")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
+    p.add_argument("--nrhs", type=int, default=1, help="columns for --mode apply / solve")
     p.add_argument("--rtol", type=float, default=1e-10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-RHS mixed-precision leg")
     p.add_argument("--no-batch24", action="store_true", help="skip the 24-mesh batched leg")
-    p.add_argument("--mode", default="step", choices=["step", "apply"],
+    p.add_argument("--mode", default="step", choices=["step", "apply", "solve"],
                    help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
     p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
     return p.parse_args()
@@ -195,12 +196,12 @@ def main():
         dist.init_process_group("nccl")
     vfd.load()
     m, s, k, prm = synth.workload(args.workload)
-    prec = vfd.VFD_FP64 if args.precision == "fp64" else vfd.VFD_FP32
+    prec = {"fp64": vfd.VFD_FP64, "fp32": vfd.VFD_FP32, "bf16": vfd.VFD_BF16}[args.precision]
     mesh = vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"],
                         lam=0.75, rho_lambda=0.75, tail_mode=prm["tail"], tail_R=prm["R"])
     info = mesh.info
     n = mesh.n_dof
-    if args.mode == "apply":
+    if args.mode in ("apply", "solve"):
         return apply_mode(args, mesh, s, k, prm, prec, torch, vfd)
     stream = torch.cuda.current_stream()
     F = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -493,10 +494,25 @@ def batch24_leg(torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
 
 
 def apply_mode(args, mesh, s, k, prm, prec, torch, vfd):
-    """Bounded run for profilers: one assembly, then --warmup + --steps applies."""
+    """Bounded runs for profilers: one assembly, then --warmup + --steps applies
+    (--parts, --nrhs columns; low precision with nrhs % 64 == 0 takes the
+    batched tensor-core path), or with --mode solve one solve of --nrhs seeded
+    N(0,1) columns to --rtol."""
     op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec)
-    X = torch.randn(mesh.n_dof, dtype=torch.float64, device="cuda")
-    Y = torch.empty_like(X)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    shape = (mesh.n_dof,) if args.nrhs == 1 else (args.nrhs, mesh.n_dof)
+    X = torch.randn(*shape, dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.zeros_like(X)
+    if args.mode == "solve":
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, it, rel = vfd.vfd_solve(op, X, Y, rtol=args.rtol, max_it=200000)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "solve", "precision": args.precision, "nrhs": args.nrhs, "status": int(st),
+                          "iters": int(it[0]), "relres_max": float(rel.max()),
+                          "ms": e0.elapsed_time(e1)}), flush=True)
+        return
     for _ in range(args.warmup):
         vfd.vfd_apply_parts(op, args.parts, X, Y)
     torch.cuda.synchronize()
@@ -506,7 +522,7 @@ def apply_mode(args, mesh, s, k, prm, prec, torch, vfd):
         vfd.vfd_apply_parts(op, args.parts, X, Y)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "apply", "parts": args.parts, "precision": args.precision,
+    print(json.dumps({"mode": "apply", "parts": args.parts, "precision": args.precision, "nrhs": args.nrhs,
                       "us_per_apply": 1000 * e0.elapsed_time(e1) / args.steps}), flush=True)
 
 

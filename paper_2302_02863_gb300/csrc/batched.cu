@@ -316,18 +316,69 @@ __device__ __forceinline__ void fma4(float4 &acc, float u, const float4 x)
 // far field, R RHS in tiles of 64 (FP32 accumulation; T the stored basis /
 // coupling type).  Thread micro-tiles of 4 outputs x 4 RHS (float4 over RHS).
 //
-// projections: part[lv][leaf][a][r] = sum_{i in leaf} Ul[lv][i][a] X[i][r].
-// CTA (256 threads) per (leaf, RHS tile): the leaf's x rows and its basis rows
-// of every level (Us[i][lva], lva = lv*k + a) staged in shared memory; thread
-// (r-quad = t % 16, g = t / 16) computes lva = c*64 + g + 16 q (q < 4), chunk
-// by chunk.
+// Far-field products on the tensor cores (mma.sync m16n8k8 TF32, FP32
+// accumulate; BF16-stored bases and blocks are widened when the fragments
+// are loaded).  Every tile is staged by cp.async (16-byte copies, all in
+// flight at once, zero-filled padding rows) in the stored type; rows are
+// padded so the fragment loads are conflict-free: [k][64 RHS] tiles with row
+// stride RT + 8, basis / block rows with k + 8 (read by columns) or k + 4
+// (read by rows, FP32) elements.  When a row of k elements is not a whole
+// number of 16-byte pieces the tiles are staged by plain loads instead.
+constexpr int FLDX = RT + 8;   // row stride of [k][RHS] tiles
+
+__host__ __device__ constexpr int far_round16(int v) { return (v + 15) & ~15; }
+template <class T>
+__host__ __device__ constexpr int far_lcol(int k) { return k + 8; }   // rows read by columns
+template <class T>
+__host__ __device__ constexpr int far_lrow(int k) { return sizeof(T) == 4 ? k + 4 : k + 8; }   // rows read by rows
+
+template <class T>
+__device__ __forceinline__ float ldf(const T *p) { return (float)*p; }
+
+// rows [0, nvalid) of kcols elements from src (row stride src_ld) to dst (row
+// stride dst_ld); rows [nvalid, npad) zero
+template <class T>
+__device__ __forceinline__ void stage_rows(T *dst, int dst_ld, const T *src, size_t src_ld, int kcols, int nvalid,
+                                           int npad, bool async)
+{
+    if (async) {
+        constexpr int E = 16 / (int)sizeof(T);
+        const int cpr = kcols / E;
+        for (int c = threadIdx.x; c < npad * cpr; c += blockDim.x) {
+            const int r = c / cpr, q = c - r * cpr;
+            const bool ok = r < nvalid;
+            cp_async16(dst + (size_t)r * dst_ld + q * E, ok ? (const void *)(src + (size_t)r * src_ld + q * E)
+                                                            : (const void *)src, ok);
+        }
+    } else {
+        for (int c = threadIdx.x; c < npad * kcols; c += blockDim.x) {
+            const int r = c / kcols, q = c - r * kcols;
+            dst[(size_t)r * dst_ld + q] = r < nvalid ? src[(size_t)r * src_ld + q] : (T)0.f;
+        }
+    }
+}
+
+template <class T>
+static size_t far_smem_proj(int nlev, int k)
+{
+    return (size_t)64 * FLDX * sizeof(float) + (size_t)nlev * 64 * far_lcol<T>(k) * sizeof(T);
+}
+template <class T>
+static size_t far_smem_expand(int nlev, int k)
+{
+    return (size_t)far_round16(nlev * k) * FLDX * sizeof(float) + (size_t)nlev * 64 * far_lrow<T>(k) * sizeof(T);
+}
+
+// projections: part[lv][leaf][a][r] = sum_{i in leaf} Ul[lv][i][a] X[i][r], i.e.
+// C[lva][r] = sum_i A[lva][i] Xs[i][r] with A[lva][i] = Ur[l][i][a] (M = nlev*k,
+// N = 64, K = leaf size).  CTA (256 threads, 8 warps) per (leaf, RHS tile);
+// warp w owns the m16 tiles w, w+8, ... of lva and all eight n8 tiles.
 template <class T>
 __global__ void __launch_bounds__(256)
 k_mr_far_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
               const int *skip, const int *mdone)
 {
-    __shared__ float4 Xs[64][RT / 4];
-    extern __shared__ float Us[];   // [n][nlev * k]
+    extern __shared__ __align__(16) unsigned char fsm[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
@@ -338,36 +389,45 @@ k_mr_far_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int
     const T *__restrict__ Ul = (const T *)Ms.Ul;
     float *__restrict__ part = Ms.part;
     const int b = Ms.kb[fl + leaf], n = Ms.ke[fl + leaf] - b;
-    const int R4 = R >> 2, NL = nlev * k;
-    for (int e = threadIdx.x; e < n * (RT / 4); e += blockDim.x) {
-        const int i = e / (RT / 4), q = e % (RT / 4);
-        Xs[i][q] = ((const float4 *)X)[(size_t)(b + i) * R4 + (rt >> 2) + q];
-    }
-    for (int e = threadIdx.x; e < nlev * n * k; e += blockDim.x) {
-        const int l = e / (n * k), r = e - l * n * k, i = r / k, al = r - i * k;
-        Us[i * NL + l * k + al] = (float)Ul[((size_t)l * N + b) * k + r];
-    }
+    const int NL = nlev * k, NL16 = far_round16(NL), LP = far_lcol<T>(k), npad = (n + 7) & ~7;
+    const bool async = (k * (int)sizeof(T)) % 16 == 0;
+    float *Xs = (float *)fsm;                              // [npad][FLDX]
+    T *Ur = (T *)(fsm + 64 * FLDX * sizeof(float));        // [nlev][npad][LP]
+    stage_rows<float>(Xs, FLDX, X + (size_t)b * R + rt, R, RT, n, npad, true);
+    for (int l = 0; l < nlev; ++l)
+        stage_rows<T>(Ur + (size_t)l * npad * LP, LP, Ul + ((size_t)l * N + b) * k, k, k, n, npad, async);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    const int rq = threadIdx.x & 15, g = threadIdx.x >> 4;
-    for (int c0 = 0; c0 < NL; c0 += 64) {
-        float4 acc[4];
-        int lva[4];
-        for (int q = 0; q < 4; ++q) {
-            acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            lva[q] = min(c0 + g + 16 * q, NL - 1);
-        }
-#pragma unroll 4
-        for (int i = 0; i < n; ++i) {
-            const float4 x = Xs[i][rq];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+    for (int mt = warp; mt < NL16 / 16; mt += 8) {
+        const int m0 = mt * 16;
+        // the two rows (lva) this lane reads: level and index inside the level
+        const int v0 = m0 + g, v1 = v0 + 8;
+        const bool ok0 = v0 < NL, ok1 = v1 < NL;
+        const T *r0 = Ur + (size_t)(ok0 ? v0 / k : 0) * npad * LP + (ok0 ? v0 % k : 0);
+        const T *r1 = Ur + (size_t)(ok1 ? v1 / k : 0) * npad * LP + (ok1 ? v1 % k : 0);
+        float acc[8][4];
+        for (int j = 0; j < 8; ++j)
+            for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+        for (int k0 = 0; k0 < npad; k0 += 8) {
+            const int i0 = (k0 + t4) * LP, i4 = i0 + 4 * LP;
+            const uint32_t a[4] = {f2tf32(ok0 ? ldf(r0 + i0) : 0.f), f2tf32(ok1 ? ldf(r1 + i0) : 0.f),
+                                   f2tf32(ok0 ? ldf(r0 + i4) : 0.f), f2tf32(ok1 ? ldf(r1 + i4) : 0.f)};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) fma4(acc[q], Us[i * NL + lva[q]], x);
-        }
-        for (int q = 0; q < 4; ++q) {
-            const int v = c0 + g + 16 * q;
-            if (v < NL) {
-                const int l = v / k, al = v % k;
-                ((float4 *)part)[((((size_t)l * nleaf + leaf) * k + al) * R + rt) / 4 + rq] = acc[q];
+            for (int j = 0; j < 8; ++j) {
+                const float *B0 = Xs + (k0 + t4) * FLDX + j * 8 + g;
+                const uint32_t bb[2] = {f2tf32(B0[0]), f2tf32(B0[4 * FLDX])};
+                MmaTraits<float>::mma(acc[j], a, bb);
             }
+        }
+        for (int h = 0; h < 2; ++h) {
+            const int v = m0 + g + 8 * h;
+            if (v >= NL) continue;
+            const int l = v / k, al = v - l * k;
+            float *dst = part + (((size_t)l * nleaf + leaf) * k + al) * R + rt;
+            for (int j = 0; j < 8; ++j)
+                *(float2 *)(dst + j * 8 + 2 * t4) = make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
         }
     }
 }
@@ -413,18 +473,21 @@ __global__ void k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restri
     ((float4 *)xhat)[(size_t)node * k * R / 4 + t] = s[0];
 }
 
-// coupling: yhat[node][a][r] = sum_e sum_b S_e[b][a] xhat[col e][b][r].
-// CTA (64 threads) per (node, RHS tile); groups of EPS blocks S_e with their
-// column nodes' xhat rows pass through a two-stage cp.async pipeline in
-// shared memory; thread (r-quad = t % 16, g = t / 16) computes a = c*16 + g +
-// 4 q (q < 4), chunk by chunk.
+// coupling: yhat[node][a][r] = sum_e sum_b S_e[b][a] xhat[col e][b][r], i.e.
+// C[a][r] = sum_e sum_b A_e[a][b] B_e[b][r] with A_e[a][b] = Ss[b][a] (M = k,
+// N = 64, K = k per block).  CTA (64 threads, 2 warps) per (node, RHS tile);
+// warp w owns n8 tiles 4w..4w+3.  Groups of EPS blocks (S_e rows and the
+// column nodes' xhat rows) pass through a two-stage cp.async pipeline.
 constexpr int EPS = 4;   // coupling blocks per pipeline stage
 
+__host__ __device__ constexpr int couple_k8(int k) { return (k + 7) & ~7; }
 template <class T>
-__host__ __device__ constexpr int couple_sbytes(int k)
+__host__ __device__ constexpr size_t couple_block_bytes(int k)
 {
-    return (k * k * (int)sizeof(T) + 15) & ~15;
+    return (size_t)couple_k8(k) * far_lcol<T>(k) * sizeof(T) + (size_t)couple_k8(k) * FLDX * sizeof(float);
 }
+template <class T>
+static size_t couple_smem(int k) { return 2 * EPS * couple_block_bytes<T>(k); }
 
 template <class T>
 __global__ void __launch_bounds__(64)
@@ -441,72 +504,79 @@ k_mr_far_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, i
     const T *__restrict__ S = (const T *)Ms.S;
     const float *__restrict__ xhat = Ms.xhat;
     float *__restrict__ yhat = Ms.yhat;
-    const int rq = threadIdx.x & 15, g = threadIdx.x >> 4;
-    const int R4 = R >> 2;
-    const int sbytes = couple_sbytes<T>(k), xbytes = k * RT * 4, slot_bytes = EPS * (sbytes + xbytes);
+    const int k8 = couple_k8(k), k16 = far_round16(k), LS = far_lcol<T>(k);
+    const size_t bb_bytes = couple_block_bytes<T>(k), sbytes = (size_t)k8 * LS * sizeof(T);
+    const bool async = (k * (int)sizeof(T)) % 16 == 0;
     const int e0 = fptr[node], ne = fptr[node + 1] - e0, ng = (ne + EPS - 1) / EPS;
-    auto stage = [&](int slot, int grp) {
+    auto stage = [&](int sl, int grp) {
         for (int j = 0; j < EPS && grp * EPS + j < ne; ++j) {
             const int e = e0 + grp * EPS + j;
-            unsigned char *base = csm + slot * slot_bytes + j * (sbytes + xbytes);
-            const unsigned char *sg = (const unsigned char *)(S + (size_t)e * k * k);
-            const int sb = k * k * (int)sizeof(T);
-            // S_e: 16-byte copies where the block is 16-byte aligned, else 4-byte words
-            if ((((size_t)sg) & 15) == 0 && (sb & 15) == 0) {
-                for (int c = threadIdx.x; c < sb / 16; c += blockDim.x) cp_async16(base + 16 * c, sg + 16 * c, true);
-            } else {
-                for (int c = threadIdx.x; c < sb / 4; c += blockDim.x) ((uint32_t *)base)[c] = ((const uint32_t *)sg)[c];
-            }
-            const float *xg = xhat + (size_t)fcol[e] * k * R + rt;
-            for (int c = threadIdx.x; c < k * (RT / 4); c += blockDim.x) {
-                const int be = c / (RT / 4), q = c - be * (RT / 4);
-                cp_async16(base + sbytes + 16 * c, xg + (size_t)be * R + 4 * q, true);
-            }
+            unsigned char *base = csm + (size_t)(sl * EPS + j) * bb_bytes;
+            stage_rows<T>((T *)base, LS, S + (size_t)e * k * k, k, k, k, k8, async);
+            stage_rows<float>((float *)(base + sbytes), FLDX, xhat + (size_t)fcol[e] * k * R + rt, R, RT, k, k8, true);
         }
     };
-    for (int c0 = 0; c0 < k; c0 += 16) {
-        float4 acc[4];
-        for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ng > 0) stage(0, 0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+    float acc[4][4][4];   // [m16 tile][n8 tile][fragment]
+    for (int a = 0; a < 4; ++a)
+        for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < 4; ++q) acc[a][j][q] = 0.f;
+    if (ng > 0) stage(0, 0);
+    cp_async_commit();
+    for (int gi = 0; gi < ng; ++gi) {
+        if (gi + 1 < ng) stage((gi + 1) & 1, gi + 1);
         cp_async_commit();
-        for (int gi = 0; gi < ng; ++gi) {
-            if (gi + 1 < ng) stage((gi + 1) & 1, gi + 1);
-            cp_async_commit();
-            cp_async_wait<1>();
-            __syncthreads();
-            for (int j = 0; j < EPS && gi * EPS + j < ne; ++j) {
-                const unsigned char *base = csm + (gi & 1) * slot_bytes + j * (sbytes + xbytes);
-                const T *Ss = (const T *)base;
-                const float4 *Xs = (const float4 *)(base + sbytes);
-                for (int be = 0; be < k; ++be) {
-                    const float4 x = Xs[be * (RT / 4) + rq];
+        cp_async_wait<1>();
+        __syncthreads();
+        for (int j = 0; j < EPS && gi * EPS + j < ne; ++j) {
+            const unsigned char *base = csm + (size_t)((gi & 1) * EPS + j) * bb_bytes;
+            const T *Ss = (const T *)base;
+            const float *Xs = (const float *)(base + sbytes);
+            for (int k0 = 0; k0 < k8; k0 += 8) {
+                uint32_t bq[4][2];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int al = c0 + g + 4 * q;
-                        if (al < k) fma4(acc[q], (float)Ss[be * k + al], x);
-                    }
+                for (int jn = 0; jn < 4; ++jn) {
+                    const float *B0 = Xs + (k0 + t4) * FLDX + (warp * 4 + jn) * 8 + g;
+                    bq[jn][0] = f2tf32(B0[0]);
+                    bq[jn][1] = f2tf32(B0[4 * FLDX]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {
+                    if (mt * 16 >= k16) break;
+                    const int a0 = mt * 16 + g, a1 = a0 + 8;
+                    const T *c0 = Ss + (k0 + t4) * LS, *c4 = c0 + 4 * LS;
+                    const uint32_t a[4] = {f2tf32(a0 < k ? ldf(c0 + a0) : 0.f), f2tf32(a1 < k ? ldf(c0 + a1) : 0.f),
+                                           f2tf32(a0 < k ? ldf(c4 + a0) : 0.f), f2tf32(a1 < k ? ldf(c4 + a1) : 0.f)};
+#pragma unroll
+                    for (int jn = 0; jn < 4; ++jn) MmaTraits<float>::mma(acc[mt][jn], a, bq[jn]);
                 }
             }
-            __syncthreads();   // the slot is refilled two steps later
         }
-        cp_async_wait<0>();
-        for (int q = 0; q < 4; ++q) {
-            const int al = c0 + g + 4 * q;
-            if (al < k) ((float4 *)yhat)[((size_t)node * k + al) * R4 + (rt >> 2) + rq] = acc[q];
+        __syncthreads();   // the slot is refilled two steps later
+    }
+    cp_async_wait<0>();
+    for (int mt = 0; mt < 4; ++mt) {
+        if (mt * 16 >= k16) break;
+        for (int h = 0; h < 2; ++h) {
+            const int al = mt * 16 + g + 8 * h;
+            if (al >= k) continue;
+            float *dst = yhat + ((size_t)node * k + al) * R + rt;
+            for (int jn = 0; jn < 4; ++jn)
+                *(float2 *)(dst + (warp * 4 + jn) * 8 + 2 * t4) = make_float2(acc[mt][jn][2 * h], acc[mt][jn][2 * h + 1]);
         }
     }
 }
 
-// expansion: Y[i][r] += sum_l sum_a Ul[l][i][a] yhat[ancestor_l(i)][a][r].
-// CTA (256 threads) per (leaf, RHS tile): the ancestors' yhat rows (nlev*k
-// rows of 64 floats) and the leaf's basis rows Us[lva][i] staged in shared
-// memory; thread (r-quad = t % 16, g = t / 16) owns rows g + 16 q (q < 4).
+// expansion: Y[i][r] += sum_l sum_a Ul[l][i][a] yhat[ancestor_l(i)][a][r], i.e.
+// C[i][r] = sum_lva A[i][lva] Ys[lva][r] with A[i][lva] = Ur[l][i][a] (M = leaf
+// size, N = 64, K = nlev*k).  CTA (256 threads, 8 warps) per (leaf, RHS tile);
+// warp w owns the m16 tile w & 3 and the n8 tiles 4 (w >> 2) .. +3.
 template <class T>
 __global__ void __launch_bounds__(256)
 k_mr_far_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
                 const int *skip, const int *mdone)
 {
-    extern __shared__ float4 Ys[];   // [nlev * k][16], then Us[nlev * k][64] (floats)
+    extern __shared__ __align__(16) unsigned char esm[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
@@ -517,38 +587,52 @@ k_mr_far_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, i
     const float *__restrict__ yhat = Ms.yhat;
     float *__restrict__ Y = Yall + (size_t)Ms.xoff * R;
     const int b = Ms.kb[fl + leaf], n = Ms.ke[fl + leaf] - b;
-    const int nlev = L - lmin + 1, NL = nlev * k, R4 = R >> 2;
-    float *Us = (float *)(Ys + NL * 16);
-    for (int e = threadIdx.x; e < NL * 16; e += blockDim.x) {
-        const int row = e >> 4, q = e & 15, l = lmin + row / k, al = row % k;
-        const int node = ((fl + leaf + 1) >> (L - l)) - 1;
-        Ys[e] = ((const float4 *)yhat)[((size_t)node * k + al) * R4 + (rt >> 2) + q];
+    const int nlev = L - lmin + 1, NL = nlev * k, NL16 = far_round16(NL), LE = far_lrow<T>(k);
+    const int mtiles = (n + 15) / 16, nrow = mtiles * 16;
+    const bool async = (k * (int)sizeof(T)) % 16 == 0;
+    float *Ys = (float *)esm;                                           // [NL16][FLDX]
+    T *Ur = (T *)(esm + (size_t)NL16 * FLDX * sizeof(float));          // [nlev][nrow][LE]
+    for (int l = 0; l < nlev; ++l) {
+        const int node = ((fl + leaf + 1) >> (L - (lmin + l))) - 1;
+        stage_rows<float>(Ys + (size_t)l * k * FLDX, FLDX, yhat + (size_t)node * k * R + rt, R, RT, k, k, true);
+        stage_rows<T>(Ur + (size_t)l * nrow * LE, LE, Ul + ((size_t)l * N + b) * k, k, k, n, nrow, async);
     }
-    for (int e = threadIdx.x; e < nlev * n * k; e += blockDim.x) {
-        const int l = e / (n * k), r = e - l * n * k, i = r / k, al = r - i * k;
-        Us[(l * k + al) * 64 + i] = (float)Ul[((size_t)l * N + b) * k + r];
-    }
+    for (int e = NL * FLDX + threadIdx.x; e < NL16 * FLDX; e += blockDim.x) Ys[e] = 0.f;
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    const int rq = threadIdx.x & 15, g = threadIdx.x >> 4;
-    float4 acc[4];
-    for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-    for (int lva = 0; lva < NL; ++lva) {
-        const float4 y = Ys[lva * 16 + rq];
-        const float *u = Us + lva * 64 + g;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+    const int mt = warp & 3, nb = (warp >> 2) * 4;
+    if (mt >= mtiles) return;
+    const int i0 = mt * 16 + g;
+    float acc[4][4];
+    for (int j = 0; j < 4; ++j)
+        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+    for (int k0 = 0; k0 < NL16; k0 += 8) {
+        // the two columns (lva) this lane reads: k0 + t4 and k0 + t4 + 4
+        const int v0 = k0 + t4, v1 = v0 + 4;
+        const bool ok0 = v0 < NL, ok1 = v1 < NL;
+        const T *c0 = Ur + ((size_t)(ok0 ? v0 / k : 0) * nrow + i0) * LE + (ok0 ? v0 % k : 0);
+        const T *c1 = Ur + ((size_t)(ok1 ? v1 / k : 0) * nrow + i0) * LE + (ok1 ? v1 % k : 0);
+        const uint32_t a[4] = {f2tf32(ok0 ? ldf(c0) : 0.f), f2tf32(ok0 ? ldf(c0 + 8 * LE) : 0.f),
+                               f2tf32(ok1 ? ldf(c1) : 0.f), f2tf32(ok1 ? ldf(c1 + 8 * LE) : 0.f)};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) fma4(acc[q], u[16 * q], y);
+        for (int j = 0; j < 4; ++j) {
+            const float *B0 = Ys + (k0 + t4) * FLDX + (nb + j) * 8 + g;
+            const uint32_t bb[2] = {f2tf32(B0[0]), f2tf32(B0[4 * FLDX])};
+            MmaTraits<float>::mma(acc[j], a, bb);
+        }
     }
-    for (int q = 0; q < 4; ++q) {
-        const int i = g + 16 * q;
-        if (i < n) {
-            float4 *yp = (float4 *)Y + (size_t)(b + i) * R4 + (rt >> 2) + rq;
-            float4 v = *yp;
-            v.x += acc[q].x;
-            v.y += acc[q].y;
-            v.z += acc[q].z;
-            v.w += acc[q].w;
-            *yp = v;
+    for (int h = 0; h < 2; ++h) {
+        const int i = mt * 16 + g + 8 * h;
+        if (i >= n) continue;
+        float *yp = Y + (size_t)(b + i) * R + rt;
+        for (int j = 0; j < 4; ++j) {
+            float2 *p2 = (float2 *)(yp + (nb + j) * 8 + 2 * t4);
+            float2 v = *p2;
+            v.x += acc[j][2 * h];
+            v.y += acc[j][2 * h + 1];
+            *p2 = v;
         }
     }
 }
@@ -556,7 +640,16 @@ k_mr_far_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, i
 // ---------------------------------------------------------------------------
 // host side: descriptors, work items, workspaces, launches
 // ---------------------------------------------------------------------------
-BatchData::~BatchData() { release_bgraph(*this); }
+BatchData::~BatchData()
+{
+    release_bgraph(*this);
+    if (side) {
+        cudaStreamSynchronize(side);
+        cudaStreamDestroy(side);
+        cudaEventDestroy(ev_fork);
+        cudaEventDestroy(ev_join);
+    }
+}
 
 void release_bgraph(BatchData &b)
 {
@@ -591,6 +684,15 @@ static void ensure_batch(BatchData &b, int R)
 {
     if (b.R == R) return;
     release_bgraph(b);
+    if (!b.side) {
+        // the far chain is a sequence of small launches: give it priority so its
+        // CTAs are not queued behind the near-panel kernel
+        int lo = 0, hi = 0;
+        VFD_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        VFD_CUDA(cudaStreamCreateWithPriority(&b.side, cudaStreamNonBlocking, hi));
+        VFD_CUDA(cudaEventCreateWithFlags(&b.ev_fork, cudaEventDisableTiming));
+        VFD_CUDA(cudaEventCreateWithFlags(&b.ev_join, cudaEventDisableTiming));
+    }
     const bool bf = b.precision == VFD_BF16;
     size_t np = 0, nh = 0;
     b.max_panel_w = b.max_k = b.max_nlev = b.max_leaf = 0;
@@ -613,13 +715,12 @@ static void ensure_batch(BatchData &b, int R)
     }
     VFD_REQUIRE(near_smem_bytes<float>(b.max_panel_w) <= 227 * 1024, VFD_EUNSUPPORTED,
                 "batched apply: near panel too wide");
-    VFD_REQUIRE(2 * EPS * ((size_t)couple_sbytes<float>(b.max_k) + (size_t)b.max_k * RT * sizeof(float)) <= 227 * 1024,
-                VFD_EUNSUPPORTED, "batched apply: rank too large for the coupling tile");
-    VFD_REQUIRE(!b.any_far || (size_t)b.max_nlev * b.max_k * (RT + 64) * sizeof(float) <= 227 * 1024,
-                VFD_EUNSUPPORTED, "batched apply: too many far levels x rank for the expansion tile");
-    VFD_REQUIRE(!b.any_far || (size_t)b.max_leaf * b.max_nlev * b.max_k * sizeof(float) + 64 * RT * sizeof(float) <=
-                                  227 * 1024,
-                VFD_EUNSUPPORTED, "batched apply: too many far levels x rank for the projection tile");
+    VFD_REQUIRE(b.max_k <= 64 && couple_smem<float>(b.max_k) <= 227 * 1024, VFD_EUNSUPPORTED,
+                "batched apply: rank too large for the coupling tile");
+    VFD_REQUIRE(!b.any_far || far_smem_expand<float>(b.max_nlev, b.max_k) <= 227 * 1024, VFD_EUNSUPPORTED,
+                "batched apply: too many far levels x rank for the expansion tile");
+    VFD_REQUIRE(!b.any_far || far_smem_proj<float>(b.max_nlev, b.max_k) <= 227 * 1024, VFD_EUNSUPPORTED,
+                "batched apply: too many far levels x rank for the projection tile");
     b.part.alloc(std::max<size_t>(np, 1));
     b.xhat.alloc(std::max<size_t>(nh, 1));
     b.yhat.alloc(std::max<size_t>(nh, 1));
@@ -705,6 +806,23 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
                              const int *mdone)
 {
     const MrMesh *ms = (const MrMesh *)b.desc.p;
+    const int k = b.max_k, nlev = b.max_nlev;
+    if (b.any_far) {
+        // projections, node sums and coupling on the side stream, concurrent with the rows
+        VFD_CUDA(cudaEventRecord(b.ev_fork, st));
+        VFD_CUDA(cudaStreamWaitEvent(b.side, b.ev_fork, 0));
+        dim3 gp(b.n_leaf_items, R / RT);
+        const size_t pshm = far_smem_proj<T>(nlev, k);
+        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
+        k_mr_far_proj<T><<<gp, 256, pshm, b.side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
+        dim3 gs(b.n_sum_items, cdiv(k * R / 4, 128));
+        k_mr_far_sum<<<gs, 128, 0, b.side>>>(ms, (const int2 *)b.sum_items.p, R, skip, mdone);
+        dim3 gc(b.n_node_items, R / RT);
+        const size_t cshm = couple_smem<T>(k);
+        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
+        k_mr_far_couple<T><<<gc, 64, cshm, b.side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
+        VFD_CUDA(cudaEventRecord(b.ev_join, b.side));
+    }
     if (b.n_near_items > 0) {
         const size_t shm = near_smem_bytes<T>(b.max_panel_w);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -714,20 +832,10 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
     k_mr_csr<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R, X,
                                                                       Y, b.y2.p, skip, mdone);
     if (b.any_far) {
-        const int k = b.max_k, nlev = b.max_nlev;
-        dim3 gp(b.n_leaf_items, R / RT);
-        const size_t pshm = (size_t)b.max_leaf * nlev * k * sizeof(float);
-        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-        k_mr_far_proj<T><<<gp, 256, pshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
-        dim3 gs(b.n_sum_items, cdiv(k * R / 4, 128));
-        k_mr_far_sum<<<gs, 128, 0, st>>>(ms, (const int2 *)b.sum_items.p, R, skip, mdone);
-        dim3 gc(b.n_node_items, R / RT);
-        const size_t cshm = 2 * EPS * ((size_t)couple_sbytes<T>(k) + (size_t)k * RT * sizeof(float));
-        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
-        k_mr_far_couple<T><<<gc, 64, cshm, st>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
-        const size_t eshm = (size_t)nlev * k * (RT + 64) * sizeof(float);
-        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eshm));
+        VFD_CUDA(cudaStreamWaitEvent(st, b.ev_join, 0));
         dim3 ge(b.n_leaf_items, R / RT);
+        const size_t eshm = far_smem_expand<T>(nlev, k);
+        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eshm));
         k_mr_far_expand<T><<<ge, 256, eshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
     }
     VFD_CUDA(cudaGetLastError());

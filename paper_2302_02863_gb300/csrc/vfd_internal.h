@@ -255,6 +255,8 @@ struct BatchData {
     DBuf<int> flag, red_items, red_mesh;
     int nred = 0, sR = 0;
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t side = nullptr;        // far-field branch of the batched apply
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~BatchData();
 };
 
