@@ -278,6 +278,13 @@ vfd_status vfd_batch_apply(vfd_batch_t batch, const double *const *X, double *co
 vfd_status vfd_batch_solve(vfd_batch_t batch, const double *const *F, double *const *U, const int64_t *ld,
                            int64_t nrhs, double rtol, int max_it, int *iters, double *relres, void *stream);
 
+/* The tile configuration the batch picked for its near-panel kernel by timing
+ * every candidate once on its first apply (zero inputs): chosen[0..2] = panel
+ * columns per pipeline stage, pipeline depth, CTAs per panel (all 0 before the
+ * first apply); us[i] = candidate i's time in microseconds (0 = not run or
+ * does not fit), n entries at most; *ncand = the number of candidates. */
+vfd_status vfd_batch_tuning(vfd_batch_t batch, int *chosen, float *us, int n, int *ncand);
+
 void vfd_batch_free(vfd_batch_t batch);
 
 /* Adjoint gradient (the paper has no gradients; derivative of the discrete

@@ -41,6 +41,16 @@ struct MrMesh {
     float *part, *xhat, *yhat;   // far-field workspaces of this mesh
 };
 
+// one (mesh, leaf) work item of the near-panel kernel, everything it needs in one load
+struct NearItem {
+    const void *D;       // the leaf's panel (row stride W)
+    const int *gcol;     // the panel's gather columns (mesh-local DoFs, -1 = padding)
+    int row0;            // first row of the leaf in the batch vectors
+    int na, W;           // leaf rows, panel width (multiple of 8)
+    int xoff;            // first row of the mesh in the batch vectors
+    int mesh, pad;
+};
+
 namespace {
 
 template <class T>
@@ -100,20 +110,20 @@ __device__ __forceinline__ float from_f<float>(float v) { return __uint_as_float
 //   Bs[stage][NK][LDB]  gathered x rows X[gcol[k]][rt .. rt+63] (FP32),
 //                       zero-filled for the padding columns (gcol = -1).
 // The gather indices of the whole panel are staged in shared memory first.
-// A fragments come from ldmatrix, B fragments from two shared loads; FP32
-// values are rounded to TF32 (cvt.rna), B values packed to BF16x2 (cvt.rn).
-// Rounding to nearest matters: truncation (what the tensor core does with raw
-// FP32 bits) biases the low-precision operator, and the refinement then
-// needed about twice the inner iterations.  The
-// panel's chunks are split over KSPLIT CTAs (blockIdx.z); CTA z writes its
-// partial product to Y (z = 0) or Y2 (z = 1), summed by the CSR kernel.
+// A fragments come from ldmatrix (FP32 panels are stored pre-rounded to TF32
+// for this kernel), B fragments from two shared loads, rounded to TF32
+// (cvt.rna) or packed to BF16x2 (cvt.rn).  Rounding to nearest matters:
+// truncation (what the tensor core does with raw FP32 bits) biases the
+// low-precision operator, and the refinement then needed about twice the
+// inner iterations.  The panel's chunks are split over gridDim.z CTAs; CTA z
+// writes its partial product to Y (z = 0) or to partial buffer z - 1 of Y2,
+// summed by the CSR kernel.  The stage width NK, the depth NSTAGE and the
+// split are picked per batch by timing the candidates (near_configs).
 // ---------------------------------------------------------------------------
-constexpr int NK = 32;       // panel columns per stage
-constexpr int NSTAGE = 3;    // pipeline depth
-constexpr int KSPLIT = 2;    // CTAs per (leaf, RHS tile), each a contiguous range of chunks
 constexpr int NEAR_THREADS = 256;
+constexpr int KSPLIT_MAX = 4;
 
-template <class T>
+template <class T, int NK>
 struct NearTile {
     static constexpr int LDA = NK + (sizeof(T) == 2 ? 8 : 4);   // A row stride (elements): conflict-free fragments
     static constexpr int LDB = RT + (sizeof(T) == 2 ? 4 : 8);   // B row stride (floats)
@@ -151,28 +161,25 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return r;
 }
 
-template <class T>
+template <class T, int NK, int NSTAGE>
 __global__ void __launch_bounds__(NEAR_THREADS)
-k_mr_near(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
-          float *__restrict__ Yall, float *__restrict__ Y2all, const int *skip, const int *mdone)
+k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
+          float *__restrict__ Y2all, size_t pstride, const int *skip, const int *mdone)
 {
-    using TT = NearTile<T>;
+    using TT = NearTile<T, NK>;
     extern __shared__ __align__(16) unsigned char smem[];
     if (skip && *skip) return;
-    const int2 item = items[blockIdx.x];
-    if (mdone && mdone[item.x]) return;
-    const MrMesh &Ms = ms[item.x];
-    const int lf = item.y, rt = blockIdx.y * RT, fl = Ms.fl;
-    const size_t xo = (size_t)Ms.xoff * R;
-    const float *__restrict__ X = Xall + xo;
-    float *__restrict__ Y = Yall + xo;
-    float *__restrict__ Y2 = Y2all + xo;
-    const T *__restrict__ D = (const T *)Ms.D;
-    const int b0 = Ms.kb[fl + lf], na = Ms.ke[fl + lf] - b0;
-    const int W = Ms.pw[lf];   // multiple of 8
-    const T *Dp = D + Ms.poff[lf];
+    const NearItem it = items[blockIdx.x];
+    if (mdone && mdone[it.mesh]) return;
+    const int rt = blockIdx.y * RT;
+    const float *__restrict__ X = Xall + (size_t)it.xoff * R;   // gather columns are mesh-local rows
+    float *__restrict__ Y = Yall;
+    float *__restrict__ Y2 = Y2all;
+    const T *__restrict__ Dp = (const T *)it.D;
+    const T *__restrict__ D = Dp;
+    const int b0 = it.row0, na = it.na, W = it.W;
     int *gs = (int *)(smem + NSTAGE * TT::STAGE_BYTES);
-    const int *gcol = Ms.gcol + Ms.goff[lf];
+    const int *gcol = it.gcol;
     for (int c = threadIdx.x; c < W; c += NEAR_THREADS) gs[c] = gcol[c];
     __syncthreads();
 
@@ -195,8 +202,8 @@ k_mr_near(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, 
         }
     };
 
-    const int nkt = (W + NK - 1) / NK;
-    const int kc0 = (int)(((long long)nkt * blockIdx.z) / KSPLIT), nk = (int)(((long long)nkt * (blockIdx.z + 1)) / KSPLIT) - kc0;
+    const int nkt = (W + NK - 1) / NK, ks = gridDim.z;
+    const int kc0 = (int)(((long long)nkt * blockIdx.z) / ks), nk = (int)(((long long)nkt * (blockIdx.z + 1)) / ks) - kc0;
     for (int s = 0; s < NSTAGE - 1; ++s) {
         if (s < nk) load_stage(s, kc0 + s);
         cp_async_commit();
@@ -223,8 +230,6 @@ k_mr_near(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, 
                 // lanes 8m..8m+7 address the rows of 8x16-byte matrix m: rows +8 for m odd, columns +16 bytes for m >= 2
                 const int m = lane >> 3, rr = lane & 7;
                 ldmatrix_x4(a, As + (r0 + rr + (m & 1) * 8) * TT::LDA + ks + (m >> 1) * (16 / (int)sizeof(T)));
-                if constexpr (sizeof(T) == 4)
-                    for (int q = 0; q < 4; ++q) a[q] = f2tf32(__uint_as_float(a[q]));
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -245,7 +250,7 @@ k_mr_near(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, 
     }
     cp_async_wait<0>();
     if (!active) return;
-    float *Yo = blockIdx.z == 0 ? Y : Y2;
+    float *Yo = blockIdx.z == 0 ? Y : Y2 + (size_t)(blockIdx.z - 1) * pstride;
     for (int j = 0; j < 4; ++j) {
         const int col = rt + n0 + j * 8 + 2 * t4;
         const int ra = r0 + g, rb = r0 + g + 8;
@@ -254,18 +259,55 @@ k_mr_near(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, 
     }
 }
 
-template <class T>
+template <class T, int NK, int NSTAGE>
 static size_t near_smem_bytes(int max_panel_w)
 {
-    return (size_t)NSTAGE * NearTile<T>::STAGE_BYTES + (size_t)max_panel_w * sizeof(int);
+    return (size_t)NSTAGE * NearTile<T, NK>::STAGE_BYTES + (size_t)max_panel_w * sizeof(int);
 }
 
-// Y[i][r..r+3] = (Y + Y2)[i][r..r+3] + sum_c val[c] X[col c][r..r+3]   (B + M
-// in FP32 added to the two partial near products; thread per (row, 4 RHS);
-// accumulate = 0: no near products)
+// candidate tile configurations of the near-panel kernel
+struct NearCfg {
+    int nk, nstage, ksplit;
+};
+static const NearCfg kNearCfgs[] = {{32, 3, 2}, {32, 3, 3}, {16, 4, 2}, {16, 4, 3}, {64, 2, 2}, {32, 4, 2}, {32, 3, 4}};
+constexpr int kNearCfgCount = (int)(sizeof(kNearCfgs) / sizeof(kNearCfgs[0]));
+
+template <class T, int NK, int NS>
+static bool launch_near_cfg(int ksplit, int n_items, int max_panel_w, const NearItem *items, int R, const float *X,
+                            float *Y, float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone)
+{
+    const size_t shm = near_smem_bytes<T, NK, NS>(max_panel_w);
+    if (shm > 227 * 1024) return false;
+    VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T, NK, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    dim3 g(n_items, R / RT, ksplit);
+    k_mr_near<T, NK, NS><<<g, NEAR_THREADS, shm, st>>>(items, R, X, Y, Y2, pstride, skip, mdone);
+    return true;
+}
+
+// launch configuration c; false if it does not fit in shared memory
+template <class T>
+static bool launch_near(int c, int n_items, int max_panel_w, const NearItem *items, int R, const float *X, float *Y,
+                        float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone)
+{
+    const NearCfg &f = kNearCfgs[c];
+#define VFD_NEAR_CASE(NKV, NSV)                                                                                  \
+    if (f.nk == NKV && f.nstage == NSV)                                                                          \
+        return launch_near_cfg<T, NKV, NSV>(f.ksplit, n_items, max_panel_w, items, R, X, Y, Y2, pstride, st, skip, \
+                                            mdone);
+    VFD_NEAR_CASE(32, 3)
+    VFD_NEAR_CASE(16, 4)
+    VFD_NEAR_CASE(64, 2)
+    VFD_NEAR_CASE(32, 4)
+#undef VFD_NEAR_CASE
+    return false;
+}
+
+// Y[i][r..r+3] = (Y + sum_z Y2_z)[i][r..r+3] + sum_c val[c] X[col c][r..r+3]
+// (B + M in FP32 added to the partial near products; thread per (row, 4 RHS);
+// meshes without near blocks: no near products)
 __global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restrict__ row_off, int nmesh,
                          long long ntot, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
-                         const float *__restrict__ Y2all, const int *skip, const int *mdone)
+                         const float *__restrict__ Y2all, int nparts, const int *skip, const int *mdone)
 {
     if (skip && *skip) return;
     const int R4 = R >> 2;
@@ -284,6 +326,7 @@ __global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restr
     const float *__restrict__ X = Xall + xo;
     float *__restrict__ Y = Yall + xo;
     const float *__restrict__ Y2 = Y2all + xo;
+    const size_t pstride = (size_t)ntot * R / 4;   // float4 stride between partial buffers
     const int *__restrict__ rowptr = Ms.rowptr, *__restrict__ colidx = Ms.colidx;
     const float *__restrict__ val = Ms.val;
     const long long t = tg - Ms.xoff * R4;
@@ -291,8 +334,14 @@ __global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restr
     const float4 *X4 = (const float4 *)X;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (Ms.has_near) {
-        const float4 a = ((const float4 *)Y)[t], b = ((const float4 *)Y2)[t];
-        acc = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+        acc = ((const float4 *)Y)[t];
+        for (int z = 0; z < nparts; ++z) {
+            const float4 b = ((const float4 *)Y2)[(size_t)z * pstride + t];
+            acc.x += b.x;
+            acc.y += b.y;
+            acc.z += b.z;
+            acc.w += b.w;
+        }
     }
     for (int c = rowptr[i]; c < rowptr[i + 1]; ++c) {
         const float v = val[c];
@@ -433,9 +482,12 @@ k_mr_far_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int
 }
 
 // xhat[node][a][r] = sum over the node's leaves of part (levels lmin..L)
-__global__ void k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip,
-                             const int *mdone)
+__global__ void __launch_bounds__(256) k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items,
+                                                   int R, const int *skip, const int *mdone)
 {
+    // CTA: 32 float4 outputs x 8 lanes over the node's leaves; the 8 lane sums
+    // are combined in a fixed order through shared memory
+    __shared__ float4 sh[8][32];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
@@ -443,34 +495,35 @@ __global__ void k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restri
     const int node = item.y, lmin = Ms.lmin, L = Ms.L, k = Ms.k, nleaf = Ms.nleaf;
     const float *__restrict__ part = Ms.part;
     float *__restrict__ xhat = Ms.xhat;
-    const int t = blockIdx.y * blockDim.x + threadIdx.x;
-    if (t >= k * R / 4) return;
+    const int o = threadIdx.x & 31, lane = threadIdx.x >> 5;
+    const int t = blockIdx.y * 32 + o;
+    const bool ok = t < k * R / 4;
     int l = 0;
     while ((2 << l) - 1 <= node) ++l;
     const int span = 1 << (L - l), leaf0 = ((node + 1) << (L - l)) - 1 - ((1 << L) - 1);
-    const float4 *p = (const float4 *)part + (((size_t)(l - lmin) * nleaf + leaf0) * k * R) / 4 + t;
-    // eight independent partial sums (loads in flight together), combined in a fixed order
-    float4 s[8];
-    for (int q = 0; q < 8; ++q) s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     const size_t stride = (size_t)k * R / 4;
-    for (int j0 = 0; j0 < span; j0 += 8) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (j0 + q < span) {
-                const float4 v = p[(size_t)(j0 + q) * stride];
-                s[q].x += v.x;
-                s[q].y += v.y;
-                s[q].z += v.z;
-                s[q].w += v.w;
-            }
+    const float4 *p = (const float4 *)part + (((size_t)(l - lmin) * nleaf + leaf0) * k * R) / 4 + (ok ? t : 0);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ok)
+#pragma unroll 4
+        for (int j = lane; j < span; j += 8) {
+            const float4 v = p[(size_t)j * stride];
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+    sh[lane][o] = s;
+    __syncthreads();
+    if (lane == 0 && ok) {
+        for (int q = 1; q < 8; ++q) {
+            s.x += sh[q][o].x;
+            s.y += sh[q][o].y;
+            s.z += sh[q][o].z;
+            s.w += sh[q][o].w;
+        }
+        ((float4 *)xhat)[(size_t)node * stride + t] = s;
     }
-    for (int q = 1; q < 8; ++q) {
-        s[0].x += s[q].x;
-        s[0].y += s[q].y;
-        s[0].z += s[q].z;
-        s[0].w += s[q].w;
-    }
-    ((float4 *)xhat)[(size_t)node * k * R / 4 + t] = s[0];
 }
 
 // coupling: yhat[node][a][r] = sum_e sum_b S_e[b][a] xhat[col e][b][r], i.e.
@@ -678,9 +731,54 @@ static void upload_items(DBuf<int> &buf, const std::vector<int> &v)
     buf.upload(v.empty() ? std::vector<int>{0, 0} : v);
 }
 
-// descriptors, item queues and workspaces for R columns (allocates: call
-// outside stream capture; a captured solve is released when they change)
-static void ensure_batch(BatchData &b, int R)
+__global__ void k_tf32_copy(long long n, const float *__restrict__ a, float *__restrict__ b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __uint_as_float(f2tf32(a[i]));
+}
+
+// time every candidate tile configuration of the near-panel kernel once on
+// this batch (zero inputs, scratch outputs) and keep the fastest
+template <class T>
+static void tune_near(BatchData &b, int R, cudaStream_t st)
+{
+    const size_t n = (size_t)b.ntot * R;
+    DBuf<float> tx, ty;
+    tx.alloc(n);
+    ty.alloc(n);
+    tx.zero(st);
+    cudaEvent_t e0, e1;
+    VFD_CUDA(cudaEventCreate(&e0));
+    VFD_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestc = 0;
+    const NearItem *items = (const NearItem *)b.near_items.p;
+    for (int c = 0; c < kNearCfgCount; ++c) {
+        if (!launch_near<T>(c, b.n_near_items, b.max_panel_w, items, R, tx.p, ty.p, b.y2.p, n, st, nullptr, nullptr))
+            continue;
+        VFD_CUDA(cudaEventRecord(e0, st));
+        for (int rep = 0; rep < 3; ++rep)
+            launch_near<T>(c, b.n_near_items, b.max_panel_w, items, R, tx.p, ty.p, b.y2.p, n, st, nullptr, nullptr);
+        VFD_CUDA(cudaEventRecord(e1, st));
+        VFD_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VFD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        b.near_cfg_us[c] = 1000.f * ms / 3;
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    VFD_CUDA(cudaStreamSynchronize(st));
+    b.near_cfg = bestc;
+}
+
+// descriptors, item queues and workspaces for R columns (allocates and times
+// the near-panel candidates: call outside stream capture; a captured solve is
+// released when they change)
+static void ensure_batch(BatchData &b, int R, cudaStream_t st)
 {
     if (b.R == R) return;
     release_bgraph(b);
@@ -713,7 +811,7 @@ static void ensure_batch(BatchData &b, int R)
         b.max_k = std::max(b.max_k, m.k);
         b.max_leaf = std::max(b.max_leaf, m.max_leaf_size);
     }
-    VFD_REQUIRE(near_smem_bytes<float>(b.max_panel_w) <= 227 * 1024, VFD_EUNSUPPORTED,
+    VFD_REQUIRE((near_smem_bytes<float, 32, 3>(b.max_panel_w) <= 227 * 1024), VFD_EUNSUPPORTED,
                 "batched apply: near panel too wide");
     VFD_REQUIRE(b.max_k <= 64 && couple_smem<float>(b.max_k) <= 227 * 1024, VFD_EUNSUPPORTED,
                 "batched apply: rank too large for the coupling tile");
@@ -724,9 +822,19 @@ static void ensure_batch(BatchData &b, int R)
     b.part.alloc(std::max<size_t>(np, 1));
     b.xhat.alloc(std::max<size_t>(nh, 1));
     b.yhat.alloc(std::max<size_t>(nh, 1));
-    b.y2.alloc((size_t)b.ntot * R);
+    b.y2.alloc((size_t)(KSPLIT_MAX - 1) * b.ntot * R);
+    if (!bf)
+        for (OpData *op : b.ops)
+            if (op->D32t.n != op->D32.n) {
+                op->D32t.alloc(op->D32.n);
+                if (op->D32.n)
+                    k_tf32_copy<<<cdiv((long long)op->D32.n, 256), 256, 0, st>>>((long long)op->D32.n, op->D32.p,
+                                                                                op->D32t.p);
+                VFD_CUDA(cudaGetLastError());
+            }
     std::vector<MrMesh> d(b.nmesh);
-    std::vector<int> li, si, ni, nri;
+    std::vector<int> li, si, ni;
+    std::vector<NearItem> nri;
     size_t po = 0, ho = 0;
     for (int i = 0; i < b.nmesh; ++i) {
         const OpData &op = *b.ops[i];
@@ -753,7 +861,7 @@ static void ensure_batch(BatchData &b, int R)
         e.fptr = m.far_ptr.p;
         e.fcol = m.far_col.p;
         e.poff = m.panel_off.p;
-        e.D = bf ? (const void *)op.D16.p : (const void *)op.D32.p;
+        e.D = bf ? (const void *)op.D16.p : (const void *)op.D32t.p;
         e.Ul = bf ? (const void *)op.Ul16.p : (const void *)op.Ul32.p;
         e.S = bf ? (const void *)op.S16.p : (const void *)op.S32.p;
         e.val = op.valBM32.p;
@@ -764,10 +872,30 @@ static void ensure_batch(BatchData &b, int R)
             po += (size_t)e.nlev * m.kt.nleaf * m.k * R;
             ho += (size_t)m.kt.nnode * m.k * R;
         }
+        std::vector<int> kb_h, ke_h, pw_h, goff_h;
+        std::vector<int64_t> poff_h;
+        if (m.nnear > 0) {
+            kb_h.assign(m.kt.begin.begin(), m.kt.begin.end());
+            ke_h.assign(m.kt.end.begin(), m.kt.end.end());
+            pw_h.resize(m.kt.nleaf);
+            goff_h.resize(m.kt.nleaf + 1);
+            poff_h.resize(m.kt.nleaf + 1);
+            VFD_CUDA(cudaMemcpy(pw_h.data(), m.panel_w.p, sizeof(int) * pw_h.size(), cudaMemcpyDeviceToHost));
+            VFD_CUDA(cudaMemcpy(goff_h.data(), m.gcol_off.p, sizeof(int) * goff_h.size(), cudaMemcpyDeviceToHost));
+            VFD_CUDA(cudaMemcpy(poff_h.data(), m.panel_off.p, sizeof(int64_t) * poff_h.size(), cudaMemcpyDeviceToHost));
+        }
+        const size_t esz = bf ? 2 : 4;
         for (int lf = 0; lf < m.kt.nleaf; ++lf) {
             if (m.nnear > 0) {
-                nri.push_back(i);
-                nri.push_back(lf);
+                NearItem it{};
+                it.D = (const unsigned char *)e.D + (size_t)poff_h[lf] * esz;
+                it.gcol = m.gcol.p + goff_h[lf];
+                it.row0 = (int)b.xoff[i] + kb_h[e.fl + lf];
+                it.na = ke_h[e.fl + lf] - kb_h[e.fl + lf];
+                it.W = pw_h[lf];
+                it.xoff = (int)b.xoff[i];
+                it.mesh = i;
+                nri.push_back(it);
             }
             if (m.nfar > 0) {
                 li.push_back(i);
@@ -791,14 +919,24 @@ static void ensure_batch(BatchData &b, int R)
     upload_items(b.leaf_items, li);
     upload_items(b.sum_items, si);
     upload_items(b.node_items, ni);
-    upload_items(b.near_items, nri);
+    {
+        std::vector<unsigned char> nb(sizeof(NearItem) * std::max<size_t>(nri.size(), 1), 0);
+        if (!nri.empty()) memcpy(nb.data(), nri.data(), sizeof(NearItem) * nri.size());
+        b.near_items.upload(nb);
+    }
     b.n_leaf_items = (int)li.size() / 2;
     b.n_sum_items = (int)si.size() / 2;
     b.n_node_items = (int)ni.size() / 2;
-    b.n_near_items = (int)nri.size() / 2;
+    b.n_near_items = (int)nri.size();
     std::vector<long long> ro(b.xoff.begin(), b.xoff.end());
     b.row_off.upload(ro);
     b.R = R;
+    if (b.n_near_items > 0) {
+        if (bf) tune_near<__nv_bfloat16>(b, R, st);
+        else tune_near<float>(b, R, st);
+    } else {
+        b.near_cfg = 0;
+    }
 }
 
 template <class T>
@@ -815,22 +953,20 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
         const size_t pshm = far_smem_proj<T>(nlev, k);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
         k_mr_far_proj<T><<<gp, 256, pshm, b.side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
-        dim3 gs(b.n_sum_items, cdiv(k * R / 4, 128));
-        k_mr_far_sum<<<gs, 128, 0, b.side>>>(ms, (const int2 *)b.sum_items.p, R, skip, mdone);
+        dim3 gs(b.n_sum_items, cdiv(k * R / 4, 32));
+        k_mr_far_sum<<<gs, 256, 0, b.side>>>(ms, (const int2 *)b.sum_items.p, R, skip, mdone);
         dim3 gc(b.n_node_items, R / RT);
         const size_t cshm = couple_smem<T>(k);
         VFD_CUDA(cudaFuncSetAttribute(k_mr_far_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
         k_mr_far_couple<T><<<gc, 64, cshm, b.side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
         VFD_CUDA(cudaEventRecord(b.ev_join, b.side));
     }
-    if (b.n_near_items > 0) {
-        const size_t shm = near_smem_bytes<T>(b.max_panel_w);
-        VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        dim3 g(b.n_near_items, R / RT, KSPLIT);
-        k_mr_near<T><<<g, NEAR_THREADS, shm, st>>>(ms, (const int2 *)b.near_items.p, R, X, Y, b.y2.p, skip, mdone);
-    }
+    const int nparts = kNearCfgs[b.near_cfg].ksplit - 1;
+    if (b.n_near_items > 0)
+        launch_near<T>(b.near_cfg, b.n_near_items, b.max_panel_w, (const NearItem *)b.near_items.p, R, X, Y, b.y2.p,
+                       (size_t)b.ntot * R, st, skip, mdone);
     k_mr_csr<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R, X,
-                                                                      Y, b.y2.p, skip, mdone);
+                                                                      Y, b.y2.p, nparts, skip, mdone);
     if (b.any_far) {
         VFD_CUDA(cudaStreamWaitEvent(st, b.ev_join, 0));
         dim3 ge(b.n_leaf_items, R / RT);
@@ -841,13 +977,26 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
     VFD_CUDA(cudaGetLastError());
 }
 
+// the near-panel tuning of a batch: chosen (stage width, depth, split) and the candidates' times
+int batch_tuning(const BatchData &b, int *chosen, float *us, int n)
+{
+    if (chosen) {
+        const NearCfg &f = kNearCfgs[b.near_cfg < 0 ? 0 : b.near_cfg];
+        chosen[0] = b.near_cfg < 0 ? 0 : f.nk;
+        chosen[1] = b.near_cfg < 0 ? 0 : f.nstage;
+        chosen[2] = b.near_cfg < 0 ? 0 : f.ksplit;
+    }
+    for (int i = 0; i < n && i < kNearCfgCount; ++i) us[i] = b.near_cfg_us[i];
+    return kNearCfgCount;
+}
+
 // Y = A_low X for R (multiple of 64) interleaved FP32 columns over all meshes;
 // skip: device flag, nonzero = launch nothing; mdone: per-mesh device flags,
 // nonzero = leave that mesh's rows of Y alone (both may be null)
 void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip, const int *mdone)
 {
     VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
-    ensure_batch(b, R);
+    ensure_batch(b, R, st);
     if (b.precision == VFD_BF16) batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
     else batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
 }

@@ -507,6 +507,16 @@ vfd_status vfd_batch_solve(vfd_batch_t h, const double *const *F, double *const 
     VFD_API_END
 }
 
+vfd_status vfd_batch_tuning(vfd_batch_t h, int *chosen, float *us, int n, int *ncand)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && chosen && (us || n == 0), VFD_EINVAL, "null argument");
+    const int c = batch_tuning(*h->b, chosen, us, n);
+    if (ncand) *ncand = c;
+    return VFD_OK;
+    VFD_API_END
+}
+
 void vfd_batch_free(vfd_batch_t h)
 {
     if (!h) return;

@@ -204,6 +204,7 @@ struct OpData {
     DBuf<double> S64;                  // nfar * k * k
     DBuf<double> D64;                  // near entries
     DBuf<float> S32, D32, Ul32;        // FP32 copies (VFD_FP32)
+    DBuf<float> D32t;                  // D32 rounded to TF32 (batched tensor-core path, built on first use)
     DBuf<unsigned short> S16, D16, Ul16;   // BF16 copies (VFD_BF16)
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
     // the batch of one used by the batched (multi-RHS) low-precision apply / solve
@@ -243,10 +244,13 @@ struct BatchData {
     std::vector<int64_t> xoff;          // first row of each mesh (nmesh + 1)
     int R = 0;                          // columns the workspaces below are built for (0: not built)
     DBuf<unsigned char> desc;           // nmesh descriptors (MrMesh)
-    DBuf<int> leaf_items, sum_items, node_items, near_items;   // (mesh, index) pairs
+    DBuf<int> leaf_items, sum_items, node_items;   // (mesh, index) pairs
+    DBuf<unsigned char> near_items;                // NearItem records
     int n_leaf_items = 0, n_sum_items = 0, n_node_items = 0, n_near_items = 0;
     DBuf<long long> row_off;            // xoff on the device
     int max_panel_w = 0, max_k = 0, max_nlev = 0, max_leaf = 0;
+    int near_cfg = -1;                  // tile configuration of the near-panel kernel (timed on first use)
+    float near_cfg_us[16] = {0};        // the timings of the candidates (0: not run)
     bool any_far = false;
     DBuf<float> part, xhat, yhat, y2;   // far-field workspaces (all meshes), second near partial
     DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
@@ -297,6 +301,7 @@ void release_graphs(OpData &op);
 void release_streams(OpData &op);
 void release_bgraph(BatchData &b);
 BatchData *op_batch(OpData &op);   // the op's batch of one (created on first use)
+int batch_tuning(const BatchData &b, int *chosen, float *us, int n);
 void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
                  const int *mdone);
 void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,

@@ -47,6 +47,8 @@ def test_batch_apply_matches_single(prec):
     Xs = [torch.randn(64, c[1].n_dof, dtype=torch.float64, device="cuda", generator=g) for c in cases]
     Ys = [torch.empty_like(x) for x in Xs]
     vfd.vfd_batch_apply(batch, Xs, Ys)
+    chosen, us = vfd.vfd_batch_tuning(batch)
+    assert chosen[0] > 0 and chosen[2] >= 1 and max(us) > 0   # a near-panel configuration was timed and picked
     for c, x, y in zip(cases, Xs, Ys):
         ref = torch.empty_like(x)
         vfd.vfd_apply(c[5], x, ref)
