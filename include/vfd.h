@@ -279,10 +279,11 @@ vfd_status vfd_batch_solve(vfd_batch_t batch, const double *const *F, double *co
                            int64_t nrhs, double rtol, int max_it, int *iters, double *relres, void *stream);
 
 /* The tile configuration the batch picked for its near-panel kernel by timing
- * every candidate once on its first apply (zero inputs): chosen[0..2] = panel
- * columns per pipeline stage, pipeline depth, CTAs per panel (all 0 before the
- * first apply); us[i] = candidate i's time in microseconds (0 = not run or
- * does not fit), n entries at most; *ncand = the number of candidates. */
+ * every candidate once on its first apply (zero inputs): chosen[0..4] = panel
+ * columns per pipeline stage, pipeline depth, CTAs per panel, warps per CTA,
+ * accumulator register sets (all 0 before the first apply); us[i] =
+ * candidate i's time in microseconds (0 = not run or does not fit), n entries
+ * at most; *ncand = the number of candidates. */
 vfd_status vfd_batch_tuning(vfd_batch_t batch, int *chosen, float *us, int n, int *ncand);
 
 void vfd_batch_free(vfd_batch_t batch);

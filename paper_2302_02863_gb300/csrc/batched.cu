@@ -120,7 +120,6 @@ __device__ __forceinline__ float from_f<float>(float v) { return __uint_as_float
 // summed by the CSR kernel.  The stage width NK, the depth NSTAGE and the
 // split are picked per batch by timing the candidates (near_configs).
 // ---------------------------------------------------------------------------
-constexpr int NEAR_THREADS = 256;
 constexpr int KSPLIT_MAX = 4;
 
 template <class T, int NK>
@@ -161,12 +160,16 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return r;
 }
 
-template <class T, int NK, int NSTAGE>
-__global__ void __launch_bounds__(NEAR_THREADS)
+// WARPS = 8: warp tile 16 rows x 32 RHS; WARPS = 4: 32 rows x 32 RHS (two m16
+// tiles share each B fragment).  NACC = 2: even and odd k-steps accumulate
+// into separate registers (twice the independent mma chains), summed at the end.
+template <class T, int NK, int NSTAGE, int WARPS, int NACC>
+__global__ void __launch_bounds__(WARPS * 32)
 k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
           float *__restrict__ Y2all, size_t pstride, const int *skip, const int *mdone)
 {
     using TT = NearTile<T, NK>;
+    constexpr int NEAR_THREADS = WARPS * 32, MT = 8 / WARPS, RW = 4 / MT;   // m16 tiles per warp, warps per row band
     extern __shared__ __align__(16) unsigned char smem[];
     if (skip && *skip) return;
     const NearItem it = items[blockIdx.x];
@@ -209,11 +212,13 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
         cp_async_commit();
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-    const int r0 = (warp & 3) * 16, n0 = (warp >> 2) * 32;
+    const int r0 = (warp % RW) * 16 * MT, n0 = (warp / RW) * 32;
     const bool active = r0 < na;
-    float acc[4][4];
-    for (int j = 0; j < 4; ++j)
-        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+    float acc[NACC][MT][4][4];
+    for (int h = 0; h < NACC; ++h)
+        for (int mt = 0; mt < MT; ++mt)
+            for (int j = 0; j < 4; ++j)
+                for (int q = 0; q < 4; ++q) acc[h][mt][j][q] = 0.f;
     for (int kt = 0; kt < nk; ++kt) {
         cp_async_wait<NSTAGE - 2>();
         __syncthreads();   // stage kt landed for every thread; stage kt-1 fully consumed
@@ -225,11 +230,12 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
         constexpr int KS = MmaTraits<T>::KS;
 #pragma unroll
         for (int ks = 0; ks < NK; ks += KS) {
-            uint32_t a[4];
-            {
+            uint32_t a[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
                 // lanes 8m..8m+7 address the rows of 8x16-byte matrix m: rows +8 for m odd, columns +16 bytes for m >= 2
                 const int m = lane >> 3, rr = lane & 7;
-                ldmatrix_x4(a, As + (r0 + rr + (m & 1) * 8) * TT::LDA + ks + (m >> 1) * (16 / (int)sizeof(T)));
+                ldmatrix_x4(a[mt], As + (r0 + 16 * mt + rr + (m & 1) * 8) * TT::LDA + ks + (m >> 1) * (16 / (int)sizeof(T)));
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -244,19 +250,26 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
                     bb[0] = f2tf32(B0[0]);
                     bb[1] = f2tf32(B0[4 * TT::LDB]);
                 }
-                MmaTraits<T>::mma(acc[j], a, bb);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+                    if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS) % NACC][mt][j], a[mt], bb);
             }
         }
     }
     cp_async_wait<0>();
     if (!active) return;
+    if constexpr (NACC == 2)
+        for (int mt = 0; mt < MT; ++mt)
+            for (int j = 0; j < 4; ++j)
+                for (int q = 0; q < 4; ++q) acc[0][mt][j][q] += acc[1][mt][j][q];
     float *Yo = blockIdx.z == 0 ? Y : Y2 + (size_t)(blockIdx.z - 1) * pstride;
-    for (int j = 0; j < 4; ++j) {
-        const int col = rt + n0 + j * 8 + 2 * t4;
-        const int ra = r0 + g, rb = r0 + g + 8;
-        if (ra < na) *(float2 *)(Yo + (size_t)(b0 + ra) * R + col) = make_float2(acc[j][0], acc[j][1]);
-        if (rb < na) *(float2 *)(Yo + (size_t)(b0 + rb) * R + col) = make_float2(acc[j][2], acc[j][3]);
-    }
+    for (int mt = 0; mt < MT; ++mt)
+        for (int j = 0; j < 4; ++j) {
+            const int col = rt + n0 + j * 8 + 2 * t4;
+            const int ra = r0 + 16 * mt + g, rb = ra + 8;
+            if (ra < na) *(float2 *)(Yo + (size_t)(b0 + ra) * R + col) = make_float2(acc[0][mt][j][0], acc[0][mt][j][1]);
+            if (rb < na) *(float2 *)(Yo + (size_t)(b0 + rb) * R + col) = make_float2(acc[0][mt][j][2], acc[0][mt][j][3]);
+        }
 }
 
 template <class T, int NK, int NSTAGE>
@@ -267,20 +280,23 @@ static size_t near_smem_bytes(int max_panel_w)
 
 // candidate tile configurations of the near-panel kernel
 struct NearCfg {
-    int nk, nstage, ksplit;
+    int nk, nstage, ksplit, warps, nacc;
 };
-static const NearCfg kNearCfgs[] = {{32, 3, 2}, {32, 3, 3}, {16, 4, 2}, {16, 4, 3}, {64, 2, 2}, {32, 4, 2}, {32, 3, 4}};
+static const NearCfg kNearCfgs[] = {{32, 3, 2, 8, 1}, {32, 3, 3, 8, 1}, {16, 4, 3, 8, 1}, {64, 2, 2, 8, 1},
+                                    {32, 3, 3, 4, 1}, {16, 4, 3, 4, 1}, {32, 3, 2, 8, 2}, {32, 3, 3, 8, 2},
+                                    {16, 4, 3, 8, 2}, {32, 3, 3, 4, 2}, {16, 4, 3, 4, 2}, {64, 2, 2, 8, 2}};
 constexpr int kNearCfgCount = (int)(sizeof(kNearCfgs) / sizeof(kNearCfgs[0]));
 
-template <class T, int NK, int NS>
+template <class T, int NK, int NS, int WARPS, int NACC>
 static bool launch_near_cfg(int ksplit, int n_items, int max_panel_w, const NearItem *items, int R, const float *X,
                             float *Y, float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone)
 {
     const size_t shm = near_smem_bytes<T, NK, NS>(max_panel_w);
     if (shm > 227 * 1024) return false;
-    VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T, NK, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T, NK, NS, WARPS, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)shm));
     dim3 g(n_items, R / RT, ksplit);
-    k_mr_near<T, NK, NS><<<g, NEAR_THREADS, shm, st>>>(items, R, X, Y, Y2, pstride, skip, mdone);
+    k_mr_near<T, NK, NS, WARPS, NACC><<<g, WARPS * 32, shm, st>>>(items, R, X, Y, Y2, pstride, skip, mdone);
     return true;
 }
 
@@ -290,14 +306,20 @@ static bool launch_near(int c, int n_items, int max_panel_w, const NearItem *ite
                         float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone)
 {
     const NearCfg &f = kNearCfgs[c];
-#define VFD_NEAR_CASE(NKV, NSV)                                                                                  \
-    if (f.nk == NKV && f.nstage == NSV)                                                                          \
-        return launch_near_cfg<T, NKV, NSV>(f.ksplit, n_items, max_panel_w, items, R, X, Y, Y2, pstride, st, skip, \
-                                            mdone);
-    VFD_NEAR_CASE(32, 3)
-    VFD_NEAR_CASE(16, 4)
-    VFD_NEAR_CASE(64, 2)
-    VFD_NEAR_CASE(32, 4)
+#define VFD_NEAR_CASE(NKV, NSV, WV, AV)                                                                          \
+    if (f.nk == NKV && f.nstage == NSV && f.warps == WV && f.nacc == AV)                                         \
+        return launch_near_cfg<T, NKV, NSV, WV, AV>(f.ksplit, n_items, max_panel_w, items, R, X, Y, Y2, pstride,   \
+                                                    st, skip, mdone);
+    VFD_NEAR_CASE(32, 3, 8, 1)
+    VFD_NEAR_CASE(16, 4, 8, 1)
+    VFD_NEAR_CASE(64, 2, 8, 1)
+    VFD_NEAR_CASE(32, 3, 4, 1)
+    VFD_NEAR_CASE(16, 4, 4, 1)
+    VFD_NEAR_CASE(32, 3, 8, 2)
+    VFD_NEAR_CASE(16, 4, 8, 2)
+    VFD_NEAR_CASE(64, 2, 8, 2)
+    VFD_NEAR_CASE(32, 3, 4, 2)
+    VFD_NEAR_CASE(16, 4, 4, 2)
 #undef VFD_NEAR_CASE
     return false;
 }
@@ -977,7 +999,8 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
     VFD_CUDA(cudaGetLastError());
 }
 
-// the near-panel tuning of a batch: chosen (stage width, depth, split) and the candidates' times
+// the near-panel tuning of a batch: chosen (stage width, depth, split, warps, accumulator sets)
+// and the candidates' times
 int batch_tuning(const BatchData &b, int *chosen, float *us, int n)
 {
     if (chosen) {
@@ -985,6 +1008,8 @@ int batch_tuning(const BatchData &b, int *chosen, float *us, int n)
         chosen[0] = b.near_cfg < 0 ? 0 : f.nk;
         chosen[1] = b.near_cfg < 0 ? 0 : f.nstage;
         chosen[2] = b.near_cfg < 0 ? 0 : f.ksplit;
+        chosen[3] = b.near_cfg < 0 ? 0 : f.warps;
+        chosen[4] = b.near_cfg < 0 ? 0 : f.nacc;
     }
     for (int i = 0; i < n && i < kNearCfgCount; ++i) us[i] = b.near_cfg_us[i];
     return kNearCfgCount;

@@ -340,8 +340,9 @@ def vfd_batch_solve(batch, Fs, Us, rtol=1e-8, max_it=100000, stream=None, raise_
 
 
 def vfd_batch_tuning(batch):
-    """(chosen (stage columns, depth, split), candidate times in us) of the batch's near-panel kernel."""
-    ch = (C.c_int * 3)()
+    """(chosen (stage columns, depth, split, warps, accumulator sets), candidate times in us) of the
+    batch's near-panel kernel."""
+    ch = (C.c_int * 5)()
     us = (C.c_float * 16)()
     nc = C.c_int()
     _check(load().vfd_batch_tuning(batch.handle, ch, us, 16, C.byref(nc)))
