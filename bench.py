@@ -75,6 +75,20 @@ def _dist():
     return rank, world, local
 
 
+def replica_value(units, seconds, dist=None, device="cuda"):
+    """Whole-job throughput of independent replicas (one per rank): the units
+    all ranks processed divided by the slowest rank's time.  Returns (value,
+    max seconds)."""
+    if dist is None:
+        return units / seconds, seconds
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    s = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(s.item()), float(s.item())
+
+
 # ----------------------------------------------------------------------------
 # clocks during the timed region
 # ----------------------------------------------------------------------------
@@ -241,11 +255,7 @@ def main():
     clk = clocks.stop()
     tot = sum(times)
     n_apply = sum(i + 2 for i in iters)          # CG iterations + initial and final residual
-    if dist:
-        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    value = world * n * n_apply / tot
+    value, tot = replica_value(n * n_apply, tot, dist, "cuda")
 
     # ---- e2e: the same step through the C ABI with HOST buffers (copies timed)
     Fh = F.cpu().numpy().copy()
@@ -414,7 +424,13 @@ def batched_leg(mesh, s, k, prm, torch, vfd, nrhs=64, rtol=1e-8, fp64_cols=8, hb
         ts = e0.elapsed_time(e1) / 1000.0
         err_sol = (torch.linalg.norm(U[:fp64_cols] - U64, dim=1) / torch.linalg.norm(U64, dim=1)).max().item()
         near_bytes = info["near_storage"] * wbytes + n * nrhs * 4 * 2 + info["nnz"] * 8
+        bt = vfd.vfd_batch_create([op])
+        vfd.vfd_batch_apply(bt, [X], [Y])
+        chosen, _ = vfd.vfd_batch_tuning(bt)
+        del bt
         out[name] = {"apply_us": ta * 1e6, "apply_dof_rhs_per_s": n * nrhs / ta,
+                     "near_kernel_tuned": {"stage_cols": chosen[0], "stages": chosen[1], "split": chosen[2],
+                                           "warps": chosen[3], "acc_sets": chosen[4]},
                      "apply_rel_err_vs_fp64": err_apply, "solve_ms": ts * 1000, "status": int(st),
                      "inner_iters": int(it[0]), "relres_max": float(rel.max()),
                      "solution_rel_err_vs_fp64_cg": err_sol,
@@ -485,7 +501,10 @@ def batch24_leg(torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
         e1.record()
         torch.cuda.synchronize()
         tseq = e0.elapsed_time(e1) / 1000.0
+        chosen, _ = vfd.vfd_batch_tuning(batch)
         out[name] = {"assemble_s": t_asm, "apply_ms": ta * 1000, "apply_dof_rhs_per_s": ntot * nrhs / ta,
+                     "near_kernel_tuned": {"stage_cols": chosen[0], "stages": chosen[1], "split": chosen[2],
+                                           "warps": chosen[3], "acc_sets": chosen[4]},
                      "solve_s": ts, "status": int(st), "inner_iters_max": int(it.max()),
                      "relres_max": float(rel.max()), "solved_dof_rhs_per_s": ntot * nrhs / ts,
                      "sequential_per_mesh_solves_s": tseq}
