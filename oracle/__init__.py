@@ -67,6 +67,9 @@ def lib():
         L.oracle_cg.restype = C.c_int
         L.oracle_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, ip, up, dp, dp, dp, C.c_int, dp, dp, dp, dp]
         L.oracle_grad.restype = C.c_int
+        L.oracle_apply_rows.argtypes = [C.c_int, C.c_int, C.c_int, dp, ip, up, dp, dp, dp, dp, dp, dp, C.c_int,
+                                        ip, dp]
+        L.oracle_apply_rows.restype = C.c_int
         _lib = L
     return _lib
 
@@ -147,6 +150,26 @@ def assemble(mesh, s, logk, s_bar=0.9, n_sing=3, tail=0, R=1.1, want_full=False)
     if n != N:
         raise RuntimeError("oracle_assemble failed")
     return Assembled(B=B, K=K, M=Mw, rho=rho, Afull=Af, dof=dof, N=N, seconds=t1 - t0)
+
+
+def apply_rows(mesh, s, logk, x, rows, s_bar=0.9, n_sing=3, tail=0, R=1.1):
+    """(A x)_i for the DoFs i in rows, A = B + K + M of the route-2 assembly
+    without any approximation, one row at a time (O(|supp| |Q|) each): for
+    sampled checks at sizes where the dense matrix does not fit."""
+    X = np.ascontiguousarray(mesh.coords, dtype=np.float64)
+    T = np.ascontiguousarray(mesh.cells, dtype=np.int32)
+    inn = np.ascontiguousarray(mesh.cell_is_interior, dtype=np.uint8)
+    sd, sn = field_desc(s)
+    kd, kn = field_desc(logk)
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    rr = np.ascontiguousarray(rows, dtype=np.int32)
+    y = np.zeros(len(rr))
+    params = np.array([s_bar, n_sing, tail, R], dtype=np.float64)
+    n = lib().oracle_apply_rows(mesh.d, mesh.n_vert, mesh.n_cell, _dp(X), _ip(T), _up(inn), _dp(sd), _dp(sn),
+                                _dp(kd), _dp(kn), _dp(params), _dp(xv), len(rr), _ip(rr), _dp(y))
+    if n < 0 or n != len(xv):
+        raise ValueError("oracle_apply_rows: bad input")
+    return y
 
 
 def grad(mesh, s_nodal, logk_nodal, U, Lam, s_bar=0.9, n_sing=3):

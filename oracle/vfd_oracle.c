@@ -1088,6 +1088,120 @@ int oracle_grad(int d, int M, int C, const double *X, const int *T, const unsign
     return N;
 }
 
+/* ------------------------------------------------------------------------ */
+/* single rows of A x (route 2, no approximation), for sampled parity checks  */
+/* ------------------------------------------------------------------------ */
+/* y[r] = (A x)_{rows[r]} with A = B + K + M exactly as oracle_assemble forms
+ * them (Sec. 3 split; B by the Sec. 4 rules over the touching pairs whose
+ * local DoFs contain the row's vertex; K and M through the point sums of
+ * e:k and e:tgt-sum over all separated points; the tail when tail_mode = 1).
+ * Cost O(|supp| x |Q|) per row.  x: N entries (DoF order of oracle_dofs);
+ * rows: DoF indices.  Returns N, or -1 on bad input. */
+int oracle_apply_rows(int d, int M, int C, const double *X, const int *T, const unsigned char *in,
+                      const double *sdesc, const double *snodal, const double *kdesc, const double *knodal,
+                      const double *params, const double *x, int nrows, const int *rows, double *y)
+{
+    omesh m = {d, M, C, X, T, in};
+    ofield fs = {sdesc, snodal}, fk = {kdesc, knodal};
+    double sbar = params[0];
+    int ns = (int)params[1], tail = (int)params[2];
+    double R = params[3];
+    int nv = d + 1;
+    if (ns < 1 || ns > 64) return -1;
+    int *dof = malloc(sizeof(int) * M);
+    int N = oracle_dofs(d, M, C, T, in, dof);
+    int *vert = malloc(sizeof(int) * (N > 0 ? N : 1));
+    for (int v = 0; v < M; ++v) if (dof[v] >= 0) vert[dof[v]] = v;
+    double gx[64], gw[64];
+    oracle_gauss01(ns, gx, gw);
+    oquad Q;
+    build_quad(&m, &fs, &fk, &Q);
+    int nq = Q.n / C;
+    double *xq = malloc(sizeof(double) * Q.n);
+    for (int iq = 0; iq < Q.n; ++iq) {
+        const int *t = T + Q.cell[iq] * nv;
+        double v = 0.0;
+        for (int a = 0; a < nv; ++a) if (dof[t[a]] >= 0) v += Q.bary[iq * 3 + a] * x[dof[t[a]]];
+        xq[iq] = v;
+    }
+    int *vdeg = calloc(M + 1, sizeof(int));
+    for (int c = 0; c < C; ++c) for (int a = 0; a < nv; ++a) vdeg[T[c * nv + a] + 1]++;
+    for (int v = 0; v < M; ++v) vdeg[v + 1] += vdeg[v];
+    int *vcell = malloc(sizeof(int) * vdeg[M]);
+    int *fill = calloc(M, sizeof(int));
+    for (int c = 0; c < C; ++c) for (int a = 0; a < nv; ++a) { int v = T[c * nv + a]; vcell[vdeg[v] + fill[v]++] = c; }
+    free(fill);
+#pragma omp parallel
+    {
+        char *touch = calloc(C, 1);
+        int *pairs = malloc(sizeof(int) * 2 * C);
+#pragma omp for schedule(dynamic, 1)
+        for (int r = 0; r < nrows; ++r) {
+            const int vi = vert[rows[r]];
+            double acc = 0.0;
+            /* ---- B: the unordered touching pairs {c, c2} with vi a local DoF ---- */
+            int np = 0;
+            for (int k = vdeg[vi]; k < vdeg[vi + 1]; ++k) {
+                int c = vcell[k];
+                const int *t = T + c * nv;
+                for (int a = 0; a < nv; ++a)
+                    for (int k2 = vdeg[t[a]]; k2 < vdeg[t[a] + 1]; ++k2) {
+                        int c2 = vcell[k2], lo = c < c2 ? c : c2, hi = c < c2 ? c2 : c, dup = 0;
+                        for (int q = 0; q < np && !dup; ++q) dup = pairs[2 * q] == lo && pairs[2 * q + 1] == hi;
+                        if (!dup) { pairs[2 * np] = lo; pairs[2 * np + 1] = hi; ++np; }
+                    }
+            }
+            for (int q = 0; q < np; ++q) {
+                int c = pairs[2 * q], c2 = pairs[2 * q + 1];
+                if (!in[c] && !in[c2]) continue;
+                opair pp; int loc[5]; double L[25];
+                int nl = make_pair(&m, c, c2, &pp, loc);
+                int li = -1;
+                for (int a = 0; a < nl; ++a) if (loc[a] == vi) li = a;
+                if (li < 0) continue;
+                pair_singular(&pp, &fs, &fk, sbar, ns, gx, gw, L);
+                double wgt = (c == c2) ? 1.0 : 2.0, s = 0.0;
+                for (int j = 0; j < nl; ++j) if (dof[loc[j]] >= 0) s += L[li * nl + j] * x[dof[loc[j]]];
+                acc += wgt * s;
+            }
+            /* ---- K and M at the points of the interior cells containing vi ---- */
+            for (int k = vdeg[vi]; k < vdeg[vi + 1]; ++k) {
+                int c = vcell[k];
+                if (!in[c]) continue;
+                const int *t = T + c * nv;
+                int ai = -1;
+                for (int a = 0; a < nv; ++a) if (t[a] == vi) ai = a;
+                for (int a = 0; a < nv; ++a)
+                    for (int k2 = vdeg[t[a]]; k2 < vdeg[t[a] + 1]; ++k2) touch[vcell[k2]] = 1;
+                for (int q = 0; q < nq; ++q) {
+                    int iq = c * nq + q;
+                    double sk = 0.0, rho = 0.0;
+                    for (int c2 = 0; c2 < C; ++c2) {
+                        if (touch[c2]) continue;
+                        for (int q2 = 0; q2 < nq; ++q2) {
+                            int jq = c2 * nq + q2;
+                            double g = kernel_gamma(d, qdist(d, Q.x + iq * d, Q.x + jq * d), Q.s[iq], Q.s[jq],
+                                                    Q.lk[iq], Q.lk[jq]) * Q.w[jq];
+                            rho += g;
+                            if (in[c2]) sk += g * xq[jq];
+                        }
+                    }
+                    if (tail) rho += oracle_tail(d, Q.x + iq * d, Q.s[iq], exp(Q.lk[iq]), R);
+                    double wpsi = Q.w[iq] * Q.bary[iq * 3 + ai];
+                    acc += -2.0 * wpsi * sk + 2.0 * wpsi * xq[iq] * rho;
+                }
+                for (int a = 0; a < nv; ++a)
+                    for (int k2 = vdeg[t[a]]; k2 < vdeg[t[a] + 1]; ++k2) touch[vcell[k2]] = 0;
+            }
+            y[r] = acc;
+        }
+        free(touch); free(pairs);
+    }
+    free(xq); free(vdeg); free(vcell); free(dof); free(vert);
+    free_quad(&Q);
+    return N;
+}
+
 /* P1 load vector F_i = int f_h psi_i over interior cells (exact P1 mass
  * matrix times nodal f), DoF order of oracle_dofs. */
 int oracle_load(int d, int M, int C, const double *X, const int *T, const unsigned char *in,

@@ -261,6 +261,17 @@ k_far_expand(FarView F, int fl, const int *__restrict__ leaf_of, const T *__rest
     if (lane == 0) Y[(size_t)r * ld + i] += v;
 }
 
+// the row kernel stages a whole panel row of x in shared memory: allow more
+// than the default 48 KB (panels of exact-mode operators are N wide)
+template <class T, class A>
+static void row_kernel_smem(size_t shm)
+{
+    VFD_REQUIRE(shm <= 227 * 1024, VFD_EUNSUPPORTED,
+                "apply: a near panel is wider than shared memory holds (use a low-rank operator, lambda > 0)");
+    if (shm > 48 * 1024)
+        VFD_CUDA(cudaFuncSetAttribute(k_near_csr<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+}
+
 // ---------------------------------------------------------------------------
 template <class T, class A>
 static void apply_impl(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
@@ -298,6 +309,7 @@ static void apply_impl(const MeshData &m, OpData &op, int parts, const double *X
     const int NR = 16;
     dim3 go(m.kt.nleaf, cdiv(m.max_leaf_size, NR), nrhs);
     size_t shm = near ? (size_t)m.max_panel_w * sizeof(T) : 0;
+    row_kernel_smem<T, A>(shm);
     k_near_csr<T, A><<<go, 128, shm, st>>>(fl, NR, m.kt_begin.p, m.kt_end.p, m.near_ptr.p, m.near_col.p, m.near_off.p,
                                            m.panel_w.p, m.panel_off.p, m.gcol.p, m.gcol_off.p, D, near ? 1 : 0,
                                            m.rowptr.p, m.colidx.p, val, Fn, Ul, yhat, hs, X, ld, Y, skip);
@@ -433,6 +445,7 @@ void apply_one_stream(const MeshData &m, const OpData &op, const double *X, doub
     const int NR = 16;
     dim3 go(m.kt.nleaf, cdiv(m.max_leaf_size, NR), nrhs);
     size_t shm = near ? (size_t)m.max_panel_w * sizeof(T) : 0;
+    row_kernel_smem<T, A>(shm);
     k_near_csr<T, A><<<go, 128, shm, st>>>(fl, NR, m.kt_begin.p, m.kt_end.p, m.near_ptr.p, m.near_col.p, m.near_off.p,
                                            m.panel_w.p, m.panel_off.p, m.gcol.p, m.gcol_off.p, D, near ? 1 : 0,
                                            m.rowptr.p, m.colidx.p, op.valBM.p, Fn, Ul, yhat, hs, X, ld, Y, nullptr);

@@ -1,0 +1,130 @@
+"""Parity at the benchmark's full size: the 2D disk of 27,361 DoFs (34,027
+vertices), the benchmark's fields and mesh options (leaf 64, Chebyshev p = 4,
+lambda = 0.75, FP64), in the launch configuration bench.py times.
+
+* sampled rows of A x against the oracle's exact rows (oracle.apply_rows,
+  no approximation): exact-mode operator (every block near, direct density)
+  to 1e-11, and the H^2 operator of the benchmark to the rank-16
+  interpolation tolerance;
+* the FP64 CG solution's true residual, and the 64-RHS TF32 / BF16
+  refinement's residuals through the FP64 operator;
+* the adjoint gradient's log-kappa shift identity sum_k g_k = -Lam^T A U
+  (holds at any size) on the exact-mode operator with P1 fields.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2302_02863_gb300 import vfd  # noqa: E402
+
+NROWS = 24
+
+
+@pytest.fixture(scope="module")
+def disk():
+    m, s, k, prm = synth.workload("disk33k")
+    dof_o, N = oracle.dofs(m)
+    return m, s, k, prm, dof_o, N
+
+
+def _mesh(m, prm, lam):
+    return vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"], lam=lam,
+                        rho_lambda=lam, tail_mode=prm["tail"], tail_R=prm["R"])
+
+
+def _sampled_rows(disk, lam, tol):
+    m, s, k, prm, dof_o, N = disk
+    mesh = _mesh(m, prm, lam)
+    dof_g, n = vfd.vfd_mesh_dofs(mesh)
+    assert n == N
+    op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"])
+    rng = np.random.default_rng(2024)
+    xo = rng.standard_normal(N)
+    sel = dof_g >= 0
+    xg = np.zeros(n)
+    xg[dof_g[sel]] = xo[dof_o[sel]]
+    X = torch.tensor(xg, device="cuda")
+    Y = torch.empty_like(X)
+    vfd.vfd_apply(op, X, Y)
+    torch.cuda.synchronize()
+    yg = Y.cpu().numpy()
+    verts = np.nonzero(sel)[0]
+    pick = rng.choice(len(verts), NROWS, replace=False)
+    rows_o = dof_o[verts[pick]]
+    y_or = oracle.apply_rows(m, s, k, xo, rows_o, s_bar=prm["s_bar"], n_sing=3, tail=prm["tail"], R=prm["R"])
+    y_gp = yg[dof_g[verts[pick]]]
+    err = np.abs(y_gp - y_or).max() / np.abs(y_or).max()
+    print(f"sampled rows, lambda {lam}: max error / max |y| = {err:.3e}")
+    assert err < tol, err
+    return err
+
+
+def test_fullsize_exact_mode_sampled_rows(disk):
+    _sampled_rows(disk, 0.0, 1e-11)
+
+
+def test_fullsize_h2_sampled_rows(disk):
+    # the benchmark operator: rank-16 Chebyshev interpolation of the far field
+    _sampled_rows(disk, 0.75, 5e-4)
+
+
+def test_fullsize_solves(disk):
+    m, s, k, prm, dof_o, N = disk
+    mesh = _mesh(m, prm, 0.75)
+    op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"])
+    F = torch.zeros(mesh.n_dof, dtype=torch.float64, device="cuda")
+    vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device="cuda"), F)
+    U = torch.zeros_like(F)
+    st, it, rel = vfd.vfd_solve(op, F, U, rtol=1e-10, max_it=100000)
+    assert st == vfd.VFD_OK
+    AU = torch.empty_like(U)
+    vfd.vfd_apply(op, U, AU)
+    torch.cuda.synchronize()
+    assert (torch.linalg.norm(F - AU) / torch.linalg.norm(F)).item() <= 1.01e-10
+    g = torch.Generator(device="cuda").manual_seed(77)
+    Fb = torch.randn(64, mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
+    for prec in (vfd.VFD_FP32, vfd.VFD_BF16):
+        opl = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec)
+        Ub = torch.zeros_like(Fb)
+        st, it, rel = vfd.vfd_solve(opl, Fb, Ub, rtol=1e-8, max_it=100000)
+        assert st == vfd.VFD_OK
+        AUb = torch.empty_like(Ub)
+        vfd.vfd_apply(op, Ub, AUb)
+        torch.cuda.synchronize()
+        r = (torch.linalg.norm(Fb - AUb, dim=1) / torch.linalg.norm(Fb, dim=1)).max().item()
+        assert r <= 1.01e-8, (prec, r)
+
+
+def _fourier_values(f, x):
+    """Vertex values of a synthetic Fourier field descriptor (input generation)."""
+    v = np.full(len(x), float(f.c0))
+    for row in np.asarray(f.fourier, dtype=float).reshape(-1, 5):
+        v += row[3] * np.cos(math.pi * (x @ row[:2]) + row[4])
+    return v
+
+
+def test_fullsize_gradient_shift_identity(disk):
+    m, s, k, prm, dof_o, N = disk
+    x = m.coords
+    s_n = 0.25 + 0.5 * (0.5 + 0.5 * np.sin(2 * math.pi * x[:, 0]) * np.cos(2 * math.pi * x[:, 1]))
+    lk_n = _fourier_values(k, x)
+    mesh = _mesh(m, prm, 0.0)
+    op = vfd.vfd_assemble(mesh, synth.nodal_field(s_n), synth.nodal_field(lk_n), prm["s_bar"])
+    g = torch.Generator(device="cuda").manual_seed(5)
+    U = torch.randn(mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
+    L = torch.randn(mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
+    gs = torch.empty(m.n_vert, dtype=torch.float64, device="cuda")
+    gk = torch.empty_like(gs)
+    vfd.vfd_grad(op, U, L, gs, gk)
+    AU = torch.empty_like(U)
+    vfd.vfd_apply(op, U, AU)
+    torch.cuda.synchronize()
+    ref = -(L @ AU).item()
+    assert abs(gk.sum().item() - ref) <= 1e-10 * abs(ref)

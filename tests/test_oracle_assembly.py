@@ -195,3 +195,24 @@ def test_closed_form_2d_disk():
     for (n0, e0), (n1, e1) in zip(res, res[1:]):
         rate = math.log(e0 / e1) / math.log(math.sqrt(n1 / n0))
         assert 0.85 < rate < 1.4, res
+
+
+def test_apply_rows_equals_dense_rows():
+    """oracle.apply_rows (one row of A x at a time, for sampled checks at full
+    size) against the pinned dense route-2 assembly: 2D variable fields, and
+    1D with the exterior tail."""
+    m = synth.disk_mesh(6, R=1.1, jitter=0.2, seed=4)
+    s, k = synth.config2_s_field(), synth.random_fourier_field(31, 0.5)
+    A = oracle.assemble(m, s, k, s_bar=0.9, n_sing=3)
+    x = np.random.default_rng(0).standard_normal(A.N)
+    rows = np.arange(0, A.N, 5)
+    y = oracle.apply_rows(m, s, k, x, rows)
+    ref = (A.A @ x)[rows]
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+    m1 = synth.interval_mesh(30, R=1.2)
+    sc, kc = synth.const_field(0.3), synth.const_field(np.log(0.4))
+    A1 = oracle.assemble(m1, sc, kc, s_bar=0.3, n_sing=3, tail=1, R=1.2)
+    x1 = np.random.default_rng(1).standard_normal(A1.N)
+    y1 = oracle.apply_rows(m1, sc, kc, x1, np.arange(A1.N), s_bar=0.3, tail=1, R=1.2)
+    ref1 = A1.A @ x1
+    assert np.abs(y1 - ref1).max() <= 1e-13 * np.abs(ref1).max()
