@@ -430,7 +430,7 @@ def batched_leg(mesh, s, k, prm, torch, vfd, nrhs=64, rtol=1e-8, fp64_cols=8, hb
         del bt
         out[name] = {"apply_us": ta * 1e6, "apply_dof_rhs_per_s": n * nrhs / ta,
                      "near_kernel_tuned": {"stage_cols": chosen[0], "stages": chosen[1], "split": chosen[2],
-                                           "warps": chosen[3], "acc_sets": chosen[4]},
+                                           "warps": chosen[3], "acc_sets": chosen[4], "tcgen05": chosen[5]},
                      "apply_rel_err_vs_fp64": err_apply, "solve_ms": ts * 1000, "status": int(st),
                      "inner_iters": int(it[0]), "relres_max": float(rel.max()),
                      "solution_rel_err_vs_fp64_cg": err_sol,
@@ -504,7 +504,7 @@ def batch24_leg(torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
         chosen, _ = vfd.vfd_batch_tuning(batch)
         out[name] = {"assemble_s": t_asm, "apply_ms": ta * 1000, "apply_dof_rhs_per_s": ntot * nrhs / ta,
                      "near_kernel_tuned": {"stage_cols": chosen[0], "stages": chosen[1], "split": chosen[2],
-                                           "warps": chosen[3], "acc_sets": chosen[4]},
+                                           "warps": chosen[3], "acc_sets": chosen[4], "tcgen05": chosen[5]},
                      "solve_s": ts, "status": int(st), "inner_iters_max": int(it.max()),
                      "relres_max": float(rel.max()), "solved_dof_rhs_per_s": ntot * nrhs / ts,
                      "sequential_per_mesh_solves_s": tseq}

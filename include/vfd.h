@@ -279,12 +279,20 @@ vfd_status vfd_batch_solve(vfd_batch_t batch, const double *const *F, double *co
                            int64_t nrhs, double rtol, int max_it, int *iters, double *relres, void *stream);
 
 /* The tile configuration the batch picked for its near-panel kernel by timing
- * every candidate once on its first apply (zero inputs): chosen[0..4] = panel
+ * every candidate once on its first apply (zero inputs): chosen[0..5] = panel
  * columns per pipeline stage, pipeline depth, CTAs per panel, warps per CTA,
- * accumulator register sets (all 0 before the first apply); us[i] =
- * candidate i's time in microseconds (0 = not run or does not fit), n entries
- * at most; *ncand = the number of candidates. */
+ * accumulator register sets, and 1 for the tcgen05 (tensor-memory) kernel, 0
+ * for the mma.sync kernel (all 0 before the first apply); us[i] = candidate
+ * i's time in microseconds (0 = not run or does not fit), n entries at most;
+ * *ncand = the number of candidates.  VFD_ETIMEOUT from an apply or solve
+ * means a tcgen05 pipeline wait expired (the kernel gave up, outputs invalid). */
 vfd_status vfd_batch_tuning(vfd_batch_t batch, int *chosen, float *us, int n, int *ncand);
+
+/* Pin the near-panel configuration of the batch to candidate cfg (0 <= cfg <
+ * *ncand; a candidate that does not fit in shared memory makes the next apply
+ * fail with VFD_EUNSUPPORTED), or cfg = -1: time the candidates on the next
+ * apply and keep the fastest (the default).  Takes effect on the next apply. */
+vfd_status vfd_batch_set_config(vfd_batch_t batch, int cfg, int *ncand);
 
 void vfd_batch_free(vfd_batch_t batch);
 

@@ -361,6 +361,7 @@ static int run_bcg(BatchData &b, int Rp, float tol, int max_it, cudaStream_t st)
         VFD_CUDA(cudaStreamSynchronize(st));
         if (hf[BF_DONE]) break;
     }
+    batch_check(b, st);
     return hf[BF_IT];
 }
 

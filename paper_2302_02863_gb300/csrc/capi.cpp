@@ -517,6 +517,16 @@ vfd_status vfd_batch_tuning(vfd_batch_t h, int *chosen, float *us, int n, int *n
     VFD_API_END
 }
 
+vfd_status vfd_batch_set_config(vfd_batch_t h, int cfg, int *ncand)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h, VFD_EINVAL, "null batch");
+    const int n = batch_set_config(*h->b, cfg);
+    if (ncand) *ncand = n;
+    return VFD_OK;
+    VFD_API_END
+}
+
 void vfd_batch_free(vfd_batch_t h)
 {
     if (!h) return;

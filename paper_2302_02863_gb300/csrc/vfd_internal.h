@@ -250,10 +250,13 @@ struct BatchData {
     DBuf<long long> row_off;            // xoff on the device
     int max_panel_w = 0, max_k = 0, max_nlev = 0, max_leaf = 0;
     int near_cfg = -1;                  // tile configuration of the near-panel kernel (timed on first use)
-    float near_cfg_us[16] = {0};        // the timings of the candidates (0: not run)
+    int forced_cfg = -1;                // >= 0: configuration pinned by the caller
+    float near_cfg_us[32] = {0};        // the timings of the candidates (0: not run)
     bool any_far = false;
     DBuf<float> part, xhat, yhat, y2;   // far-field workspaces (all meshes), second near partial
     DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
+    DBuf<unsigned char> xc;             // x in the tcgen05 MMA element type (BF16 / TF32-rounded FP32)
+    DBuf<int> tc_err;                   // set by the tcgen05 kernel when a pipeline wait expires
     // batched refinement solve
     DBuf<float> x, r, p, q, b, red, sc;
     DBuf<int> flag, red_items, red_mesh;
@@ -302,6 +305,8 @@ void release_streams(OpData &op);
 void release_bgraph(BatchData &b);
 BatchData *op_batch(OpData &op);   // the op's batch of one (created on first use)
 int batch_tuning(const BatchData &b, int *chosen, float *us, int n);
+void batch_check(BatchData &b, cudaStream_t st);
+int batch_set_config(BatchData &b, int cfg);
 void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
                  const int *mdone);
 void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,

@@ -34,7 +34,7 @@ INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "no
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
            "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_grad", "vfd_load", "vfd_op_rho", "vfd_op_timings",
            "vfd_selftest_math", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve", "vfd_batch_tuning",
-           "vfd_batch_free",
+           "vfd_batch_set_config", "vfd_batch_free",
            "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
 
 
@@ -94,6 +94,7 @@ def load():
     L.vfd_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int64), C.c_int64, C.c_double,
                                   C.c_int, C.POINTER(C.c_int), dp, vp]
     L.vfd_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
+    L.vfd_batch_set_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     L.vfd_batch_free.argtypes = [vp]
     L.vfd_batch_free.restype = None
     L.vfd_free_op.argtypes = [vp]
@@ -103,7 +104,7 @@ def load():
     L.vfd_last_error.restype = C.c_char_p
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
               "vfd_apply_noalloc", "vfd_grad", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve",
-              "vfd_batch_tuning",
+              "vfd_batch_tuning", "vfd_batch_set_config",
               "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -340,13 +341,20 @@ def vfd_batch_solve(batch, Fs, Us, rtol=1e-8, max_it=100000, stream=None, raise_
 
 
 def vfd_batch_tuning(batch):
-    """(chosen (stage columns, depth, split, warps, accumulator sets), candidate times in us) of the
-    batch's near-panel kernel."""
-    ch = (C.c_int * 5)()
-    us = (C.c_float * 16)()
+    """(chosen (stage columns, depth, split, warps, accumulator sets, tcgen05), candidate times in us) of
+    the batch's near-panel kernel."""
+    ch = (C.c_int * 6)()
+    us = (C.c_float * 32)()
     nc = C.c_int()
-    _check(load().vfd_batch_tuning(batch.handle, ch, us, 16, C.byref(nc)))
+    _check(load().vfd_batch_tuning(batch.handle, ch, us, 32, C.byref(nc)))
     return tuple(ch), list(us)[:nc.value]
+
+
+def vfd_batch_set_config(batch, cfg):
+    """Pin the near-panel candidate cfg (or -1: time them all); returns the number of candidates."""
+    n = C.c_int()
+    _check(load().vfd_batch_set_config(batch.handle, int(cfg), C.byref(n)))
+    return n.value
 
 
 def vfd_load(mesh, f_nodal, F, stream=None):

@@ -73,3 +73,41 @@ def test_batched_refinement_solve(disk, prec):
     Uo = np.linalg.solve(L.T, np.linalg.solve(L, Fo.T)).T
     err = np.linalg.norm(Ug[:, gi] - Uo[:, oi], axis=1) / np.linalg.norm(Uo, axis=1)
     assert err.max() < 1e-8, err.max()
+
+
+@pytest.mark.parametrize("prec,tol", [(vfd.VFD_FP32, 2e-3), (vfd.VFD_BF16, 2e-2)])
+def test_every_near_configuration(disk, prec, tol):
+    """Each candidate of the near-panel tuner (mma.sync stage shapes, splits,
+    warp tilings, and for BF16 the tcgen05 / tensor-memory kernels), pinned in
+    turn, against the FP64 operator; all candidates agree with each other to
+    FP32 rounding."""
+    m, s, k = disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=32, lam=0.75, rho_lambda=0.75)
+    op64 = vfd.vfd_assemble(mesh, s, k, 0.9)
+    opl = vfd.vfd_assemble(mesh, s, k, 0.9, precision=prec)
+    X = torch.randn(64, mesh.n_dof, dtype=torch.float64, device="cuda")
+    Y64 = torch.empty_like(X)
+    vfd.vfd_apply(op64, X, Y64)
+    batch = vfd.vfd_batch_create([opl])
+    ncand = vfd.vfd_batch_set_config(batch, 0)
+    ref = None
+    seen_tc = False
+    for c in range(ncand):
+        vfd.vfd_batch_set_config(batch, c)
+        Y = torch.empty_like(X)
+        try:
+            vfd.vfd_batch_apply(batch, [X], [Y])
+        except vfd.VfdError as e:   # candidates not offered for this precision
+            assert e.status == vfd.VFD_EUNSUPPORTED
+            continue
+        torch.cuda.synchronize()
+        chosen, _ = vfd.vfd_batch_tuning(batch)
+        seen_tc |= chosen[5] == 1
+        err = (torch.linalg.norm(Y - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)).max().item()
+        assert err < tol, (c, chosen, err)
+        if ref is None:
+            ref = Y
+        else:
+            d = (torch.linalg.norm(Y - ref) / torch.linalg.norm(ref)).item()
+            assert d < 1e-5, (c, chosen, d)
+    assert seen_tc == (prec == vfd.VFD_BF16)   # the tcgen05 kernels run with BF16 operands
