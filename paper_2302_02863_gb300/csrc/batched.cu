@@ -1315,6 +1315,72 @@ int batch_tuning(const BatchData &b, int *chosen, float *us, int n)
     return kNearCfgCount;
 }
 
+__global__ void k_fill1(long long n, float *__restrict__ a)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 1.f;
+}
+
+__global__ void k_fill1d(long long n, double *__restrict__ a)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 1.0;
+}
+
+// add c_i = (A_64 1)_i - (A_low 1)_i to the diagonal entry of row i of the FP32 B + M
+__global__ void k_comp_diag(int N, int R, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                            const double *__restrict__ y64, const float *__restrict__ ylow, float *__restrict__ val)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double c = y64[i] - (double)ylow[(size_t)i * R];
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+        if (colidx[e] == i) {
+            val[e] = (float)((double)val[e] + c);
+            break;
+        }
+}
+
+// Diagonal compensation of the low-precision operators, once per operator, on
+// its first batched use: rounding the near panels, bases and coupling
+// matrices to TF32 / BF16 perturbs every entry by up to 2^-11 / 2^-8 of
+// itself, and the perturbation's row sums shift the smallest eigenvalues of
+// the (nearly zero-row-sum) operator by a fraction of the largest -- enough to
+// stall the inner CG on fine meshes.  Adding c = A_64 1 - A_low 1 to the
+// diagonal makes the low-precision operator exact on constant vectors, so the
+// remaining perturbation acts on differences u_j - u_i only and leaves the
+// smooth low modes alone.  The outer FP64 residual is unaffected.
+template <class T>
+static void compensate_diag(BatchData &b, int R, cudaStream_t st)
+{
+    bool need = false;
+    for (const OpData *op : b.ops) need |= !op->comp_done && op->m->N > 0;
+    if (!need) return;
+    const long long n = (long long)b.ntot * R;
+    DBuf<float> ones, y;
+    ones.alloc((size_t)n);
+    y.alloc((size_t)n);
+    k_fill1<<<cdiv(n, 256), 256, 0, st>>>(n, ones.p);
+    VFD_CUDA(cudaGetLastError());
+    batch_apply_impl<T>(b, ones.p, y.p, R, st, nullptr, nullptr);
+    for (int i = 0; i < b.nmesh; ++i) {
+        OpData &op = *b.ops[i];
+        const MeshData &m = *op.m;
+        if (op.comp_done || m.N == 0) continue;
+        DBuf<double> one64, y64;
+        one64.alloc(m.N);
+        y64.alloc(m.N);
+        k_fill1d<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, one64.p);
+        apply_parts_ex(m, op, VFD_PART_ALL, one64.p, y64.p, 1, m.N, false, st, nullptr);
+        k_comp_diag<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, R, m.rowptr.p, m.colidx.p, y64.p,
+                                                                  y.p + (size_t)b.xoff[i] * R, op.valBM32.p);
+        VFD_CUDA(cudaGetLastError());
+        VFD_CUDA(cudaStreamSynchronize(st));
+        op.comp_done = true;
+    }
+    VFD_CUDA(cudaStreamSynchronize(st));
+}
+
 // Y = A_low X for R (multiple of 64) interleaved FP32 columns over all meshes;
 // skip: device flag, nonzero = launch nothing; mdone: per-mesh device flags,
 // nonzero = leave that mesh's rows of Y alone (both may be null)
@@ -1322,8 +1388,13 @@ void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st,
 {
     VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
     ensure_batch(b, R, st);
-    if (b.precision == VFD_BF16) batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
-    else batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
+    if (b.precision == VFD_BF16) {
+        compensate_diag<__nv_bfloat16>(b, R, st);
+        batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
+    } else {
+        compensate_diag<float>(b, R, st);
+        batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
+    }
 }
 
 // column-major FP64 <-> interleaved FP32

@@ -1,13 +1,24 @@
 // Batched mixed-precision solve of A_m U_m = F_m for a batch of operators
 // (meshes) m with R right-hand sides each (the CG of the paper's Sec. 7 run
-// on all columns of all meshes at once): iterative refinement with an FP64
-// residual F - A U from each mesh's FP64 operator, and an inner batched CG on
-// the low-precision operators (K in TF32 or BF16 on the tensor cores, B + M in
-// FP32) in FP32 vectors of interleaved layout [sum N_m][Rp] (Rp = R rounded
-// up to 64).  Scalars per (mesh, column); deterministic segmented reductions
-// (every reduction block works inside one mesh; the last block of a mesh sums
-// that mesh's block partials in a fixed order); a device flag ends a captured
-// chunk of iterations once every column of every mesh has converged.
+// on all columns of all meshes at once): CG on the low-precision operators
+// (K in TF32 or BF16 on the tensor cores, B + M in FP32) in FP32 vectors of
+// interleaved layout [sum N_m][Rp] (Rp = R rounded up to 64), solving for the
+// correction to the FP64 iterate U, with reliable updates per mesh: once every
+// still-iterating column of a mesh has cut its recursive residual by RU_DROP
+// since that mesh's last update (or the mesh's inner iteration has
+// converged), the mesh's correction is added to U in FP64, its true residual
+// F - A U is recomputed with the FP64 operator and replaces the recursive one,
+// and the search direction continues as p = r_true + beta p_old with beta
+// taken from the true residual norm -- the Krylov space is not restarted, so
+// the iteration count stays close to that of FP64 CG.  A column restarts from
+// p = r_true instead (an iterative-refinement step) when its inner iteration
+// had converged, when its true and recursive residuals differ by more than a
+// factor of two, or when its true residual grew since the last update.  Other
+// meshes keep iterating untouched.  Scalars per (mesh, column); deterministic
+// segmented reductions (every reduction block works inside one mesh; the last
+// block of a mesh sums that mesh's block partials in a fixed order); a device
+// flag ends a captured chunk of iterations once every column of every mesh
+// has converged.
 #include <algorithm>
 #include <cmath>
 
@@ -100,8 +111,10 @@ __device__ int seg_reduce(const Seg &S, Elem f, Fin fin)
     return m;
 }
 
+// x = 0, r = p = b; per column the stopping threshold tol2 (on rr, scaled units)
 __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ b, float *__restrict__ x,
-                                               float *__restrict__ r, float *__restrict__ p, float tol, int max_it)
+                                               float *__restrict__ r, float *__restrict__ p,
+                                               const float *__restrict__ tol2, int max_it)
 {
     __shared__ int live;
     if (threadIdx.x == 0) live = 0;
@@ -117,10 +130,10 @@ __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ 
         },
         [&](int m, int c, float s) {
             scal(S, C_RR, m, c) = s;
-            scal(S, C_TOL, m, c) = tol * tol * s;
+            scal(S, C_TOL, m, c) = tol2[m * S.Rp + c];
             scal(S, C_AL, m, c) = 0.f;
             scal(S, C_BE, m, c) = 0.f;
-            if (s > 0.f) atomicAdd(&live, 1);
+            if (s > tol2[m * S.Rp + c]) atomicAdd(&live, 1);
         });
     if (m >= 0) {
         __syncthreads();
@@ -209,6 +222,46 @@ __global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, 
         const int c = (int)(e % Rp);
         p[base + e] = fmaf(scal(S, C_BE, m, c), p[base + e], r[base + e]);
     }
+}
+
+// reliable update of the meshes with upd[m] != 0: the recursive residual is
+// replaced by the (rescaled) true residual b, the accumulated correction x
+// restarts at zero, and the direction becomes p = b + gamma (p - r) per column
+// (p - r = beta_old p_old from the last direction update, gamma converting it
+// to the new scale and to beta from the true residual norm), or p = b where
+// gamma < 0 (restart); rr, the thresholds and the done flags are recomputed.
+// Meshes with upd[m] == 0 are left exactly as they are.
+__global__ void __launch_bounds__(BT) k_b_replace(Seg S, const float *__restrict__ b, float *__restrict__ x,
+                                                  float *__restrict__ r, float *__restrict__ p,
+                                                  const float *__restrict__ gamma, const float *__restrict__ tol2,
+                                                  const int *__restrict__ upd)
+{
+    __shared__ int live;
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    const int m = seg_reduce<false>(
+        S,
+        [&](size_t t, int mm, int c) {
+            if (!upd[mm]) return 0.f;
+            const float v = b[t], g = gamma[mm * S.Rp + c];
+            p[t] = g < 0.f ? v : fmaf(g, p[t] - r[t], v);
+            x[t] = 0.f;
+            r[t] = v;
+            return v * v;
+        },
+        [&](int mm, int c, float s) {
+            if (!upd[mm]) return;
+            scal(S, C_RR, mm, c) = s;
+            scal(S, C_TOL, mm, c) = tol2[mm * S.Rp + c];
+            scal(S, C_AL, mm, c) = 0.f;
+            scal(S, C_BE, mm, c) = 0.f;
+            if (s > tol2[mm * S.Rp + c]) atomicAdd(&live, 1);
+        });
+    if (m >= 0 && upd[m]) {
+        __syncthreads();
+        if (threadIdx.x == 0) S.mdone()[m] = live == 0 ? 1 : 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.flag[BF_DONE] = 0;
 }
 
 // residual scaling between the FP64 column-major and the FP32 interleaved layouts
@@ -323,113 +376,196 @@ static Seg make_seg(BatchData &b, int Rp)
     return S;
 }
 
-// inner batched CG: z ~ A_low^-1 b on b.b (interleaved [ntot][Rp]); returns iterations
-static int run_bcg(BatchData &b, int Rp, float tol, int max_it, cudaStream_t st)
+// capture one chunk of BCHUNK low-precision CG iterations (apply, p.q, x/r
+// update, p update) as a graph; the eager apply first builds the apply's
+// descriptors and workspaces outside the capture
+static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
 {
     const Seg S = make_seg(b, Rp);
-    k_b_init<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, tol, max_it);
-    VFD_CUDA(cudaGetLastError());
-    // eager apply first: builds the apply's descriptors and workspaces outside the capture
     batch_apply(b, b.p.p, b.q.p, Rp, st, nullptr, nullptr);
-    if (!b.exec) {
-        cudaStream_t cs;
-        VFD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph;
-        VFD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        try {
-            for (int it = 0; it < BCHUNK; ++it) {
-                batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh);
-                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
-                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p);
-                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p);
-            }
-        } catch (...) {
-            cudaStreamEndCapture(cs, &graph);
-            cudaStreamDestroy(cs);
-            throw;
+    if (b.exec) return;
+    cudaStream_t cs;
+    VFD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    VFD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int it = 0; it < BCHUNK; ++it) {
+            batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh);
+            k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
+            k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p);
+            k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p);
         }
-        VFD_CUDA(cudaStreamEndCapture(cs, &graph));
+    } catch (...) {
+        cudaStreamEndCapture(cs, &graph);
         cudaStreamDestroy(cs);
-        cudaError_t ie = cudaGraphInstantiate(&b.exec, graph, 0);
-        cudaGraphDestroy(graph);
-        VFD_CUDA(ie);
+        throw;
     }
-    int hf[3] = {0, 0, 0};
-    while (true) {
-        VFD_CUDA(cudaGraphLaunch(b.exec, st));
-        VFD_CUDA(cudaMemcpyAsync(hf, b.flag.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        VFD_CUDA(cudaStreamSynchronize(st));
-        if (hf[BF_DONE]) break;
-    }
-    batch_check(b, st);
-    return hf[BF_IT];
+    VFD_CUDA(cudaStreamEndCapture(cs, &graph));
+    cudaStreamDestroy(cs);
+    cudaError_t ie = cudaGraphInstantiate(&b.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    VFD_CUDA(ie);
 }
 
 // R columns per mesh of F_m, U_m (FP64, column-major, leading dimension ld_m,
-// device); relres and iters: nmesh x R, mesh-major (may be null)
+// device); relres and iters: nmesh x R, mesh-major (may be null); iters holds
+// the inner iterations run until the column's mesh met rtol
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
                        int max_it, int *iters, double *relres, cudaStream_t st)
 {
+    constexpr double RU_DROP = 1e-2;   // recursive-residual reduction between reliable updates
     const int Rp = ((R + 63) / 64) * 64, nm = b.nmesh;
+    const size_t nc = (size_t)nm * Rp, nr = (size_t)nm * R;
     ensure_solve(b, Rp);
     std::vector<DBuf<double>> AU(nm), res(nm);
     DBuf<double> n2, f2, scale;
+    DBuf<float> gamma_d, tol2_d;
+    DBuf<int> upd_d;
     for (int i = 0; i < nm; ++i) {
         AU[i].alloc((size_t)ld[i] * R);
         res[i].alloc((size_t)ld[i] * R);
     }
-    n2.alloc((size_t)nm * R);
-    f2.alloc((size_t)nm * R);
-    scale.alloc((size_t)nm * R);
-    std::vector<double> hn((size_t)nm * R), hf((size_t)nm * R), sc((size_t)nm * R);
-    int total = 0;
-    const float inner_tol = 1e-4f;
-    vfd_status status = VFD_ENOCONV;   // until every column meets rtol
-    for (int outer = 0; outer < 100; ++outer) {
-        // FP64 residuals with the FP64 operators
+    n2.alloc(nr);
+    f2.alloc(nr);
+    scale.alloc(nr);
+    gamma_d.alloc(nc);
+    tol2_d.alloc(nc);
+    upd_d.alloc(nm);
+    // host state: true residual norms^2 (hn, F norms^2 hf), the scale of each
+    // column's inner problem (sc: 0 = converged, frozen), the last true relres
+    std::vector<double> hn(nr, 0.0), hf(nr, 0.0), sc(nr, 0.0), rel_last(nr, HUGE_VAL);
+    std::vector<float> gamma(nc, 0.f), tol2(nc, 0.f), rr(nc, 0.f), rr_last(nc, 0.f);
+    std::vector<int> upd(nm, 1), conv(nm, 0), it_conv(nm, 0), hflag(FL_CNT + 3 * (size_t)nm, 0);
+    const Seg S = make_seg(b, Rp);
+    bool breakdown = false;   // a non-finite residual: the solve stops with VFD_ENOCONV
+
+    // for the meshes with upd[i]: FP64 residuals res = F - A U, relres, the new
+    // scales, thresholds and direction factors (gamma); sets conv[i]
+    auto true_residual = [&](int it_now) {
         for (int i = 0; i < nm; ++i) {
+            if (!upd[i]) continue;
             OpData &op = *b.ops[i];
             apply_parts_ex(*op.m, op, VFD_PART_ALL, U[i], AU[i].p, R, ld[i], false, st, nullptr);
             k_b_resid<<<R, 256, 0, st>>>(op.m->N, ld[i], F[i], AU[i].p, res[i].p, n2.p + (size_t)i * R,
                                          f2.p + (size_t)i * R);
             VFD_CUDA(cudaGetLastError());
         }
-        VFD_CUDA(cudaMemcpyAsync(hn.data(), n2.p, sizeof(double) * nm * R, cudaMemcpyDeviceToHost, st));
-        VFD_CUDA(cudaMemcpyAsync(hf.data(), f2.p, sizeof(double) * nm * R, cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaMemcpyAsync(hn.data(), n2.p, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaMemcpyAsync(hf.data(), f2.p, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
         VFD_CUDA(cudaStreamSynchronize(st));
-        bool all = true;
-        for (size_t c = 0; c < (size_t)nm * R; ++c) {
-            const double rel = hf[c] > 0.0 ? std::sqrt(hn[c] / hf[c]) : std::sqrt(hn[c]);
-            if (relres) relres[c] = rel;
-            // converged columns get scale 0: no correction, zero inner RHS
-            sc[c] = (rel > rtol) ? std::sqrt(hn[c]) : 0.0;
-            if (rel > rtol) all = false;
-        }
-        if (all) {
-            status = VFD_OK;
-            break;
-        }
-        if (total >= max_it) break;
-        VFD_CUDA(cudaMemcpyAsync(scale.p, sc.data(), sizeof(double) * nm * R, cudaMemcpyHostToDevice, st));
         for (int i = 0; i < nm; ++i) {
+            if (!upd[i]) continue;
+            const bool mesh_was_done = hflag[FL_CNT + 2 * (size_t)nm + i] != 0;
+            bool all = true;
+            for (int c = 0; c < R; ++c) {
+                const size_t h = (size_t)i * R + c, k = (size_t)i * Rp + c;
+                const double rel = hf[h] > 0.0 ? std::sqrt(hn[h] / hf[h]) : std::sqrt(hn[h]);
+                if (relres) relres[h] = rel;
+                if (!std::isfinite(rel)) breakdown = true;
+                if (!(rel <= rtol)) all = false;
+                const double s_new = rel > rtol ? std::sqrt(hn[h]) : 0.0;
+                // continue the direction only for a column still iterating whose recursive
+                // residual (sqrt(rr) in the old scale) agrees with the true one to a factor
+                // of two and whose true residual did not grow since the last update
+                const double rec = std::sqrt((double)rr[k]) * sc[h];
+                const bool iterating = !mesh_was_done && tol2[k] > 0.f && rr[k] > tol2[k];
+                const bool keep = s_new > 0.0 && sc[h] > 0.0 && iterating && rec < 2.0 * s_new &&
+                                  s_new < 2.0 * rec && rel <= rel_last[h];
+                // p_new = r_true + (|r_true|^2 / |r_rec|^2) beta_old p_old, in the new scale
+                gamma[k] = s_new <= 0.0 ? 0.f : keep ? (float)(s_new / (sc[h] * (double)rr[k])) : -1.f;
+                // inner target in the scaled units: half of rtol (room for the recursive residual's drift)
+                const double tgt = s_new > 0.0 ? 0.5 * rtol * std::sqrt(hf[h]) / s_new : 0.0;
+                tol2[k] = (float)(tgt * tgt);
+                rr_last[k] = s_new > 0.0 ? 1.f : 0.f;   // |b|^2 after the update
+                sc[h] = s_new;
+                rel_last[h] = rel;
+            }
+            if (all && !conv[i]) {
+                conv[i] = 1;
+                it_conv[i] = it_now;
+            }
+        }
+    };
+    // the scaled true residuals of the meshes with upd[i] into the inner right-hand side b
+    auto residual_to_inner = [&]() {
+        VFD_CUDA(cudaMemcpyAsync(scale.p, sc.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+        VFD_CUDA(cudaMemcpyAsync(tol2_d.p, tol2.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, st));
+        VFD_CUDA(cudaMemcpyAsync(gamma_d.p, gamma.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, st));
+        VFD_CUDA(cudaMemcpyAsync(upd_d.p, upd.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, st));
+        for (int i = 0; i < nm; ++i) {
+            if (!upd[i]) continue;
             const int N = b.ops[i]->m->N;
             k_b_to_inner<<<cdiv((long long)N * Rp, 256), 256, 0, st>>>(N, R, Rp, ld[i], res[i].p,
                                                                        scale.p + (size_t)i * R,
                                                                        b.b.p + (size_t)b.xoff[i] * Rp);
         }
         VFD_CUDA(cudaGetLastError());
-        total += run_bcg(b, Rp, inner_tol, std::max(1, max_it - total), st);
+    };
+    // U += scale x for the meshes with upd[i] (their correction since the last update)
+    auto add_correction = [&]() {
         for (int i = 0; i < nm; ++i) {
+            if (!upd[i]) continue;
             const int N = b.ops[i]->m->N;
             k_b_from_inner<<<cdiv((long long)N * R, 256), 256, 0, st>>>(N, R, Rp, ld[i],
                                                                         b.x.p + (size_t)b.xoff[i] * Rp,
                                                                         scale.p + (size_t)i * R, U[i]);
         }
         VFD_CUDA(cudaGetLastError());
+    };
+    auto all_conv = [&]() { return std::all_of(conv.begin(), conv.end(), [](int v) { return v != 0; }); };
+
+    vfd_status status = VFD_ENOCONV;   // until every column meets rtol
+    true_residual(0);
+    if (breakdown) return VFD_ENOCONV;
+    if (all_conv()) {
+        if (iters) std::fill(iters, iters + nr, 0);
+        return VFD_OK;
+    }
+    residual_to_inner();
+    k_b_init<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, tol2_d.p, std::max(1, max_it));
+    VFD_CUDA(cudaGetLastError());
+    capture_bcg(b, Rp, st);
+    const float drop2 = (float)(RU_DROP * RU_DROP);
+    int it = 0;
+    while (true) {
+        VFD_CUDA(cudaGraphLaunch(b.exec, st));
+        VFD_CUDA(cudaMemcpyAsync(hflag.data(), b.flag.p, sizeof(int) * hflag.size(), cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaMemcpyAsync(rr.data(), b.sc.p + (size_t)C_RR * nc, sizeof(float) * nc, cudaMemcpyDeviceToHost,
+                                 st));
+        VFD_CUDA(cudaStreamSynchronize(st));
+        batch_check(b, st);
+        it = hflag[BF_IT];
+        const bool out_of_its = it >= max_it;
+        // meshes due for a reliable update
+        bool any = false;
+        for (int i = 0; i < nm; ++i) {
+            bool ready = !conv[i] && (out_of_its || hflag[FL_CNT + 2 * (size_t)nm + i] != 0);
+            if (!conv[i] && !ready) {
+                ready = true;
+                for (int c = 0; c < R && ready; ++c) {
+                    const size_t k = (size_t)i * Rp + c;
+                    if (rr[k] > tol2[k] && rr[k] > drop2 * rr_last[k]) ready = false;
+                }
+            }
+            upd[i] = ready ? 1 : 0;
+            any |= ready;
+        }
+        if (!any) continue;
+        add_correction();
+        true_residual(it);
+        if (all_conv()) {
+            status = VFD_OK;
+            break;
+        }
+        if (out_of_its || breakdown) break;
+        residual_to_inner();
+        k_b_replace<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, gamma_d.p, tol2_d.p, upd_d.p);
+        VFD_CUDA(cudaGetLastError());
     }
     VFD_CUDA(cudaStreamSynchronize(st));
     if (iters)
-        for (size_t c = 0; c < (size_t)nm * R; ++c) iters[c] = total;
+        for (int i = 0; i < nm; ++i)
+            for (int c = 0; c < R; ++c) iters[(size_t)i * R + c] = conv[i] ? it_conv[i] : it;
     return status;
 }
 

@@ -207,6 +207,7 @@ struct OpData {
     DBuf<float> D32t;                  // D32 rounded to TF32 (batched tensor-core path, built on first use)
     DBuf<unsigned short> S16, D16, Ul16;   // BF16 copies (VFD_BF16)
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
+    bool comp_done = false;            // valBM32's diagonal compensated (batched path, first use)
     // the batch of one used by the batched (multi-RHS) low-precision apply / solve
     struct BatchData *self = nullptr;
     // adjoint gradient workspaces
