@@ -1315,30 +1315,36 @@ int batch_tuning(const BatchData &b, int *chosen, float *us, int n)
     return kNearCfgCount;
 }
 
-__global__ void k_fill1(long long n, float *__restrict__ a)
-{
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = 1.f;
-}
-
 __global__ void k_fill1d(long long n, double *__restrict__ a)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = 1.0;
 }
 
-// add c_i = (A_64 1)_i - (A_low 1)_i to the diagonal entry of row i of the FP32 B + M
-__global__ void k_comp_diag(int N, int R, const int *__restrict__ rowptr, const int *__restrict__ colidx,
-                            const double *__restrict__ y64, const float *__restrict__ ylow, float *__restrict__ val)
+// the values the tensor-core kernels multiply: BF16 rounded to nearest from FP64,
+// or TF32 (cvt.rna) of the FP32 copy; returned in FP64
+__global__ void k_round_f64(long long n, int bf, const double *__restrict__ a, double *__restrict__ b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    b[i] = bf ? (double)__bfloat162float(__double2bfloat16(a[i])) : (double)__uint_as_float(f2tf32((float)a[i]));
+}
+
+// c_i = (K_64 1)_i - (K_low 1)_i + sum_e (BM_64 - BM_32)[i, e], added to the
+// diagonal entry of row i of the FP32 B + M
+__global__ void k_comp_diag(int N, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                            const double *__restrict__ val64, const double *__restrict__ y64,
+                            const double *__restrict__ ylow, float *__restrict__ val)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double c = y64[i] - (double)ylow[(size_t)i * R];
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
-        if (colidx[e] == i) {
-            val[e] = (float)((double)val[e] + c);
-            break;
-        }
+    double c = y64[i] - ylow[i];
+    int dg = -1;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        c += val64[e] - (double)val[e];
+        if (colidx[e] == i) dg = e;
+    }
+    if (dg >= 0) val[dg] = (float)((double)val[dg] + c);
 }
 
 // Diagonal compensation of the low-precision operators, once per operator, on
@@ -1346,39 +1352,40 @@ __global__ void k_comp_diag(int N, int R, const int *__restrict__ rowptr, const 
 // matrices to TF32 / BF16 perturbs every entry by up to 2^-11 / 2^-8 of
 // itself, and the perturbation's row sums shift the smallest eigenvalues of
 // the (nearly zero-row-sum) operator by a fraction of the largest -- enough to
-// stall the inner CG on fine meshes.  Adding c = A_64 1 - A_low 1 to the
-// diagonal makes the low-precision operator exact on constant vectors, so the
-// remaining perturbation acts on differences u_j - u_i only and leaves the
-// smooth low modes alone.  The outer FP64 residual is unaffected.
-template <class T>
-static void compensate_diag(BatchData &b, int R, cudaStream_t st)
+// stall the inner CG on fine meshes.  Adding the row sums of the matrix
+// perturbation, c = A_64 1 - A_rounded 1 (both in FP64 arithmetic, so no
+// vector rounding enters c), to the FP32 diagonal makes the rounded matrix
+// exact on constant vectors: the remaining perturbation acts on differences
+// u_j - u_i only and leaves the smooth low modes alone.  The outer FP64
+// residual is unaffected.
+static void compensate_diag(BatchData &b, cudaStream_t st)
 {
-    bool need = false;
-    for (const OpData *op : b.ops) need |= !op->comp_done && op->m->N > 0;
-    if (!need) return;
-    const long long n = (long long)b.ntot * R;
-    DBuf<float> ones, y;
-    ones.alloc((size_t)n);
-    y.alloc((size_t)n);
-    k_fill1<<<cdiv(n, 256), 256, 0, st>>>(n, ones.p);
-    VFD_CUDA(cudaGetLastError());
-    batch_apply_impl<T>(b, ones.p, y.p, R, st, nullptr, nullptr);
+    const int bf = b.precision == VFD_BF16 ? 1 : 0;
     for (int i = 0; i < b.nmesh; ++i) {
         OpData &op = *b.ops[i];
         const MeshData &m = *op.m;
         if (op.comp_done || m.N == 0) continue;
-        DBuf<double> one64, y64;
-        one64.alloc(m.N);
+        auto rounded = [&](const DBuf<double> &a, DBuf<double> &r) {
+            r.alloc(std::max<size_t>(a.n, 1));
+            if (a.n) k_round_f64<<<cdiv((long long)a.n, 256), 256, 0, st>>>((long long)a.n, bf, a.p, r.p);
+            VFD_CUDA(cudaGetLastError());
+        };
+        DBuf<double> Ulr, Sr, Dr, one, y64, ylow;
+        rounded(m.Ul64, Ulr);
+        rounded(op.S64, Sr);
+        rounded(op.D64, Dr);
+        one.alloc(m.N);
         y64.alloc(m.N);
-        k_fill1d<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, one64.p);
-        apply_parts_ex(m, op, VFD_PART_ALL, one64.p, y64.p, 1, m.N, false, st, nullptr);
-        k_comp_diag<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, R, m.rowptr.p, m.colidx.p, y64.p,
-                                                                  y.p + (size_t)b.xoff[i] * R, op.valBM32.p);
+        ylow.alloc(m.N);
+        k_fill1d<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, one.p);
+        apply_k_with(m, op, m.Ul64.p, op.S64.p, op.D64.p, one.p, y64.p, st);
+        apply_k_with(m, op, Ulr.p, Sr.p, Dr.p, one.p, ylow.p, st);
+        k_comp_diag<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, m.rowptr.p, m.colidx.p, op.valBM.p, y64.p,
+                                                                  ylow.p, op.valBM32.p);
         VFD_CUDA(cudaGetLastError());
         VFD_CUDA(cudaStreamSynchronize(st));
         op.comp_done = true;
     }
-    VFD_CUDA(cudaStreamSynchronize(st));
 }
 
 // Y = A_low X for R (multiple of 64) interleaved FP32 columns over all meshes;
@@ -1388,13 +1395,9 @@ void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st,
 {
     VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
     ensure_batch(b, R, st);
-    if (b.precision == VFD_BF16) {
-        compensate_diag<__nv_bfloat16>(b, R, st);
-        batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
-    } else {
-        compensate_diag<float>(b, R, st);
-        batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
-    }
+    compensate_diag(b, st);
+    if (b.precision == VFD_BF16) batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
+    else batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
 }
 
 // column-major FP64 <-> interleaved FP32

@@ -10,7 +10,9 @@
 // F - A U is recomputed with the FP64 operator and replaces the recursive one,
 // and the search direction continues as p = r_true + beta p_old with beta
 // taken from the true residual norm -- the Krylov space is not restarted, so
-// the iteration count stays close to that of FP64 CG.  A column restarts from
+// the iteration count stays close to that of FP64 CG (the first step after an
+// update takes the exact line search r.p / p.Ap, which keeps the iteration a
+// descent method whatever the kept direction).  A column restarts from
 // p = r_true instead (an iterative-refinement step) when its inner iteration
 // had converged, when its true and recursive residuals differ by more than a
 // factor of two, or when its true residual grew since the last update.  Other
@@ -30,8 +32,9 @@ namespace {
 
 constexpr int BCHUNK = 8;
 constexpr int BT = 1024;   // threads of the reduction kernels
-// per (mesh, column) scalars, arrays of nmesh * Rp floats: rr, pq, alpha, beta, tol2
-enum { C_RR = 0, C_PQ = 1, C_AL = 2, C_BE = 3, C_TOL = 4, C_N = 5 };
+// per (mesh, column) scalars, arrays of nmesh * Rp floats: rr, pq, alpha, beta,
+// tol2, and rp = r.p (equal to rr except right after a reliable update)
+enum { C_RR = 0, C_PQ = 1, C_AL = 2, C_BE = 3, C_TOL = 4, C_RP = 5, C_N = 6 };
 // flags (int): [0] all done, [1] iterations, [2] max_it, [3] mesh-finish counter,
 // then per mesh: a block counter (FL_CNT + m), its live-column count
 // (FL_CNT + nmesh + m) and its done flag (FL_CNT + 2 nmesh + m: every column
@@ -130,6 +133,7 @@ __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ 
         },
         [&](int m, int c, float s) {
             scal(S, C_RR, m, c) = s;
+            scal(S, C_RP, m, c) = s;
             scal(S, C_TOL, m, c) = tol2[m * S.Rp + c];
             scal(S, C_AL, m, c) = 0.f;
             scal(S, C_BE, m, c) = 0.f;
@@ -146,17 +150,21 @@ __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ 
     }
 }
 
-// pq = p.q per (mesh, column); alpha = rr / pq (0 for converged columns)
+// pq = p.q per (mesh, column); alpha = rp / pq, the exact line search along p
+// (rp = rr in plain CG; it differs right after a reliable update, where the
+// step rr / pq would overshoot and break r_new . p = 0 for good); alpha = 0
+// for converged columns and for a direction that is not a descent direction
+// (the next p update then restarts the column from p = r)
 __global__ void __launch_bounds__(BT) k_b_pq(Seg S, const float *__restrict__ p, const float *__restrict__ q)
 {
     if (S.flag[BF_DONE]) return;
     seg_reduce<true>(
         S, [&](size_t t, int, int) { return p[t] * q[t]; },
         [&](int m, int c, float s) {
-            const float rr = scal(S, C_RR, m, c);
-            const bool live = rr > scal(S, C_TOL, m, c) && s > 0.f;
+            const float rr = scal(S, C_RR, m, c), rp = scal(S, C_RP, m, c);
+            const bool live = rr > scal(S, C_TOL, m, c) && s > 0.f && rp > 0.f;
             scal(S, C_PQ, m, c) = s;
-            scal(S, C_AL, m, c) = live ? rr / s : 0.f;
+            scal(S, C_AL, m, c) = live ? rp / s : 0.f;
         });
 }
 
@@ -184,9 +192,11 @@ __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float
             if (scal(S, C_AL, mm, c) != 0.f) {
                 scal(S, C_BE, mm, c) = rr > 0.f ? s / rr : 0.f;
                 scal(S, C_RR, mm, c) = s;
+                scal(S, C_RP, mm, c) = s;   // r_new . p_old = 0, so r_new . p_new = rr_new
                 if (s > scal(S, C_TOL, mm, c)) atomicAdd(&live, 1);
             } else {
-                scal(S, C_BE, mm, c) = 0.f;
+                scal(S, C_BE, mm, c) = 0.f;   // p = r next
+                scal(S, C_RP, mm, c) = rr;
             }
         });
     if (m < 0) return;
@@ -262,6 +272,17 @@ __global__ void __launch_bounds__(BT) k_b_replace(Seg S, const float *__restrict
         if (threadIdx.x == 0) S.mdone()[m] = live == 0 ? 1 : 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) S.flag[BF_DONE] = 0;
+}
+
+// rp = r . p of the meshes just updated (the step length of their first step)
+__global__ void __launch_bounds__(BT) k_b_rp(Seg S, const float *__restrict__ r, const float *__restrict__ p,
+                                             const int *__restrict__ upd)
+{
+    seg_reduce<false>(
+        S, [&](size_t t, int mm, int) { return upd[mm] ? r[t] * p[t] : 0.f; },
+        [&](int mm, int c, float s) {
+            if (upd[mm]) scal(S, C_RP, mm, c) = s;
+        });
 }
 
 // residual scaling between the FP64 column-major and the FP32 interleaved layouts
@@ -413,7 +434,7 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
                        int max_it, int *iters, double *relres, cudaStream_t st)
 {
-    constexpr double RU_DROP = 1e-2;   // recursive-residual reduction between reliable updates
+    constexpr double RU_DROP = 0.03;   // recursive-residual reduction between reliable updates
     const int Rp = ((R + 63) / 64) * 64, nm = b.nmesh;
     const size_t nc = (size_t)nm * Rp, nr = (size_t)nm * R;
     ensure_solve(b, Rp);
@@ -560,6 +581,7 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
         if (out_of_its || breakdown) break;
         residual_to_inner();
         k_b_replace<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, gamma_d.p, tol2_d.p, upd_d.p);
+        k_b_rp<<<b.nred, BT, 0, st>>>(S, b.r.p, b.p.p, upd_d.p);
         VFD_CUDA(cudaGetLastError());
     }
     VFD_CUDA(cudaStreamSynchronize(st));

@@ -292,6 +292,8 @@ void launch_convert_fp32(const MeshData &m, OpData &op, cudaStream_t st);
 void launch_load(const MeshData &m, const double *f, double *F, cudaStream_t st);
 void launch_selftest_math(const MeshData &m, int which, long long n, const double *x, double *out, cudaStream_t st);
 // apply.cu
+void apply_k_with(const MeshData &m, OpData &op, const double *Ul, const double *S, const double *D, const double *X,
+                  double *Y, cudaStream_t st);
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                     bool lowp, cudaStream_t st, const int *skip);
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
