@@ -93,7 +93,12 @@ void upload_field(const vfd_field *f, int n_vert, DBuf<double> &rows, DBuf<doubl
                 VFD_EINVAL, "missing field rows");
     std::vector<double> h;
     int kmax = 0;
-    for (int t = 0; t < f->n_fourier; ++t) {
+    // Fourier rows sorted by k_1 (stable): the device sums rows of equal k_1 together
+    std::vector<int> order(f->n_fourier);
+    for (int t = 0; t < f->n_fourier; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return f->fourier[5 * a] < f->fourier[5 * b]; });
+    for (int t : order) {
         const double *r = f->fourier + 5 * t;
         for (int j = 0; j < 3; ++j) {
             if (r[j] != std::floor(r[j])) kmax = 99;           // non-integer: general path

@@ -38,27 +38,45 @@ __device__ __forceinline__ void trig_table(int d, int kmax, const double *x, Tri
     }
 }
 
+// A Fourier row (k, A = amp e^{i phase}) contributes Re(A e^{i pi k.x}).  With
+// the trig table the rows (sorted by k_1 on the host) are summed in groups of
+// equal k_1: Re(e^{i pi k_1 x_1} sum_group A e^{i pi (k_2 x_2 + k_3 x_3)}), one
+// complex multiply-add per row instead of d complex products.
 __device__ __forceinline__ double field_terms(const DField &F, int d, const double *x, const TrigTable *tab)
 {
     double v = F.c0;
     const double *r = F.rows;
-    for (int t = 0; t < F.nF; ++t, r += 5) {
-        double er = 1.0, ei = 0.0;  // e^{i pi k.x}
-        if (tab) {
-            for (int j = 0; j < d; ++j) {
-                int kj = (int)r[j];
-                int ak = kj < 0 ? -kj : kj;
-                double cr = tab->c[j][ak], ci = kj < 0 ? -tab->s[j][ak] : tab->s[j][ak];
-                double nr = er * cr - ei * ci, ni = er * ci + ei * cr;
-                er = nr;
-                ei = ni;
+    if (tab) {
+        int t = 0;
+        while (t < F.nF) {
+            const int k1 = (int)r[5 * t];
+            double gr = 0.0, gi = 0.0;
+            for (; t < F.nF && (int)r[5 * t] == k1; ++t) {
+                const double *q = r + 5 * t;
+                double er = q[3], ei = q[4];
+                for (int j = 1; j < d; ++j) {
+                    const int kj = (int)q[j], ak = kj < 0 ? -kj : kj;
+                    const double cr = tab->c[j][ak], ci = kj < 0 ? -tab->s[j][ak] : tab->s[j][ak];
+                    const double nr = fma(er, cr, -ei * ci), ni = fma(er, ci, ei * cr);
+                    er = nr;
+                    ei = ni;
+                }
+                gr += er;
+                gi += ei;
             }
-        } else {
+            const int a1 = k1 < 0 ? -k1 : k1;
+            const double ur = tab->c[0][a1], ui = k1 < 0 ? -tab->s[0][a1] : tab->s[0][a1];
+            v = fma(ur, gr, fma(-ui, gi, v));
+        }
+        r += 5 * F.nF;
+    } else {
+        for (int t = 0; t < F.nF; ++t, r += 5) {
+            double er, ei;   // e^{i pi k.x}
             double kx = 0.0;
             for (int j = 0; j < d; ++j) kx += r[j] * x[j];
             sincospi(kx, &ei, &er);
+            v += r[3] * er - r[4] * ei;  // amp cos(pi k.x + phase)
         }
-        v += r[3] * er - r[4] * ei;  // amp cos(pi k.x + phase)
     }
     for (int t = 0; t < F.nG; ++t, r += 5) {
         double q = 0.0;
