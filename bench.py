@@ -324,6 +324,14 @@ def main():
     roof["algorithmic_bytes"] = leaf_bytes
     roof["launch_us"] = t_leaf * 1e6
     roof["traffic"] = _traffic_from_profile(args.workload, args.precision)
+    # the assembly's two largest kernels: FP64-pipe bound (their DRAM traffic is
+    # negligible); throughput in kernel evaluations per second from the live
+    # phase timings (mean over the timed assemblies)
+    asm_k = {}
+    for name, key, ev in (("k_singular2d", "singular", "sing_points"), ("k_near_build", "near", "near_point_pairs")):
+        if info.get(ev) and ph.get(key):
+            asm_k[name] = {"bound": "alu (FP64 pipe)", "unit": "Geval/s", "evals": info[ev], "ms": round(ph[key], 3),
+                           "achieved": info[ev] / (ph[key] / 1e3) / 1e9}
 
     # apply: far projections, node sums, coupling, row kernel, far expansion
     apply_kernels = 5 if info["far_blocks"] > 0 else 1
@@ -361,7 +369,7 @@ def main():
             "assemble_ms": ph["total"], "phases_ms": {k2: round(v2, 3) for k2, v2 in ph.items()},
             "solve_ms": 1000 * tot / args.steps - ph["total"], "apply_us": t_apply * 1e6,
             "apply_dof_rhs_per_s": n / t_apply,
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "assembly_kernels": asm_k, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "batched_mixed_precision": batched,
             "batch_24_meshes": batch24,

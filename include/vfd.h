@@ -160,7 +160,10 @@ vfd_status vfd_mesh_dofs(vfd_mesh_t mesh, int32_t *dof_of_vertex, int64_t *n_dof
  * [9] inadmissible leaf blocks of K  [10] dense near entries of K
  * [11] quadrature points  [12] interior quadrature points
  * [13] admissible blocks of the density sweep  [14] near point pairs of the
- * density sweep  [15] stored near entries (row panels, padded to 4 columns). */
+ * density sweep  [15] stored near entries (row panels, padded to 4 columns)
+ * [16] kernel evaluations of the near-block build (point pairs of the
+ * computed leaf blocks)  [17] 4D points of the singular rules over all
+ * touching pairs (2D; 0 in 1D). */
 vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info);
 
 /* Assemble the operator for the fields s and log kappa (Algorithm 1):

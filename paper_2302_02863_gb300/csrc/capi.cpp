@@ -70,7 +70,8 @@ void require_device()
 }
 
 // upload a field descriptor; Fourier rows become (k, amp cos(phase), amp sin(phase))
-void upload_field(const vfd_field *f, int n_vert, DBuf<double> &rows, DBuf<double> &vals, DField &out)
+void upload_field(const vfd_field *f, int n_vert, DBuf<double> &rows, DBuf<double> &vals, DBuf<int> &gint,
+                  DField &out)
 {
     VFD_REQUIRE(f, VFD_EINVAL, "null field");
     out = DField{};
@@ -110,12 +111,54 @@ void upload_field(const vfd_field *f, int n_vert, DBuf<double> &rows, DBuf<doubl
     }
     for (int t = 0; t < 5 * f->n_gauss; ++t) h.push_back(f->gauss[t]);
     for (int t = 0; t < 5 * f->n_tbump; ++t) h.push_back(f->tbump[t]);
+    // grouped form of 2D rows (integer |k| <= 4, k_3 = 0): group k_1 (signed)
+    // holds rows A = amp e^{i phase}; with t = cos(pi|k_2|x_2) + i sign(k_2) sin(..)
+    // and e_1 likewise, Re(e_1 sum A t) = c_1 gr + s_1 gq, gr = a0 c_2 + a1 s_2,
+    // gq = a2 s_2 + a3 c_2 (the signs folded into a0..a3)
+    bool grouped = f->n_fourier > 0;
+    for (int t = 0; t < f->n_fourier && grouped; ++t) {
+        const double *r = f->fourier + 5 * t;
+        for (int j = 0; j < 3; ++j)
+            if (r[j] != std::floor(r[j]) || std::fabs(r[j]) > 4.0) grouped = false;
+        if (r[2] != 0.0) grouped = false;
+    }
+    std::vector<int> gi;
+    size_t coef_off = h.size();
+    int ngrp = 0;
+    if (grouped) {
+        std::vector<int> mk;
+        size_t t0 = 0;
+        while (t0 < order.size()) {
+            const double k1 = f->fourier[5 * order[t0]];
+            size_t t1 = t0;
+            while (t1 < order.size() && f->fourier[5 * order[t1]] == k1) ++t1;
+            gi.push_back((int)std::fabs(k1));
+            gi.push_back((int)(t1 - t0));
+            const double s1 = k1 < 0 ? -1.0 : 1.0;
+            for (size_t q = t0; q < t1; ++q) {
+                const double *r = f->fourier + 5 * order[q];
+                const double ar = r[3] * std::cos(r[4]), ai = r[3] * std::sin(r[4]), s2 = r[1] < 0 ? -1.0 : 1.0;
+                mk.push_back((int)std::fabs(r[1]));
+                h.push_back(ar);
+                h.push_back(-ai * s2);
+                h.push_back(-s1 * s2 * ar);
+                h.push_back(-s1 * ai);
+            }
+            ++ngrp;
+            t0 = t1;
+        }
+        gi.insert(gi.end(), mk.begin(), mk.end());
+    }
     rows.upload(h);
+    gint.upload(gi);
     out.nF = f->n_fourier;
     out.nG = f->n_gauss;
     out.nT = f->n_tbump;
     out.kmax = kmax;
     out.rows = rows.p;
+    out.ngrp = ngrp;
+    out.gint = ngrp ? gint.p : nullptr;
+    out.gcoef = ngrp ? rows.p + coef_off : nullptr;
 }
 
 bool field_is_const(const vfd_field *f)
@@ -183,10 +226,11 @@ vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info)
     VFD_API_BEGIN
     VFD_REQUIRE(mesh && info && n_info >= 0, VFD_EINVAL, "bad argument");
     const MeshData &m = *mesh->m;
-    int64_t v[16] = {m.N,    m.M,     m.C,      m.npairs, m.nnz,   m.kt.L,      m.kt.nnode,  m.k,
-                     m.nfar, m.nnear, m.near_entries_alg, m.nQ, m.nQint, m.nrfar, m.rnear_pairs, m.near_entries};
-    for (int i = 0; i < n_info && i < 16; ++i) info[i] = v[i];
-    for (int i = 16; i < n_info; ++i) info[i] = 0;
+    int64_t v[18] = {m.N,    m.M,     m.C,      m.npairs, m.nnz,   m.kt.L,      m.kt.nnode,  m.k,
+                     m.nfar, m.nnear, m.near_entries_alg, m.nQ, m.nQint, m.nrfar, m.rnear_pairs, m.near_entries,
+                     m.near_point_pairs, m.sing_points};
+    for (int i = 0; i < n_info && i < 18; ++i) info[i] = v[i];
+    for (int i = 18; i < n_info; ++i) info[i] = 0;
     return VFD_OK;
     VFD_API_END
 }
@@ -215,8 +259,8 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
     op->precision = precision;
     op->s_bar = s_bar;
     op->check_fields = !(flags & VFD_ASSEMBLE_UNCHECKED);
-    upload_field(s, m.M, op->f_rows_s, op->f_vals_s, op->fs);
-    upload_field(log_kappa, m.M, op->f_rows_k, op->f_vals_k, op->fk);
+    upload_field(s, m.M, op->f_rows_s, op->f_vals_s, op->f_gint_s, op->fs);
+    upload_field(log_kappa, m.M, op->f_rows_k, op->f_vals_k, op->f_gint_k, op->fk);
     op->errflag.alloc(2);
     op->errflag.zero(st);
     op->timed = (flags & VFD_ASSEMBLE_TIMED) != 0;

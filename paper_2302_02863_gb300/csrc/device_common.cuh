@@ -39,14 +39,30 @@ __device__ __forceinline__ void trig_table(int d, int kmax, const double *x, Tri
 }
 
 // A Fourier row (k, A = amp e^{i phase}) contributes Re(A e^{i pi k.x}).  With
-// the trig table the rows (sorted by k_1 on the host) are summed in groups of
-// equal k_1: Re(e^{i pi k_1 x_1} sum_group A e^{i pi (k_2 x_2 + k_3 x_3)}), one
-// complex multiply-add per row instead of d complex products.
+// the trig table the rows are summed in groups of equal k_1:
+// Re(e^{i pi k_1 x_1} sum_group A e^{i pi (k_2 x_2 + k_3 x_3)}).  2D rows with
+// integer |k| <= 4 use the grouping prepared on the host (integer indices, the
+// signs folded into four coefficients per row: four FMAs per row); other rows
+// (sorted by k_1 on the host) are grouped on the fly.
 __device__ __forceinline__ double field_terms(const DField &F, int d, const double *x, const TrigTable *tab)
 {
     double v = F.c0;
     const double *r = F.rows;
-    if (tab) {
+    if (tab && F.ngrp > 0 && d == 2) {
+        const int *mk = F.gint + 2 * F.ngrp;
+        const double *a = F.gcoef;
+        for (int g = 0; g < F.ngrp; ++g) {
+            const int k1 = F.gint[2 * g], nm = F.gint[2 * g + 1];
+            double gr = 0.0, gq = 0.0;
+            for (int q = 0; q < nm; ++q, ++mk, a += 4) {
+                const double c = tab->c[1][*mk], s = tab->s[1][*mk];
+                gr = fma(a[0], c, fma(a[1], s, gr));
+                gq = fma(a[2], s, fma(a[3], c, gq));
+            }
+            v = fma(tab->c[0][k1], gr, fma(tab->s[0][k1], gq, v));
+        }
+        r += 5 * F.nF;
+    } else if (tab) {
         int t = 0;
         while (t < F.nF) {
             const int k1 = (int)r[5 * t];

@@ -560,6 +560,14 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             }
             m->pair_info.upload(pinfo);
             m->pair_info_h = pinfo;
+            if (d == 2) {   // regions per pair type: vertex 2, edge 5, identical 3; ns^4 points each
+                const int64_t n4 = (int64_t)opts.n_sing * opts.n_sing * opts.n_sing * opts.n_sing;
+                m->sing_points = 0;
+                for (int p = 0; p < m->npairs; ++p) {
+                    const int ty = pinfo[(size_t)p * 8];
+                    m->sing_points += n4 * (ty == 1 ? 2 : ty == 2 ? 5 : 3);
+                }
+            }
         }
 
         // ---- K tree: support-extended boxes (Sec. 5.1, omega^e), Chebyshev nodes
@@ -743,6 +751,13 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                     sc.push_back(e.second);
                 }
             }
+            m->near_point_pairs = 0;
+            for (int a = 0; a < nleaf; ++a)
+                for (int e = m->near_ptr_h[a]; e < m->near_ptr_h[a + 1]; ++e) {
+                    const int b = m->near_col_h[e];
+                    if (a <= b)
+                        m->near_point_pairs += (int64_t)(lp_ptr[a + 1] - lp_ptr[a]) * (lp_ptr[b + 1] - lp_ptr[b]);
+                }
             m->lp_ptr.upload(lp_ptr);
             m->lp_pts.upload(lp_pts);
             m->supp_ptr.upload(sp);

@@ -79,6 +79,12 @@ struct DField {
     double c0, lo, hi;
     const double *rows; // device, (nF + nG + nT) * 5
     const double *vals; // device, n_vert (nodal)
+    // 2D Fourier rows with integer |k| <= 4 and k_3 = 0, grouped by k_1 (0 groups
+    // otherwise): gint = per group (|k_1|, rows), then per row |k_2|; gcoef = per
+    // row four coefficients with the signs of k_1, k_2 folded in
+    int ngrp;
+    const int *gint;
+    const double *gcoef;
 };
 
 // ---------------------------------------------------------------------------
@@ -156,6 +162,8 @@ struct MeshData {
     DBuf<int> panel_w;         // per row leaf: panel row stride (padded to 8)
     DBuf<int64_t> panel_off;   // per row leaf: panel start (nleaf + 1)
     int64_t near_entries_alg = 0;   // sum |sigma||sigma'| over near blocks (no padding)
+    int64_t near_point_pairs = 0;   // kernel evaluations of the near-block build (computed blocks)
+    int64_t sing_points = 0;        // 4D points of the singular rules over all touching pairs (2D)
     DBuf<int> gcol, gcol_off;  // per panel column the DoF of its x entry (-1: padding)
     DBuf<int> vleaf;           // leaf of every DoF
     int max_panel_w = 0;
@@ -196,6 +204,7 @@ struct OpData {
     bool check_fields = true;
     DField fs{}, fk{};
     DBuf<double> f_rows_s, f_rows_k, f_vals_s, f_vals_k;
+    DBuf<int> f_gint_s, f_gint_k;
     DBuf<double> q_s, q_lk;            // at all quadrature points
     DBuf<double> kc_s, kc_lk;          // at K-tree Chebyshev nodes
     DBuf<double> tc_s, tc_lk, sc_s, sc_lk;  // density trees' Chebyshev nodes

@@ -29,7 +29,7 @@ TIMING_KEYS = ["fields", "coupling", "near", "density", "singular", "gather", "t
 VFD_FIELD_ANALYTIC, VFD_FIELD_NODAL = 0, 1
 INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "nodes", "rank",
              "far_blocks", "near_blocks", "near_entries", "n_q", "n_qint", "rho_far_blocks",
-             "rho_near_pairs", "near_storage"]
+             "rho_near_pairs", "near_storage", "near_point_pairs", "sing_points"]
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
            "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_grad", "vfd_load", "vfd_op_rho", "vfd_op_timings",

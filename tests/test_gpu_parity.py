@@ -213,3 +213,28 @@ def test_field_range_is_checked():
     with pytest.raises(vfd.VfdError) as e:
         vfd.vfd_assemble(mesh, synth.const_field(0.95), synth.const_field(0.0), 0.9)
     assert e.value.status == vfd.VFD_EINVAL
+
+
+def test_assembly_evaluation_counts(small_disk):
+    """The structure counts behind the assembly throughput figures: touching
+    pairs (unordered, at least one interior cell) and their singular-rule 4D
+    points (vertex 2, edge 5, identical 3 regions of n_s^4 points, Sec. 4),
+    counted here from the cells directly."""
+    m = small_disk[0]
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16, lam=0.75, rho_lambda=0.75)
+    cells = np.asarray(m.cells)
+    inter = np.asarray(m.cell_is_interior).astype(bool)
+    by_vert = {}
+    for c, tri in enumerate(cells):
+        for v in tri:
+            by_vert.setdefault(int(v), []).append(c)
+    shared = {}
+    for cs in by_vert.values():
+        for a in cs:
+            for b in cs:
+                if a <= b and (inter[a] or inter[b]):
+                    shared[(a, b)] = shared.get((a, b), 0) + 1
+    regions = {1: 2, 2: 5, 3: 3}
+    assert mesh.info["touching_pairs"] == len(shared)
+    assert mesh.info["sing_points"] == 81 * sum(regions[v] for v in shared.values())
+    assert mesh.info["near_point_pairs"] > 0
