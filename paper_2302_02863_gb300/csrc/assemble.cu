@@ -400,11 +400,13 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
         int id = act ? P.tt_perm[i] : 0;
         double x[3] = {0, 0, 0};
         int cv[3] = {-1, -1, -1};
-        double s_ = 0, l_ = 0;
+        double s_ = 0, l_ = 0, a_ = 0, b_ = 0;
         if (act) {
             for (int c = 0; c < d; ++c) x[c] = P.qx[(size_t)c * P.nQ + id];
             s_ = P.qs[id];
             l_ = P.qlk[id];
+            a_ = 0.5 * l_;
+            b_ = fma(0.5, s_, 0.25 * d);
             int cell = P.qcell[id];
             for (int a = 0; a < P.nv; ++a) cv[a] = P.cells[(size_t)cell * P.nv + a];
         }
@@ -419,9 +421,10 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
                 for (int t = threadIdx.x; t < nj; t += blockDim.x) {
                     int jd = P.st_perm[j0 + t];
                     for (int c = 0; c < d; ++c) sx[t * d + c] = P.qx[(size_t)c * P.nQ + jd];
+                    // exponent terms of the source, its weight folded in: w gamma = exp(log w + ...)
                     sw[t] = P.qw[jd];
-                    ss[t] = P.qs[jd];
-                    sl[t] = P.qlk[jd];
+                    ss[t] = fma(0.5, P.qs[jd], 0.25 * d);
+                    sl[t] = fma(0.5, P.qlk[jd], fast_log(P.mt, P.qw[jd]));
                     int cell = P.qcell[jd];
                     for (int a = 0; a < 3; ++a) sv[t * 3 + a] = a < P.nv ? P.cells[(size_t)cell * P.nv + a] : -2;
                 }
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
                             double dd = x[c] - sx[t * d + c];
                             r2 += dd * dd;
                         }
-                        acc += gamma_r2t(P.mt, d, r2, s_, ss[t], l_, sl[t]) * sw[t];
+                        acc += gamma_ab(P.mt, r2, a_, sl[t], b_, ss[t]);
                     }
             }
         }
@@ -623,14 +626,19 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
     double *Tm = G + (size_t)TQ * P.maxpts;          // TQ * maxleaf
     double *Dacc = Tm + (size_t)TQ * P.maxleaf;      // maxleaf * maxleaf
     double *bx = Dacc + (size_t)P.maxleaf * P.maxleaf;  // maxpts * d
-    double *bs = bx + (size_t)P.maxpts * d;
-    double *bl = bs + P.maxpts;
-    int *bv = (int *)(bl + P.maxpts);                 // maxpts * 3
+    double *bs = bx + (size_t)P.maxpts * d;           // b = s/2 + d/4 of the column points
+    double *bl = bs + P.maxpts;                       // a = log(kappa)/2
+    double *tx = bl + P.maxpts;                       // row tile: TQ * d coordinates, a, b
+    double *ta = tx + (size_t)TQ * d;
+    double *tb = ta + TQ;
+    int *bv = (int *)(tb + TQ);                       // maxpts * 3
+    int *tv = bv + (size_t)P.maxpts * 3;              // TQ * 3
+    const double dq = 0.25 * d;
     for (int t = threadIdx.x; t < npb; t += blockDim.x) {
         int id = P.lp_pts[pb0 + t];
         for (int c = 0; c < d; ++c) bx[t * d + c] = P.qx[(size_t)c * P.nQ + id];
-        bs[t] = P.qs[id];
-        bl[t] = P.qlk[id];
+        bs[t] = fma(0.5, P.qs[id], dq);
+        bl[t] = 0.5 * P.qlk[id];
         int cell = P.qcell[id];
         for (int q = 0; q < 3; ++q) bv[t * 3 + q] = q < nv ? P.cells[(size_t)cell * nv + q] : -2;
     }
@@ -638,24 +646,30 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
     __syncthreads();
     for (int t0 = 0; t0 < npa; t0 += TQ) {
         const int nt = min(TQ, npa - t0);
+        for (int tq = threadIdx.x; tq < nt; tq += blockDim.x) {
+            const int id = P.lp_pts[pa0 + t0 + tq], cell = P.qcell[id];
+            for (int c = 0; c < d; ++c) tx[tq * d + c] = P.qx[(size_t)c * P.nQ + id];
+            ta[tq] = 0.5 * P.qlk[id];
+            tb[tq] = fma(0.5, P.qs[id], dq);
+            for (int u = 0; u < 3; ++u) tv[tq * 3 + u] = u < nv ? P.cells[(size_t)cell * nv + u] : -3;
+        }
+        __syncthreads();
         // kernel tile G[tq][l] = gamma_T(q_{t0+tq}, q_l)
         for (int idx = threadIdx.x; idx < nt * npb; idx += blockDim.x) {
             int tq = idx / npb, l = idx - tq * npb;
-            int id = P.lp_pts[pa0 + t0 + tq];
-            int cell = P.qcell[id];
             bool touch = false;
             for (int u = 0; u < nv; ++u) {
-                int va = P.cells[(size_t)cell * nv + u];
+                int va = tv[tq * 3 + u];
                 for (int w = 0; w < nv; ++w) touch |= (va == bv[l * 3 + w]);
             }
             double g = 0.0;
             if (!touch) {
                 double r2 = 0.0;
                 for (int c = 0; c < d; ++c) {
-                    double dd = P.qx[(size_t)c * P.nQ + id] - bx[l * d + c];
+                    double dd = tx[tq * d + c] - bx[l * d + c];
                     r2 += dd * dd;
                 }
-                g = gamma_r2t(P.mt, d, r2, P.qs[id], bs[l], P.qlk[id], bl[l]);
+                g = gamma_ab(P.mt, r2, ta[tq], bl[l], tb[tq], bs[l]);
             }
             G[(size_t)tq * npb + l] = g;
         }
@@ -744,7 +758,8 @@ void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st)
     P.D = op.D64.p;
     auto shm_for = [&](int TQ) {
         return (size_t)TQ * P.maxpts * 8 + (size_t)TQ * P.maxleaf * 8 + (size_t)P.maxleaf * P.maxleaf * 8 +
-               (size_t)P.maxpts * (m.d + 2) * 8 + (size_t)P.maxpts * 3 * 4;
+               (size_t)P.maxpts * (m.d + 2) * 8 + (size_t)TQ * (m.d + 2) * 8 + (size_t)P.maxpts * 3 * 4 +
+               (size_t)TQ * 3 * 4;
     };
     int TQ = 32;
     while (TQ > 1 && shm_for(TQ) > 200 * 1024) TQ /= 2;

@@ -169,8 +169,8 @@ __device__ __forceinline__ double fast_log(const double *__restrict__ mt, double
     const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
     const int j = (int)(((bits >> 44) & 0xff) + 1) >> 1;   // nearest j/128 to m - 1
     const double r = fma(m, __ldg(mt + MT_C + j), -1.0);   // |r| <= 2^-8
-    double q = 1.0 / 7.0;
-    q = fma(q, r, -1.0 / 6.0);
+    // log(1 + r) = r q(r) through r^6 (the next term, r^7 / 7, is below 2^-58)
+    double q = -1.0 / 6.0;
     q = fma(q, r, 1.0 / 5.0);
     q = fma(q, r, -0.25);
     q = fma(q, r, 1.0 / 3.0);
@@ -183,12 +183,15 @@ __device__ __forceinline__ double fast_log(const double *__restrict__ mt, double
 __device__ __forceinline__ double fast_exp(const double *__restrict__ mt, double y)
 {
     y = fmin(fmax(y, -700.0), 700.0);
-    const double kf = rint(y * 92.33248261689366);   // 64 / ln 2
-    const long long ki = (long long)kf;
+    // k = nearest integer to y 64/ln2: adding 1.5 2^52 leaves it in the low bits
+    const double big = 6755399441055744.0;
+    const double tk = fma(y, 92.33248261689366, big);   // 64 / ln 2
+    const double kf = tk - big;
+    const long long ki = (long long)(int)__double2loint(tk);
     double r = fma(-kf, __ldg(mt + MT_CONST + 2), y);
-    r = fma(-kf, __ldg(mt + MT_CONST + 3), r);        // |r| <= ln2/128
-    double q = 1.0 / 720.0;
-    q = fma(q, r, 1.0 / 120.0);
+    r = fma(-kf, __ldg(mt + MT_CONST + 3), r);        // |r| <= ln2/128 (+ rounding)
+    // exp(r) = 1 + r q(r) through r^5 (the next term, r^6 / 720, is below 4e-17)
+    double q = 1.0 / 120.0;
     q = fma(q, r, 1.0 / 24.0);
     q = fma(q, r, 1.0 / 6.0);
     q = fma(q, r, 0.5);
@@ -196,6 +199,14 @@ __device__ __forceinline__ double fast_exp(const double *__restrict__ mt, double
     const double s = __ldg(mt + MT_EXP2 + (int)(ki & 63));
     const double v = fma(s, q * r, s);
     return __longlong_as_double(__double_as_longlong(v) + ((ki >> 6) << 52));
+}
+
+// gamma from r^2 and per-point exponent terms a = log(kappa)/2 (plus any log
+// weight folded in) and b = s/2 + d/4: exp(a_x + a_y - (b_x + b_y) log r^2)
+__device__ __forceinline__ double gamma_ab(const double *__restrict__ mt, double r2, double ax, double ay, double bx,
+                                           double by)
+{
+    return fast_exp(mt, (ax + ay) - (bx + by) * fast_log(mt, r2));
 }
 
 // gamma from r^2 with the table-driven log/exp
