@@ -331,9 +331,10 @@ vfd_status vfd_op_timings(vfd_op_t op, double *ms, int n);
 
 /* Self-test of the library's table-driven FP64 logarithm / exponential used
  * for the kernel evaluations (Tang's table-driven method): out[i] =
- * log(x[i]) (which = 0) or exp(x[i]) (which = 1), computed on the device.
+ * log(x[i]) (which = 0), exp(x[i]) (which = 1), cos(pi x[i]) (which = 2) or
+ * sin(pi x[i]) (which = 3), computed on the device.
  * x, out: device pointers, n entries.  Needs a mesh handle for the tables.
- * Valid inputs: x > 0 normal (log), |x| < 700 (exp). */
+ * Valid inputs: x > 0 normal (log), |x| < 700 (exp), |x| < 2^24 (cos, sin). */
 vfd_status vfd_selftest_math(vfd_mesh_t mesh, int which, int64_t n, const double *x, double *out, void *stream);
 
 void vfd_free_op(vfd_op_t op);

@@ -192,42 +192,70 @@ k_near_csr(int fl, int NR, const int *__restrict__ kb, const int *__restrict__ k
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const A *yh = yhat + (size_t)r * hs;
-    for (int i = b + warp; i < e; i += nw) {
-        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        if (use_near) {
-            const V *row = (const V *)(D + P0 + (size_t)(i - b_leaf) * W);
-            const V *xv = (const V *)xg;
-            const int nv = W / VW;
-            int c = lane;
-            for (; c + 96 < nv; c += 128) {
-                V a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
-                fma_v(a0, xv[c], s0, s1);
-                fma_v(a1, xv[c + 32], s2, s3);
-                fma_v(a2, xv[c + 64], s0, s1);
-                fma_v(a3, xv[c + 96], s2, s3);
-            }
-            for (; c < nv; c += 32) fma_v(row[c], xv[c], s0, s1);
-        }
-        A fa = 0;
-        if (F.use) {
-            // lanes cover (level, alpha) pairs: 32/k levels per instruction when k <= 32
-            const int per = F.k <= 32 ? 32 / F.k : 1;
-            const int kk = F.k <= 32 ? F.k : 32;
-            for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
-                const int l = l0 + lane / kk;
-                if (lane / kk < per && l <= F.L) {
-                    const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
-                    const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
-                    const A *y = yh + (size_t)node * F.k;
-                    for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
+    // a warp takes four rows (b + warp + q nw, q = 0..3) at a time: one
+    // accumulator per row and lane (FP64 issue is slow enough on this part that
+    // the dependency chain costs nothing), then one butterfly over the four
+    // rows together (6 adds instead of 4 x 5 for separate warp sums)
+    for (int g0 = b; g0 < e; g0 += 4 * nw) {
+        double part[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = g0 + warp + q * nw;
+            double acc = 0.0;
+            if (i < e) {
+                if (use_near) {
+                    T s = 0;
+                    const V *row = (const V *)(D + P0 + (size_t)(i - b_leaf) * W);
+                    const V *xv = (const V *)xg;
+                    const int nv = W / VW;
+                    int c = lane;
+                    for (; c + 96 < nv; c += 128) {
+                        V a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
+                        fma_v(a0, xv[c], s, s);
+                        fma_v(a1, xv[c + 32], s, s);
+                        fma_v(a2, xv[c + 64], s, s);
+                        fma_v(a3, xv[c + 96], s, s);
+                    }
+                    for (; c < nv; c += 32) fma_v(row[c], xv[c], s, s);
+                    acc = (double)s;
                 }
+                if (F.use) {
+                    // lanes cover (level, alpha) pairs: 32/k levels per instruction when k <= 32
+                    A fa = 0;
+                    const int per = F.k <= 32 ? 32 / F.k : 1;
+                    const int kk = F.k <= 32 ? F.k : 32;
+                    for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
+                        const int l = l0 + lane / kk;
+                        if (lane / kk < per && l <= F.L) {
+                            const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
+                            const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
+                            const A *y = yh + (size_t)node * F.k;
+                            for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
+                        }
+                    }
+                    acc += (double)fa;
+                }
+                if (val)
+                    for (int c = rowptr[i] + lane; c < rowptr[i + 1]; c += 32) acc = fma(val[c], x[colidx[c]], acc);
             }
+            part[q] = acc;
         }
-        double acc = (double)((s0 + s1) + (s2 + s3)) + (double)fa;
-        if (val)
-            for (int c = rowptr[i] + lane; c < rowptr[i + 1]; c += 32) acc = fma(val[c], x[colidx[c]], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) Y[(size_t)r * ld + i] = acc;
+        // butterfly: after the xor-16 and xor-8 steps lane L holds row
+        // 2 (L >> 4 & 1) + (L >> 3 & 1) summed over 4 lanes; xor 4, 2, 1 finish it
+        const bool h16 = lane & 16, h8 = lane & 8;
+        double k0 = h16 ? part[2] : part[0], k1 = h16 ? part[3] : part[1];
+        const double o0 = h16 ? part[0] : part[2], o1 = h16 ? part[1] : part[3];
+        k0 += __shfl_xor_sync(0xffffffffu, o0, 16);
+        k1 += __shfl_xor_sync(0xffffffffu, o1, 16);
+        double kq = h8 ? k1 : k0;
+        kq += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+        kq += __shfl_xor_sync(0xffffffffu, kq, 4);
+        kq += __shfl_xor_sync(0xffffffffu, kq, 2);
+        kq += __shfl_xor_sync(0xffffffffu, kq, 1);
+        if ((lane & 7) == 0) {
+            const int i = g0 + warp + ((lane >> 4) * 2 + ((lane >> 3) & 1)) * nw;
+            if (i < e) Y[(size_t)r * ld + i] = kq;
+        }
     }
 }
 

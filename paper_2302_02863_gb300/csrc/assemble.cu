@@ -829,7 +829,13 @@ __global__ void k_selftest_math(int which, long long n, const double *__restrict
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = which == 0 ? fast_log(mt, x[i]) : fast_exp(mt, x[i]);
+    if (which <= 1) {
+        out[i] = which == 0 ? fast_log(mt, x[i]) : fast_exp(mt, x[i]);
+    } else {
+        double s, c;
+        sincospi_tab(mt, x[i], s, c);
+        out[i] = which == 2 ? c : s;
+    }
 }
 
 void launch_selftest_math(const MeshData &m, int which, long long n, const double *x, double *out, cudaStream_t st)

@@ -477,7 +477,7 @@ vfd_status vfd_op_rho(vfd_op_t h, double *rho, void *stream)
 vfd_status vfd_selftest_math(vfd_mesh_t mesh, int which, int64_t n, const double *x, double *out, void *stream)
 {
     VFD_API_BEGIN
-    VFD_REQUIRE(mesh && x && out && n >= 0 && (which == 0 || which == 1), VFD_EINVAL, "bad argument");
+    VFD_REQUIRE(mesh && x && out && n >= 0 && which >= 0 && which <= 3, VFD_EINVAL, "bad argument");
     VFD_REQUIRE(is_device_ptr(x) && is_device_ptr(out), VFD_EINVAL, "x and out must be device pointers");
     cudaStream_t st = (cudaStream_t)stream;
     launch_selftest_math(*mesh->m, which, n, x, out, st);

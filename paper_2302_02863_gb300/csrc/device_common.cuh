@@ -22,11 +22,17 @@ struct TrigTable {
     double c[3][5], s[3][5];
 };
 
-__device__ __forceinline__ void trig_table(int d, int kmax, const double *x, TrigTable &t)
+__device__ __forceinline__ void sincospi_tab(const double *__restrict__ mt, double x, double &s, double &c);
+
+// e^{i pi m x_j}, m = 0..kmax; with the math tables mt, sin/cos of pi x_j by
+// the table-driven scheme, else by sincospi
+__device__ __forceinline__ void trig_table(int d, int kmax, const double *x, TrigTable &t,
+                                           const double *mt = nullptr)
 {
     for (int j = 0; j < d; ++j) {
         double sj, cj;
-        sincospi(x[j], &sj, &cj);
+        if (mt) sincospi_tab(mt, x[j], sj, cj);
+        else sincospi(x[j], &sj, &cj);
         t.c[j][0] = 1.0;
         t.s[j][0] = 0.0;
         t.c[j][1] = cj;
@@ -114,12 +120,12 @@ __device__ __forceinline__ double field_terms(const DField &F, int d, const doub
 // s and log kappa at a point.  For P1 fields the point must lie in a cell
 // with vertex ids vid[0..d] and barycentric coordinates bary.
 __device__ __forceinline__ void fields2(const DField &Fs, const DField &Fk, int d, const double *x, const int *vid,
-                                        const double *bary, double &s, double &lk)
+                                        const double *bary, double &s, double &lk, const double *mt = nullptr)
 {
     TrigTable tab;
     bool need = (!Fs.nodal && Fs.nF > 0 && Fs.kmax <= 4) || (!Fk.nodal && Fk.nF > 0 && Fk.kmax <= 4);
     int km = max(Fs.nodal ? 0 : Fs.kmax, Fk.nodal ? 0 : Fk.kmax);
-    if (need) trig_table(d, km < 1 ? 1 : (km > 4 ? 4 : km), x, tab);
+    if (need) trig_table(d, km < 1 ? 1 : (km > 4 ? 4 : km), x, tab, mt);
     if (Fs.nodal) {
         s = 0.0;
         for (int a = 0; a <= d; ++a) s += bary[a] * Fs.vals[vid[a]];
@@ -157,10 +163,12 @@ namespace vfd {
 //   [129..257] log F_j
 //   [258..321] 2^(j/64)
 //   [322..325] ln2_hi, ln2_lo, ln2/64 hi, ln2/64 lo   (Cody-Waite splits)
+//   [326..453] cos(pi j/64), [454..581] sin(pi j/64), j = 0..127
 // Valid for normal positive x (log) and |y| < 700 (exp); relative error of a
 // few ulp (tests/test_gpu_math.py).
 // ---------------------------------------------------------------------------
-constexpr int MT_C = 0, MT_LOGF = 129, MT_EXP2 = 258, MT_CONST = 322, MT_SIZE = 326;
+constexpr int MT_C = 0, MT_LOGF = 129, MT_EXP2 = 258, MT_CONST = 322, MT_COSPI = 326, MT_SINPI = 454,
+              MT_SIZE = 582;
 
 __device__ __forceinline__ double fast_log(const double *__restrict__ mt, double x)
 {
@@ -199,6 +207,24 @@ __device__ __forceinline__ double fast_exp(const double *__restrict__ mt, double
     const double s = __ldg(mt + MT_EXP2 + (int)(ki & 63));
     const double v = fma(s, q * r, s);
     return __longlong_as_double(__double_as_longlong(v) + ((ki >> 6) << 52));
+}
+
+// sin and cos of pi x by the same table-driven scheme: x = j/64 + f with j the
+// nearest integer to 64 x and |f| <= 1/128, the table's values at pi j/64
+// combined with the Taylor series of cos and sin at theta = pi f (|theta| <=
+// pi/128; cos through theta^6, sin through theta^7, truncation below 4e-18)
+__device__ __forceinline__ void sincospi_tab(const double *__restrict__ mt, double x, double &s, double &c)
+{
+    const double big = 6755399441055744.0;   // 1.5 2^52
+    const double tj = fma(x, 64.0, big);
+    const double jf = tj - big;
+    const int j = (int)__double2loint(tj) & 127;
+    const double th = 3.141592653589793 * fma(jf, -1.0 / 64.0, x), u = th * th;
+    const double ct = fma(fma(fma(u, -1.0 / 720.0, 1.0 / 24.0), u, -0.5), u, 1.0);
+    const double st = th * fma(fma(fma(u, -1.0 / 5040.0, 1.0 / 120.0), u, -1.0 / 6.0), u, 1.0);
+    const double cj = __ldg(mt + MT_COSPI + j), sj = __ldg(mt + MT_SINPI + j);
+    c = fma(cj, ct, -sj * st);
+    s = fma(sj, ct, cj * st);
 }
 
 // gamma from r^2 and per-point exponent terms a = log(kappa)/2 (plus any log

@@ -52,7 +52,7 @@ std::vector<double> make_math_tables()
 {
     // tables of the table-driven log/exp (layout in device_common.cuh),
     // computed with the host C library in extended precision
-    std::vector<double> t(326, 0.0);
+    std::vector<double> t(582, 0.0);
     for (int j = 0; j <= 128; ++j) {
         double c = 1.0 / (1.0 + j / 128.0);
         t[j] = c;
@@ -70,6 +70,12 @@ std::vector<double> make_math_tables()
     t[323] = lo;
     t[324] = hi / 64.0;
     t[325] = lo / 64.0;
+    // cos and sin of pi j / 64, j = 0..127 (the table-driven sin/cos of pi x)
+    const long double pi = std::acos(-1.0L);
+    for (int j = 0; j < 128; ++j) {
+        t[326 + j] = (double)std::cos(pi * j / 64.0L);
+        t[454 + j] = (double)std::sin(pi * j / 64.0L);
+    }
     return t;
 }
 

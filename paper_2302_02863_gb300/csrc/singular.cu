@@ -174,11 +174,11 @@ __global__ void __launch_bounds__(256) k_singular2d(Sing2Params P, double *__res
                 if (side == 0) {
                     h[0] = xi * a[0]; h[1] = xi * a[1];
                     phys(Pv, h, x, bary);
-                    fields2(P.Fs, P.Fk, 2, x, pv, bary, sv, kv);
+                    fields2(P.Fs, P.Fk, 2, x, pv, bary, sv, kv, P.mt);
                 } else {
                     h[0] = xi * b[0]; h[1] = xi * b[1];
                     phys(Vy, h, x, bary);
-                    fields2(P.Fs, P.Fk, 2, x, vy, bary, sv, kv);
+                    fields2(P.Fs, P.Fk, 2, x, vy, bary, sv, kv, P.mt);
                 }
                 fs[off + t] = sv;
                 fk[off + t] = kv;

@@ -375,8 +375,9 @@ def vfd_op_timings(op):
 
 
 def vfd_selftest_math(mesh, which, x, out, stream=None):
-    """out = log(x) (which=0) or exp(x) (which=1) by the library's table-driven
-    FP64 routines (device tensors)."""
+    """out = log(x) (which=0), exp(x) (which=1), cos(pi x) (which=2) or
+    sin(pi x) (which=3) by the library's table-driven FP64 routines (device
+    tensors)."""
     _check(load().vfd_selftest_math(mesh.handle, int(which), x.numel(), _ptr(x), _ptr(out), _stream(stream)))
     return out
 

@@ -45,3 +45,20 @@ def test_exp_accuracy(mesh):
     ref = np.exp(x)
     rel = np.abs(y - ref) / ref
     assert np.max(rel) < 4e-16
+
+
+@pytest.mark.parametrize("which,fn", [(2, np.cos), (3, np.sin)])
+def test_trig_pi_accuracy(mesh, which, fn):
+    """The table-driven cos / sin of pi x used for the Fourier fields, against an
+    extended-precision reference (long double, pi from 4 atan 1)."""
+    rng = np.random.default_rng(2 + which)
+    x = np.concatenate([rng.uniform(-2.5, 2.5, 200000), rng.uniform(-40, 40, 20000),
+                        np.array([0.0, 0.5, 1.0, -1.0, 1.0 / 128, -1.0 / 128, 0.25, 2.0])])
+    X = torch.tensor(x, device="cuda")
+    Y = torch.empty_like(X)
+    vfd.vfd_selftest_math(mesh, which, X, Y)
+    torch.cuda.synchronize()
+    y = Y.cpu().numpy()
+    pi = 4 * np.arctan(np.longdouble(1))
+    ref = fn(pi * x.astype(np.longdouble)).astype(np.float64)
+    assert np.max(np.abs(y - ref)) < 4e-16
