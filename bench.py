@@ -324,6 +324,7 @@ def main():
     roof["algorithmic_bytes"] = leaf_bytes
     roof["launch_us"] = t_leaf * 1e6
     roof["traffic"] = _traffic_from_profile(args.workload, args.precision)
+    roof_apply = roof
     # the assembly's two largest kernels: FP64-pipe bound (their DRAM traffic is
     # negligible); throughput in kernel evaluations per second from the live
     # phase timings (mean over the timed assemblies)
@@ -332,6 +333,21 @@ def main():
         if info.get(ev) and ph.get(key):
             asm_k[name] = {"bound": "alu (FP64 pipe)", "unit": "Geval/s", "evals": info[ev], "ms": round(ph[key], 3),
                            "achieved": info[ev] / (ph[key] / 1e3) / 1e9}
+    # the step's largest kernel (launch list share) is the near-block build: an
+    # FP64-ALU roofline in kernel evaluations per second, peak = the measured FP64
+    # FMA issue rate (1.2538 TFLOP/s = 0.6269e12 FP64 instructions/s) divided by the
+    # FP64 instructions of one evaluation as implemented (2D: r^2 4, exponent 3,
+    # table-driven log 11, exp 12 = 30; the leaf contractions come on top)
+    if prec == vfd.VFD_FP64 and "k_near_build" in asm_k:
+        peak_ev = 0.6269e12 / 30 / 1e9
+        nb = asm_k["k_near_build"]
+        roof = {"bound": "alu", "kernel": "k_near_build (dense inadmissible leaf blocks, Sec. 5.2)",
+                "achieved": nb["achieved"], "peak": peak_ev, "unit": "Geval/s", "frac": nb["achieved"] / peak_ev,
+                "traffic": _profile_value("k_near_build", args.workload, args.precision, "dram_bytes_per_launch"),
+                "fp64_pipe_active_ncu": _profile_value("k_near_build", args.workload, args.precision,
+                                                       "fp64_pipe_active"),
+                "evals_per_launch": nb["evals"], "fp64_inst_per_eval": 30, "launch_ms": nb["ms"],
+                "peak_source": "measured FP64 FMA rate (profiles/fp_rates_gb300.md) / 30 FP64 instructions"}
 
     # apply: far projections, node sums, coupling, row kernel, far expansion
     apply_kernels = 5 if info["far_blocks"] > 0 else 1
@@ -369,7 +385,7 @@ def main():
             "assemble_ms": ph["total"], "phases_ms": {k2: round(v2, 3) for k2, v2 in ph.items()},
             "solve_ms": 1000 * tot / args.steps - ph["total"], "apply_us": t_apply * 1e6,
             "apply_dof_rhs_per_s": n / t_apply,
-            "roofline": roof, "assembly_kernels": asm_k, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_apply": roof_apply, "assembly_kernels": asm_k, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "batched_mixed_precision": batched,
             "batch_24_meshes": batch24,
@@ -556,6 +572,15 @@ def apply_mode(args, mesh, s, k, prm, prec, torch, vfd):
     torch.cuda.synchronize()
     print(json.dumps({"mode": "apply", "parts": args.parts, "precision": args.precision, "nrhs": args.nrhs,
                       "us_per_apply": 1000 * e0.elapsed_time(e1) / args.steps}), flush=True)
+
+
+def _profile_value(kernel, workload, precision, key):
+    """A figure from the committed ncu summary of a kernel (else null)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_{precision}.json")
+    try:
+        return json.load(open(p)).get(key)
+    except Exception:
+        return None
 
 
 def _traffic_from_profile(workload, precision):
