@@ -261,32 +261,55 @@ k_near_csr(int fl, int NR, const int *__restrict__ kb, const int *__restrict__ k
 
 // ---------------------------------------------------------------------------
 // 5. far expansion after the join: Y[i] += sum_l Ul^(l)[i] . yhat[ancestor_l(i)]
-//    (warp per row, lanes over (level, alpha))
+//    (a warp takes rows i0 + q nw, q = 0..3, of its block's 4 nw; lanes over
+//    (level, alpha); the four rows are reduced together by one xor butterfly)
 // ---------------------------------------------------------------------------
+constexpr int EXPAND_ROWS_PER_BLOCK = 16;   // 4 warps x 4 rows
+
 template <class T, class A>
 __global__ void __launch_bounds__(128)
 k_far_expand(FarView F, int fl, const int *__restrict__ leaf_of, const T *__restrict__ Ul, const A *__restrict__ yhat,
              int64_t hs, double *__restrict__ Y, int64_t ld, const int *skip)
 {
     if (skip && *skip) return;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31, r = blockIdx.y;
-    if (i >= F.N) return;
-    const int lf = leaf_of[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5, r = blockIdx.y;
+    const int i0 = blockIdx.x * 4 * nw + warp;
     const A *yh = yhat + (size_t)r * hs;
     const int per = F.k <= 32 ? 32 / F.k : 1;
     const int kk = F.k <= 32 ? F.k : 32;
-    A fa = 0;
-    for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
-        const int l = l0 + lane / kk;
-        if (lane / kk < per && l <= F.L) {
-            const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
-            const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
-            const A *y = yh + (size_t)node * F.k;
-            for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
+    double part[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q * nw;
+        A fa = 0;
+        if (i < F.N) {
+            const int lf = leaf_of[i];
+            for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
+                const int l = l0 + lane / kk;
+                if (lane / kk < per && l <= F.L) {
+                    const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
+                    const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
+                    const A *y = yh + (size_t)node * F.k;
+                    for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
+                }
+            }
         }
+        part[q] = (double)fa;
     }
-    double v = warp_sum((double)fa);
-    if (lane == 0) Y[(size_t)r * ld + i] += v;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    double k0 = h16 ? part[2] : part[0], k1 = h16 ? part[3] : part[1];
+    const double o0 = h16 ? part[0] : part[2], o1 = h16 ? part[1] : part[3];
+    k0 += __shfl_xor_sync(0xffffffffu, o0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, o1, 16);
+    double kq = h8 ? k1 : k0;
+    kq += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+    kq += __shfl_xor_sync(0xffffffffu, kq, 4);
+    kq += __shfl_xor_sync(0xffffffffu, kq, 2);
+    kq += __shfl_xor_sync(0xffffffffu, kq, 1);
+    if ((lane & 7) == 0) {
+        const int i = i0 + ((lane >> 4) * 2 + ((lane >> 3) & 1)) * nw;
+        if (i < F.N) Y[(size_t)r * ld + i] += kq;
+    }
 }
 
 // the row kernel stages a whole panel row of x in shared memory: allow more
@@ -344,7 +367,7 @@ static void apply_impl(const MeshData &m, OpData &op, int parts, const double *X
     if (F.use) {
         VFD_CUDA(cudaEventRecord(op.ev_join, op.side));
         VFD_CUDA(cudaStreamWaitEvent(st, op.ev_join, 0));
-        dim3 ge(cdiv(m.N, 4), nrhs);
+        dim3 ge(cdiv(m.N, EXPAND_ROWS_PER_BLOCK), nrhs);
         k_far_expand<T, A><<<ge, 128, 0, st>>>(F, fl, m.vleaf.p, Ul, yhat, hs, Y, ld, skip);
     }
     VFD_CUDA(cudaGetLastError());
@@ -498,7 +521,7 @@ void apply_one_stream(const MeshData &m, const OpData &op, const double *X, doub
                                            m.panel_w.p, m.panel_off.p, m.gcol.p, m.gcol_off.p, D, near ? 1 : 0,
                                            m.rowptr.p, m.colidx.p, op.valBM.p, Fn, Ul, yhat, hs, X, ld, Y, nullptr);
     if (F.use) {
-        dim3 ge(cdiv(m.N, 4), nrhs);
+        dim3 ge(cdiv(m.N, EXPAND_ROWS_PER_BLOCK), nrhs);
         k_far_expand<T, A><<<ge, 128, 0, st>>>(F, fl, m.vleaf.p, Ul, yhat, hs, Y, ld, nullptr);
     }
     VFD_CUDA(cudaGetLastError());
