@@ -207,15 +207,20 @@ k_near_csr(int fl, int NR, const int *__restrict__ kb, const int *__restrict__ k
                     T s = 0;
                     const V *row = (const V *)(D + P0 + (size_t)(i - b_leaf) * W);
                     const V *xv = (const V *)xg;
-                    const int nv = W / VW;
+                    // a warp-uniform trip count for the full 128-vector steps and no
+                    // unrolled copies of the ragged loops: predicated-off copies would
+                    // still take FP64 issue slots
+                    const int nv = W / VW, nfull = nv >> 7;
                     int c = lane;
-                    for (; c + 96 < nv; c += 128) {
+#pragma unroll 1
+                    for (int it = 0; it < nfull; ++it, c += 128) {
                         V a0 = row[c], a1 = row[c + 32], a2 = row[c + 64], a3 = row[c + 96];
                         fma_v(a0, xv[c], s, s);
                         fma_v(a1, xv[c + 32], s, s);
                         fma_v(a2, xv[c + 64], s, s);
                         fma_v(a3, xv[c + 96], s, s);
                     }
+#pragma unroll 1
                     for (; c < nv; c += 32) fma_v(row[c], xv[c], s, s);
                     acc = (double)s;
                 }
@@ -235,8 +240,10 @@ k_near_csr(int fl, int NR, const int *__restrict__ kb, const int *__restrict__ k
                     }
                     acc += (double)fa;
                 }
-                if (val)
+                if (val) {
+#pragma unroll 1
                     for (int c = rowptr[i] + lane; c < rowptr[i + 1]; c += 32) acc = fma(val[c], x[colidx[c]], acc);
+                }
             }
             part[q] = acc;
         }
