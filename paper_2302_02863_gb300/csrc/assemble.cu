@@ -390,9 +390,8 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
     const int b = P.tt_begin[node], e = P.tt_end[node];
     const int CH = 128;
     double *sx = sh;                  // CH * d
-    double *sw = sx + CH * d;         // CH
-    double *ss = sw + CH;             // CH
-    double *sl = ss + CH;             // CH
+    double *ss = sx + CH * d;         // CH: b = s/2 + d/4
+    double *sl = ss + CH;             // CH: a = log(kappa)/2 + log w
     int *sv = (int *)(sl + CH);       // CH * 3 vertex ids of the source cell
     for (int i0 = b; i0 < e; i0 += blockDim.x) {
         int i = i0 + threadIdx.x;
@@ -422,7 +421,6 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
                     int jd = P.st_perm[j0 + t];
                     for (int c = 0; c < d; ++c) sx[t * d + c] = P.qx[(size_t)c * P.nQ + jd];
                     // exponent terms of the source, its weight folded in: w gamma = exp(log w + ...)
-                    sw[t] = P.qw[jd];
                     ss[t] = fma(0.5, P.qs[jd], 0.25 * d);
                     sl[t] = fma(0.5, P.qlk[jd], fast_log(P.mt, P.qw[jd]));
                     int cell = P.qcell[jd];
@@ -542,7 +540,7 @@ void launch_density(const MeshData &m, OpData &op, cudaStream_t st)
     P.g9w = m.gl9_w.p;
     P.mt = m.mtab.p;
     P.rho = op.rho.p;
-    size_t shm = 128 * (d + 3) * sizeof(double) + 128 * 3 * sizeof(int);
+    size_t shm = 128 * (d + 2) * sizeof(double) + 128 * 3 * sizeof(int);
     k_rho_points<<<m.tt.nleaf, 128, shm, st>>>(P);
     VFD_CUDA(cudaGetLastError());
     VFD_CUDA(cudaStreamSynchronize(st));   // yt is released on return
