@@ -40,6 +40,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -100,7 +101,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the samples are summarised into the JSON line; the raw CSV goes to a
+        # scratch directory (VFD_CLOCKS_DIR if set)
+        d = os.environ.get("VFD_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"vfd_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
