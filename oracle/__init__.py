@@ -127,7 +127,9 @@ class Assembled:
 
 def assemble(mesh, s, logk, s_bar=0.9, n_sing=3, tail=0, R=1.1, want_full=False):
     """Oracle assembly by the split B + K + M (route 2) and, if requested, by
-    definition over all element pairs (route 1)."""
+    definition over all element pairs (route 1).  In 3D (tetrahedra) only the
+    separated parts K, rho and M are assembled: the paper gives no singular
+    rules for tetrahedron pairs, so B is returned as zeros (reading R20)."""
     L = lib()
     X = np.ascontiguousarray(mesh.coords, dtype=np.float64)
     T = np.ascontiguousarray(mesh.cells, dtype=np.int32)
@@ -138,7 +140,7 @@ def assemble(mesh, s, logk, s_bar=0.9, n_sing=3, tail=0, R=1.1, want_full=False)
     B = np.zeros((N, N))
     K = np.zeros((N, N))
     Mw = np.zeros((N, N))
-    nq = 3
+    nq = 4 if mesh.d == 3 else 3   # element-rule points per cell (R3, R20)
     nqi = int(inn.sum()) * nq
     rho = np.zeros(nqi)
     Af = np.zeros((mesh.n_vert, mesh.n_vert)) if want_full else None

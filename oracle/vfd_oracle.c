@@ -37,6 +37,12 @@
  *       relative coordinate z = zeta^(1/(2-2 sbar)); adjacent cells with
  *       (xi, xi*eta) / (xi*eta, xi) and xi = zeta^(1/(3-2 sbar)), the same
  *       construction as the 2D vertex case (exponent of zeta >= 0).
+ *   R20 3D (tetrahedra): the element rule is the symmetric 4-point degree-2
+ *       rule (barycentric (a,b,b,b) and permutations, a = (5+3 sqrt 5)/20,
+ *       b = (5-sqrt 5)/20, weights |tau|/4); the paper gives no singular
+ *       rules for tetrahedron pairs, so in 3D only the separated parts K, rho
+ *       and M are assembled (B = 0; route 1, the tail, the gradient and single
+ *       rows refuse d = 3).
  *
  * Reference triangle: (0,0),(1,0),(1,1) with basis phi0 = 1-x1,
  * phi1 = x1-x2, phi2 = x2 (Sec. 4).  Reference interval [0,1] with
@@ -185,19 +191,40 @@ static int shared_count(const omesh *m, int c1, int c2)
     return n;
 }
 
+/* barycentric coordinates are stored with stride NB (entries beyond d are 0) */
+#define NB 4
+
 static double cell_measure(const omesh *m, int c)
 {
     int nv = m->d + 1;
     const int *t = m->T + c * nv;
     if (m->d == 1) return fabs(m->X[t[1]] - m->X[t[0]]);
+    if (m->d == 3) {
+        /* |det(p1 - p0, p2 - p0, p3 - p0)| / 6 */
+        const double *p0 = m->X + 3 * t[0], *p1 = m->X + 3 * t[1], *p2 = m->X + 3 * t[2], *p3 = m->X + 3 * t[3];
+        double a[3], b[3], e[3];
+        for (int i = 0; i < 3; ++i) { a[i] = p1[i] - p0[i]; b[i] = p2[i] - p0[i]; e[i] = p3[i] - p0[i]; }
+        double det = a[0] * (b[1] * e[2] - b[2] * e[1]) - a[1] * (b[0] * e[2] - b[2] * e[0]) + a[2] * (b[0] * e[1] - b[1] * e[0]);
+        return fabs(det) / 6.0;
+    }
     const double *p0 = m->X + 2 * t[0], *p1 = m->X + 2 * t[1], *p2 = m->X + 2 * t[2];
     return 0.5 * fabs((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p1[1] - p0[1]) * (p2[0] - p0[0]));
 }
 
 /* element rule (R3): nq points per cell, barycentric coordinates bq[q][a]
  * w.r.t. the cell's stored vertex order, weights relative to the measure. */
-static int elem_rule(int d, double bq[][3], double *wq)
+static int elem_rule(int d, double bq[][NB], double *wq)
 {
+    memset(bq, 0, sizeof(double) * NB * NB);
+    if (d == 3) {
+        /* R20: the symmetric 4-point rule, exact for quadratics on a tetrahedron */
+        const double a = (5.0 + 3.0 * sqrt(5.0)) / 20.0, b = (5.0 - sqrt(5.0)) / 20.0;
+        for (int q = 0; q < 4; ++q) {
+            for (int k = 0; k < 4; ++k) bq[q][k] = (k == q) ? a : b;
+            wq[q] = 0.25;
+        }
+        return 4;
+    }
     if (d == 2) {
         for (int q = 0; q < 3; ++q) {
             for (int a = 0; a < 3; ++a) bq[q][a] = (a == q) ? 2.0 / 3.0 : 1.0 / 6.0;
@@ -524,13 +551,13 @@ typedef struct {
     double *w;             /* n, weight incl. measure */
     double *s, *lk;        /* field values */
     int *cell;             /* n */
-    double *bary;          /* n*3 barycentric w.r.t. stored cell vertex order */
+    double *bary;          /* n*NB barycentric w.r.t. stored cell vertex order */
 } oquad;
 
 static void build_quad(const omesh *m, const ofield *fs, const ofield *fk, oquad *Q)
 {
     int d = m->d, nv = d + 1;
-    double bq[3][3], wq[3];
+    double bq[NB][NB], wq[NB];
     int nq = elem_rule(d, bq, wq);
     Q->n = m->C * nq;
     Q->x = malloc(sizeof(double) * Q->n * d);
@@ -538,7 +565,7 @@ static void build_quad(const omesh *m, const ofield *fs, const ofield *fk, oquad
     Q->s = malloc(sizeof(double) * Q->n);
     Q->lk = malloc(sizeof(double) * Q->n);
     Q->cell = malloc(sizeof(int) * Q->n);
-    Q->bary = malloc(sizeof(double) * Q->n * 3);
+    Q->bary = malloc(sizeof(double) * Q->n * NB);
     for (int c = 0; c < m->C; ++c) {
         double meas = cell_measure(m, c);
         const int *t = m->T + c * nv;
@@ -551,7 +578,7 @@ static void build_quad(const omesh *m, const ofield *fs, const ofield *fk, oquad
             }
             Q->w[id] = wq[q] * meas;
             Q->cell[id] = c;
-            for (int a = 0; a < 3; ++a) Q->bary[id * 3 + a] = bq[q][a];
+            for (int a = 0; a < NB; ++a) Q->bary[id * NB + a] = bq[q][a];
             Q->s[id] = field_eval(fs, d, Q->x + id * d, t, bq[q]);
             Q->lk[id] = field_eval(fk, d, Q->x + id * d, t, bq[q]);
         }
@@ -612,6 +639,7 @@ int oracle_assemble(int d, int M, int C, const double *X, const int *T, const un
     int N = oracle_dofs(d, M, C, T, in, dof);
     double gx[64], gw[64];
     if (ns < 1 || ns > 64) { free(dof); return -1; }
+    if (d == 3 && (Afull || tail)) { free(dof); return -1; }   /* R20: no singular rules, no 3D tail */
     oracle_gauss01(ns, gx, gw);
     if (B) memset(B, 0, sizeof(double) * N * N);
     if (K) memset(K, 0, sizeof(double) * N * N);
@@ -651,6 +679,7 @@ int oracle_assemble(int d, int M, int C, const double *X, const int *T, const un
                 int c2 = list[k];
                 mark[c2] = 0;
                 if (c2 < c) continue;                     /* unordered pairs once */
+                if (d == 3) continue;                     /* R20: B is not assembled in 3D */
                 if (!in[c] && !in[c2]) continue;          /* U,V vanish on ext x ext */
                 opair pp; int loc[5]; double L[25];
                 int nl = make_pair(&m, c, c2, &pp, loc);
@@ -707,7 +736,7 @@ int oracle_assemble(int d, int M, int C, const double *X, const int *T, const un
             for (int c2 = 0; c2 < C; ++c2) {
                 if (touch[c2]) continue;
                 const int *u = T + c2 * nv;
-                double G[3][3];
+                double G[NB][NB];
                 for (int q = 0; q < nq; ++q)
                     for (int q2 = 0; q2 < nq; ++q2) {
                         int iq = c * nq + q, jq = c2 * nq + q2;
@@ -716,13 +745,13 @@ int oracle_assemble(int d, int M, int C, const double *X, const int *T, const un
                     }
                 if (K && in[c2]) {
                     /* K_ij += -2 sum_q sum_q' w w' psi_i(q) psi_j(q') gamma */
-                    double loc[3][3];
+                    double loc[NB][NB];
                     for (int a = 0; a < nv; ++a)
                         for (int b = 0; b < nv; ++b) {
                             double acc = 0.0;
                             for (int q = 0; q < nq; ++q)
                                 for (int q2 = 0; q2 < nq; ++q2)
-                                    acc += Q.bary[(c * nq + q) * 3 + a] * Q.bary[(c2 * nq + q2) * 3 + b] * G[q][q2];
+                                    acc += Q.bary[(c * nq + q) * NB + a] * Q.bary[(c2 * nq + q2) * NB + b] * G[q][q2];
                             loc[a][b] = -2.0 * acc;
                         }
 #pragma omp critical
@@ -737,16 +766,16 @@ int oracle_assemble(int d, int M, int C, const double *X, const int *T, const un
                      * of c and c2 (when c2 is interior the reverse order is
                      * visited from c2 itself, so count once there) */
                     double wgt = in[c2] ? 1.0 : 2.0;
-                    int vids[6];
+                    int vids[2 * NB];
                     for (int a = 0; a < nv; ++a) { vids[a] = t[a]; vids[nv + a] = u[a]; }
-                    double loc[6][6];
+                    double loc[2 * NB][2 * NB];
                     memset(loc, 0, sizeof(loc));
                     for (int q = 0; q < nq; ++q)
                         for (int q2 = 0; q2 < nq; ++q2) {
-                            double diff[6];
+                            double diff[2 * NB];
                             for (int a = 0; a < nv; ++a) {
-                                diff[a] = Q.bary[(c * nq + q) * 3 + a];
-                                diff[nv + a] = -Q.bary[(c2 * nq + q2) * 3 + a];
+                                diff[a] = Q.bary[(c * nq + q) * NB + a];
+                                diff[nv + a] = -Q.bary[(c2 * nq + q2) * NB + a];
                             }
                             for (int i = 0; i < 2 * nv; ++i)
                                 for (int j = 0; j < 2 * nv; ++j) loc[i][j] += G[q][q2] * diff[i] * diff[j];
@@ -776,7 +805,7 @@ int oracle_assemble(int d, int M, int C, const double *X, const int *T, const un
                     double acc = 0.0;
                     for (int q = 0; q < nq; ++q) {
                         int iq = c * nq + q;
-                        acc += Q.w[iq] * Q.bary[iq * 3 + a] * Q.bary[iq * 3 + b] * rho_all[iq];
+                        acc += Q.w[iq] * Q.bary[iq * NB + a] * Q.bary[iq * NB + b] * rho_all[iq];
                     }
                     Mw[(size_t)i * N + j] += 2.0 * acc;
                 }
@@ -951,7 +980,7 @@ int oracle_grad(int d, int M, int C, const double *X, const int *T, const unsign
     double sbar = params[0];
     int ns = (int)params[1], tail = (int)params[2];
     int nv = d + 1;
-    if (!snodal || !knodal || tail != 0 || ns < 1 || ns > 64 || nrhs < 1) return -1;
+    if (!snodal || !knodal || tail != 0 || ns < 1 || ns > 64 || nrhs < 1 || d == 3) return -1;
     int *dof = malloc(sizeof(int) * M);
     int N = oracle_dofs(d, M, C, T, in, dof);
     double gx[64], gw[64];
@@ -968,7 +997,7 @@ int oracle_grad(int d, int M, int C, const double *X, const int *T, const unsign
             double u = 0.0, l = 0.0;
             for (int a = 0; a < nv; ++a) {
                 int i = dof[t[a]];
-                if (i >= 0) { u += Q.bary[iq * 3 + a] * U[(size_t)r * N + i]; l += Q.bary[iq * 3 + a] * Lam[(size_t)r * N + i]; }
+                if (i >= 0) { u += Q.bary[iq * NB + a] * U[(size_t)r * N + i]; l += Q.bary[iq * NB + a] * Lam[(size_t)r * N + i]; }
             }
             Uq[(size_t)r * Q.n + iq] = u;
             Lq[(size_t)r * Q.n + iq] = l;
@@ -1064,7 +1093,7 @@ int oracle_grad(int d, int M, int C, const double *X, const int *T, const unsign
                         double ts = 2.0 * G * log(r) * (mu - lu);
                         double tk = G * (lu - mu);
                         for (int a = 0; a < nv; ++a) {
-                            double bq = Q.bary[iq * 3 + a], bq2 = Q.bary[jq * 3 + a];
+                            double bq = Q.bary[iq * NB + a], bq2 = Q.bary[jq * NB + a];
                             gS[t[a]] += ts * bq; gS[u[a]] += ts * bq2;
                             gK[t[a]] += tk * bq; gK[u[a]] += tk * bq2;
                         }
@@ -1107,7 +1136,7 @@ int oracle_apply_rows(int d, int M, int C, const double *X, const int *T, const 
     int ns = (int)params[1], tail = (int)params[2];
     double R = params[3];
     int nv = d + 1;
-    if (ns < 1 || ns > 64) return -1;
+    if (ns < 1 || ns > 64 || d == 3) return -1;
     int *dof = malloc(sizeof(int) * M);
     int N = oracle_dofs(d, M, C, T, in, dof);
     int *vert = malloc(sizeof(int) * (N > 0 ? N : 1));
@@ -1121,7 +1150,7 @@ int oracle_apply_rows(int d, int M, int C, const double *X, const int *T, const 
     for (int iq = 0; iq < Q.n; ++iq) {
         const int *t = T + Q.cell[iq] * nv;
         double v = 0.0;
-        for (int a = 0; a < nv; ++a) if (dof[t[a]] >= 0) v += Q.bary[iq * 3 + a] * x[dof[t[a]]];
+        for (int a = 0; a < nv; ++a) if (dof[t[a]] >= 0) v += Q.bary[iq * NB + a] * x[dof[t[a]]];
         xq[iq] = v;
     }
     int *vdeg = calloc(M + 1, sizeof(int));
@@ -1187,7 +1216,7 @@ int oracle_apply_rows(int d, int M, int C, const double *X, const int *T, const 
                         }
                     }
                     if (tail) rho += oracle_tail(d, Q.x + iq * d, Q.s[iq], exp(Q.lk[iq]), R);
-                    double wpsi = Q.w[iq] * Q.bary[iq * 3 + ai];
+                    double wpsi = Q.w[iq] * Q.bary[iq * NB + ai];
                     acc += -2.0 * wpsi * sk + 2.0 * wpsi * xq[iq] * rho;
                 }
                 for (int a = 0; a < nv; ++a)
@@ -1221,7 +1250,7 @@ int oracle_load(int d, int M, int C, const double *X, const int *T, const unsign
             if (i < 0) continue;
             for (int b = 0; b < nv; ++b) {
                 /* int_tau lambda_a lambda_b = |tau| (1+delta_ab) d! / (d+2)! */
-                double mab = (d == 2) ? meas * (a == b ? 2.0 : 1.0) / 12.0 : meas * (a == b ? 2.0 : 1.0) / 6.0;
+                double mab = meas * (a == b ? 2.0 : 1.0) / (d == 3 ? 20.0 : d == 2 ? 12.0 : 6.0);
                 F[i] += mab * fnodal[t[b]];
             }
         }

@@ -221,6 +221,53 @@ def square_mesh_for_dofs(n_dofs: int, jitter: float = 0.2, seed: int = 0) -> Mes
 # ----------------------------------------------------------------------------
 # field descriptors
 # ----------------------------------------------------------------------------
+def kuhn_ball_mesh(n: int, L: float = 1.1, R_in: float = 1.0, R_out: float = 1.1) -> Mesh:
+    """Tetrahedral mesh of a ball: the cube [-L, L]^3 cut into n^3 cubes, each
+    cube into the 6 Kuhn tetrahedra around its main diagonal (conforming
+    across cubes); cells whose centroid lies in |c| < R_out are kept (Omega),
+    those with |c| < R_in are interior (Omega_i, a polytope approximating the
+    unit ball).  Vertices are renumbered to the ones used; every tetrahedron
+    has positive orientation."""
+    h = 2.0 * L / n
+    g = np.arange(n + 1) * h - L
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    coords = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+    def vid(i, j, k):
+        return (i * (n + 1) + j) * (n + 1) + k
+
+    # the 6 monotone lattice paths from (0,0,0) to (1,1,1)
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    I, J, K = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    I, J, K = I.ravel(), J.ravel(), K.ravel()
+    cells = []
+    for p in perms:
+        o = np.zeros((len(I), 3), dtype=np.int64)
+        vs = [vid(I, J, K)]
+        for ax in p:
+            o[:, ax] += 1
+            vs.append(vid(I + o[:, 0], J + o[:, 1], K + o[:, 2]))
+        cells.append(np.stack(vs, axis=1))
+    cells = np.concatenate(cells, axis=0)
+    cen = coords[cells].mean(axis=1)
+    r = np.linalg.norm(cen, axis=1)
+    keep = r < R_out
+    cells, r = cells[keep], r[keep]
+    inter = (r < R_in).astype(np.uint8)
+    used = np.unique(cells)
+    remap = -np.ones(len(coords), dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    coords = coords[used]
+    cells = remap[cells]
+    # positive orientation
+    P = coords[cells]
+    det = np.einsum("ij,ij->i", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))
+    neg = det < 0
+    cells[neg, 2], cells[neg, 3] = cells[neg, 3].copy(), cells[neg, 2].copy()
+    return Mesh(3, coords.astype(np.float64), cells.astype(np.int32), inter, name=f"kuhn_ball_{n}",
+                meta={"L": L, "R_in": R_in, "R_out": R_out, "h": h})
+
+
 @dataclass
 class Field:
     """A scalar field on R^d, value = squash(c0 + sum of terms).
