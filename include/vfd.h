@@ -239,11 +239,12 @@ vfd_status vfd_apply_noalloc(vfd_op_t op, const double *X, double *Y, int64_t nr
  * initial guess on entry.  Converged when ||F - A U|| <= rtol ||F||.
  * iters, relres: host arrays of nrhs entries (may be NULL).
  * VFD_FP64 operators: FP64 CG, column by column.  VFD_FP32 / VFD_BF16
- * operators: iterative refinement, the residual F - A U in FP64 with the FP64
- * operator; with nrhs = 1 the inner CG uses FP32 K; with nrhs > 1 all columns
- * are solved together by a batched inner CG in FP32 vectors whose near-field
- * products run on the tensor cores (TF32 or BF16) -- this needs leaves of at
- * most 64 DoFs.  iters reports the inner CG iterations.
+ * operators: the residual F - A U in FP64 with the FP64 operator; with
+ * nrhs = 1 iterative refinement around an inner CG with FP32 K; with nrhs > 1
+ * all columns are solved together as in vfd_batch_solve (a batched CG in
+ * FP32 vectors whose near-field products run on the tensor cores, TF32 or
+ * BF16, with FP64 reliable updates) -- this needs leaves of at most 64 DoFs.
+ * iters reports the inner CG iterations.
  * Returns VFD_ENOCONV when some column did not converge in max_it. */
 vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int64_t ld, double rtol,
                      int max_it, int *iters, double *relres, void *stream);
@@ -254,7 +255,7 @@ vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *str
 
 /* Batch of operators (meshes) for the batched low-precision path: one
  * launch per stage over a global queue of work items of all meshes, and one
- * batched refinement solve with scalars per (mesh, column).  The paper solves
+ * batched mixed-precision solve with scalars per (mesh, column).  The paper solves
  * one mesh at a time; the batch is a throughput construction on top of the
  * per-mesh operators of Sec. 5-7.
  * ops: nops operators, all VFD_FP32 or all VFD_BF16, leaves of at most 64
@@ -270,14 +271,21 @@ vfd_status vfd_batch_create(const vfd_op_t *ops, int nops, vfd_batch_t *out);
 vfd_status vfd_batch_apply(vfd_batch_t batch, const double *const *X, double *const *Y, const int64_t *ld,
                            int64_t nrhs, void *stream);
 
-/* Solve A_m U_m = F_m for every mesh (nrhs columns each) by iterative
- * refinement: FP64 residuals with each mesh's FP64 operator, inner batched
- * CG on the low-precision operators of all meshes at once (per-(mesh,
- * column) scalars, inner tolerance 1e-4), until ||F - A U|| <= rtol ||F||
- * for every column of every mesh.  F, U: host arrays of nops device
- * pointers (U holds the initial guess).  iters, relres: host, nops x nrhs
- * (mesh-major), may be NULL.  VFD_ENOCONV when max_it inner iterations did
- * not suffice (U holds the last iterate). */
+/* Solve A_m U_m = F_m for every mesh (nrhs columns each): one CG on the
+ * low-precision operators of all meshes at once (FP32 vectors, per-(mesh,
+ * column) scalars) for the correction to U, with reliable updates per mesh:
+ * once every still-iterating column of a mesh has cut its recursive residual
+ * 0.03-fold, the mesh's correction is added to U in FP64 and its residual is
+ * replaced by the true F - A U computed with its FP64 operator, the search
+ * direction continuing (or restarting where the two residuals disagree).
+ * The low-precision operators are made exact on constant vectors by a
+ * diagonal compensation computed on their first batched use.  Stops when
+ * ||F - A U|| <= rtol ||F|| for every column of every mesh.  F, U: host
+ * arrays of nops device pointers (U holds the initial guess).  iters,
+ * relres: host, nops x nrhs (mesh-major), may be NULL; iters = the inner
+ * iterations run until the column's mesh converged.  VFD_ENOCONV when max_it
+ * inner iterations did not suffice or a residual became non-finite (U holds
+ * the last iterate). */
 vfd_status vfd_batch_solve(vfd_batch_t batch, const double *const *F, double *const *U, const int64_t *ld,
                            int64_t nrhs, double rtol, int max_it, int *iters, double *relres, void *stream);
 

@@ -327,7 +327,8 @@ def vfd_batch_apply(batch, Xs, Ys, stream=None):
 
 
 def vfd_batch_solve(batch, Fs, Us, rtol=1e-8, max_it=100000, stream=None, raise_on_noconv=False):
-    """Batched refinement solve; returns (status, iters (nmesh, nrhs), relres (nmesh, nrhs))."""
+    """Batched mixed-precision solve (CG with FP64 reliable updates); returns
+    (status, iters (nmesh, nrhs), relres (nmesh, nrhs))."""
     fp, lds, nrhs = _blocks(batch, Fs)
     up, _, _ = _blocks(batch, Us)
     n = len(Fs) * nrhs
