@@ -41,8 +41,8 @@
  *       rule (barycentric (a,b,b,b) and permutations, a = (5+3 sqrt 5)/20,
  *       b = (5-sqrt 5)/20, weights |tau|/4); the paper gives no singular
  *       rules for tetrahedron pairs, so in 3D only the separated parts K, rho
- *       and M are assembled (B = 0; route 1, the tail, the gradient and single
- *       rows refuse d = 3).
+ *       and M are assembled (B = 0; single-row applies give rows of K + M;
+ *       route 1, the tail and the gradient refuse d = 3).
  *
  * Reference triangle: (0,0),(1,0),(1,1) with basis phi0 = 1-x1,
  * phi1 = x1-x2, phi2 = x2 (Sec. 4).  Reference interval [0,1] with
@@ -1136,7 +1136,7 @@ int oracle_apply_rows(int d, int M, int C, const double *X, const int *T, const 
     int ns = (int)params[1], tail = (int)params[2];
     double R = params[3];
     int nv = d + 1;
-    if (ns < 1 || ns > 64 || d == 3) return -1;
+    if (ns < 1 || ns > 64 || (d == 3 && tail)) return -1;
     int *dof = malloc(sizeof(int) * M);
     int N = oracle_dofs(d, M, C, T, in, dof);
     int *vert = malloc(sizeof(int) * (N > 0 ? N : 1));
@@ -1168,9 +1168,10 @@ int oracle_apply_rows(int d, int M, int C, const double *X, const int *T, const 
         for (int r = 0; r < nrows; ++r) {
             const int vi = vert[rows[r]];
             double acc = 0.0;
-            /* ---- B: the unordered touching pairs {c, c2} with vi a local DoF ---- */
+            /* ---- B: the unordered touching pairs {c, c2} with vi a local DoF
+             * (none in 3D: R20) ---- */
             int np = 0;
-            for (int k = vdeg[vi]; k < vdeg[vi + 1]; ++k) {
+            for (int k = vdeg[vi]; k < vdeg[vi + 1] && d != 3; ++k) {
                 int c = vcell[k];
                 const int *t = T + c * nv;
                 for (int a = 0; a < nv; ++a)

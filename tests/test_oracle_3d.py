@@ -10,7 +10,8 @@ not assembled in 3D).
   quadratics exactly) -- closed forms;
 * a variable kernel (s = 0.3, a 3D Fourier log kappa) against a numpy brute
   force of the same sums written from the definitions;
-* the P1 load in 3D; refusals of what needs singular rules.
+* single-row applies (rows of K + M) and the P1 load in 3D; refusals of what
+  needs singular rules or the 2D tail.
 """
 import math
 
@@ -130,9 +131,23 @@ def test_load_3d(ball):
     assert np.abs(Fx - ex).max() <= 1e-13 * e1.max()
 
 
+def test_single_rows_3d(ball):
+    """oracle.apply_rows in 3D gives the rows of K + M (B = 0) of the dense assembly."""
+    m = ball
+    s, k = synth.const_field(0.4), synth.random_fourier_field(11, 0.5, d=3)
+    ref = oracle.assemble(m, s, k, s_bar=0.9)
+    x = np.random.default_rng(5).standard_normal(ref.N)
+    rows = np.arange(0, ref.N, 3)
+    y = oracle.apply_rows(m, s, k, x, rows, s_bar=0.9)
+    yd = (ref.K + ref.M) @ x
+    assert np.abs(y - yd[rows]).max() <= 1e-12 * np.abs(yd).max()
+
+
 def test_3d_refuses_what_needs_singular_rules(ball):
     s, k = synth.const_field(0.3), synth.const_field(0.0)
     with pytest.raises(RuntimeError):
         oracle.assemble(ball, s, k, want_full=True)
     with pytest.raises(RuntimeError):
         oracle.assemble(ball, s, k, tail=1)
+    with pytest.raises(ValueError):
+        oracle.apply_rows(ball, s, k, np.zeros(oracle.dofs(ball)[1]), [0], tail=1)
