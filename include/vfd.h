@@ -172,7 +172,7 @@ vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info);
  * (Sec. 4), density rho (Sec. 6.2) plus tail, and M (eq. e:m).
  *   s_bar: quadrature parameter of the singular rules (Sec. 4), 0 <= s <= s_bar < 1
  *          must hold at every evaluation point unless VFD_ASSEMBLE_UNCHECKED.
- *   precision: VFD_FP64 or VFD_FP32.  stream: cudaStream_t.
+ *   precision: VFD_FP64, VFD_FP32 or VFD_BF16.  stream: cudaStream_t.
  * Blocks the host once to read the field check.
  * Errors: VFD_EINVAL (field out of range, bad s_bar), VFD_EUNSUPPORTED
  * (nodal field with a low-rank part; tail with non-constant fields),
@@ -215,7 +215,8 @@ vfd_status vfd_apply_parts(vfd_op_t op, int parts, const double *X, double *Y, i
  *    host pointers are rejected with VFD_EINVAL.
  *  - The far-field scratch lives in one file-scope device array of
  *    VFD_APPLY_NOALLOC_SCRATCH_BYTES bytes per device.  An operator and nrhs
- *    whose scratch, 8 or 4 bytes (VFD_FP64 or VFD_FP32 operators) times
+ *    whose scratch, 8 bytes (VFD_FP64 operators) or 4 bytes (VFD_FP32 and
+ *    VFD_BF16 operators) times
  *    nrhs x (2 x tree nodes x rank + far levels x leaves x rank), rounded up
  *    to 256-byte pieces, exceeds that size is rejected with VFD_EINVAL and a
  *    message that gives both sizes; nothing is launched then.

@@ -404,7 +404,7 @@ void release_streams(OpData &op)
     }
 }
 
-// parts: VFD_PART_* mask; lowp: use the FP32 copies of K (VFD_FP32 operators)
+// parts: VFD_PART_* mask; lowp: use the FP32 copies of K (VFD_FP32 and VFD_BF16 operators)
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                     bool lowp, cudaStream_t st, const int *skip)
 {
@@ -456,7 +456,9 @@ void apply_k_with(const MeshData &m, OpData &op, const double *Ul, const double 
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                  cudaStream_t st)
 {
-    apply_parts_ex(m, op, parts, X, Y, nrhs, ld, op.precision == VFD_FP32, st, nullptr);
+    // VFD_FP32 and VFD_BF16 operators both keep FP32 copies of K for the
+    // column-by-column low-precision apply (BF16 is used by the batched path only)
+    apply_parts_ex(m, op, parts, X, Y, nrhs, ld, op.precision != VFD_FP64, st, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -539,7 +541,7 @@ void apply_one_stream(const MeshData &m, const OpData &op, const double *X, doub
 void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
                    cudaStream_t st)
 {
-    const bool lowp = op.precision == VFD_FP32;
+    const bool lowp = op.precision != VFD_FP64;   // K in FP32 for VFD_FP32 and VFD_BF16 operators
     const size_t es = lowp ? sizeof(float) : sizeof(double);
     const int nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
     const size_t nh = (size_t)m.kt.nnode * m.k * nrhs;

@@ -1,0 +1,33 @@
+// Shared declarations of the batched multi-RHS low-precision apply
+// (batched.cu, near_tc.cu, bsolve.cu): the per-mesh descriptor table and
+// the near-panel work items.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace vfd {
+
+constexpr int RT = 64;   // RHS per tile
+
+// one operator of a batch, as the kernels see it (device-resident table)
+struct MrMesh {
+    int N, fl, k, L, lmin, nlev, nleaf, nnode, has_near, has_far;
+    long long xoff;   // first row of this mesh in the batch vectors
+    const int *kb, *ke, *pw, *gcol, *goff, *rowptr, *colidx, *fptr, *fcol;
+    const int64_t *poff;
+    const void *D, *Ul, *S;   // near panels, level bases, coupling blocks (FP32 or BF16)
+    const float *val;         // B + M in FP32 (CSR)
+    float *part, *xhat, *yhat;   // far-field workspaces of this mesh
+};
+
+// one (mesh, leaf) work item of the near-panel kernel, everything it needs in one load
+struct NearItem {
+    const void *D;       // the leaf's panel (row stride W)
+    const int *gcol;     // the panel's gather columns (mesh-local DoFs, -1 = padding)
+    int row0;            // first row of the leaf in the batch vectors
+    int na, W;           // leaf rows, panel width (multiple of 8)
+    int xoff;            // first row of the mesh in the batch vectors
+    int mesh, pad;
+};
+
+}  // namespace vfd

@@ -16,35 +16,45 @@ namespace vfd {
 
 void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w)
 {
-    // Golub-Welsch would need an eigen-solver; Newton on the three-term
-    // recurrence of P_n is enough for n <= 64.
+    // Golub-Welsch form of the rule: the nodes on [-1,1] are the eigenvalues of
+    // the symmetric tridiagonal Jacobi matrix of the Legendre recurrence (zero
+    // diagonal, off-diagonal b_k = k / sqrt(4k^2 - 1)), found one by one by
+    // bisection on the Sturm count (number of negative pivots of J - t I); the
+    // weights are the Christoffel numbers 1 / sum_{k<n} q_k(t)^2 with q_k the
+    // Legendre polynomials orthonormal on [-1,1].  Mapped to [0,1] at the end.
     x.assign(n, 0.0);
     w.assign(n, 0.0);
+    std::vector<double> b2(n, 0.0);
+    for (int k = 1; k < n; ++k) b2[k] = (double)k * k / (4.0 * k * k - 1.0);
+    auto below = [&](double t) {   // eigenvalues of J smaller than t
+        int cnt = 0;
+        double q = -t;
+        for (int k = 0; k < n; ++k) {
+            if (k > 0) q = -t - b2[k] / q;
+            if (q == 0.0) q = -1e-300;   // a zero pivot counts as negative (t just above it)
+            if (q < 0.0) ++cnt;
+        }
+        return cnt;
+    };
     for (int i = 0; i < n; ++i) {
-        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double pm = 1.0, pc = z;
-            for (int k = 2; k <= n; ++k) {
-                double pn = ((2.0 * k - 1.0) * z * pc - (k - 1.0) * pm) / k;
-                pm = pc;
-                pc = pn;
-            }
-            if (n == 1) { pc = z; pm = 1.0; }
-            dp = n * (z * pc - pm) / (z * z - 1.0);
-            double dz = pc / dp;
-            z -= dz;
-            if (std::fabs(dz) < 1e-16) break;
+        double lo = -1.0, hi = 1.0;   // the spectrum lies inside (-1, 1)
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (below(mid) > i) hi = mid;
+            else lo = mid;
         }
-        double pm = 1.0, pc = z;
-        for (int k = 2; k <= n; ++k) {
-            double pn = ((2.0 * k - 1.0) * z * pc - (k - 1.0) * pm) / k;
-            pm = pc;
-            pc = pn;
+        const double t = 0.5 * (lo + hi);
+        double qm = 0.0, q = std::sqrt(0.5), s = 0.5;
+        for (int k = 0; k + 1 < n; ++k) {
+            const double bk1 = std::sqrt(b2[k + 1]);
+            const double qn = (t * q - (k > 0 ? std::sqrt(b2[k]) * qm : 0.0)) / bk1;
+            qm = q;
+            q = qn;
+            s += q * q;
         }
-        if (n == 1) { pc = z; pm = 1.0; }
-        dp = n * (z * pc - pm) / (z * z - 1.0);
-        x[n - 1 - i] = 0.5 * (1.0 + z);
-        w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = 0.5 * (1.0 + t);
+        w[i] = 0.5 / s;
     }
 }
 

@@ -5,9 +5,9 @@
 // iterations into no-ops.  The host replays one captured CUDA graph per
 // chunk and reads the flag once per chunk.
 //
-// For VFD_FP32 operators the solve is iterative refinement: FP64 residual
-// r = F - A U with the FP64 operator, inner CG on the operator whose K part
-// is FP32, U += correction.
+// For VFD_FP32 and VFD_BF16 operators the single-column solve is iterative
+// refinement: FP64 residual r = F - A U with the FP64 operator, inner CG on
+// the operator whose K part is FP32, U += correction.
 #include <algorithm>
 #include <cmath>
 
@@ -251,7 +251,7 @@ vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, i
         double *u = U + (size_t)r * ld;
         int total = 0;
         double rel = 0.0;
-        if (op.precision != VFD_FP32) {
+        if (op.precision == VFD_FP64) {
             VFD_CUDA(cudaMemcpyAsync(op.cg_b.p, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
             VFD_CUDA(cudaMemcpyAsync(op.cg_x.p, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
             // CG; when the recursive residual has converged but the true
