@@ -308,6 +308,17 @@ vfd_status vfd_batch_tuning(vfd_batch_t batch, int *chosen, float *us, int n, in
  * apply and keep the fastest (the default).  Takes effect on the next apply. */
 vfd_status vfd_batch_set_config(vfd_batch_t batch, int cfg, int *ncand);
 
+/* Bound of the device-side pipeline waits of the batch's tensor-core near
+ * kernel (default 1 second; the paper has no counterpart).  A wait that runs
+ * out makes every CTA of the kernel stop issuing work, wait (again bounded)
+ * for the copies and products it already issued, free its tensor memory and
+ * leave its outputs unwritten; the apply or solve then returns VFD_ETIMEOUT
+ * without touching the caller's output blocks, and the next call starts
+ * clean.  seconds >= 0; 0 makes every wait that is not already satisfied
+ * give up at once (a way to exercise the failure path).  Errors:
+ * VFD_EINVAL (negative or non-finite seconds). */
+vfd_status vfd_batch_set_wait_limit(vfd_batch_t batch, double seconds);
+
 void vfd_batch_free(vfd_batch_t batch);
 
 /* Adjoint gradient (the paper has no gradients; derivative of the discrete

@@ -245,233 +245,11 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
         }
 }
 
-// ---------------------------------------------------------------------------
-// near panels on the 5th-generation tensor cores (tcgen05.mma, accumulator in
-// tensor memory).  CTA = (leaf, 64-RHS tile, panel part), 4 warps.  Per stage
-// of NK panel columns the CTA stages, by cp.async, the panel rows as the A
-// operand (M = 128 rows: the leaf's rows, the rest zero; K-major, no swizzle)
-// and the gathered x rows as the B operand (N = 64 RHS; MN-major, no swizzle),
-// both in BF16 (kind::f16).  The kernel is also written for FP32 operands read
-// as TF32 (kind::tf32, x handed in already rounded), but that combination gave
-// wrong products with this MN-major layout and is not launched.  Thread 0 issues the
-// MMAs of a stage and commits them to that stage's mbarrier, which frees the
-// stage's buffers for the copies NSTAGE-1 stages later; the accumulator
-// (128 lanes x 64 FP32 columns of tensor memory) is read back by the four
-// warps, one row per thread.  Every mbarrier wait is bounded: on expiry the
-// kernel sets *err and skips the rest (leaving its outputs unwritten).
-//
-// Shared layouts (core matrices of 8 rows x 16 bytes, 128 B each):
-//   A: chunk (row m, K-chunk c) at (m/8)*SBO_A + c*128 + (m%8)*16, SBO_A = 128*(NK*sizeof(T)/16);
-//      descriptor LBO = 128 (next K-chunk), SBO = SBO_A (next 8 rows);
-//   B: chunk (k, N-chunk c)   at c*128 + (k/8)*LBO_B + (k%8)*16, LBO_B = 128*(64*sizeof(T)/16);
-//      descriptor LBO = LBO_B (next 8 k), SBO = 128 (next N-chunk).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
-    d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version 1; base offset 0, relative LBO, no swizzle
-    return d;
-}
-
-// instruction descriptor: FP32 accumulate, A K-major, B MN-major, M = 128, N = 64;
-// element format 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32)
-__host__ __device__ constexpr uint32_t umma_idesc(uint32_t fmt)
-{
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | (1u << 16) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// bounded wait for the completion of the mbarrier phase with the given parity
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    for (long it = 0; it < (1L << 24); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-template <class T, int NK, int NSTAGE>
-struct TcTile {
-    static constexpr int E = 16 / (int)sizeof(T);             // elements per 16-byte chunk
-    static constexpr int SBO_A = 128 * (NK / E);                // bytes per 8-row group of A
-    static constexpr int A_BYTES = 128 * NK * (int)sizeof(T);  // 128 rows
-    static constexpr int LBO_B = 128 * (64 / E);                // bytes per 8-k group of B
-    static constexpr int B_BYTES = NK * 64 * (int)sizeof(T);
-    static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int KS = sizeof(T) == 2 ? 16 : 8;          // K per MMA instruction
-    static constexpr uint32_t IDESC = umma_idesc(sizeof(T) == 2 ? 1u : 2u);
-    static constexpr int HEAD = NSTAGE * STAGE;                 // then barriers, TMEM slot, gather indices
-    static_assert(NK % KS == 0 && NK % 8 == 0, "stage width");
-};
-
-template <class T>
-__device__ __forceinline__ void umma_issue(uint32_t taddr, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc);
-template <>
-__device__ __forceinline__ void umma_issue<__nv_bfloat16>(uint32_t taddr, uint64_t da, uint64_t db, uint32_t idesc,
-                                                          uint32_t acc)
-{
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
-                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-template <>
-__device__ __forceinline__ void umma_issue<float>(uint32_t taddr, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
-                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-
-template <class T, int NK, int NSTAGE>
-__global__ void __launch_bounds__(128)
-k_mr_near_tc(const NearItem *__restrict__ items, int R, const T *__restrict__ Xall, float *__restrict__ Yall,
-             float *__restrict__ Y2all, size_t pstride, const int *skip, const int *mdone, int *err)
-{
-    using TT = TcTile<T, NK, NSTAGE>;
-    constexpr int E = TT::E;
-    extern __shared__ __align__(1024) unsigned char tsm[];
-    if (skip && *skip) return;
-    const NearItem it = items[blockIdx.x];
-    if (mdone && mdone[it.mesh]) return;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, rt = blockIdx.y * RT;
-    const T *__restrict__ X = Xall + (size_t)it.xoff * R;
-    const T *__restrict__ Dp = (const T *)it.D;
-    const int b0 = it.row0, na = it.na, W = it.W;
-    uint64_t *bars = (uint64_t *)(tsm + TT::HEAD);          // NSTAGE stage barriers + 1 final
-    uint32_t *tslot = (uint32_t *)(bars + NSTAGE + 1);
-    int *gs = (int *)(tslot + 4);
-    for (int c = tid; c < W; c += 128) gs[c] = it.gcol[c];
-    // rows 64..127 of every A buffer stay zero
-    for (int c = tid; c < NSTAGE * 64 * (NK / E); c += 128) {
-        const int s = c / (64 * (NK / E)), r = c % (64 * (NK / E)), m = 64 + r / (NK / E), kc = r % (NK / E);
-        *(uint4 *)(tsm + s * TT::STAGE + (m / 8) * TT::SBO_A + kc * 128 + (m % 8) * 16) = make_uint4(0, 0, 0, 0);
-    }
-    if (tid == 0) {
-        for (int s = 0; s <= NSTAGE; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bars + s)));
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(smem_addr(tslot)));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t taddr = *tslot;
-
-    auto load_stage = [&](int slot, int chunk) {
-        const int k0 = chunk * NK;
-        unsigned char *sA = tsm + slot * TT::STAGE, *sB = sA + TT::A_BYTES;
-        for (int c = tid; c < 64 * (NK / E); c += 128) {
-            const int m = c / (NK / E), kc = c % (NK / E), col = k0 + kc * E;
-            const bool ok = m < na && col < W;
-            cp_async16(sA + (m / 8) * TT::SBO_A + kc * 128 + (m % 8) * 16,
-                       ok ? (const void *)(Dp + (size_t)m * W + col) : (const void *)Dp, ok);
-        }
-        for (int c = tid; c < NK * (64 / E); c += 128) {
-            const int k = c / (64 / E), nc = c % (64 / E), col = k0 + k;
-            const int j = col < W ? gs[col] : -1;
-            cp_async16(sB + nc * 128 + (k / 8) * TT::LBO_B + (k % 8) * 16,
-                       j >= 0 ? (const void *)(X + (size_t)j * R + rt + nc * E) : (const void *)X, j >= 0);
-        }
-    };
-
-    const int nkt = (W + NK - 1) / NK, ksplit = gridDim.z;
-    const int kc0 = (int)(((long long)nkt * blockIdx.z) / ksplit), nk = (int)(((long long)nkt * (blockIdx.z + 1)) / ksplit) - kc0;
-    bool ok = true;
-    for (int s = 0; s < NSTAGE - 1; ++s) {
-        if (s < nk) load_stage(s, kc0 + s);
-        cp_async_commit();
-    }
-    for (int kt = 0; kt < nk && ok; ++kt) {
-        cp_async_wait<NSTAGE - 2>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a0 = smem_addr(tsm + (kt % NSTAGE) * TT::STAGE), b0s = a0 + TT::A_BYTES;
-            for (int ks = 0; ks < NK / TT::KS; ++ks) {
-                const uint64_t da = umma_desc(a0 + ks * (TT::KS / E) * 128, 128, TT::SBO_A);
-                const uint64_t db = umma_desc(b0s + ks * (TT::KS / 8) * TT::LBO_B, TT::LBO_B, 128);
-                umma_issue<T>(taddr, da, db, TT::IDESC, (kt > 0 || ks > 0) ? 1u : 0u);
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_addr(bars + kt % NSTAGE)));
-        }
-        if (kt + NSTAGE - 1 < nk) {
-            // the buffers of stage kt-1 are refilled: wait for its MMAs (completion #(kt-1)/NSTAGE of its
-            // barrier); every thread takes the same decision (block-wide AND)
-            bool w = kt < 1 || mbar_wait(smem_addr(bars + (kt - 1) % NSTAGE), ((kt - 1) / NSTAGE) & 1);
-            ok = __syncthreads_and(w);
-            if (ok) load_stage((kt + NSTAGE - 1) % NSTAGE, kc0 + kt + NSTAGE - 1);
-        }
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    // all MMAs of this CTA complete -> the final barrier
-    if (tid == 0 && nk > 0)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_addr(bars + NSTAGE)));
-    bool wf = nk == 0 || mbar_wait(smem_addr(bars + NSTAGE), 0);
-    ok = __syncthreads_and(ok && wf);
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-    } else {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        float *Yo = blockIdx.z == 0 ? Yall : Y2all + (size_t)(blockIdx.z - 1) * pstride;
-        const int row = 32 * warp + lane;
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-            uint32_t r[16];
-            if (nk > 0) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];\n"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            } else {
-                for (int q = 0; q < 16; ++q) r[q] = 0u;
-            }
-            if (row < na) {
-                float4 *dst = (float4 *)(Yo + (size_t)(b0 + row) * R + rt + c0);
-                for (int q = 0; q < 4; ++q)
-                    dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                         __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(taddr));
-}
-
-template <class T, int NK, int NSTAGE>
-static size_t near_tc_smem_bytes(int max_panel_w)
-{
-    return (size_t)TcTile<T, NK, NSTAGE>::HEAD + (NSTAGE + 1) * 8 + 16 + (size_t)max_panel_w * sizeof(int);
-}
-
-// x in the MMA's element type: BF16, or FP32 rounded to TF32
+// x in BF16 for the tcgen05 near kernel
 __global__ void k_x_to_bf16(long long n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ b)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = __float2bfloat16_rn(a[i]);
-}
-__global__ void k_x_to_tf32(long long n, const float *__restrict__ a, float *__restrict__ b)
-{
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = __uint_as_float(f2tf32(a[i]));
 }
 
 template <class T, int NK, int NSTAGE>
@@ -482,13 +260,13 @@ static size_t near_smem_bytes(int max_panel_w)
 
 // candidate tile configurations of the near-panel kernel
 struct NearCfg {
-    int nk, nstage, ksplit, warps, nacc, tc;   // tc = 1: tcgen05 kernel (4 warps, accumulator in tensor memory)
+    int nk, nstage, ksplit, warps, nacc, tc;   // tc = 1: TMA-fed tcgen05 kernel (near_tc.cu; BF16, B + M fused)
 };
 static const NearCfg kNearCfgs[] = {{32, 3, 2, 8, 1, 0}, {32, 3, 3, 8, 1, 0}, {16, 4, 3, 8, 1, 0},
                                     {64, 2, 2, 8, 1, 0}, {32, 3, 3, 4, 1, 0}, {16, 4, 3, 4, 1, 0},
                                     {32, 3, 2, 8, 2, 0}, {16, 4, 3, 8, 2, 0}, {16, 4, 3, 4, 2, 0},
-                                    {32, 4, 1, 4, 1, 1}, {32, 4, 2, 4, 1, 1}, {32, 4, 3, 4, 1, 1},
-                                    {64, 3, 1, 4, 1, 1}, {64, 3, 2, 4, 1, 1}, {32, 6, 2, 4, 1, 1}};
+                                    {64, 4, 1, 4, 1, 1}, {64, 4, 2, 4, 1, 1}, {64, 6, 1, 4, 1, 1},
+                                    {64, 6, 2, 4, 1, 1}, {64, 3, 2, 4, 1, 1}, {64, 3, 3, 4, 1, 1}};
 constexpr int kNearCfgCount = (int)(sizeof(kNearCfgs) / sizeof(kNearCfgs[0]));
 
 template <class T, int NK, int NS, int WARPS, int NACC>
@@ -504,40 +282,14 @@ static bool launch_near_cfg(int ksplit, int n_items, int max_panel_w, const Near
     return true;
 }
 
-template <class T, int NK, int NS>
-static bool launch_near_tc_cfg(int ksplit, int n_items, int max_panel_w, const NearItem *items, int R, const void *Xc,
-                               float *Y, float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone,
-                               int *err)
-{
-    const size_t shm = near_tc_smem_bytes<T, NK, NS>(max_panel_w);
-    if (shm > 227 * 1024) return false;
-    VFD_CUDA(cudaFuncSetAttribute(k_mr_near_tc<T, NK, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    dim3 g(n_items, R / RT, ksplit);
-    k_mr_near_tc<T, NK, NS><<<g, 128, shm, st>>>(items, R, (const T *)Xc, Y, Y2, pstride, skip, mdone, err);
-    return true;
-}
-
-// launch configuration c; false if it does not fit in shared memory.  X: FP32
-// x; Xc: x in the tcgen05 MMA's element type (BF16, or TF32-rounded FP32)
+// launch configuration c of the mma.sync kernel (near products only); false
+// if it does not fit in shared memory or c is a tcgen05 candidate
 template <class T>
-static bool launch_near(int c, int n_items, int max_panel_w, const NearItem *items, int R, const float *X,
-                        const void *Xc, float *Y, float *Y2, size_t pstride, cudaStream_t st, const int *skip,
-                        const int *mdone, int *err)
+static bool launch_near(int c, int n_items, int max_panel_w, const NearItem *items, int R, const float *X, float *Y,
+                        float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone)
 {
     const NearCfg &f = kNearCfgs[c];
-    if (f.tc) {
-        // BF16 only: with TF32 operands the MN-major x tile of this layout gave wrong products
-        if (sizeof(T) != 2) return false;
-#define VFD_TC_CASE(NKV, NSV)                                                                                    \
-    if (f.nk == NKV && f.nstage == NSV)                                                                          \
-        return launch_near_tc_cfg<T, NKV, NSV>(f.ksplit, n_items, max_panel_w, items, R, Xc, Y, Y2, pstride, st,  \
-                                               skip, mdone, err);
-        VFD_TC_CASE(32, 4)
-        VFD_TC_CASE(64, 3)
-        VFD_TC_CASE(32, 6)
-#undef VFD_TC_CASE
-        return false;
-    }
+    if (f.tc) return false;
 #define VFD_NEAR_CASE(NKV, NSV, WV, AV)                                                                          \
     if (f.nk == NKV && f.nstage == NSV && f.warps == WV && f.nacc == AV)                                         \
         return launch_near_cfg<T, NKV, NSV, WV, AV>(f.ksplit, n_items, max_panel_w, items, R, X, Y, Y2, pstride,   \
@@ -606,6 +358,32 @@ __global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restr
         acc.w = fmaf(v, x.w, acc.w);
     }
     ((float4 *)Y)[t] = acc;
+}
+
+// the near phase of the apply for candidate c: Y = (near panels + B + M) X.
+// mma.sync candidates: the panel products (partial sums of a split in Y2),
+// then k_mr_csr adds the partials and the CSR rows; tcgen05 candidates: one
+// kernel (near_tc.cu) with the CSR rows in its epilogue.  Xc: x in BF16 for the
+// tcgen05 kernel (its tensor map is built over that buffer).  false: the
+// candidate does not apply (shared memory, precision, meshes without panels).
+template <class T>
+static bool launch_near_phase(BatchData &b, int c, int R, const float *X, float *Y, cudaStream_t st,
+                              const int *skip, const int *mdone)
+{
+    const NearCfg &f = kNearCfgs[c];
+    if (f.tc) {
+        if (sizeof(T) != 2 || b.n_tc_items != b.n_near_items) return false;
+        return launch_near_tma(b, f.nstage, f.ksplit, R, X, Y, st, skip, mdone);
+    }
+    if (b.n_near_items > 0 &&
+        !launch_near<T>(c, b.n_near_items, b.max_panel_w, (const NearItem *)b.near_items.p, R, X, Y, b.y2.p,
+                        (size_t)b.ntot * R, st, skip, mdone))
+        return false;
+    const MrMesh *ms = (const MrMesh *)b.desc.p;
+    k_mr_csr<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R, X,
+                                                                      Y, b.y2.p, f.ksplit - 1, skip, mdone);
+    VFD_CUDA(cudaGetLastError());
+    return true;
 }
 
 __device__ __forceinline__ void fma4(float4 &acc, float u, const float4 x)
@@ -991,8 +769,8 @@ __global__ void k_tf32_copy(long long n, const float *__restrict__ a, float *__r
     if (i < n) b[i] = __uint_as_float(f2tf32(a[i]));
 }
 
-// time every candidate tile configuration of the near-panel kernel once on
-// this batch (zero inputs, scratch outputs) and keep the fastest
+// time every candidate configuration of the near phase (panels + B + M) once
+// on this batch (zero inputs, scratch outputs) and keep the fastest
 template <class T>
 static void tune_near(BatchData &b, int R, cudaStream_t st)
 {
@@ -1001,20 +779,17 @@ static void tune_near(BatchData &b, int R, cudaStream_t st)
     tx.alloc(n);
     ty.alloc(n);
     tx.zero(st);
+    if (b.xc.n) VFD_CUDA(cudaMemsetAsync(b.xc.p, 0, b.xc.n, st));
     cudaEvent_t e0, e1;
     VFD_CUDA(cudaEventCreate(&e0));
     VFD_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     int bestc = 0;
-    const NearItem *items = (const NearItem *)b.near_items.p;
     for (int c = 0; c < kNearCfgCount; ++c) {
-        if (!launch_near<T>(c, b.n_near_items, b.max_panel_w, items, R, tx.p, b.xc.p, ty.p, b.y2.p, n, st, nullptr,
-                            nullptr, b.tc_err.p))
-            continue;
+        b.near_cfg_us[c] = 0.f;
+        if (!launch_near_phase<T>(b, c, R, tx.p, ty.p, st, nullptr, nullptr)) continue;
         VFD_CUDA(cudaEventRecord(e0, st));
-        for (int rep = 0; rep < 3; ++rep)
-            launch_near<T>(c, b.n_near_items, b.max_panel_w, items, R, tx.p, b.xc.p, ty.p, b.y2.p, n, st, nullptr,
-                           nullptr, b.tc_err.p);
+        for (int rep = 0; rep < 3; ++rep) launch_near_phase<T>(b, c, R, tx.p, ty.p, st, nullptr, nullptr);
         VFD_CUDA(cudaEventRecord(e1, st));
         VFD_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1030,6 +805,7 @@ static void tune_near(BatchData &b, int R, cudaStream_t st)
     VFD_CUDA(cudaStreamSynchronize(st));
     int herr = 0;
     VFD_CUDA(cudaMemcpy(&herr, b.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) VFD_CUDA(cudaMemset(b.tc_err.p, 0, sizeof(int)));
     VFD_REQUIRE(herr == 0, VFD_ETIMEOUT, "batched apply: a tensor-core pipeline wait expired while tuning");
     b.near_cfg = bestc;
 }
@@ -1082,10 +858,19 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
     b.xhat.alloc(std::max<size_t>(nh, 1));
     b.yhat.alloc(std::max<size_t>(nh, 1));
     b.y2.alloc((size_t)(KSPLIT_MAX - 1) * b.ntot * R);
-    b.xc.alloc((size_t)b.ntot * R * (bf ? 2 : 4));
+    b.xc.alloc((size_t)b.ntot * R * 2);   // x in BF16 for the tcgen05 kernel
     if (!b.tc_err.p) {
         b.tc_err.alloc(1);
         VFD_CUDA(cudaMemset(b.tc_err.p, 0, sizeof(int)));
+    }
+    b.n_tc_items = 0;
+    if (bf) {
+        // tcgen05 near kernel: pre-tiled panels, items, split partials and their counters
+        for (OpData *op : b.ops) build_tiled_panels(*op->m, *op, st);
+        build_tc_items(b);
+        b.tc_part.alloc((size_t)std::max(b.n_tc_items, 1) * (R / RT) * 4 * 64 * RT);
+        b.tc_cnt.alloc((size_t)std::max(b.n_tc_items, 1) * (R / RT));
+        b.tc_cnt.zero(st);
     }
     if (!bf)
         for (OpData *op : b.ops)
@@ -1225,22 +1010,13 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
         k_mr_far_couple<T><<<gc, 64, cshm, b.side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
         VFD_CUDA(cudaEventRecord(b.ev_join, b.side));
     }
-    const int nparts = kNearCfgs[b.near_cfg].ksplit - 1;
-    if (b.n_near_items > 0) {
-        if (kNearCfgs[b.near_cfg].tc) {
-            const long long n = (long long)b.ntot * R;
-            if (b.precision == VFD_BF16)
-                k_x_to_bf16<<<cdiv(n, 256), 256, 0, st>>>(n, X, (__nv_bfloat16 *)b.xc.p);
-            else
-                k_x_to_tf32<<<cdiv(n, 256), 256, 0, st>>>(n, X, (float *)b.xc.p);
-        }
-        const bool launched = launch_near<T>(b.near_cfg, b.n_near_items, b.max_panel_w,
-                                             (const NearItem *)b.near_items.p, R, X, b.xc.p, Y, b.y2.p,
-                                             (size_t)b.ntot * R, st, skip, mdone, b.tc_err.p);
-        VFD_REQUIRE(launched, VFD_EUNSUPPORTED, "batched apply: the pinned near-panel configuration does not fit");
+    if (kNearCfgs[b.near_cfg].tc) {
+        const long long n = (long long)b.ntot * R;
+        k_x_to_bf16<<<cdiv(n, 256), 256, 0, st>>>(n, X, (__nv_bfloat16 *)b.xc.p);
+        VFD_CUDA(cudaGetLastError());
     }
-    k_mr_csr<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R, X,
-                                                                      Y, b.y2.p, nparts, skip, mdone);
+    const bool launched = launch_near_phase<T>(b, b.near_cfg, R, X, Y, st, skip, mdone);
+    VFD_REQUIRE(launched, VFD_EUNSUPPORTED, "batched apply: the pinned near-panel configuration does not apply");
     if (b.any_far) {
         VFD_CUDA(cudaStreamWaitEvent(st, b.ev_join, 0));
         dim3 ge(b.n_leaf_items, R / RT);
@@ -1268,6 +1044,7 @@ void batch_check(BatchData &b, cudaStream_t st)
     int e = 0;
     VFD_CUDA(cudaMemcpyAsync(&e, b.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     VFD_CUDA(cudaStreamSynchronize(st));
+    if (e) VFD_CUDA(cudaMemset(b.tc_err.p, 0, sizeof(int)));   // reported once; later calls start clean
     VFD_REQUIRE(e == 0, VFD_ETIMEOUT, "batched apply: a tensor-core pipeline wait expired");
 }
 

@@ -576,6 +576,17 @@ vfd_status vfd_batch_set_config(vfd_batch_t h, int cfg, int *ncand)
     VFD_API_END
 }
 
+vfd_status vfd_batch_set_wait_limit(vfd_batch_t h, double seconds)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h, VFD_EINVAL, "null batch");
+    VFD_REQUIRE(std::isfinite(seconds) && seconds >= 0.0 && seconds < 3600.0, VFD_EINVAL,
+                "the wait limit must be in [0, 3600) seconds");
+    h->b->wait_ns = (long long)(seconds * 1e9);
+    return VFD_OK;
+    VFD_API_END
+}
+
 void vfd_batch_free(vfd_batch_t h)
 {
     if (!h) return;

@@ -213,6 +213,9 @@ struct OpData {
     DBuf<double> S64;                  // nfar * k * k
     DBuf<double> D64;                  // near entries
     DBuf<float> S32, D32, Ul32;        // FP32 copies (VFD_FP32)
+    DBuf<unsigned short> Dtc;          // BF16 near panels pre-tiled for the TMA-fed tcgen05 kernel (first batched use)
+    std::vector<int64_t> Dtc_off;      //   element offset of each leaf's image (nleaf + 1)
+    DBuf<int64_t> Dtc_doff;
     DBuf<float> D32t;                  // D32 rounded to TF32 (batched tensor-core path, built on first use)
     DBuf<unsigned short> S16, D16, Ul16;   // BF16 copies (VFD_BF16)
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
@@ -265,8 +268,13 @@ struct BatchData {
     bool any_far = false;
     DBuf<float> part, xhat, yhat, y2;   // far-field workspaces (all meshes), second near partial
     DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
-    DBuf<unsigned char> xc;             // x in the tcgen05 MMA element type (BF16 / TF32-rounded FP32)
+    DBuf<unsigned char> xc;             // x in BF16 for the tcgen05 kernel ([ntot][R])
     DBuf<int> tc_err;                   // set by the tcgen05 kernel when a pipeline wait expires
+    DBuf<unsigned char> tc_items;       // TcItem records of the tcgen05 kernel (one per (mesh, leaf))
+    int n_tc_items = 0;
+    DBuf<float> tc_part;                // split partial tiles of the tcgen05 kernel
+    DBuf<int> tc_cnt;                   // per (item, RHS tile) arrival counters (zero between launches)
+    long long wait_ns = 1000000000LL;   // bound of the tcgen05 kernel's pipeline waits
     // batched refinement solve
     DBuf<float> x, r, p, q, b, red, sc;
     DBuf<int> flag, red_items, red_mesh;
@@ -326,6 +334,12 @@ void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
                        int max_it, int *iters, double *relres, cudaStream_t st);
 void launch_convert_bf16(const MeshData &m, OpData &op, cudaStream_t st);
+// near_tc.cu (tcgen05 near panels with bulk-copied panel stages, BF16)
+void build_tiled_panels(const MeshData &m, OpData &op, cudaStream_t st);
+void build_tc_items(BatchData &b);
+size_t near_tma_smem(int nstage);
+bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X, float *Y, cudaStream_t st,
+                     const int *skip, const int *mdone);
 void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st);
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st);

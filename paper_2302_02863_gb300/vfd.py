@@ -34,7 +34,7 @@ INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "no
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
            "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_grad", "vfd_load", "vfd_op_rho", "vfd_op_timings",
            "vfd_selftest_math", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve", "vfd_batch_tuning",
-           "vfd_batch_set_config", "vfd_batch_free",
+           "vfd_batch_set_config", "vfd_batch_set_wait_limit", "vfd_batch_free",
            "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
 
 
@@ -95,6 +95,7 @@ def load():
                                   C.c_int, C.POINTER(C.c_int), dp, vp]
     L.vfd_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
     L.vfd_batch_set_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+    L.vfd_batch_set_wait_limit.argtypes = [vp, C.c_double]
     L.vfd_batch_free.argtypes = [vp]
     L.vfd_batch_free.restype = None
     L.vfd_free_op.argtypes = [vp]
@@ -104,7 +105,7 @@ def load():
     L.vfd_last_error.restype = C.c_char_p
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
               "vfd_apply_noalloc", "vfd_grad", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve",
-              "vfd_batch_tuning", "vfd_batch_set_config",
+              "vfd_batch_tuning", "vfd_batch_set_config", "vfd_batch_set_wait_limit",
               "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -356,6 +357,11 @@ def vfd_batch_set_config(batch, cfg):
     n = C.c_int()
     _check(load().vfd_batch_set_config(batch.handle, int(cfg), C.byref(n)))
     return n.value
+
+
+def vfd_batch_set_wait_limit(batch, seconds):
+    """Bound (seconds) of the tensor-core kernel's device waits; 0 = give up at once."""
+    _check(load().vfd_batch_set_wait_limit(batch.handle, float(seconds)))
 
 
 def vfd_load(mesh, f_nodal, F, stream=None):
