@@ -223,7 +223,8 @@ def main():
     m, s, k, prm = synth.workload(args.workload)
     prec = {"fp64": vfd.VFD_FP64, "fp32": vfd.VFD_FP32, "bf16": vfd.VFD_BF16}[args.precision]
     mesh = vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"],
-                        lam=0.75, rho_lambda=0.75, tail_mode=prm["tail"], tail_R=prm["R"])
+                        lam=prm["lam"], rho_lambda=prm["lam"], tail_mode=prm["tail"], tail_R=prm["R"],
+                        inner_p=prm.get("inner_p", 0))
     info = mesh.info
     n = mesh.n_dof
     if args.mode in ("apply", "solve"):

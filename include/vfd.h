@@ -106,6 +106,12 @@ typedef struct {
     int rho_leaf_m;     /* max points per leaf of the density cluster trees (Sec. 6.2); default 64 */
     double rho_lambda;  /* admissibility of the density sweep on plain point boxes, with the
                            extra condition dist > 2 h_max (Sec. 6.2); default 0.75; 0 = direct */
+    int inner_p;        /* Chebyshev nodes per dimension of the far field of the low-precision
+                           inner operator of the batched mixed-precision solves (VFD_FP32 /
+                           VFD_BF16 operators, nrhs a multiple of 64); 0 = cheb_p.  That
+                           operator only has to match the FP64 operator to its own rounding
+                           level (2^-11 or 2^-8), so a lower order serves; the solves still
+                           converge to the solution of the FP64 operator.  Default 0. */
 } vfd_mesh_opts;
 
 /* Scalar field on R^d: value = squash(c0 + sum of terms), or a P1 field.
@@ -163,7 +169,8 @@ vfd_status vfd_mesh_dofs(vfd_mesh_t mesh, int32_t *dof_of_vertex, int64_t *n_dof
  * density sweep  [15] stored near entries (row panels, padded to 4 columns)
  * [16] kernel evaluations of the near-block build (point pairs of the
  * computed leaf blocks)  [17] 4D points of the singular rules over all
- * touching pairs (2D; 0 in 1D). */
+ * touching pairs (2D; 0 in 1D)  [18] rank of the far field of the inner
+ * operator of the batched mixed-precision solves. */
 vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info);
 
 /* Assemble the operator for the fields s and log kappa (Algorithm 1):

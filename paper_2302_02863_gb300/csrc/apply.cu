@@ -433,26 +433,6 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
     }
 }
 
-// Y = (K_near + K_far) X for one column, in FP64 arithmetic, with caller-supplied
-// FP64 leaf bases, coupling blocks and near panels (e.g. the rounded values of a
-// low-precision operator)
-void apply_k_with(const MeshData &m, OpData &op, const double *Ul, const double *S, const double *D, const double *X,
-                  double *Y, cudaStream_t st)
-{
-    ensure_streams(op);
-    const int nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
-    const size_t need = (size_t)m.kt.nnode * m.k;
-    const size_t needp = (size_t)std::max(nlev, 1) * m.kt.nleaf * m.k;
-    if (op.xhat.n < need || op.P64.n < needp) {
-        release_graphs(op);
-        op.xhat.alloc(need);
-        op.yhat.alloc(need);
-        op.P64.alloc(needp);
-    }
-    apply_impl<double, double>(m, op, VFD_PART_KNEAR | VFD_PART_KFAR, X, Y, 1, m.N, Ul, S, D, op.xhat.p, op.yhat.p,
-                               op.P64.p, st, nullptr);
-}
-
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                  cudaStream_t st)
 {

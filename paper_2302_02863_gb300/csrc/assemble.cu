@@ -61,6 +61,15 @@ void launch_field_points(const MeshData &m, OpData &op, cudaStream_t st)
         VFD_CUDA(cudaGetLastError());
     };
     if (m.nfar) nodes(m.kt_cheb, m.kt.nnode, op.kc_s, op.kc_lk);
+    if (m.nfar && m.k_in && op.precision != VFD_FP64) {
+        // the inner operator's nodes (k_in per box)
+        const int n = m.kt.nnode * m.k_in;
+        op.kc_s_in.alloc(n);
+        op.kc_lk_in.alloc(n);
+        k_fields_nodes<<<cdiv(n, 256), 256, 0, st>>>(d, n, m.kt_cheb_in.p, op.fs, op.fk, op.kc_s_in.p, op.kc_lk_in.p,
+                                                      smin, smax, op.errflag.p);
+        VFD_CUDA(cudaGetLastError());
+    }
     if (m.nrfar) {
         nodes(m.tt_cheb, m.tt.nnode, op.tc_s, op.tc_lk);
         nodes(m.st_cheb, m.st.nnode, op.sc_s, op.sc_lk);
@@ -584,6 +593,14 @@ void launch_coupling_build(const MeshData &m, OpData &op, cudaStream_t st)
     k_coupling<<<cdiv(n, 256), 256, 0, st>>>(m.d, m.k, m.kt.nnode, m.far_ptr.p, m.far_col.p, m.kt_cheb.p, op.kc_s.p,
                                              op.kc_lk.p, m.mtab.p, op.S64.p);
     VFD_CUDA(cudaGetLastError());
+    if (m.k_in && op.precision != VFD_FP64) {
+        // the inner operator's coupling blocks at its lower interpolation order
+        const long long ni = (long long)m.nfar * m.k_in * m.k_in;
+        op.S64_in.alloc(ni);
+        k_coupling<<<cdiv(ni, 256), 256, 0, st>>>(m.d, m.k_in, m.kt.nnode, m.far_ptr.p, m.far_col.p, m.kt_cheb_in.p,
+                                                  op.kc_s_in.p, op.kc_lk_in.p, m.mtab.p, op.S64_in.p);
+        VFD_CUDA(cudaGetLastError());
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -308,12 +308,13 @@ static bool launch_near(int c, int n_items, int max_panel_w, const NearItem *ite
     return false;
 }
 
-// Y[i][r..r+3] = (Y + sum_z Y2_z)[i][r..r+3] + sum_c val[c] X[col c][r..r+3]
-// (B + M in FP32 added to the partial near products; thread per (row, 4 RHS);
-// meshes without near blocks: no near products)
-__global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restrict__ row_off, int nmesh,
-                         long long ntot, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
-                         const float *__restrict__ Y2all, int nparts, const int *skip, const int *mdone)
+// Y[i][r..r+3] = (Y + sum_z Y2_z)[i][r..r+3] + the rest of row i of A times X:
+// the partial products of a split panel plus, per mesh, either the B + M CSR
+// row (FP32) or, where B + M off the diagonal is folded into the panels, the
+// diagonal term diag_i X[i]; thread per (row, 4 RHS)
+__global__ void k_mr_rows(const MrMesh *__restrict__ ms, const long long *__restrict__ row_off, int nmesh,
+                          long long ntot, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
+                          const float *__restrict__ Y2all, int nparts, const int *skip, const int *mdone)
 {
     if (skip && *skip) return;
     const int R4 = R >> 2;
@@ -328,42 +329,45 @@ __global__ void k_mr_csr(const MrMesh *__restrict__ ms, const long long *__restr
     }
     if (mdone && mdone[lo]) return;
     const MrMesh &Ms = ms[lo];
-    const size_t xo = (size_t)Ms.xoff * R;
-    const float *__restrict__ X = Xall + xo;
-    float *__restrict__ Y = Yall + xo;
-    const float *__restrict__ Y2 = Y2all + xo;
     const size_t pstride = (size_t)ntot * R / 4;   // float4 stride between partial buffers
-    const int *__restrict__ rowptr = Ms.rowptr, *__restrict__ colidx = Ms.colidx;
-    const float *__restrict__ val = Ms.val;
-    const long long t = tg - Ms.xoff * R4;
-    const int i = (int)(t / R4), q = (int)(t % R4);
-    const float4 *X4 = (const float4 *)X;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (Ms.has_near) {
-        acc = ((const float4 *)Y)[t];
+        acc = ((const float4 *)Yall)[tg];
         for (int z = 0; z < nparts; ++z) {
-            const float4 b = ((const float4 *)Y2)[(size_t)z * pstride + t];
+            const float4 b = ((const float4 *)Y2all)[(size_t)z * pstride + tg];
             acc.x += b.x;
             acc.y += b.y;
             acc.z += b.z;
             acc.w += b.w;
         }
     }
-    for (int c = rowptr[i]; c < rowptr[i + 1]; ++c) {
-        const float v = val[c];
-        const float4 x = X4[(size_t)colidx[c] * R4 + q];
-        acc.x = fmaf(v, x.x, acc.x);
-        acc.y = fmaf(v, x.y, acc.y);
-        acc.z = fmaf(v, x.z, acc.z);
-        acc.w = fmaf(v, x.w, acc.w);
+    const int i = (int)(ig - Ms.xoff), q = (int)(tg % R4);
+    const float4 *X4 = (const float4 *)(Xall + (size_t)Ms.xoff * R);
+    if (Ms.diag) {
+        const float dg = Ms.diag[i];
+        const float4 x = X4[(size_t)i * R4 + q];
+        acc.x = fmaf(dg, x.x, acc.x);
+        acc.y = fmaf(dg, x.y, acc.y);
+        acc.z = fmaf(dg, x.z, acc.z);
+        acc.w = fmaf(dg, x.w, acc.w);
+    } else {
+        for (int c = Ms.rowptr[i]; c < Ms.rowptr[i + 1]; ++c) {
+            const float v = Ms.val[c];
+            const float4 x = X4[(size_t)Ms.colidx[c] * R4 + q];
+            acc.x = fmaf(v, x.x, acc.x);
+            acc.y = fmaf(v, x.y, acc.y);
+            acc.z = fmaf(v, x.z, acc.z);
+            acc.w = fmaf(v, x.w, acc.w);
+        }
     }
-    ((float4 *)Y)[t] = acc;
+    ((float4 *)Yall)[tg] = acc;
 }
 
 // the near phase of the apply for candidate c: Y = (near panels + B + M) X.
 // mma.sync candidates: the panel products (partial sums of a split in Y2),
-// then k_mr_csr adds the partials and the CSR rows; tcgen05 candidates: one
-// kernel (near_tc.cu) with the CSR rows in its epilogue.  Xc: x in BF16 for the
+// then k_mr_rows adds the partials and the B + M rows (or the diagonal, where
+// B + M is folded into the panels); tcgen05 candidates: one kernel
+// (near_tc.cu) with those rows in its epilogue.  Xc: x in BF16 for the
 // tcgen05 kernel (its tensor map is built over that buffer).  false: the
 // candidate does not apply (shared memory, precision, meshes without panels).
 template <class T>
@@ -380,346 +384,10 @@ static bool launch_near_phase(BatchData &b, int c, int R, const float *X, float 
                         (size_t)b.ntot * R, st, skip, mdone))
         return false;
     const MrMesh *ms = (const MrMesh *)b.desc.p;
-    k_mr_csr<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R, X,
-                                                                      Y, b.y2.p, f.ksplit - 1, skip, mdone);
+    k_mr_rows<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R,
+                                                                       X, Y, b.y2.p, f.ksplit - 1, skip, mdone);
     VFD_CUDA(cudaGetLastError());
     return true;
-}
-
-__device__ __forceinline__ void fma4(float4 &acc, float u, const float4 x)
-{
-    acc.x = fmaf(u, x.x, acc.x);
-    acc.y = fmaf(u, x.y, acc.y);
-    acc.z = fmaf(u, x.z, acc.z);
-    acc.w = fmaf(u, x.w, acc.w);
-}
-
-// far field, R RHS in tiles of 64 (FP32 accumulation; T the stored basis /
-// coupling type).  Thread micro-tiles of 4 outputs x 4 RHS (float4 over RHS).
-//
-// Far-field products on the tensor cores (mma.sync m16n8k8 TF32, FP32
-// accumulate; BF16-stored bases and blocks are widened when the fragments
-// are loaded).  Every tile is staged by cp.async (16-byte copies, all in
-// flight at once, zero-filled padding rows) in the stored type; rows are
-// padded so the fragment loads are conflict-free: [k][64 RHS] tiles with row
-// stride RT + 8, basis / block rows with k + 8 (read by columns) or k + 4
-// (read by rows, FP32) elements.  When a row of k elements is not a whole
-// number of 16-byte pieces the tiles are staged by plain loads instead.
-constexpr int FLDX = RT + 8;   // row stride of [k][RHS] tiles
-
-__host__ __device__ constexpr int far_round16(int v) { return (v + 15) & ~15; }
-template <class T>
-__host__ __device__ constexpr int far_lcol(int k) { return k + 8; }   // rows read by columns
-template <class T>
-__host__ __device__ constexpr int far_lrow(int k) { return sizeof(T) == 4 ? k + 4 : k + 8; }   // rows read by rows
-
-template <class T>
-__device__ __forceinline__ float ldf(const T *p) { return (float)*p; }
-
-// rows [0, nvalid) of kcols elements from src (row stride src_ld) to dst (row
-// stride dst_ld); rows [nvalid, npad) zero
-template <class T>
-__device__ __forceinline__ void stage_rows(T *dst, int dst_ld, const T *src, size_t src_ld, int kcols, int nvalid,
-                                           int npad, bool async)
-{
-    if (async) {
-        constexpr int E = 16 / (int)sizeof(T);
-        const int cpr = kcols / E;
-        for (int c = threadIdx.x; c < npad * cpr; c += blockDim.x) {
-            const int r = c / cpr, q = c - r * cpr;
-            const bool ok = r < nvalid;
-            cp_async16(dst + (size_t)r * dst_ld + q * E, ok ? (const void *)(src + (size_t)r * src_ld + q * E)
-                                                            : (const void *)src, ok);
-        }
-    } else {
-        for (int c = threadIdx.x; c < npad * kcols; c += blockDim.x) {
-            const int r = c / kcols, q = c - r * kcols;
-            dst[(size_t)r * dst_ld + q] = r < nvalid ? src[(size_t)r * src_ld + q] : (T)0.f;
-        }
-    }
-}
-
-template <class T>
-static size_t far_smem_proj(int nlev, int k)
-{
-    return (size_t)64 * FLDX * sizeof(float) + (size_t)nlev * 64 * far_lcol<T>(k) * sizeof(T);
-}
-template <class T>
-static size_t far_smem_expand(int nlev, int k)
-{
-    return (size_t)far_round16(nlev * k) * FLDX * sizeof(float) + (size_t)nlev * 64 * far_lrow<T>(k) * sizeof(T);
-}
-
-// projections: part[lv][leaf][a][r] = sum_{i in leaf} Ul[lv][i][a] X[i][r], i.e.
-// C[lva][r] = sum_i A[lva][i] Xs[i][r] with A[lva][i] = Ur[l][i][a] (M = nlev*k,
-// N = 64, K = leaf size).  CTA (256 threads, 8 warps) per (leaf, RHS tile);
-// warp w owns the m16 tiles w, w+8, ... of lva and all eight n8 tiles.
-template <class T>
-__global__ void __launch_bounds__(256)
-k_mr_far_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
-              const int *skip, const int *mdone)
-{
-    extern __shared__ __align__(16) unsigned char fsm[];
-    if (skip && *skip) return;
-    const int2 item = items[blockIdx.x];
-    if (mdone && mdone[item.x]) return;
-    const MrMesh &Ms = ms[item.x];
-    const int leaf = item.y, rt = blockIdx.y * RT;
-    const int fl = Ms.fl, k = Ms.k, nlev = Ms.nlev, N = Ms.N, nleaf = Ms.nleaf;
-    const float *__restrict__ X = Xall + (size_t)Ms.xoff * R;
-    const T *__restrict__ Ul = (const T *)Ms.Ul;
-    float *__restrict__ part = Ms.part;
-    const int b = Ms.kb[fl + leaf], n = Ms.ke[fl + leaf] - b;
-    const int NL = nlev * k, NL16 = far_round16(NL), LP = far_lcol<T>(k), npad = (n + 7) & ~7;
-    const bool async = (k * (int)sizeof(T)) % 16 == 0;
-    float *Xs = (float *)fsm;                              // [npad][FLDX]
-    T *Ur = (T *)(fsm + 64 * FLDX * sizeof(float));        // [nlev][npad][LP]
-    stage_rows<float>(Xs, FLDX, X + (size_t)b * R + rt, R, RT, n, npad, true);
-    for (int l = 0; l < nlev; ++l)
-        stage_rows<T>(Ur + (size_t)l * npad * LP, LP, Ul + ((size_t)l * N + b) * k, k, k, n, npad, async);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-    for (int mt = warp; mt < NL16 / 16; mt += 8) {
-        const int m0 = mt * 16;
-        // the two rows (lva) this lane reads: level and index inside the level
-        const int v0 = m0 + g, v1 = v0 + 8;
-        const bool ok0 = v0 < NL, ok1 = v1 < NL;
-        const T *r0 = Ur + (size_t)(ok0 ? v0 / k : 0) * npad * LP + (ok0 ? v0 % k : 0);
-        const T *r1 = Ur + (size_t)(ok1 ? v1 / k : 0) * npad * LP + (ok1 ? v1 % k : 0);
-        float acc[8][4];
-        for (int j = 0; j < 8; ++j)
-            for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-        for (int k0 = 0; k0 < npad; k0 += 8) {
-            const int i0 = (k0 + t4) * LP, i4 = i0 + 4 * LP;
-            const uint32_t a[4] = {f2tf32(ok0 ? ldf(r0 + i0) : 0.f), f2tf32(ok1 ? ldf(r1 + i0) : 0.f),
-                                   f2tf32(ok0 ? ldf(r0 + i4) : 0.f), f2tf32(ok1 ? ldf(r1 + i4) : 0.f)};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float *B0 = Xs + (k0 + t4) * FLDX + j * 8 + g;
-                const uint32_t bb[2] = {f2tf32(B0[0]), f2tf32(B0[4 * FLDX])};
-                MmaTraits<float>::mma(acc[j], a, bb);
-            }
-        }
-        for (int h = 0; h < 2; ++h) {
-            const int v = m0 + g + 8 * h;
-            if (v >= NL) continue;
-            const int l = v / k, al = v - l * k;
-            float *dst = part + (((size_t)l * nleaf + leaf) * k + al) * R + rt;
-            for (int j = 0; j < 8; ++j)
-                *(float2 *)(dst + j * 8 + 2 * t4) = make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
-        }
-    }
-}
-
-// xhat[node][a][r] = sum over the node's leaves of part (levels lmin..L)
-__global__ void __launch_bounds__(256) k_mr_far_sum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items,
-                                                   int R, const int *skip, const int *mdone)
-{
-    // CTA: 32 float4 outputs x 8 lanes over the node's leaves; the 8 lane sums
-    // are combined in a fixed order through shared memory
-    __shared__ float4 sh[8][32];
-    if (skip && *skip) return;
-    const int2 item = items[blockIdx.x];
-    if (mdone && mdone[item.x]) return;
-    const MrMesh &Ms = ms[item.x];
-    const int node = item.y, lmin = Ms.lmin, L = Ms.L, k = Ms.k, nleaf = Ms.nleaf;
-    const float *__restrict__ part = Ms.part;
-    float *__restrict__ xhat = Ms.xhat;
-    const int o = threadIdx.x & 31, lane = threadIdx.x >> 5;
-    const int t = blockIdx.y * 32 + o;
-    const bool ok = t < k * R / 4;
-    int l = 0;
-    while ((2 << l) - 1 <= node) ++l;
-    const int span = 1 << (L - l), leaf0 = ((node + 1) << (L - l)) - 1 - ((1 << L) - 1);
-    const size_t stride = (size_t)k * R / 4;
-    const float4 *p = (const float4 *)part + (((size_t)(l - lmin) * nleaf + leaf0) * k * R) / 4 + (ok ? t : 0);
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ok)
-#pragma unroll 4
-        for (int j = lane; j < span; j += 8) {
-            const float4 v = p[(size_t)j * stride];
-            s.x += v.x;
-            s.y += v.y;
-            s.z += v.z;
-            s.w += v.w;
-        }
-    sh[lane][o] = s;
-    __syncthreads();
-    if (lane == 0 && ok) {
-        for (int q = 1; q < 8; ++q) {
-            s.x += sh[q][o].x;
-            s.y += sh[q][o].y;
-            s.z += sh[q][o].z;
-            s.w += sh[q][o].w;
-        }
-        ((float4 *)xhat)[(size_t)node * stride + t] = s;
-    }
-}
-
-// coupling: yhat[node][a][r] = sum_e sum_b S_e[b][a] xhat[col e][b][r], i.e.
-// C[a][r] = sum_e sum_b A_e[a][b] B_e[b][r] with A_e[a][b] = Ss[b][a] (M = k,
-// N = 64, K = k per block).  CTA (64 threads, 2 warps) per (node, RHS tile);
-// warp w owns n8 tiles 4w..4w+3.  Groups of EPS blocks (S_e rows and the
-// column nodes' xhat rows) pass through a two-stage cp.async pipeline.
-constexpr int EPS = 4;   // coupling blocks per pipeline stage
-
-__host__ __device__ constexpr int couple_k8(int k) { return (k + 7) & ~7; }
-template <class T>
-__host__ __device__ constexpr size_t couple_block_bytes(int k)
-{
-    return (size_t)couple_k8(k) * far_lcol<T>(k) * sizeof(T) + (size_t)couple_k8(k) * FLDX * sizeof(float);
-}
-template <class T>
-static size_t couple_smem(int k) { return 2 * EPS * couple_block_bytes<T>(k); }
-
-template <class T>
-__global__ void __launch_bounds__(64)
-k_mr_far_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip,
-                const int *mdone)
-{
-    extern __shared__ __align__(16) unsigned char csm[];
-    if (skip && *skip) return;
-    const int2 item = items[blockIdx.x];
-    if (mdone && mdone[item.x]) return;
-    const MrMesh &Ms = ms[item.x];
-    const int node = item.y, rt = blockIdx.y * RT, k = Ms.k;
-    const int *__restrict__ fptr = Ms.fptr, *__restrict__ fcol = Ms.fcol;
-    const T *__restrict__ S = (const T *)Ms.S;
-    const float *__restrict__ xhat = Ms.xhat;
-    float *__restrict__ yhat = Ms.yhat;
-    const int k8 = couple_k8(k), k16 = far_round16(k), LS = far_lcol<T>(k);
-    const size_t bb_bytes = couple_block_bytes<T>(k), sbytes = (size_t)k8 * LS * sizeof(T);
-    const bool async = (k * (int)sizeof(T)) % 16 == 0;
-    const int e0 = fptr[node], ne = fptr[node + 1] - e0, ng = (ne + EPS - 1) / EPS;
-    auto stage = [&](int sl, int grp) {
-        for (int j = 0; j < EPS && grp * EPS + j < ne; ++j) {
-            const int e = e0 + grp * EPS + j;
-            unsigned char *base = csm + (size_t)(sl * EPS + j) * bb_bytes;
-            stage_rows<T>((T *)base, LS, S + (size_t)e * k * k, k, k, k, k8, async);
-            stage_rows<float>((float *)(base + sbytes), FLDX, xhat + (size_t)fcol[e] * k * R + rt, R, RT, k, k8, true);
-        }
-    };
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-    float acc[4][4][4];   // [m16 tile][n8 tile][fragment]
-    for (int a = 0; a < 4; ++a)
-        for (int j = 0; j < 4; ++j)
-            for (int q = 0; q < 4; ++q) acc[a][j][q] = 0.f;
-    if (ng > 0) stage(0, 0);
-    cp_async_commit();
-    for (int gi = 0; gi < ng; ++gi) {
-        if (gi + 1 < ng) stage((gi + 1) & 1, gi + 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        for (int j = 0; j < EPS && gi * EPS + j < ne; ++j) {
-            const unsigned char *base = csm + (size_t)((gi & 1) * EPS + j) * bb_bytes;
-            const T *Ss = (const T *)base;
-            const float *Xs = (const float *)(base + sbytes);
-            for (int k0 = 0; k0 < k8; k0 += 8) {
-                uint32_t bq[4][2];
-#pragma unroll
-                for (int jn = 0; jn < 4; ++jn) {
-                    const float *B0 = Xs + (k0 + t4) * FLDX + (warp * 4 + jn) * 8 + g;
-                    bq[jn][0] = f2tf32(B0[0]);
-                    bq[jn][1] = f2tf32(B0[4 * FLDX]);
-                }
-#pragma unroll
-                for (int mt = 0; mt < 4; ++mt) {
-                    if (mt * 16 >= k16) break;
-                    const int a0 = mt * 16 + g, a1 = a0 + 8;
-                    const T *c0 = Ss + (k0 + t4) * LS, *c4 = c0 + 4 * LS;
-                    const uint32_t a[4] = {f2tf32(a0 < k ? ldf(c0 + a0) : 0.f), f2tf32(a1 < k ? ldf(c0 + a1) : 0.f),
-                                           f2tf32(a0 < k ? ldf(c4 + a0) : 0.f), f2tf32(a1 < k ? ldf(c4 + a1) : 0.f)};
-#pragma unroll
-                    for (int jn = 0; jn < 4; ++jn) MmaTraits<float>::mma(acc[mt][jn], a, bq[jn]);
-                }
-            }
-        }
-        __syncthreads();   // the slot is refilled two steps later
-    }
-    cp_async_wait<0>();
-    for (int mt = 0; mt < 4; ++mt) {
-        if (mt * 16 >= k16) break;
-        for (int h = 0; h < 2; ++h) {
-            const int al = mt * 16 + g + 8 * h;
-            if (al >= k) continue;
-            float *dst = yhat + ((size_t)node * k + al) * R + rt;
-            for (int jn = 0; jn < 4; ++jn)
-                *(float2 *)(dst + (warp * 4 + jn) * 8 + 2 * t4) = make_float2(acc[mt][jn][2 * h], acc[mt][jn][2 * h + 1]);
-        }
-    }
-}
-
-// expansion: Y[i][r] += sum_l sum_a Ul[l][i][a] yhat[ancestor_l(i)][a][r], i.e.
-// C[i][r] = sum_lva A[i][lva] Ys[lva][r] with A[i][lva] = Ur[l][i][a] (M = leaf
-// size, N = 64, K = nlev*k).  CTA (256 threads, 8 warps) per (leaf, RHS tile);
-// warp w owns the m16 tile w & 3 and the n8 tiles 4 (w >> 2) .. +3.
-template <class T>
-__global__ void __launch_bounds__(256)
-k_mr_far_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
-                const int *skip, const int *mdone)
-{
-    extern __shared__ __align__(16) unsigned char esm[];
-    if (skip && *skip) return;
-    const int2 item = items[blockIdx.x];
-    if (mdone && mdone[item.x]) return;
-    const MrMesh &Ms = ms[item.x];
-    const int leaf = item.y, rt = blockIdx.y * RT;
-    const int fl = Ms.fl, lmin = Ms.lmin, L = Ms.L, k = Ms.k, N = Ms.N;
-    const T *__restrict__ Ul = (const T *)Ms.Ul;
-    const float *__restrict__ yhat = Ms.yhat;
-    float *__restrict__ Y = Yall + (size_t)Ms.xoff * R;
-    const int b = Ms.kb[fl + leaf], n = Ms.ke[fl + leaf] - b;
-    const int nlev = L - lmin + 1, NL = nlev * k, NL16 = far_round16(NL), LE = far_lrow<T>(k);
-    const int mtiles = (n + 15) / 16, nrow = mtiles * 16;
-    const bool async = (k * (int)sizeof(T)) % 16 == 0;
-    float *Ys = (float *)esm;                                           // [NL16][FLDX]
-    T *Ur = (T *)(esm + (size_t)NL16 * FLDX * sizeof(float));          // [nlev][nrow][LE]
-    for (int l = 0; l < nlev; ++l) {
-        const int node = ((fl + leaf + 1) >> (L - (lmin + l))) - 1;
-        stage_rows<float>(Ys + (size_t)l * k * FLDX, FLDX, yhat + (size_t)node * k * R + rt, R, RT, k, k, true);
-        stage_rows<T>(Ur + (size_t)l * nrow * LE, LE, Ul + ((size_t)l * N + b) * k, k, k, n, nrow, async);
-    }
-    for (int e = NL * FLDX + threadIdx.x; e < NL16 * FLDX; e += blockDim.x) Ys[e] = 0.f;
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
-    const int mt = warp & 3, nb = (warp >> 2) * 4;
-    if (mt >= mtiles) return;
-    const int i0 = mt * 16 + g;
-    float acc[4][4];
-    for (int j = 0; j < 4; ++j)
-        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-    for (int k0 = 0; k0 < NL16; k0 += 8) {
-        // the two columns (lva) this lane reads: k0 + t4 and k0 + t4 + 4
-        const int v0 = k0 + t4, v1 = v0 + 4;
-        const bool ok0 = v0 < NL, ok1 = v1 < NL;
-        const T *c0 = Ur + ((size_t)(ok0 ? v0 / k : 0) * nrow + i0) * LE + (ok0 ? v0 % k : 0);
-        const T *c1 = Ur + ((size_t)(ok1 ? v1 / k : 0) * nrow + i0) * LE + (ok1 ? v1 % k : 0);
-        const uint32_t a[4] = {f2tf32(ok0 ? ldf(c0) : 0.f), f2tf32(ok0 ? ldf(c0 + 8 * LE) : 0.f),
-                               f2tf32(ok1 ? ldf(c1) : 0.f), f2tf32(ok1 ? ldf(c1 + 8 * LE) : 0.f)};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float *B0 = Ys + (k0 + t4) * FLDX + (nb + j) * 8 + g;
-            const uint32_t bb[2] = {f2tf32(B0[0]), f2tf32(B0[4 * FLDX])};
-            MmaTraits<float>::mma(acc[j], a, bb);
-        }
-    }
-    for (int h = 0; h < 2; ++h) {
-        const int i = mt * 16 + g + 8 * h;
-        if (i >= n) continue;
-        float *yp = Y + (size_t)(b + i) * R + rt;
-        for (int j = 0; j < 4; ++j) {
-            float2 *p2 = (float2 *)(yp + (nb + j) * 8 + 2 * t4);
-            float2 v = *p2;
-            v.x += acc[j][2 * h];
-            v.y += acc[j][2 * h + 1];
-            *p2 = v;
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -827,20 +495,21 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
         VFD_CUDA(cudaEventCreateWithFlags(&b.ev_join, cudaEventDisableTiming));
     }
     const bool bf = b.precision == VFD_BF16;
-    size_t np = 0, nh = 0;
-    b.max_panel_w = b.max_k = b.max_nlev = b.max_leaf = 0;
+    size_t nh = 0, nc = 0;
+    b.max_panel_w = b.max_k = b.max_kp = b.max_leaf = 0;
     b.any_far = false;
     for (OpData *op : b.ops) {
         const MeshData &m = *op->m;
         VFD_REQUIRE(op->precision == b.precision, VFD_EINVAL, "batched apply: operators of different precision");
         VFD_REQUIRE(op->precision != VFD_FP64, VFD_EINVAL, "batched apply needs VFD_FP32 or VFD_BF16 operators");
         VFD_REQUIRE(m.max_leaf_size <= 64, VFD_EUNSUPPORTED, "batched apply needs leaves of at most 64 DoFs");
-        const int nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
         if (m.nfar > 0) {
-            np += (size_t)nlev * m.kt.nleaf * m.k * R;
-            nh += (size_t)m.kt.nnode * m.k * R;
+            const int kp = (m.k + 7) & ~7;
+            nh += (size_t)m.kt.nnode * kp * R;
+            nc += (size_t)m.kt.nnode * (R / RT);
             b.any_far = true;
-            b.max_nlev = std::max(b.max_nlev, nlev);
+            b.max_kp = std::max(b.max_kp, kp);
+            build_far_lowp(m, *op, st);
         }
         b.max_panel_w = std::max(b.max_panel_w, m.max_panel_w);
         b.max_k = std::max(b.max_k, m.k);
@@ -848,43 +517,31 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
     }
     VFD_REQUIRE((near_smem_bytes<float, 32, 3>(b.max_panel_w) <= 227 * 1024), VFD_EUNSUPPORTED,
                 "batched apply: near panel too wide");
-    VFD_REQUIRE(b.max_k <= 64 && couple_smem<float>(b.max_k) <= 227 * 1024, VFD_EUNSUPPORTED,
-                "batched apply: rank too large for the coupling tile");
-    VFD_REQUIRE(!b.any_far || far_smem_expand<float>(b.max_nlev, b.max_k) <= 227 * 1024, VFD_EUNSUPPORTED,
-                "batched apply: too many far levels x rank for the expansion tile");
-    VFD_REQUIRE(!b.any_far || far_smem_proj<float>(b.max_nlev, b.max_k) <= 227 * 1024, VFD_EUNSUPPORTED,
-                "batched apply: too many far levels x rank for the projection tile");
-    b.part.alloc(std::max<size_t>(np, 1));
+    VFD_REQUIRE(b.max_kp <= 64 && far_batched_smem(b.max_kp) <= 227 * 1024, VFD_EUNSUPPORTED,
+                "batched apply: rank too large for the far-field tiles");
     b.xhat.alloc(std::max<size_t>(nh, 1));
     b.yhat.alloc(std::max<size_t>(nh, 1));
+    b.fcnt.alloc(std::max<size_t>(nc, 1));
+    b.fcnt.zero(st);
     b.y2.alloc((size_t)(KSPLIT_MAX - 1) * b.ntot * R);
     b.xc.alloc((size_t)b.ntot * R * 2);   // x in BF16 for the tcgen05 kernel
     if (!b.tc_err.p) {
         b.tc_err.alloc(1);
         VFD_CUDA(cudaMemset(b.tc_err.p, 0, sizeof(int)));
     }
+    for (OpData *op : b.ops) build_batched_panels(*op->m, *op, st);
     b.n_tc_items = 0;
     if (bf) {
         // tcgen05 near kernel: pre-tiled panels, items, split partials and their counters
-        for (OpData *op : b.ops) build_tiled_panels(*op->m, *op, st);
         build_tc_items(b);
         b.tc_part.alloc((size_t)std::max(b.n_tc_items, 1) * (R / RT) * 4 * 64 * RT);
         b.tc_cnt.alloc((size_t)std::max(b.n_tc_items, 1) * (R / RT));
         b.tc_cnt.zero(st);
     }
-    if (!bf)
-        for (OpData *op : b.ops)
-            if (op->D32t.n != op->D32.n) {
-                op->D32t.alloc(op->D32.n);
-                if (op->D32.n)
-                    k_tf32_copy<<<cdiv((long long)op->D32.n, 256), 256, 0, st>>>((long long)op->D32.n, op->D32.p,
-                                                                                op->D32t.p);
-                VFD_CUDA(cudaGetLastError());
-            }
     std::vector<MrMesh> d(b.nmesh);
-    std::vector<int> li, si, ni;
+    std::vector<int> li, ni;
     std::vector<NearItem> nri;
-    size_t po = 0, ho = 0;
+    size_t ho = 0, co = 0;
     for (int i = 0; i < b.nmesh; ++i) {
         const OpData &op = *b.ops[i];
         const MeshData &m = *op.m;
@@ -911,15 +568,18 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
         e.fcol = m.far_col.p;
         e.poff = m.panel_off.p;
         e.D = bf ? (const void *)op.D16.p : (const void *)op.D32t.p;
-        e.Ul = bf ? (const void *)op.Ul16.p : (const void *)op.Ul32.p;
-        e.S = bf ? (const void *)op.S16.p : (const void *)op.S32.p;
+        e.kp = op.far_kp;
+        e.Ul = op.Up_lp.p;
+        e.E = op.Ep_lp.p;
+        e.S = op.Sp_lp.p;
         e.val = op.valBM32.p;
-        e.part = b.part.p + po;
+        e.diag = op.precision == VFD_FP32 ? op.diag32.p : nullptr;   // folded B + M (TF32 panels only)
         e.xhat = b.xhat.p + ho;
         e.yhat = b.yhat.p + ho;
+        e.cnt = b.fcnt.p + co;
         if (m.nfar > 0) {
-            po += (size_t)e.nlev * m.kt.nleaf * m.k * R;
-            ho += (size_t)m.kt.nnode * m.k * R;
+            ho += (size_t)m.kt.nnode * op.far_kp * R;
+            co += (size_t)m.kt.nnode * (R / RT);
         }
         std::vector<int> kb_h, ke_h, pw_h, goff_h;
         std::vector<int64_t> poff_h;
@@ -951,22 +611,17 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
                 li.push_back(lf);
             }
         }
-        if (m.nfar > 0) {
-            for (int nd = (1 << m.far_lmin) - 1; nd < m.kt.nnode; ++nd) {
-                si.push_back(i);
-                si.push_back(nd);
-            }
-            for (int nd = 0; nd < m.kt.nnode; ++nd) {
-                ni.push_back(i);
-                ni.push_back(nd);
-            }
-        }
+        if (m.nfar > 0)
+            for (int nd = 0; nd < m.kt.nnode; ++nd)
+                if (m.far_ptr_h[nd + 1] > m.far_ptr_h[nd]) {
+                    ni.push_back(i);
+                    ni.push_back(nd);
+                }
     }
     std::vector<unsigned char> bytes(sizeof(MrMesh) * d.size());
     memcpy(bytes.data(), d.data(), bytes.size());
     b.desc.upload(bytes);
     upload_items(b.leaf_items, li);
-    upload_items(b.sum_items, si);
     upload_items(b.node_items, ni);
     {
         std::vector<unsigned char> nb(sizeof(NearItem) * std::max<size_t>(nri.size(), 1), 0);
@@ -974,7 +629,6 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
         b.near_items.upload(nb);
     }
     b.n_leaf_items = (int)li.size() / 2;
-    b.n_sum_items = (int)si.size() / 2;
     b.n_node_items = (int)ni.size() / 2;
     b.n_near_items = (int)nri.size();
     std::vector<long long> ro(b.xoff.begin(), b.xoff.end());
@@ -992,22 +646,11 @@ template <class T>
 static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
                              const int *mdone)
 {
-    const MrMesh *ms = (const MrMesh *)b.desc.p;
-    const int k = b.max_k, nlev = b.max_nlev;
     if (b.any_far) {
-        // projections, node sums and coupling on the side stream, concurrent with the rows
+        // upsweep and coupling on the side stream, concurrent with the near panels
         VFD_CUDA(cudaEventRecord(b.ev_fork, st));
         VFD_CUDA(cudaStreamWaitEvent(b.side, b.ev_fork, 0));
-        dim3 gp(b.n_leaf_items, R / RT);
-        const size_t pshm = far_smem_proj<T>(nlev, k);
-        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pshm));
-        k_mr_far_proj<T><<<gp, 256, pshm, b.side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
-        dim3 gs(b.n_sum_items, cdiv(k * R / 4, 32));
-        k_mr_far_sum<<<gs, 256, 0, b.side>>>(ms, (const int2 *)b.sum_items.p, R, skip, mdone);
-        dim3 gc(b.n_node_items, R / RT);
-        const size_t cshm = couple_smem<T>(k);
-        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
-        k_mr_far_couple<T><<<gc, 64, cshm, b.side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
+        launch_far_side(b, R, X, b.side, skip, mdone);
         VFD_CUDA(cudaEventRecord(b.ev_join, b.side));
     }
     if (kNearCfgs[b.near_cfg].tc) {
@@ -1019,10 +662,7 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
     VFD_REQUIRE(launched, VFD_EUNSUPPORTED, "batched apply: the pinned near-panel configuration does not apply");
     if (b.any_far) {
         VFD_CUDA(cudaStreamWaitEvent(st, b.ev_join, 0));
-        dim3 ge(b.n_leaf_items, R / RT);
-        const size_t eshm = far_smem_expand<T>(nlev, k);
-        VFD_CUDA(cudaFuncSetAttribute(k_mr_far_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eshm));
-        k_mr_far_expand<T><<<ge, 256, eshm, st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
+        launch_far_down(b, R, Y, st, skip, mdone);
     }
     VFD_CUDA(cudaGetLastError());
 }
@@ -1065,73 +705,76 @@ int batch_tuning(const BatchData &b, int *chosen, float *us, int n)
     return kNearCfgCount;
 }
 
+__global__ void k_fill1f(long long n, float *__restrict__ a)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 1.f;
+}
 __global__ void k_fill1d(long long n, double *__restrict__ a)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = 1.0;
 }
 
-// the values the tensor-core kernels multiply: BF16 rounded to nearest from FP64,
-// or TF32 (cvt.rna) of the FP32 copy; returned in FP64
-__global__ void k_round_f64(long long n, int bf, const double *__restrict__ a, double *__restrict__ b)
-{
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    b[i] = bf ? (double)__bfloat162float(__double2bfloat16(a[i])) : (double)__uint_as_float(f2tf32((float)a[i]));
-}
-
-// c_i = (K_64 1)_i - (K_low 1)_i + sum_e (BM_64 - BM_32)[i, e], added to the
-// diagonal entry of row i of the FP32 B + M
-__global__ void k_comp_diag(int N, const int *__restrict__ rowptr, const int *__restrict__ colidx,
-                            const double *__restrict__ val64, const double *__restrict__ y64,
-                            const double *__restrict__ ylow, float *__restrict__ val)
+// c_i = (A_64 1)_i - (A_low 1)_i (ylow: column 0 of an interleaved block of
+// stride R), added to the FP32 diagonal of the batched operator: diag[i], or
+// the diagonal entry of the FP32 B + M row where B + M is not folded
+__global__ void k_comp_diag(int N, const double *__restrict__ y64, const float *__restrict__ ylow, int R,
+                            float *__restrict__ diag, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                            float *__restrict__ val)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double c = y64[i] - ylow[i];
-    int dg = -1;
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-        c += val64[e] - (double)val[e];
-        if (colidx[e] == i) dg = e;
+    const double c = y64[i] - (double)ylow[(size_t)i * R];
+    if (diag) {
+        diag[i] = (float)((double)diag[i] + c);
+        return;
     }
-    if (dg >= 0) val[dg] = (float)((double)val[dg] + c);
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+        if (colidx[e] == i) val[e] = (float)((double)val[e] + c);
 }
 
 // Diagonal compensation of the low-precision operators, once per operator, on
-// its first batched use: rounding the near panels, bases and coupling
-// matrices to TF32 / BF16 perturbs every entry by up to 2^-11 / 2^-8 of
-// itself, and the perturbation's row sums shift the smallest eigenvalues of
-// the (nearly zero-row-sum) operator by a fraction of the largest -- enough to
-// stall the inner CG on fine meshes.  Adding the row sums of the matrix
-// perturbation, c = A_64 1 - A_rounded 1 (both in FP64 arithmetic, so no
-// vector rounding enters c), to the FP32 diagonal makes the rounded matrix
-// exact on constant vectors: the remaining perturbation acts on differences
-// u_j - u_i only and leaves the smooth low modes alone.  The outer FP64
-// residual is unaffected.
+// its first batched use: rounding the near panels, bases, transfers and
+// coupling matrices (and B + M, folded into the panels) to TF32 / BF16
+// perturbs every entry by up to 2^-11 / 2^-8 of itself, and the perturbation's row sums shift the smallest eigenvalues
+// of the (nearly zero-row-sum) operator by a fraction of the largest -- enough
+// to stall the inner CG on fine meshes.  Adding the row sums of the
+// perturbation, c = A_64 1 - A_low 1 (A_low 1 computed by the batched
+// low-precision apply itself, before compensation), to the FP32 diagonal makes
+// the rounded operator exact on constant vectors up to FP32 arithmetic: the
+// remaining perturbation acts on differences u_j - u_i only and leaves the
+// smooth low modes alone.  The outer FP64 residual is unaffected.
+template <class T>
+static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
+                             const int *mdone);
+
+template <class T>
 static void compensate_diag(BatchData &b, cudaStream_t st)
 {
-    const int bf = b.precision == VFD_BF16 ? 1 : 0;
+    bool any = false;
+    for (OpData *op : b.ops) any |= !op->comp_done && op->m->N > 0;
+    if (!any) return;
+    const int R = b.R;
+    const long long n = (long long)b.ntot * R;
+    DBuf<float> ones, ylow;
+    ones.alloc(n);
+    ylow.alloc(n);
+    k_fill1f<<<cdiv(n, 256), 256, 0, st>>>(n, ones.p);
+    batch_apply_impl<T>(b, ones.p, ylow.p, R, st, nullptr, nullptr);
+    batch_check(b, st);
     for (int i = 0; i < b.nmesh; ++i) {
         OpData &op = *b.ops[i];
         const MeshData &m = *op.m;
         if (op.comp_done || m.N == 0) continue;
-        auto rounded = [&](const DBuf<double> &a, DBuf<double> &r) {
-            r.alloc(std::max<size_t>(a.n, 1));
-            if (a.n) k_round_f64<<<cdiv((long long)a.n, 256), 256, 0, st>>>((long long)a.n, bf, a.p, r.p);
-            VFD_CUDA(cudaGetLastError());
-        };
-        DBuf<double> Ulr, Sr, Dr, one, y64, ylow;
-        rounded(m.Ul64, Ulr);
-        rounded(op.S64, Sr);
-        rounded(op.D64, Dr);
+        DBuf<double> one, y64;
         one.alloc(m.N);
         y64.alloc(m.N);
-        ylow.alloc(m.N);
         k_fill1d<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, one.p);
-        apply_k_with(m, op, m.Ul64.p, op.S64.p, op.D64.p, one.p, y64.p, st);
-        apply_k_with(m, op, Ulr.p, Sr.p, Dr.p, one.p, ylow.p, st);
-        k_comp_diag<<<cdiv((long long)m.N, 256), 256, 0, st>>>(m.N, m.rowptr.p, m.colidx.p, op.valBM.p, y64.p,
-                                                                  ylow.p, op.valBM32.p);
+        apply_parts_ex(m, op, VFD_PART_ALL, one.p, y64.p, 1, m.N, false, st, nullptr);
+        k_comp_diag<<<cdiv((long long)m.N, 256), 256, 0, st>>>(
+            m.N, y64.p, ylow.p + (size_t)b.xoff[i] * R, R, op.precision == VFD_FP32 ? op.diag32.p : nullptr,
+            m.rowptr.p, m.colidx.p, op.valBM32.p);
         VFD_CUDA(cudaGetLastError());
         VFD_CUDA(cudaStreamSynchronize(st));
         op.comp_done = true;
@@ -1145,9 +788,13 @@ void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st,
 {
     VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
     ensure_batch(b, R, st);
-    compensate_diag(b, st);
-    if (b.precision == VFD_BF16) batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
-    else batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
+    if (b.precision == VFD_BF16) {
+        compensate_diag<__nv_bfloat16>(b, st);
+        batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
+    } else {
+        compensate_diag<float>(b, st);
+        batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
+    }
 }
 
 // column-major FP64 <-> interleaved FP32
@@ -1192,6 +839,68 @@ void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y
 }
 
 // ---------------------------------------------------------------------------
+// panels of the batched path: D + (B + M) off the diagonal, the diagonal of
+// A kept apart in FP32 (first batched use of an operator)
+// ---------------------------------------------------------------------------
+__global__ void k_fold_bm(int N, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                          const int64_t *__restrict__ pos, const double *__restrict__ val, double *__restrict__ Dp,
+                          float *__restrict__ diag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double dg = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int64_t p = pos[e];   // every entry has its own panel position
+        if (colidx[e] == i) {
+            dg = val[e] + Dp[p];
+            Dp[p] = 0.0;
+        } else {
+            Dp[p] += val[e];
+        }
+    }
+    diag[i] = (float)dg;
+}
+
+__global__ void k_to_bf16(long long n, const double *__restrict__ a, __nv_bfloat16 *__restrict__ b);
+
+__global__ void k_to_tf32(long long n, const double *__restrict__ a, float *__restrict__ b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __uint_as_float(f2tf32((float)a[i]));
+}
+
+// TF32 (VFD_FP32): B + M off the diagonal folded into the panels, the
+// diagonal in FP32 (diag32) -- the near phase reads no CSR rows.  BF16
+// (VFD_BF16): plain D in BF16 (row panels and the tiled images of the
+// tcgen05 kernel); B + M stays an FP32 CSR matrix, because BF16 rounding of
+// the large singular entries perturbs the low modes of the operator enough
+// to triple the inner iterations.
+void build_batched_panels(const MeshData &m, OpData &op, cudaStream_t st)
+{
+    if (op.bm_folded) return;
+    const long long n = (long long)op.D64.n;
+    if (op.precision == VFD_BF16) {
+        op.D16.alloc(op.D64.n);
+        if (n) k_to_bf16<<<cdiv(n, 256), 256, 0, st>>>(n, op.D64.p, (__nv_bfloat16 *)op.D16.p);
+        build_tiled_panels(m, op, op.D64.p, st);
+    } else {
+        VFD_REQUIRE(m.bm_in_panels, VFD_EUNSUPPORTED,
+                    "batched apply: some B + M entries lie outside the near blocks (admissibility lambda >= 1)");
+        DBuf<double> Dp;
+        Dp.alloc(std::max<size_t>(op.D64.n, 1));
+        if (n) VFD_CUDA(cudaMemcpyAsync(Dp.p, op.D64.p, op.D64.bytes(), cudaMemcpyDeviceToDevice, st));
+        op.diag32.alloc(m.N);
+        k_fold_bm<<<cdiv(m.N, 256), 256, 0, st>>>(m.N, m.rowptr.p, m.colidx.p, m.bm_pos.p, op.valBM.p, Dp.p,
+                                                  op.diag32.p);
+        op.D32t.alloc(op.D64.n);
+        if (n) k_to_tf32<<<cdiv(n, 256), 256, 0, st>>>(n, Dp.p, op.D32t.p);
+        VFD_CUDA(cudaStreamSynchronize(st));   // Dp is released on return
+    }
+    VFD_CUDA(cudaGetLastError());
+    op.bm_folded = true;
+}
+
+// ---------------------------------------------------------------------------
 // BF16 copies of the K data (VFD_BF16 operators)
 // ---------------------------------------------------------------------------
 __global__ void k_to_bf16(long long n, const double *__restrict__ a, __nv_bfloat16 *__restrict__ b)
@@ -1200,12 +909,6 @@ __global__ void k_to_bf16(long long n, const double *__restrict__ a, __nv_bfloat
     if (i < n) b[i] = __double2bfloat16(a[i]);
 }
 
-static void to16(const DBuf<double> &a, DBuf<unsigned short> &b, cudaStream_t st)
-{
-    b.alloc(a.n);
-    if (a.n) k_to_bf16<<<cdiv((long long)a.n, 256), 256, 0, st>>>((long long)a.n, a.p, (__nv_bfloat16 *)b.p);
-    VFD_CUDA(cudaGetLastError());
-}
 
 __global__ void k_d2f(long long n, const double *__restrict__ a, float *__restrict__ b)
 {
@@ -1213,12 +916,7 @@ __global__ void k_d2f(long long n, const double *__restrict__ a, float *__restri
     if (i < n) b[i] = (float)a[i];
 }
 
-void launch_convert_bf16(const MeshData &m, OpData &op, cudaStream_t st)
-{
-    to16(op.S64, op.S16, st);
-    to16(op.D64, op.D16, st);
-    to16(m.Ul64, op.Ul16, st);
-}
+
 
 void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st)
 {

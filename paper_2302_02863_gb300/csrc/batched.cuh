@@ -11,13 +11,16 @@ constexpr int RT = 64;   // RHS per tile
 
 // one operator of a batch, as the kernels see it (device-resident table)
 struct MrMesh {
-    int N, fl, k, L, lmin, nlev, nleaf, nnode, has_near, has_far;
+    int N, fl, k, kp, L, lmin, nlev, nleaf, nnode, has_near, has_far;
     long long xoff;   // first row of this mesh in the batch vectors
     const int *kb, *ke, *pw, *gcol, *goff, *rowptr, *colidx, *fptr, *fcol;
     const int64_t *poff;
-    const void *D, *Ul, *S;   // near panels, level bases, coupling blocks (FP32 or BF16)
+    const void *D;            // near panels (FP32 rounded to TF32, or BF16)
+    const void *Ul, *E, *S;   // leaf bases N x kp, transfers nnode x kp x kp, coupling nfar x kp x kp (rank padded)
     const float *val;         // B + M in FP32 (CSR)
-    float *part, *xhat, *yhat;   // far-field workspaces of this mesh
+    const float *diag;        // diagonal of A in FP32 (compensated), B + M off it folded into D
+    float *xhat, *yhat;       // far-field workspaces of this mesh: nnode x kp x R
+    int *cnt;                 // upsweep arrival counters, nnode x (R / 64), zero between launches
 };
 
 // one (mesh, leaf) work item of the near-panel kernel, everything it needs in one load

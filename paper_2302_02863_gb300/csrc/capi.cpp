@@ -191,6 +191,7 @@ void vfd_default_mesh_opts(vfd_mesh_opts *o)
     o->tail_R = 1.1;
     o->rho_leaf_m = 64;
     o->rho_lambda = 0.75;
+    o->inner_p = 0;
 }
 
 const char *vfd_last_error(void) { return vfd::g_err.c_str(); }
@@ -226,11 +227,11 @@ vfd_status vfd_mesh_info(vfd_mesh_t mesh, int64_t *info, int n_info)
     VFD_API_BEGIN
     VFD_REQUIRE(mesh && info && n_info >= 0, VFD_EINVAL, "bad argument");
     const MeshData &m = *mesh->m;
-    int64_t v[18] = {m.N,    m.M,     m.C,      m.npairs, m.nnz,   m.kt.L,      m.kt.nnode,  m.k,
+    int64_t v[19] = {m.N,    m.M,     m.C,      m.npairs, m.nnz,   m.kt.L,      m.kt.nnode,  m.k,
                      m.nfar, m.nnear, m.near_entries_alg, m.nQ, m.nQint, m.nrfar, m.rnear_pairs, m.near_entries,
-                     m.near_point_pairs, m.sing_points};
-    for (int i = 0; i < n_info && i < 18; ++i) info[i] = v[i];
-    for (int i = 18; i < n_info; ++i) info[i] = 0;
+                     m.near_point_pairs, m.sing_points, m.k_in ? m.k_in : m.k};
+    for (int i = 0; i < n_info && i < 19; ++i) info[i] = v[i];
+    for (int i = 19; i < n_info; ++i) info[i] = 0;
     return VFD_OK;
     VFD_API_END
 }
@@ -303,7 +304,6 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
         launch_convert_fp32(m, *op, st);
         launch_lowp_csr(m, *op, st);
     }
-    if (precision == VFD_BF16) launch_convert_bf16(m, *op, st);
     mark();
     VFD_CUDA(cudaStreamSynchronize(st));
     if (op->timed) {

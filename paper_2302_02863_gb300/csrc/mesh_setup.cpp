@@ -264,6 +264,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
     int kk = 1;
     for (int i = 0; i < d; ++i) kk *= opts.cheb_p;
     VFD_REQUIRE(kk <= KMAX, VFD_EINVAL, "rank p^d too large");
+    VFD_REQUIRE(opts.inner_p >= 0 && opts.inner_p <= opts.cheb_p, VFD_EINVAL, "inner_p must be in [0, cheb_p]");
 
     auto *m = new MeshData();
     try {
@@ -690,6 +691,29 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             goff[nleaf] = (int)gcol.size();
             m->gcol.upload(gcol);
             m->gcol_off.upload(goff);
+            // panel position of every B + M entry (flat offset into the near
+            // panels, -1 if its column is not among the row leaf's partners), for
+            // the batched low-precision apply, which folds B + M into the panels.
+            // Touching cells give overlapping support boxes, which are never
+            // admissible for lambda < 1, so every entry has a position then.
+            {
+                std::vector<int> colpos(N, -1);
+                std::vector<int64_t> bpos(m->nnz, -1);
+                for (int a = 0; a < nleaf; ++a) {
+                    const int W = pw[a];
+                    for (int c = 0; c < W; ++c)
+                        if (gcol[goff[a] + c] >= 0) colpos[gcol[goff[a] + c]] = c;
+                    for (int i = kt.begin[fl + a]; i < kt.end[fl + a]; ++i)
+                        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                            const int c = colpos[colidx[e]];
+                            if (c >= 0) bpos[e] = poff[a] + (int64_t)(i - kt.begin[fl + a]) * W + c;
+                        }
+                    for (int c = 0; c < W; ++c)
+                        if (gcol[goff[a] + c] >= 0) colpos[gcol[goff[a] + c]] = -1;
+                }
+                m->bm_in_panels = std::all_of(bpos.begin(), bpos.end(), [](int64_t v) { return v >= 0; });
+                m->bm_pos.upload(bpos);
+            }
             std::vector<int> vl(N);
             for (int a = 0; a < nleaf; ++a)
                 for (int j = kt.begin[fl + a]; j < kt.end[fl + a]; ++j) vl[j] = a;
@@ -703,15 +727,26 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             m->near_pair_row.upload(prow);
         }
 
+        // the far field of the low-precision inner operator may use a lower
+        // interpolation order (inner_p); only with admissible blocks
+        const int pin = (m->nfar > 0 && opts.inner_p > 0 && opts.inner_p != p) ? opts.inner_p : 0;
+        int kin = 0;
+        if (pin) {
+            kin = 1;
+            for (int i = 0; i < d; ++i) kin *= pin;
+        }
+        m->p_in = pin;
+        m->k_in = kin;
+
         // ---- per-leaf point sets and DoF supports; leaf bases U (Sec. 5.3, R5)
         std::vector<double> Uh;   // N x k, tree order
         {
             std::vector<int> lp_ptr(nleaf + 1, 0), lp_pts;
             std::vector<std::vector<std::pair<int, double>>> supp(N);
-            std::vector<double> U;
+            std::vector<double> U, Uin;
             std::vector<int> Uoff(nleaf);
             std::vector<int> mark(C, -1);
-            std::vector<double> lag(k);
+            std::vector<double> lag(KMAX);
             for (int lf = 0; lf < nleaf; ++lf) {
                 int node = fl + lf;
                 std::vector<int> lc;
@@ -747,15 +782,20 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                     }
                     m->max_supp = std::max(m->max_supp, (int)supp[i].size());
                     // U_{i,alpha} = sum_{q in supp(i)} w_q psi_i(q) l_alpha(q)
-                    std::vector<double> row(k, 0.0);
+                    std::vector<double> row(k, 0.0), row_in(kin, 0.0);
                     for (auto &sc : supp[i]) {
                         int id = lp_pts[base + sc.first];
                         double x[3];
                         for (int c = 0; c < d; ++c) x[c] = qpos(id, c);
                         lagrange_box(d, p, &kt.lo[(size_t)node * d], &kt.hi[(size_t)node * d], x, lag.data());
                         for (int al = 0; al < k; ++al) row[al] += sc.second * lag[al];
+                        if (kin) {
+                            lagrange_box(d, pin, &kt.lo[(size_t)node * d], &kt.hi[(size_t)node * d], x, lag.data());
+                            for (int al = 0; al < kin; ++al) row_in[al] += sc.second * lag[al];
+                        }
                     }
                     U.insert(U.end(), row.begin(), row.end());
+                    Uin.insert(Uin.end(), row_in.begin(), row_in.end());
                 }
             }
             std::vector<int> sp(N + 1, 0), sl;
@@ -780,6 +820,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             m->supp_loc.upload(sl);
             m->supp_coef.upload(sc);
             Uh = U;
+            if (kin) m->U_in64.upload(Uin);
             m->kt_Uoff.upload(Uoff);
         }
         // transfers E_c[beta][alpha] = l^parent_alpha(xi^c_beta) (nested bases,
@@ -826,6 +867,24 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                     }
             }
             m->Ul64.upload(Ul);
+            if (m->nfar > 0) m->E64.upload(E);
+            if (kin) {
+                // the lower-order interpolation of the inner operator: its Chebyshev
+                // nodes on the same boxes and its transfers
+                std::vector<double> kcin((size_t)nnode * kin * d), Ein((size_t)nnode * kin * kin, 0.0), lg(KMAX);
+                for (int n = 0; n < nnode; ++n)
+                    cheb_box(d, pin, &kt.lo[(size_t)n * d], &kt.hi[(size_t)n * d], &kcin[(size_t)n * kin * d]);
+                for (int c = 1; c < nnode; ++c) {
+                    int par = (c - 1) / 2;
+                    for (int be = 0; be < kin; ++be) {
+                        lagrange_box(d, pin, &kt.lo[(size_t)par * d], &kt.hi[(size_t)par * d],
+                                     &kcin[((size_t)c * kin + be) * d], lg.data());
+                        for (int al = 0; al < kin; ++al) Ein[((size_t)c * kin + be) * kin + al] = lg[al];
+                    }
+                }
+                m->kt_cheb_in.upload(kcin);
+                m->E_in64.upload(Ein);
+            }
         }
 
         // ---- density sweep trees (Sec. 6.2): targets = interior points, sources = all points

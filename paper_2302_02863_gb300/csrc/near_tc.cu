@@ -1,6 +1,6 @@
 // Near panels of the batched BF16 apply on the 5th-generation tensor cores,
-// the panel streamed by bulk (TMA-engine) copies, with the B + M rows fused
-// into the epilogue:  Y[leaf rows][rt .. rt+63] = D_panel Xg + (B + M) X.
+// the panel streamed by bulk (TMA-engine) copies, with the B + M rows in the
+// epilogue:  Y[leaf rows][rt .. rt+63] = D_panel Xg + (B + M) X.
 //
 // This is the dense inadmissible-leaf product of Sec. 5.2 (eq. e:k-near) for
 // 64 right-hand sides at a time, plus the sparse singular near field and the
@@ -28,7 +28,8 @@
 // they only produce accumulator rows that are never read.
 // Epilogue: warps 0 and 1 read the accumulator rows of the leaf (tensor
 // memory lanes 0..63) into shared memory; all four warps add the B + M CSR
-// rows (FP32, x in FP32) and write Y.  With the panel split over P CTAs each
+// rows (FP32, x in FP32; or only the diagonal where B + M is folded into the
+// panel) and write Y.  With the panel split over P CTAs each
 // CTA writes its partial tile; the last CTA of the item to finish (counter)
 // sums the partials in a fixed order, so the result is deterministic.
 //
@@ -216,7 +217,7 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
         // B producers (warps 2, 3): thread t copies x row k = t of every stage
         // (128 bytes = 8 core-matrix pieces of 16 bytes) with cp.async; it
         // signals a stage once its own copies of that stage have landed
-        constexpr int LAG = 1;
+        constexpr int LAG = NSTAGE - 1;   // stages of copies a thread keeps in flight
         const int t = tid - 64;
         int posted = 0, arrived = 0;
         for (int i = 0; i < n; ++i) {
@@ -335,13 +336,22 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
             v = *(const float4 *)(acc_s + row * TC_LDS + 4 * q);
         }
         const int i = i0 + row;
-        for (int c = M.rowptr[i]; c < M.rowptr[i + 1]; ++c) {
-            const float a = M.val[c];
-            const float4 x = X4[(size_t)M.colidx[c] * R4 + q];
+        if (M.diag) {   // B + M off the diagonal folded into the panel
+            const float a = M.diag[i];
+            const float4 x = X4[(size_t)i * R4 + q];
             v.x = fmaf(a, x.x, v.x);
             v.y = fmaf(a, x.y, v.y);
             v.z = fmaf(a, x.z, v.z);
             v.w = fmaf(a, x.w, v.w);
+        } else {        // B + M rows (FP32 CSR)
+            for (int c = M.rowptr[i]; c < M.rowptr[i + 1]; ++c) {
+                const float a = M.val[c];
+                const float4 x = X4[(size_t)M.colidx[c] * R4 + q];
+                v.x = fmaf(a, x.x, v.x);
+                v.y = fmaf(a, x.y, v.y);
+                v.z = fmaf(a, x.z, v.z);
+                v.w = fmaf(a, x.w, v.w);
+            }
         }
         *(float4 *)(Yall + (size_t)(it.row0 + row) * R + rt + 4 * q) = v;
     }
@@ -376,9 +386,9 @@ __global__ void k_tile_panels(const double *__restrict__ D, const int64_t *__res
 }
 
 // element offsets of the leaves' tiled images (nleaf + 1 entries) and the images
-void build_tiled_panels(const MeshData &m, OpData &op, cudaStream_t st)
+void build_tiled_panels(const MeshData &m, OpData &op, const double *D, cudaStream_t st)
 {
-    if (op.Dtc.p || m.nnear == 0) return;
+    if (m.nnear == 0) return;
     std::vector<int> pw(m.kt.nleaf);
     VFD_CUDA(cudaMemcpy(pw.data(), m.panel_w.p, sizeof(int) * pw.size(), cudaMemcpyDeviceToHost));
     const int fl = m.kt.first_leaf();
@@ -390,7 +400,7 @@ void build_tiled_panels(const MeshData &m, OpData &op, cudaStream_t st)
     op.Dtc_off = off;
     op.Dtc_doff.upload(off);
     op.Dtc.alloc(std::max<int64_t>(off.back(), 8));
-    k_tile_panels<<<m.kt.nleaf, 256, 0, st>>>(op.D64.p, m.panel_off.p, m.panel_w.p, m.kt_begin.p, m.kt_end.p, fl,
+    k_tile_panels<<<m.kt.nleaf, 256, 0, st>>>(D, m.panel_off.p, m.panel_w.p, m.kt_begin.p, m.kt_end.p, fl,
                                              op.Dtc_doff.p, (__nv_bfloat16 *)op.Dtc.p);
     VFD_CUDA(cudaGetLastError());
 }

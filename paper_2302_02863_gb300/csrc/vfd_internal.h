@@ -147,7 +147,10 @@ struct MeshData {
     DBuf<double> kt_cheb;      // nnode * k * d (node-major, point, dim)
     DBuf<int> kt_Uoff;         // nleaf
     int far_lmin = 0;          // first level with admissible blocks
-    DBuf<double> Ul64;         // per-level bases, (L - far_lmin + 1) x N x k
+    DBuf<double> Ul64;         // per-level bases, (L - far_lmin + 1) x N x k (the last slice is U)
+    DBuf<double> E64;          // transfers E_c[beta][alpha] = l^parent_alpha(xi^c_beta), nnode x k x k
+    int p_in = 0, k_in = 0;    // interpolation order / rank of the inner operator's far field (0: p, k)
+    DBuf<double> kt_cheb_in, U_in64, E_in64;   // its Chebyshev nodes, leaf bases (N x k_in), transfers
     // admissible blocks (both orders), CSR by row node
     int nfar = 0;
     std::vector<int> far_ptr_h, far_col_h;
@@ -165,6 +168,8 @@ struct MeshData {
     int64_t near_point_pairs = 0;   // kernel evaluations of the near-block build (computed blocks)
     int64_t sing_points = 0;        // 4D points of the singular rules over all touching pairs (2D)
     DBuf<int> gcol, gcol_off;  // per panel column the DoF of its x entry (-1: padding)
+    DBuf<int64_t> bm_pos;      // per B + M entry its flat position in the near panels (-1: none)
+    bool bm_in_panels = false; // every B + M entry has a panel position
     DBuf<int> vleaf;           // leaf of every DoF
     int max_panel_w = 0;
     DBuf<int> near_src;        // per block: index of the computed block it is the transpose of, or -1
@@ -207,6 +212,8 @@ struct OpData {
     DBuf<int> f_gint_s, f_gint_k;
     DBuf<double> q_s, q_lk;            // at all quadrature points
     DBuf<double> kc_s, kc_lk;          // at K-tree Chebyshev nodes
+    DBuf<double> kc_s_in, kc_lk_in;    // at the inner operator's Chebyshev nodes (low-precision operators)
+    DBuf<double> S64_in;               // the inner operator's coupling blocks, nfar x k_in x k_in
     DBuf<double> tc_s, tc_lk, sc_s, sc_lk;  // density trees' Chebyshev nodes
     DBuf<double> valB, valM, valBM;    // CSR values
     DBuf<double> rho;                  // interior points, canonical order
@@ -217,7 +224,12 @@ struct OpData {
     std::vector<int64_t> Dtc_off;      //   element offset of each leaf's image (nleaf + 1)
     DBuf<int64_t> Dtc_doff;
     DBuf<float> D32t;                  // D32 rounded to TF32 (batched tensor-core path, built on first use)
-    DBuf<unsigned short> S16, D16, Ul16;   // BF16 copies (VFD_BF16)
+    DBuf<unsigned short> D16;          // batched-path BF16 near panels (VFD_BF16, mma.sync candidates)
+    DBuf<float> diag32;                // batched TF32 path: diagonal of A (FP32, compensated); B + M off the
+                                       //   diagonal is folded into its panels D32t
+    bool bm_folded = false;            // the batched panels (D16 + Dtc, or D32t + diag32) are built
+    int far_kp = 0;                    // padded rank of the batched far-field copies (0: not built)
+    DBuf<unsigned char> Up_lp, Ep_lp, Sp_lp;   // U, E, S in the operator's low precision, rank padded (batched path)
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
     bool comp_done = false;            // valBM32's diagonal compensated (batched path, first use)
     // the batch of one used by the batched (multi-RHS) low-precision apply / solve
@@ -257,16 +269,17 @@ struct BatchData {
     std::vector<int64_t> xoff;          // first row of each mesh (nmesh + 1)
     int R = 0;                          // columns the workspaces below are built for (0: not built)
     DBuf<unsigned char> desc;           // nmesh descriptors (MrMesh)
-    DBuf<int> leaf_items, sum_items, node_items;   // (mesh, index) pairs
-    DBuf<unsigned char> near_items;                // NearItem records
-    int n_leaf_items = 0, n_sum_items = 0, n_node_items = 0, n_near_items = 0;
+    DBuf<int> leaf_items, node_items;   // (mesh, leaf) / (mesh, node with admissible blocks) pairs
+    DBuf<unsigned char> near_items;     // NearItem records
+    int n_leaf_items = 0, n_node_items = 0, n_near_items = 0;
     DBuf<long long> row_off;            // xoff on the device
-    int max_panel_w = 0, max_k = 0, max_nlev = 0, max_leaf = 0;
+    int max_panel_w = 0, max_k = 0, max_kp = 0, max_leaf = 0;
     int near_cfg = -1;                  // tile configuration of the near-panel kernel (timed on first use)
     int forced_cfg = -1;                // >= 0: configuration pinned by the caller
     float near_cfg_us[32] = {0};        // the timings of the candidates (0: not run)
     bool any_far = false;
-    DBuf<float> part, xhat, yhat, y2;   // far-field workspaces (all meshes), second near partial
+    DBuf<float> xhat, yhat, y2;         // far-field workspaces (all meshes), near partials of a split
+    DBuf<int> fcnt;                     // upsweep arrival counters (all meshes)
     DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
     DBuf<unsigned char> xc;             // x in BF16 for the tcgen05 kernel ([ntot][R])
     DBuf<int> tc_err;                   // set by the tcgen05 kernel when a pipeline wait expires
@@ -309,8 +322,6 @@ void launch_convert_fp32(const MeshData &m, OpData &op, cudaStream_t st);
 void launch_load(const MeshData &m, const double *f, double *F, cudaStream_t st);
 void launch_selftest_math(const MeshData &m, int which, long long n, const double *x, double *out, cudaStream_t st);
 // apply.cu
-void apply_k_with(const MeshData &m, OpData &op, const double *Ul, const double *S, const double *D, const double *X,
-                  double *Y, cudaStream_t st);
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                     bool lowp, cudaStream_t st, const int *skip);
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
@@ -333,13 +344,18 @@ void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y
                           cudaStream_t st);
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
                        int max_it, int *iters, double *relres, cudaStream_t st);
-void launch_convert_bf16(const MeshData &m, OpData &op, cudaStream_t st);
+void build_batched_panels(const MeshData &m, OpData &op, cudaStream_t st);
 // near_tc.cu (tcgen05 near panels with bulk-copied panel stages, BF16)
-void build_tiled_panels(const MeshData &m, OpData &op, cudaStream_t st);
+void build_tiled_panels(const MeshData &m, OpData &op, const double *D, cudaStream_t st);
 void build_tc_items(BatchData &b);
 size_t near_tma_smem(int nstage);
 bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X, float *Y, cudaStream_t st,
                      const int *skip, const int *mdone);
+// far_batched.cu (nested H^2 far field of the batched apply)
+void build_far_lowp(const MeshData &m, OpData &op, cudaStream_t st);
+size_t far_batched_smem(int kp);
+void launch_far_side(BatchData &b, int R, const float *X, cudaStream_t side, const int *skip, const int *mdone);
+void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone);
 void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st);
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st);

@@ -29,7 +29,7 @@ TIMING_KEYS = ["fields", "coupling", "near", "density", "singular", "gather", "t
 VFD_FIELD_ANALYTIC, VFD_FIELD_NODAL = 0, 1
 INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "nodes", "rank",
              "far_blocks", "near_blocks", "near_entries", "n_q", "n_qint", "rho_far_blocks",
-             "rho_near_pairs", "near_storage", "near_point_pairs", "sing_points"]
+             "rho_near_pairs", "near_storage", "near_point_pairs", "sing_points", "inner_rank"]
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
            "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_grad", "vfd_load", "vfd_op_rho", "vfd_op_timings",
@@ -47,7 +47,7 @@ class VfdError(RuntimeError):
 class MeshOpts(C.Structure):
     _fields_ = [("leaf_m", C.c_int), ("cheb_p", C.c_int), ("lam", C.c_double), ("n_sing", C.c_int),
                 ("tail_mode", C.c_int), ("tail_R", C.c_double), ("rho_leaf_m", C.c_int),
-                ("rho_lambda", C.c_double)]
+                ("rho_lambda", C.c_double), ("inner_p", C.c_int)]
 
 
 class FieldStruct(C.Structure):
@@ -182,7 +182,7 @@ def vfd_default_mesh_opts():
 
 def vfd_mesh(d, coords, cells, cell_is_interior, opts=None, **kw):
     """Build a mesh handle (host arrays).  kw overrides fields of the default
-    options (leaf_m, cheb_p, lam, n_sing, tail_mode, tail_R, rho_leaf_m, rho_lambda)."""
+    options (leaf_m, cheb_p, lam, n_sing, tail_mode, tail_R, rho_leaf_m, rho_lambda, inner_p)."""
     L = load()
     o = vfd_default_mesh_opts() if opts is None else opts
     for k, v in kw.items():

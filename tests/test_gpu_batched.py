@@ -111,3 +111,35 @@ def test_every_near_configuration(disk, prec, tol):
             d = (torch.linalg.norm(Y - ref) / torch.linalg.norm(ref)).item()
             assert d < 1e-5, (c, chosen, d)
     assert seen_tc == (prec == vfd.VFD_BF16)   # the tcgen05 kernels run with BF16 operands
+
+
+def test_inner_order_refinement_reaches_fp64_solution(disk):
+    """A mesh with Chebyshev p = 6 whose low-precision inner operator uses
+    p = 4 (inner_p): the batched apply stays within the BF16 / TF32 rounding
+    of the FP64 (p = 6) operator, and the mixed-precision solve converges to
+    the FP64 operator's solution (its residual is the FP64 operator's)."""
+    m, s, k = disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=32, cheb_p=6, lam=0.75, rho_lambda=0.75,
+                        inner_p=4)
+    assert mesh.info["rank"] == 36 and mesh.info["inner_rank"] == 16 and mesh.info["far_blocks"] > 0
+    op64 = vfd.vfd_assemble(mesh, s, k, 0.9)
+    n = mesh.n_dof
+    g = torch.Generator(device="cuda").manual_seed(21)
+    X = torch.randn(64, n, dtype=torch.float64, device="cuda", generator=g)
+    Y64 = torch.empty_like(X)
+    vfd.vfd_apply(op64, X, Y64)
+    U64 = torch.zeros_like(X)
+    st, it, rel = vfd.vfd_solve(op64, X, U64, rtol=1e-11, max_it=20000)
+    assert st == vfd.VFD_OK
+    for prec, tol in ((vfd.VFD_FP32, 2e-3), (vfd.VFD_BF16, 2e-2)):
+        opl = vfd.vfd_assemble(mesh, s, k, 0.9, precision=prec)
+        Yl = torch.empty_like(X)
+        vfd.vfd_apply(opl, X, Yl)
+        torch.cuda.synchronize()
+        err = (torch.linalg.norm(Yl - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)).max().item()
+        assert err < tol, (prec, err)
+        U = torch.zeros_like(X)
+        st, it, rel = vfd.vfd_solve(opl, X, U, rtol=1e-10, max_it=20000)
+        assert st == vfd.VFD_OK and np.all(rel <= 1e-10)
+        d = (torch.linalg.norm(U - U64, dim=1) / torch.linalg.norm(U64, dim=1)).max().item()
+        assert d < 1e-8, (prec, d)

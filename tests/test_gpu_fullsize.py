@@ -1,11 +1,12 @@
 """Parity at the benchmark's full size: the 2D disk of 27,361 DoFs (34,027
-vertices), the benchmark's fields and mesh options (leaf 64, Chebyshev p = 4,
+vertices), the benchmark's fields and mesh options (leaf 64, Chebyshev p = 7,
 lambda = 0.75, FP64), in the launch configuration bench.py times.
 
 * sampled rows of A x against the oracle's exact rows (oracle.apply_rows,
   no approximation): exact-mode operator (every block near, direct density)
-  to 1e-11, and the H^2 operator of the benchmark to the rank-16
-  interpolation tolerance;
+  to 1e-11; the benchmark's H^2 operator (rank 49) to the matvec tolerance
+  1e-6 (its measured error is about 1.5e-7); the rank-16 operator (p = 4) to
+  its interpolation error (about 3e-5);
 * the FP64 CG solution's true residual, and the 64-RHS TF32 / BF16
   refinement's residuals through the FP64 operator;
 * the adjoint gradient's log-kappa shift identity sum_k g_k = -Lam^T A U
@@ -24,7 +25,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2302_02863_gb300 import vfd  # noqa: E402
 
-NROWS = 24
+NROWS = 48
 
 
 @pytest.fixture(scope="module")
@@ -34,14 +35,14 @@ def disk():
     return m, s, k, prm, dof_o, N
 
 
-def _mesh(m, prm, lam):
-    return vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"], lam=lam,
-                        rho_lambda=lam, tail_mode=prm["tail"], tail_R=prm["R"])
+def _mesh(m, prm, lam, p=None):
+    return vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=p or prm["p"],
+                        lam=lam, rho_lambda=lam, tail_mode=prm["tail"], tail_R=prm["R"])
 
 
-def _sampled_rows(disk, lam, tol):
+def _sampled_rows(disk, lam, tol, p=None):
     m, s, k, prm, dof_o, N = disk
-    mesh = _mesh(m, prm, lam)
+    mesh = _mesh(m, prm, lam, p)
     dof_g, n = vfd.vfd_mesh_dofs(mesh)
     assert n == N
     op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"])
@@ -71,8 +72,14 @@ def test_fullsize_exact_mode_sampled_rows(disk):
 
 
 def test_fullsize_h2_sampled_rows(disk):
-    # the benchmark operator: rank-16 Chebyshev interpolation of the far field
-    _sampled_rows(disk, 0.75, 5e-4)
+    # the benchmark operator: rank-49 Chebyshev interpolation of the far field
+    # meets the matvec tolerance 1e-6 of the hot-path definition
+    _sampled_rows(disk, 0.75, 1e-6)
+
+
+def test_fullsize_rank16_sampled_rows(disk):
+    # rank 16 (p = 4): the interpolation error is about 3e-5
+    _sampled_rows(disk, 0.75, 1e-4, p=4)
 
 
 def test_fullsize_solves(disk):
