@@ -351,6 +351,7 @@ __global__ void k_mr_rows(const MrMesh *__restrict__ ms, const long long *__rest
         acc.z = fmaf(dg, x.z, acc.z);
         acc.w = fmaf(dg, x.w, acc.w);
     } else {
+#pragma unroll 4
         for (int c = Ms.rowptr[i]; c < Ms.rowptr[i + 1]; ++c) {
             const float v = Ms.val[c];
             const float4 x = X4[(size_t)Ms.colidx[c] * R4 + q];
@@ -644,7 +645,7 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
 
 template <class T>
 static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
-                             const int *mdone)
+                             const int *mdone, bool x_bf16_ready)
 {
     if (b.any_far) {
         // upsweep and coupling on the side stream, concurrent with the near panels
@@ -653,7 +654,7 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
         launch_far_side(b, R, X, b.side, skip, mdone);
         VFD_CUDA(cudaEventRecord(b.ev_join, b.side));
     }
-    if (kNearCfgs[b.near_cfg].tc) {
+    if (kNearCfgs[b.near_cfg].tc && !x_bf16_ready) {
         const long long n = (long long)b.ntot * R;
         k_x_to_bf16<<<cdiv(n, 256), 256, 0, st>>>(n, X, (__nv_bfloat16 *)b.xc.p);
         VFD_CUDA(cudaGetLastError());
@@ -684,8 +685,11 @@ void batch_check(BatchData &b, cudaStream_t st)
     int e = 0;
     VFD_CUDA(cudaMemcpyAsync(&e, b.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     VFD_CUDA(cudaStreamSynchronize(st));
-    if (e) VFD_CUDA(cudaMemset(b.tc_err.p, 0, sizeof(int)));   // reported once; later calls start clean
-    VFD_REQUIRE(e == 0, VFD_ETIMEOUT, "batched apply: a tensor-core pipeline wait expired");
+    if (e) {   // reported once; later calls start clean
+        VFD_CUDA(cudaMemset(b.tc_err.p, 0, sizeof(int)));
+        if (b.gbar.p) VFD_CUDA(cudaMemset(b.gbar.p, 0, b.gbar.bytes()));
+    }
+    VFD_REQUIRE(e == 0, VFD_ETIMEOUT, "batched apply / solve: a bounded device wait expired");
 }
 
 // the near-panel tuning of a batch: chosen (stage width, depth, split, warps, accumulator sets)
@@ -747,7 +751,7 @@ __global__ void k_comp_diag(int N, const double *__restrict__ y64, const float *
 // smooth low modes alone.  The outer FP64 residual is unaffected.
 template <class T>
 static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
-                             const int *mdone);
+                             const int *mdone, bool x_bf16_ready);
 
 template <class T>
 static void compensate_diag(BatchData &b, cudaStream_t st)
@@ -761,7 +765,7 @@ static void compensate_diag(BatchData &b, cudaStream_t st)
     ones.alloc(n);
     ylow.alloc(n);
     k_fill1f<<<cdiv(n, 256), 256, 0, st>>>(n, ones.p);
-    batch_apply_impl<T>(b, ones.p, ylow.p, R, st, nullptr, nullptr);
+    batch_apply_impl<T>(b, ones.p, ylow.p, R, st, nullptr, nullptr, false);
     batch_check(b, st);
     for (int i = 0; i < b.nmesh; ++i) {
         OpData &op = *b.ops[i];
@@ -784,17 +788,31 @@ static void compensate_diag(BatchData &b, cudaStream_t st)
 // Y = A_low X for R (multiple of 64) interleaved FP32 columns over all meshes;
 // skip: device flag, nonzero = launch nothing; mdone: per-mesh device flags,
 // nonzero = leave that mesh's rows of Y alone (both may be null)
-void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip, const int *mdone)
+void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip, const int *mdone,
+                 bool x_bf16_ready)
 {
     VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
     ensure_batch(b, R, st);
     if (b.precision == VFD_BF16) {
         compensate_diag<__nv_bfloat16>(b, st);
-        batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone);
+        batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone, x_bf16_ready);
     } else {
         compensate_diag<float>(b, st);
-        batch_apply_impl<float>(b, X, Y, R, st, skip, mdone);
+        batch_apply_impl<float>(b, X, Y, R, st, skip, mdone, x_bf16_ready);
     }
+}
+
+// p (interleaved FP32, R columns) into the tcgen05 kernel's BF16 x block
+void batch_x_to_bf16(BatchData &b, const float *X, int R, cudaStream_t st)
+{
+    const long long n = (long long)b.ntot * R;
+    k_x_to_bf16<<<cdiv(n, 256), 256, 0, st>>>(n, X, (__nv_bfloat16 *)b.xc.p);
+    VFD_CUDA(cudaGetLastError());
+}
+
+void *batch_tc_x(BatchData &b)
+{
+    return (b.near_cfg >= 0 && kNearCfgs[b.near_cfg].tc) ? (void *)b.xc.p : nullptr;
 }
 
 // column-major FP64 <-> interleaved FP32

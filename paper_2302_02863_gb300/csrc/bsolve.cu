@@ -21,6 +21,8 @@
 // block of a mesh sums that mesh's block partials in a fixed order); a device
 // flag ends a captured chunk of iterations once every column of every mesh
 // has converged.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -337,6 +339,185 @@ __global__ void k_b_resid(int N, int64_t ld, const double *__restrict__ F, const
     }
 }
 
+__device__ __forceinline__ uint64_t b_gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// grid-wide barrier of a cooperative launch (every block resident): arrival
+// counter + generation, the wait bounded by the global timer; false (and
+// *err set) if the other blocks did not arrive in time
+__device__ bool grid_barrier(unsigned *cnt, unsigned *gen, unsigned nblocks, long long wait_ns, int *err)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok_s = 1;
+        const unsigned g = atomicAdd(gen, 0u);
+        __threadfence();
+        if (atomicAdd(cnt, 1u) == nblocks - 1) {
+            atomicExch(cnt, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t deadline = b_gtimer() + (uint64_t)wait_ns;
+            while (atomicAdd(gen, 0u) == g)
+                if (b_gtimer() > deadline) {
+                    ok_s = 0;
+                    atomicOr(err, 1);
+                    break;
+                }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// the sum over the blocks of mesh m of the per-column partials red[block][c],
+// in block order (every block of the mesh gets the same value)
+__device__ __forceinline__ float mesh_sum(const Seg &S, const float *red, int m, int c)
+{
+    const int b0 = S.mesh[4 * m], nb = S.mesh[4 * m + 1];
+    float s = 0.f;
+    for (int bI = 0; bI < nb; ++bI) s += __ldcg(red + (size_t)(b0 + bI) * S.Rp + c);
+    return s;
+}
+
+// One CG iteration's vector work after q = A p, for every (mesh, column), in
+// one cooperative launch with two grid barriers:
+//   A: p.q (block partials) | alpha = r.p / p.q per column
+//   B: x += alpha p, r -= alpha q, r.r (partials) | beta, convergence
+//   C: p = r + beta p, and p in BF16 for the tensor-core near kernel (p16)
+// Same arithmetic and the same fixed summation orders as k_b_pq, k_b_xr and
+// k_b_p.  red2 holds the second partials (the first are still being read).
+__global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, float *__restrict__ x,
+                                               float *__restrict__ r, float *__restrict__ p,
+                                               const float *__restrict__ q, __nv_bfloat16 *__restrict__ p16,
+                                               unsigned *gbar, long long wait_ns, int *err)
+{
+    __shared__ float sh[BT];
+    __shared__ float al_s[BT], be_s[BT], rr_s[BT];   // per column (Rp <= BT)
+    __shared__ int live_s, done_s;
+    if (S.flag[BF_DONE]) return;   // stable during this launch: only written after barrier 1
+    const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
+    const bool work = !S.mdone()[m];   // likewise written only after barrier 1
+    const int nb = S.mesh[4 * m + 1], N = S.mesh[4 * m + 2], r0 = S.mesh[4 * m + 3];
+    const int Rp = S.Rp, Rc = min(Rp, (int)blockDim.x), lanes = blockDim.x / Rc;
+    const int cl = threadIdx.x % Rc, rl = threadIdx.x / Rc;
+    // A: partials of p.q
+    for (int c0 = 0; c0 < Rp; c0 += Rc) {
+        const int c = c0 + cl;
+        float v = 0.f;
+        if (work && rl < lanes && c < Rp)
+#pragma unroll 4
+            for (int i = j * lanes + rl; i < N; i += nb * lanes) {
+                const size_t t = (size_t)(r0 + i) * Rp + c;
+                v += p[t] * q[t];
+            }
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        if (rl == 0 && c < Rp) {
+            float s = 0.f;
+            for (int qq = 0; qq < lanes; ++qq) s += sh[qq * Rc + cl];
+            S.red[(size_t)blockIdx.x * Rp + c] = s;
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(gbar, gbar + 1, gridDim.x, wait_ns, err)) return;
+    // alpha per column (the exact line search r.p / p.q)
+    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+        const float pq = mesh_sum(S, S.red, m, c);
+        const float rr = scal(S, C_RR, m, c), rp = scal(S, C_RP, m, c);
+        const bool live = work && rr > scal(S, C_TOL, m, c) && pq > 0.f && rp > 0.f;
+        al_s[c] = live ? rp / pq : 0.f;
+        rr_s[c] = rr;   // read before block 0 of the mesh overwrites it after barrier 2
+        if (j == 0 && work) {
+            scal(S, C_PQ, m, c) = pq;
+            scal(S, C_AL, m, c) = al_s[c];
+        }
+    }
+    __syncthreads();
+    // B: x += alpha p; r -= alpha q; partials of r.r
+    for (int c0 = 0; c0 < Rp; c0 += Rc) {
+        const int c = c0 + cl;
+        float v = 0.f;
+        if (work && rl < lanes && c < Rp) {
+            const float al = al_s[c];
+#pragma unroll 4
+            for (int i = j * lanes + rl; i < N; i += nb * lanes) {
+                const size_t t = (size_t)(r0 + i) * Rp + c;
+                x[t] = fmaf(al, p[t], x[t]);
+                const float rn = fmaf(-al, q[t], r[t]);
+                r[t] = rn;
+                v += rn * rn;
+            }
+        }
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        if (rl == 0 && c < Rp) {
+            float s = 0.f;
+            for (int qq = 0; qq < lanes; ++qq) s += sh[qq * Rc + cl];
+            red2[(size_t)blockIdx.x * Rp + c] = s;
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(gbar, gbar + 1, gridDim.x, wait_ns, err)) return;
+    // beta and convergence per column; every block of a mesh reaches the same decision
+    if (threadIdx.x == 0) live_s = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
+        float be = 0.f;
+        if (work) {
+            const float s = mesh_sum(S, red2, m, c), rr = rr_s[c];
+            const bool moved = al_s[c] != 0.f;
+            if (moved) {
+                be = rr > 0.f ? s / rr : 0.f;
+                if (s > scal(S, C_TOL, m, c)) atomicAdd(&live_s, 1);
+            }
+            if (j == 0) {
+                scal(S, C_BE, m, c) = be;
+                if (moved) {
+                    scal(S, C_RR, m, c) = s;
+                    scal(S, C_RP, m, c) = s;   // r_new . p_old = 0, so r_new . p_new = rr_new
+                } else {
+                    scal(S, C_RP, m, c) = rr;  // p = r next
+                }
+            }
+        }
+        be_s[c] = be;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) done_s = work && live_s == 0;
+    __syncthreads();
+    if (j == 0 && threadIdx.x == 0 && work) {
+        S.flag[FL_CNT + S.nmesh + m] = live_s;
+        if (done_s) S.mdone()[m] = 1;
+    }
+    // C: p = r + beta p (meshes still iterating), p16 = BF16(p)
+    if (work && !done_s) {
+        const size_t base = (size_t)r0 * Rp, n = (size_t)N * Rp;
+        for (size_t e = (size_t)j * blockDim.x + threadIdx.x; e < n; e += (size_t)nb * blockDim.x) {
+            const int c = (int)(e % Rp);
+            const float v = fmaf(be_s[c], p[base + e], r[base + e]);
+            p[base + e] = v;
+            if (p16) p16[base + e] = __float2bfloat16_rn(v);
+        }
+    }
+    if (!grid_barrier(gbar, gbar + 1, gridDim.x, wait_ns, err)) return;
+    // the whole batch: iteration count, done when no column anywhere is live
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int tot = 0;
+        for (int mm = 0; mm < S.nmesh; ++mm)
+            if (!S.mdone()[mm]) tot += __ldcg(S.flag + FL_CNT + S.nmesh + mm);
+        const int it = S.flag[BF_IT] + 1;
+        S.flag[BF_IT] = it;
+        if (tot == 0 || it >= S.flag[BF_MAX]) S.flag[BF_DONE] = 1;
+    }
+}
+
 }  // namespace
 
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
@@ -378,6 +559,7 @@ static void ensure_solve(BatchData &b, int Rp)
     b.q.alloc(nv);
     b.b.alloc(nv);
     b.red.alloc((size_t)nred * Rp);
+    b.red2.alloc((size_t)nred * Rp);
     b.sc.alloc((size_t)C_N * b.nmesh * Rp);
     b.flag.alloc(FL_CNT + 3 * (size_t)b.nmesh);
     VFD_CUDA(cudaMemset(b.flag.p, 0, b.flag.bytes()));
@@ -405,16 +587,46 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
     const Seg S = make_seg(b, Rp);
     batch_apply(b, b.p.p, b.q.p, Rp, st, nullptr, nullptr);
     if (b.exec) return;
+    // the fused vector kernel needs every block resident (cooperative launch)
+    // and at most BT columns; p in BF16 goes to the tensor-core kernel's x
+    // block when that kernel is the tuned one
+    {
+        int dev = 0, nsm = 0, per = 0, coop = 0;
+        VFD_CUDA(cudaGetDevice(&dev));
+        VFD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        VFD_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        VFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_iter, BT, 0));
+        b.fused = coop && Rp <= BT && b.nred <= per * nsm;
+        b.p16_target = batch_tc_x(b) ;
+        if (b.fused && !b.gbar.p) {
+            b.gbar.alloc(2);
+            VFD_CUDA(cudaMemset(b.gbar.p, 0, 2 * sizeof(unsigned)));
+        }
+    }
     cudaStream_t cs;
     VFD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph;
     VFD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     try {
         for (int it = 0; it < BCHUNK; ++it) {
-            batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh);
-            k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
-            k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p);
-            k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p);
+            batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh, b.fused);
+            if (b.fused) {
+                // one cooperative launch for the iteration's vector work; p also in
+                // BF16 for the next apply's tensor-core near kernel
+                Seg Sv = S;
+                float *red2 = b.red2.p, *xv = b.x.p, *rv = b.r.p, *pv = b.p.p;
+                const float *qv = b.q.p;
+                __nv_bfloat16 *p16 = (__nv_bfloat16 *)b.p16_target;
+                unsigned *gb = b.gbar.p;
+                long long wns = b.wait_ns;
+                int *err = b.tc_err.p;
+                void *args[] = {&Sv, &red2, &xv, &rv, &pv, &qv, &p16, &gb, &wns, &err};
+                VFD_CUDA(cudaLaunchCooperativeKernel((const void *)k_b_iter, b.nred, BT, args, 0, cs));
+            } else {
+                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
+                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p);
+                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p);
+            }
         }
     } catch (...) {
         cudaStreamEndCapture(cs, &graph);
@@ -546,6 +758,8 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
     k_b_init<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, tol2_d.p, std::max(1, max_it));
     VFD_CUDA(cudaGetLastError());
     capture_bcg(b, Rp, st);
+    // the captured apply reads p in BF16 from the fused kernel: provide the first one
+    if (b.fused && b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
     const float drop2 = (float)(RU_DROP * RU_DROP);
     int it = 0;
     while (true) {
@@ -583,6 +797,7 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
         k_b_replace<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, gamma_d.p, tol2_d.p, upd_d.p);
         k_b_rp<<<b.nred, BT, 0, st>>>(S, b.r.p, b.p.p, upd_d.p);
         VFD_CUDA(cudaGetLastError());
+        if (b.fused && b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
     }
     VFD_CUDA(cudaStreamSynchronize(st));
     if (iters)

@@ -190,7 +190,7 @@ __device__ __forceinline__ void acc_add(float (&acc)[8][4], const float *src, si
 }  // namespace
 
 // shared memory of the three kernels (floats)
-static size_t fb_smem_up(int kp) { return 4 * ((size_t)64 * LDB + (size_t)64 * lda_t(kp) + (size_t)kp * LDB + (size_t)kp * lda_t(kp)); }
+static size_t fb_smem_up(int kp) { return 4 * ((size_t)64 * LDB + (size_t)64 * lda_t(kp) + 2 * (size_t)kp * LDB + 2 * (size_t)kp * lda_t(kp)); }
 static size_t fb_smem_couple(int kp) { return 4 * ((size_t)kp * lda_t(kp) + (size_t)kp * LDB); }
 static size_t fb_smem_down(int kp) { return 4 * ((size_t)kp * lda_r(kp) + (size_t)kp * LDB + (size_t)64 * lda_r(kp)); }
 
@@ -212,8 +212,10 @@ k_fb_up(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, co
     const int LA = lda_t(kp);
     float *Xs = fsm;                 // [64][LDB]   x rows of the leaf
     float *Us = Xs + 64 * LDB;       // [64][LA]    U rows of the leaf (A transposed)
-    float *Hs = Us + 64 * LA;        // [kp][LDB]   a child's xhat
-    float *Es = Hs + kp * LDB;       // [kp][LA]    a child's transfer (A transposed)
+    float *Ho = Us + 64 * LA;        // [kp][LDB]   xhat of the CTA's current node
+    float *Hb = Ho + kp * LDB;       // [kp][LDB]   xhat of its sibling
+    float *E1 = Hb + kp * LDB;       // [kp][LA]    transfers of the two children (A transposed)
+    float *E2 = E1 + kp * LA;
     const T *U = (const T *)M.Ul, *E = (const T *)M.E;
     float *xhat = M.xhat;
     const size_t hs = (size_t)kp * R;   // node stride of xhat
@@ -225,11 +227,16 @@ k_fb_up(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, co
     __syncthreads();
     float acc[8][4];
     acc_zero(acc);
-    if (16 * (threadIdx.x >> 5) < kp) cta_gemm<true>(acc, Us, LA, Xs, npad);
+    const bool mw = 16 * (threadIdx.x >> 5) < kp;   // this warp owns rows of the result
+    if (mw) cta_gemm<true>(acc, Us, LA, Xs, npad);
     acc_store(acc, xhat + (size_t)node * hs + rt, R, kp, false);
+    acc_store(acc, Ho, LDB, kp, false);
     int lev = M.L;
     while (lev > M.lmin) {
-        const int par = (node - 1) / 2;
+        const int par = (node - 1) / 2, c1 = 2 * par + 1, sib = node == c1 ? c1 + 1 : c1;
+        // the transfers are fixed data: fetch them before waiting for the sibling
+        stage<T>(E1, LA, E + (size_t)c1 * kp * kp, kp, kp, kp);
+        stage<T>(E2, LA, E + (size_t)(c1 + 1) * kp * kp, kp, kp, kp);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -240,15 +247,18 @@ k_fb_up(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, co
         __syncthreads();
         if (!last) return;
         __threadfence();
+        stage_x(Hb, xhat + (size_t)sib * hs + rt, R, kp, kp);
+        __syncthreads();
+        // always child 1 then child 2, whichever CTA arrived last
+        const float *H1 = node == c1 ? Ho : Hb, *H2 = node == c1 ? Hb : Ho;
         acc_zero(acc);
-        for (int c = 2 * par + 1; c <= 2 * par + 2; ++c) {   // always child 1 then child 2
-            stage_x(Hs, xhat + (size_t)c * hs + rt, R, kp, kp);
-            stage<T>(Es, LA, E + (size_t)c * kp * kp, kp, kp, kp);
-            __syncthreads();
-            if (16 * (threadIdx.x >> 5) < kp) cta_gemm<true>(acc, Es, LA, Hs, kp);
-            __syncthreads();
+        if (mw) {
+            cta_gemm<true>(acc, E1, LA, H1, kp);
+            cta_gemm<true>(acc, E2, LA, H2, kp);
         }
+        __syncthreads();   // Ho read by every warp
         acc_store(acc, xhat + (size_t)par * hs + rt, R, kp, false);
+        acc_store(acc, Ho, LDB, kp, false);
         node = par;
         --lev;
     }

@@ -134,6 +134,7 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
     uint32_t *tslot = (uint32_t *)(bars + 3 * NSTAGE + 1);
     volatile int *abort_f = (volatile int *)(tslot + 1);
     int *last_f = (int *)(tslot + 2);
+    int *gs = (int *)(tslot + 4);   // gather columns of this CTA's stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rt = blockIdx.y * RT, ksplit = gridDim.z, z = blockIdx.z;
     const int s0 = (int)(((long long)it.nst * z) / ksplit), n = (int)(((long long)it.nst * (z + 1)) / ksplit) - s0;
@@ -152,6 +153,10 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         *abort_f = 0;
+    }
+    for (int c = tid; c < n * TC_NK; c += 128) {
+        const int col = s0 * TC_NK + c;
+        gs[c] = col < it.W ? it.gcol[col] : -1;
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(s_addr(tslot)));
@@ -226,8 +231,7 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
                 *abort_f = 1;
                 break;
             }
-            const int col = (s0 + i) * TC_NK + t;
-            const int g = col < it.W ? it.gcol[col] : -1;
+            const int g = gs[i * TC_NK + t];
             const unsigned char *src = g >= 0 ? Xb + ((size_t)(it.xoff + g) * R + rt) * 2 : Xb;
             unsigned char *dst = tsm + s * TC_STAGE_BYTES + 8192 + (t >> 3) * 1024 + (t & 7) * 16;
 #pragma unroll
@@ -344,6 +348,7 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
             v.z = fmaf(a, x.z, v.z);
             v.w = fmaf(a, x.w, v.w);
         } else {        // B + M rows (FP32 CSR)
+#pragma unroll 4
             for (int c = M.rowptr[i]; c < M.rowptr[i + 1]; ++c) {
                 const float a = M.val[c];
                 const float4 x = X4[(size_t)M.colidx[c] * R4 + q];
@@ -436,13 +441,16 @@ void build_tc_items(BatchData &b)
     b.tc_items.upload(bytes);
 }
 
-size_t near_tma_smem(int nstage) { return (size_t)nstage * TC_STAGE_BYTES + (3 * nstage + 1) * 8 + 16 + 1024; }
+size_t near_tma_smem(int nstage, int max_panel_w)
+{
+    return (size_t)nstage * TC_STAGE_BYTES + (3 * nstage + 1) * 8 + 16 + (size_t)(max_panel_w + TC_NK) * 4 + 1024;
+}
 
 // launch with nstage pipeline stages and the panel split over ksplit CTAs
 bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X, float *Y, cudaStream_t st,
                      const int *skip, const int *mdone)
 {
-    const size_t shm = near_tma_smem(nstage);
+    const size_t shm = near_tma_smem(nstage, b.max_panel_w);
     if (shm > 227 * 1024 || ksplit < 1 || ksplit > 4 || b.n_tc_items == 0) return false;
     const size_t need = (size_t)b.n_tc_items * (R / RT) * ksplit * 64 * RT;
     if (ksplit > 1 && b.tc_part.n < need) return false;

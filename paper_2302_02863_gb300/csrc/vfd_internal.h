@@ -289,7 +289,10 @@ struct BatchData {
     DBuf<int> tc_cnt;                   // per (item, RHS tile) arrival counters (zero between launches)
     long long wait_ns = 1000000000LL;   // bound of the tcgen05 kernel's pipeline waits
     // batched refinement solve
-    DBuf<float> x, r, p, q, b, red, sc;
+    DBuf<float> x, r, p, q, b, red, red2, sc;
+    bool fused = false;                 // the captured iteration uses the cooperative vector kernel
+    void *p16_target = nullptr;         // where that kernel writes p in BF16 (the tcgen05 x block), or null
+    DBuf<unsigned> gbar;                // its grid-barrier counter and generation
     DBuf<int> flag, red_items, red_mesh;
     int nred = 0, sR = 0;
     cudaGraphExec_t exec = nullptr;
@@ -339,7 +342,9 @@ int batch_tuning(const BatchData &b, int *chosen, float *us, int n);
 void batch_check(BatchData &b, cudaStream_t st);
 int batch_set_config(BatchData &b, int cfg);
 void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
-                 const int *mdone);
+                 const int *mdone, bool x_bf16_ready = false);
+void *batch_tc_x(BatchData &b);   // the BF16 x block of the tuned tcgen05 near kernel, or null
+void batch_x_to_bf16(BatchData &b, const float *X, int R, cudaStream_t st);
 void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,
                           cudaStream_t st);
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
@@ -348,7 +353,7 @@ void build_batched_panels(const MeshData &m, OpData &op, cudaStream_t st);
 // near_tc.cu (tcgen05 near panels with bulk-copied panel stages, BF16)
 void build_tiled_panels(const MeshData &m, OpData &op, const double *D, cudaStream_t st);
 void build_tc_items(BatchData &b);
-size_t near_tma_smem(int nstage);
+size_t near_tma_smem(int nstage, int max_panel_w);
 bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X, float *Y, cudaStream_t st,
                      const int *skip, const int *mdone);
 // far_batched.cu (nested H^2 far field of the batched apply)
