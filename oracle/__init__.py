@@ -63,6 +63,8 @@ def lib():
         L.oracle_gamma.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
         L.oracle_gamma.restype = C.c_double
         L.oracle_num_threads.restype = C.c_int
+        L.oracle_set_threads.argtypes = [C.c_int]
+        L.oracle_set_threads.restype = None
         L.oracle_cg.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.c_int]
         L.oracle_cg.restype = C.c_int
         L.oracle_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, ip, up, dp, dp, dp, C.c_int, dp, dp, dp, dp]
@@ -264,6 +266,11 @@ def gamma(d, r, sx, sy, lkx, lky):
 
 def num_threads():
     return lib().oracle_num_threads()
+
+
+def set_threads(n):
+    """OpenMP threads of the following oracle calls (for timing baselines)."""
+    lib().oracle_set_threads(int(n))
 
 
 def quad_points(mesh):

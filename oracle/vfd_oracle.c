@@ -1306,6 +1306,16 @@ int oracle_num_threads(void)
 #endif
 }
 
+/* threads of the following calls (timing baselines only) */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* plain conjugate gradients on the dense matrix (the paper's solver, Sec. 7),
  * for the CPU timing baseline: A U = F from U = 0 until ||F - A U|| <= rtol ||F||.
  * Returns the number of iterations (matrix-vector products). */
