@@ -1,11 +1,11 @@
 """Parity at the benchmark's full size: the 2D disk of 27,361 DoFs (34,027
-vertices), the benchmark's fields and mesh options (leaf 64, Chebyshev p = 7,
+vertices), the benchmark's fields and mesh options (leaf 64, Chebyshev p = 8,
 lambda = 0.75, FP64), in the launch configuration bench.py times.
 
 * sampled rows of A x against the oracle's exact rows (oracle.apply_rows,
   no approximation): exact-mode operator (every block near, direct density)
-  to 1e-11; the benchmark's H^2 operator (rank 49) to the matvec tolerance
-  1e-6 (its measured error is about 1.5e-7); the rank-16 operator (p = 4) to
+  to 1e-11; the benchmark's H^2 operator (rank 64) to the matvec tolerance
+  1e-6 (its measured error is about 1e-7); the rank-16 operator (p = 4) to
   its interpolation error (about 3e-5);
 * the FP64 CG solution's true residual, and the 64-RHS TF32 / BF16
   refinement's residuals through the FP64 operator;
@@ -72,7 +72,7 @@ def test_fullsize_exact_mode_sampled_rows(disk):
 
 
 def test_fullsize_h2_sampled_rows(disk):
-    # the benchmark operator: rank-49 Chebyshev interpolation of the far field
+    # the benchmark operator: rank-64 Chebyshev interpolation of the far field
     # meets the matvec tolerance 1e-6 of the hot-path definition
     _sampled_rows(disk, 0.75, 1e-6)
 
