@@ -70,6 +70,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-RHS mixed-precision leg")
     p.add_argument("--no-batch24", action="store_true", help="skip the 24-mesh batched leg")
+    p.add_argument("--no-graded", action="store_true", help="skip the graded-exterior leg")
     p.add_argument("--mode", default="step", choices=["step", "apply", "solve"],
                    help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
     p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
@@ -386,6 +387,8 @@ def main():
     # ---- sampled rows of A x on the GPU (checked against the oracle's exact rows in the CPU leg)
     rows = sampled_rows_gpu({"operator": mesh, "rank16": mesh16}, m, s, k, prm, prec, vfd, torch)
 
+    graded = None if args.no_graded else graded_leg(torch, vfd)
+
     batched = None
     if not args.no_batched:
         batched = batched_leg(mesh, s, k, prm, torch, vfd, hbm=hbm)
@@ -415,11 +418,55 @@ def main():
             "roofline": roof, "roofline_apply": roof_apply, "assembly_kernels": asm_k, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "rank16_operator": r16,
-            "batched_mixed_precision": batched, "batch_24_meshes": batch24,
+            "graded_exterior": graded, "batched_mixed_precision": batched, "batch_24_meshes": batch24,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def graded_leg(torch, vfd, mc=128, grade=1.5, rtol=1e-10):
+    """The square of Sec. 7.2 at T_6 (mc = 128, 16,129 DoFs): quasi-uniform
+    exterior (131,072 cells) against a graded exterior (cells growing by the
+    factor `grade` away from the interface): mesh sizes, assembly phases, CG
+    solve to rtol with f = 1, and the relative difference of the solutions
+    (s = 0.7, log kappa = 0; rank 16, lambda 0.75)."""
+    import numpy as np
+
+    import synth
+    s, k = synth.const_field(0.7), synth.const_field(0.0)
+    out = {"mc": mc, "grade": grade, "fields": "s = 0.7, kappa = 1"}
+    sols = {}
+    for name, m in (("uniform", synth.square_mesh(mc)), ("graded", synth.square_mesh_graded(mc, grade))):
+        mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior)
+        info = mesh.info
+        n = mesh.n_dof
+        F = torch.zeros(n, dtype=torch.float64, device="cuda")
+        vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device="cuda"), F)
+        vfd.vfd_assemble(mesh, s, k, 0.9)   # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        op = vfd.vfd_assemble(mesh, s, k, 0.9, flags=vfd.VFD_ASSEMBLE_TIMED)
+        U = torch.zeros_like(F)
+        st, it, rel = vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)
+        e1.record()
+        torch.cuda.synchronize()
+        ph = vfd.vfd_op_timings(op)
+        dof, _ = vfd.vfd_mesh_dofs(mesh)
+        inner = np.abs(m.coords).max(axis=1) < 1.0 - 1e-9
+        order = np.lexsort((m.coords[inner, 0], m.coords[inner, 1]))
+        u = np.zeros(m.n_vert)
+        sel = dof >= 0
+        u[sel] = U.cpu().numpy()[dof[sel]]
+        sols[name] = u[inner][order]
+        out[name] = {"cells": info["n_cell"], "n_q": info["n_q"], "n_dof": n, "rho_near_pairs": info["rho_near_pairs"],
+                     "assemble_ms": round(ph["total"], 2), "density_ms": round(ph["density"], 2),
+                     "singular_ms": round(ph["singular"], 2), "step_ms": e0.elapsed_time(e1), "cg_iters": int(it[0])}
+    out["solution_rel_diff"] = float(np.linalg.norm(sols["graded"] - sols["uniform"]) /
+                                     np.linalg.norm(sols["uniform"]))
+    out["step_speedup"] = out["uniform"]["step_ms"] / out["graded"]["step_ms"]
+    return out
 
 
 def rank16_leg(mesh16, s, k, prm, F, args, vfd, torch, flush, stream, steps=3):

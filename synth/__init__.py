@@ -19,7 +19,7 @@ from typing import Optional
 import numpy as np
 
 __all__ = [
-    "Mesh", "Field", "interval_mesh", "disk_mesh", "square_mesh",
+    "Mesh", "Field", "interval_mesh", "disk_mesh", "square_mesh", "square_mesh_graded", "graded_coordinates",
     "disk_mesh_for_dofs", "square_mesh_for_dofs", "const_field", "fourier_field",
     "random_fourier_field", "config2_s_field", "sigmoid_field", "gauss_bump_field",
     "tensor_bump_field", "nodal_field", "frac_laplacian_const", "closed_form_u",
@@ -208,6 +208,50 @@ def square_mesh(mc: int, jitter: float = 0.0, seed: int = 0) -> Mesh:
     cells = _orient(coords, cells)
     return Mesh(2, coords, cells, is_int, name=f"square_mc{mc}",
                 meta={"h": hl, "mc": mc, "seed": seed})
+
+
+def graded_coordinates(mc: int, grade: float) -> np.ndarray:
+    """1D nodes of [-2, 2]: mc equal cells on [-1, 1] (spacing h = 2/mc), and on
+    each side of it cells growing geometrically by the factor `grade` from h*grade
+    until the side's length 1 is filled; the outer cells are scaled by a common
+    factor so that the last node is exactly at +-2 (the ratio stays `grade`)."""
+    h = 2.0 / mc
+    sp = []
+    tot = 0.0
+    while tot < 1.0 - 1e-12:
+        sp.append(h * grade ** (len(sp) + 1))
+        tot += sp[-1]
+    sp = np.array(sp) / tot          # spacings of one side, summing to 1
+    inner = -1.0 + h * np.arange(mc + 1)
+    inner[-1] = 1.0
+    right = 1.0 + np.cumsum(sp)
+    right[-1] = 2.0
+    return np.concatenate([-right[::-1], inner, right])
+
+
+def square_mesh_graded(mc: int, grade: float = 1.5) -> Mesh:
+    """Triangulation of Omega = (-2,2)^2 with Omega_i = (-1,1)^2 whose exterior
+    is graded: the tensor grid of graded_coordinates(mc, grade) in x and y,
+    each rectangle cut along its (+1,+1) diagonal.  Omega_i is meshed exactly as
+    by square_mesh(mc) (the same (mc-1)^2 interior DoFs); the exterior cells
+    grow geometrically away from the interface (the remark of Sec. 7.2 on the
+    cost of M with a quasi-uniform exterior)."""
+    assert mc % 2 == 0 and grade >= 1.0
+    g = graded_coordinates(mc, grade)
+    n = len(g) - 1
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    coords = np.stack([X.ravel(), Y.ravel()], axis=1)
+    I, J = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    I, J = I.ravel(), J.ravel()
+    a, b, c, e = J * (n + 1) + I, J * (n + 1) + I + 1, (J + 1) * (n + 1) + I + 1, (J + 1) * (n + 1) + I
+    cells = np.concatenate([np.stack([a, b, c], 1), np.stack([a, c, e], 1)], axis=0).astype(np.int32)
+    cx = 0.5 * (g[I] + g[I + 1])
+    cy = 0.5 * (g[J] + g[J + 1])
+    inside = ((np.abs(cx) < 1.0) & (np.abs(cy) < 1.0)).astype(np.uint8)
+    is_int = np.concatenate([inside, inside])
+    cells = _orient(coords, cells)
+    return Mesh(2, coords, cells, is_int, name=f"square_graded_mc{mc}_g{grade:g}",
+                meta={"h": 2.0 / mc, "mc": mc, "grade": grade})
 
 
 def square_mesh_for_dofs(n_dofs: int, jitter: float = 0.2, seed: int = 0) -> Mesh:
