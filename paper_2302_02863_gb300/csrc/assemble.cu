@@ -20,7 +20,7 @@ __global__ void k_fields_points(int d, int nQ, const double *__restrict__ qx, co
     for (int j = 0; j < d; ++j) x[j] = qx[(size_t)j * nQ + i];
     const int *vid = cells + (size_t)qcell[i] * (d + 1);
     double s, lk;
-    fields2(Fs, Fk, d, x, vid, qbary + (size_t)i * 3, s, lk);
+    fields2(Fs, Fk, d, x, vid, qbary + (size_t)i * QB, s, lk);
     out_s[i] = s;
     out_lk[i] = lk;
     if (!(s >= smin && s <= smax)) atomicOr(err, 1);
@@ -289,6 +289,10 @@ void launch_singular_B_generic(const MeshData &m, OpData &op, DBuf<double> &Lbuf
 {
     Lbuf.alloc((size_t)m.npairs * 25);
     if (!m.npairs) return;
+    if (m.d == 3) {   // tetrahedra: no singular rules (B = 0, reading R20)
+        Lbuf.zero(st);
+        return;
+    }
     SingParams P;
     P.d = m.d;
     P.ns = m.opts.n_sing;
@@ -401,13 +405,13 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
     double *sx = sh;                  // CH * d
     double *ss = sx + CH * d;         // CH: b = s/2 + d/4
     double *sl = ss + CH;             // CH: a = log(kappa)/2 + log w
-    int *sv = (int *)(sl + CH);       // CH * 3 vertex ids of the source cell
+    int *sv = (int *)(sl + CH);       // CH * 4 vertex ids of the source cell
     for (int i0 = b; i0 < e; i0 += blockDim.x) {
         int i = i0 + threadIdx.x;
         bool act = i < e;
         int id = act ? P.tt_perm[i] : 0;
         double x[3] = {0, 0, 0};
-        int cv[3] = {-1, -1, -1};
+        int cv[4] = {-1, -1, -1, -1};
         double s_ = 0, l_ = 0, a_ = 0, b_ = 0;
         if (act) {
             for (int c = 0; c < d; ++c) x[c] = P.qx[(size_t)c * P.nQ + id];
@@ -433,14 +437,14 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
                     ss[t] = fma(0.5, P.qs[jd], 0.25 * d);
                     sl[t] = fma(0.5, P.qlk[jd], fast_log(P.mt, P.qw[jd]));
                     int cell = P.qcell[jd];
-                    for (int a = 0; a < 3; ++a) sv[t * 3 + a] = a < P.nv ? P.cells[(size_t)cell * P.nv + a] : -2;
+                    for (int a = 0; a < 4; ++a) sv[t * 4 + a] = a < P.nv ? P.cells[(size_t)cell * P.nv + a] : -2;
                 }
                 __syncthreads();
                 if (act)
                     for (int t = 0; t < nj; ++t) {
                         bool touch = false;
                         for (int a = 0; a < P.nv; ++a)
-                            for (int bb = 0; bb < P.nv; ++bb) touch |= (cv[a] == sv[t * 3 + bb]);
+                            for (int bb = 0; bb < P.nv; ++bb) touch |= (cv[a] == sv[t * 4 + bb]);
                         if (touch) continue;
                         double r2 = 0.0;
                         for (int c = 0; c < d; ++c) {
@@ -549,7 +553,7 @@ void launch_density(const MeshData &m, OpData &op, cudaStream_t st)
     P.g9w = m.gl9_w.p;
     P.mt = m.mtab.p;
     P.rho = op.rho.p;
-    size_t shm = 128 * (d + 2) * sizeof(double) + 128 * 3 * sizeof(int);
+    size_t shm = 128 * (d + 2) * sizeof(double) + 128 * 4 * sizeof(int);
     k_rho_points<<<m.tt.nleaf, 128, shm, st>>>(P);
     VFD_CUDA(cudaGetLastError());
     VFD_CUDA(cudaStreamSynchronize(st));   // yt is released on return
@@ -646,8 +650,8 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
     double *tx = bl + P.maxpts;                       // row tile: TQ * d coordinates, a, b
     double *ta = tx + (size_t)TQ * d;
     double *tb = ta + TQ;
-    int *bv = (int *)(tb + TQ);                       // maxpts * 3
-    int *tv = bv + (size_t)P.maxpts * 3;              // TQ * 3
+    int *bv = (int *)(tb + TQ);                       // maxpts * 4 cell vertex ids
+    int *tv = bv + (size_t)P.maxpts * 4;              // TQ * 4
     const double dq = 0.25 * d;
     for (int t = threadIdx.x; t < npb; t += blockDim.x) {
         int id = P.lp_pts[pb0 + t];
@@ -655,7 +659,7 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
         bs[t] = fma(0.5, P.qs[id], dq);
         bl[t] = 0.5 * P.qlk[id];
         int cell = P.qcell[id];
-        for (int q = 0; q < 3; ++q) bv[t * 3 + q] = q < nv ? P.cells[(size_t)cell * nv + q] : -2;
+        for (int q = 0; q < 4; ++q) bv[t * 4 + q] = q < nv ? P.cells[(size_t)cell * nv + q] : -2;
     }
     for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Dacc[t] = 0.0;
     __syncthreads();
@@ -666,7 +670,7 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
             for (int c = 0; c < d; ++c) tx[tq * d + c] = P.qx[(size_t)c * P.nQ + id];
             ta[tq] = 0.5 * P.qlk[id];
             tb[tq] = fma(0.5, P.qs[id], dq);
-            for (int u = 0; u < 3; ++u) tv[tq * 3 + u] = u < nv ? P.cells[(size_t)cell * nv + u] : -3;
+            for (int u = 0; u < 4; ++u) tv[tq * 4 + u] = u < nv ? P.cells[(size_t)cell * nv + u] : -3;
         }
         __syncthreads();
         // kernel tile G[tq][l] = gamma_T(q_{t0+tq}, q_l)
@@ -674,8 +678,8 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
             int tq = idx / npb, l = idx - tq * npb;
             bool touch = false;
             for (int u = 0; u < nv; ++u) {
-                int va = tv[tq * 3 + u];
-                for (int w = 0; w < nv; ++w) touch |= (va == bv[l * 3 + w]);
+                int va = tv[tq * 4 + u];
+                for (int w = 0; w < nv; ++w) touch |= (va == bv[l * 4 + w]);
             }
             double g = 0.0;
             if (!touch) {
@@ -716,6 +720,109 @@ __global__ void __launch_bounds__(256) k_near_build(NearParams P)
     const int W = P.panel_w[a];
     for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
         int i = t / nb, j = t - i * nb;
+        out[(size_t)i * W + j] = -2.0 * Dacc[t];
+    }
+}
+
+// The same block, with the column points tiled as well (leaf point sets too
+// large to stage whole, as with tetrahedra): for each tile of TQ row points,
+// T[tq][j] accumulates over tiles of TC column points, then the row supports
+// fold T into the block.  Every gamma_T(q, q') is still evaluated once per block.
+constexpr int NB_TC = 128;   // column points per tile
+
+__global__ void __launch_bounds__(256) k_near_build_tiled(NearParams P)
+{
+    extern __shared__ double sh[];
+    const int e = blockIdx.x;
+    if (P.near_src[e] >= 0) return;   // transposed copy, filled by k_near_transpose
+    const int a = P.prow[e], b = P.near_col[e];
+    const int d = P.d, nv = P.nv, TQ = P.TQ, TC = NB_TC;
+    const int ra = P.kt_begin[P.fl + a], na = P.kt_end[P.fl + a] - ra;
+    const int rb = P.kt_begin[P.fl + b], nb = P.kt_end[P.fl + b] - rb;
+    const int pa0 = P.lp_ptr[a], npa = P.lp_ptr[a + 1] - pa0;
+    const int pb0 = P.lp_ptr[b], npb = P.lp_ptr[b + 1] - pb0;
+    double *G = sh;                                   // TQ * TC
+    double *Tm = G + (size_t)TQ * TC;                 // TQ * maxleaf
+    double *Dacc = Tm + (size_t)TQ * P.maxleaf;       // maxleaf * maxleaf
+    double *cx = Dacc + (size_t)P.maxleaf * P.maxleaf;   // TC * d, then b, a of the column tile
+    double *cb = cx + (size_t)TC * d;
+    double *ca = cb + TC;
+    double *tx = ca + TC;                             // TQ * d, a, b of the row tile
+    double *ta = tx + (size_t)TQ * d;
+    double *tb = ta + TQ;
+    int *cv = (int *)(tb + TQ);                       // TC * 4 cell vertex ids
+    int *tv = cv + (size_t)TC * 4;                    // TQ * 4
+    const double dq = 0.25 * d;
+    for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Dacc[t] = 0.0;
+    for (int t0 = 0; t0 < npa; t0 += TQ) {
+        const int nt = min(TQ, npa - t0);
+        __syncthreads();
+        for (int tq = threadIdx.x; tq < nt; tq += blockDim.x) {
+            const int id = P.lp_pts[pa0 + t0 + tq], cell = P.qcell[id];
+            for (int c = 0; c < d; ++c) tx[tq * d + c] = P.qx[(size_t)c * P.nQ + id];
+            ta[tq] = 0.5 * P.qlk[id];
+            tb[tq] = fma(0.5, P.qs[id], dq);
+            for (int u = 0; u < 4; ++u) tv[tq * 4 + u] = u < nv ? P.cells[(size_t)cell * nv + u] : -3;
+        }
+        for (int t = threadIdx.x; t < nt * nb; t += blockDim.x) Tm[t] = 0.0;
+        for (int c0 = 0; c0 < npb; c0 += TC) {
+            const int nc = min(TC, npb - c0);
+            __syncthreads();   // previous G / column tile consumed
+            for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+                const int id = P.lp_pts[pb0 + c0 + t], cell = P.qcell[id];
+                for (int c = 0; c < d; ++c) cx[t * d + c] = P.qx[(size_t)c * P.nQ + id];
+                cb[t] = fma(0.5, P.qs[id], dq);
+                ca[t] = 0.5 * P.qlk[id];
+                for (int q = 0; q < 4; ++q) cv[t * 4 + q] = q < nv ? P.cells[(size_t)cell * nv + q] : -2;
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < nt * nc; idx += blockDim.x) {
+                const int tq = idx / nc, l = idx - tq * nc;
+                bool touch = false;
+                for (int u = 0; u < nv; ++u) {
+                    const int va = tv[tq * 4 + u];
+                    for (int w = 0; w < nv; ++w) touch |= (va == cv[l * 4 + w]);
+                }
+                double g = 0.0;
+                if (!touch) {
+                    double r2 = 0.0;
+                    for (int c = 0; c < d; ++c) {
+                        const double dd = tx[tq * d + c] - cx[l * d + c];
+                        r2 += dd * dd;
+                    }
+                    g = gamma_ab(P.mt, r2, ta[tq], ca[l], tb[tq], cb[l]);
+                }
+                G[(size_t)tq * TC + l] = g;
+            }
+            __syncthreads();
+            // T[tq][j] += sum_{(l,c) in supp(j), l in this column tile} G[tq][l - c0] c
+            for (int idx = threadIdx.x; idx < nt * nb; idx += blockDim.x) {
+                const int tq = idx / nb, j = idx - tq * nb, dj = rb + j;
+                double v = 0.0;
+                for (int s2 = P.supp_ptr[dj]; s2 < P.supp_ptr[dj + 1]; ++s2) {
+                    const int l = P.supp_loc[s2] - c0;
+                    if (l >= 0 && l < nc) v += G[(size_t)tq * TC + l] * P.supp_coef[s2];
+                }
+                Tm[idx] += v;
+            }
+        }
+        __syncthreads();
+        // Dacc[i][j] += sum_{(l,c) in supp(i), l in the row tile} c T[l - t0][j]
+        for (int idx = threadIdx.x; idx < na * nb; idx += blockDim.x) {
+            const int i = idx / nb, j = idx - i * nb, di = ra + i;
+            double v = 0.0;
+            for (int s2 = P.supp_ptr[di]; s2 < P.supp_ptr[di + 1]; ++s2) {
+                const int l = P.supp_loc[s2] - t0;
+                if (l >= 0 && l < nt) v += P.supp_coef[s2] * Tm[(size_t)l * nb + j];
+            }
+            Dacc[idx] += v;
+        }
+    }
+    __syncthreads();
+    double *out = P.D + P.near_off[e];
+    const int W = P.panel_w[a];
+    for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
+        const int i = t / nb, j = t - i * nb;
         out[(size_t)i * W + j] = -2.0 * Dacc[t];
     }
 }
@@ -773,16 +880,26 @@ void launch_near_build(const MeshData &m, OpData &op, cudaStream_t st)
     P.D = op.D64.p;
     auto shm_for = [&](int TQ) {
         return (size_t)TQ * P.maxpts * 8 + (size_t)TQ * P.maxleaf * 8 + (size_t)P.maxleaf * P.maxleaf * 8 +
-               (size_t)P.maxpts * (m.d + 2) * 8 + (size_t)TQ * (m.d + 2) * 8 + (size_t)P.maxpts * 3 * 4 +
-               (size_t)TQ * 3 * 4;
+               (size_t)P.maxpts * (m.d + 2) * 8 + (size_t)TQ * (m.d + 2) * 8 + (size_t)P.maxpts * 4 * 4 +
+               (size_t)TQ * 4 * 4;
     };
     int TQ = 32;
     while (TQ > 1 && shm_for(TQ) > 200 * 1024) TQ /= 2;
     size_t shm = shm_for(TQ);
-    VFD_REQUIRE(shm <= 220 * 1024, VFD_EUNSUPPORTED, "leaf point sets too large for the near-block kernel");
-    P.TQ = TQ;
-    VFD_CUDA(cudaFuncSetAttribute(k_near_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_near_build<<<m.nnear, 256, shm, st>>>(P);
+    if (shm <= 200 * 1024 && TQ >= 8) {
+        P.TQ = TQ;
+        VFD_CUDA(cudaFuncSetAttribute(k_near_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        k_near_build<<<m.nnear, 256, shm, st>>>(P);
+    } else {
+        // the column points tiled too (large leaf point sets, e.g. tetrahedra)
+        P.TQ = 32;
+        const size_t tshm = (size_t)P.TQ * NB_TC * 8 + (size_t)P.TQ * P.maxleaf * 8 + (size_t)P.maxleaf * P.maxleaf * 8 +
+                            (size_t)NB_TC * (m.d + 2) * 8 + (size_t)P.TQ * (m.d + 2) * 8 + (size_t)NB_TC * 4 * 4 +
+                            (size_t)P.TQ * 4 * 4;
+        VFD_REQUIRE(tshm <= 220 * 1024, VFD_EUNSUPPORTED, "leaves too large for the near-block kernel");
+        VFD_CUDA(cudaFuncSetAttribute(k_near_build_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm));
+        k_near_build_tiled<<<m.nnear, 256, tshm, st>>>(P);
+    }
     VFD_CUDA(cudaGetLastError());
     k_near_transpose<<<m.nnear, 256, 0, st>>>(m.nnear, m.near_src.p, m.near_pair_row.p, m.near_col.p, m.kt_begin.p,
                                               m.kt_end.p, P.fl, m.near_off.p, m.panel_w.p, op.D64.p);
@@ -829,11 +946,17 @@ __global__ void k_load(int N, int d, int M, const int *__restrict__ ptr, const i
         double meas;
         if (d == 1) {
             meas = fabs(vx[t[1]] - vx[t[0]]);
-        } else {
+        } else if (d == 2) {
             double x0 = vx[t[0]], y0 = vx[M + t[0]], x1 = vx[t[1]], y1 = vx[M + t[1]], x2 = vx[t[2]], y2 = vx[M + t[2]];
             meas = 0.5 * fabs((x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0));
+        } else {
+            double e[3][3];
+            for (int u = 0; u < 3; ++u)
+                for (int c = 0; c < 3; ++c) e[u][c] = vx[(size_t)c * M + t[u + 1]] - vx[(size_t)c * M + t[0]];
+            meas = fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                        e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])) / 6.0;
         }
-        double den = (d == 1) ? 6.0 : 12.0;   // int lam_a lam_b = |tau|(1+delta_ab) d!/(d+2)!
+        double den = (d == 1) ? 6.0 : (d == 2) ? 12.0 : 20.0;   // int lam_a lam_b = |tau|(1+delta_ab) d!/(d+2)!
         for (int bb = 0; bb < nv; ++bb) acc += meas * (a == bb ? 2.0 : 1.0) / den * f[t[bb]];
     }
     F[i] = acc;

@@ -454,6 +454,7 @@ vfd_status vfd_grad(vfd_op_t h, const double *U, const double *Lam, int64_t nrhs
     MeshData &m = *op.m;
     VFD_REQUIRE(op.fs.nodal && op.fk.nodal, VFD_EUNSUPPORTED, "vfd_grad needs P1 (nodal) s and log kappa");
     VFD_REQUIRE(m.opts.tail_mode == 0, VFD_EUNSUPPORTED, "vfd_grad needs a bounded exterior (tail_mode 0)");
+    VFD_REQUIRE(m.d <= 2, VFD_EUNSUPPORTED, "vfd_grad is built for d = 1, 2");
     VFD_REQUIRE(nrhs >= 1 && ld >= m.N, VFD_EINVAL, "bad nrhs or ld");
     VFD_REQUIRE(is_device_ptr(U) && is_device_ptr(Lam) && is_device_ptr(g_s) && is_device_ptr(g_logkappa),
                 VFD_EINVAL, "vfd_grad: U, Lam, g_s and g_logkappa must be device pointers");

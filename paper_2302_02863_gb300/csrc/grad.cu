@@ -45,8 +45,8 @@ __global__ void k_grad_vals(int nQ, int d, int nrhs, int64_t ld, const int *__re
         for (int a = 0; a < nv; ++a) {
             const int i = vdof[cells[(size_t)c * nv + a]];
             if (i >= 0) {
-                u += qbary[(size_t)q * 3 + a] * U[(size_t)r * ld + i];
-                l += qbary[(size_t)q * 3 + a] * Lam[(size_t)r * ld + i];
+                u += qbary[(size_t)q * QB + a] * U[(size_t)r * ld + i];
+                l += qbary[(size_t)q * QB + a] * Lam[(size_t)r * ld + i];
             }
         }
         Uq[(size_t)r * nQ + q] = u;
@@ -344,8 +344,8 @@ __global__ void k_grad_gather(int M, const int *__restrict__ qptr, const int *__
     if (v >= M) return;
     double a = 0.0, b = 0.0;
     for (int e = qptr[v]; e < qptr[v + 1]; ++e) {
-        const int code = qidx[e], q = code / 3;
-        const double w = qbary[(size_t)code];   // qbary[q * 3 + slot]
+        const int code = qidx[e], q = code / QB;
+        const double w = qbary[(size_t)code];   // qbary[q * QB + slot]
         a += 2.0 * w * hs[q];
         b -= w * h1[q];
     }
@@ -381,7 +381,7 @@ static void ensure_grad_lists(MeshData &m)
     for (int q = 0; q < m.nQ; ++q)
         for (int a = 0; a < nv; ++a) {
             const int v = m.T[(size_t)m.qcell_host[q] * nv + a];
-            qidx[qf[v]++] = q * 3 + a;
+            qidx[qf[v]++] = q * QB + a;
         }
     for (int p = 0; p < m.npairs; ++p)
         for (int a = 0; a < nv; ++a) {

@@ -252,7 +252,8 @@ void csr_from_lists(const std::vector<std::vector<T>> &lists, std::vector<int> &
 MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell, const int32_t *cells,
                      const uint8_t *inter, const vfd_mesh_opts &opts)
 {
-    VFD_REQUIRE(d == 1 || d == 2, VFD_EINVAL, "d must be 1 or 2");
+    VFD_REQUIRE(d >= 1 && d <= 3, VFD_EINVAL, "d must be 1, 2 or 3");
+    VFD_REQUIRE(d < 3 || opts.tail_mode == 0, VFD_EUNSUPPORTED, "the exterior tail is built for d = 1, 2");
     VFD_REQUIRE(n_vert > 0 && n_cell > 0 && n_vert < (1LL << 30) && n_cell < (1LL << 28), VFD_EINVAL,
                 "bad mesh size");
     VFD_REQUIRE(opts.leaf_m >= 2 && opts.leaf_m <= 256, VFD_EINVAL, "leaf_m must be in [2,256]");
@@ -289,6 +290,20 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             if (d == 1) {
                 mu = std::fabs(m->X[t[1]] - m->X[t[0]]);
                 diam = mu;
+            } else if (d == 3) {
+                const double *a = &m->X[3 * t[0]];
+                double e[3][3];
+                for (int u = 0; u < 3; ++u)
+                    for (int c = 0; c < 3; ++c) e[u][c] = m->X[3 * t[u + 1] + c] - a[c];
+                mu = std::fabs(e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                               e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                               e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])) / 6.0;
+                for (int u = 0; u < 4; ++u)
+                    for (int v = u + 1; v < 4; ++v) {
+                        double s2 = 0.0;
+                        for (int c = 0; c < 3; ++c) s2 += (m->X[3 * t[u] + c] - m->X[3 * t[v] + c]) * (m->X[3 * t[u] + c] - m->X[3 * t[v] + c]);
+                        diam = std::max(diam, std::sqrt(s2));
+                    }
             } else {
                 const double *a = &m->X[2 * t[0]], *b = &m->X[2 * t[1]], *e = &m->X[2 * t[2]];
                 mu = 0.5 * std::fabs((b[0] - a[0]) * (e[1] - a[1]) - (b[1] - a[1]) * (e[0] - a[0]));
@@ -358,8 +373,17 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             if (!m->inter[c]) cell_order.push_back(c);
         std::vector<int> cell_slot(C);
         for (int i = 0; i < C; ++i) cell_slot[cell_order[i]] = i;
-        double bq[3][3], wq[3];
-        if (d == 2) {
+        double bq[NQMAX][QB] = {}, wq[NQMAX] = {};
+        const int NQ = d == 3 ? 4 : 3;
+        m->nqc = NQ;
+        if (d == 3) {
+            // symmetric 4-point degree-2 rule (reading R20): barycentric (a, b, b, b), weights |tau|/4
+            const double a = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, b = (5.0 - std::sqrt(5.0)) / 20.0;
+            for (int q = 0; q < 4; ++q) {
+                for (int c = 0; c < 4; ++c) bq[q][c] = (c == q) ? a : b;
+                wq[q] = 0.25;
+            }
+        } else if (d == 2) {
             for (int q = 0; q < 3; ++q) {
                 for (int a = 0; a < 3; ++a) bq[q][a] = (a == q) ? 2.0 / 3.0 : 1.0 / 6.0;
                 wq[q] = 1.0 / 3.0;
@@ -377,7 +401,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
         m->nQ = C * NQ;
         m->nQint = nint * NQ;
         const int nQ = m->nQ;
-        std::vector<double> qx((size_t)nQ * d), qw(nQ), qb((size_t)nQ * 3);
+        std::vector<double> qx((size_t)nQ * d), qw(nQ), qb((size_t)nQ * QB, 0.0);
         m->qcell_host.resize(nQ);
         for (int i = 0; i < C; ++i) {
             int c = cell_order[i];
@@ -391,7 +415,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                 }
                 qw[id] = wq[q] * meas[c];
                 m->qcell_host[id] = c;
-                for (int a = 0; a < 3; ++a) qb[(size_t)id * 3 + a] = bq[q][a];
+                for (int a = 0; a < QB; ++a) qb[(size_t)id * QB + a] = bq[q][a];
             }
         }
         auto qpos = [&](int id, int dim) { return qx[(size_t)dim * nQ + id]; };
@@ -418,6 +442,9 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                 for (int c2 : nb) {
                     if (c2 < c) continue;
                     if (!m->inter[c] && !m->inter[c2]) continue;
+                    // tetrahedra: no singular rules (B = 0, reading R20); only the
+                    // cells themselves, for the sparsity of the weighted mass matrix
+                    if (d == 3 && c2 != c) continue;
                     int first = c, second = c2;
                     if (c != c2 && m->inter[c] != m->inter[c2]) {
                         first = m->inter[c] ? c : c2;
@@ -429,7 +456,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                     for (int a = 0; a < 3; ++a) pr.pv[a] = pr.qv[a] = -1;
                     if (first == second) {
                         pr.type = 3;
-                        for (int a = 0; a < nv; ++a) pr.pv[a] = pr.qv[a] = u1[a];
+                        for (int a = 0; a < std::min(nv, 3); ++a) pr.pv[a] = pr.qv[a] = u1[a];
                     } else {
                         int shared[3], ns = 0;
                         for (int a = 0; a < nv; ++a)
@@ -458,7 +485,10 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                         }
                     }
                     // local DoF list
-                    if (d == 2) {
+                    if (d == 3) {
+                        pr.nl = 4;
+                        for (int a = 0; a < 4; ++a) pr.loc[a] = u1[a];
+                    } else if (d == 2) {
                         if (pr.type == 3) { pr.nl = 3; for (int a = 0; a < 3; ++a) pr.loc[a] = pr.pv[a]; }
                         else if (pr.type == 2) { pr.nl = 4; pr.loc[0] = pr.pv[0]; pr.loc[1] = pr.pv[1]; pr.loc[2] = pr.pv[2]; pr.loc[3] = pr.qv[2]; }
                         else { pr.nl = 5; pr.loc[0] = pr.pv[0]; pr.loc[1] = pr.pv[1]; pr.loc[2] = pr.pv[2]; pr.loc[3] = pr.qv[1]; pr.loc[4] = pr.qv[2]; }
@@ -543,7 +573,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                         int e = entry(di, dj);
                         for (int q = 0; q < NQ; ++q) {
                             int id = i * NQ + q;
-                            cont.push_back({e, id, 2.0 * qw[id] * qb[(size_t)id * 3 + a] * qb[(size_t)id * 3 + b]});
+                            cont.push_back({e, id, 2.0 * qw[id] * qb[(size_t)id * QB + a] * qb[(size_t)id * QB + b]});
                         }
                     }
                 }
@@ -777,7 +807,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                         while (t[a] != v) ++a;
                         for (int q = 0; q < NQ; ++q) {
                             int id = cell_slot[c] * NQ + q;
-                            supp[i].push_back({j * NQ + q, qw[id] * qb[(size_t)id * 3 + a]});
+                            supp[i].push_back({j * NQ + q, qw[id] * qb[(size_t)id * QB + a]});
                         }
                     }
                     m->max_supp = std::max(m->max_supp, (int)supp[i].size());

@@ -66,7 +66,8 @@ struct DBuf {
 constexpr int KMAX = 64;       // max rank p^d handled by the kernels
 constexpr int PMAX = 8;        // max Chebyshev nodes per dimension
 constexpr int NSMAX = 16;      // max Gauss points per direction of the singular rules
-constexpr int NQ = 3;          // element-rule points per cell (triangle and interval)
+constexpr int QB = 4;          // stride of the barycentric coordinates of a quadrature point (d + 1 <= 4)
+constexpr int NQMAX = 4;       // element-rule points per cell: 3 (interval, triangle), 4 (tetrahedron)
 
 // ---------------------------------------------------------------------------
 // device view of a field descriptor
@@ -106,6 +107,7 @@ struct Tree {
 struct MeshData {
     int d = 2, M = 0, C = 0, N = 0;
     int nQ = 0, nQint = 0;
+    int nqc = 3;                     // element-rule points per cell
     vfd_mesh_opts opts{};
     double h_max = 0.0;
     int k = 16, p = 4;
@@ -124,7 +126,7 @@ struct MeshData {
     DBuf<double> qx;       // nQ*d SoA
     DBuf<double> qw;       // nQ
     DBuf<int> qcell;       // nQ
-    DBuf<double> qbary;    // nQ*3
+    DBuf<double> qbary;    // nQ*QB barycentric coordinates
 
     // touching pairs (unordered, canonical orientation)
     int npairs = 0;

@@ -23,7 +23,7 @@ __all__ = [
     "disk_mesh_for_dofs", "square_mesh_for_dofs", "const_field", "fourier_field",
     "random_fourier_field", "config2_s_field", "sigmoid_field", "gauss_bump_field",
     "tensor_bump_field", "nodal_field", "frac_laplacian_const", "closed_form_u",
-    "rhs_vectors", "workload",
+    "rhs_vectors", "workload", "ball_workload", "kuhn_ball_mesh",
 ]
 
 
@@ -438,6 +438,23 @@ def batch_workload(n_mesh: int = 24, n_min: int = 2000, ratio: float = 65.0, see
         k = random_fourier_field(seed + 200, 0.5)
         out.append((m, s, k, n))
     return out
+
+
+def ball_workload(n: int, seed: int = 5000):
+    """The 3D configuration: the Kuhn-grid ball kuhn_ball_mesh(n) (spacing
+    2.2/n; Omega_i the cells with centroid inside the unit ball, Omega those
+    inside radius 1.1), s = 0.2 + 0.6 exp(-4 |x - x0|^2) with x0 seeded uniform
+    in the ball of radius 0.5, log kappa a seeded 3D Fourier field (sigma 0.5).
+    Returns (mesh, s_field, logkappa_field, params)."""
+    rng = np.random.default_rng(seed)
+    while True:
+        x0 = rng.uniform(-0.5, 0.5, 3)
+        if np.linalg.norm(x0) < 0.5:
+            break
+    m = kuhn_ball_mesh(n)
+    s = gauss_bump_field(0.2, x0, 0.6, 4.0)
+    k = random_fourier_field(seed + 1, 0.5, d=3)
+    return m, s, k, dict(s_bar=0.9, tail=0, R=1.1, leaf=64, p=4, lam=0.75, x0=x0.tolist())
 
 
 def workload(name: str):
