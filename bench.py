@@ -71,6 +71,7 @@ def _args():
     p.add_argument("--no-batched", action="store_true", help="skip the 64-RHS mixed-precision leg")
     p.add_argument("--no-batch24", action="store_true", help="skip the 24-mesh batched leg")
     p.add_argument("--no-graded", action="store_true", help="skip the graded-exterior leg")
+    p.add_argument("--no-ball", action="store_true", help="skip the 3D ball leg")
     p.add_argument("--mode", default="step", choices=["step", "apply", "solve"],
                    help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
     p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
@@ -395,6 +396,7 @@ def main():
     del mesh_x
 
     graded = None if args.no_graded else graded_leg(torch, vfd)
+    ball = None if args.no_ball else ball_leg(torch, vfd)
 
     batched = None
     if not args.no_batched:
@@ -425,7 +427,8 @@ def main():
             "roofline": roof, "roofline_apply": roof_apply, "assembly_kernels": asm_k, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "rank16_operator": r16,
-            "graded_exterior": graded, "batched_mixed_precision": batched, "batch_24_meshes": batch24,
+            "graded_exterior": graded, "ball_3d": ball, "batched_mixed_precision": batched,
+            "batch_24_meshes": batch24,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -473,6 +476,71 @@ def graded_leg(torch, vfd, mc=128, grade=1.5, rtol=1e-10):
     out["solution_rel_diff"] = float(np.linalg.norm(sols["graded"] - sols["uniform"]) /
                                      np.linalg.norm(sols["uniform"]))
     out["step_speedup"] = out["uniform"]["step_ms"] / out["graded"]["step_ms"]
+    return out
+
+
+def ball_leg(torch, vfd, n=40, nrhs=16):
+    """The 3D configuration on a smaller ball: the Kuhn-grid ball with n^3 cubes
+    (n = 40: spacing 0.055, 22,321 DoFs; the full configuration has n = 88),
+    Gaussian-bump order and 3D Fourier log kappa, leaf 64, p = 4 (rank 64),
+    lambda 0.75.  B is not included: the paper gives no singular rules for
+    tetrahedron pairs (reading R20), so the operator is K + M.  FP64 assembly,
+    apply and CG (f = 1, to 1e-8); 16 seeded right-hand sides solved to 1e-8
+    with FP32 / TF32 coupling and FP64 residuals against FP64 CG."""
+    import synth
+    m, s, k, prm = synth.ball_workload(n)
+    t0 = time.perf_counter()
+    mesh = vfd.vfd_mesh(3, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"],
+                        lam=prm["lam"], rho_lambda=prm["lam"])
+    t_setup = time.perf_counter() - t0
+    info = mesh.info
+    N = mesh.n_dof
+    op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], flags=vfd.VFD_ASSEMBLE_TIMED)
+    ph = vfd.vfd_op_timings(op)
+    X = torch.randn(N, dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        vfd.vfd_apply(op, X, Y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        vfd.vfd_apply(op, X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    ta = e0.elapsed_time(e1) / 10 / 1000.0
+    F = torch.zeros(N, dtype=torch.float64, device="cuda")
+    vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device="cuda"), F)
+    U = torch.zeros_like(F)
+    e0.record()
+    st, it, rel = vfd.vfd_solve(op, F, U, rtol=1e-8, max_it=100000)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"workload": f"Kuhn ball n={n}", "n_dof": N, "cells": info["n_cell"], "rank": info["rank"],
+           "note": "B not included (no tetrahedron-pair singular rules): operator K + M",
+           "mesh_setup_s_host": t_setup, "assemble_ms": round(ph["total"], 1),
+           "phases_ms": {kk: round(v, 1) for kk, v in ph.items()}, "near_point_pairs": info["near_point_pairs"],
+           "apply_ms": ta * 1e3, "apply_dof_rhs_per_s": N / ta, "cg_iters": int(it[0]),
+           "solve_ms": e0.elapsed_time(e1), "status": int(st)}
+    g = torch.Generator(device="cuda").manual_seed(5000)
+    Fb = torch.randn(nrhs, N, dtype=torch.float64, device="cuda", generator=g)
+    U64 = torch.zeros_like(Fb)
+    e0.record()
+    vfd.vfd_solve(op, Fb, U64, rtol=1e-8, max_it=100000)
+    e1.record()
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
+    op32 = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=vfd.VFD_FP32)
+    U = torch.zeros_like(Fb)
+    vfd.vfd_solve(op32, Fb, U, rtol=1e-8, max_it=100000)   # warm-up (tuning, capture)
+    U.zero_()
+    e0.record()
+    st, it, rel = vfd.vfd_solve(op32, Fb, U, rtol=1e-8, max_it=100000)
+    e1.record()
+    torch.cuda.synchronize()
+    out["mixed_16rhs"] = {"nrhs": nrhs, "fp64_cg_ms": t64, "mixed_ms": e0.elapsed_time(e1), "status": int(st),
+                          "inner_iters": int(it[0]), "relres_max": float(rel.max()),
+                          "solution_rel_err_vs_fp64_cg": (torch.linalg.norm(U - U64, dim=1) /
+                                                          torch.linalg.norm(U64, dim=1)).max().item()}
     return out
 
 
