@@ -259,6 +259,21 @@ vfd_status vfd_apply_noalloc(vfd_op_t op, const double *X, double *Y, int64_t nr
 vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int64_t ld, double rtol,
                      int max_it, int *iters, double *relres, void *stream);
 
+/* Preconditioner of the FP64 CG of vfd_solve (the paper solves with plain
+ * CG, Sec. 7, and names a multilevel preconditioner as the next step,
+ * Sec. 8).  kind VFD_PREC_TWO_LEVEL: additive two-level preconditioner,
+ * M^-1 = sum over the leaves of the cluster tree of exact solves with the
+ * leaf's diagonal block of A, plus a coarse solve on the leaf-wise constant
+ * functions (A_c = R A R^T, R the leaf indicators); both parts are SPD, so
+ * vfd_solve runs preconditioned CG (stopping test unchanged: the residual
+ * of A).  Setup: the diagonal blocks and A_c (formed by applying A to the
+ * leaf indicators) are inverted once, on the host, in FP64; blocks until
+ * done.  VFD_PREC_NONE switches back to plain CG.  Only VFD_FP64 operators;
+ * at most 2048 leaves.  Errors: VFD_EINVAL (unknown kind, a block that is
+ * not positive definite), VFD_EUNSUPPORTED, VFD_ECUDA. */
+enum { VFD_PREC_NONE = 0, VFD_PREC_TWO_LEVEL = 1 };
+vfd_status vfd_precondition(vfd_op_t op, int kind, void *stream);
+
 /* P1 load F = M0 f (exact P1 mass matrix of the interior cells times the
  * nodal values f at all n_vert vertices).  f_nodal, F: host or device. */
 vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *stream);

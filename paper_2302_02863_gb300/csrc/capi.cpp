@@ -418,6 +418,15 @@ vfd_status vfd_solve(vfd_op_t h, const double *F, double *U, int64_t nrhs, int64
     VFD_API_END
 }
 
+vfd_status vfd_precondition(vfd_op_t h, int kind, void *stream)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h, VFD_EINVAL, "null operator");
+    precond_setup(*h->op->m, *h->op, kind, (cudaStream_t)stream);
+    return VFD_OK;
+    VFD_API_END
+}
+
 vfd_status vfd_load(vfd_mesh_t mesh, const double *f_nodal, double *F, void *stream)
 {
     VFD_API_BEGIN

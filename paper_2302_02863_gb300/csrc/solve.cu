@@ -22,7 +22,7 @@ namespace {
 
 constexpr int RB = 256;        // reduction block size
 constexpr int CHUNK = 8;       // CG iterations per captured graph
-enum { S_RR = 0, S_PQ = 1, S_BB = 2, S_TOL2 = 3, S_BETA = 4, S_TMP = 5 };
+enum { S_RR = 0, S_PQ = 1, S_BB = 2, S_TOL2 = 3, S_BETA = 4, S_TMP = 5 };   // 6, 7: PCG (r.z)
 enum { F_DONE = 0, F_ITERS = 1, F_MAXIT = 2, F_CNT = 4 };  // F_CNT..F_CNT+3: block counters
 
 int red_blocks(int n) { return std::max(1, std::min(cdiv(n, RB * 4), 264)); }
@@ -151,6 +151,11 @@ void release_graphs(OpData &op)
             op.cg_exec[i] = nullptr;
             op.cg_key[i] = nullptr;
         }
+    if (op.pcg_exec) {
+        cudaGraphExecDestroy(op.pcg_exec);
+        op.pcg_exec = nullptr;
+        op.pcg_key = nullptr;
+    }
 }
 
 // CG on (lowp ? A32 : A64) z = b, b and z in op.cg_b / op.cg_x (device, n).
@@ -240,6 +245,121 @@ static double dev_dot(const MeshData &m, OpData &op, const double *a, const doub
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// preconditioned CG (two-level preconditioner of precond.cu):
+//   z = M^-1 r = (block inverse of the leaf's diagonal block) r + R^T A_c^-1 R r
+// with R the leaf-indicator restriction.  Scalars: S_RZ = r.z, S_RZN = the new
+// r.z, S_RR = r.r (the stopping test is on the true recursive residual r).
+// ---------------------------------------------------------------------------
+namespace {
+enum { S_RZ = 6, S_RZN = 7 };
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; rr = r.r; convergence test
+__global__ void __launch_bounds__(RB) k_pcg_xr(int n, double *__restrict__ x, double *__restrict__ r,
+                                               const double *__restrict__ p, const double *__restrict__ q,
+                                               double *part, unsigned *cnt, double *scal, int *flag)
+{
+    __shared__ double sh[32];
+    if (flag[F_DONE]) return;
+    const double rz = scal[S_RZ], pq = scal[S_PQ];
+    const double alpha = (pq != 0.0) ? rz / pq : 0.0;
+    double v = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        v += ri * ri;
+    }
+    double rrn;
+    if (last_block_sum(v, part, cnt, &rrn, sh) && threadIdx.x == 0) {
+        const int it = flag[F_ITERS] + 1;
+        flag[F_ITERS] = it;
+        scal[S_RR] = rrn;
+        if (rrn <= scal[S_TOL2] || it >= flag[F_MAXIT] || !(pq > 0.0)) flag[F_DONE] = 1;
+    }
+}
+
+// p = z + (rz_new / rz) p; rz = rz_new
+__global__ void k_pcg_p(int n, const double *__restrict__ z, double *__restrict__ p, double *scal, const int *flag)
+{
+    if (flag[F_DONE]) return;
+    const double rzn = scal[S_RZN], rz = scal[S_RZ];
+    const double beta = rz != 0.0 ? rzn / rz : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_pcg_rz_commit(double *scal, const int *flag)
+{
+    if (flag && flag[F_DONE]) return;
+    scal[S_RZ] = scal[S_RZN];
+}
+}  // namespace
+
+// z = M^-1 r (precond.cu)
+void precond_apply(const MeshData &m, const OpData &op, const double *r, double *z, cudaStream_t st, const int *skip);
+
+static int run_pcg(const MeshData &m, OpData &op, double rtol, int max_it, cudaStream_t st, double *rr_out,
+                   double *bb_out)
+{
+    const int n = m.N, NB = red_blocks(n), VB = std::max(1, std::min(cdiv(n, RB), 1024));
+    double *part = op.cg_red.p;
+    unsigned *cnt = (unsigned *)(op.cg_flag.p + F_CNT);
+    int *flag = op.cg_flag.p;
+    double *scal = op.cg_scal.p;
+    // init: r = b - A x; z = M^-1 r; p = z; rz = r.z; bb; rr
+    apply_parts_ex(m, op, VFD_PART_ALL, op.cg_x.p, op.cg_q.p, 1, n, false, st, nullptr);
+    k_sub<<<VB, RB, 0, st>>>(n, op.cg_b.p, op.cg_q.p, op.cg_r.p);
+    precond_apply(m, op, op.cg_r.p, op.cg_z.p, st, nullptr);
+    VFD_CUDA(cudaMemcpyAsync(op.cg_p.p, op.cg_z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    k_dot<<<NB, RB, 0, st>>>(n, op.cg_b.p, op.cg_b.p, part, cnt, scal, S_BB, nullptr);
+    k_dot<<<NB, RB, 0, st>>>(n, op.cg_r.p, op.cg_r.p, part, cnt, scal, S_RR, nullptr);
+    k_dot<<<NB, RB, 0, st>>>(n, op.cg_r.p, op.cg_z.p, part, cnt, scal, S_RZ, nullptr);
+    k_init_flag<<<1, 1, 0, st>>>(flag, scal, rtol, max_it);
+    VFD_CUDA(cudaGetLastError());
+    cudaGraphExec_t &gexec = op.pcg_exec;
+    if (!gexec || op.pcg_key != (const void *)op.cg_p.p) {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        cudaStream_t cs;
+        VFD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        VFD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        try {
+            for (int it = 0; it < CHUNK; ++it) {
+                apply_parts_ex(m, op, VFD_PART_ALL, op.cg_p.p, op.cg_q.p, 1, n, false, cs, flag);
+                k_dot<<<NB, RB, 0, cs>>>(n, op.cg_p.p, op.cg_q.p, part, cnt, scal, S_PQ, flag);
+                k_pcg_xr<<<NB, RB, 0, cs>>>(n, op.cg_x.p, op.cg_r.p, op.cg_p.p, op.cg_q.p, part, cnt, scal, flag);
+                precond_apply(m, op, op.cg_r.p, op.cg_z.p, cs, flag);
+                k_dot<<<NB, RB, 0, cs>>>(n, op.cg_r.p, op.cg_z.p, part, cnt, scal, S_RZN, flag);
+                k_pcg_p<<<VB, RB, 0, cs>>>(n, op.cg_z.p, op.cg_p.p, scal, flag);
+                k_pcg_rz_commit<<<1, 1, 0, cs>>>(scal, flag);
+            }
+        } catch (...) {
+            cudaStreamEndCapture(cs, &graph);
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        VFD_CUDA(cudaStreamEndCapture(cs, &graph));
+        cudaStreamDestroy(cs);
+        cudaError_t ie = cudaGraphInstantiate(&gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
+        cudaGraphDestroy(graph);
+        VFD_CUDA(ie);
+        op.pcg_key = op.cg_p.p;
+    }
+    int hflag[3] = {0, 0, 0};
+    while (true) {
+        VFD_CUDA(cudaGraphLaunch(gexec, st));
+        VFD_CUDA(cudaMemcpyAsync(hflag, flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaStreamSynchronize(st));
+        if (hflag[F_DONE]) break;
+    }
+    double hs[3];
+    VFD_CUDA(cudaMemcpy(hs, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost));
+    *rr_out = hs[S_RR];
+    *bb_out = hs[S_BB];
+    return hflag[F_ITERS];
+}
+
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st)
 {
@@ -259,7 +379,8 @@ vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, i
             // (residual replacement), at most a few times
             for (int restart = 0; restart < 4; ++restart) {
                 double rr, bb;
-                total += run_cg(m, op, false, rtol, max_it - total, st, &rr, &bb);
+                total += op.prec_kind ? run_pcg(m, op, rtol, max_it - total, st, &rr, &bb)
+                                      : run_cg(m, op, false, rtol, max_it - total, st, &rr, &bb);
                 apply_parts_ex(m, op, VFD_PART_ALL, op.cg_x.p, op.cg_q.p, 1, n, false, st, nullptr);
                 k_sub<<<VB, RB, 0, st>>>(n, f, op.cg_q.p, op.cg_r.p);
                 double res2 = dev_dot(m, op, op.cg_r.p, op.cg_r.p, st);

@@ -250,13 +250,20 @@ struct OpData {
     // solver workspace
     DBuf<double> cg_r, cg_p, cg_q, cg_x, cg_b, cg_z;
     DBuf<double> cg_red;               // reduction partials
-    DBuf<double> cg_scal;              // device scalars
+    DBuf<double> cg_scal;              // device scalars (8)
     DBuf<int> cg_flag;
     DBuf<int> errflag;
     double phase_ms[VFD_T_COUNT] = {0};
     bool timed = false;
     cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};   // captured CG chunks (FP64 K, FP32 K)
     const void *cg_key[2] = {nullptr, nullptr};
+    cudaGraphExec_t pcg_exec = nullptr;  // captured PCG chunk
+    const void *pcg_key = nullptr;
+    // two-level preconditioner (precond.cu): leaf-block inverses and the coarse inverse
+    int prec_kind = 0;
+    DBuf<double> prec_blk;             // nleaf x maxleaf x maxleaf (inverse of each leaf's diagonal block)
+    DBuf<double> prec_coarse;          // nleaf x nleaf (inverse of R A R^T)
+    DBuf<double> prec_rc, prec_zc;     // coarse residual / correction (nleaf)
 };
 
 // ---------------------------------------------------------------------------
@@ -366,5 +373,7 @@ void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *
 void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st);
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st);
+// precond.cu
+void precond_setup(const MeshData &m, OpData &op, int kind, cudaStream_t st);
 
 }  // namespace vfd

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libvfd.so")
 VFD_OK, VFD_EINVAL, VFD_ENOMEM, VFD_ECUDA, VFD_ENOCONV, VFD_ETIMEOUT, VFD_EUNSUPPORTED = range(7)
 VFD_FP64, VFD_FP32, VFD_BF16 = 0, 1, 2
 VFD_PART_B, VFD_PART_M, VFD_PART_KNEAR, VFD_PART_KFAR, VFD_PART_ALL = 1, 2, 4, 8, 15
+VFD_PREC_NONE, VFD_PREC_TWO_LEVEL = 0, 1
 VFD_ASSEMBLE_UNCHECKED = 1
 VFD_ASSEMBLE_TIMED = 2
 VFD_APPLY_NOALLOC_SCRATCH_BYTES = 8388608   # static scratch of vfd_apply_noalloc, per device
@@ -32,7 +33,8 @@ INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "no
              "rho_near_pairs", "near_storage", "near_point_pairs", "sing_points", "inner_rank"]
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
-           "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_grad", "vfd_load", "vfd_op_rho", "vfd_op_timings",
+           "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_precondition", "vfd_grad", "vfd_load",
+           "vfd_op_rho", "vfd_op_timings",
            "vfd_selftest_math", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve", "vfd_batch_tuning",
            "vfd_batch_set_config", "vfd_batch_set_wait_limit", "vfd_batch_free",
            "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
@@ -86,6 +88,7 @@ def load():
     L.vfd_solve.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, C.c_double, C.c_int, C.POINTER(C.c_int),
                             dp, vp]
     L.vfd_load.argtypes = [vp, vp, vp, vp]
+    L.vfd_precondition.argtypes = [vp, C.c_int, vp]
     L.vfd_op_rho.argtypes = [vp, vp, vp]
     L.vfd_op_timings.argtypes = [vp, dp, C.c_int]
     L.vfd_selftest_math.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp]
@@ -106,7 +109,7 @@ def load():
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
               "vfd_apply_noalloc", "vfd_grad", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve",
               "vfd_batch_tuning", "vfd_batch_set_config", "vfd_batch_set_wait_limit",
-              "vfd_solve", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
+              "vfd_solve", "vfd_precondition", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -362,6 +365,11 @@ def vfd_batch_set_config(batch, cfg):
 def vfd_batch_set_wait_limit(batch, seconds):
     """Bound (seconds) of the tensor-core kernel's device waits; 0 = give up at once."""
     _check(load().vfd_batch_set_wait_limit(batch.handle, float(seconds)))
+
+
+def vfd_precondition(op, kind=VFD_PREC_TWO_LEVEL, stream=None):
+    """Two-level preconditioner for the FP64 CG of vfd_solve (VFD_PREC_NONE: plain CG)."""
+    _check(load().vfd_precondition(op.handle, int(kind), _stream(stream)))
 
 
 def vfd_load(mesh, f_nodal, F, stream=None):
