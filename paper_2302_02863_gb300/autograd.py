@@ -24,9 +24,9 @@ class VfdSolve(torch.autograd.Function):
     """U = VfdSolve.apply(s, logk, F, mesh, s_bar, rtol, max_it).
 
     s, logk: float64 CUDA tensors of n_vert vertex values; F: float64 CUDA
-    tensor (n_dof,) or (nrhs, n_dof).  The mesh must be built with
-    lam = rho_lambda = 0 (P1 fields need an operator without low-rank
-    blocks) and tail_mode 0."""
+    tensor (n_dof,) or (nrhs, n_dof).  Any admissibility (the gradient is
+    that of the H^2 operator the solve uses, P1 fields at the Chebyshev
+    nodes by the nearest-point rule); tail_mode 0."""
 
     @staticmethod
     def forward(ctx, s, logk, F, mesh, s_bar=0.9, rtol=1e-12, max_it=100000):

@@ -26,16 +26,20 @@ __global__ void k_fields_points(int d, int nQ, const double *__restrict__ qx, co
     if (!(s >= smin && s <= smax)) atomicOr(err, 1);
 }
 
+// lcell, lbary (nodal fields): the node's closest cell and the barycentric
+// coordinates of its closest point there (nearest-point rule outside the mesh)
 __global__ void k_fields_nodes(int d, int n, const double *__restrict__ pts, DField Fs, DField Fk,
-                               double *__restrict__ out_s, double *__restrict__ out_lk, double smin, double smax,
-                               int *err)
+                               const int *__restrict__ lcell, const double *__restrict__ lbary,
+                               const int *__restrict__ cells, double *__restrict__ out_s, double *__restrict__ out_lk,
+                               double smin, double smax, int *err)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x[3];
     for (int j = 0; j < d; ++j) x[j] = pts[(size_t)i * d + j];
     double s, lk;
-    fields2(Fs, Fk, d, x, nullptr, nullptr, s, lk);
+    const int *vid = lcell ? cells + (size_t)lcell[i] * (d + 1) : nullptr;
+    fields2(Fs, Fk, d, x, vid, lcell ? lbary + (size_t)i * QB : nullptr, s, lk);
     out_s[i] = s;
     out_lk[i] = lk;
     if (!(s >= smin && s <= smax)) atomicOr(err, 2);
@@ -51,28 +55,24 @@ void launch_field_points(const MeshData &m, OpData &op, cudaStream_t st)
     k_fields_points<<<cdiv(m.nQ, 256), 256, 0, st>>>(d, m.nQ, m.qx.p, m.qcell.p, m.qbary.p, m.cells.p, op.fs, op.fk,
                                                      op.q_s.p, op.q_lk.p, smin, smax, op.errflag.p);
     VFD_CUDA(cudaGetLastError());
-    if (op.fs.nodal || op.fk.nodal) return;   // nodal fields: no low-rank part (checked on the host)
-    auto nodes = [&](const DBuf<double> &pts, int nn, DBuf<double> &os, DBuf<double> &ol) {
-        int n = nn * k;
+    const bool nodal = op.fs.nodal || op.fk.nodal;
+    auto nodes = [&](const DBuf<double> &pts, int n, const NodeLoc &loc, DBuf<double> &os, DBuf<double> &ol) {
         os.alloc(n);
         ol.alloc(n);
-        if (n) k_fields_nodes<<<cdiv(n, 256), 256, 0, st>>>(d, n, pts.p, op.fs, op.fk, os.p, ol.p, smin, smax,
-                                                            op.errflag.p);
+        VFD_REQUIRE(!nodal || loc.done, VFD_ECUDA, "Chebyshev nodes not located for a nodal field");
+        if (n)
+            k_fields_nodes<<<cdiv(n, 256), 256, 0, st>>>(d, n, pts.p, op.fs, op.fk, nodal ? loc.cell.p : nullptr,
+                                                          nodal ? loc.bary.p : nullptr, m.cells.p, os.p, ol.p, smin,
+                                                          smax, op.errflag.p);
         VFD_CUDA(cudaGetLastError());
     };
-    if (m.nfar) nodes(m.kt_cheb, m.kt.nnode, op.kc_s, op.kc_lk);
-    if (m.nfar && m.k_in && op.precision != VFD_FP64) {
-        // the inner operator's nodes (k_in per box)
-        const int n = m.kt.nnode * m.k_in;
-        op.kc_s_in.alloc(n);
-        op.kc_lk_in.alloc(n);
-        k_fields_nodes<<<cdiv(n, 256), 256, 0, st>>>(d, n, m.kt_cheb_in.p, op.fs, op.fk, op.kc_s_in.p, op.kc_lk_in.p,
-                                                      smin, smax, op.errflag.p);
-        VFD_CUDA(cudaGetLastError());
-    }
+    if (m.nfar) nodes(m.kt_cheb, m.kt.nnode * k, m.kt_loc, op.kc_s, op.kc_lk);
+    // the inner operator's nodes (k_in per box)
+    if (m.nfar && m.k_in && op.precision != VFD_FP64)
+        nodes(m.kt_cheb_in, m.kt.nnode * m.k_in, m.kt_in_loc, op.kc_s_in, op.kc_lk_in);
     if (m.nrfar) {
-        nodes(m.tt_cheb, m.tt.nnode, op.tc_s, op.tc_lk);
-        nodes(m.st_cheb, m.st.nnode, op.sc_s, op.sc_lk);
+        nodes(m.tt_cheb, m.tt.nnode * k, m.tt_loc, op.tc_s, op.tc_lk);
+        nodes(m.st_cheb, m.st.nnode * k, m.st_loc, op.sc_s, op.sc_lk);
     }
 }
 

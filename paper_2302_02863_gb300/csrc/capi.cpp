@@ -244,15 +244,15 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
     VFD_REQUIRE(mesh && s && log_kappa && out, VFD_EINVAL, "null argument");
     *out = nullptr;
     require_device();
-    const MeshData &m = *mesh->m;
+    MeshData &m = *mesh->m;
     cudaStream_t st = (cudaStream_t)stream;
     VFD_REQUIRE(precision == VFD_FP64 || precision == VFD_FP32 || precision == VFD_BF16, VFD_EINVAL,
                 "unknown precision");
     VFD_REQUIRE(s_bar < 1.0 && ((flags & VFD_ASSEMBLE_UNCHECKED) || s_bar >= 0.0), VFD_EINVAL,
                 "s_bar must satisfy 0 <= s_bar < 1");
     bool nodal = s->kind == VFD_FIELD_NODAL || log_kappa->kind == VFD_FIELD_NODAL;
-    VFD_REQUIRE(!nodal || (m.nfar == 0 && m.nrfar == 0), VFD_EUNSUPPORTED,
-                "P1 (nodal) fields need an operator without low-rank blocks (lambda = rho_lambda = 0)");
+    // P1 fields at Chebyshev nodes: the nearest-point rule (located once per mesh)
+    if (nodal && (m.nfar > 0 || m.nrfar > 0)) locate_nodes(m);
     VFD_REQUIRE(m.opts.tail_mode == 0 || (field_is_const(s) && field_is_const(log_kappa)), VFD_EUNSUPPORTED,
                 "the exterior tail needs constant s and kappa");
     op = new OpData();
@@ -422,6 +422,7 @@ vfd_status vfd_precondition(vfd_op_t h, int kind, void *stream)
 {
     VFD_API_BEGIN
     VFD_REQUIRE(h, VFD_EINVAL, "null operator");
+    require_device();
     precond_setup(*h->op->m, *h->op, kind, (cudaStream_t)stream);
     return VFD_OK;
     VFD_API_END
@@ -464,10 +465,11 @@ vfd_status vfd_grad(vfd_op_t h, const double *U, const double *Lam, int64_t nrhs
     VFD_REQUIRE(op.fs.nodal && op.fk.nodal, VFD_EUNSUPPORTED, "vfd_grad needs P1 (nodal) s and log kappa");
     VFD_REQUIRE(m.opts.tail_mode == 0, VFD_EUNSUPPORTED, "vfd_grad needs a bounded exterior (tail_mode 0)");
     VFD_REQUIRE(m.d <= 2, VFD_EUNSUPPORTED, "vfd_grad is built for d = 1, 2");
+    VFD_REQUIRE(op.q_s.n == (size_t)m.nQ, VFD_EINVAL, "vfd_grad: operator without point fields");
     VFD_REQUIRE(nrhs >= 1 && ld >= m.N, VFD_EINVAL, "bad nrhs or ld");
     VFD_REQUIRE(is_device_ptr(U) && is_device_ptr(Lam) && is_device_ptr(g_s) && is_device_ptr(g_logkappa),
                 VFD_EINVAL, "vfd_grad: U, Lam, g_s and g_logkappa must be device pointers");
-    grad_exact(m, op, U, Lam, (int)nrhs, ld, g_s, g_logkappa, (cudaStream_t)stream);
+    grad_adjoint(m, op, U, Lam, (int)nrhs, ld, g_s, g_logkappa, (cudaStream_t)stream);
     return VFD_OK;
     VFD_API_END
 }

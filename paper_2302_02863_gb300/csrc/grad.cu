@@ -3,25 +3,41 @@
 //
 //   g_s[k]  = -sum_r Lam_r^T (dA/ds_k) U_r,   g_lk[k] = -sum_r Lam_r^T (dA/dlogk_k) U_r.
 //
-// The paper has no gradients; A is the operator of Sec. 3 (B + K + M) with
-// every quadrature rule held fixed, and every term carries the kernel
-// gamma(x,y) = sqrt(kappa(x) kappa(y)) |x-y|^-(d+s(x)+s(y)), so that
-//   d gamma / d s_k    = -ln|x-y| (psi_k(x) + psi_k(y)) gamma,
-//   d gamma / d logk_k =  1/2     (psi_k(x) + psi_k(y)) gamma.
+// The paper has no gradients; A is the operator the solves use (Sec. 3,
+// A = B + K + M, with K's admissible blocks and the density's far part in
+// their interpolated H^2 forms of Sec. 5.3 and 6.2), every quadrature rule held
+// fixed.  Every term carries the kernel
+// gamma(x,y) = sqrt(kappa(x) kappa(y)) |x-y|^-(d+s(x)+s(y)), so
+//   d gamma / d s(x) = -ln|x-y| gamma,   d gamma / d logk(x) = gamma / 2,
+// where x is an element-rule point, a singular-rule point or, inside an
+// interpolated block, a Chebyshev node whose field value is the P1
+// interpolant at the node's nearest mesh point.  The contributions, each an
+// "s-sensitivity" -d(Lam^T A U)/d s(x) at one point x, pushed to the vertices
+// through the barycentric coordinates of x:
 //
-// Separated point pairs (K and M together): the bilinear form over ordered
-// pairs (q, q') of element-rule points in non-touching cells, not both
-// exterior, is sum G(q,q') dU dLam with G = w w' gamma and dU = U(q) - U(q')
-// (Sec. 3, the split of the form into K and M is an identity), so
-//   g_s[k]  =  2 sum_q psi_k(q) h_s(q),  h_s(q) = sum_q' G ln|q-q'| sum_r dU_r dLam_r,
-//   g_lk[k] = -  sum_q psi_k(q) h_1(q),  h_1(q) = sum_q' G sum_r dU_r dLam_r.
-// Touching pairs (B): the singular rules of Sec. 4 point by point, with
-// d(log w)/dS read off the factors of the rule weight that depend on S.
+//   B (touching pairs)   the singular rules of Sec. 4 point by point, with
+//                        d(log w)/dS read off the factors of the rule weight
+//                        that depend on S (k_grad_sing);
+//   K near blocks        D_ab = -2 sum_{q in P_a, q' in P_b} gamma_T(q,q')
+//                        c_a(q) c_b(q'), c_a(q) = w_q sum_{i in a} psi_i(q) x_i:
+//                        per row leaf a and point q of P_a the sum over the
+//                        leaf's blocks of gamma_T (c_a^Lam(q) c_b^U(q') +
+//                        c_a^U(q) c_b^Lam(q')) (k_gh_knear);
+//   K admissible blocks  Lam^T U_a S_ab U_b^T U, S_ab = -2 gamma(xi, eta): per
+//                        node and Chebyshev node xi the same contraction with
+//                        the moments Uhat_b, Lamhat_b of the upsweep and S
+//                        recomputed on the fly (k_gh_kfar);
+//   M (density)          Lam^T M U = sum_q c_q rho(q), c_q = 2 w_q Lam(q) U(q):
+//                        near sources by direct sums on the target side and,
+//                        over the transposed lists, on the source side
+//                        (k_gh_rho_near_t / _s); far sources through the target
+//                        moments chat_t = sum_q c_q l^t(q) and the source
+//                        moments (k_gh_rho_moments, k_gh_rho_far_t / _s).
 //
-// Operators with P1 fields have no low-rank part (every block is near and
-// the density is a direct sum), so the gradient is that of the operator the
-// solves use.  All sums are in a fixed order (per-point and per-pair partial
-// results gathered per vertex through precomputed lists).
+// With lambda = rho_lambda = 0 every block is near and the density a direct
+// sum: the same kernels then give the gradient of the exact-mode operator.
+// All sums run in a fixed order (per-point and per-node results gathered per
+// vertex through precomputed lists), so the result is deterministic.
 #include <algorithm>
 #include <cmath>
 
@@ -54,81 +70,506 @@ __global__ void k_grad_vals(int nQ, int d, int nrhs, int64_t ld, const int *__re
     }
 }
 
-constexpr int GT = 128;     // target points per CTA and source points per tile
-constexpr int GNR = 8;      // right-hand sides per pass of the separated-pair kernel
 
-// h_s(q), h_1(q) for every element-rule point q (targets), over all source
-// points in tiles staged in shared memory.  Points q < nQint lie in interior
-// cells.  accumulate: add to h (later passes over the right-hand sides).
+constexpr int GT = 128;     // points per CTA and per staged tile
+constexpr int GNR = 8;      // right-hand sides per pass of the K kernels
+
+// c_q = 2 w_q sum_r Lam_r(q) U_r(q) at the interior points (0 elsewhere)
+__global__ void k_gh_cq(int nQ, int nQint, int nrhs, const double *__restrict__ qw, const double *__restrict__ Uq,
+                        const double *__restrict__ Lq, double *__restrict__ cq)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nQ) return;
+    double v = 0.0;
+    if (q < nQint)
+        for (int r = 0; r < nrhs; ++r) v = fma(Uq[(size_t)r * nQ + q], Lq[(size_t)r * nQ + q], v);
+    cq[q] = 2.0 * qw[q] * v;
+}
+
+struct GKN {
+    int nQ, fl, nr, accumulate;
+    int64_t ld;
+    const double *U, *Lam;   // first column of this pass
+    const int *kt_begin, *kt_end, *lp_ptr, *lp_pts, *near_ptr, *near_col;
+    const double *qx, *qw, *qs, *qlk, *qbary;
+    const int *qcell, *cells, *vdof;
+    const double *mt;
+    double *hs, *hk;   // per leaf-point entry
+};
+
+// c_a(q) for the columns of this pass: w_q sum over the cell's vertices whose
+// DoF lies in [r0, r1) of the barycentric coordinate times x
+template <int NV>
+__device__ __forceinline__ void leaf_coef(const GKN &P, int q, int r0, int r1, double *cl, double *cu)
+{
+    const int cell = P.qcell[q];
+    const double w = P.qw[q];
+#pragma unroll
+    for (int r = 0; r < GNR; ++r) cl[r] = cu[r] = 0.0;
+    for (int k = 0; k < NV; ++k) {
+        const int i = P.vdof[P.cells[(size_t)cell * NV + k]];
+        if (i >= r0 && i < r1) {
+            const double c = w * P.qbary[(size_t)q * QB + k];
+#pragma unroll
+            for (int r = 0; r < GNR; ++r)
+                if (r < P.nr) {
+                    cl[r] = fma(c, P.Lam[(size_t)r * P.ld + i], cl[r]);
+                    cu[r] = fma(c, P.U[(size_t)r * P.ld + i], cu[r]);
+                }
+        }
+    }
+}
+
+// K near blocks, row side: CTA (row leaf a, slice of GT points of P_a); the
+// column points of every block (a, b) staged in tiles
 template <int D>
-__global__ void __launch_bounds__(GT)
-k_grad_sep(int nQ, int nQint, int nr, int accumulate, const double *__restrict__ qx, const double *__restrict__ qw,
-           const double *__restrict__ qs, const double *__restrict__ qlk, const int *__restrict__ qcell,
-           const int *__restrict__ cells, const double *__restrict__ Uq, const double *__restrict__ Lq,
-           const double *__restrict__ mt, double *__restrict__ hs, double *__restrict__ h1)
+__global__ void __launch_bounds__(GT) k_gh_knear(GKN P)
 {
     constexpr int NV = D + 1;
-    __shared__ double sx[D][GT], sw[GT], ss[GT], sa[GT];
-    __shared__ double su[GNR][GT], sl[GNR][GT];
+    __shared__ double sx[D][GT], sa[GT], sb[GT], sl[GNR][GT], su[GNR][GT];
     __shared__ int sv[NV][GT];
-    const int q = blockIdx.x * GT + threadIdx.x;
-    const bool live = q < nQ;
-    const int qq = live ? q : 0;
-    double x[D], u[GNR], l[GNR];
-    for (int i = 0; i < D; ++i) x[i] = qx[(size_t)i * nQ + qq];
-    const double w = qw[qq], s = qs[qq], a = 0.5 * qlk[qq];
-    const bool ext = qq >= nQint;
+    const int a = blockIdx.x;
+    const int pa0 = P.lp_ptr[a], npa = P.lp_ptr[a + 1] - pa0;
+    if ((int)blockIdx.y * GT >= npa) return;   // the whole CTA
+    const int t = blockIdx.y * GT + threadIdx.x;
+    const bool live = t < npa;
+    const int q = P.lp_pts[pa0 + (live ? t : 0)];
+    double x[D];
+    for (int c = 0; c < D; ++c) x[c] = P.qx[(size_t)c * P.nQ + q];
+    const double aq = 0.5 * P.qlk[q], bq = fma(0.5, P.qs[q], 0.25 * D);
     int v[NV];
-    for (int i = 0; i < NV; ++i) v[i] = cells[(size_t)qcell[qq] * NV + i];
+    for (int k = 0; k < NV; ++k) v[k] = P.cells[(size_t)P.qcell[q] * NV + k];
+    double cl[GNR], cu[GNR];
+    leaf_coef<NV>(P, q, P.kt_begin[P.fl + a], P.kt_end[P.fl + a], cl, cu);
+    double accs = 0.0, acc1 = 0.0;
+    for (int e = P.near_ptr[a]; e < P.near_ptr[a + 1]; ++e) {
+        const int b = P.near_col[e];
+        const int pb0 = P.lp_ptr[b], npb = P.lp_ptr[b + 1] - pb0;
+        const int rb0 = P.kt_begin[P.fl + b], rb1 = P.kt_end[P.fl + b];
+        for (int j0 = 0; j0 < npb; j0 += GT) {
+            const int nt = min(GT, npb - j0);
+            __syncthreads();
+            if ((int)threadIdx.x < nt) {
+                const int id = P.lp_pts[pb0 + j0 + threadIdx.x];
+                for (int c = 0; c < D; ++c) sx[c][threadIdx.x] = P.qx[(size_t)c * P.nQ + id];
+                sa[threadIdx.x] = 0.5 * P.qlk[id];
+                sb[threadIdx.x] = fma(0.5, P.qs[id], 0.25 * D);
+                for (int k = 0; k < NV; ++k) sv[k][threadIdx.x] = P.cells[(size_t)P.qcell[id] * NV + k];
+                double ml[GNR], mu[GNR];
+                leaf_coef<NV>(P, id, rb0, rb1, ml, mu);
+#pragma unroll
+                for (int r = 0; r < GNR; ++r) {
+                    sl[r][threadIdx.x] = ml[r];
+                    su[r][threadIdx.x] = mu[r];
+                }
+            }
+            __syncthreads();
+            if (live)
+                for (int jj = 0; jj < nt; ++jj) {
+                    bool touch = false;
+#pragma unroll
+                    for (int i = 0; i < NV; ++i)
+#pragma unroll
+                        for (int k = 0; k < NV; ++k) touch |= (v[i] == sv[k][jj]);
+                    if (touch) continue;   // touching cells belong to B
+                    double r2 = 0.0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        const double dd = x[c] - sx[c][jj];
+                        r2 = fma(dd, dd, r2);
+                    }
+                    const double lr2 = fast_log(P.mt, r2);
+                    const double g = fast_exp(P.mt, aq + sa[jj] - (bq + sb[jj]) * lr2);
+                    double X = 0.0;
+#pragma unroll
+                    for (int r = 0; r < GNR; ++r)
+                        if (r < P.nr) X = fma(cl[r], su[r][jj], fma(cu[r], sl[r][jj], X));
+                    const double tX = g * X;
+                    acc1 += tX;
+                    accs = fma(tX, lr2, accs);
+                }
+        }
+    }
+    if (live) {
+        // -d/ds(q) of -2 gamma X = -ln(r^2) gamma X; -d/dlogk(q) = gamma X
+        const size_t o = (size_t)pa0 + t;
+        P.hs[o] = P.accumulate ? P.hs[o] - accs : -accs;
+        P.hk[o] = P.accumulate ? P.hk[o] + acc1 : acc1;
+    }
+}
+
+// K far moments of U and Lam for the nodes with admissible blocks:
+// xU[r][n][alpha] = sum_{i in n} Ul^(level n)[i][alpha] U_r[i]
+__global__ void __launch_bounds__(128)
+k_gh_moments(int nr, int k, int N, int lmin, int nnode, const int *__restrict__ fptr, const int *__restrict__ kb,
+             const int *__restrict__ ke, const double *__restrict__ Ul, const double *__restrict__ U,
+             const double *__restrict__ Lam, int64_t ld, double *__restrict__ xU, double *__restrict__ xL)
+{
+    __shared__ double ru[128], rl[128];
+    const int n = blockIdx.x;
+    if (fptr[n + 1] == fptr[n]) return;
+    int l = 0;
+    while ((2 << l) - 1 <= n) ++l;
+    const int lv = l - lmin;
+    const int b = kb[n], e = ke[n];
+    const int kk = min(k, (int)blockDim.x), parts = blockDim.x / kk;
+    const int al = threadIdx.x % kk, pt = threadIdx.x / kk;
+    const double *u = Ul + (size_t)lv * N * k;
+    for (int r = 0; r < nr; ++r)
+        for (int a0 = 0; a0 < k; a0 += kk) {
+            double au = 0.0, aL = 0.0;
+            if (pt < parts)
+                for (int i = b + pt; i < e; i += parts) {
+                    const double w = u[(size_t)i * k + a0 + al];
+                    au = fma(w, U[(size_t)r * ld + i], au);
+                    aL = fma(w, Lam[(size_t)r * ld + i], aL);
+                }
+            ru[threadIdx.x] = au;
+            rl[threadIdx.x] = aL;
+            __syncthreads();
+            if ((int)threadIdx.x < kk) {
+                double su = 0.0, sl = 0.0;
+                for (int q = 0; q < parts; ++q) {
+                    su += ru[q * kk + threadIdx.x];
+                    sl += rl[q * kk + threadIdx.x];
+                }
+                xU[((size_t)r * nnode + n) * k + a0 + threadIdx.x] = su;
+                xL[((size_t)r * nnode + n) * k + a0 + threadIdx.x] = sl;
+            }
+            __syncthreads();
+        }
+}
+
+// K admissible blocks: per row node a and node alpha, over the blocks e of
+// the row (threads (alpha, block slot)), S_e recomputed:
+//   Gs[a][alpha] += sum_e sum_beta ln(r^2)/2 S (Lhat_a Uhat_b + Uhat_a Lhat_b),
+//   Gk[a][alpha] -= sum_e sum_beta S/2 (Lhat_a Uhat_b + Uhat_a Lhat_b)
+__global__ void __launch_bounds__(256)
+k_gh_kfar(int d, int k, int nnode, int nr, const int *__restrict__ fptr, const int *__restrict__ fcol,
+          const double *__restrict__ ch, const double *__restrict__ cs, const double *__restrict__ clk,
+          const double *__restrict__ xU, const double *__restrict__ xL, const double *__restrict__ mt,
+          double *__restrict__ Gs, double *__restrict__ Gk)
+{
+    __shared__ double rs[256], rk[256];
+    const int a = blockIdx.x;
+    const int e0 = fptr[a], ne = fptr[a + 1] - e0;
+    if (ne == 0) return;
+    const int al = threadIdx.x % k, g = threadIdx.x / k, per = blockDim.x / k;
+    const int ia = a * k + al;
+    double xa[3];
+    for (int c = 0; c < d; ++c) xa[c] = ch[(size_t)ia * d + c];
+    const double sa = cs[ia], la = clk[ia];
+    double Ua[GNR], La[GNR];
 #pragma unroll
     for (int r = 0; r < GNR; ++r) {
-        u[r] = r < nr ? Uq[(size_t)r * nQ + qq] : 0.0;
-        l[r] = r < nr ? Lq[(size_t)r * nQ + qq] : 0.0;
+        Ua[r] = r < nr ? xU[((size_t)r * nnode + a) * k + al] : 0.0;
+        La[r] = r < nr ? xL[((size_t)r * nnode + a) * k + al] : 0.0;
     }
-    double acc_s = 0.0, acc_1 = 0.0;
-    for (int t0 = 0; t0 < nQ; t0 += GT) {
-        const int j = t0 + threadIdx.x;
-        if (j < nQ) {
-            for (int i = 0; i < D; ++i) sx[i][threadIdx.x] = qx[(size_t)i * nQ + j];
-            sw[threadIdx.x] = qw[j];
-            ss[threadIdx.x] = qs[j];
-            sa[threadIdx.x] = 0.5 * qlk[j];
-            for (int i = 0; i < NV; ++i) sv[i][threadIdx.x] = cells[(size_t)qcell[j] * NV + i];
-            for (int r = 0; r < nr; ++r) {
-                su[r][threadIdx.x] = Uq[(size_t)r * nQ + j];
-                sl[r][threadIdx.x] = Lq[(size_t)r * nQ + j];
-            }
-        }
-        __syncthreads();
-        const int nt = min(GT, nQ - t0);
-        if (live)
-            for (int jj = 0; jj < nt; ++jj) {
-                if (ext && t0 + jj >= nQint) continue;   // exterior x exterior: no term
-                bool touch = false;
-                for (int i = 0; i < NV; ++i)
-                    for (int k = 0; k < NV; ++k) touch |= (v[i] == sv[k][jj]);
-                if (touch) continue;                      // touching cells belong to B
+    double gs = 0.0, gk = 0.0;
+    if (g < per)
+        for (int e = g; e < ne; e += per) {
+            const int b = fcol[e0 + e];
+            double yU[GNR], yL[GNR], zU[GNR], zL[GNR];
+#pragma unroll
+            for (int r = 0; r < GNR; ++r) yU[r] = yL[r] = zU[r] = zL[r] = 0.0;
+            for (int be = 0; be < k; ++be) {
+                const int jb = b * k + be;
                 double r2 = 0.0;
-                for (int i = 0; i < D; ++i) {
-                    const double dd = x[i] - sx[i][jj];
+                for (int c = 0; c < d; ++c) {
+                    const double dd = xa[c] - ch[(size_t)jb * d + c];
                     r2 = fma(dd, dd, r2);
                 }
                 const double lr2 = fast_log(mt, r2);
-                const double G = w * sw[jj] * fast_exp(mt, a + sa[jj] - 0.5 * (D + s + ss[jj]) * lr2);
-                double ul = 0.0;
+                const double S = -2.0 * fast_exp(mt, 0.5 * (la + clk[jb]) - 0.5 * (d + sa + cs[jb]) * lr2);
+                const double hS = 0.5 * lr2 * S;
 #pragma unroll
                 for (int r = 0; r < GNR; ++r)
-                    if (r < nr) ul = fma(u[r] - su[r][jj], l[r] - sl[r][jj], ul);
-                const double t = G * ul;
-                acc_1 += t;
-                acc_s = fma(t, 0.5 * lr2, acc_s);
+                    if (r < nr) {
+                        const double ub = xU[((size_t)r * nnode + b) * k + be], lb = xL[((size_t)r * nnode + b) * k + be];
+                        yU[r] = fma(hS, ub, yU[r]);
+                        yL[r] = fma(hS, lb, yL[r]);
+                        zU[r] = fma(S, ub, zU[r]);
+                        zL[r] = fma(S, lb, zL[r]);
+                    }
             }
+#pragma unroll
+            for (int r = 0; r < GNR; ++r) {
+                gs += La[r] * yU[r] + Ua[r] * yL[r];
+                gk -= 0.5 * (La[r] * zU[r] + Ua[r] * zL[r]);
+            }
+        }
+    rs[threadIdx.x] = gs;
+    rk[threadIdx.x] = gk;
+    __syncthreads();
+    if (g == 0) {
+        double ts = 0.0, tk = 0.0;
+        for (int q = 0; q < per; ++q) {
+            ts += rs[q * k + al];
+            tk += rk[q * k + al];
+        }
+        Gs[ia] += ts;
+        Gk[ia] += tk;
+    }
+}
+
+struct GRho {
+    int d, nv, nQ, k, p;
+    int tfl, sfl;   // first leaf of the target / source tree
+    const int *tt_begin, *tt_end, *tt_perm, *st_begin, *st_end, *st_perm;
+    const int *rnear_ptr, *rnear_col, *rnearT_ptr, *rnearT_col;
+    const double *qx, *qw, *qs, *qlk, *cq;
+    const int *qcell, *cells;
+    const double *mt;
+    double *hs, *hk;   // per point
+};
+
+constexpr int RCH = 128;   // staged points per tile of the density kernels
+
+// density near part, target side: per interior point q
+//   hs[q] = c_q/2 sum_{q'} w' gamma ln(r^2),  hk[q] = -c_q/2 sum_{q'} w' gamma
+__global__ void __launch_bounds__(RCH) k_gh_rho_near_t(GRho P)
+{
+    __shared__ double sx[3][RCH], ss[RCH], sl[RCH];
+    __shared__ int sv[4][RCH];
+    const int d = P.d, leaf = blockIdx.x, node = P.tfl + leaf;
+    const int b = P.tt_begin[node], e = P.tt_end[node];
+    for (int i0 = b; i0 < e; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool act = i < e;
+        const int id = act ? P.tt_perm[i] : P.tt_perm[b];
+        double x[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) x[c] = P.qx[(size_t)c * P.nQ + id];
+        const double a_ = 0.5 * P.qlk[id], b_ = fma(0.5, P.qs[id], 0.25 * d);
+        int cv[4] = {-1, -1, -1, -1};
+        for (int a = 0; a < P.nv; ++a) cv[a] = P.cells[(size_t)P.qcell[id] * P.nv + a];
+        double accs = 0.0, acc1 = 0.0;
+        for (int ne = P.rnear_ptr[leaf]; ne < P.rnear_ptr[leaf + 1]; ++ne) {
+            const int sn = P.rnear_col[ne];
+            const int sb = P.st_begin[sn], se = P.st_end[sn];
+            for (int j0 = sb; j0 < se; j0 += RCH) {
+                const int nj = min(RCH, se - j0);
+                __syncthreads();
+                if ((int)threadIdx.x < nj) {
+                    const int jd = P.st_perm[j0 + threadIdx.x];
+                    for (int c = 0; c < d; ++c) sx[c][threadIdx.x] = P.qx[(size_t)c * P.nQ + jd];
+                    ss[threadIdx.x] = fma(0.5, P.qs[jd], 0.25 * d);
+                    sl[threadIdx.x] = fma(0.5, P.qlk[jd], fast_log(P.mt, P.qw[jd]));
+                    for (int a = 0; a < 4; ++a)
+                        sv[a][threadIdx.x] = a < P.nv ? P.cells[(size_t)P.qcell[jd] * P.nv + a] : -2;
+                }
+                __syncthreads();
+                if (act)
+                    for (int t = 0; t < nj; ++t) {
+                        bool touch = false;
+                        for (int a = 0; a < P.nv; ++a)
+                            for (int bb = 0; bb < P.nv; ++bb) touch |= (cv[a] == sv[bb][t]);
+                        if (touch) continue;
+                        double r2 = 0.0;
+                        for (int c = 0; c < d; ++c) {
+                            const double dd = x[c] - sx[c][t];
+                            r2 = fma(dd, dd, r2);
+                        }
+                        const double lr2 = fast_log(P.mt, r2);
+                        const double g = fast_exp(P.mt, a_ + sl[t] - (b_ + ss[t]) * lr2);   // w' gamma
+                        acc1 += g;
+                        accs = fma(g, lr2, accs);
+                    }
+            }
+        }
+        if (act) {
+            const double c = P.cq[id];
+            P.hs[id] = 0.5 * c * accs;
+            P.hk[id] = -0.5 * c * acc1;
+        }
+    }
+}
+
+// density near part, source side: per point q' of a source leaf, over the
+// target leaves whose near list holds it
+//   hs[q'] += w'/2 sum_q c_q gamma ln(r^2),  hk[q'] -= w'/2 sum_q c_q gamma
+__global__ void __launch_bounds__(RCH) k_gh_rho_near_s(GRho P)
+{
+    __shared__ double sx[3][RCH], ss[RCH], sl[RCH], sc[RCH];
+    __shared__ int sv[4][RCH];
+    const int d = P.d, sleaf = blockIdx.x, node = P.sfl + sleaf;
+    const int b = P.st_begin[node], e = P.st_end[node];
+    for (int i0 = b; i0 < e; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool act = i < e;
+        const int id = act ? P.st_perm[i] : P.st_perm[b];
+        double x[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) x[c] = P.qx[(size_t)c * P.nQ + id];
+        const double a_ = 0.5 * P.qlk[id], b_ = fma(0.5, P.qs[id], 0.25 * d);
+        int cv[4] = {-1, -1, -1, -1};
+        for (int a = 0; a < P.nv; ++a) cv[a] = P.cells[(size_t)P.qcell[id] * P.nv + a];
+        double accs = 0.0, acc1 = 0.0;
+        for (int ne = P.rnearT_ptr[sleaf]; ne < P.rnearT_ptr[sleaf + 1]; ++ne) {
+            const int tn = P.tfl + P.rnearT_col[ne];
+            const int tb = P.tt_begin[tn], te = P.tt_end[tn];
+            for (int j0 = tb; j0 < te; j0 += RCH) {
+                const int nj = min(RCH, te - j0);
+                __syncthreads();
+                if ((int)threadIdx.x < nj) {
+                    const int jd = P.tt_perm[j0 + threadIdx.x];
+                    for (int c = 0; c < d; ++c) sx[c][threadIdx.x] = P.qx[(size_t)c * P.nQ + jd];
+                    ss[threadIdx.x] = fma(0.5, P.qs[jd], 0.25 * d);
+                    sl[threadIdx.x] = 0.5 * P.qlk[jd];
+                    sc[threadIdx.x] = P.cq[jd];
+                    for (int a = 0; a < 4; ++a)
+                        sv[a][threadIdx.x] = a < P.nv ? P.cells[(size_t)P.qcell[jd] * P.nv + a] : -2;
+                }
+                __syncthreads();
+                if (act)
+                    for (int t = 0; t < nj; ++t) {
+                        bool touch = false;
+                        for (int a = 0; a < P.nv; ++a)
+                            for (int bb = 0; bb < P.nv; ++bb) touch |= (cv[a] == sv[bb][t]);
+                        if (touch) continue;
+                        double r2 = 0.0;
+                        for (int c = 0; c < d; ++c) {
+                            const double dd = x[c] - sx[c][t];
+                            r2 = fma(dd, dd, r2);
+                        }
+                        const double lr2 = fast_log(P.mt, r2);
+                        const double cg = sc[t] * fast_exp(P.mt, a_ + sl[t] - (b_ + ss[t]) * lr2);
+                        acc1 += cg;
+                        accs = fma(cg, lr2, accs);
+                    }
+            }
+        }
+        if (act) {
+            const double w = P.qw[id];
+            P.hs[id] += 0.5 * w * accs;
+            P.hk[id] -= 0.5 * w * acc1;
+        }
+    }
+}
+
+// target moments chat[t][alpha] = sum_{q in t} c_q l^t_alpha(q) for the target
+// nodes with admissible blocks (the transpose of the downsweep's evaluation)
+constexpr int MCH = 64;
+__global__ void __launch_bounds__(128)
+k_gh_rho_moments(int d, int p, int k, int nQ, const int *__restrict__ fptr, const int *__restrict__ tb,
+                 const int *__restrict__ te, const int *__restrict__ perm, const double *__restrict__ tch,
+                 const double *__restrict__ qx, const double *__restrict__ cq, double *__restrict__ chat)
+{
+    __shared__ double l1[MCH][3][PMAX], sc[MCH];
+    const int t = blockIdx.x;
+    if (fptr[t + 1] == fptr[t]) return;
+    const double *ch = tch + (size_t)t * k * d;
+    const int b = tb[t], e = te[t];
+    double acc = 0.0;
+    for (int i0 = b; i0 < e; i0 += MCH) {
+        const int n = min(MCH, e - i0);
         __syncthreads();
+        for (int pt = threadIdx.x; pt < n; pt += blockDim.x) {
+            const int id = perm[i0 + pt];
+            int stride = 1;
+            for (int c = 0; c < d; ++c) {
+                const double x = qx[(size_t)c * nQ + id];
+                for (int a = 0; a < p; ++a) {
+                    const double na = ch[(size_t)(a * stride) * d + c];
+                    double v = 1.0;
+                    for (int bb = 0; bb < p; ++bb)
+                        if (bb != a) {
+                            const double nb = ch[(size_t)(bb * stride) * d + c];
+                            v *= (x - nb) / (na - nb);
+                        }
+                    l1[pt][c][a] = v;
+                }
+                stride *= p;
+            }
+            sc[pt] = cq[id];
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < k)
+            for (int pt = 0; pt < n; ++pt) {
+                double v = sc[pt];
+                int r = threadIdx.x;
+                for (int c = 0; c < d; ++c) {
+                    v *= l1[pt][c][r % p];
+                    r /= p;
+                }
+                acc += v;
+            }
     }
-    if (live) {
-        hs[q] = accumulate ? hs[q] + acc_s : acc_s;
-        h1[q] = accumulate ? h1[q] + acc_1 : acc_1;
+    if ((int)threadIdx.x < k) chat[(size_t)t * k + threadIdx.x] = acc;
+}
+
+// density far part, target nodes: thread per (t, alpha)
+//   Gs = chat/2 sum gamma ln(r^2) xs,  Gk = -chat/2 sum gamma xs
+__global__ void k_gh_rho_far_t(int d, int k, int nnode_t, const int *__restrict__ fptr, const int *__restrict__ fcol,
+                               const double *__restrict__ tch, const double *__restrict__ ts,
+                               const double *__restrict__ tlk, const double *__restrict__ sch,
+                               const double *__restrict__ ss, const double *__restrict__ slk,
+                               const double *__restrict__ xs, const double *__restrict__ chat,
+                               const double *__restrict__ mt, double *__restrict__ Gs, double *__restrict__ Gk)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nnode_t * k) return;
+    const int t = i / k;
+    double accs = 0.0, acc1 = 0.0;
+    if (fptr[t + 1] > fptr[t]) {
+        const double *xa = tch + (size_t)i * d;
+        const double sa = ts[i], la = tlk[i];
+        for (int e = fptr[t]; e < fptr[t + 1]; ++e) {
+            const int s = fcol[e];
+            for (int be = 0; be < k; ++be) {
+                const int j = s * k + be;
+                double r2 = 0.0;
+                for (int c = 0; c < d; ++c) {
+                    const double dd = xa[c] - sch[(size_t)j * d + c];
+                    r2 = fma(dd, dd, r2);
+                }
+                const double lr2 = fast_log(mt, r2);
+                const double g = fast_exp(mt, 0.5 * (la + slk[j]) - 0.5 * (d + sa + ss[j]) * lr2) * xs[j];
+                acc1 += g;
+                accs = fma(g, lr2, accs);
+            }
+        }
+        accs *= 0.5 * chat[i];
+        acc1 *= -0.5 * chat[i];
     }
+    Gs[i] = accs;
+    Gk[i] = acc1;
+}
+
+// density far part, source nodes: thread per (s, beta) over the target nodes
+// whose admissible list holds s
+__global__ void k_gh_rho_far_s(int d, int k, int nnode_s, const int *__restrict__ tptr, const int *__restrict__ tcol,
+                               const double *__restrict__ tch, const double *__restrict__ ts,
+                               const double *__restrict__ tlk, const double *__restrict__ sch,
+                               const double *__restrict__ ss, const double *__restrict__ slk,
+                               const double *__restrict__ xs, const double *__restrict__ chat,
+                               const double *__restrict__ mt, double *__restrict__ Gs, double *__restrict__ Gk)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nnode_s * k) return;
+    const int s = j / k;
+    double accs = 0.0, acc1 = 0.0;
+    if (tptr[s + 1] > tptr[s]) {
+        const double *xb = sch + (size_t)j * d;
+        const double sb = ss[j], lb = slk[j];
+        for (int e = tptr[s]; e < tptr[s + 1]; ++e) {
+            const int t = tcol[e];
+            for (int al = 0; al < k; ++al) {
+                const int i = t * k + al;
+                double r2 = 0.0;
+                for (int c = 0; c < d; ++c) {
+                    const double dd = tch[(size_t)i * d + c] - xb[c];
+                    r2 = fma(dd, dd, r2);
+                }
+                const double lr2 = fast_log(mt, r2);
+                const double g = fast_exp(mt, 0.5 * (tlk[i] + lb) - 0.5 * (d + ts[i] + sb) * lr2) * chat[i];
+                acc1 += g;
+                accs = fma(g, lr2, accs);
+            }
+        }
+        accs *= 0.5 * xs[j];
+        acc1 *= -0.5 * xs[j];
+    }
+    Gs[j] = accs;
+    Gk[j] = acc1;
 }
 
 // touching pairs: per pair the 12 partial gradients (s at pv[0..2], qv[0..2];
@@ -333,12 +774,19 @@ __global__ void __launch_bounds__(256) k_grad_sing(GradSing P, double *__restric
         }
 }
 
-// per vertex: g_s = 2 sum bary h_s + sum of its pair slots, g_lk = -sum bary h_1 + ...
-__global__ void k_grad_gather(int M, const int *__restrict__ qptr, const int *__restrict__ qidx,
-                              const double *__restrict__ qbary, const double *__restrict__ hs,
-                              const double *__restrict__ h1, const int *__restrict__ pptr,
-                              const int *__restrict__ pidx, const double *__restrict__ pg, double *__restrict__ g_s,
-                              double *__restrict__ g_lk)
+// per vertex: the point sensitivities (density), the K-near leaf-point
+// sensitivities, the node sensitivities (K, target, source nodes) and the
+// touching pairs' slots, each times the barycentric coordinate of the vertex
+__global__ void k_gh_gather(int M, const int *__restrict__ qptr, const int *__restrict__ qidx,
+                            const double *__restrict__ qbary, const double *__restrict__ hPs,
+                            const double *__restrict__ hPk, const int *__restrict__ lptr,
+                            const int *__restrict__ lidx, const int *__restrict__ lp_pts,
+                            const double *__restrict__ hKs, const double *__restrict__ hKk,
+                            const int *__restrict__ nptr, const int *__restrict__ nidx,
+                            const double *__restrict__ nbary, const double *__restrict__ Gs,
+                            const double *__restrict__ Gk, const int *__restrict__ pptr,
+                            const int *__restrict__ pidx, const double *__restrict__ pg, double *__restrict__ g_s,
+                            double *__restrict__ g_lk)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= M) return;
@@ -346,8 +794,20 @@ __global__ void k_grad_gather(int M, const int *__restrict__ qptr, const int *__
     for (int e = qptr[v]; e < qptr[v + 1]; ++e) {
         const int code = qidx[e], q = code / QB;
         const double w = qbary[(size_t)code];   // qbary[q * QB + slot]
-        a += 2.0 * w * hs[q];
-        b -= w * h1[q];
+        a = fma(w, hPs[q], a);
+        b = fma(w, hPk[q], b);
+    }
+    for (int e = lptr[v]; e < lptr[v + 1]; ++e) {
+        const int code = lidx[e], t = code / QB, slot = code - t * QB;
+        const double w = qbary[(size_t)lp_pts[t] * QB + slot];
+        a = fma(w, hKs[t], a);
+        b = fma(w, hKk[t], b);
+    }
+    for (int e = nptr[v]; e < nptr[v + 1]; ++e) {
+        const int code = nidx[e], n = code / QB;
+        const double w = nbary[code];
+        a = fma(w, Gs[n], a);
+        b = fma(w, Gk[n], b);
     }
     for (int e = pptr[v]; e < pptr[v + 1]; ++e) {
         const int code = pidx[e], p = code / 6, slot = code - p * 6;
@@ -360,47 +820,95 @@ __global__ void k_grad_gather(int M, const int *__restrict__ qptr, const int *__
 
 }  // namespace
 
-// vertex -> (point, slot) and vertex -> (pair, slot) lists, built once per mesh
+// node entries of the gradient: the K tree's nodes (when it has admissible
+// blocks), then the density target and source trees' nodes (when the density
+// has admissible blocks)
+static int64_t node_entries(const MeshData &m, int64_t *oT, int64_t *oS)
+{
+    const int64_t nK = m.nfar > 0 ? (int64_t)m.kt.nnode * m.k : 0;
+    const int64_t nT = m.nrfar > 0 ? (int64_t)m.tt.nnode * m.k : 0;
+    const int64_t nS = m.nrfar > 0 ? (int64_t)m.st.nnode * m.k : 0;
+    *oT = nK;
+    *oS = nK + nT;
+    return nK + nT + nS;
+}
+
+// vertex -> (point, slot), (pair, slot), (leaf-point entry, slot) and
+// (node entry, slot) lists, built once per mesh
 static void ensure_grad_lists(MeshData &m)
 {
     if (m.grad_lists) return;
     const int nv = m.d + 1;
-    std::vector<int> qcnt(m.M + 1, 0), pcnt(m.M + 1, 0);
-    for (int q = 0; q < m.nQ; ++q)
-        for (int a = 0; a < nv; ++a) qcnt[m.T[(size_t)m.qcell_host[q] * nv + a] + 1]++;
-    for (int p = 0; p < m.npairs; ++p)
-        for (int a = 0; a < nv; ++a) {
-            pcnt[m.pair_info_h[(size_t)p * 8 + 2 + a] + 1]++;
-            pcnt[m.pair_info_h[(size_t)p * 8 + 5 + a] + 1]++;
-        }
-    for (int v = 0; v < m.M; ++v) {
-        qcnt[v + 1] += qcnt[v];
-        pcnt[v + 1] += pcnt[v];
+    auto build = [&](int n_items, auto vert_of, std::vector<int> &ptr, std::vector<int> &idx) {
+        ptr.assign(m.M + 1, 0);
+        for (int it = 0; it < n_items; ++it)
+            for (int a = 0; a < nv; ++a) ptr[vert_of(it, a) + 1]++;
+        for (int v = 0; v < m.M; ++v) ptr[v + 1] += ptr[v];
+        idx.assign(ptr[m.M], 0);
+        std::vector<int> f(ptr.begin(), ptr.end() - 1);
+        for (int it = 0; it < n_items; ++it)
+            for (int a = 0; a < nv; ++a) idx[f[vert_of(it, a)]++] = it * QB + a;
+    };
+    std::vector<int> ptr, idx;
+    build(m.nQ, [&](int q, int a) { return m.T[(size_t)m.qcell_host[q] * nv + a]; }, ptr, idx);
+    m.gq_ptr.upload(ptr);
+    m.gq_idx.upload(idx);
+    // pairs: two vertex triples per pair, slots 0..2 and 3..5
+    {
+        std::vector<int> pc(m.M + 1, 0);
+        for (int p = 0; p < m.npairs; ++p)
+            for (int a = 0; a < nv; ++a) {
+                pc[m.pair_info_h[(size_t)p * 8 + 2 + a] + 1]++;
+                pc[m.pair_info_h[(size_t)p * 8 + 5 + a] + 1]++;
+            }
+        for (int v = 0; v < m.M; ++v) pc[v + 1] += pc[v];
+        std::vector<int> pidx(pc[m.M]), pf(pc.begin(), pc.end() - 1);
+        for (int p = 0; p < m.npairs; ++p)
+            for (int a = 0; a < nv; ++a) {
+                pidx[pf[m.pair_info_h[(size_t)p * 8 + 2 + a]]++] = p * 6 + a;
+                pidx[pf[m.pair_info_h[(size_t)p * 8 + 5 + a]]++] = p * 6 + 3 + a;
+            }
+        m.gp_ptr.upload(pc);
+        m.gp_idx.upload(pidx);
     }
-    std::vector<int> qidx(qcnt[m.M]), pidx(pcnt[m.M]), qf(qcnt.begin(), qcnt.end() - 1), pf(pcnt.begin(), pcnt.end() - 1);
-    for (int q = 0; q < m.nQ; ++q)
-        for (int a = 0; a < nv; ++a) {
-            const int v = m.T[(size_t)m.qcell_host[q] * nv + a];
-            qidx[qf[v]++] = q * QB + a;
+    build((int)m.lp_pts_h.size(), [&](int t, int a) { return m.T[(size_t)m.qcell_host[m.lp_pts_h[t]] * nv + a]; },
+          ptr, idx);
+    m.gl_ptr.upload(ptr);
+    m.gl_idx.upload(idx);
+    // node entries with their located cells
+    int64_t oT, oS;
+    const int64_t nn = node_entries(m, &oT, &oS);
+    VFD_REQUIRE(nn * QB < (int64_t)1 << 31, VFD_EUNSUPPORTED, "vfd_grad: too many Chebyshev nodes");
+    std::vector<int> ncell(nn);
+    std::vector<double> nb((size_t)nn * QB, 0.0);
+    auto put = [&](const NodeLoc &loc, int64_t off, int64_t n) {
+        VFD_REQUIRE(n == 0 || (loc.done && (int64_t)loc.cell_h.size() == n), VFD_ECUDA, "nodes not located");
+        for (int64_t i = 0; i < n; ++i) {
+            ncell[off + i] = loc.cell_h[i];
+            for (int a = 0; a < QB; ++a) nb[(size_t)(off + i) * QB + a] = loc.bary_h[(size_t)i * QB + a];
         }
-    for (int p = 0; p < m.npairs; ++p)
-        for (int a = 0; a < nv; ++a) {
-            const int v1 = m.pair_info_h[(size_t)p * 8 + 2 + a], v2 = m.pair_info_h[(size_t)p * 8 + 5 + a];
-            pidx[pf[v1]++] = p * 6 + a;
-            pidx[pf[v2]++] = p * 6 + 3 + a;
-        }
-    m.gq_ptr.upload(qcnt);
-    m.gq_idx.upload(qidx);
-    m.gp_ptr.upload(pcnt);
-    m.gp_idx.upload(pidx);
+    };
+    put(m.kt_loc, 0, oT);
+    put(m.tt_loc, oT, oS - oT);
+    put(m.st_loc, oS, nn - oS);
+    build((int)nn, [&](int n, int a) { return m.T[(size_t)ncell[n] * nv + a]; }, ptr, idx);
+    m.gn_ptr.upload(ptr);
+    m.gn_idx.upload(idx);
+    if (nn) m.gn_bary.upload(nb);
+    else m.gn_bary.alloc(1);
     m.grad_lists = true;
 }
 
-void grad_exact(MeshData &m, OpData &op, const double *U, const double *Lam, int nrhs, int64_t ld, double *g_s,
-                double *g_lk, cudaStream_t st)
+void grad_adjoint(MeshData &m, OpData &op, const double *U, const double *Lam, int nrhs, int64_t ld, double *g_s,
+                  double *g_lk, cudaStream_t st)
 {
+    VFD_REQUIRE(m.d <= 2, VFD_EUNSUPPORTED, "vfd_grad is built for d = 1, 2");
+    VFD_REQUIRE((m.nfar == 0 && m.nrfar == 0) || m.nodes_located, VFD_ECUDA, "vfd_grad: nodes not located");
     ensure_grad_lists(m);
-    const size_t nq = (size_t)m.nQ;
+    const size_t nq = (size_t)m.nQ, nlp = m.lp_pts_h.size();
+    const int k = m.k;
+    int64_t oT, oS;
+    const int64_t nn = node_entries(m, &oT, &oS);
     if (op.gr_uq.n < nq * nrhs) {
         op.gr_uq.alloc(nq * nrhs);
         op.gr_lq.alloc(nq * nrhs);
@@ -408,22 +916,126 @@ void grad_exact(MeshData &m, OpData &op, const double *U, const double *Lam, int
     if (op.gr_hs.n < nq) {
         op.gr_hs.alloc(nq);
         op.gr_h1.alloc(nq);
+        op.gr_cq.alloc(nq);
     }
-    if (op.gr_pg.n < (size_t)m.npairs * 12) op.gr_pg.alloc((size_t)m.npairs * 12 + 1);
+    if (op.gr_hKs.n < std::max<size_t>(nlp, 1)) {
+        op.gr_hKs.alloc(std::max<size_t>(nlp, 1));
+        op.gr_hKk.alloc(std::max<size_t>(nlp, 1));
+    }
+    if (op.gr_Gs.n < (size_t)std::max<int64_t>(nn, 1)) {
+        op.gr_Gs.alloc(std::max<int64_t>(nn, 1));
+        op.gr_Gk.alloc(std::max<int64_t>(nn, 1));
+    }
+    if (op.gr_pg.n < (size_t)m.npairs * 12 + 1) op.gr_pg.alloc((size_t)m.npairs * 12 + 1);
+    // U, Lam at the points; c_q
     k_grad_vals<<<cdiv(m.nQ, 256), 256, 0, st>>>(m.nQ, m.d, nrhs, ld, m.qcell.p, m.qbary.p, m.cells.p, m.vdof.p, U,
                                                  Lam, op.gr_uq.p, op.gr_lq.p);
+    k_gh_cq<<<cdiv(m.nQ, 256), 256, 0, st>>>(m.nQ, m.nQint, nrhs, m.qw.p, op.gr_uq.p, op.gr_lq.p, op.gr_cq.p);
     VFD_CUDA(cudaGetLastError());
+    VFD_CUDA(cudaMemsetAsync(op.gr_Gs.p, 0, sizeof(double) * std::max<int64_t>(nn, 1), st));
+    VFD_CUDA(cudaMemsetAsync(op.gr_Gk.p, 0, sizeof(double) * std::max<int64_t>(nn, 1), st));
+    // K: near blocks and admissible blocks, GNR columns per pass
+    const int fl = m.kt.first_leaf();
+    const size_t hsz = (size_t)m.kt.nnode * k;
+    if (m.nfar > 0 && op.gr_xU.n < hsz * GNR) {
+        op.gr_xU.alloc(hsz * GNR);
+        op.gr_xL.alloc(hsz * GNR);
+    }
+    if (m.nnear == 0) {
+        VFD_CUDA(cudaMemsetAsync(op.gr_hKs.p, 0, sizeof(double) * std::max<size_t>(nlp, 1), st));
+        VFD_CUDA(cudaMemsetAsync(op.gr_hKk.p, 0, sizeof(double) * std::max<size_t>(nlp, 1), st));
+    }
     for (int r0 = 0; r0 < nrhs; r0 += GNR) {
         const int nr = std::min(GNR, nrhs - r0);
-        const double *uq = op.gr_uq.p + (size_t)r0 * nq, *lq = op.gr_lq.p + (size_t)r0 * nq;
-        if (m.d == 2)
-            k_grad_sep<2><<<cdiv(m.nQ, GT), GT, 0, st>>>(m.nQ, m.nQint, nr, r0 > 0, m.qx.p, m.qw.p, op.q_s.p,
-                                                        op.q_lk.p, m.qcell.p, m.cells.p, uq, lq, m.mtab.p,
-                                                        op.gr_hs.p, op.gr_h1.p);
-        else
-            k_grad_sep<1><<<cdiv(m.nQ, GT), GT, 0, st>>>(m.nQ, m.nQint, nr, r0 > 0, m.qx.p, m.qw.p, op.q_s.p,
-                                                        op.q_lk.p, m.qcell.p, m.cells.p, uq, lq, m.mtab.p,
-                                                        op.gr_hs.p, op.gr_h1.p);
+        if (m.nnear > 0) {
+            GKN P;
+            P.nQ = m.nQ;
+            P.fl = fl;
+            P.nr = nr;
+            P.accumulate = r0 > 0;
+            P.ld = ld;
+            P.U = U + (size_t)r0 * ld;
+            P.Lam = Lam + (size_t)r0 * ld;
+            P.kt_begin = m.kt_begin.p;
+            P.kt_end = m.kt_end.p;
+            P.lp_ptr = m.lp_ptr.p;
+            P.lp_pts = m.lp_pts.p;
+            P.near_ptr = m.near_ptr.p;
+            P.near_col = m.near_col.p;
+            P.qx = m.qx.p;
+            P.qw = m.qw.p;
+            P.qs = op.q_s.p;
+            P.qlk = op.q_lk.p;
+            P.qbary = m.qbary.p;
+            P.qcell = m.qcell.p;
+            P.cells = m.cells.p;
+            P.vdof = m.vdof.p;
+            P.mt = m.mtab.p;
+            P.hs = op.gr_hKs.p;
+            P.hk = op.gr_hKk.p;
+            dim3 g(m.kt.nleaf, cdiv(m.max_leaf_pts, GT));
+            if (m.d == 2) k_gh_knear<2><<<g, GT, 0, st>>>(P);
+            else k_gh_knear<1><<<g, GT, 0, st>>>(P);
+            VFD_CUDA(cudaGetLastError());
+        }
+        if (m.nfar > 0) {
+            k_gh_moments<<<m.kt.nnode, 128, 0, st>>>(nr, k, m.N, m.far_lmin, m.kt.nnode, m.far_ptr.p, m.kt_begin.p,
+                                                     m.kt_end.p, m.Ul64.p, U + (size_t)r0 * ld, Lam + (size_t)r0 * ld,
+                                                     ld, op.gr_xU.p, op.gr_xL.p);
+            k_gh_kfar<<<m.kt.nnode, 256, 0, st>>>(m.d, k, m.kt.nnode, nr, m.far_ptr.p, m.far_col.p, m.kt_cheb.p,
+                                                  op.kc_s.p, op.kc_lk.p, op.gr_xU.p, op.gr_xL.p, m.mtab.p, op.gr_Gs.p,
+                                                  op.gr_Gk.p);
+            VFD_CUDA(cudaGetLastError());
+        }
+    }
+    // density: near sources on both sides, then the admissible blocks
+    {
+        GRho P;
+        P.d = m.d;
+        P.nv = m.d + 1;
+        P.nQ = m.nQ;
+        P.k = k;
+        P.p = m.p;
+        P.tfl = m.tt.first_leaf();
+        P.sfl = m.st.first_leaf();
+        P.tt_begin = m.tt_begin.p;
+        P.tt_end = m.tt_end.p;
+        P.tt_perm = m.tt_perm.p;
+        P.st_begin = m.st_begin.p;
+        P.st_end = m.st_end.p;
+        P.st_perm = m.st_perm.p;
+        P.rnear_ptr = m.rnear_ptr.p;
+        P.rnear_col = m.rnear_col.p;
+        P.rnearT_ptr = m.rnearT_ptr.p;
+        P.rnearT_col = m.rnearT_col.p;
+        P.qx = m.qx.p;
+        P.qw = m.qw.p;
+        P.qs = op.q_s.p;
+        P.qlk = op.q_lk.p;
+        P.cq = op.gr_cq.p;
+        P.qcell = m.qcell.p;
+        P.cells = m.cells.p;
+        P.mt = m.mtab.p;
+        P.hs = op.gr_hs.p;
+        P.hk = op.gr_h1.p;
+        VFD_CUDA(cudaMemsetAsync(op.gr_hs.p, 0, sizeof(double) * nq, st));
+        VFD_CUDA(cudaMemsetAsync(op.gr_h1.p, 0, sizeof(double) * nq, st));
+        k_gh_rho_near_t<<<m.tt.nleaf, RCH, 0, st>>>(P);
+        k_gh_rho_near_s<<<m.st.nleaf, RCH, 0, st>>>(P);
+        VFD_CUDA(cudaGetLastError());
+    }
+    if (m.nrfar > 0) {
+        const size_t nt = (size_t)m.tt.nnode * k;
+        if (op.gr_ct.n < nt) op.gr_ct.alloc(nt);
+        VFD_CUDA(cudaMemsetAsync(op.gr_ct.p, 0, sizeof(double) * nt, st));
+        k_gh_rho_moments<<<m.tt.nnode, 128, 0, st>>>(m.d, m.p, k, m.nQ, m.rfar_ptr.p, m.tt_begin.p, m.tt_end.p,
+                                                     m.tt_perm.p, m.tt_cheb.p, m.qx.p, op.gr_cq.p, op.gr_ct.p);
+        k_gh_rho_far_t<<<cdiv((long long)m.tt.nnode * k, 128), 128, 0, st>>>(
+            m.d, k, m.tt.nnode, m.rfar_ptr.p, m.rfar_col.p, m.tt_cheb.p, op.tc_s.p, op.tc_lk.p, m.st_cheb.p,
+            op.sc_s.p, op.sc_lk.p, m.st_xhat.p, op.gr_ct.p, m.mtab.p, op.gr_Gs.p + oT, op.gr_Gk.p + oT);
+        k_gh_rho_far_s<<<cdiv((long long)m.st.nnode * k, 128), 128, 0, st>>>(
+            m.d, k, m.st.nnode, m.rfarT_ptr.p, m.rfarT_col.p, m.tt_cheb.p, op.tc_s.p, op.tc_lk.p, m.st_cheb.p,
+            op.sc_s.p, op.sc_lk.p, m.st_xhat.p, op.gr_ct.p, m.mtab.p, op.gr_Gs.p + oS, op.gr_Gk.p + oS);
         VFD_CUDA(cudaGetLastError());
     }
     if (m.npairs > 0) {
@@ -447,8 +1059,10 @@ void grad_exact(MeshData &m, OpData &op, const double *U, const double *Lam, int
         k_grad_sing<<<cdiv((long long)m.npairs * 32, 256), 256, 0, st>>>(P, op.gr_pg.p);
         VFD_CUDA(cudaGetLastError());
     }
-    k_grad_gather<<<cdiv(m.M, 256), 256, 0, st>>>(m.M, m.gq_ptr.p, m.gq_idx.p, m.qbary.p, op.gr_hs.p, op.gr_h1.p,
-                                                  m.gp_ptr.p, m.gp_idx.p, op.gr_pg.p, g_s, g_lk);
+    k_gh_gather<<<cdiv(m.M, 256), 256, 0, st>>>(m.M, m.gq_ptr.p, m.gq_idx.p, m.qbary.p, op.gr_hs.p, op.gr_h1.p,
+                                                m.gl_ptr.p, m.gl_idx.p, m.lp_pts.p, op.gr_hKs.p, op.gr_hKk.p,
+                                                m.gn_ptr.p, m.gn_idx.p, m.gn_bary.p, op.gr_Gs.p, op.gr_Gk.p,
+                                                m.gp_ptr.p, m.gp_idx.p, op.gr_pg.p, g_s, g_lk);
     VFD_CUDA(cudaGetLastError());
 }
 

@@ -9,6 +9,8 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
+#include <vector>
 
 #include "vfd_internal.h"
 
@@ -648,6 +650,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
         std::vector<double> kcheb((size_t)nnode * k * d);
         for (int n = 0; n < nnode; ++n) cheb_box(d, p, &kt.lo[(size_t)n * d], &kt.hi[(size_t)n * d], &kcheb[(size_t)n * k * d]);
         m->kt_cheb.upload(kcheb);
+        m->kt_cheb_h = kcheb;
         m->kt_begin.upload(kt.begin);
         m->kt_end.upload(kt.end);
 
@@ -846,6 +849,8 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                 }
             m->lp_ptr.upload(lp_ptr);
             m->lp_pts.upload(lp_pts);
+            m->lp_ptr_h = lp_ptr;
+            m->lp_pts_h = lp_pts;
             m->supp_ptr.upload(sp);
             m->supp_loc.upload(sl);
             m->supp_coef.upload(sc);
@@ -913,6 +918,7 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
                     }
                 }
                 m->kt_cheb_in.upload(kcin);
+                m->kt_cheb_in_h = kcin;
                 m->E_in64.upload(Ein);
             }
         }
@@ -985,6 +991,22 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             m->rfar_col.upload(fc);
             m->rnear_ptr.upload(np_);
             m->rnear_col.upload(nc);
+            // transposed lists (by source node / source leaf) for the gradient's
+            // source-side sums
+            {
+                std::vector<std::vector<int>> ft(st.nnode), nt(st.nleaf);
+                for (int a = 0; a < tt.nnode; ++a)
+                    for (int e = fp[a]; e < fp[a + 1]; ++e) ft[fc[e]].push_back(a);
+                for (int a = 0; a < tt.nleaf; ++a)
+                    for (int e = np_[a]; e < np_[a + 1]; ++e) nt[nc[e] - st.first_leaf()].push_back(a);
+                std::vector<int> tp, tc, up, uc;
+                csr_from_lists(ft, tp, tc);
+                csr_from_lists(nt, up, uc);
+                m->rfarT_ptr.upload(tp);
+                m->rfarT_col.upload(tc);
+                m->rnearT_ptr.upload(up);
+                m->rnearT_col.upload(uc);
+            }
             m->tt_begin.upload(tt.begin);
             m->tt_end.upload(tt.end);
             m->tt_perm.upload(tt.perm);
@@ -995,6 +1017,8 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
             m->tt_hi.upload(tt.hi);
             m->tt_cheb.upload(tch);
             m->st_cheb.upload(sch);
+            m->tt_cheb_h = tch;
+            m->st_cheb_h = sch;
             m->st_xhat.upload(xs);
         }
 
@@ -1040,6 +1064,229 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
         throw;
     }
     return m;
+}
+
+// ---------------------------------------------------------------------------
+// Nearest-point location of the Chebyshev nodes (P1 fields at the nodes).
+// A node inside the meshed region takes the P1 interpolant of its cell; a
+// node outside it (boxes reach past the mesh) takes the value at the nearest
+// point of the mesh.  Both are the barycentric coordinates of the closest
+// point of the closest cell, found by a bucket grid over the cells' bounding
+// boxes searched in rings of growing distance.
+// ---------------------------------------------------------------------------
+namespace {
+
+// closest point of the simplex V[0..d] (row-major, d coordinates) to x, as
+// barycentric coordinates: the orthogonal projections onto the affine hulls
+// of all faces, the nearest projection whose coordinates are non-negative
+double closest_in_simplex(int d, const double *V, const double *x, double *bary)
+{
+    const int nvx = d + 1;
+    double best = 1e300;
+    for (int mask = 1; mask < (1 << nvx); ++mask) {
+        int idx[4], n = 0;
+        for (int a = 0; a < nvx; ++a)
+            if (mask >> a & 1) idx[n++] = a;
+        const double *v0 = V + (size_t)idx[0] * d;
+        double e[3][3], G[3][3], rhs[3], lam[3] = {0, 0, 0};
+        const int m = n - 1;
+        for (int j = 0; j < m; ++j)
+            for (int c = 0; c < d; ++c) e[j][c] = V[(size_t)idx[j + 1] * d + c] - v0[c];
+        for (int i = 0; i < m; ++i) {
+            rhs[i] = 0.0;
+            for (int c = 0; c < d; ++c) rhs[i] += e[i][c] * (x[c] - v0[c]);
+            for (int j = 0; j < m; ++j) {
+                G[i][j] = 0.0;
+                for (int c = 0; c < d; ++c) G[i][j] += e[i][c] * e[j][c];
+            }
+        }
+        // Gaussian elimination with partial pivoting on the m x m Gram system
+        bool ok = true;
+        for (int c = 0; c < m && ok; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < m; ++r)
+                if (std::fabs(G[r][c]) > std::fabs(G[piv][c])) piv = r;
+            if (!(std::fabs(G[piv][c]) > 1e-300)) {
+                ok = false;
+                break;
+            }
+            if (piv != c) {
+                for (int j = 0; j < m; ++j) std::swap(G[c][j], G[piv][j]);
+                std::swap(rhs[c], rhs[piv]);
+            }
+            for (int r = c + 1; r < m; ++r) {
+                const double f = G[r][c] / G[c][c];
+                for (int j = c; j < m; ++j) G[r][j] -= f * G[c][j];
+                rhs[r] -= f * rhs[c];
+            }
+        }
+        if (!ok) continue;
+        for (int c = m - 1; c >= 0; --c) {
+            double v = rhs[c];
+            for (int j = c + 1; j < m; ++j) v -= G[c][j] * lam[j];
+            lam[c] = v / G[c][c];
+        }
+        double l0 = 1.0;
+        bool inside = true;
+        for (int j = 0; j < m; ++j) {
+            l0 -= lam[j];
+            inside &= lam[j] >= -1e-13;
+        }
+        inside &= l0 >= -1e-13;
+        if (!inside) continue;
+        double dist2 = 0.0;
+        for (int c = 0; c < d; ++c) {
+            double pc = v0[c];
+            for (int j = 0; j < m; ++j) pc += lam[j] * e[j][c];
+            dist2 += (x[c] - pc) * (x[c] - pc);
+        }
+        if (dist2 < best) {
+            best = dist2;
+            for (int a = 0; a < nvx; ++a) bary[a] = 0.0;
+            bary[idx[0]] = std::max(l0, 0.0);
+            for (int j = 0; j < m; ++j) bary[idx[j + 1]] = std::max(lam[j], 0.0);
+        }
+    }
+    double sum = 0.0;
+    for (int a = 0; a < nvx; ++a) sum += bary[a];
+    for (int a = 0; a < nvx; ++a) bary[a] /= sum;
+    return best;
+}
+
+struct CellGrid {
+    int d = 2, n[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, h = 1.0;
+    std::vector<int> ptr, idx;
+    int bucket(const int *c) const { return (c[2] * n[1] + c[1]) * n[0] + c[0]; }
+};
+
+CellGrid make_cell_grid(const MeshData &m)
+{
+    CellGrid g;
+    const int d = m.d, nv = d + 1;
+    g.d = d;
+    double hi[3] = {0, 0, 0};
+    for (int c = 0; c < d; ++c) {
+        g.lo[c] = 1e300;
+        hi[c] = -1e300;
+    }
+    for (int v = 0; v < m.M; ++v)
+        for (int c = 0; c < d; ++c) {
+            g.lo[c] = std::min(g.lo[c], m.X[(size_t)v * d + c]);
+            hi[c] = std::max(hi[c], m.X[(size_t)v * d + c]);
+        }
+    double ext = 0.0;
+    for (int c = 0; c < d; ++c) ext = std::max(ext, hi[c] - g.lo[c]);
+    g.h = std::max(m.h_max, ext / (d == 3 ? 128.0 : 1024.0));
+    if (!(g.h > 0.0)) g.h = 1.0;
+    for (int c = 0; c < d; ++c) g.n[c] = std::max(1, (int)std::ceil((hi[c] - g.lo[c]) / g.h) + 1);
+    const size_t nb = (size_t)g.n[0] * g.n[1] * g.n[2];
+    std::vector<std::vector<int>> lists(nb);
+    for (int cell = 0; cell < m.C; ++cell) {
+        int clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) {
+            double a = 1e300, b = -1e300;
+            for (int k = 0; k < nv; ++k) {
+                const double x = m.X[(size_t)m.T[(size_t)cell * nv + k] * d + c];
+                a = std::min(a, x);
+                b = std::max(b, x);
+            }
+            clo[c] = std::min(g.n[c] - 1, std::max(0, (int)std::floor((a - g.lo[c]) / g.h)));
+            chi[c] = std::min(g.n[c] - 1, std::max(0, (int)std::floor((b - g.lo[c]) / g.h)));
+        }
+        int b3[3];
+        for (b3[2] = clo[2]; b3[2] <= chi[2]; ++b3[2])
+            for (b3[1] = clo[1]; b3[1] <= chi[1]; ++b3[1])
+                for (b3[0] = clo[0]; b3[0] <= chi[0]; ++b3[0]) lists[g.bucket(b3)].push_back(cell);
+    }
+    csr_from_lists(lists, g.ptr, g.idx);
+    return g;
+}
+
+// closest cell and barycentric coordinates for each of n points (node-major,
+// d coords); points split over host threads
+void locate(const MeshData &m, const CellGrid &g, const std::vector<double> &pts, NodeLoc &out)
+{
+    const int d = m.d, nv = d + 1;
+    const int n = (int)(pts.size() / d);
+    out.cell_h.assign(n, -1);
+    out.bary_h.assign((size_t)n * QB, 0.0);
+    auto work = [&](int i_begin, int i_end) {
+        std::vector<int> stamp(m.C, -1);
+        double V[12], bary[4];
+        for (int i = i_begin; i < i_end; ++i) {
+            const double *x = &pts[(size_t)i * d];
+            int c0[3] = {0, 0, 0};
+            for (int c = 0; c < d; ++c)
+                c0[c] = std::min(g.n[c] - 1, std::max(0, (int)std::floor((x[c] - g.lo[c]) / g.h)));
+            double best = 1e300;
+            int bcell = -1;
+            double bb[4] = {0, 0, 0, 0};
+            const int rmax = std::max(g.n[0], std::max(g.n[1], g.n[2]));
+            for (int r = 0; r <= rmax && best > 0.0; ++r) {
+                int lo3[3] = {0, 0, 0}, hi3[3] = {0, 0, 0};
+                for (int c = 0; c < d; ++c) {
+                    lo3[c] = c0[c] - r;
+                    hi3[c] = c0[c] + r;
+                }
+                int b3[3];
+                for (b3[2] = lo3[2]; b3[2] <= hi3[2] && best > 0.0; ++b3[2])
+                    for (b3[1] = lo3[1]; b3[1] <= hi3[1] && best > 0.0; ++b3[1])
+                        for (b3[0] = lo3[0]; b3[0] <= hi3[0] && best > 0.0; ++b3[0]) {
+                            bool ring = false, in = true;
+                            for (int c = 0; c < d; ++c) {
+                                ring |= (b3[c] == lo3[c] || b3[c] == hi3[c]);
+                                in &= (b3[c] >= 0 && b3[c] < g.n[c]);
+                            }
+                            if (!ring || !in) continue;
+                            const int bk = g.bucket(b3);
+                            for (int e = g.ptr[bk]; e < g.ptr[bk + 1] && best > 0.0; ++e) {
+                                const int cell = g.idx[e];
+                                if (stamp[cell] == i) continue;
+                                stamp[cell] = i;
+                                for (int a = 0; a < nv; ++a)
+                                    for (int c = 0; c < d; ++c)
+                                        V[a * d + c] = m.X[(size_t)m.T[(size_t)cell * nv + a] * d + c];
+                                const double dist2 = closest_in_simplex(d, V, x, bary);
+                                if (dist2 < best) {
+                                    best = dist2;
+                                    bcell = cell;
+                                    for (int a = 0; a < nv; ++a) bb[a] = bary[a];
+                                }
+                            }
+                        }
+                // every cell first met in a later ring lies at least r * h away
+                if (bcell >= 0 && best <= (r * g.h) * (r * g.h)) break;
+            }
+            out.cell_h[i] = bcell;
+            for (int a = 0; a < nv; ++a) out.bary_h[(size_t)i * QB + a] = bb[a];
+        }
+    };
+    const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 4096 || nth == 1) {
+        work(0, n);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t) th.emplace_back(work, (int)((int64_t)n * t / nth), (int)((int64_t)n * (t + 1) / nth));
+        for (auto &t : th) t.join();
+    }
+    for (int i = 0; i < n; ++i) VFD_REQUIRE(out.cell_h[i] >= 0, VFD_EINVAL, "node location: no cell found");
+    out.cell.upload(out.cell_h);
+    out.bary.upload(out.bary_h);
+    out.done = true;
+}
+
+}  // namespace
+
+void locate_nodes(MeshData &m)
+{
+    if (m.nodes_located) return;
+    const CellGrid g = make_cell_grid(m);
+    if (!m.kt_cheb_h.empty()) locate(m, g, m.kt_cheb_h, m.kt_loc);
+    if (!m.kt_cheb_in_h.empty()) locate(m, g, m.kt_cheb_in_h, m.kt_in_loc);
+    if (!m.tt_cheb_h.empty()) locate(m, g, m.tt_cheb_h, m.tt_loc);
+    if (!m.st_cheb_h.empty()) locate(m, g, m.st_cheb_h, m.st_loc);
+    m.nodes_located = true;
 }
 
 }  // namespace vfd

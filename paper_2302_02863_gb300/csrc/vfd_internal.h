@@ -101,6 +101,16 @@ struct Tree {
     bool is_leaf(int n) const { return n >= first_leaf(); }
 };
 
+// closest cell and its barycentric coordinates (QB per point) for a set of
+// points (the Chebyshev nodes of a tree): P1 field values there
+struct NodeLoc {
+    bool done = false;
+    std::vector<int> cell_h;
+    std::vector<double> bary_h;
+    DBuf<int> cell;
+    DBuf<double> bary;
+};
+
 // ---------------------------------------------------------------------------
 // mesh handle: geometry-only data, built once per mesh
 // ---------------------------------------------------------------------------
@@ -132,7 +142,7 @@ struct MeshData {
     int npairs = 0;
     DBuf<int> pair_info;   // npairs * 8: type, w(1|2), pv0..2, qv0..2
     std::vector<int> pair_info_h;   // host copy
-    // gradient gather lists (built on the first vfd_grad): vertex -> point*3 + slot, vertex -> pair*6 + slot
+    // gradient gather lists (built on the first vfd_grad): vertex -> point * QB + slot, vertex -> pair * 6 + slot
     bool grad_lists = false;
     DBuf<int> gq_ptr, gq_idx, gp_ptr, gp_idx;
     // B/M sparsity (DoF CSR) and deterministic gather lists
@@ -197,8 +207,21 @@ struct MeshData {
     DBuf<double> gl9_x, gl9_w;          // 9-point rule for the tail
     DBuf<double> mtab;                  // tables of the table-driven FP64 log/exp
 
+    DBuf<int> rfarT_ptr, rfarT_col;     // transposed: source node -> target nodes
+    DBuf<int> rnearT_ptr, rnearT_col;   // transposed: source leaf index -> target leaf indices
+
     // load assembly (exact P1 mass)
     DBuf<int> ld_ptr, ld_idx;           // DoF -> list of cell*(d+1)+a contributions
+
+    // host copies for the nearest-point location of the Chebyshev nodes
+    std::vector<double> kt_cheb_h, kt_cheb_in_h, tt_cheb_h, st_cheb_h;
+    std::vector<int> lp_ptr_h, lp_pts_h;
+    bool nodes_located = false;
+    NodeLoc kt_loc, kt_in_loc, tt_loc, st_loc;   // built by locate_nodes (first nodal-field assembly)
+    // gradient lists through the K-near point sets and the Chebyshev nodes (built on the first vfd_grad)
+    DBuf<int> gl_ptr, gl_idx;           // vertex -> leaf-point entry * QB + slot (K near point sets)
+    DBuf<int> gn_ptr, gn_idx;           // vertex -> node entry * QB + slot (K, target, source nodes)
+    DBuf<double> gn_bary;               // barycentric coordinates of every node entry (QB each)
 };
 
 // ---------------------------------------------------------------------------
@@ -237,7 +260,9 @@ struct OpData {
     // the batch of one used by the batched (multi-RHS) low-precision apply / solve
     struct BatchData *self = nullptr;
     // adjoint gradient workspaces
-    DBuf<double> gr_uq, gr_lq, gr_hs, gr_h1, gr_pg;
+    DBuf<double> gr_uq, gr_lq, gr_hs, gr_h1, gr_pg;   // point values, point sensitivities, pair slots
+    DBuf<double> gr_cq, gr_hKs, gr_hKk;                // c_q; K-near leaf-point sensitivities
+    DBuf<double> gr_Gs, gr_Gk, gr_xU, gr_xL, gr_ct;    // node sensitivities; K far moments; target moments
     // apply workspace
     int ws_nrhs = 0;
     DBuf<double> xhat, yhat;           // nnode * k * ws_nrhs
@@ -324,6 +349,8 @@ void cheb_nodes_1d(int p, double lo, double hi, double *out);
 // ---------------------------------------------------------------------------
 // assemble.cu
 void launch_field_points(const MeshData &m, OpData &op, cudaStream_t st);
+// nearest-point location of every tree's Chebyshev nodes (mesh_setup.cpp)
+void locate_nodes(MeshData &m);
 void launch_singular_B(const MeshData &m, OpData &op, DBuf<double> &Lbuf, cudaStream_t st);
 void launch_gather_B(const MeshData &m, OpData &op, const DBuf<double> &Lbuf, cudaStream_t st);
 void launch_density(const MeshData &m, OpData &op, cudaStream_t st);
@@ -338,7 +365,7 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
                     bool lowp, cudaStream_t st, const int *skip);
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                  cudaStream_t st);
-void grad_exact(MeshData &m, OpData &op, const double *U, const double *Lam, int nrhs, int64_t ld, double *g_s,
+void grad_adjoint(MeshData &m, OpData &op, const double *U, const double *Lam, int nrhs, int64_t ld, double *g_s,
                 double *g_lk, cudaStream_t st);
 void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
                    cudaStream_t st);

@@ -10,7 +10,9 @@ lambda = 0.75, FP64), in the launch configuration bench.py times.
 * the FP64 CG solution's true residual, and the 64-RHS TF32 / BF16
   refinement's residuals through the FP64 operator;
 * the adjoint gradient's log-kappa shift identity sum_k g_k = -Lam^T A U
-  (holds at any size) on the exact-mode operator with P1 fields.
+  (holds at any size) on the benchmark H^2 operator with P1 fields, and the
+  autograd gradient of a solution misfit against central differences along
+  20 seeded directions (the differentiation workload at full size).
 """
 import math
 
@@ -117,24 +119,74 @@ def _fourier_values(f, x):
     return v
 
 
-def test_fullsize_gradient_shift_identity(disk):
-    m, s, k, prm, dof_o, N = disk
-    x = m.coords
+def _nodal(k, x):
     s_n = 0.25 + 0.5 * (0.5 + 0.5 * np.sin(2 * math.pi * x[:, 0]) * np.cos(2 * math.pi * x[:, 1]))
-    lk_n = _fourier_values(k, x)
-    mesh = _mesh(m, prm, 0.0)
+    return s_n, _fourier_values(k, x)
+
+
+def test_fullsize_gradient_shift_identity(disk):
+    """The benchmark's H^2 operator (rank 64) with P1 fields: the log-kappa
+    shift identity sum_k g_k = -Lam^T A U, two columns."""
+    m, s, k, prm, dof_o, N = disk
+    s_n, lk_n = _nodal(k, m.coords)
+    mesh = _mesh(m, prm, prm["lam"])
     op = vfd.vfd_assemble(mesh, synth.nodal_field(s_n), synth.nodal_field(lk_n), prm["s_bar"])
     g = torch.Generator(device="cuda").manual_seed(5)
-    U = torch.randn(mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
-    L = torch.randn(mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
+    U = torch.randn(2, mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
+    L = torch.randn(2, mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
     gs = torch.empty(m.n_vert, dtype=torch.float64, device="cuda")
     gk = torch.empty_like(gs)
     vfd.vfd_grad(op, U, L, gs, gk)
     AU = torch.empty_like(U)
     vfd.vfd_apply(op, U, AU)
     torch.cuda.synchronize()
-    ref = -(L @ AU).item()
+    ref = -(L * AU).sum().item()
     assert abs(gk.sum().item() - ref) <= 1e-10 * abs(ref)
+
+
+def test_fullsize_autograd_finite_differences(disk):
+    """The differentiation workload at full size: nodal s and log kappa on the
+    benchmark disk (H^2 operator, rank 64), loss = ||u - u_obs||^2 in the
+    lumped mass norm with u_obs the solution for a seeded reference s field;
+    the autograd gradient (adjoint solve + vfd_grad) against central
+    differences (h = 1e-6) of the loss through the solve along 20 seeded
+    directions in (s, log kappa) jointly."""
+    from paper_2302_02863_gb300 import inverse
+    from paper_2302_02863_gb300.autograd import solve as vsolve
+
+    m, s, k, prm, dof_o, N = disk
+    x = m.coords
+    s_n, lk_n = _nodal(k, x)
+    s_ref = np.clip(s_n + 0.05 * np.sin(3.0 * x[:, 0] + 1.0) * np.cos(2.0 * x[:, 1]), 0.1, 0.85)
+    mesh = _mesh(m, prm, prm["lam"])
+    dev = "cuda"
+    F = torch.zeros(mesh.n_dof, dtype=torch.float64, device=dev)
+    vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device=dev), F)
+    m_l = inverse.lumped_mass(mesh, m.n_vert, dev)
+    lk_t = torch.tensor(lk_n, device=dev)
+    rtol = 1e-12
+    with torch.no_grad():
+        u_obs = vsolve(torch.tensor(s_ref, device=dev), lk_t, F, mesh, prm["s_bar"], rtol)
+
+    def J(sv, lv):
+        e = vsolve(sv, lv, F, mesh, prm["s_bar"], rtol) - u_obs
+        return (m_l * e * e).sum()
+
+    s_t = torch.tensor(s_n, device=dev, requires_grad=True)
+    l_t = torch.tensor(lk_n, device=dev, requires_grad=True)
+    J(s_t, l_t).backward()
+    rng = np.random.default_rng(4)
+    h = 1e-6
+    worst = 0.0
+    with torch.no_grad():
+        for _ in range(20):
+            vs = torch.tensor(rng.standard_normal(m.n_vert), device=dev)
+            vl = torch.tensor(rng.standard_normal(m.n_vert), device=dev)
+            fd = (J(s_t + h * vs, l_t + h * vl) - J(s_t - h * vs, l_t - h * vl)).item() / (2 * h)
+            ad = ((s_t.grad * vs).sum() + (l_t.grad * vl).sum()).item()
+            worst = max(worst, abs(ad - fd) / abs(fd))
+    print(f"full-size autograd vs FD (20 directions, h = 1e-6): max rel gap {worst:.3e}")
+    assert worst < 1e-6, worst   # measured 1.4e-7
 
 
 def test_fullsize_h2_all_rows_vs_exact_mode(disk):
