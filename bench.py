@@ -72,6 +72,7 @@ def _args():
     p.add_argument("--no-batch24", action="store_true", help="skip the 24-mesh batched leg")
     p.add_argument("--no-graded", action="store_true", help="skip the graded-exterior leg")
     p.add_argument("--no-ball", action="store_true", help="skip the 3D ball leg")
+    p.add_argument("--no-grad", action="store_true", help="skip the gradient leg")
     p.add_argument("--mode", default="step", choices=["step", "apply", "solve"],
                    help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
     p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
@@ -395,6 +396,8 @@ def main():
                             torch)
     del mesh_x
 
+    grad = None if args.no_grad else gradient_leg(m, k, prm, torch, vfd)
+    prec_leg = precond_leg(mesh, s, k, prm, F, torch, vfd) if prec == vfd.VFD_FP64 else None
     graded = None if args.no_graded else graded_leg(torch, vfd)
     ball = None if args.no_ball else ball_leg(torch, vfd)
 
@@ -428,7 +431,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "rank16_operator": r16,
             "graded_exterior": graded, "ball_3d": ball, "batched_mixed_precision": batched,
-            "batch_24_meshes": batch24,
+            "batch_24_meshes": batch24, "gradient": grad, "preconditioner": prec_leg,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -796,6 +799,122 @@ def batch24_leg(torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
                      "relres_max": float(rel.max()), "solved_dof_rhs_per_s": ntot * nrhs / ts,
                      "sequential_per_mesh_solves_s": tseq}
         del batch, ops
+    return out
+
+
+def _vertex_fields(k, x):
+    """P1 (vertex) values of the benchmark fields: the disk's s(x) and its
+    Fourier log-kappa rows (input generation only)."""
+    import numpy as np
+
+    s_n = 0.25 + 0.5 * (0.5 + 0.5 * np.sin(2 * math.pi * x[:, 0]) * np.cos(2 * math.pi * x[:, 1]))
+    lk = np.full(len(x), float(k.c0))
+    for row in np.asarray(k.fourier, dtype=float).reshape(-1, 5):
+        lk += row[3] * np.cos(math.pi * (x @ row[:2]) + row[4])
+    return s_n, lk
+
+
+def gradient_leg(m, k, prm, torch, vfd, n_dir=4, h=1e-6, rtol=1e-12):
+    """The differentiation workload on the benchmark disk and operator (H^2,
+    rank 64) with P1 s and log kappa: loss ||u - u_obs||^2 in the lumped mass
+    norm, u_obs from a seeded reference s field.  Times vfd_grad alone and the
+    autograd forward (assembly + solve) and backward (adjoint solve + vfd_grad),
+    and checks the gradient against central differences along n_dir seeded
+    directions (the full 20-direction check is a GPU test)."""
+    import numpy as np
+
+    import synth
+    from paper_2302_02863_gb300 import inverse
+    from paper_2302_02863_gb300.autograd import solve as vsolve
+
+    x = m.coords
+    s_n, lk_n = _vertex_fields(k, x)
+    s_ref = np.clip(s_n + 0.05 * np.sin(3.0 * x[:, 0] + 1.0) * np.cos(2.0 * x[:, 1]), 0.1, 0.85)
+    mesh = vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"],
+                        lam=prm["lam"], rho_lambda=prm["lam"], tail_mode=prm["tail"], tail_R=prm["R"])
+    dev = "cuda"
+    t0 = time.perf_counter()
+    op = vfd.vfd_assemble(mesh, synth.nodal_field(s_n), synth.nodal_field(lk_n), prm["s_bar"])
+    torch.cuda.synchronize()
+    first_assemble_s = time.perf_counter() - t0          # includes the nodes' nearest-point location
+    F = torch.zeros(mesh.n_dof, dtype=torch.float64, device=dev)
+    vfd.vfd_load(mesh, torch.ones(m.n_vert, dtype=torch.float64, device=dev), F)
+    m_l = inverse.lumped_mass(mesh, m.n_vert, dev)
+    lk_t = torch.tensor(lk_n, device=dev)
+    with torch.no_grad():
+        u_obs = vsolve(torch.tensor(s_ref, device=dev), lk_t, F, mesh, prm["s_bar"], rtol)
+    # vfd_grad alone (U the solution, Lam a solve for a seeded right-hand side)
+    U = torch.zeros_like(F)
+    vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)
+    g = torch.Generator(device=dev).manual_seed(9)
+    Lam = torch.randn(mesh.n_dof, dtype=torch.float64, device=dev, generator=g)
+    gs = torch.empty(m.n_vert, dtype=torch.float64, device=dev)
+    gk = torch.empty_like(gs)
+    stream = torch.cuda.current_stream()
+    vfd.vfd_grad(op, U, Lam, gs, gk)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(3):
+        vfd.vfd_grad(op, U, Lam, gs, gk)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    grad_ms = ev[0].elapsed_time(ev[1]) / 3
+
+    def J(sv, lv):
+        e = vsolve(sv, lv, F, mesh, prm["s_bar"], rtol) - u_obs
+        return (m_l * e * e).sum()
+
+    s_t = torch.tensor(s_n, device=dev, requires_grad=True)
+    l_t = torch.tensor(lk_n, device=dev, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = J(s_t, l_t)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    rng = np.random.default_rng(4)
+    worst = 0.0
+    with torch.no_grad():
+        for _ in range(n_dir):
+            vs = torch.tensor(rng.standard_normal(m.n_vert), device=dev)
+            vl = torch.tensor(rng.standard_normal(m.n_vert), device=dev)
+            fd = (J(s_t + h * vs, l_t + h * vl) - J(s_t - h * vs, l_t - h * vl)).item() / (2 * h)
+            ad = ((s_t.grad * vs).sum() + (l_t.grad * vl).sum()).item()
+            worst = max(worst, abs(ad - fd) / abs(fd))
+    return {"workload": "benchmark disk, P1 s and log kappa, H^2 rank 64", "n_vert": m.n_vert,
+            "n_dof": mesh.n_dof, "vfd_grad_ms": round(grad_ms, 3), "forward_s": round(t1 - t0, 4),
+            "backward_s": round(t2 - t1, 4), "first_assemble_s_incl_node_location": round(first_assemble_s, 3),
+            "fd_directions": n_dir, "fd_h": h, "fd_max_rel_gap": worst, "loss": loss.item()}
+
+
+def precond_leg(mesh, s, k, prm, F, torch, vfd, rtol=1e-10):
+    """Plain CG against the two-level preconditioned CG (leaf blocks + the
+    leaf-constant coarse space) on the benchmark operator, one right-hand side."""
+    out = {}
+    op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"])
+    for name in ("cg", "pcg"):
+        if name == "pcg":
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vfd.vfd_precondition(op)
+            torch.cuda.synchronize()
+            out["setup_s"] = round(time.perf_counter() - t0, 4)
+        U = torch.zeros_like(F)
+        vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)        # warm (graph capture)
+        U.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, rel = vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)
+        torch.cuda.synchronize()
+        out[name] = {"iters": int(it[0]), "solve_ms": round(1000 * (time.perf_counter() - t0), 3),
+                     "relres": float(rel[0])}
+        if name == "cg":
+            U_cg = U.clone()
+        else:
+            out["solution_rel_diff"] = (torch.linalg.norm(U - U_cg) / torch.linalg.norm(U_cg)).item()
+    out["rtol"] = rtol
     return out
 
 

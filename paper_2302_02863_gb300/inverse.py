@@ -9,7 +9,7 @@ projected gradient descent with Armijo backtracking; s is kept in
 [s_min, s_max] inside the quadrature bound s_bar of Sec. 4.  The paper stops at
 the forward problem and names the inverse problem as the next step (Sec. 8);
 every solve and gradient runs in libvfd.so through autograd.solve (adjoint
-solve + vfd_grad), so the mesh must allow P1 fields (lambda = rho_lambda = 0).
+solve + vfd_grad, exact for the H^2 operator the solve uses).
 """
 from __future__ import annotations
 
