@@ -259,19 +259,27 @@ vfd_status vfd_apply_noalloc(vfd_op_t op, const double *X, double *Y, int64_t nr
 vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int64_t ld, double rtol,
                      int max_it, int *iters, double *relres, void *stream);
 
-/* Preconditioner of the FP64 CG of vfd_solve (the paper solves with plain
+/* Preconditioner of the CG solves of vfd_solve (the paper solves with plain
  * CG, Sec. 7, and names a multilevel preconditioner as the next step,
  * Sec. 8).  kind VFD_PREC_TWO_LEVEL: additive two-level preconditioner,
  * M^-1 = sum over the leaves of the cluster tree of exact solves with the
- * leaf's diagonal block of A, plus a coarse solve on the leaf-wise constant
- * functions (A_c = R A R^T, R the leaf indicators); both parts are SPD, so
- * vfd_solve runs preconditioned CG (stopping test unchanged: the residual
- * of A).  Setup: the diagonal blocks and A_c (formed by applying A to the
- * leaf indicators) are inverted once, on the host, in FP64; blocks until
- * done.  VFD_PREC_NONE switches back to plain CG.  Only VFD_FP64 operators;
- * at most 2048 leaves.  Errors: VFD_EINVAL (unknown kind, a block that is
- * not positive definite), VFD_EUNSUPPORTED, VFD_ECUDA. */
-enum { VFD_PREC_NONE = 0, VFD_PREC_TWO_LEVEL = 1 };
+ * leaf's diagonal block of A (near panel block plus the B + M entries inside
+ * the leaf), plus a coarse solve on the functions constant on the clusters of
+ * one tree level (the deepest with at most 512 clusters; A_c = R A R^T, R the
+ * cluster indicators); VFD_PREC_BLOCK_JACOBI: the leaf blocks only.  Both
+ * parts are SPD, so the solves run preconditioned CG (stopping test
+ * unchanged: the residual of A).  Used by the FP64 CG of VFD_FP64 operators
+ * and by the batched mixed-precision solve (nrhs > 1 on a VFD_FP32 or
+ * VFD_BF16 operator, or vfd_batch_solve when every operator of the batch is
+ * preconditioned: FP32 copies of the inverses); not by the one-column
+ * refinement of low-precision operators.  Setup, FP64 from the operator's
+ * FP64 parts: the leaf blocks inverted on the device (Cholesky in shared
+ * memory; leaves above 96 DoFs on the host), A_c formed by applying A to the
+ * cluster indicators and inverted on the host; blocks until done.
+ * VFD_PREC_NONE switches back to plain CG.  The batched solve needs leaves of
+ * at most 128 DoFs.  Errors: VFD_EINVAL (unknown kind, a block that is not
+ * positive definite), VFD_ECUDA. */
+enum { VFD_PREC_NONE = 0, VFD_PREC_TWO_LEVEL = 1, VFD_PREC_BLOCK_JACOBI = 2 };
 vfd_status vfd_precondition(vfd_op_t op, int kind, void *stream);
 
 /* P1 load F = M0 f (exact P1 mass matrix of the interior cells times the

@@ -36,7 +36,8 @@ constexpr int BCHUNK = 8;
 constexpr int BT = 1024;   // threads of the reduction kernels
 // per (mesh, column) scalars, arrays of nmesh * Rp floats: rr, pq, alpha, beta,
 // tol2, and rp = r.p (equal to rr except right after a reliable update)
-enum { C_RR = 0, C_PQ = 1, C_AL = 2, C_BE = 3, C_TOL = 4, C_RP = 5, C_N = 6 };
+// and rz = r.z of the preconditioned iteration
+enum { C_RR = 0, C_PQ = 1, C_AL = 2, C_BE = 3, C_TOL = 4, C_RP = 5, C_RZ = 6, C_N = 7 };
 // flags (int): [0] all done, [1] iterations, [2] max_it, [3] mesh-finish counter,
 // then per mesh: a block counter (FL_CNT + m), its live-column count
 // (FL_CNT + nmesh + m) and its done flag (FL_CNT + 2 nmesh + m: every column
@@ -171,8 +172,9 @@ __global__ void __launch_bounds__(BT) k_b_pq(Seg S, const float *__restrict__ p,
 }
 
 // x += alpha p; r -= alpha q; rr_new; beta; convergence of every column
+// (pcg: beta and r.p come from r.z after the preconditioner, k_bp_zr)
 __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float *__restrict__ r,
-                                             const float *__restrict__ p, const float *__restrict__ q)
+                                             const float *__restrict__ p, const float *__restrict__ q, int pcg)
 {
     if (S.flag[BF_DONE]) return;
     __shared__ int live;
@@ -192,11 +194,13 @@ __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float
         [&](int mm, int c, float s) {
             const float rr = scal(S, C_RR, mm, c);
             if (scal(S, C_AL, mm, c) != 0.f) {
-                scal(S, C_BE, mm, c) = rr > 0.f ? s / rr : 0.f;
+                if (!pcg) {
+                    scal(S, C_BE, mm, c) = rr > 0.f ? s / rr : 0.f;
+                    scal(S, C_RP, mm, c) = s;   // r_new . p_old = 0, so r_new . p_new = rr_new
+                }
                 scal(S, C_RR, mm, c) = s;
-                scal(S, C_RP, mm, c) = s;   // r_new . p_old = 0, so r_new . p_new = rr_new
                 if (s > scal(S, C_TOL, mm, c)) atomicAdd(&live, 1);
-            } else {
+            } else if (!pcg) {
                 scal(S, C_BE, mm, c) = 0.f;   // p = r next
                 scal(S, C_RP, mm, c) = rr;
             }
@@ -221,12 +225,14 @@ __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float
     if (tot == 0 || it >= S.flag[BF_MAX]) S.flag[BF_DONE] = 1;
 }
 
-// p = r + beta p (same block decomposition as the reductions)
-__global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, float *__restrict__ p)
+// p = r + beta p (same block decomposition as the reductions); r is z in the
+// preconditioned iteration; upd (non-null): only the meshes just updated
+__global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, float *__restrict__ p,
+                                            const int *__restrict__ upd)
 {
     if (S.flag[BF_DONE]) return;
     const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
-    if (S.mdone()[m]) return;
+    if (upd ? !upd[m] : S.mdone()[m]) return;
     const int nb = S.mesh[4 * m + 1], N = S.mesh[4 * m + 2], r0 = S.mesh[4 * m + 3];
     const int Rp = S.Rp;
     const size_t base = (size_t)r0 * Rp, n = (size_t)N * Rp;
@@ -243,10 +249,12 @@ __global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, 
 // to the new scale and to beta from the true residual norm), or p = b where
 // gamma < 0 (restart); rr, the thresholds and the done flags are recomputed.
 // Meshes with upd[m] == 0 are left exactly as they are.
+// (pcg: p keeps beta_old p_old = p - z_old; the preconditioner and k_bp_zr then
+// form the new direction)
 __global__ void __launch_bounds__(BT) k_b_replace(Seg S, const float *__restrict__ b, float *__restrict__ x,
                                                   float *__restrict__ r, float *__restrict__ p,
                                                   const float *__restrict__ gamma, const float *__restrict__ tol2,
-                                                  const int *__restrict__ upd)
+                                                  const int *__restrict__ upd, const float *__restrict__ z)
 {
     __shared__ int live;
     if (threadIdx.x == 0) live = 0;
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(BT) k_b_replace(Seg S, const float *__restrict
         [&](size_t t, int mm, int c) {
             if (!upd[mm]) return 0.f;
             const float v = b[t], g = gamma[mm * S.Rp + c];
-            p[t] = g < 0.f ? v : fmaf(g, p[t] - r[t], v);
+            p[t] = z ? p[t] - z[t] : g < 0.f ? v : fmaf(g, p[t] - r[t], v);
             x[t] = 0.f;
             r[t] = v;
             return v * v;
@@ -518,6 +526,140 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// preconditioner of the batched iteration (the two-level preconditioner of
+// precond.cu in FP32 on the interleaved vectors): z = Binv_a r_a per leaf,
+// leaf sums rl, zc = Cinv rc per mesh (rc = the sums over each coarse
+// cluster's leaves), z += zc[cluster of the row]
+// ---------------------------------------------------------------------------
+constexpr int PC_TILE = 64;   // columns per pass of the preconditioner kernels
+constexpr int PC_CROWS = 16;  // coarse rows per CTA
+
+// leaf item: mesh, first row (global), rows, block stride, global leaf index
+__global__ void __launch_bounds__(256) k_bp_local(Seg S, const int *__restrict__ items,
+                                                  const long long *__restrict__ boff, const float *__restrict__ blk,
+                                                  const float *__restrict__ r, float *__restrict__ z,
+                                                  float *__restrict__ rl, const int *__restrict__ upd)
+{
+    extern __shared__ float smf[];
+    if (S.flag[BF_DONE]) return;
+    const int *it = items + 5 * blockIdx.x;
+    const int m = it[0], row0 = it[1], na = it[2], mb = it[3], gl = it[4];
+    if (upd ? !upd[m] : S.mdone()[m]) return;
+    const int Rp = S.Rp;
+    float *B = smf, *Rs = smf + (size_t)mb * mb;
+    const float *g = blk + boff[blockIdx.x];
+    for (int t = threadIdx.x; t < na * na; t += blockDim.x) B[(t / na) * mb + t % na] = g[(t / na) * mb + t % na];
+    const int c = threadIdx.x % PC_TILE, grp = threadIdx.x / PC_TILE, ngrp = blockDim.x / PC_TILE;
+    for (int c0 = 0; c0 < Rp; c0 += PC_TILE) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < na * PC_TILE; t += blockDim.x)
+            Rs[t] = r[(size_t)(row0 + t / PC_TILE) * Rp + c0 + t % PC_TILE];
+        __syncthreads();
+        // rows grp, grp + ngrp, ... four at a time; Binv symmetric, B[i][j] the
+        // same address across the warp (broadcast)
+        for (int i0 = grp; i0 < na; i0 += 4 * ngrp) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int j = 0; j < na; ++j) {
+                const float rv = Rs[j * PC_TILE + c];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * ngrp;
+                    if (i < na) acc[k] = fmaf(B[i * mb + j], rv, acc[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k * ngrp;
+                if (i < na) z[(size_t)(row0 + i) * Rp + c0 + c] = acc[k];
+            }
+        }
+        if (grp == 0) {
+            float sum = 0.f;
+            for (int i = 0; i < na; ++i) sum += Rs[i * PC_TILE + c];
+            rl[(size_t)gl * Rp + c0 + c] = sum;
+        }
+    }
+}
+
+// coarse tile: mesh, first coarse row; per mesh (pmesh): clusters nc, leaves
+// per cluster span, global index of its first leaf and of its first cluster
+__global__ void __launch_bounds__(256) k_bp_coarse(Seg S, const int *__restrict__ tiles, const int *__restrict__ pmesh,
+                                                   const long long *__restrict__ coff,
+                                                   const float *__restrict__ Cinv, const float *__restrict__ rl,
+                                                   float *__restrict__ zc, const int *__restrict__ upd)
+{
+    if (S.flag[BF_DONE]) return;
+    const int m = tiles[2 * blockIdx.x], a0 = tiles[2 * blockIdx.x + 1];
+    if (upd ? !upd[m] : S.mdone()[m]) return;
+    const int nc = pmesh[4 * m], span = pmesh[4 * m + 1], gl0 = pmesh[4 * m + 2], gc0 = pmesh[4 * m + 3];
+    const int Rp = S.Rp;
+    const float *C = Cinv + coff[m];
+    const int c = threadIdx.x % PC_TILE, grp = threadIdx.x / PC_TILE, ngrp = blockDim.x / PC_TILE;
+    constexpr int K = PC_CROWS / 4;
+    for (int c0 = 0; c0 < Rp; c0 += PC_TILE) {
+        float acc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = 0.f;
+        for (int b = 0; b < nc; ++b) {
+            float rc = 0.f;
+            for (int q = 0; q < span; ++q) rc += rl[(size_t)(gl0 + b * span + q) * Rp + c0 + c];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int a = a0 + grp + k * ngrp;
+                if (a < nc) acc[k] = fmaf(C[(size_t)a * nc + b], rc, acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int a = a0 + grp + k * ngrp;
+            if (a < nc) zc[(size_t)(gc0 + a) * Rp + c0 + c] = acc[k];
+        }
+    }
+}
+
+// z += zc[cluster of the row] (rowclu -1: no coarse space), rz = r.z, and
+// the CG scalars:
+//   mode 0 (start):  rz, r.p = rz, beta = 0 (then p = z)
+//   mode 1 (step):   beta = rz_new / rz (0 for a column that did not move), rz, r.p = rz
+//   mode 2 (reliable update of the meshes with upd): beta = g0 rz_new / rz_old
+//            (g0 <= 0: restart from p = z), rz; r.p follows from k_b_rp
+__global__ void __launch_bounds__(BT) k_bp_zr(Seg S, const int *__restrict__ rowclu, const float *__restrict__ zc,
+                                              const float *__restrict__ r, float *__restrict__ z, int mode,
+                                              const float *__restrict__ g0, const int *__restrict__ upd)
+{
+    if (S.flag[BF_DONE]) return;
+    seg_reduce<true>(
+        S,
+        [&](size_t t, int mm, int c) {
+            if (upd && !upd[mm]) return 0.f;
+            float zv = z[t];
+            if (zc) {
+                const int cl = rowclu[t / S.Rp];
+                if (cl >= 0) zv += zc[(size_t)cl * S.Rp + c];
+                z[t] = zv;
+            }
+            return r[t] * zv;
+        },
+        [&](int mm, int c, float s) {
+            if (upd && !upd[mm]) return;
+            const float rz = scal(S, C_RZ, mm, c);
+            if (mode == 0) {
+                scal(S, C_RP, mm, c) = s;
+                scal(S, C_BE, mm, c) = 0.f;
+            } else if (mode == 1) {
+                const bool moved = scal(S, C_AL, mm, c) != 0.f;
+                scal(S, C_BE, mm, c) = moved && rz > 0.f ? s / rz : 0.f;
+                scal(S, C_RP, mm, c) = s;   // r_new . p_old = 0, so r_new . p_new = r_new . z_new
+            } else {
+                const float g = g0[(size_t)mm * S.Rp + c];
+                scal(S, C_BE, mm, c) = g > 0.f && rz > 0.f ? g * s / rz : 0.f;
+            }
+            scal(S, C_RZ, mm, c) = s;
+        });
+}
+
 }  // namespace
 
 void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
@@ -579,6 +721,107 @@ static Seg make_seg(BatchData &b, int Rp)
     return S;
 }
 
+// preconditioner tables of the batch: built when every operator carries a
+// preconditioner (vfd_precondition), rebuilt when one of them changed
+static void ensure_bprec(BatchData &b, int Rp)
+{
+    int npre = 0;
+    for (OpData *op : b.ops) npre += op->prec_kind != 0;
+    VFD_REQUIRE(npre == 0 || npre == b.nmesh, VFD_EINVAL,
+                "batched solve: precondition every operator of the batch or none");
+    const bool want = npre == b.nmesh;
+    std::vector<long long> key;
+    if (want) {
+        key.push_back(Rp);
+        for (OpData *op : b.ops) key.push_back(op->prec_version);
+    }
+    if (want == b.pcg && (!want || key == b.pc_key)) return;
+    release_bgraph(b);   // the captured chunk differs
+    b.pcg = want;
+    b.pc_key = key;
+    if (!want) return;
+    std::vector<int> items, pmesh(4 * (size_t)b.nmesh), tiles, rowclu((size_t)b.ntot, -1);
+    std::vector<long long> boff, coff(b.nmesh);
+    long long nblk = 0, ncoarse = 0;
+    int gleaf = 0, gclu = 0, mbmax = 0, any_coarse = 0;
+    for (int i = 0; i < b.nmesh; ++i) {
+        const OpData &op = *b.ops[i];
+        const MeshData &m = *op.m;
+        const int nleaf = m.kt.nleaf, fl = m.kt.first_leaf(), mb = op.prec_mb, nc = op.prec_nc;
+        VFD_REQUIRE(mb <= 128, VFD_EUNSUPPORTED, "batched preconditioned solve: leaves of at most 128 DoFs");
+        mbmax = std::max(mbmax, mb);
+        for (int a = 0; a < nleaf; ++a) {
+            items.push_back(i);
+            items.push_back((int)b.xoff[i] + m.kt.begin[fl + a]);
+            items.push_back(m.kt.end[fl + a] - m.kt.begin[fl + a]);
+            items.push_back(mb);
+            items.push_back(gleaf + a);
+            boff.push_back(nblk + (long long)a * mb * mb);
+        }
+        pmesh[4 * i] = nc;
+        pmesh[4 * i + 1] = op.prec_span;
+        pmesh[4 * i + 2] = gleaf;
+        pmesh[4 * i + 3] = gclu;
+        coff[i] = ncoarse;
+        if (nc > 0) {
+            any_coarse = 1;
+            for (int a0 = 0; a0 < nc; a0 += PC_CROWS) {
+                tiles.push_back(i);
+                tiles.push_back(a0);
+            }
+            for (int c = 0; c < nc; ++c) {
+                const int r0 = m.kt.begin[fl + c * op.prec_span];
+                const int r1 = c + 1 < nc ? m.kt.begin[fl + (c + 1) * op.prec_span] : m.N;
+                for (int row = r0; row < r1; ++row) rowclu[(size_t)b.xoff[i] + row] = gclu + c;
+            }
+        }
+        nblk += (long long)nleaf * mb * mb;
+        ncoarse += (long long)nc * nc;
+        gleaf += nleaf;
+        gclu += nc;
+    }
+    b.pc_blk.alloc(nblk);
+    b.pc_coarse.alloc(std::max<long long>(ncoarse, 1));
+    for (int i = 0; i < b.nmesh; ++i) {
+        const OpData &op = *b.ops[i];
+        long long off = 0;
+        for (int j = 0; j < i; ++j) off += (long long)b.ops[j]->m->kt.nleaf * b.ops[j]->prec_mb * b.ops[j]->prec_mb;
+        VFD_CUDA(cudaMemcpy(b.pc_blk.p + off, op.prec_blk32.p, op.prec_blk32.bytes(), cudaMemcpyDeviceToDevice));
+        if (op.prec_nc > 0)
+            VFD_CUDA(cudaMemcpy(b.pc_coarse.p + coff[i], op.prec_coarse32.p, op.prec_coarse32.bytes(),
+                                cudaMemcpyDeviceToDevice));
+    }
+    b.pc_items.upload(items);
+    b.pc_boff.upload(boff);
+    b.pc_pmesh.upload(pmesh);
+    b.pc_coff.upload(coff);
+    b.pc_ctiles.upload(tiles.empty() ? std::vector<int>{0, 0} : tiles);
+    b.pc_rowclu.upload(rowclu);
+    b.n_pc_items = (int)(items.size() / 5);
+    b.n_pc_ctiles = (int)(tiles.size() / 2);
+    b.pc_mbmax = mbmax;
+    b.pc_any_coarse = any_coarse;
+    b.z.alloc((size_t)b.ntot * Rp);
+    b.pc_rl.alloc((size_t)gleaf * Rp);
+    b.pc_zc.alloc((size_t)std::max(gclu, 1) * Rp);
+    const size_t shm = ((size_t)mbmax * mbmax + (size_t)mbmax * PC_TILE) * sizeof(float);
+    VFD_CUDA(cudaFuncSetAttribute(k_bp_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+}
+
+// z = M^-1 r (all meshes, or the meshes with upd), then the scalars of mode (k_bp_zr)
+static void bprec_apply(BatchData &b, const Seg &S, int mode, const float *g0, const int *upd, cudaStream_t st)
+{
+    const size_t shm = ((size_t)b.pc_mbmax * b.pc_mbmax + (size_t)b.pc_mbmax * PC_TILE) * sizeof(float);
+    k_bp_local<<<b.n_pc_items, 256, shm, st>>>(S, b.pc_items.p, b.pc_boff.p, b.pc_blk.p, b.r.p, b.z.p, b.pc_rl.p,
+                                               upd);
+    if (b.pc_any_coarse)
+        k_bp_coarse<<<b.n_pc_ctiles, 256, 0, st>>>(S, b.pc_ctiles.p, b.pc_pmesh.p, b.pc_coff.p, b.pc_coarse.p,
+                                                   b.pc_rl.p, b.pc_zc.p, upd);
+    k_bp_zr<<<b.nred, BT, 0, st>>>(S, b.pc_rowclu.p, b.pc_any_coarse ? b.pc_zc.p : nullptr, b.r.p, b.z.p, mode, g0,
+                                   upd);
+    VFD_CUDA(cudaGetLastError());
+}
+
 // capture one chunk of BCHUNK low-precision CG iterations (apply, p.q, x/r
 // update, p update) as a graph; the eager apply first builds the apply's
 // descriptors and workspaces outside the capture
@@ -596,7 +839,7 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
         VFD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         VFD_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         VFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_iter, BT, 0));
-        b.fused = coop && Rp <= BT && b.nred <= per * nsm;
+        b.fused = coop && Rp <= BT && b.nred <= per * nsm && !b.pcg;
         b.p16_target = batch_tc_x(b) ;
         if (b.fused && !b.gbar.p) {
             b.gbar.alloc(2);
@@ -622,10 +865,16 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
                 int *err = b.tc_err.p;
                 void *args[] = {&Sv, &red2, &xv, &rv, &pv, &qv, &p16, &gb, &wns, &err};
                 VFD_CUDA(cudaLaunchCooperativeKernel((const void *)k_b_iter, b.nred, BT, args, 0, cs));
+            } else if (b.pcg) {
+                // preconditioned: p.q, x/r update, z = M^-1 r with r.z and beta, p = z + beta p
+                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
+                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, 1);
+                bprec_apply(b, S, 1, nullptr, nullptr, cs);
+                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.z.p, b.p.p, nullptr);
             } else {
                 k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
-                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p);
-                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p);
+                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, 0);
+                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p, nullptr);
             }
         }
     } catch (...) {
@@ -650,6 +899,7 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
     const int Rp = ((R + 63) / 64) * 64, nm = b.nmesh;
     const size_t nc = (size_t)nm * Rp, nr = (size_t)nm * R;
     ensure_solve(b, Rp);
+    ensure_bprec(b, Rp);
     std::vector<DBuf<double>> AU(nm), res(nm);
     DBuf<double> n2, f2, scale;
     DBuf<float> gamma_d, tol2_d;
@@ -704,8 +954,12 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
                 const bool iterating = !mesh_was_done && tol2[k] > 0.f && rr[k] > tol2[k];
                 const bool keep = s_new > 0.0 && sc[h] > 0.0 && iterating && rec < 2.0 * s_new &&
                                   s_new < 2.0 * rec && rel <= rel_last[h];
-                // p_new = r_true + (|r_true|^2 / |r_rec|^2) beta_old p_old, in the new scale
-                gamma[k] = s_new <= 0.0 ? 0.f : keep ? (float)(s_new / (sc[h] * (double)rr[k])) : -1.f;
+                // p_new = r_true + (|r_true|^2 / |r_rec|^2) beta_old p_old, in the new scale;
+                // preconditioned: p_new = z_true + (rz_true / rz_rec) beta_old p_old, the
+                // factor s_new / s_old here and the r.z ratio on the device (k_bp_zr)
+                gamma[k] = s_new <= 0.0 ? 0.f
+                           : keep       ? (float)(b.pcg ? s_new / sc[h] : s_new / (sc[h] * (double)rr[k]))
+                                        : -1.f;
                 // inner target in the scaled units: half of rtol (room for the recursive residual's drift)
                 const double tgt = s_new > 0.0 ? 0.5 * rtol * std::sqrt(hf[h]) / s_new : 0.0;
                 tol2[k] = (float)(tgt * tgt);
@@ -757,6 +1011,10 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
     residual_to_inner();
     k_b_init<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, tol2_d.p, std::max(1, max_it));
     VFD_CUDA(cudaGetLastError());
+    if (b.pcg) {   // z = M^-1 r, r.p = r.z, p = z
+        bprec_apply(b, S, 0, nullptr, nullptr, st);
+        k_b_p<<<b.nred, BT, 0, st>>>(S, b.z.p, b.p.p, nullptr);
+    }
     capture_bcg(b, Rp, st);
     // the captured apply reads p in BF16 from the fused kernel: provide the first one
     if (b.fused && b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
@@ -794,7 +1052,12 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
         }
         if (out_of_its || breakdown) break;
         residual_to_inner();
-        k_b_replace<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, gamma_d.p, tol2_d.p, upd_d.p);
+        k_b_replace<<<b.nred, BT, 0, st>>>(S, b.b.p, b.x.p, b.r.p, b.p.p, gamma_d.p, tol2_d.p, upd_d.p,
+                                           b.pcg ? b.z.p : nullptr);
+        if (b.pcg) {   // z = M^-1 r_true, beta from r.z, p = z + beta (beta_old p_old)
+            bprec_apply(b, S, 2, gamma_d.p, upd_d.p, st);
+            k_b_p<<<b.nred, BT, 0, st>>>(S, b.z.p, b.p.p, upd_d.p);
+        }
         k_b_rp<<<b.nred, BT, 0, st>>>(S, b.r.p, b.p.p, upd_d.p);
         VFD_CUDA(cudaGetLastError());
         if (b.fused && b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);

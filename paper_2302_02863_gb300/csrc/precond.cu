@@ -1,4 +1,4 @@
-// Two-level preconditioner for the CG solve of A U = F (Sec. 7 solves with
+// Two-level preconditioner for the CG solves of A U = F (Sec. 7 solves with
 // plain CG; a multilevel preconditioner is the paper's stated next step,
 // Sec. 8):
 //
@@ -7,16 +7,20 @@
 // an additive combination of exact solves with the diagonal block A_aa of
 // every leaf of the cluster tree (its DoFs, A's rows and columns of that
 // leaf: near panel block (a, a) plus the B + M entries inside the leaf) and a
-// coarse solve on the space of leaf-wise constant functions (R the leaf
-// indicator restriction, A_c = R A R^T, one row and column per leaf).  Both
-// factors are symmetric positive definite, so M is too and CG applies.
+// coarse solve on the space of functions constant on the clusters of one tree
+// level (R the cluster indicator restriction, A_c = R A R^T; the level is the
+// deepest one with at most PREC_MAX_COARSE clusters, the leaves themselves on
+// meshes of up to that many leaves).  Both parts are symmetric positive
+// definite, so M is too and CG applies.  Kind VFD_PREC_BLOCK_JACOBI keeps the
+// leaf blocks only.
 //
 // Setup (once per operator, vfd_precondition): the diagonal blocks are
-// gathered on the device and inverted on the host (Cholesky, FP64); A_c is
-// formed on the device by applying A to the leaf indicator vectors and
-// summing rows per leaf, and inverted on the host.  Apply (every PCG
-// iteration): one kernel per leaf for the local solves and the restriction,
-// one for the coarse product, one for the prolongation.
+// gathered and inverted on the device (one CTA per leaf: Cholesky and the
+// triangular inverses in shared memory, FP64); A_c is formed by applying A to
+// the cluster indicators and summing rows per cluster, and inverted on the
+// host.  FP32 copies of both serve the batched mixed-precision solve.  Apply
+// (every PCG iteration, FP64 solve): one kernel per leaf for the local solves
+// and the leaf sums, one for the coarse product, one for the prolongation.
 #include <cmath>
 #include <vector>
 
@@ -28,6 +32,9 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
                     bool lowp, cudaStream_t st, const int *skip);
 
 namespace {
+
+constexpr int PREC_MAX_COARSE = 512;
+constexpr int PREC_SMEM_BLK = 96;   // largest leaf whose block is inverted in shared memory
 
 // dense diagonal block of leaf a (na x na, row stride mb) from the near panel
 // block (a, a) and the B + M rows of the leaf's DoFs
@@ -58,37 +65,93 @@ __global__ void k_diag_blocks(int fl, int mb, const int *__restrict__ kb, const 
         }
 }
 
-// leaf indicator columns: X[c][i] = 1 if DoF i lies in leaf c0 + c
-__global__ void k_indicators(int N, int ncol, int c0, const int *__restrict__ vleaf, double *__restrict__ X)
+// in-place inverse of every leaf's SPD block (mb x mb, symmetric) in shared
+// memory: right-looking Cholesky A = L L^T, Li = L^-1 column by column, then
+// A^-1 = Li^T Li; err set when a pivot is not positive.  Also writes the FP32 copy.
+__global__ void __launch_bounds__(256) k_blk_inv(int mb, double *__restrict__ blk, float *__restrict__ blk32,
+                                                 int *err)
+{
+    extern __shared__ double sm[];
+    double *A = sm;                       // mb x mb: L in the lower triangle
+    double *Li = sm + (size_t)mb * mb;    // mb x mb
+    __shared__ int bad;
+    double *g = blk + (size_t)blockIdx.x * mb * mb;
+    for (int t = threadIdx.x; t < mb * mb; t += blockDim.x) {
+        A[t] = g[t];
+        Li[t] = 0.0;
+    }
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < mb; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = A[j * mb + j];
+            if (!(d > 0.0)) bad = 1;
+            A[j * mb + j] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        const double ljj = A[j * mb + j];
+        for (int i = j + 1 + threadIdx.x; i < mb; i += blockDim.x) A[i * mb + j] /= ljj;
+        __syncthreads();
+        // trailing update of the lower triangle: A[i][k] -= L[i][j] L[k][j], j < k <= i
+        const int n = mb - j - 1;
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = j + 1 + t / n, k = j + 1 + t % n;
+            if (k <= i) A[i * mb + k] -= A[i * mb + j] * A[k * mb + j];
+        }
+        __syncthreads();
+    }
+    // Li = L^-1: thread per column c, forward substitution
+    for (int c = threadIdx.x; c < mb; c += blockDim.x) {
+        Li[c * mb + c] = 1.0 / A[c * mb + c];
+        for (int i = c + 1; i < mb; ++i) {
+            double v = 0.0;
+            for (int k = c; k < i; ++k) v -= A[i * mb + k] * Li[k * mb + c];
+            Li[i * mb + c] = v / A[i * mb + i];
+        }
+    }
+    __syncthreads();
+    // A^-1[i][j] = sum_{k >= max(i,j)} Li[k][i] Li[k][j]
+    for (int t = threadIdx.x; t < mb * mb; t += blockDim.x) {
+        const int i = t / mb, j = t % mb;
+        double v = 0.0;
+        for (int k = max(i, j); k < mb; ++k) v += Li[k * mb + i] * Li[k * mb + j];
+        g[t] = v;
+        blk32[(size_t)blockIdx.x * mb * mb + t] = (float)v;
+    }
+    if (threadIdx.x == 0 && bad) atomicOr(err, 1);
+}
+
+// cluster indicator columns: X[c][i] = 1 if DoF i lies in cluster c0 + c
+__global__ void k_indicators(int N, int ncol, int c0, const int *__restrict__ cidx, double *__restrict__ X)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)N * ncol) return;
     const int c = (int)(t / N), i = (int)(t % N);
-    X[t] = vleaf[i] == c0 + c ? 1.0 : 0.0;
+    X[t] = cidx[i] == c0 + c ? 1.0 : 0.0;
 }
 
-// Ac[a][c0 + c] = sum over the DoFs of leaf a of Y[c][i]
-__global__ void k_leaf_sums(int N, int nleaf, int ncol, int c0, int fl, const int *__restrict__ kb,
-                            const int *__restrict__ ke, const double *__restrict__ Y, double *__restrict__ Ac)
+// Ac[a][c0 + c] = sum over the DoFs of cluster a (rows [cb[a], cb[a+1])) of Y[c][i]
+__global__ void k_cluster_sums(int N, int nc, int ncol, int c0, const int *__restrict__ cb,
+                               const double *__restrict__ Y, double *__restrict__ Ac)
 {
     const int a = blockIdx.x, c = blockIdx.y;
     __shared__ double sh[128];
     double v = 0.0;
-    for (int i = kb[fl + a] + threadIdx.x; i < ke[fl + a]; i += blockDim.x) v += Y[(size_t)c * N + i];
+    for (int i = cb[a] + threadIdx.x; i < cb[a + 1]; i += blockDim.x) v += Y[(size_t)c * N + i];
     sh[threadIdx.x] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int q = 0; q < (int)blockDim.x; ++q) s += sh[q];
-        Ac[(size_t)a * nleaf + c0 + c] = s;
+        Ac[(size_t)a * nc + c0 + c] = s;
     }
 }
 
-// local solves z_a = Binv_a r_a and the restriction rc[a] = sum_{i in a} r_i
+// local solves z_a = Binv_a r_a and the leaf sums rl[a] = sum_{i in a} r_i
 __global__ void __launch_bounds__(128) k_prec_local(int fl, int mb, const int *__restrict__ kb,
                                                     const int *__restrict__ ke, const double *__restrict__ Binv,
                                                     const double *__restrict__ r, double *__restrict__ z,
-                                                    double *__restrict__ rc, const int *skip)
+                                                    double *__restrict__ rl, const int *skip)
 {
     extern __shared__ double rs[];
     __shared__ double red[128];
@@ -104,7 +167,7 @@ __global__ void __launch_bounds__(128) k_prec_local(int fl, int mb, const int *_
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int q = 0; q < (int)blockDim.x; ++q) s += red[q];
-        rc[a] = s;
+        rl[a] = s;
     }
     // Binv_a is symmetric: row i is read as column i, so a warp's loads of
     // one j are contiguous
@@ -116,25 +179,33 @@ __global__ void __launch_bounds__(128) k_prec_local(int fl, int mb, const int *_
     }
 }
 
-// zc = Cinv rc (warp per row)
-__global__ void k_prec_coarse(int nleaf, const double *__restrict__ Cinv, const double *__restrict__ rc,
+// zc = Cinv rc (warp per row), rc[c] = sum of the leaf sums of cluster c
+// (span consecutive leaves), formed per block in shared memory
+__global__ void k_prec_coarse(int nc, int span, const double *__restrict__ Cinv, const double *__restrict__ rl,
                               double *__restrict__ zc, const int *skip)
 {
+    extern __shared__ double rc[];
     if (skip && *skip) return;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < span; ++q) s += rl[(size_t)c * span + q];
+        rc[c] = s;
+    }
+    __syncthreads();
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= nleaf) return;
+    if (row >= nc) return;
     double v = 0.0;
-    for (int b = lane; b < nleaf; b += 32) v = fma(Cinv[(size_t)row * nleaf + b], rc[b], v);
+    for (int b = lane; b < nc; b += 32) v = fma(Cinv[(size_t)row * nc + b], rc[b], v);
     v = warp_sum(v);
     if (lane == 0) zc[row] = v;
 }
 
-__global__ void k_prec_add(int N, const int *__restrict__ vleaf, const double *__restrict__ zc, double *__restrict__ z,
+__global__ void k_prec_add(int N, const int *__restrict__ cidx, const double *__restrict__ zc, double *__restrict__ z,
                            const int *skip)
 {
     if (skip && *skip) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) z[i] += zc[vleaf[i]];
+    if (i < N) z[i] += zc[cidx[i]];
 }
 
 // in-place inverse of an SPD n x n matrix (row stride ld) by Cholesky:
@@ -181,61 +252,106 @@ void precond_setup(const MeshData &m, OpData &op, int kind, cudaStream_t st)
     release_graphs(op);
     op.prec_kind = 0;
     if (kind == 0) return;
-    VFD_REQUIRE(kind == 1, VFD_EINVAL, "unknown preconditioner kind");
-    VFD_REQUIRE(op.precision == VFD_FP64, VFD_EUNSUPPORTED, "the preconditioner is built for VFD_FP64 operators");
-    const int nleaf = m.kt.nleaf, fl = m.kt.first_leaf(), N = m.N;
-    VFD_REQUIRE(nleaf <= 2048, VFD_EUNSUPPORTED, "too many leaves for the dense coarse solve (at most 2048)");
+    VFD_REQUIRE(kind == 1 || kind == 2, VFD_EINVAL, "unknown preconditioner kind");
+    const int nleaf = m.kt.nleaf, fl = m.kt.first_leaf(), N = m.N, L = m.kt.L;
     const int mb = m.max_leaf_size;
-    // leaf diagonal blocks, inverted on the host
+    // leaf diagonal blocks, inverted on the device (large leaves on the host)
     op.prec_blk.alloc((size_t)nleaf * mb * mb);
+    op.prec_blk32.alloc((size_t)nleaf * mb * mb);
     k_diag_blocks<<<nleaf, 128, 0, st>>>(fl, mb, m.kt_begin.p, m.kt_end.p, m.near_ptr.p, m.near_col.p, m.near_off.p,
                                          m.panel_w.p, op.D64.p, m.rowptr.p, m.colidx.p, op.valBM.p, op.prec_blk.p);
     VFD_CUDA(cudaGetLastError());
-    std::vector<double> blk((size_t)nleaf * mb * mb);
-    VFD_CUDA(cudaMemcpyAsync(blk.data(), op.prec_blk.p, blk.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    VFD_CUDA(cudaStreamSynchronize(st));
-    for (int a = 0; a < nleaf; ++a)
-        VFD_REQUIRE(spd_inverse(&blk[(size_t)a * mb * mb], mb, mb), VFD_EINVAL,
-                    "a leaf diagonal block is not positive definite");
-    VFD_CUDA(cudaMemcpyAsync(op.prec_blk.p, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    // coarse matrix A_c = R A R^T by applying A to the leaf indicators (in column chunks)
-    DBuf<double> X, Y, Ac;
-    const int chunk = std::max(1, std::min(nleaf, (int)(((size_t)1 << 27) / std::max(N, 1))));
-    X.alloc((size_t)N * chunk);
-    Y.alloc((size_t)N * chunk);
-    Ac.alloc((size_t)nleaf * nleaf);
-    for (int c0 = 0; c0 < nleaf; c0 += chunk) {
-        const int nc = std::min(chunk, nleaf - c0);
-        k_indicators<<<cdiv((long long)N * nc, 256), 256, 0, st>>>(N, nc, c0, m.vleaf.p, X.p);
-        apply_parts_ex(m, op, VFD_PART_ALL, X.p, Y.p, nc, N, false, st, nullptr);
-        dim3 g(nleaf, nc);
-        k_leaf_sums<<<g, 128, 0, st>>>(N, nleaf, nc, c0, fl, m.kt_begin.p, m.kt_end.p, Y.p, Ac.p);
+    if (mb <= PREC_SMEM_BLK) {
+        const size_t shm = 2 * (size_t)mb * mb * sizeof(double);
+        VFD_CUDA(cudaFuncSetAttribute(k_blk_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        DBuf<int> err;
+        err.alloc(1);
+        err.zero(st);
+        k_blk_inv<<<nleaf, 256, shm, st>>>(mb, op.prec_blk.p, op.prec_blk32.p, err.p);
         VFD_CUDA(cudaGetLastError());
+        int herr = 0;
+        VFD_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaStreamSynchronize(st));
+        VFD_REQUIRE(herr == 0, VFD_EINVAL, "a leaf diagonal block is not positive definite");
+    } else {
+        std::vector<double> blk((size_t)nleaf * mb * mb);
+        VFD_CUDA(cudaMemcpyAsync(blk.data(), op.prec_blk.p, blk.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaStreamSynchronize(st));
+        for (int a = 0; a < nleaf; ++a)
+            VFD_REQUIRE(spd_inverse(&blk[(size_t)a * mb * mb], mb, mb), VFD_EINVAL,
+                        "a leaf diagonal block is not positive definite");
+        std::vector<float> b32(blk.begin(), blk.end());
+        VFD_CUDA(cudaMemcpyAsync(op.prec_blk.p, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        VFD_CUDA(cudaMemcpyAsync(op.prec_blk32.p, b32.data(), b32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        VFD_CUDA(cudaStreamSynchronize(st));
     }
-    std::vector<double> ac((size_t)nleaf * nleaf);
-    VFD_CUDA(cudaMemcpyAsync(ac.data(), Ac.p, ac.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    VFD_CUDA(cudaStreamSynchronize(st));
-    for (int a = 0; a < nleaf; ++a)   // symmetrise the rounding
-        for (int b = 0; b < a; ++b) {
-            const double v = 0.5 * (ac[(size_t)a * nleaf + b] + ac[(size_t)b * nleaf + a]);
-            ac[(size_t)a * nleaf + b] = ac[(size_t)b * nleaf + a] = v;
+    op.prec_mb = mb;
+    op.prec_nc = 0;
+    if (kind == 1) {
+        // coarse level: the deepest with at most PREC_MAX_COARSE clusters
+        int lc = L;
+        while (lc > 0 && (1 << lc) > PREC_MAX_COARSE) --lc;
+        const int nc = 1 << lc, span = 1 << (L - lc);
+        std::vector<int> cidx(N), cb(nc + 1);
+        for (int c = 0; c <= nc; ++c) cb[c] = c < nc ? m.kt.begin[fl + c * span] : N;
+        for (int c = 0; c < nc; ++c)
+            for (int i = cb[c]; i < cb[c + 1]; ++i) cidx[i] = c;
+        op.prec_cidx.upload(cidx);
+        DBuf<int> cbd;
+        cbd.upload(cb);
+        // coarse matrix A_c = R A R^T by applying A to the cluster indicators (in column chunks)
+        DBuf<double> X, Y, Ac;
+        // (32 columns per apply: the multi-column apply's far-field workspaces grow with
+        // the column count; they are released again below)
+        const int chunk = std::max(1, std::min(std::min(nc, 32), (int)(((size_t)1 << 26) / std::max(N, 1))));
+        const size_t ws0 = op.xhat.n;
+        X.alloc((size_t)N * chunk);
+        Y.alloc((size_t)N * chunk);
+        Ac.alloc((size_t)nc * nc);
+        for (int c0 = 0; c0 < nc; c0 += chunk) {
+            const int ncol = std::min(chunk, nc - c0);
+            k_indicators<<<cdiv((long long)N * ncol, 256), 256, 0, st>>>(N, ncol, c0, op.prec_cidx.p, X.p);
+            apply_parts_ex(m, op, VFD_PART_ALL, X.p, Y.p, ncol, N, false, st, nullptr);
+            dim3 g(nc, ncol);
+            k_cluster_sums<<<g, 128, 0, st>>>(N, nc, ncol, c0, cbd.p, Y.p, Ac.p);
+            VFD_CUDA(cudaGetLastError());
         }
-    VFD_REQUIRE(spd_inverse(ac.data(), nleaf, nleaf), VFD_EINVAL, "the coarse matrix is not positive definite");
-    op.prec_coarse.upload(ac);
-    op.prec_rc.alloc(nleaf);
-    op.prec_zc.alloc(nleaf);
+        std::vector<double> ac((size_t)nc * nc);
+        VFD_CUDA(cudaMemcpyAsync(ac.data(), Ac.p, ac.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaStreamSynchronize(st));
+        if (op.xhat.n > ws0) {   // the apply's workspaces return to their earlier size on next use
+            op.xhat.release();
+            op.yhat.release();
+            op.P64.release();
+        }
+        for (int a = 0; a < nc; ++a)   // symmetrise the rounding
+            for (int b = 0; b < a; ++b) {
+                const double v = 0.5 * (ac[(size_t)a * nc + b] + ac[(size_t)b * nc + a]);
+                ac[(size_t)a * nc + b] = ac[(size_t)b * nc + a] = v;
+            }
+        VFD_REQUIRE(spd_inverse(ac.data(), nc, nc), VFD_EINVAL, "the coarse matrix is not positive definite");
+        op.prec_coarse.upload(ac);
+        op.prec_coarse32.upload(std::vector<float>(ac.begin(), ac.end()));
+        op.prec_nc = nc;
+        op.prec_span = span;
+        op.prec_zc.alloc(nc);
+    }
+    op.prec_rl.alloc(nleaf);
     VFD_CUDA(cudaStreamSynchronize(st));
     op.prec_kind = kind;
+    ++op.prec_version;
 }
 
 void precond_apply(const MeshData &m, const OpData &op, const double *r, double *z, cudaStream_t st, const int *skip)
 {
-    const int nleaf = m.kt.nleaf, mb = m.max_leaf_size;
+    const int nleaf = m.kt.nleaf, mb = op.prec_mb;
     k_prec_local<<<nleaf, 128, (size_t)mb * sizeof(double), st>>>(m.kt.first_leaf(), mb, m.kt_begin.p, m.kt_end.p,
-                                                                 op.prec_blk.p, r, z, op.prec_rc.p, skip);
-    k_prec_coarse<<<cdiv((long long)nleaf * 32, 256), 256, 0, st>>>(nleaf, op.prec_coarse.p, op.prec_rc.p,
-                                                                    op.prec_zc.p, skip);
-    k_prec_add<<<cdiv(m.N, 256), 256, 0, st>>>(m.N, m.vleaf.p, op.prec_zc.p, z, skip);
+                                                                 op.prec_blk.p, r, z, op.prec_rl.p, skip);
+    if (op.prec_nc > 0) {
+        k_prec_coarse<<<cdiv((long long)op.prec_nc * 32, 256), 256, (size_t)op.prec_nc * sizeof(double), st>>>(
+            op.prec_nc, op.prec_span, op.prec_coarse.p, op.prec_rl.p, op.prec_zc.p, skip);
+        k_prec_add<<<cdiv(m.N, 256), 256, 0, st>>>(m.N, op.prec_cidx.p, op.prec_zc.p, z, skip);
+    }
     VFD_CUDA(cudaGetLastError());
 }
 

@@ -285,10 +285,15 @@ struct OpData {
     cudaGraphExec_t pcg_exec = nullptr;  // captured PCG chunk
     const void *pcg_key = nullptr;
     // two-level preconditioner (precond.cu): leaf-block inverses and the coarse inverse
-    int prec_kind = 0;
-    DBuf<double> prec_blk;             // nleaf x maxleaf x maxleaf (inverse of each leaf's diagonal block)
-    DBuf<double> prec_coarse;          // nleaf x nleaf (inverse of R A R^T)
-    DBuf<double> prec_rc, prec_zc;     // coarse residual / correction (nleaf)
+    int prec_kind = 0;                 // 0 none, 1 two-level, 2 leaf blocks only
+    long long prec_version = 0;        // incremented by every setup
+    int prec_mb = 0, prec_nc = 0, prec_span = 1;   // block size; coarse clusters; leaves per cluster
+    DBuf<double> prec_blk;             // nleaf x mb x mb (inverse of each leaf's diagonal block)
+    DBuf<float> prec_blk32;            //   FP32 copy (batched solve)
+    DBuf<double> prec_coarse;          // nc x nc (inverse of R A R^T)
+    DBuf<float> prec_coarse32;         //   FP32 copy
+    DBuf<int> prec_cidx;               // coarse cluster of every DoF
+    DBuf<double> prec_rl, prec_zc;     // leaf sums of the residual (nleaf), coarse correction (nc)
 };
 
 // ---------------------------------------------------------------------------
@@ -329,6 +334,14 @@ struct BatchData {
     DBuf<unsigned> gbar;                // its grid-barrier counter and generation
     DBuf<int> flag, red_items, red_mesh;
     int nred = 0, sR = 0;
+    // preconditioned batched solve (every operator of the batch preconditioned):
+    // FP32 leaf-block and coarse inverses of all meshes, work items and maps
+    bool pcg = false;                   // the captured chunk is the preconditioned one
+    std::vector<long long> pc_key;      // preconditioner versions the tables below were built from
+    DBuf<float> z, pc_blk, pc_coarse, pc_rl, pc_zc;
+    DBuf<int> pc_items, pc_pmesh, pc_ctiles, pc_rowclu;
+    DBuf<long long> pc_boff, pc_coff;
+    int n_pc_items = 0, n_pc_ctiles = 0, pc_mbmax = 0, pc_any_coarse = 0;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t side = nullptr;        // far-field branch of the batched apply
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libvfd.so")
 VFD_OK, VFD_EINVAL, VFD_ENOMEM, VFD_ECUDA, VFD_ENOCONV, VFD_ETIMEOUT, VFD_EUNSUPPORTED = range(7)
 VFD_FP64, VFD_FP32, VFD_BF16 = 0, 1, 2
 VFD_PART_B, VFD_PART_M, VFD_PART_KNEAR, VFD_PART_KFAR, VFD_PART_ALL = 1, 2, 4, 8, 15
-VFD_PREC_NONE, VFD_PREC_TWO_LEVEL = 0, 1
+VFD_PREC_NONE, VFD_PREC_TWO_LEVEL, VFD_PREC_BLOCK_JACOBI = 0, 1, 2
 VFD_ASSEMBLE_UNCHECKED = 1
 VFD_ASSEMBLE_TIMED = 2
 VFD_APPLY_NOALLOC_SCRATCH_BYTES = 8388608   # static scratch of vfd_apply_noalloc, per device
@@ -368,7 +368,8 @@ def vfd_batch_set_wait_limit(batch, seconds):
 
 
 def vfd_precondition(op, kind=VFD_PREC_TWO_LEVEL, stream=None):
-    """Two-level preconditioner for the FP64 CG of vfd_solve (VFD_PREC_NONE: plain CG)."""
+    """Preconditioner of the op's CG solves: FP64 CG and the batched mixed-precision
+    solve (VFD_PREC_TWO_LEVEL, VFD_PREC_BLOCK_JACOBI; VFD_PREC_NONE: plain CG)."""
     _check(load().vfd_precondition(op.handle, int(kind), _stream(stream)))
 
 
