@@ -689,6 +689,20 @@ def batched_leg(mesh, s, k, prm, torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
     ta64 = ev_time(lambda: vfd.vfd_apply(op64, X, Y), 3)
     out["fp64"] = {"apply_us": ta64 * 1e6, "apply_dof_rhs_per_s": n * nrhs / ta64, "solve_ms": 1000 * t64,
                    "cg_iters_mean": float(sum(it64) / len(it64)), "cols_timed": nrhs, "status": int(st)}
+    # the same with the two-level preconditioner (setup timed separately)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vfd.vfd_precondition(op64)
+    torch.cuda.synchronize()
+    tsu64 = time.perf_counter() - t0
+    Up = torch.zeros_like(F)
+    vfd.vfd_solve(op64, F[:1], Up[:1], rtol=rtol, max_it=100000)   # graph capture
+    tp64 = ev_time(lambda: vfd.vfd_solve(op64, F, Up.zero_(), rtol=rtol, max_it=100000), 1)
+    st, itp, _ = vfd.vfd_solve(op64, F, Up.zero_(), rtol=rtol, max_it=100000)
+    out["fp64_pcg"] = {"setup_s": tsu64, "solve_ms": 1000 * tp64, "cg_iters_mean": float(sum(itp) / len(itp)),
+                       "status": int(st),
+                       "solution_rel_err_vs_fp64_cg": (torch.linalg.norm(Up - U64, dim=1) /
+                                                       torch.linalg.norm(U64, dim=1)).max().item()}
     for name, prec, wbytes in (("tf32", vfd.VFD_FP32, 4), ("bf16", vfd.VFD_BF16, 2)):
         op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], precision=prec)
         for _ in range(3):
@@ -706,6 +720,27 @@ def batched_leg(mesh, s, k, prm, torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
         torch.cuda.synchronize()
         ts = e0.elapsed_time(e1) / 1000.0
         err_sol = (torch.linalg.norm(U - U64, dim=1) / torch.linalg.norm(U64, dim=1)).max().item()
+        # preconditioned (two-level, FP32 inverses in the batched iteration)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vfd.vfd_precondition(op)
+        torch.cuda.synchronize()
+        tsu = time.perf_counter() - t0
+        Up = torch.zeros_like(F)
+        vfd.vfd_solve(op, F, Up, rtol=rtol, max_it=100000)   # warm-up (graph capture)
+        Up.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        stp, itp, relp = vfd.vfd_solve(op, F, Up, rtol=rtol, max_it=100000)
+        e1.record()
+        torch.cuda.synchronize()
+        tsp = e0.elapsed_time(e1) / 1000.0
+        pcg = {"setup_s": tsu, "solve_ms": tsp * 1000, "status": int(stp), "inner_iters": int(itp[0]),
+               "ms_per_inner_iter": tsp * 1000 / max(1, int(itp[0])), "relres_max": float(relp.max()),
+               "solution_rel_err_vs_fp64_cg": (torch.linalg.norm(Up - U64, dim=1) /
+                                               torch.linalg.norm(U64, dim=1)).max().item(),
+               "speedup_vs_fp64_cg": t64 / tsp, "speedup_vs_fp64_pcg": tp64 / tsp}
+        vfd.vfd_precondition(op, vfd.VFD_PREC_NONE)
         bt = vfd.vfd_batch_create([op])
         vfd.vfd_batch_apply(bt, [X], [Y])
         chosen, cand_us = vfd.vfd_batch_tuning(bt)
@@ -722,7 +757,7 @@ def batched_leg(mesh, s, k, prm, torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
                      "apply_rel_err_vs_fp64": err_apply, "solve_ms": ts * 1000, "status": int(st),
                      "inner_iters": int(it[0]), "ms_per_inner_iter": ts * 1000 / max(1, int(it[0])),
                      "relres_max": float(rel.max()), "solution_rel_err_vs_fp64_cg": err_sol,
-                     "speedup_vs_fp64_solve": t64 / ts,
+                     "speedup_vs_fp64_solve": t64 / ts, "preconditioned": pcg,
                      "near_kernel_roofline": {"bound": "hbm", "launch_us": t_near * 1e6,
                                               "algorithmic_bytes": near_bytes,
                                               "achieved_gbs": near_bytes / t_near / 1e9, "peak_gbs": hbm,
@@ -792,12 +827,35 @@ def batch24_leg(torch, vfd, nrhs=64, rtol=1e-8, hbm=6800.0):
         torch.cuda.synchronize()
         tseq = e0.elapsed_time(e1) / 1000.0
         chosen, _ = vfd.vfd_batch_tuning(batch)
+        # preconditioned: every operator gets the two-level preconditioner
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for op in ops:
+            vfd.vfd_precondition(op)
+        torch.cuda.synchronize()
+        tsu = time.perf_counter() - t0
+        Us3 = [torch.zeros_like(f) for f in Fs]
+        e0.record()
+        stp, itp, relp = vfd.vfd_batch_solve(batch, Fs, Us3, rtol=rtol, max_it=200000)
+        e1.record()
+        torch.cuda.synchronize()
+        tsp = e0.elapsed_time(e1) / 1000.0
+        Us4 = [torch.zeros_like(f) for f in Fs]
+        e0.record()
+        for op, F, U in zip(ops, Fs, Us4):
+            vfd.vfd_solve(op, F, U, rtol=rtol, max_it=200000)
+        e1.record()
+        torch.cuda.synchronize()
+        tseqp = e0.elapsed_time(e1) / 1000.0
+        pcg = {"setup_s": tsu, "solve_s": tsp, "status": int(stp), "inner_iters_max": int(itp.max()),
+               "relres_max": float(relp.max()), "solved_dof_rhs_per_s": ntot * nrhs / tsp,
+               "sequential_per_mesh_solves_s": tseqp}
         out[name] = {"assemble_s": t_asm, "apply_ms": ta * 1000, "apply_dof_rhs_per_s": ntot * nrhs / ta,
                      "near_kernel_tuned": {"stage_cols": chosen[0], "stages": chosen[1], "split": chosen[2],
                                            "warps": chosen[3], "acc_sets": chosen[4], "tcgen05": chosen[5]},
                      "solve_s": ts, "status": int(st), "inner_iters_max": int(it.max()),
                      "relres_max": float(rel.max()), "solved_dof_rhs_per_s": ntot * nrhs / ts,
-                     "sequential_per_mesh_solves_s": tseq}
+                     "sequential_per_mesh_solves_s": tseq, "preconditioned": pcg}
         del batch, ops
     return out
 

@@ -314,7 +314,16 @@ __global__ void k_b_from_inner(int N, int R, int Rp, int64_t ld, const float *__
     if (scale[c] > 0.0) U[(size_t)c * ld + i] += scale[c] * (double)z[(size_t)i * Rp + c];
 }
 
-// res = F - AU (column-major FP64), and per-column norms^2 (FP64, one block per column)
+// any nonzero entry in the first N rows of R columns of U (flag |= 1)
+__global__ void k_b_nonzero(int N, int R, int64_t ld, const double *__restrict__ U, int *flag)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)N * R) return;
+    const int c = (int)(t / N), i = (int)(t % N);
+    if (U[(size_t)c * ld + i] != 0.0) atomicOr(flag, 1);
+}
+
+// res = F - AU (column-major FP64; AU null: U = 0), and per-column norms^2 (FP64, one block per column)
 __global__ void k_b_resid(int N, int64_t ld, const double *__restrict__ F, const double *__restrict__ AU,
                           double *__restrict__ res, double *__restrict__ nrm2, double *__restrict__ fn2)
 {
@@ -322,7 +331,7 @@ __global__ void k_b_resid(int N, int64_t ld, const double *__restrict__ F, const
     const int c = blockIdx.x;
     double v = 0.0, f = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double d = F[(size_t)c * ld + i] - AU[(size_t)c * ld + i];
+        double d = AU ? F[(size_t)c * ld + i] - AU[(size_t)c * ld + i] : F[(size_t)c * ld + i];
         res[(size_t)c * ld + i] = d;
         v += d * d;
         f += F[(size_t)c * ld + i] * F[(size_t)c * ld + i];
@@ -895,7 +904,10 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
                        int max_it, int *iters, double *relres, cudaStream_t st)
 {
-    constexpr double RU_DROP = 0.03;   // recursive-residual reduction between reliable updates
+    // recursive-residual reduction between reliable updates: the preconditioned
+    // iteration runs few, fast-converging steps between FP64 residuals (each an
+    // FP64 apply of all columns), so it waits for a deeper drop
+    const double RU_DROP = 0.03, RU_DROP_PCG = 0.003;
     const int Rp = ((R + 63) / 64) * 64, nm = b.nmesh;
     const size_t nc = (size_t)nm * Rp, nr = (size_t)nm * R;
     ensure_solve(b, Rp);
@@ -924,13 +936,30 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
 
     // for the meshes with upd[i]: FP64 residuals res = F - A U, relres, the new
     // scales, thresholds and direction factors (gamma); sets conv[i]
+    // the first call skips the FP64 apply for meshes whose initial U is zero
+    std::vector<int> u_nonzero(nm, 1);
+    {
+        DBuf<int> nzf;
+        nzf.alloc(nm);
+        nzf.zero(st);
+        for (int i = 0; i < nm; ++i)
+            k_b_nonzero<<<cdiv((long long)b.ops[i]->m->N * R, 256), 256, 0, st>>>(b.ops[i]->m->N, R, ld[i], U[i],
+                                                                                 nzf.p + i);
+        VFD_CUDA(cudaGetLastError());
+        VFD_CUDA(cudaMemcpyAsync(u_nonzero.data(), nzf.p, sizeof(int) * nm, cudaMemcpyDeviceToHost, st));
+        VFD_CUDA(cudaStreamSynchronize(st));
+    }
+    bool first_residual = true;
     auto true_residual = [&](int it_now) {
+        const bool first = first_residual;
+        first_residual = false;
         for (int i = 0; i < nm; ++i) {
             if (!upd[i]) continue;
             OpData &op = *b.ops[i];
-            apply_parts_ex(*op.m, op, VFD_PART_ALL, U[i], AU[i].p, R, ld[i], false, st, nullptr);
-            k_b_resid<<<R, 256, 0, st>>>(op.m->N, ld[i], F[i], AU[i].p, res[i].p, n2.p + (size_t)i * R,
-                                         f2.p + (size_t)i * R);
+            const bool zero_u = first && !u_nonzero[i];
+            if (!zero_u) apply_parts_ex(*op.m, op, VFD_PART_ALL, U[i], AU[i].p, R, ld[i], false, st, nullptr);
+            k_b_resid<<<R, 256, 0, st>>>(op.m->N, ld[i], F[i], zero_u ? nullptr : AU[i].p, res[i].p,
+                                         n2.p + (size_t)i * R, f2.p + (size_t)i * R);
             VFD_CUDA(cudaGetLastError());
         }
         VFD_CUDA(cudaMemcpyAsync(hn.data(), n2.p, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
@@ -1018,7 +1047,8 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
     capture_bcg(b, Rp, st);
     // the captured apply reads p in BF16 from the fused kernel: provide the first one
     if (b.fused && b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
-    const float drop2 = (float)(RU_DROP * RU_DROP);
+    const double ru_drop = b.pcg ? RU_DROP_PCG : RU_DROP;
+    const float drop2 = (float)(ru_drop * ru_drop);
     int it = 0;
     while (true) {
         VFD_CUDA(cudaGraphLaunch(b.exec, st));
