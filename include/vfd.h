@@ -274,8 +274,9 @@ vfd_status vfd_solve(vfd_op_t op, const double *F, double *U, int64_t nrhs, int6
  * preconditioned: FP32 copies of the inverses); not by the one-column
  * refinement of low-precision operators.  Setup, FP64 from the operator's
  * FP64 parts: the leaf blocks inverted on the device (Cholesky in shared
- * memory; leaves above 96 DoFs on the host), A_c formed by applying A to the
- * cluster indicators and inverted on the host; blocks until done.
+ * memory; leaves above 96 DoFs on the host), A_c summed from the operator's
+ * parts (near-block sums, B + M entries, admissible blocks contracted with the
+ * clusters' per-level basis sums) and inverted on the host; blocks until done.
  * VFD_PREC_NONE switches back to plain CG.  The batched solve needs leaves of
  * at most 128 DoFs.  Errors: VFD_EINVAL (unknown kind, a block that is not
  * positive definite), VFD_ECUDA. */

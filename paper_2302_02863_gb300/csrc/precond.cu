@@ -16,20 +16,19 @@
 //
 // Setup (once per operator, vfd_precondition): the diagonal blocks are
 // gathered and inverted on the device (one CTA per leaf: Cholesky and the
-// triangular inverses in shared memory, FP64); A_c is formed by applying A to
-// the cluster indicators and summing rows per cluster, and inverted on the
-// host.  FP32 copies of both serve the batched mixed-precision solve.  Apply
+// triangular inverses in shared memory, FP64); A_c is summed from the
+// operator's parts (near-block sums, B + M entries, and per admissible block
+// the coupling contracted with the per-level basis sums of the clusters) and
+// inverted on the host.  FP32 copies of both serve the batched mixed-precision solve.  Apply
 // (every PCG iteration, FP64 solve): one kernel per leaf for the local solves
 // and the leaf sums, one for the coarse product, one for the prolongation.
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "device_common.cuh"
 
 namespace vfd {
-
-void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
-                    bool lowp, cudaStream_t st, const int *skip);
 
 namespace {
 
@@ -121,29 +120,78 @@ __global__ void __launch_bounds__(256) k_blk_inv(int mb, double *__restrict__ bl
     if (threadIdx.x == 0 && bad) atomicOr(err, 1);
 }
 
-// cluster indicator columns: X[c][i] = 1 if DoF i lies in cluster c0 + c
-__global__ void k_indicators(int N, int ncol, int c0, const int *__restrict__ cidx, double *__restrict__ X)
+// A_c = R A R^T from the operator's parts directly (no applies): the sum of
+// every near block's entries, the B + M entries, and for every admissible
+// block (sigma, tau) the sums u_A^T S u_B over the coarse units A, B under
+// sigma and tau, u_A = sum_{i in A} Ul^(l)[i] (l the block's level).
+// Sum of the entries of near block e (rows of its row leaf, columns of its
+// column leaf) in the row panel
+__global__ void k_near_blocksum(int fl, const int *__restrict__ prow, const int *__restrict__ ncol,
+                                const int *__restrict__ kb, const int *__restrict__ ke,
+                                const int64_t *__restrict__ noff, const int *__restrict__ pw,
+                                const double *__restrict__ D, double *__restrict__ out)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)N * ncol) return;
-    const int c = (int)(t / N), i = (int)(t % N);
-    X[t] = cidx[i] == c0 + c ? 1.0 : 0.0;
-}
-
-// Ac[a][c0 + c] = sum over the DoFs of cluster a (rows [cb[a], cb[a+1])) of Y[c][i]
-__global__ void k_cluster_sums(int N, int nc, int ncol, int c0, const int *__restrict__ cb,
-                               const double *__restrict__ Y, double *__restrict__ Ac)
-{
-    const int a = blockIdx.x, c = blockIdx.y;
-    __shared__ double sh[128];
+    __shared__ double sh[256];
+    const int e = blockIdx.x, a = prow[e], b = ncol[e];
+    const int na = ke[fl + a] - kb[fl + a], nb = ke[fl + b] - kb[fl + b], W = pw[a];
     double v = 0.0;
-    for (int i = cb[a] + threadIdx.x; i < cb[a + 1]; i += blockDim.x) v += Y[(size_t)c * N + i];
+    for (int t = threadIdx.x; t < na * nb; t += blockDim.x) v += D[noff[e] + (size_t)(t / nb) * W + t % nb];
     sh[threadIdx.x] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int q = 0; q < (int)blockDim.x; ++q) s += sh[q];
-        Ac[(size_t)a * nc + c0 + c] = s;
+        out[e] = s;
+    }
+}
+
+// unit moments u[l][unit][alpha] = sum over the unit's rows of Ul^(l)[i][alpha],
+// the units of level l being the nodes of level max(l, lc); CTA per (unit, level)
+__global__ void k_unit_moments(int k, int N, int lmin, int lc, int nu_max, const int *__restrict__ kb,
+                               const int *__restrict__ ke, const double *__restrict__ Ul, double *__restrict__ u)
+{
+    const int lv = blockIdx.y, l = lmin + lv, lu = max(l, lc);
+    const int unit = blockIdx.x;
+    if (unit >= (1 << lu)) return;
+    const int node = (1 << lu) - 1 + unit;
+    const double *U = Ul + (size_t)lv * N * k;
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+        double s = 0.0;
+        for (int i = kb[node]; i < ke[node]; ++i) s += U[(size_t)i * k + a];
+        u[((size_t)lv * nu_max + unit) * k + a] = s;
+    }
+}
+
+// per admissible block e (row node sigma, column tau, level l) and unit pair
+// (A under sigma, B under tau): u_A^T S_e u_B; thread per pair; the pairs of
+// block e start at off[e] (nA x nB of them, A-major)
+__global__ void k_far_unitpairs(int k, int lmin, int lc, int nu_max, int nnode, int nfar, const int *__restrict__ fptr,
+                                const int *__restrict__ fcol, const long long *__restrict__ off,
+                                const double *__restrict__ S, const double *__restrict__ u, double *__restrict__ out)
+{
+    const int e = blockIdx.x;
+    if (e >= nfar) return;
+    int lo = 0, hi = nnode;   // row node of block e
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (fptr[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int sg = lo, tau = fcol[e];
+    int l = 0;
+    while ((2 << l) - 1 <= sg) ++l;
+    const int lu = max(l, lc), sh = lu - l, nA = 1 << sh;
+    const int ua0 = ((sg + 1) << sh) - (1 << lu), ub0 = ((tau + 1) << sh) - (1 << lu);
+    const double *Se = S + (size_t)e * k * k;   // stored [b][a]
+    const double *ul = u + (size_t)(l - lmin) * nu_max * k;
+    for (int t = threadIdx.x; t < nA * nA; t += blockDim.x) {
+        const double *uA = ul + (size_t)(ua0 + t / nA) * k, *uB = ul + (size_t)(ub0 + t % nA) * k;
+        double v = 0.0;
+        for (int b = 0; b < k; ++b) {
+            double w = 0.0;
+            for (int a = 0; a < k; ++a) w = fma(Se[(size_t)b * k + a], uA[a], w);
+            v = fma(w, uB[b], v);
+        }
+        out[off[e] + t] = v;
     }
 }
 
@@ -209,38 +257,60 @@ __global__ void k_prec_add(int N, const int *__restrict__ cidx, const double *__
 }
 
 // in-place inverse of an SPD n x n matrix (row stride ld) by Cholesky:
-// A = L L^T, A^-1 = L^-T L^-1; false if a pivot is not positive
+// A = L L^T (row dot products, sequential), then the columns of A^-1 by a
+// forward and a backward substitution each, split over host threads; false if
+// a pivot is not positive
 bool spd_inverse(double *A, int n, int ld)
 {
-    std::vector<double> L((size_t)n * n, 0.0), Li((size_t)n * n, 0.0);
-    for (int j = 0; j < n; ++j) {
-        double d = A[(size_t)j * ld + j];
-        for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-        if (!(d > 0.0)) return false;
-        const double ljj = std::sqrt(d);
-        L[(size_t)j * n + j] = ljj;
-        for (int i = j + 1; i < n; ++i) {
-            double v = A[(size_t)i * ld + j];
-            for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-            L[(size_t)i * n + j] = v / ljj;
-        }
-    }
-    // Li = L^-1 (lower triangular), column by column
-    for (int c = 0; c < n; ++c) {
-        Li[(size_t)c * n + c] = 1.0 / L[(size_t)c * n + c];
-        for (int i = c + 1; i < n; ++i) {
-            double v = 0.0;
-            for (int k = c; k < i; ++k) v -= L[(size_t)i * n + k] * Li[(size_t)k * n + c];
-            Li[(size_t)i * n + c] = v / L[(size_t)i * n + i];
-        }
-    }
-    // A^-1 = Li^T Li
-    for (int i = 0; i < n; ++i)
+    std::vector<double> L((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double *Li = &L[(size_t)i * n];
         for (int j = 0; j <= i; ++j) {
-            double v = 0.0;
-            for (int k = i; k < n; ++k) v += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
-            A[(size_t)i * ld + j] = v;
-            A[(size_t)j * ld + i] = v;
+            const double *Lj = &L[(size_t)j * n];
+            double v = A[(size_t)i * ld + j];
+            for (int k = 0; k < j; ++k) v -= Li[k] * Lj[k];
+            if (j == i) {
+                if (!(v > 0.0)) return false;
+                L[(size_t)i * n + i] = std::sqrt(v);
+            } else {
+                L[(size_t)i * n + j] = v / Lj[j];
+            }
+        }
+    }
+    std::vector<double> Lt((size_t)n * n);   // L^T row-major: the backward solve reads rows
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) Lt[(size_t)j * n + i] = L[(size_t)i * n + j];
+    auto solve_cols = [&](int c0, int c1) {
+        std::vector<double> y(n);
+        for (int c = c0; c < c1; ++c) {
+            for (int i = 0; i < n; ++i) {   // L y = e_c
+                double v = i == c ? 1.0 : 0.0;
+                const double *Li = &L[(size_t)i * n];
+                for (int k = c; k < i; ++k) v -= Li[k] * y[k];
+                y[i] = i < c ? 0.0 : v / Li[i];
+            }
+            for (int i = n - 1; i >= 0; --i) {   // L^T x = y, x overwrites y
+                double v = y[i];
+                const double *Ui = &Lt[(size_t)i * n];
+                for (int k = i + 1; k < n; ++k) v -= Ui[k] * y[k];
+                y[i] = v / Ui[i];
+            }
+            for (int i = 0; i < n; ++i) A[(size_t)i * ld + c] = y[i];
+        }
+    };
+    const int nth = n >= 128 ? (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1;
+    if (nth == 1) {
+        solve_cols(0, n);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t)
+            th.emplace_back(solve_cols, (int)((int64_t)n * t / nth), (int)((int64_t)n * (t + 1) / nth));
+        for (auto &t : th) t.join();
+    }
+    for (int i = 0; i < n; ++i)   // symmetrise the rounding
+        for (int j = 0; j < i; ++j) {
+            const double v = 0.5 * (A[(size_t)i * ld + j] + A[(size_t)j * ld + i]);
+            A[(size_t)i * ld + j] = A[(size_t)j * ld + i] = v;
         }
     return true;
 }
@@ -297,32 +367,71 @@ void precond_setup(const MeshData &m, OpData &op, int kind, cudaStream_t st)
         for (int c = 0; c < nc; ++c)
             for (int i = cb[c]; i < cb[c + 1]; ++i) cidx[i] = c;
         op.prec_cidx.upload(cidx);
-        DBuf<int> cbd;
-        cbd.upload(cb);
-        // coarse matrix A_c = R A R^T by applying A to the cluster indicators (in column chunks)
-        DBuf<double> X, Y, Ac;
-        // (32 columns per apply: the multi-column apply's far-field workspaces grow with
-        // the column count; they are released again below)
-        const int chunk = std::max(1, std::min(std::min(nc, 32), (int)(((size_t)1 << 26) / std::max(N, 1))));
-        const size_t ws0 = op.xhat.n;
-        X.alloc((size_t)N * chunk);
-        Y.alloc((size_t)N * chunk);
-        Ac.alloc((size_t)nc * nc);
-        for (int c0 = 0; c0 < nc; c0 += chunk) {
-            const int ncol = std::min(chunk, nc - c0);
-            k_indicators<<<cdiv((long long)N * ncol, 256), 256, 0, st>>>(N, ncol, c0, op.prec_cidx.p, X.p);
-            apply_parts_ex(m, op, VFD_PART_ALL, X.p, Y.p, ncol, N, false, st, nullptr);
-            dim3 g(nc, ncol);
-            k_cluster_sums<<<g, 128, 0, st>>>(N, nc, ncol, c0, cbd.p, Y.p, Ac.p);
+        // coarse matrix A_c = R A R^T from the operator's parts
+        std::vector<double> ac((size_t)nc * nc, 0.0);
+        auto clu_of_leaf = [&](int leaf) { return leaf / span; };
+        {   // near blocks
+            DBuf<double> bs;
+            bs.alloc(std::max(m.nnear, 1));
+            if (m.nnear > 0)
+                k_near_blocksum<<<m.nnear, 256, 0, st>>>(fl, m.near_pair_row.p, m.near_col.p, m.kt_begin.p,
+                                                          m.kt_end.p, m.near_off.p, m.panel_w.p, op.D64.p, bs.p);
             VFD_CUDA(cudaGetLastError());
+            std::vector<double> hb(m.nnear);
+            VFD_CUDA(cudaMemcpyAsync(hb.data(), bs.p, sizeof(double) * m.nnear, cudaMemcpyDeviceToHost, st));
+            VFD_CUDA(cudaStreamSynchronize(st));
+            for (int a = 0; a < nleaf; ++a)
+                for (int e = m.near_ptr_h[a]; e < m.near_ptr_h[a + 1]; ++e)
+                    ac[(size_t)clu_of_leaf(a) * nc + clu_of_leaf(m.near_col_h[e])] += hb[e];
         }
-        std::vector<double> ac((size_t)nc * nc);
-        VFD_CUDA(cudaMemcpyAsync(ac.data(), Ac.p, ac.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-        VFD_CUDA(cudaStreamSynchronize(st));
-        if (op.xhat.n > ws0) {   // the apply's workspaces return to their earlier size on next use
-            op.xhat.release();
-            op.yhat.release();
-            op.P64.release();
+        {   // B + M
+            std::vector<int> rp(N + 1), ci(m.nnz);
+            std::vector<double> v(m.nnz);
+            VFD_CUDA(cudaMemcpyAsync(rp.data(), m.rowptr.p, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, st));
+            VFD_CUDA(cudaMemcpyAsync(ci.data(), m.colidx.p, sizeof(int) * m.nnz, cudaMemcpyDeviceToHost, st));
+            VFD_CUDA(cudaMemcpyAsync(v.data(), op.valBM.p, sizeof(double) * m.nnz, cudaMemcpyDeviceToHost, st));
+            VFD_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i < N; ++i)
+                for (int e = rp[i]; e < rp[i + 1]; ++e) ac[(size_t)cidx[i] * nc + cidx[ci[e]]] += v[e];
+        }
+        if (m.nfar > 0) {   // admissible blocks
+            const int k = m.k, lmin = m.far_lmin, nlev = L - lmin + 1;
+            const int nu_max = 1 << std::max(L, lc);
+            DBuf<double> u;
+            u.alloc((size_t)nlev * nu_max * k);
+            dim3 gu(nu_max, nlev);
+            k_unit_moments<<<gu, 64, 0, st>>>(k, N, lmin, lc, nu_max, m.kt_begin.p, m.kt_end.p, m.Ul64.p, u.p);
+            std::vector<long long> off(m.nfar + 1, 0);
+            std::vector<int> erow(m.nfar);
+            for (int n = 0; n < m.kt.nnode; ++n)
+                for (int e = m.far_ptr_h[n]; e < m.far_ptr_h[n + 1]; ++e) erow[e] = n;
+            for (int e = 0; e < m.nfar; ++e) {
+                int l = 0;
+                while ((2 << l) - 1 <= erow[e]) ++l;
+                const long long nA = 1LL << (std::max(l, lc) - l);
+                off[e + 1] = off[e] + nA * nA;
+            }
+            DBuf<long long> offd;
+            offd.upload(off);
+            DBuf<double> pv;
+            pv.alloc(off[m.nfar]);
+            k_far_unitpairs<<<m.nfar, 128, 0, st>>>(k, lmin, lc, nu_max, m.kt.nnode, m.nfar, m.far_ptr.p,
+                                                     m.far_col.p, offd.p, op.S64.p, u.p, pv.p);
+            VFD_CUDA(cudaGetLastError());
+            std::vector<double> hv(off[m.nfar]);
+            VFD_CUDA(cudaMemcpyAsync(hv.data(), pv.p, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+            VFD_CUDA(cudaStreamSynchronize(st));
+            for (int e = 0; e < m.nfar; ++e) {
+                const int sg = erow[e], tau = m.far_col_h[e];
+                int l = 0;
+                while ((2 << l) - 1 <= sg) ++l;
+                const int lu = std::max(l, lc), sh = lu - l, nA = 1 << sh;
+                const int ua0 = ((sg + 1) << sh) - (1 << lu), ub0 = ((tau + 1) << sh) - (1 << lu);
+                for (int t = 0; t < nA * nA; ++t) {
+                    const int A = (ua0 + t / nA) >> (lu - lc), B = (ub0 + t % nA) >> (lu - lc);
+                    ac[(size_t)A * nc + B] += hv[off[e] + t];
+                }
+            }
         }
         for (int a = 0; a < nc; ++a)   // symmetrise the rounding
             for (int b = 0; b < a; ++b) {
