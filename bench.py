@@ -76,6 +76,9 @@ def _args():
     p.add_argument("--mode", default="step", choices=["step", "apply", "solve"],
                    help="apply: assemble once, then --steps applies of --parts (bounded run for profilers)")
     p.add_argument("--parts", type=int, default=15, help="VFD_PART_* mask for --mode apply")
+    p.add_argument("--precondition", type=int, default=0, help="VFD_PREC_* kind for --mode solve")
+    p.add_argument("--near-config", type=int, default=-1,
+                   help="--mode apply, low precision, 64-column multiples: pin the near-panel configuration")
     return p.parse_args()
 
 
@@ -987,25 +990,34 @@ def apply_mode(args, mesh, s, k, prm, prec, torch, vfd):
     X = torch.randn(*shape, dtype=torch.float64, device="cuda", generator=g)
     Y = torch.zeros_like(X)
     if args.mode == "solve":
+        if args.precondition:
+            vfd.vfd_precondition(op, args.precondition)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         st, it, rel = vfd.vfd_solve(op, X, Y, rtol=args.rtol, max_it=200000)
         e1.record()
         torch.cuda.synchronize()
         print(json.dumps({"mode": "solve", "precision": args.precision, "nrhs": args.nrhs, "status": int(st),
+                          "precondition": args.precondition,
                           "iters": int(it[0]), "relres_max": float(rel.max()),
                           "ms": e0.elapsed_time(e1)}), flush=True)
         return
+    run = lambda: vfd.vfd_apply_parts(op, args.parts, X, Y)   # noqa: E731
+    if args.near_config >= 0:
+        batch = vfd.vfd_batch_create([op])
+        vfd.vfd_batch_set_config(batch, args.near_config)
+        run = lambda: vfd.vfd_batch_apply(batch, [X], [Y])   # noqa: E731
     for _ in range(args.warmup):
-        vfd.vfd_apply_parts(op, args.parts, X, Y)
+        run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        vfd.vfd_apply_parts(op, args.parts, X, Y)
+        run()
     e1.record()
     torch.cuda.synchronize()
     print(json.dumps({"mode": "apply", "parts": args.parts, "precision": args.precision, "nrhs": args.nrhs,
+                      "near_config": args.near_config,
                       "us_per_apply": 1000 * e0.elapsed_time(e1) / args.steps}), flush=True)
 
 

@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
 // cluster's leaves), z += zc[cluster of the row]
 // ---------------------------------------------------------------------------
 constexpr int PC_TILE = 64;   // columns per pass of the preconditioner kernels
-constexpr int PC_CROWS = 16;  // coarse rows per CTA
+constexpr int PC_CROWS = 32;  // coarse rows per CTA
 
 // leaf item: mesh, first row (global), rows, block stride, global leaf index
 __global__ void __launch_bounds__(256) k_bp_local(Seg S, const int *__restrict__ items,
@@ -592,37 +592,56 @@ __global__ void __launch_bounds__(256) k_bp_local(Seg S, const int *__restrict__
     }
 }
 
-// coarse tile: mesh, first coarse row; per mesh (pmesh): clusters nc, leaves
-// per cluster span, global index of its first leaf and of its first cluster
+// coarse tile: mesh, first coarse row (PC_CROWS rows); per mesh (pmesh):
+// clusters nc, leaves per cluster span, global index of its first leaf and
+// of its first cluster.  zc = Cinv rc as a tiled product: chunks of PC_CB
+// columns of Cinv and rows of rc (the cluster sums of the leaf sums, formed
+// while staging) in shared memory; thread (column c, row group) keeps
+// PC_CROWS / 4 rows
+constexpr int PC_CB = 32;
 __global__ void __launch_bounds__(256) k_bp_coarse(Seg S, const int *__restrict__ tiles, const int *__restrict__ pmesh,
                                                    const long long *__restrict__ coff,
                                                    const float *__restrict__ Cinv, const float *__restrict__ rl,
                                                    float *__restrict__ zc, const int *__restrict__ upd)
 {
+    __shared__ float Cs[PC_CROWS][PC_CB + 1], Rs[PC_CB][PC_TILE];
     if (S.flag[BF_DONE]) return;
     const int m = tiles[2 * blockIdx.x], a0 = tiles[2 * blockIdx.x + 1];
     if (upd ? !upd[m] : S.mdone()[m]) return;
     const int nc = pmesh[4 * m], span = pmesh[4 * m + 1], gl0 = pmesh[4 * m + 2], gc0 = pmesh[4 * m + 3];
     const int Rp = S.Rp;
     const float *C = Cinv + coff[m];
-    const int c = threadIdx.x % PC_TILE, grp = threadIdx.x / PC_TILE, ngrp = blockDim.x / PC_TILE;
+    const int c = threadIdx.x % PC_TILE, grp = threadIdx.x / PC_TILE;   // 4 groups
     constexpr int K = PC_CROWS / 4;
     for (int c0 = 0; c0 < Rp; c0 += PC_TILE) {
         float acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = 0.f;
-        for (int b = 0; b < nc; ++b) {
-            float rc = 0.f;
-            for (int q = 0; q < span; ++q) rc += rl[(size_t)(gl0 + b * span + q) * Rp + c0 + c];
+        for (int b0 = 0; b0 < nc; b0 += PC_CB) {
+            const int nb = min(PC_CB, nc - b0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < PC_CROWS * PC_CB; t += blockDim.x) {
+                const int i = t / PC_CB, bb = t % PC_CB;
+                Cs[i][bb] = (a0 + i < nc && bb < nb) ? C[(size_t)(a0 + i) * nc + b0 + bb] : 0.f;
+            }
+            for (int t = threadIdx.x; t < PC_CB * PC_TILE; t += blockDim.x) {
+                const int bb = t / PC_TILE, cc = t % PC_TILE;
+                float v = 0.f;
+                if (bb < nb)
+                    for (int q = 0; q < span; ++q) v += rl[(size_t)(gl0 + (b0 + bb) * span + q) * Rp + c0 + cc];
+                Rs[bb][cc] = v;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int bb = 0; bb < PC_CB; ++bb) {
+                const float r = Rs[bb][c];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const int a = a0 + grp + k * ngrp;
-                if (a < nc) acc[k] = fmaf(C[(size_t)a * nc + b], rc, acc[k]);
+                for (int k = 0; k < K; ++k) acc[k] = fmaf(Cs[grp * K + k][bb], r, acc[k]);
             }
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const int a = a0 + grp + k * ngrp;
+            const int a = a0 + grp * K + k;
             if (a < nc) zc[(size_t)(gc0 + a) * Rp + c0 + c] = acc[k];
         }
     }

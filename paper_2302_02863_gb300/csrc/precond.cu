@@ -163,12 +163,18 @@ __global__ void k_unit_moments(int k, int N, int lmin, int lc, int nu_max, const
 }
 
 // per admissible block e (row node sigma, column tau, level l) and unit pair
-// (A under sigma, B under tau): u_A^T S_e u_B; thread per pair; the pairs of
-// block e start at off[e] (nA x nB of them, A-major)
-__global__ void k_far_unitpairs(int k, int lmin, int lc, int nu_max, int nnode, int nfar, const int *__restrict__ fptr,
-                                const int *__restrict__ fcol, const long long *__restrict__ off,
-                                const double *__restrict__ S, const double *__restrict__ u, double *__restrict__ out)
+// (A under sigma, B under tau): u_A^T S_e u_B; the pairs of block e start at
+// off[e] (nA x nA of them, A-major).  CTA per block: t_B = S_e u_B for a chunk
+// of units B in shared memory (threads over the rows of S_e), then a thread
+// per pair (A, B) of the chunk
+constexpr int UP_CHUNK = 16;
+__global__ void __launch_bounds__(128) k_far_unitpairs(int k, int lmin, int lc, int nu_max, int nnode, int nfar,
+                                                       const int *__restrict__ fptr, const int *__restrict__ fcol,
+                                                       const long long *__restrict__ off,
+                                                       const double *__restrict__ S, const double *__restrict__ u,
+                                                       double *__restrict__ out)
 {
+    __shared__ double tB[UP_CHUNK][KMAX];
     const int e = blockIdx.x;
     if (e >= nfar) return;
     int lo = 0, hi = nnode;   // row node of block e
@@ -181,17 +187,26 @@ __global__ void k_far_unitpairs(int k, int lmin, int lc, int nu_max, int nnode, 
     while ((2 << l) - 1 <= sg) ++l;
     const int lu = max(l, lc), sh = lu - l, nA = 1 << sh;
     const int ua0 = ((sg + 1) << sh) - (1 << lu), ub0 = ((tau + 1) << sh) - (1 << lu);
-    const double *Se = S + (size_t)e * k * k;   // stored [b][a]
+    const double *Se = S + (size_t)e * k * k;   // stored [b][a]: S(a, b) = Se[b * k + a]
     const double *ul = u + (size_t)(l - lmin) * nu_max * k;
-    for (int t = threadIdx.x; t < nA * nA; t += blockDim.x) {
-        const double *uA = ul + (size_t)(ua0 + t / nA) * k, *uB = ul + (size_t)(ub0 + t % nA) * k;
-        double v = 0.0;
-        for (int b = 0; b < k; ++b) {
+    for (int B0 = 0; B0 < nA; B0 += UP_CHUNK) {
+        const int nb = min(UP_CHUNK, nA - B0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb * k; t += blockDim.x) {
+            const int jb = t / k, a = t % k;
+            const double *uB = ul + (size_t)(ub0 + B0 + jb) * k;
             double w = 0.0;
-            for (int a = 0; a < k; ++a) w = fma(Se[(size_t)b * k + a], uA[a], w);
-            v = fma(w, uB[b], v);
+            for (int b = 0; b < k; ++b) w = fma(Se[(size_t)b * k + a], uB[b], w);
+            tB[jb][a] = w;
         }
-        out[off[e] + t] = v;
+        __syncthreads();
+        for (int t = threadIdx.x; t < nA * nb; t += blockDim.x) {
+            const int iA = t / nb, jb = t % nb;
+            const double *uA = ul + (size_t)(ua0 + iA) * k;
+            double v = 0.0;
+            for (int a = 0; a < k; ++a) v = fma(uA[a], tB[jb][a], v);
+            out[off[e] + (size_t)iA * nA + B0 + jb] = v;
+        }
     }
 }
 

@@ -471,6 +471,9 @@ def workload(name: str):
                    batched solves uses p=4.
     'disk33k_r16': the same disk and fields with p=4 (rank 16).
     'disk_small':  same fields on a K=12 disk (parity-size).
+    'disk130k':    the same fields on a K=208 disk (~130k DoFs, rank 64): panels
+                   larger than the 129 MB L2 (profiling captures of the
+                   near-panel kernels).
     """
     if name == "interval512":
         s = 0.3
@@ -478,7 +481,8 @@ def workload(name: str):
         return m, const_field(s), const_field(math.log(frac_laplacian_const(1, s) / 2)), \
             dict(s_bar=0.3, tail=1, R=1.1, leaf=64, p=4)
     if name.startswith("disk"):
-        K, p = {"disk33k": (96, 8), "disk33k_r16": (96, 4), "disk_small": (12, 4), "disk_medium": (30, 4)}[name]
+        K, p = {"disk33k": (96, 8), "disk33k_r16": (96, 4), "disk_small": (12, 4), "disk_medium": (30, 4),
+                "disk130k": (208, 8)}[name]
         m = disk_mesh(K, R=1.1, jitter=0.2, seed=2000 + K)
         return m, config2_s_field(), random_fourier_field(2001, 0.5), \
             dict(s_bar=0.9, tail=0, R=1.1, leaf=64, p=p, lam=0.75, inner_p=min(p, 4))
