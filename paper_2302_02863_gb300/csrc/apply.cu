@@ -8,7 +8,8 @@
 // work:
 //   1. k_far_proj:   per (leaf, level) the projection Ul^(l)_leaf^T x_leaf
 //   2. k_far_sum:    per node, xhat = sum of its leaves' projections
-//   3. k_far_couple: per node, yhat = sum_e S_e xhat[col e] (CTA per node)
+//   3. k_far_couple: per admissible block e (a warp) S_e xhat[col e], then
+//                    k_far_couple_sum: per node the sum over its blocks
 //   4. k_near_csr:   per row, the near panel row and the B + M CSR row
 //                    (concurrently with 1-3, which run on a high-priority
 //                    side stream)
@@ -120,39 +121,105 @@ k_far_sum(FarView F, int nleaf, const A *__restrict__ part, A *__restrict__ xhat
 
 // ---------------------------------------------------------------------------
 // 3. coupling  yhat[node][a] = sum_{e in row node} sum_b S_e[b][a] xhat[col e][b]
-//    (S stored [b][a]); one CTA per node: every (block e, a) partial in its own
-//    thread, then a shared-memory sum over the node's blocks
+//    (S stored [b][a]).  The partial of one block for one a (couple_part, the
+//    same arithmetic in both kernels below) takes the even and the odd rows b
+//    in two chains; the node sum adds the partials in list order from zero,
+//    so both kernels give bit-identical yhat.
+//    k_far_couple + k_far_couple_sum: a warp per admissible block (lanes over
+//    a, a contiguous row of S_e per step) into ye[e][a], then per (node, a)
+//    the sum over the node's blocks.  k_far_couple_node (the no-allocation
+//    apply): a CTA per node, a warp per block of each pass of eight.
 // ---------------------------------------------------------------------------
 template <class T, class A>
-__global__ void __launch_bounds__(256)
-k_far_couple(FarView F, const int *__restrict__ fptr, const int *__restrict__ fcol, const T *__restrict__ S,
-             const A *__restrict__ xhat, A *__restrict__ yhat, int64_t hs, const int *skip)
+__device__ __forceinline__ void couple_part(const T *__restrict__ sp, const A *__restrict__ xc, int k, int a1, int a2,
+                                            A &r1, A &r2)
 {
-    __shared__ A red[256];
+    // columns a1 and a2 (a2 may be >= k: unused) together, each in two chains
+    A s1 = 0, t1 = 0, s2 = 0, t2 = 0;
+    const bool two = a2 < k;
+    int be = 0;
+#pragma unroll 4
+    for (; be + 1 < k; be += 2) {
+        const A x0 = xc[be], x1 = xc[be + 1];
+        s1 += (A)sp[(size_t)be * k + a1] * x0;
+        t1 += (A)sp[(size_t)(be + 1) * k + a1] * x1;
+        if (two) {
+            s2 += (A)sp[(size_t)be * k + a2] * x0;
+            t2 += (A)sp[(size_t)(be + 1) * k + a2] * x1;
+        }
+    }
+    if (be < k) {
+        s1 += (A)sp[(size_t)be * k + a1] * xc[be];
+        if (two) s2 += (A)sp[(size_t)be * k + a2] * xc[be];
+    }
+    r1 = s1 + t1;
+    r2 = s2 + t2;
+}
+
+template <class T, class A>
+__global__ void __launch_bounds__(256)
+k_far_couple(FarView F, int nfar, int nnode, const int *__restrict__ fptr, const int *__restrict__ fcol,
+             const T *__restrict__ S, const A *__restrict__ xhat, A *__restrict__ ye, int64_t hs, const int *skip)
+{
+    if (skip && *skip) return;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, r = blockIdx.y;
+    if (e >= nfar) return;
+    const int k = F.k;
+    const T *sp = S + (size_t)e * k * k;
+    const A *xc = xhat + (size_t)r * hs + (size_t)fcol[e] * k;
+    A *out = ye + ((size_t)r * nfar + e) * k;
+    for (int a = lane; a < k; a += 64) {
+        A r1, r2;
+        couple_part(sp, xc, k, a, a + 32, r1, r2);
+        out[a] = r1;
+        if (a + 32 < k) out[a + 32] = r2;
+    }
+}
+
+template <class A>
+__global__ void k_far_couple_sum(FarView F, int nfar, int nnode, const int *__restrict__ fptr,
+                                 const A *__restrict__ ye, A *__restrict__ yhat, int64_t hs, const int *skip)
+{
+    if (skip && *skip) return;
+    const int k = F.k, r = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnode * k) return;
+    const int node = t / k, a = t % k;
+    A s = 0;
+    for (int e = fptr[node]; e < fptr[node + 1]; ++e) s += ye[((size_t)r * nfar + e) * k + a];
+    yhat[(size_t)r * hs + t] = s;
+}
+
+template <class T, class A>
+__global__ void __launch_bounds__(256)
+k_far_couple_node(FarView F, const int *__restrict__ fptr, const int *__restrict__ fcol, const T *__restrict__ S,
+                  const A *__restrict__ xhat, A *__restrict__ yhat, int64_t hs, const int *skip)
+{
+    __shared__ A pt[8][KMAX];
     if (skip && *skip) return;
     const int node = blockIdx.x, r = blockIdx.y, k = F.k;
     const int e0 = fptr[node], ne = fptr[node + 1] - e0;
     const A *xh = xhat + (size_t)r * hs;
-    const int kk = min(k, (int)blockDim.x), per = blockDim.x / kk;   // blocks handled per pass
-    for (int a0 = 0; a0 < k; a0 += kk) {
-        const int al = threadIdx.x % kk, g = threadIdx.x / kk;
-        A tot = 0;   // meaningful in threads g == 0
-        for (int eb = 0; eb < ne; eb += per) {
-            A acc = 0;
-            const int e = eb + g;
-            if (g < per && e < ne) {
-                const T *sp = S + (size_t)(e0 + e) * k * k + a0 + al;
-                const A *xc = xh + (size_t)fcol[e0 + e] * k;
-                for (int be = 0; be < k; ++be) acc += (A)sp[(size_t)be * k] * xc[be];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    A tot = 0;   // thread a < k: the node sum of column a
+    for (int eb = 0; eb < ne; eb += 8) {
+        const int e = eb + warp;
+        if (e < ne) {
+            const T *sp = S + (size_t)(e0 + e) * k * k;
+            const A *xc = xh + (size_t)fcol[e0 + e] * k;
+            for (int a = lane; a < k; a += 64) {
+                A r1, r2;
+                couple_part(sp, xc, k, a, a + 32, r1, r2);
+                pt[warp][a] = r1;
+                if (a + 32 < k) pt[warp][a + 32] = r2;
             }
-            red[threadIdx.x] = acc;
-            __syncthreads();
-            if (g == 0)
-                for (int q = 0; q < per && eb + q < ne; ++q) tot += red[q * kk + al];
-            __syncthreads();
         }
-        if (g == 0) yhat[(size_t)r * hs + (size_t)node * k + a0 + al] = tot;
+        __syncthreads();
+        if ((int)threadIdx.x < k)
+            for (int w = 0; w < 8 && eb + w < ne; ++w) tot += pt[w][threadIdx.x];
+        __syncthreads();
     }
+    if ((int)threadIdx.x < k) yhat[(size_t)r * hs + (size_t)node * k + threadIdx.x] = tot;
 }
 
 // ---------------------------------------------------------------------------
@@ -333,7 +400,7 @@ static void row_kernel_smem(size_t shm)
 // ---------------------------------------------------------------------------
 template <class T, class A>
 static void apply_impl(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
-                       const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, cudaStream_t st,
+                       const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, A *ye, cudaStream_t st,
                        const int *skip)
 {
     const int k = m.k, fl = m.kt.first_leaf(), L = m.kt.L, nnode = m.kt.nnode;
@@ -361,8 +428,10 @@ static void apply_impl(const MeshData &m, OpData &op, int parts, const double *X
         const int nn = nnode - ((1 << F.lmin) - 1);
         dim3 gs(nn, nrhs);
         k_far_sum<A><<<gs, 128, 0, op.side>>>(F, m.kt.nleaf, part, xhat, hs, skip);
-        dim3 gc(nnode, nrhs);
-        k_far_couple<T, A><<<gc, 256, 0, op.side>>>(F, m.far_ptr.p, m.far_col.p, S, xhat, yhat, hs, skip);
+        dim3 gc(cdiv((long long)m.nfar * 32, 256), nrhs);
+        k_far_couple<T, A><<<gc, 256, 0, op.side>>>(F, m.nfar, nnode, m.far_ptr.p, m.far_col.p, S, xhat, ye, hs, skip);
+        dim3 gy(cdiv((long long)nnode * k, 256), nrhs);
+        k_far_couple_sum<A><<<gy, 256, 0, op.side>>>(F, m.nfar, nnode, m.far_ptr.p, ye, yhat, hs, skip);
     }
     const int NR = 16;
     dim3 go(m.kt.nleaf, cdiv(m.max_leaf_size, NR), nrhs);
@@ -412,24 +481,27 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
     const int nlev = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
     const size_t need = (size_t)m.kt.nnode * m.k * nrhs;
     const size_t needp = (size_t)std::max(nlev, 1) * m.kt.nleaf * m.k * nrhs;
+    const size_t needy = (size_t)std::max(m.nfar, 1) * m.k * nrhs;
     if (lowp) {
-        if (op.xhat32.n < need || op.P32.n < needp) {
+        if (op.xhat32.n < need || op.P32.n < needp || op.ye32.n < needy) {
             release_graphs(op);   // captured solves refer to the old workspace
             op.xhat32.alloc(need);
             op.yhat32.alloc(need);
             op.P32.alloc(needp);
+            op.ye32.alloc(needy);
         }
         apply_impl<float, float>(m, op, parts, X, Y, nrhs, ld, op.Ul32.p, op.S32.p, op.D32.p, op.xhat32.p, op.yhat32.p,
-                                 op.P32.p, st, skip);
+                                 op.P32.p, op.ye32.p, st, skip);
     } else {
-        if (op.xhat.n < need || op.P64.n < needp) {
+        if (op.xhat.n < need || op.P64.n < needp || op.ye64.n < needy) {
             release_graphs(op);
             op.xhat.alloc(need);
             op.yhat.alloc(need);
             op.P64.alloc(needp);
+            op.ye64.alloc(needy);
         }
         apply_impl<double, double>(m, op, parts, X, Y, nrhs, ld, m.Ul64.p, op.S64.p, op.D64.p, op.xhat.p, op.yhat.p,
-                                   op.P64.p, st, skip);
+                                   op.P64.p, op.ye64.p, st, skip);
     }
 }
 
@@ -500,7 +572,7 @@ void apply_one_stream(const MeshData &m, const OpData &op, const double *X, doub
         dim3 gs(nn, nrhs);
         k_far_sum<A><<<gs, 128, 0, st>>>(F, m.kt.nleaf, part, xhat, hs, nullptr);
         dim3 gc(nnode, nrhs);
-        k_far_couple<T, A><<<gc, 256, 0, st>>>(F, m.far_ptr.p, m.far_col.p, S, xhat, yhat, hs, nullptr);
+        k_far_couple_node<T, A><<<gc, 256, 0, st>>>(F, m.far_ptr.p, m.far_col.p, S, xhat, yhat, hs, nullptr);
     }
     const int NR = 16;
     dim3 go(m.kt.nleaf, cdiv(m.max_leaf_size, NR), nrhs);

@@ -268,6 +268,8 @@ struct OpData {
     DBuf<double> xhat, yhat;           // nnode * k * ws_nrhs
     DBuf<float> xhat32, yhat32;
     DBuf<double> P64;                  // leaf-level projections nlev * nleaf * k * nrhs
+    DBuf<double> ye64;                 // per admissible block coupling products nfar * k * nrhs
+    DBuf<float> ye32;
     DBuf<float> P32;
     cudaStream_t side = nullptr;       // far-field branch of the apply
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
