@@ -497,7 +497,7 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
     }
     const bool bf = b.precision == VFD_BF16;
     size_t nh = 0, nc = 0;
-    b.max_panel_w = b.max_k = b.max_kp = b.max_leaf = 0;
+    b.max_panel_w = b.max_k = b.max_kp = b.max_leaf = b.max_mt = 0;
     b.any_far = false;
     for (OpData *op : b.ops) {
         const MeshData &m = *op->m;
@@ -505,12 +505,13 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
         VFD_REQUIRE(op->precision != VFD_FP64, VFD_EINVAL, "batched apply needs VFD_FP32 or VFD_BF16 operators");
         VFD_REQUIRE(m.max_leaf_size <= 64, VFD_EUNSUPPORTED, "batched apply needs leaves of at most 64 DoFs");
         if (m.nfar > 0) {
-            const int kp = (m.k + 7) & ~7;
+            build_far_lowp(m, *op, st);
+            const int kp = op->far_kp, mt = (m.kt.L - m.far_lmin + 1) * kp;
             nh += (size_t)m.kt.nnode * kp * R;
-            nc += (size_t)m.kt.nnode * (R / RT);
+            nc += (size_t)m.kt.nleaf * mt * R;
             b.any_far = true;
             b.max_kp = std::max(b.max_kp, kp);
-            build_far_lowp(m, *op, st);
+            b.max_mt = std::max(b.max_mt, mt);
         }
         b.max_panel_w = std::max(b.max_panel_w, m.max_panel_w);
         b.max_k = std::max(b.max_k, m.k);
@@ -518,12 +519,11 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
     }
     VFD_REQUIRE((near_smem_bytes<float, 32, 3>(b.max_panel_w) <= 227 * 1024), VFD_EUNSUPPORTED,
                 "batched apply: near panel too wide");
-    VFD_REQUIRE(b.max_kp <= 64 && far_batched_smem(b.max_kp) <= 227 * 1024, VFD_EUNSUPPORTED,
+    VFD_REQUIRE(b.max_kp <= 64 && far_batched_smem(b.max_kp, b.max_mt) <= 227 * 1024, VFD_EUNSUPPORTED,
                 "batched apply: rank too large for the far-field tiles");
     b.xhat.alloc(std::max<size_t>(nh, 1));
     b.yhat.alloc(std::max<size_t>(nh, 1));
-    b.fcnt.alloc(std::max<size_t>(nc, 1));
-    b.fcnt.zero(st);
+    b.fpart.alloc(std::max<size_t>(nc, 1));
     b.y2.alloc((size_t)(KSPLIT_MAX - 1) * b.ntot * R);
     b.xc.alloc((size_t)b.ntot * R * 2);   // x in BF16 for the tcgen05 kernel
     if (!b.tc_err.p) {
@@ -570,17 +570,17 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
         e.poff = m.panel_off.p;
         e.D = bf ? (const void *)op.D16.p : (const void *)op.D32t.p;
         e.kp = op.far_kp;
-        e.Ul = op.Up_lp.p;
-        e.E = op.Ep_lp.p;
+        e.Ulf = op.Up_lp.p;
+        e.mt = m.nfar > 0 ? (m.kt.L - m.far_lmin + 1) * op.far_kp : 0;
         e.S = op.Sp_lp.p;
         e.val = op.valBM32.p;
         e.diag = op.precision == VFD_FP32 ? op.diag32.p : nullptr;   // folded B + M (TF32 panels only)
         e.xhat = b.xhat.p + ho;
         e.yhat = b.yhat.p + ho;
-        e.cnt = b.fcnt.p + co;
+        e.part = b.fpart.p + co;
         if (m.nfar > 0) {
             ho += (size_t)m.kt.nnode * op.far_kp * R;
-            co += (size_t)m.kt.nnode * (R / RT);
+            co += (size_t)m.kt.nleaf * e.mt * R;
         }
         std::vector<int> kb_h, ke_h, pw_h, goff_h;
         std::vector<int64_t> poff_h;

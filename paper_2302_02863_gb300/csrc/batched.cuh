@@ -16,11 +16,12 @@ struct MrMesh {
     const int *kb, *ke, *pw, *gcol, *goff, *rowptr, *colidx, *fptr, *fcol;
     const int64_t *poff;
     const void *D;            // near panels (FP32 rounded to TF32, or BF16)
-    const void *Ul, *E, *S;   // leaf bases N x kp, transfers nnode x kp x kp, coupling nfar x kp x kp (rank padded)
+    const void *Ulf, *S;      // flattened bases N x mt (every far level, rank padded), coupling nfar x kp x kp
+    int mt;                   // nlev * kp
     const float *val;         // B + M in FP32 (CSR)
     const float *diag;        // diagonal of A in FP32 (compensated), B + M off it folded into D
     float *xhat, *yhat;       // far-field workspaces of this mesh: nnode x kp x R
-    int *cnt;                 // upsweep arrival counters, nnode x (R / 64), zero between launches
+    float *part;              // leaf projections of every level, nleaf x mt x R
 };
 
 // one (mesh, leaf) work item of the near-panel kernel, everything it needs in one load

@@ -1,26 +1,20 @@
 // Far field of the batched low-precision apply (the admissible blocks of K,
-// Sec. 5.3) for 64-RHS tiles, with the nested bases of the interpolation H^2
-// matrix (the transfer matrices of the last paragraph of Sec. 5.3):
+// Sec. 5.3) for 64-RHS tiles, with the bases of every level flattened
+// (Ul^(l) = U E ... E, the nested bases of the last paragraph of Sec. 5.3
+// multiplied out once per operator), so that no step waits on another level:
 //
-//   K1 upsweep   (CTA per leaf):  xhat_leaf = U_leaf^T X_leaf; then up the
-//                tree: the second child to finish computes
-//                xhat_parent = E_c1^T xhat_c1 + E_c2^T xhat_c2 (a counter per
-//                node picks the last arriver; the two children are always
-//                added in the same order, so the result is deterministic),
-//                up to the first level with admissible blocks;
-//   K2 coupling  (CTA per node):  yc_node = sum_e S_e xhat_col(e)  (eq.
-//                eq:triple_product_factored), blocks streamed through shared
-//                memory;
-//   K3 downsweep + expansion (CTA per leaf): t = yc at the leaf's ancestor on
-//                the first far level, then t = E_node t + yc_node down the
-//                leaf's path, and Y_leaf += U_leaf t.  Each leaf walks its own
-//                path (the ancestors' transfers are recomputed per leaf: a few
-//                small products that cost less than a level-by-level chain of
-//                launches).
+//   K1 projections (CTA per leaf): P_leaf = Ulf_leaf^T X_leaf, all levels at
+//                once (Ulf row i = [Ul^(lmin)[i], ..., Ul^(L)[i]]);
+//   K1b node sums  (CTA per node with admissible blocks): xhat_node = sum of
+//                the node's leaves' level-slices of P, in leaf order;
+//   K2 coupling    (CTA per node):  yc_node = sum_e S_e xhat_col(e)  (eq.
+//                eq:triple_product_factored);
+//   K3 expansion   (CTA per leaf):  Y_leaf += Ulf_leaf [yc of the leaf's
+//                ancestors, stacked by level].
 //
 // Matrices are stored in the operator's low precision (BF16, or FP32 rounded
-// to TF32) with the rank padded to kp = k rounded up to 8 (zero rows and
-// columns), products run on the tensor cores (mma.sync m16n8k8 TF32, FP32
+// to TF32) with the rank padded to kp = k rounded up to 8 (zero columns),
+// products run on the tensor cores (mma.sync m16n8k8 TF32, FP32
 // accumulation), vectors are FP32 in the interleaved layout [row][R].
 #include <cuda_bf16.h>
 
@@ -189,78 +183,90 @@ __device__ __forceinline__ void acc_add(float (&acc)[8][4], const float *src, si
 
 }  // namespace
 
-// shared memory of the three kernels (floats)
-static size_t fb_smem_up(int kp) { return 4 * ((size_t)64 * LDB + (size_t)64 * lda_t(kp) + 2 * (size_t)kp * LDB + 2 * (size_t)kp * lda_t(kp)); }
+// shared memory of the kernels (bytes); mt = nlev * kp, the flattened row width
+static size_t fb_smem_proj(int mt) { return 4 * ((size_t)64 * LDB + (size_t)64 * lda_t(mt)); }
 static size_t fb_smem_couple(int kp) { return 4 * ((size_t)kp * lda_t(kp) + (size_t)kp * LDB); }
-static size_t fb_smem_down(int kp) { return 4 * ((size_t)kp * lda_r(kp) + (size_t)kp * LDB + (size_t)64 * lda_r(kp)); }
+static size_t fb_smem_expand(int mt) { return 4 * ((size_t)64 * lda_r(mt) + (size_t)mt * LDB); }
 
 // ---------------------------------------------------------------------------
-// K1: leaf projections and the transfer upsweep (last arriver per node)
+// K1: leaf projections of every level, part[leaf][m][R-slice], m < mt
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(FT)
-k_fb_up(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
-        const int *skip, const int *mdone)
+k_fb_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
+          const int *skip, const int *mdone)
 {
     extern __shared__ __align__(16) float fsm[];
-    __shared__ int last;
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
     const MrMesh &M = ms[item.x];
-    const int kp = M.kp, rt = blockIdx.y * RT, fl = M.fl;
-    const int LA = lda_t(kp);
+    const int mt = M.mt, rt = blockIdx.y * RT;
+    const int LA = lda_t(mt);
     float *Xs = fsm;                 // [64][LDB]   x rows of the leaf
-    float *Us = Xs + 64 * LDB;       // [64][LA]    U rows of the leaf (A transposed)
-    float *Ho = Us + 64 * LA;        // [kp][LDB]   xhat of the CTA's current node
-    float *Hb = Ho + kp * LDB;       // [kp][LDB]   xhat of its sibling
-    float *E1 = Hb + kp * LDB;       // [kp][LA]    transfers of the two children (A transposed)
-    float *E2 = E1 + kp * LA;
-    const T *U = (const T *)M.Ul, *E = (const T *)M.E;
-    float *xhat = M.xhat;
-    const size_t hs = (size_t)kp * R;   // node stride of xhat
-    int node = fl + item.y;
+    float *Us = Xs + 64 * LDB;       // [64][LA]    Ulf rows of the leaf (A transposed)
+    const int node = M.fl + item.y;
     const int b = M.kb[node], na = M.ke[node] - b;
     const int npad = (na + 7) & ~7;
     stage_x(Xs, Xall + (size_t)(M.xoff + b) * R + rt, R, na, npad);
-    stage<T>(Us, LA, U + (size_t)b * kp, kp, na, npad);
+    stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt, mt, na, npad);
     __syncthreads();
-    float acc[8][4];
-    acc_zero(acc);
-    const bool mw = 16 * (threadIdx.x >> 5) < kp;   // this warp owns rows of the result
-    if (mw) cta_gemm<true>(acc, Us, LA, Xs, npad);
-    acc_store(acc, xhat + (size_t)node * hs + rt, R, kp, false);
-    acc_store(acc, Ho, LDB, kp, false);
-    int lev = M.L;
-    while (lev > M.lmin) {
-        const int par = (node - 1) / 2, c1 = 2 * par + 1, sib = node == c1 ? c1 + 1 : c1;
-        // the transfers are fixed data: fetch them before waiting for the sibling
-        stage<T>(E1, LA, E + (size_t)c1 * kp * kp, kp, kp, kp);
-        stage<T>(E2, LA, E + (size_t)(c1 + 1) * kp * kp, kp, kp, kp);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int prev = atomicAdd(M.cnt + (size_t)par * (R / RT) + blockIdx.y, 1);
-            last = prev == 1;
-            if (last) M.cnt[(size_t)par * (R / RT) + blockIdx.y] = 0;   // ready for the next launch
-        }
-        __syncthreads();
-        if (!last) return;
-        __threadfence();
-        stage_x(Hb, xhat + (size_t)sib * hs + rt, R, kp, kp);
-        __syncthreads();
-        // always child 1 then child 2, whichever CTA arrived last
-        const float *H1 = node == c1 ? Ho : Hb, *H2 = node == c1 ? Hb : Ho;
+    float *dst = M.part + (size_t)item.y * mt * R + rt;
+    for (int m0 = 0; m0 < mt; m0 += 64) {
+        float acc[8][4];
         acc_zero(acc);
-        if (mw) {
-            cta_gemm<true>(acc, E1, LA, H1, kp);
-            cta_gemm<true>(acc, E2, LA, H2, kp);
+        if (m0 + 16 * (threadIdx.x >> 5) < mt) cta_gemm<true>(acc, Us + m0, LA, Xs, npad);
+        acc_store(acc, dst + (size_t)m0 * R, R, min(64, mt - m0), false);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1b: node sums xhat[node][a][R-slice] = sum over the node's leaves of their
+// level-(node) slice of part, in leaf order
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_fb_nsum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip, const int *mdone)
+{
+    if (skip && *skip) return;
+    const int2 item = items[blockIdx.x];
+    if (mdone && mdone[item.x]) return;
+    const MrMesh &M = ms[item.x];
+    const int kp = M.kp, mt = M.mt, rt = blockIdx.y * RT, node = item.y;
+    int l = 0;
+    while ((2 << l) - 1 <= node) ++l;
+    const int span = 1 << (M.L - l), leaf0 = ((node + 1) << (M.L - l)) - 1 - M.fl;
+    const size_t hs = (size_t)kp * R;
+    const float *src = M.part + (size_t)leaf0 * mt * R + (size_t)(l - M.lmin) * kp * R + rt;
+    for (int e = threadIdx.x; e < kp * (RT / 4); e += blockDim.x) {
+        const int a = e / (RT / 4), q = e % (RT / 4);
+        // four interleaved partial sums (leaves j = 4t + u), combined in a fixed order
+        float4 p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float *base = src + (size_t)a * R;
+        int j = 0;
+        for (; j + 4 <= span; j += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 w = __ldcg((const float4 *)(base + (size_t)(j + u) * mt * R) + q);
+                p[u].x += w.x;
+                p[u].y += w.y;
+                p[u].z += w.z;
+                p[u].w += w.w;
+            }
+        for (int u = 0; j < span; ++j, ++u) {
+            const float4 w = __ldcg((const float4 *)(base + (size_t)j * mt * R) + q);
+            p[u].x += w.x;
+            p[u].y += w.y;
+            p[u].z += w.z;
+            p[u].w += w.w;
         }
-        __syncthreads();   // Ho read by every warp
-        acc_store(acc, xhat + (size_t)par * hs + rt, R, kp, false);
-        acc_store(acc, Ho, LDB, kp, false);
-        node = par;
-        --lev;
+        float4 v;
+        v.x = (p[0].x + p[1].x) + (p[2].x + p[3].x);
+        v.y = (p[0].y + p[1].y) + (p[2].y + p[3].y);
+        v.z = (p[0].z + p[1].z) + (p[2].z + p[3].z);
+        v.w = (p[0].w + p[1].w) + (p[2].w + p[3].w);
+        *(float4 *)(M.xhat + (size_t)node * hs + (size_t)a * R + rt + 4 * q) = v;
     }
 }
 
@@ -295,94 +301,129 @@ k_fb_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R
 }
 
 // ---------------------------------------------------------------------------
-// K3: downsweep along the leaf's path and expansion Y_leaf += U_leaf t
+// K3: expansion Y_leaf += Ulf_leaf [yc of the leaf's ancestors by level]
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(FT)
-k_fb_down(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
-          const int *skip, const int *mdone)
+k_fb_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
+            const int *skip, const int *mdone)
 {
     extern __shared__ __align__(16) float fsm[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
     const MrMesh &M = ms[item.x];
-    const int kp = M.kp, rt = blockIdx.y * RT, fl = M.fl, L = M.L, lmin = M.lmin;
-    const int LA = lda_r(kp);
-    float *Es = fsm;              // [kp][LA]  E_node (row-major A)
-    float *Ts = Es + kp * LA;     // [kp][LDB] the running t
-    float *Us = Ts + kp * LDB;    // [64][LA]  U rows of the leaf (row-major A)
-    const T *U = (const T *)M.Ul, *E = (const T *)M.E;
+    const int kp = M.kp, mt = M.mt, rt = blockIdx.y * RT, L = M.L, lmin = M.lmin;
+    const int LA = lda_r(mt);
+    float *Us = fsm;               // [64][LA]  Ulf rows of the leaf (row-major A)
+    float *Ys = Us + 64 * LA;      // [mt][LDB] the ancestors' yc, level by level
     const size_t hs = (size_t)kp * R;
-    const int leafnode = fl + item.y;
+    const int leafnode = M.fl + item.y;
     const int b = M.kb[leafnode], na = M.ke[leafnode] - b;
-    float acc[8][4];
     for (int l = lmin; l <= L; ++l) {
         const int node = ((leafnode + 1) >> (L - l)) - 1;
-        acc_zero(acc);
-        if (l > lmin) {
-            stage<T>(Es, LA, E + (size_t)node * kp * kp, kp, kp, kp);
-            __syncthreads();
-            if (16 * (threadIdx.x >> 5) < kp) cta_gemm<false>(acc, Es, LA, Ts, kp);
+        float *dst = Ys + (size_t)(l - lmin) * kp * LDB;
+        if (M.fptr[node + 1] > M.fptr[node]) {
+            stage_x(dst, M.yhat + (size_t)node * hs + rt, R, kp, kp);
+        } else {
+            for (int e = threadIdx.x; e < kp * (RT / 4); e += blockDim.x)
+                *(float4 *)(dst + (e / (RT / 4)) * LDB + 4 * (e % (RT / 4))) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (M.fptr[node + 1] > M.fptr[node]) acc_add(acc, M.yhat + (size_t)node * hs + rt, R, kp);
-        __syncthreads();   // Ts fully read
-        acc_store(acc, Ts, LDB, kp, false);
-        __syncthreads();
     }
     const int npad = (na + 15) & ~15;
-    stage<T>(Us, LA, U + (size_t)b * kp, kp, na, npad);
+    stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt, mt, na, npad);
     __syncthreads();
+    float acc[8][4];
     acc_zero(acc);
-    if (16 * (threadIdx.x >> 5) < npad) cta_gemm<false>(acc, Us, LA, Ts, kp);
+    if (16 * (threadIdx.x >> 5) < npad) cta_gemm<false>(acc, Us, LA, Ys, mt);
     acc_store(acc, Yall + (size_t)(M.xoff + b) * R + rt, R, na, true);
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t far_batched_smem(int kp) { return std::max(fb_smem_up(kp), std::max(fb_smem_couple(kp), fb_smem_down(kp))); }
-
-template <class T>
-static void far_attrs(int kp)
+// the largest shared memory of the far kernels for padded rank kp and mt = nlev * kp
+size_t far_batched_smem(int kp, int mt)
 {
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_up(kp)));
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_couple(kp)));
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_down(kp)));
+    return std::max(fb_smem_proj(mt), std::max(fb_smem_couple(kp), fb_smem_expand(mt)));
 }
 
-// upsweep and coupling (K1, K2) on stream `side`
+template <class T>
+static void far_attrs(int kp, int mt)
+{
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_proj(mt)));
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_couple(kp)));
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_expand(mt)));
+}
+
+// projections, node sums and coupling (K1, K1b, K2) on stream `side`
 void launch_far_side(BatchData &b, int R, const float *X, cudaStream_t side, const int *skip, const int *mdone)
 {
     const MrMesh *ms = (const MrMesh *)b.desc.p;
-    const int kp = b.max_kp;
+    const int kp = b.max_kp, mt = b.max_mt;
     dim3 gl(b.n_leaf_items, R / RT), gn(b.n_node_items, R / RT);
     if (b.precision == VFD_BF16) {
-        far_attrs<__nv_bfloat16>(kp);
-        k_fb_up<__nv_bfloat16><<<gl, FT, fb_smem_up(kp), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
-        if (b.n_node_items)
+        far_attrs<__nv_bfloat16>(kp, mt);
+        k_fb_proj<__nv_bfloat16><<<gl, FT, fb_smem_proj(mt), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip,
+                                                                     mdone);
+    } else {
+        far_attrs<float>(kp, mt);
+        k_fb_proj<float><<<gl, FT, fb_smem_proj(mt), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
+    }
+    if (b.n_node_items) {
+        k_fb_nsum<<<gn, 256, 0, side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
+        if (b.precision == VFD_BF16)
             k_fb_couple<__nv_bfloat16><<<gn, FT, fb_smem_couple(kp), side>>>(ms, (const int2 *)b.node_items.p, R, skip,
                                                                              mdone);
-    } else {
-        far_attrs<float>(kp);
-        k_fb_up<float><<<gl, FT, fb_smem_up(kp), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
-        if (b.n_node_items)
+        else
             k_fb_couple<float><<<gn, FT, fb_smem_couple(kp), side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
     }
     VFD_CUDA(cudaGetLastError());
 }
 
-// downsweep and expansion (K3) on stream `st`, adding into Y
+// expansion (K3) on stream `st`, adding into Y
 void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone)
 {
     const MrMesh *ms = (const MrMesh *)b.desc.p;
-    const int kp = b.max_kp;
+    const int mt = b.max_mt;
     dim3 gl(b.n_leaf_items, R / RT);
     if (b.precision == VFD_BF16)
-        k_fb_down<__nv_bfloat16><<<gl, FT, fb_smem_down(kp), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
+        k_fb_expand<__nv_bfloat16><<<gl, FT, fb_smem_expand(mt), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip,
+                                                                       mdone);
     else
-        k_fb_down<float><<<gl, FT, fb_smem_down(kp), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
+        k_fb_expand<float><<<gl, FT, fb_smem_expand(mt), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
     VFD_CUDA(cudaGetLastError());
+}
+
+// flattened bases of every far level in the operator's low precision:
+// out[i][lv * kp + a] = (U_i E_{c_L} ... E_{c_{l+1}})[a], l = lmin + lv, c_j the
+// level-j ancestor of row i's leaf (zero for a >= k); thread per row
+__global__ void k_flat_bases(int N, int k, int kp, int nlev, int lmin, int L, int fl, const int *__restrict__ vleaf,
+                             const double *__restrict__ U, const double *__restrict__ E, int bf, void *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double t[KMAX], t2[KMAX];
+    for (int a = 0; a < k; ++a) t[a] = U[(size_t)i * k + a];
+    const int leafnode = fl + vleaf[i], mt = nlev * kp;
+    for (int l = L; l >= lmin; --l) {
+        if (l < L) {   // t = t E_c, c the level-(l+1) ancestor
+            const int c = ((leafnode + 1) >> (L - (l + 1))) - 1;
+            const double *Ec = E + (size_t)c * k * k;
+            for (int a = 0; a < k; ++a) {
+                double v = 0.0;
+                for (int be = 0; be < k; ++be) v += t[be] * Ec[(size_t)be * k + a];
+                t2[a] = v;
+            }
+            for (int a = 0; a < k; ++a) t[a] = t2[a];
+        }
+        const size_t o = (size_t)i * mt + (size_t)(l - lmin) * kp;
+        for (int a = 0; a < kp; ++a) {
+            const double v = a < k ? t[a] : 0.0;
+            if (bf) ((__nv_bfloat16 *)out)[o + a] = __double2bfloat16(v);
+            else ((float *)out)[o + a] = __uint_as_float(tf32(__double2float_rn(v)));
+        }
+    }
 }
 
 // padded low-precision copies: nmat row-major matrices srows x scols (FP64)
@@ -419,8 +460,11 @@ void build_far_lowp(const MeshData &m, OpData &op, cudaStream_t st)
     const int k = m.k_in ? m.k_in : m.k, kp = (k + 7) & ~7, bf = op.precision == VFD_BF16 ? 1 : 0;
     const int nlev = m.kt.L - m.far_lmin + 1;
     const double *U = m.k_in ? m.U_in64.p : m.Ul64.p + (size_t)(nlev - 1) * m.N * m.k;   // leaf bases
-    pad_copy(1, m.N, k, m.N, kp, U, bf, op.Up_lp, st);
-    pad_copy(m.kt.nnode, k, k, kp, kp, m.k_in ? m.E_in64.p : m.E64.p, bf, op.Ep_lp, st);
+    const int mt = nlev * kp;
+    op.Up_lp.alloc((size_t)m.N * mt * (bf ? 2 : 4));
+    k_flat_bases<<<cdiv(m.N, 128), 128, 0, st>>>(m.N, k, kp, nlev, m.far_lmin, m.kt.L, m.kt.first_leaf(), m.vleaf.p, U,
+                                                m.k_in ? m.E_in64.p : m.E64.p, bf, op.Up_lp.p);
+    VFD_CUDA(cudaGetLastError());
     pad_copy(m.nfar, k, k, kp, kp, m.k_in ? op.S64_in.p : op.S64.p, bf, op.Sp_lp, st);
     op.far_kp = kp;
 }

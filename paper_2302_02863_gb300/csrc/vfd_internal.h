@@ -254,7 +254,7 @@ struct OpData {
                                        //   diagonal is folded into its panels D32t
     bool bm_folded = false;            // the batched panels (D16 + Dtc, or D32t + diag32) are built
     int far_kp = 0;                    // padded rank of the batched far-field copies (0: not built)
-    DBuf<unsigned char> Up_lp, Ep_lp, Sp_lp;   // U, E, S in the operator's low precision, rank padded (batched path)
+    DBuf<unsigned char> Up_lp, Sp_lp;   // flattened bases (N x nlev kp) and S in the operator's low precision (batched path)
     DBuf<float> valBM32;               // FP32 copy of B + M (inner operator of refinement)
     bool comp_done = false;            // valBM32's diagonal compensated (batched path, first use)
     // the batch of one used by the batched (multi-RHS) low-precision apply / solve
@@ -320,7 +320,8 @@ struct BatchData {
     float near_cfg_us[32] = {0};        // the timings of the candidates (0: not run)
     bool any_far = false;
     DBuf<float> xhat, yhat, y2;         // far-field workspaces (all meshes), near partials of a split
-    DBuf<int> fcnt;                     // upsweep arrival counters (all meshes)
+    DBuf<float> fpart;                  // far-field leaf projections (all meshes)
+    int max_mt = 0;                     // largest flattened basis width nlev * kp
     DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
     DBuf<unsigned char> xc;             // x in BF16 for the tcgen05 kernel ([ntot][R])
     DBuf<int> tc_err;                   // set by the tcgen05 kernel when a pipeline wait expires
@@ -409,7 +410,7 @@ bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X
                      const int *skip, const int *mdone);
 // far_batched.cu (nested H^2 far field of the batched apply)
 void build_far_lowp(const MeshData &m, OpData &op, cudaStream_t st);
-size_t far_batched_smem(int kp);
+size_t far_batched_smem(int kp, int mt);
 void launch_far_side(BatchData &b, int R, const float *X, cudaStream_t side, const int *skip, const int *mdone);
 void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone);
 void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st);
