@@ -384,6 +384,8 @@ struct RhoParams {
     int d, k, p, Lt, nQ, nQint, nv;
     const int *tt_begin, *tt_end, *tt_perm, *st_begin, *st_end, *st_perm;
     const double *tt_cheb, *yt;
+    const double *tt_lo, *tt_hi;     // target boxes
+    double tref[PMAX], wref[PMAX];   // first-kind Chebyshev points of [-1, 1] and their barycentric weights
     const int *rnear_ptr, *rnear_col;
     const double *qx, *qw, *qs, *qlk;
     const int *qcell, *cells;
@@ -459,30 +461,46 @@ __global__ void __launch_bounds__(128) k_rho_points(RhoParams P)
             // far part: sum over the ancestors of the leaf of l^node(q) . yhat_node
             int nd = node;
             for (int lev = P.Lt; lev >= 0; --lev) {
-                const double *ch = P.tt_cheb + (size_t)nd * P.k * d;
+                // 1D Lagrange values on the node's box from the reference points:
+                // l_a(t) = w_a prod_{b != a} (t - t_b), t the point in [-1, 1] box
+                // coordinates (prefix and suffix products, no divisions per a)
                 double l1[3][PMAX];
-                int stride = 1;
                 for (int c = 0; c < d; ++c) {
+                    const double lo = P.tt_lo[(size_t)nd * d + c], hi = P.tt_hi[(size_t)nd * d + c];
+                    const double t = (x[c] - 0.5 * (lo + hi)) / (0.5 * (hi - lo));
+                    double df[PMAX], pre = 1.0;
+                    for (int a = 0; a < P.p; ++a) df[a] = t - P.tref[a];
                     for (int a = 0; a < P.p; ++a) {
-                        double na = ch[(size_t)(a * stride) * d + c], v = 1.0;
-                        for (int bb = 0; bb < P.p; ++bb)
-                            if (bb != a) {
-                                double nb = ch[(size_t)(bb * stride) * d + c];
-                                v *= (x[c] - nb) / (na - nb);
-                            }
-                        l1[c][a] = v;
+                        l1[c][a] = pre;
+                        pre *= df[a];
                     }
-                    stride *= P.p;
+                    double suf = 1.0;
+                    for (int a = P.p - 1; a >= 0; --a) {
+                        l1[c][a] *= suf * P.wref[a];
+                        suf *= df[a];
+                    }
                 }
+                // tensor basis alpha = a0 + p a1 (+ p^2 a2): nested loops, no index division
                 const double *y = P.yt + (size_t)nd * P.k;
-                for (int al = 0; al < P.k; ++al) {
-                    int r = al;
-                    double v = 1.0;
-                    for (int c = 0; c < d; ++c) {
-                        v *= l1[c][r % P.p];
-                        r /= P.p;
+                const int pp = P.p;
+                if (d == 1) {
+                    for (int a0 = 0; a0 < pp; ++a0) acc += l1[0][a0] * y[a0];
+                } else if (d == 2) {
+                    for (int a1 = 0; a1 < pp; ++a1) {
+                        double s1 = 0.0;
+                        for (int a0 = 0; a0 < pp; ++a0) s1 += l1[0][a0] * y[a1 * pp + a0];
+                        acc += l1[1][a1] * s1;
                     }
-                    acc += v * y[al];
+                } else {
+                    for (int a2 = 0; a2 < pp; ++a2) {
+                        double s2 = 0.0;
+                        for (int a1 = 0; a1 < pp; ++a1) {
+                            double s1 = 0.0;
+                            for (int a0 = 0; a0 < pp; ++a0) s1 += l1[0][a0] * y[(a2 * pp + a1) * pp + a0];
+                            s2 += l1[1][a1] * s1;
+                        }
+                        acc += l1[2][a2] * s2;
+                    }
                 }
                 nd = (nd - 1) / 2;
             }
@@ -539,6 +557,16 @@ void launch_density(const MeshData &m, OpData &op, cudaStream_t st)
     P.st_perm = m.st_perm.p;
     P.tt_cheb = m.tt_cheb.p;
     P.yt = yt.p;
+    P.tt_lo = m.tt_lo.p;
+    P.tt_hi = m.tt_hi.p;
+    for (int a = 0; a < PMAX; ++a) P.tref[a] = P.wref[a] = 0.0;
+    for (int a = 0; a < m.p; ++a) P.tref[a] = std::cos((2.0 * a + 1.0) * M_PI / (2.0 * m.p));
+    for (int a = 0; a < m.p; ++a) {
+        double w = 1.0;
+        for (int b = 0; b < m.p; ++b)
+            if (b != a) w *= P.tref[a] - P.tref[b];
+        P.wref[a] = 1.0 / w;
+    }
     P.rnear_ptr = m.rnear_ptr.p;
     P.rnear_col = m.rnear_col.p;
     P.qx = m.qx.p;

@@ -75,17 +75,17 @@ __device__ __forceinline__ int piece(const float *p, float *v)
 }
 
 // rows [0, nrow) of kp columns (kp a multiple of 8) of a row-major global
-// matrix with row stride kp into shared memory (row stride lds, FP32), rows
+// matrix with row stride sstride (default kp) into shared memory (row stride lds, FP32), rows
 // [nrow, npad) zero; 16-byte loads, eight threads per row
 template <class T>
-__device__ __forceinline__ void stage(float *dst, int lds, const T *src, int kp, int nrow, int npad)
+__device__ __forceinline__ void stage(float *dst, int lds, const T *src, int kp, int nrow, int npad, int sstride = 0)
 {
     constexpr int E = 16 / (int)sizeof(T);
-    const int cpr = kp / E, sub = threadIdx.x & 7;
+    const int cpr = kp / E, sub = threadIdx.x & 7, ss = sstride ? sstride : kp;
     for (int r = threadIdx.x >> 3; r < npad; r += blockDim.x >> 3)
         for (int c = sub; c < cpr; c += 8) {
             float v[8];
-            if (r < nrow) piece(src + (size_t)r * kp + c * E, v);
+            if (r < nrow) piece(src + (size_t)r * ss + c * E, v);
             else
 #pragma unroll
                 for (int j = 0; j < E; ++j) v[j] = 0.f;
@@ -184,9 +184,12 @@ __device__ __forceinline__ void acc_add(float (&acc)[8][4], const float *src, si
 }  // namespace
 
 // shared memory of the kernels (bytes); mt = nlev * kp, the flattened row width
-static size_t fb_smem_proj(int mt) { return 4 * ((size_t)64 * LDB + (size_t)64 * lda_t(mt)); }
+// the flattened width is processed in chunks of fb_mc(kp, mt) columns (whole levels)
+__host__ __device__ constexpr int fb_mc(int kp, int mt) { return kp * (kp >= 128 ? 1 : 128 / kp) < mt ? kp * (kp >= 128 ? 1 : 128 / kp) : mt; }
+// host: shared memory for column chunks of at most mcmax = min(128, largest mt) columns
+static size_t fb_smem_proj(int mcmax) { return 4 * ((size_t)64 * LDB + (size_t)64 * lda_t(mcmax)); }
 static size_t fb_smem_couple(int kp) { return 4 * ((size_t)kp * lda_t(kp) + (size_t)kp * LDB); }
-static size_t fb_smem_expand(int mt) { return 4 * ((size_t)64 * lda_r(mt) + (size_t)mt * LDB); }
+static size_t fb_smem_expand(int mcmax) { return 4 * ((size_t)64 * lda_r(mcmax) + (size_t)mcmax * LDB); }
 
 // ---------------------------------------------------------------------------
 // K1: leaf projections of every level, part[leaf][m][R-slice], m < mt
@@ -201,22 +204,26 @@ k_fb_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, 
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
     const MrMesh &M = ms[item.x];
-    const int mt = M.mt, rt = blockIdx.y * RT;
-    const int LA = lda_t(mt);
+    const int mt = M.mt, rt = blockIdx.y * RT, mc = fb_mc(M.kp, mt);
+    const int LA = lda_t(mc);
     float *Xs = fsm;                 // [64][LDB]   x rows of the leaf
-    float *Us = Xs + 64 * LDB;       // [64][LA]    Ulf rows of the leaf (A transposed)
+    float *Us = Xs + 64 * LDB;       // [64][LA]    a column chunk of the leaf's Ulf rows (A transposed)
     const int node = M.fl + item.y;
     const int b = M.kb[node], na = M.ke[node] - b;
     const int npad = (na + 7) & ~7;
     stage_x(Xs, Xall + (size_t)(M.xoff + b) * R + rt, R, na, npad);
-    stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt, mt, na, npad);
-    __syncthreads();
     float *dst = M.part + (size_t)item.y * mt * R + rt;
-    for (int m0 = 0; m0 < mt; m0 += 64) {
-        float acc[8][4];
-        acc_zero(acc);
-        if (m0 + 16 * (threadIdx.x >> 5) < mt) cta_gemm<true>(acc, Us + m0, LA, Xs, npad);
-        acc_store(acc, dst + (size_t)m0 * R, R, min(64, mt - m0), false);
+    for (int c0 = 0; c0 < mt; c0 += mc) {
+        const int nc = min(mc, mt - c0);
+        __syncthreads();   // the previous chunk's products are done with Us
+        stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt + c0, nc, na, npad, mt);
+        __syncthreads();
+        for (int m0 = 0; m0 < nc; m0 += 64) {
+            float acc[8][4];
+            acc_zero(acc);
+            if (m0 + 16 * (threadIdx.x >> 5) < nc) cta_gemm<true>(acc, Us + m0, LA, Xs, npad);
+            acc_store(acc, dst + (size_t)(c0 + m0) * R, R, min(64, nc - m0), false);
+        }
     }
 }
 
@@ -313,29 +320,34 @@ k_fb_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
     const MrMesh &M = ms[item.x];
-    const int kp = M.kp, mt = M.mt, rt = blockIdx.y * RT, L = M.L, lmin = M.lmin;
-    const int LA = lda_r(mt);
-    float *Us = fsm;               // [64][LA]  Ulf rows of the leaf (row-major A)
-    float *Ys = Us + 64 * LA;      // [mt][LDB] the ancestors' yc, level by level
+    const int kp = M.kp, mt = M.mt, rt = blockIdx.y * RT, L = M.L, lmin = M.lmin, mc = fb_mc(kp, mt);
+    const int LA = lda_r(mc);
+    float *Us = fsm;               // [64][LA]  a column chunk of the leaf's Ulf rows (row-major A)
+    float *Ys = Us + 64 * LA;      // [mc][LDB] the matching levels of the ancestors' yc
     const size_t hs = (size_t)kp * R;
     const int leafnode = M.fl + item.y;
     const int b = M.kb[leafnode], na = M.ke[leafnode] - b;
-    for (int l = lmin; l <= L; ++l) {
-        const int node = ((leafnode + 1) >> (L - l)) - 1;
-        float *dst = Ys + (size_t)(l - lmin) * kp * LDB;
-        if (M.fptr[node + 1] > M.fptr[node]) {
-            stage_x(dst, M.yhat + (size_t)node * hs + rt, R, kp, kp);
-        } else {
-            for (int e = threadIdx.x; e < kp * (RT / 4); e += blockDim.x)
-                *(float4 *)(dst + (e / (RT / 4)) * LDB + 4 * (e % (RT / 4))) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
     const int npad = (na + 15) & ~15;
-    stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt, mt, na, npad);
-    __syncthreads();
     float acc[8][4];
     acc_zero(acc);
-    if (16 * (threadIdx.x >> 5) < npad) cta_gemm<false>(acc, Us, LA, Ys, mt);
+    for (int c0 = 0; c0 < mt; c0 += mc) {
+        const int nc = min(mc, mt - c0);
+        __syncthreads();   // the previous chunk's products are done with Us, Ys
+        for (int lc = 0; lc < nc / kp; ++lc) {
+            const int l = lmin + c0 / kp + lc;
+            const int node = ((leafnode + 1) >> (L - l)) - 1;
+            float *dst = Ys + (size_t)lc * kp * LDB;
+            if (M.fptr[node + 1] > M.fptr[node]) {
+                stage_x(dst, M.yhat + (size_t)node * hs + rt, R, kp, kp);
+            } else {
+                for (int e = threadIdx.x; e < kp * (RT / 4); e += blockDim.x)
+                    *(float4 *)(dst + (e / (RT / 4)) * LDB + 4 * (e % (RT / 4))) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt + c0, nc, na, npad, mt);
+        __syncthreads();
+        if (16 * (threadIdx.x >> 5) < npad) cta_gemm<false>(acc, Us, LA, Ys, nc);
+    }
     acc_store(acc, Yall + (size_t)(M.xoff + b) * R + rt, R, na, true);
 }
 
@@ -345,15 +357,16 @@ k_fb_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R
 // the largest shared memory of the far kernels for padded rank kp and mt = nlev * kp
 size_t far_batched_smem(int kp, int mt)
 {
-    return std::max(fb_smem_proj(mt), std::max(fb_smem_couple(kp), fb_smem_expand(mt)));
+    const int mc = std::min(128, mt);
+    return std::max(fb_smem_proj(mc), std::max(fb_smem_couple(kp), fb_smem_expand(mc)));
 }
 
 template <class T>
 static void far_attrs(int kp, int mt)
 {
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_proj(mt)));
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_proj(std::min(128, mt))));
     VFD_CUDA(cudaFuncSetAttribute(k_fb_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_couple(kp)));
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_expand(mt)));
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_expand(std::min(128, mt))));
 }
 
 // projections, node sums and coupling (K1, K1b, K2) on stream `side`
@@ -364,11 +377,11 @@ void launch_far_side(BatchData &b, int R, const float *X, cudaStream_t side, con
     dim3 gl(b.n_leaf_items, R / RT), gn(b.n_node_items, R / RT);
     if (b.precision == VFD_BF16) {
         far_attrs<__nv_bfloat16>(kp, mt);
-        k_fb_proj<__nv_bfloat16><<<gl, FT, fb_smem_proj(mt), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip,
+        k_fb_proj<__nv_bfloat16><<<gl, FT, fb_smem_proj(std::min(128, mt)), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip,
                                                                      mdone);
     } else {
         far_attrs<float>(kp, mt);
-        k_fb_proj<float><<<gl, FT, fb_smem_proj(mt), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
+        k_fb_proj<float><<<gl, FT, fb_smem_proj(std::min(128, mt)), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
     }
     if (b.n_node_items) {
         k_fb_nsum<<<gn, 256, 0, side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
@@ -388,10 +401,10 @@ void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *
     const int mt = b.max_mt;
     dim3 gl(b.n_leaf_items, R / RT);
     if (b.precision == VFD_BF16)
-        k_fb_expand<__nv_bfloat16><<<gl, FT, fb_smem_expand(mt), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip,
+        k_fb_expand<__nv_bfloat16><<<gl, FT, fb_smem_expand(std::min(128, mt)), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip,
                                                                        mdone);
     else
-        k_fb_expand<float><<<gl, FT, fb_smem_expand(mt), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
+        k_fb_expand<float><<<gl, FT, fb_smem_expand(std::min(128, mt)), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
     VFD_CUDA(cudaGetLastError());
 }
 
