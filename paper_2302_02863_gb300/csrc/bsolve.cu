@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
 // cluster's leaves), z += zc[cluster of the row]
 // ---------------------------------------------------------------------------
 constexpr int PC_TILE = 64;   // columns per pass of the preconditioner kernels
-constexpr int PC_CROWS = 32;  // coarse rows per CTA
+constexpr int PC_CROWS = 4;   // coarse rows per CTA (one per thread group: many CTAs)
 
 // leaf item: mesh, first row (global), rows, block stride, global leaf index
 __global__ void __launch_bounds__(256) k_bp_local(Seg S, const int *__restrict__ items,
