@@ -112,6 +112,13 @@ typedef struct {
                            operator only has to match the FP64 operator to its own rounding
                            level (2^-11 or 2^-8), so a lower order serves; the solves still
                            converge to the solution of the FP64 operator.  Default 0. */
+    double recompress_tol;  /* algebraic recompression of the far field of K of VFD_FP64 operators
+                           (Sec. 5.3, last paragraph), done by vfd_assemble: every node's basis
+                           is orthogonalised and cut to the singular directions of its coupling
+                           row above recompress_tol x the largest over all nodes; ranks padded
+                           per level.  The apply, the solves and the batched solves' FP64
+                           residuals use the recompressed far field; vfd_grad differentiates
+                           the interpolation operator before recompression.  0 = off (default). */
 } vfd_mesh_opts;
 
 /* Scalar field on R^d: value = squash(c0 + sum of terms), or a P1 field.
@@ -120,9 +127,10 @@ typedef struct {
  * tbump rows   (x0,y0,z0, amp, ell):            amp prod_i exp(-1/(1-r_i^2)), r_i = 2(x_i-x0_i)/ell, |r_i|<1
  * squash = 1: lo + (hi-lo)/(1+exp(-v)).
  * Row arrays are host memory, read during the call.  kind = VFD_FIELD_NODAL
- * takes `nodal`, values at the n_vert mesh vertices (host or device); it is
- * supported only when the operator has no low-rank part (lambda = 0 and
- * rho_lambda = 0), where every evaluation point lies in a known cell. */
+ * takes `nodal`, values at the n_vert mesh vertices (host or device): the P1
+ * interpolant at element and singular-rule points, and at a Chebyshev node
+ * the interpolant at the node's nearest point of the mesh (located once per
+ * mesh on the first such assembly). */
 enum { VFD_FIELD_ANALYTIC = 0, VFD_FIELD_NODAL = 1 };
 typedef struct {
     int kind;
@@ -376,6 +384,12 @@ vfd_status vfd_grad(vfd_op_t op, const double *U, const double *Lam, int64_t nrh
  * the point nearest to stored vertex 0, 1, 2; interval: Gauss points left
  * to right in the stored orientation).  rho: host or device, n_qint doubles. */
 vfd_status vfd_op_rho(vfd_op_t op, double *rho, void *stream);
+
+/* Rank of every far level of the operator's FP64 far field, coarsest first:
+ * the interpolation rank p^d, or after recompression (recompress_tol > 0)
+ * the padded rank of each level.  *nlev = number of far levels (0 without
+ * admissible blocks); ranks (may be null) receives min(n, *nlev) entries. */
+vfd_status vfd_op_far_ranks(vfd_op_t op, int *ranks, int n, int *nlev);
 
 /* Device time per assembly phase (VFD_T_* order) of the vfd_assemble call
  * that created op, if it was given VFD_ASSEMBLE_TIMED; ms: host, n entries

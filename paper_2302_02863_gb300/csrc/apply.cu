@@ -48,10 +48,22 @@ __device__ __forceinline__ void fma_v(const float4 a, const float4 x, float &s0,
     s1 = fmaf(a.w, x.w, s1);
 }
 
+constexpr int FV_MAXLEV = 24;
 struct FarView {
     int use;         // apply K_far
-    int lmin, L, nlev, k, N;
+    int lmin, L, nlev, k, N;    // k: the node stride of xhat / yhat / the projections (largest rank)
+    int kl[FV_MAXLEV];          // rank of each far level (k, or less after recompression)
+    long long uo[FV_MAXLEV];    // offset of each level's flattened basis (row stride kl[lv])
+    const long long *so;        // offset of each admissible block's coupling (kl x kl), or null: e k^2
+    const int *bk;              // rank of each admissible block, or null: k
 };
+
+__device__ __forceinline__ int fv_level(int node)
+{
+    int l = 0;
+    while ((2 << l) - 1 <= node) ++l;
+    return l;
+}
 
 // ---------------------------------------------------------------------------
 // 1. leaf-level projections  part[r][lv][leaf][a] = sum_{i in leaf} Ul^(lmin+lv)[i][a] x[i]
@@ -63,12 +75,12 @@ k_far_proj(FarView F, int fl, int nleaf, const int *__restrict__ kb, const int *
 {
     __shared__ A red[128];
     if (skip && *skip) return;
-    const int leaf = blockIdx.x, lv = blockIdx.y, r = blockIdx.z, k = F.k;
+    const int leaf = blockIdx.x, lv = blockIdx.y, r = blockIdx.z, k = F.kl[lv];
     const int b = kb[fl + leaf], e = ke[fl + leaf];
     const int kk = min(k, (int)blockDim.x);
     const int parts = blockDim.x / kk;
     const int al = threadIdx.x % kk, pt = threadIdx.x / kk;
-    const T *u = Ul + ((size_t)lv * F.N) * k;
+    const T *u = Ul + F.uo[lv];
     const double *x = X + (size_t)r * ld;
     for (int a0 = 0; a0 < k; a0 += kk) {
         A acc = 0;
@@ -79,7 +91,7 @@ k_far_proj(FarView F, int fl, int nleaf, const int *__restrict__ kb, const int *
         if (threadIdx.x < kk) {
             A s = 0;
             for (int q = 0; q < parts; ++q) s += red[q * kk + threadIdx.x];
-            part[(((size_t)r * F.nlev + lv) * nleaf + leaf) * k + a0 + threadIdx.x] = s;
+            part[(((size_t)r * F.nlev + lv) * nleaf + leaf) * F.k + a0 + threadIdx.x] = s;
         }
         __syncthreads();
     }
@@ -96,24 +108,23 @@ k_far_sum(FarView F, int nleaf, const A *__restrict__ part, A *__restrict__ xhat
 {
     __shared__ A red[128];
     if (skip && *skip) return;
-    const int k = F.k, node = (1 << F.lmin) - 1 + blockIdx.x, r = blockIdx.y;
-    int l = 0;
-    while ((2 << l) - 1 <= node) ++l;
-    const int lv = l - F.lmin, span = 1 << (F.L - l);
+    const int node = (1 << F.lmin) - 1 + blockIdx.x, r = blockIdx.y;
+    const int l = fv_level(node);
+    const int lv = l - F.lmin, span = 1 << (F.L - l), k = F.kl[lv], K = F.k;
     const int leaf0 = ((node + 1) << (F.L - l)) - 1 - ((1 << F.L) - 1);
     const int kk = min(k, (int)blockDim.x), parts = blockDim.x / kk;
     const int al = threadIdx.x % kk, pt = threadIdx.x / kk;
-    const A *p = part + (((size_t)r * F.nlev + lv) * nleaf + leaf0) * k;
+    const A *p = part + (((size_t)r * F.nlev + lv) * nleaf + leaf0) * K;
     for (int a0 = 0; a0 < k; a0 += kk) {
         A s = 0;
         if (pt < parts)
-            for (int j = pt; j < span; j += parts) s += p[(size_t)j * k + a0 + al];
+            for (int j = pt; j < span; j += parts) s += p[(size_t)j * K + a0 + al];
         red[threadIdx.x] = s;
         __syncthreads();
         if (threadIdx.x < kk) {
             A t = 0;
             for (int q = 0; q < parts; ++q) t += red[q * kk + threadIdx.x];
-            xhat[(size_t)r * hs + (size_t)node * k + a0 + threadIdx.x] = t;
+            xhat[(size_t)r * hs + (size_t)node * K + a0 + threadIdx.x] = t;
         }
         __syncthreads();
     }
@@ -164,10 +175,10 @@ k_far_couple(FarView F, int nfar, int nnode, const int *__restrict__ fptr, const
     if (skip && *skip) return;
     const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, r = blockIdx.y;
     if (e >= nfar) return;
-    const int k = F.k;
-    const T *sp = S + (size_t)e * k * k;
-    const A *xc = xhat + (size_t)r * hs + (size_t)fcol[e] * k;
-    A *out = ye + ((size_t)r * nfar + e) * k;
+    const int k = F.bk ? F.bk[e] : F.k;
+    const T *sp = S + (F.so ? (size_t)F.so[e] : (size_t)e * k * k);
+    const A *xc = xhat + (size_t)r * hs + (size_t)fcol[e] * F.k;
+    A *out = ye + ((size_t)r * nfar + e) * F.k;
     for (int a = lane; a < k; a += 64) {
         A r1, r2;
         couple_part(sp, xc, k, a, a + 32, r1, r2);
@@ -185,8 +196,10 @@ __global__ void k_far_couple_sum(FarView F, int nfar, int nnode, const int *__re
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nnode * k) return;
     const int node = t / k, a = t % k;
+    const int l = fv_level(node), kl = l >= F.lmin ? F.kl[l - F.lmin] : k;
     A s = 0;
-    for (int e = fptr[node]; e < fptr[node + 1]; ++e) s += ye[((size_t)r * nfar + e) * k + a];
+    if (a < kl)
+        for (int e = fptr[node]; e < fptr[node + 1]; ++e) s += ye[((size_t)r * nfar + e) * k + a];
     yhat[(size_t)r * hs + t] = s;
 }
 
@@ -197,7 +210,8 @@ k_far_couple_node(FarView F, const int *__restrict__ fptr, const int *__restrict
 {
     __shared__ A pt[8][KMAX];
     if (skip && *skip) return;
-    const int node = blockIdx.x, r = blockIdx.y, k = F.k;
+    const int node = blockIdx.x, r = blockIdx.y, K = F.k;
+    const int l = fv_level(node), k = l >= F.lmin ? F.kl[l - F.lmin] : K;
     const int e0 = fptr[node], ne = fptr[node + 1] - e0;
     const A *xh = xhat + (size_t)r * hs;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,8 +219,8 @@ k_far_couple_node(FarView F, const int *__restrict__ fptr, const int *__restrict
     for (int eb = 0; eb < ne; eb += 8) {
         const int e = eb + warp;
         if (e < ne) {
-            const T *sp = S + (size_t)(e0 + e) * k * k;
-            const A *xc = xh + (size_t)fcol[e0 + e] * k;
+            const T *sp = S + (F.so ? (size_t)F.so[e0 + e] : (size_t)(e0 + e) * k * k);
+            const A *xc = xh + (size_t)fcol[e0 + e] * K;
             for (int a = lane; a < k; a += 64) {
                 A r1, r2;
                 couple_part(sp, xc, k, a, a + 32, r1, r2);
@@ -219,7 +233,7 @@ k_far_couple_node(FarView F, const int *__restrict__ fptr, const int *__restrict
             for (int w = 0; w < 8 && eb + w < ne; ++w) tot += pt[w][threadIdx.x];
         __syncthreads();
     }
-    if ((int)threadIdx.x < k) yhat[(size_t)r * hs + (size_t)node * k + threadIdx.x] = tot;
+    if ((int)threadIdx.x < K) yhat[(size_t)r * hs + (size_t)node * K + threadIdx.x] = (int)threadIdx.x < k ? tot : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -291,22 +305,6 @@ k_near_csr(int fl, int NR, const int *__restrict__ kb, const int *__restrict__ k
                     for (; c < nv; c += 32) fma_v(row[c], xv[c], s, s);
                     acc = (double)s;
                 }
-                if (F.use) {
-                    // lanes cover (level, alpha) pairs: 32/k levels per instruction when k <= 32
-                    A fa = 0;
-                    const int per = F.k <= 32 ? 32 / F.k : 1;
-                    const int kk = F.k <= 32 ? F.k : 32;
-                    for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
-                        const int l = l0 + lane / kk;
-                        if (lane / kk < per && l <= F.L) {
-                            const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
-                            const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
-                            const A *y = yh + (size_t)node * F.k;
-                            for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
-                        }
-                    }
-                    acc += (double)fa;
-                }
                 if (val) {
 #pragma unroll 1
                     for (int c = rowptr[i] + lane; c < rowptr[i + 1]; c += 32) acc = fma(val[c], x[colidx[c]], acc);
@@ -349,8 +347,6 @@ k_far_expand(FarView F, int fl, const int *__restrict__ leaf_of, const T *__rest
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5, r = blockIdx.y;
     const int i0 = blockIdx.x * 4 * nw + warp;
     const A *yh = yhat + (size_t)r * hs;
-    const int per = F.k <= 32 ? 32 / F.k : 1;
-    const int kk = F.k <= 32 ? F.k : 32;
     double part[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -358,14 +354,12 @@ k_far_expand(FarView F, int fl, const int *__restrict__ leaf_of, const T *__rest
         A fa = 0;
         if (i < F.N) {
             const int lf = leaf_of[i];
-            for (int l0 = F.lmin; l0 <= F.L; l0 += per) {
-                const int l = l0 + lane / kk;
-                if (lane / kk < per && l <= F.L) {
-                    const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
-                    const T *u = Ul + ((size_t)(l - F.lmin) * F.N + i) * F.k;
-                    const A *y = yh + (size_t)node * F.k;
-                    for (int al = lane % kk; al < F.k; al += kk) fa += (A)u[al] * y[al];
-                }
+            for (int l = F.lmin; l <= F.L; ++l) {
+                const int lv = l - F.lmin, kl = F.kl[lv];
+                const int node = ((fl + lf + 1) >> (F.L - l)) - 1;
+                const T *u = Ul + F.uo[lv] + (size_t)i * kl;
+                const A *y = yh + (size_t)node * F.k;
+                for (int al = lane; al < kl; al += 32) fa += (A)u[al] * y[al];
             }
         }
         part[q] = (double)fa;
@@ -398,20 +392,43 @@ static void row_kernel_smem(size_t shm)
 }
 
 // ---------------------------------------------------------------------------
+// the far-field view: uniform rank k over the levels, or the per-level ranks
+// of the recompressed far field (rc)
+static FarView make_far_view(const MeshData &m, const OpData &op, bool use, bool rc)
+{
+    FarView F;
+    F.use = (use && m.nfar > 0) ? 1 : 0;
+    F.lmin = m.far_lmin;
+    F.L = m.kt.L;
+    F.nlev = F.use ? m.kt.L - m.far_lmin + 1 : 0;
+    F.k = m.k;
+    F.N = m.N;
+    VFD_REQUIRE(F.nlev <= FV_MAXLEV, VFD_EUNSUPPORTED, "apply: too many far levels");
+    for (int lv = 0; lv < FV_MAXLEV; ++lv) {
+        F.kl[lv] = m.k;
+        F.uo[lv] = (long long)lv * m.N * m.k;
+    }
+    F.so = nullptr;
+    F.bk = nullptr;
+    if (rc && F.use) {
+        for (int lv = 0; lv < F.nlev; ++lv) {
+            F.kl[lv] = op.rc_kl[lv];
+            F.uo[lv] = op.rc_uo[lv];
+        }
+        F.so = op.rc_so.p;
+        F.bk = op.rc_bk.p;
+    }
+    return F;
+}
+
 template <class T, class A>
 static void apply_impl(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
-                       const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, A *ye, cudaStream_t st,
+                       const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, A *ye, bool rc, cudaStream_t st,
                        const int *skip)
 {
-    const int k = m.k, fl = m.kt.first_leaf(), L = m.kt.L, nnode = m.kt.nnode;
+    const int k = m.k, fl = m.kt.first_leaf(), nnode = m.kt.nnode;
     const int64_t hs = (int64_t)nnode * k;
-    FarView F;
-    F.use = ((parts & VFD_PART_KFAR) && m.nfar > 0) ? 1 : 0;
-    F.lmin = m.far_lmin;
-    F.L = L;
-    F.nlev = F.use ? L - m.far_lmin + 1 : 0;
-    F.k = k;
-    F.N = m.N;
+    const FarView F = make_far_view(m, op, (parts & VFD_PART_KFAR) != 0, rc);
     const bool near = (parts & VFD_PART_KNEAR) && m.nnear > 0;
     const double *val = nullptr;
     if ((parts & VFD_PART_B) && (parts & VFD_PART_M)) val = op.valBM.p;
@@ -491,7 +508,7 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
             op.ye32.alloc(needy);
         }
         apply_impl<float, float>(m, op, parts, X, Y, nrhs, ld, op.Ul32.p, op.S32.p, op.D32.p, op.xhat32.p, op.yhat32.p,
-                                 op.P32.p, op.ye32.p, st, skip);
+                                 op.P32.p, op.ye32.p, false, st, skip);
     } else {
         if (op.xhat.n < need || op.P64.n < needp || op.ye64.n < needy) {
             release_graphs(op);
@@ -500,8 +517,9 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
             op.P64.alloc(needp);
             op.ye64.alloc(needy);
         }
-        apply_impl<double, double>(m, op, parts, X, Y, nrhs, ld, m.Ul64.p, op.S64.p, op.D64.p, op.xhat.p, op.yhat.p,
-                                   op.P64.p, op.ye64.p, st, skip);
+        const bool rc = op.rc_on;   // the recompressed far field of the FP64 operator
+        apply_impl<double, double>(m, op, parts, X, Y, nrhs, ld, rc ? op.Ulc64.p : m.Ul64.p, rc ? op.Sc64.p : op.S64.p,
+                                   op.D64.p, op.xhat.p, op.yhat.p, op.P64.p, op.ye64.p, rc, st, skip);
     }
 }
 
@@ -551,17 +569,11 @@ void *noalloc_scratch()
 // the launches of apply_impl, in order, on one stream
 template <class T, class A>
 void apply_one_stream(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,
-                      const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, cudaStream_t st)
+                      const T *Ul, const T *S, const T *D, A *xhat, A *yhat, A *part, bool rc, cudaStream_t st)
 {
-    const int k = m.k, fl = m.kt.first_leaf(), L = m.kt.L, nnode = m.kt.nnode;
+    const int k = m.k, fl = m.kt.first_leaf(), nnode = m.kt.nnode;
     const int64_t hs = (int64_t)nnode * k;
-    FarView F;
-    F.use = m.nfar > 0 ? 1 : 0;
-    F.lmin = m.far_lmin;
-    F.L = L;
-    F.nlev = F.use ? L - m.far_lmin + 1 : 0;
-    F.k = k;
-    F.N = m.N;
+    const FarView F = make_far_view(m, op, true, rc);
     const bool near = m.nnear > 0;
     FarView Fn = F;
     Fn.use = 0;
@@ -610,10 +622,11 @@ void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double 
     unsigned char *base = (unsigned char *)noalloc_scratch();
     if (lowp)
         apply_one_stream<float, float>(m, op, X, Y, nrhs, ld, op.Ul32.p, op.S32.p, op.D32.p, (float *)base,
-                                       (float *)(base + bh), (float *)(base + 2 * bh), st);
+                                       (float *)(base + bh), (float *)(base + 2 * bh), false, st);
     else
-        apply_one_stream<double, double>(m, op, X, Y, nrhs, ld, m.Ul64.p, op.S64.p, op.D64.p, (double *)base,
-                                         (double *)(base + bh), (double *)(base + 2 * bh), st);
+        apply_one_stream<double, double>(m, op, X, Y, nrhs, ld, op.rc_on ? op.Ulc64.p : m.Ul64.p,
+                                         op.rc_on ? op.Sc64.p : op.S64.p, op.D64.p, (double *)base,
+                                         (double *)(base + bh), (double *)(base + 2 * bh), op.rc_on, st);
 }
 
 }  // namespace vfd

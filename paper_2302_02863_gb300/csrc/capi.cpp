@@ -192,6 +192,7 @@ void vfd_default_mesh_opts(vfd_mesh_opts *o)
     o->rho_leaf_m = 64;
     o->rho_lambda = 0.75;
     o->inner_p = 0;
+    o->recompress_tol = 0.0;
 }
 
 const char *vfd_last_error(void) { return vfd::g_err.c_str(); }
@@ -281,8 +282,9 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
     VFD_CUDA(cudaMemcpyAsync(herr, op->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     VFD_CUDA(cudaStreamSynchronize(st));
     VFD_REQUIRE(herr[0] == 0, VFD_EINVAL, "s(x) outside [0, s_bar] at some evaluation point");
-    // a3: coupling blocks
+    // a3: coupling blocks (and their algebraic recompression, FP64 operators)
     launch_coupling_build(m, *op, st);
+    if (m.opts.recompress_tol > 0.0) recompress_far(m, *op, m.opts.recompress_tol, st);
     mark();
     // a4: dense inadmissible leaves
     launch_near_build(m, *op, st);
@@ -494,6 +496,19 @@ vfd_status vfd_selftest_math(vfd_mesh_t mesh, int which, int64_t n, const double
     cudaStream_t st = (cudaStream_t)stream;
     launch_selftest_math(*mesh->m, which, n, x, out, st);
     VFD_CUDA(cudaStreamSynchronize(st));
+    return VFD_OK;
+    VFD_API_END
+}
+
+vfd_status vfd_op_far_ranks(vfd_op_t h, int *ranks, int n, int *nlev)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h && nlev, VFD_EINVAL, "null argument");
+    const OpData &op = *h->op;
+    const MeshData &m = *op.m;
+    const int nl = m.nfar > 0 ? m.kt.L - m.far_lmin + 1 : 0;
+    *nlev = nl;
+    for (int lv = 0; lv < nl && lv < n && ranks; ++lv) ranks[lv] = op.rc_on ? op.rc_kl[lv] : m.k;
     return VFD_OK;
     VFD_API_END
 }

@@ -268,6 +268,8 @@ MeshData *build_mesh(int d, int64_t n_vert, const double *coords, int64_t n_cell
     for (int i = 0; i < d; ++i) kk *= opts.cheb_p;
     VFD_REQUIRE(kk <= KMAX, VFD_EINVAL, "rank p^d too large");
     VFD_REQUIRE(opts.inner_p >= 0 && opts.inner_p <= opts.cheb_p, VFD_EINVAL, "inner_p must be in [0, cheb_p]");
+    VFD_REQUIRE(opts.recompress_tol >= 0.0 && opts.recompress_tol < 1.0, VFD_EINVAL,
+                "recompress_tol must be in [0, 1)");
 
     auto *m = new MeshData();
     try {

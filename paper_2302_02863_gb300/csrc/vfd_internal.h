@@ -213,6 +213,10 @@ struct MeshData {
     // load assembly (exact P1 mass)
     DBuf<int> ld_ptr, ld_idx;           // DoF -> list of cell*(d+1)+a contributions
 
+    // orthogonal factors of the far-field bases (recompress.cu, first recompressing assembly)
+    bool rc_factors = false;
+    DBuf<double> rc_T1, rc_R;          // per node W L^-1/2 and L^1/2 W^T of the basis Gram matrix
+
     // host copies for the nearest-point location of the Chebyshev nodes
     std::vector<double> kt_cheb_h, kt_cheb_in_h, tt_cheb_h, st_cheb_h;
     std::vector<int> lp_ptr_h, lp_pts_h;
@@ -269,6 +273,13 @@ struct OpData {
     DBuf<float> xhat32, yhat32;
     DBuf<double> P64;                  // leaf-level projections nlev * nleaf * k * nrhs
     DBuf<double> ye64;                 // per admissible block coupling products nfar * k * nrhs
+    // recompressed far field of the FP64 operator (recompress.cu): per-level ranks
+    bool rc_on = false;
+    std::vector<int> rc_kl;            // rank of each far level
+    std::vector<long long> rc_uo;      // offset of each level's flattened basis in Ulc64
+    DBuf<double> Ulc64, Sc64;          // flattened bases (N x kl per level), couplings (kl x kl per block)
+    DBuf<long long> rc_so;             // offset of each block's coupling in Sc64
+    DBuf<int> rc_bk;                   // rank of each block
     DBuf<float> ye32;
     DBuf<float> P32;
     cudaStream_t side = nullptr;       // far-field branch of the apply
@@ -381,6 +392,7 @@ void apply_parts_ex(const MeshData &m, OpData &op, int parts, const double *X, d
                     bool lowp, cudaStream_t st, const int *skip);
 void apply_parts(const MeshData &m, OpData &op, int parts, const double *X, double *Y, int nrhs, int64_t ld,
                  cudaStream_t st);
+void recompress_far(MeshData &m, OpData &op, double tol, cudaStream_t st);
 void grad_adjoint(MeshData &m, OpData &op, const double *U, const double *Lam, int nrhs, int64_t ld, double *g_s,
                 double *g_lk, cudaStream_t st);
 void apply_noalloc(const MeshData &m, const OpData &op, const double *X, double *Y, int nrhs, int64_t ld,

@@ -34,7 +34,7 @@ INFO_KEYS = ["n_dof", "n_vert", "n_cell", "touching_pairs", "nnz", "levels", "no
 
 EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble",
            "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_precondition", "vfd_grad", "vfd_load",
-           "vfd_op_rho", "vfd_op_timings",
+           "vfd_op_rho", "vfd_op_timings", "vfd_op_far_ranks",
            "vfd_selftest_math", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve", "vfd_batch_tuning",
            "vfd_batch_set_config", "vfd_batch_set_wait_limit", "vfd_batch_free",
            "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
@@ -49,7 +49,7 @@ class VfdError(RuntimeError):
 class MeshOpts(C.Structure):
     _fields_ = [("leaf_m", C.c_int), ("cheb_p", C.c_int), ("lam", C.c_double), ("n_sing", C.c_int),
                 ("tail_mode", C.c_int), ("tail_R", C.c_double), ("rho_leaf_m", C.c_int),
-                ("rho_lambda", C.c_double), ("inner_p", C.c_int)]
+                ("rho_lambda", C.c_double), ("inner_p", C.c_int), ("recompress_tol", C.c_double)]
 
 
 class FieldStruct(C.Structure):
@@ -91,6 +91,7 @@ def load():
     L.vfd_precondition.argtypes = [vp, C.c_int, vp]
     L.vfd_op_rho.argtypes = [vp, vp, vp]
     L.vfd_op_timings.argtypes = [vp, dp, C.c_int]
+    L.vfd_op_far_ranks.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
     L.vfd_selftest_math.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp]
     L.vfd_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
     L.vfd_batch_apply.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int64), C.c_int64, vp]
@@ -109,7 +110,8 @@ def load():
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
               "vfd_apply_noalloc", "vfd_grad", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve",
               "vfd_batch_tuning", "vfd_batch_set_config", "vfd_batch_set_wait_limit",
-              "vfd_solve", "vfd_precondition", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_selftest_math"]:
+              "vfd_solve", "vfd_precondition", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_op_far_ranks",
+              "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -185,7 +187,8 @@ def vfd_default_mesh_opts():
 
 def vfd_mesh(d, coords, cells, cell_is_interior, opts=None, **kw):
     """Build a mesh handle (host arrays).  kw overrides fields of the default
-    options (leaf_m, cheb_p, lam, n_sing, tail_mode, tail_R, rho_leaf_m, rho_lambda, inner_p)."""
+    options (leaf_m, cheb_p, lam, n_sing, tail_mode, tail_R, rho_leaf_m, rho_lambda, inner_p,
+    recompress_tol)."""
     L = load()
     o = vfd_default_mesh_opts() if opts is None else opts
     for k, v in kw.items():
@@ -388,6 +391,16 @@ def vfd_op_timings(op):
     a = np.zeros(len(TIMING_KEYS))
     _check(load().vfd_op_timings(op.handle, a.ctypes.data_as(C.POINTER(C.c_double)), len(a)))
     return dict(zip(TIMING_KEYS, a.tolist()))
+
+
+def vfd_op_far_ranks(op):
+    """Rank of every far level of the FP64 far field, coarsest first (after
+    recompression the padded per-level ranks)."""
+    nl = C.c_int()
+    _check(load().vfd_op_far_ranks(op.handle, None, 0, C.byref(nl)))
+    r = (C.c_int * max(nl.value, 1))()
+    _check(load().vfd_op_far_ranks(op.handle, r, nl.value, C.byref(nl)))
+    return [int(r[i]) for i in range(nl.value)]
 
 
 def vfd_selftest_math(mesh, which, x, out, stream=None):
