@@ -400,6 +400,7 @@ def main():
     del mesh_x
 
     grad = None if args.no_grad else gradient_leg(m, k, prm, torch, vfd)
+    recomp = recompress_leg(m, s, k, prm, F, torch, vfd) if prec == vfd.VFD_FP64 else None
     prec_leg = precond_leg(mesh, s, k, prm, F, torch, vfd) if prec == vfd.VFD_FP64 else None
     graded = None if args.no_graded else graded_leg(torch, vfd)
     ball = None if args.no_ball else ball_leg(torch, vfd)
@@ -434,7 +435,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": gpu_launches, "clocks": clk, "mesh": info, "rank16_operator": r16,
             "graded_exterior": graded, "ball_3d": ball, "batched_mixed_precision": batched,
-            "batch_24_meshes": batch24, "gradient": grad, "preconditioner": prec_leg,
+            "batch_24_meshes": batch24, "gradient": grad, "preconditioner": prec_leg, "recompression": recomp,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -976,6 +977,55 @@ def precond_leg(mesh, s, k, prm, F, torch, vfd, rtol=1e-10):
         else:
             out["solution_rel_diff"] = (torch.linalg.norm(U - U_cg) / torch.linalg.norm(U_cg)).item()
     out["rtol"] = rtol
+    return out
+
+
+def recompress_leg(m, s, k, prm, F, torch, vfd, tol=1e-6, rtol=1e-10):
+    """The benchmark operator with the algebraic recompression of its far field
+    (recompress_tol = tol): per-level ranks, assembly and FP64 apply time, FP64
+    CG, and the matvec gap to the interpolation operator it was cut from
+    (every row, seeded x) -- next to the same figures without recompression."""
+    def mk(t):
+        return vfd.vfd_mesh(m.d, m.coords, m.cells, m.cell_is_interior, leaf_m=prm["leaf"], cheb_p=prm["p"],
+                            lam=prm["lam"], rho_lambda=prm["lam"], tail_mode=prm["tail"], tail_R=prm["R"],
+                            recompress_tol=t)
+
+    stream = torch.cuda.current_stream()
+    out = {"tol": tol}
+    g = torch.Generator(device="cuda").manual_seed(12)
+    X = torch.randn(mk(0.0).n_dof, dtype=torch.float64, device="cuda", generator=g)
+    Ys = {}
+    for name, t in (("interpolation", 0.0), ("recompressed", tol)):
+        mesh = mk(t)
+        for _ in range(2):
+            op = vfd.vfd_assemble(mesh, s, k, prm["s_bar"], flags=vfd.VFD_ASSEMBLE_TIMED)
+        ph = vfd.vfd_op_timings(op)
+        Y = torch.empty_like(X)
+        for _ in range(5):
+            vfd.vfd_apply(op, X, Y)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(50):
+            vfd.vfd_apply(op, X, Y)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        apply_us = ev[0].elapsed_time(ev[1]) * 1000 / 50
+        Ys[name] = Y.clone()
+        U = torch.zeros_like(F)
+        vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)   # warm-up (graph capture)
+        U.zero_()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        st, it, rel = vfd.vfd_solve(op, F, U, rtol=rtol, max_it=100000)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"far_ranks": vfd.vfd_op_far_ranks(op), "assemble_ms": ph["total"],
+                     "coupling_phase_ms": ph["coupling"], "apply_us": apply_us, "cg_iters": int(it[0]),
+                     "cg_ms": ev[0].elapsed_time(ev[1])}
+        out[name]["step_ms"] = out[name]["assemble_ms"] + out[name]["cg_ms"]
+        del op
+    out["matvec_rel_gap"] = (torch.linalg.norm(Ys["recompressed"] - Ys["interpolation"]) /
+                             torch.linalg.norm(Ys["interpolation"])).item()
     return out
 
 
