@@ -358,6 +358,15 @@ vfd_status vfd_batch_set_config(vfd_batch_t batch, int cfg, int *ncand);
  * VFD_EINVAL (negative or non-finite seconds). */
 vfd_status vfd_batch_set_wait_limit(vfd_batch_t batch, double seconds);
 
+/* The factor by which every still-iterating column of a mesh must cut its
+ * recursive (inner, low-precision) residual before the batched solve replaces
+ * it by the FP64 true residual F - A U (a reliable update; the mixed
+ * precision is not in the paper, whose CG is FP64, Sec. 7).  Default 0.03.
+ * A deeper drop (smaller factor) runs fewer FP64 applies but trusts the
+ * low-precision recursion longer.  Takes effect on the next solve.  Errors:
+ * VFD_EINVAL (drop not in (0, 1)). */
+vfd_status vfd_batch_set_update_drop(vfd_batch_t batch, double drop);
+
 void vfd_batch_free(vfd_batch_t batch);
 
 /* Adjoint gradient (the paper has no gradients; derivative of the discrete

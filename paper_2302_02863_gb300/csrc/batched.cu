@@ -88,7 +88,13 @@ __device__ __forceinline__ float from_f<float>(float v) { return __uint_as_float
 // (cvt.rna) or packed to BF16x2 (cvt.rn).  Rounding to nearest matters:
 // truncation (what the tensor core does with raw FP32 bits) biases the
 // low-precision operator, and the refinement then needed about twice the
-// inner iterations.  The panel's chunks are split over gridDim.z CTAs; CTA z
+// inner iterations.  x enters as two terms, hi = round(x) and lo =
+// round(x - hi), each multiplied by the panel (twice the MMAs): the panel's
+// own rounding is a fixed perturbation of the operator (its row sums are
+// compensated), but rounding x anew in every apply adds noise of the unit
+// roundoff relative to each entry of x, and for the smooth directions of the
+// preconditioned iteration that noise is larger than A x itself (the inner
+// iteration on one 21k-DoF mesh took 1253 BF16 steps instead of 39).  The panel's chunks are split over gridDim.z CTAs; CTA z
 // writes its partial product to Y (z = 0) or to partial buffer z - 1 of Y2,
 // summed by the CSR kernel.  The stage width NK, the depth NSTAGE and the
 // split are picked per batch by timing the candidates (near_configs).
@@ -132,6 +138,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
 }
+// the two halves of a packed pair as FP32 (exact)
+__device__ __forceinline__ float bf16_lo(uint32_t r) { return __uint_as_float(r << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t r) { return __uint_as_float(r & 0xffff0000u); }
 
 // WARPS = 8: warp tile 16 rows x 32 RHS; WARPS = 4: 32 rows x 32 RHS (two m16
 // tiles share each B fragment).  NACC = 2: even and odd k-steps accumulate
@@ -215,13 +224,29 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
                 const int n = n0 + j * 8 + g;
                 uint32_t bb[2];
                 if constexpr (sizeof(T) == 2) {
+                    // x = hi + lo, both BF16: the product sees x to ~2^-16 (one BF16
+                    // rounding of x alone is noise of 2^-9 relative in every entry,
+                    // which swamps A x for the smooth directions of the
+                    // preconditioned iteration)
                     const float *B0 = Bs + (ks + 2 * t4) * TT::LDB + n;
-                    bb[0] = pack_bf16x2(B0[0], B0[TT::LDB]);
-                    bb[1] = pack_bf16x2(B0[8 * TT::LDB], B0[9 * TT::LDB]);
+                    const float x0 = B0[0], x1 = B0[TT::LDB], x2 = B0[8 * TT::LDB], x3 = B0[9 * TT::LDB];
+                    bb[0] = pack_bf16x2(x0, x1);
+                    bb[1] = pack_bf16x2(x2, x3);
+                    const uint32_t bl[2] = {pack_bf16x2(x0 - bf16_lo(bb[0]), x1 - bf16_hi(bb[0])),
+                                            pack_bf16x2(x2 - bf16_lo(bb[1]), x3 - bf16_hi(bb[1]))};
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+                        if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS + 1) % NACC][mt][j], a[mt], bl);
                 } else {
+                    // the same split in TF32: x = hi + lo, both rounded to TF32
                     const float *B0 = Bs + (ks + t4) * TT::LDB + n;
-                    bb[0] = f2tf32(B0[0]);
-                    bb[1] = f2tf32(B0[4 * TT::LDB]);
+                    const float x0 = B0[0], x1 = B0[4 * TT::LDB];
+                    bb[0] = f2tf32(x0);
+                    bb[1] = f2tf32(x1);
+                    const uint32_t bl[2] = {f2tf32(x0 - __uint_as_float(bb[0])), f2tf32(x1 - __uint_as_float(bb[1]))};
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+                        if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS + 1) % NACC][mt][j], a[mt], bl);
                 }
 #pragma unroll
                 for (int mt = 0; mt < MT; ++mt)
@@ -245,11 +270,16 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
         }
 }
 
-// x in BF16 for the tcgen05 near kernel
+// x for the tcgen05 near kernel as two BF16 terms: b[i] = hi = BF16(x),
+// b[n + i] = lo = BF16(x - hi)
 __global__ void k_x_to_bf16(long long n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ b)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+    if (i >= n) return;
+    const float v = a[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    b[i] = h;
+    b[n + i] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
 template <class T, int NK, int NSTAGE>
@@ -525,7 +555,7 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
     b.yhat.alloc(std::max<size_t>(nh, 1));
     b.fpart.alloc(std::max<size_t>(nc, 1));
     b.y2.alloc((size_t)(KSPLIT_MAX - 1) * b.ntot * R);
-    b.xc.alloc((size_t)b.ntot * R * 2);   // x in BF16 for the tcgen05 kernel
+    b.xc.alloc((size_t)b.ntot * R * 2 * 2);   // x as BF16 hi and lo blocks for the tcgen05 kernel
     if (!b.tc_err.p) {
         b.tc_err.alloc(1);
         VFD_CUDA(cudaMemset(b.tc_err.p, 0, sizeof(int)));

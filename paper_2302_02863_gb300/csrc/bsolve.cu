@@ -407,13 +407,14 @@ __device__ __forceinline__ float mesh_sum(const Seg &S, const float *red, int m,
 // one cooperative launch with two grid barriers:
 //   A: p.q (block partials) | alpha = r.p / p.q per column
 //   B: x += alpha p, r -= alpha q, r.r (partials) | beta, convergence
-//   C: p = r + beta p, and p in BF16 for the tensor-core near kernel (p16)
+//   C: p = r + beta p, and p as two BF16 terms for the tensor-core near kernel
+//      (p16: hi; p16 + p16lo: lo = the rounding error of hi)
 // Same arithmetic and the same fixed summation orders as k_b_pq, k_b_xr and
 // k_b_p.  red2 holds the second partials (the first are still being read).
 __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, float *__restrict__ x,
                                                float *__restrict__ r, float *__restrict__ p,
                                                const float *__restrict__ q, __nv_bfloat16 *__restrict__ p16,
-                                               unsigned *gbar, long long wait_ns, int *err)
+                                               long long p16lo, unsigned *gbar, long long wait_ns, int *err)
 {
     __shared__ float sh[BT];
     __shared__ float al_s[BT], be_s[BT], rr_s[BT];   // per column (Rp <= BT)
@@ -513,14 +514,18 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
         S.flag[FL_CNT + S.nmesh + m] = live_s;
         if (done_s) S.mdone()[m] = 1;
     }
-    // C: p = r + beta p (meshes still iterating), p16 = BF16(p)
+    // C: p = r + beta p (meshes still iterating), p16 = BF16(p) and its rounding error
     if (work && !done_s) {
         const size_t base = (size_t)r0 * Rp, n = (size_t)N * Rp;
         for (size_t e = (size_t)j * blockDim.x + threadIdx.x; e < n; e += (size_t)nb * blockDim.x) {
             const int c = (int)(e % Rp);
             const float v = fmaf(be_s[c], p[base + e], r[base + e]);
             p[base + e] = v;
-            if (p16) p16[base + e] = __float2bfloat16_rn(v);
+            if (p16) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                p16[base + e] = h;
+                p16[p16lo + base + e] = __float2bfloat16_rn(v - __bfloat162float(h));
+            }
         }
     }
     if (!grid_barrier(gbar, gbar + 1, gridDim.x, wait_ns, err)) return;
@@ -888,10 +893,11 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
                 float *red2 = b.red2.p, *xv = b.x.p, *rv = b.r.p, *pv = b.p.p;
                 const float *qv = b.q.p;
                 __nv_bfloat16 *p16 = (__nv_bfloat16 *)b.p16_target;
+                long long p16lo = (long long)b.ntot * Rp;
                 unsigned *gb = b.gbar.p;
                 long long wns = b.wait_ns;
                 int *err = b.tc_err.p;
-                void *args[] = {&Sv, &red2, &xv, &rv, &pv, &qv, &p16, &gb, &wns, &err};
+                void *args[] = {&Sv, &red2, &xv, &rv, &pv, &qv, &p16, &p16lo, &gb, &wns, &err};
                 VFD_CUDA(cudaLaunchCooperativeKernel((const void *)k_b_iter, b.nred, BT, args, 0, cs));
             } else if (b.pcg) {
                 // preconditioned: p.q, x/r update, z = M^-1 r with r.z and beta, p = z + beta p
@@ -923,10 +929,7 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
 vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, const int64_t *ld, int R, double rtol,
                        int max_it, int *iters, double *relres, cudaStream_t st)
 {
-    // recursive-residual reduction between reliable updates (a deeper drop saved
-    // one FP64 residual on the disk but stalled the BF16 inner iteration on
-    // some meshes of the 24-mesh batch)
-    const double RU_DROP = 0.03;
+    const double RU_DROP = b.ru_drop;   // recursive-residual reduction between reliable updates
     const int Rp = ((R + 63) / 64) * 64, nm = b.nmesh;
     const size_t nc = (size_t)nm * Rp, nr = (size_t)nm * R;
     ensure_solve(b, Rp);

@@ -614,6 +614,16 @@ vfd_status vfd_batch_set_wait_limit(vfd_batch_t h, double seconds)
     VFD_API_END
 }
 
+vfd_status vfd_batch_set_update_drop(vfd_batch_t h, double drop)
+{
+    VFD_API_BEGIN
+    VFD_REQUIRE(h, VFD_EINVAL, "null batch");
+    VFD_REQUIRE(std::isfinite(drop) && drop > 0.0 && drop < 1.0, VFD_EINVAL, "the update drop must be in (0, 1)");
+    h->b->ru_drop = drop;
+    return VFD_OK;
+    VFD_API_END
+}
+
 void vfd_batch_free(vfd_batch_t h)
 {
     if (!h) return;

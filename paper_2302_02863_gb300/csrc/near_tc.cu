@@ -15,14 +15,15 @@
 //     128-byte-swizzled layout the MMA reads, so the copy is one contiguous
 //     block;
 //   warps 2-3 (B producers): thread t gathers the x row of panel column t
-//     (BF16, 64 RHS = 128 B) with 16-byte cp.async into the MN-major
-//     core-matrix layout (zero fill for padding columns); once its copies of
-//     a stage have landed it fences them for the async proxy and arrives on
-//     the stage's "full B" barrier (64 arrivals);
-//   warp 1, lane 0 (MMA issuer): waits for both, issues four tcgen05.mma
+//     with 16-byte cp.async into the MN-major core-matrix layout (zero fill
+//     for padding columns), x as two BF16 terms hi + lo (64 RHS = 128 B
+//     each, two B tiles); once its copies of a stage have landed it fences
+//     them for the async proxy and arrives on the stage's "full B" barrier
+//     (64 arrivals);
+//   warp 1, lane 0 (MMA issuer): waits for both, issues eight tcgen05.mma
 //     (kind::f16, M = 128, N = 64, K = 16, FP32 accumulator in tensor
-//     memory) and commits them to the stage's "empty" barrier, which hands
-//     the buffers back to the producers;
+//     memory; per K step the hi and the lo tile) and commits them to the
+//     stage's "empty" barrier, which hands the buffers back to the producers;
 //   warp 2 also allocates / frees the 64 tensor-memory columns.
 // Rows na..127 of the M = 128 operand are whatever the shared memory holds;
 // they only produce accumulator rows that are never read.
@@ -46,7 +47,7 @@ namespace vfd {
 namespace {
 
 constexpr int TC_NK = 64;                     // panel columns per stage (one 128-byte BF16 row)
-constexpr int TC_STAGE_BYTES = 2 * 8192;      // A (<= 64 rows x 128 B) + B (64 rows x 128 B)
+constexpr int TC_STAGE_BYTES = 3 * 8192;      // A (<= 64 rows x 128 B) + B hi, B lo (64 rows x 128 B each)
 constexpr int TC_LDS = RT + 4;                // row stride (floats) of the epilogue tile
 constexpr long long TC_DRAIN_NS = 1000000000LL;   // bound of the waits that drain work already issued
 
@@ -121,7 +122,7 @@ struct TcItem {
 template <int NSTAGE>
 __global__ void __launch_bounds__(128, 1)
 k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int R, const void *__restrict__ Xc,
-           const float *__restrict__ Xall, float *__restrict__ Yall, float *__restrict__ part, int *__restrict__ cnt,
+           size_t xlo, const float *__restrict__ Xall, float *__restrict__ Yall, float *__restrict__ part, int *__restrict__ cnt,
            long long wait_ns, int *err, const int *skip, const int *mdone)
 {
     extern __shared__ unsigned char tsm_raw[];
@@ -168,7 +169,7 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
     const uint32_t taddr = *tslot;
     const uint32_t a_bytes = (uint32_t)it.na * 128u;
 
-    const unsigned char *Xb = (const unsigned char *)Xc;   // x in BF16, [nrow][R]
+    const unsigned char *Xb = (const unsigned char *)Xc;   // x in BF16, [nrow][R]: hi, then lo at element xlo
     int issued = 0;   // A producer: stages whose bulk copies were issued
     if (warp == 0) {
         if (lane == 0)
@@ -204,10 +205,14 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
                 for (int k = 0; k < TC_NK / 16; ++k) {
                     const uint64_t da = desc_sw128(sa + 32u * k, 16u, 1024u);   // K-major, 128-byte swizzle: +32 B per K step
                     const uint64_t db = desc_plain(sb + 2048u * k, 1024u, 128u);  // MN-major, no swizzle: +16 rows per K step
+                    const uint64_t dl = desc_plain(sb + 8192u + 2048u * k, 1024u, 128u);   // the lo tile
                     const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
                     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
                                  "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+                                 "l"(da), "l"(dl), "r"(TC_IDESC), "r"(1u));
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                     empty_b(s)));
@@ -220,8 +225,8 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
         }
     } else {
         // B producers (warps 2, 3): thread t copies x row k = t of every stage
-        // (128 bytes = 8 core-matrix pieces of 16 bytes) with cp.async; it
-        // signals a stage once its own copies of that stage have landed
+        // (hi and lo: 2 x 128 bytes = 16 core-matrix pieces of 16 bytes) with
+        // cp.async; it signals a stage once its own copies of that stage have landed
         constexpr int LAG = NSTAGE - 1;   // stages of copies a thread keeps in flight
         const int t = tid - 64;
         int posted = 0, arrived = 0;
@@ -233,9 +238,12 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
             }
             const int g = gs[i * TC_NK + t];
             const unsigned char *src = g >= 0 ? Xb + ((size_t)(it.xoff + g) * R + rt) * 2 : Xb;
+            const unsigned char *srl = g >= 0 ? src + xlo * 2 : Xb;
             unsigned char *dst = tsm + s * TC_STAGE_BYTES + 8192 + (t >> 3) * 1024 + (t & 7) * 16;
 #pragma unroll
             for (int c = 0; c < 8; ++c) tc_cp16(dst + c * 128, src + c * 16, g >= 0);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) tc_cp16(dst + 8192 + c * 128, srl + c * 16, g >= 0);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             posted = i + 1;
             if (i >= LAG) {
@@ -460,7 +468,8 @@ bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X
 #define VFD_TMA_CASE(NS)                                                                                         \
     if (nstage == NS) {                                                                                          \
         VFD_CUDA(cudaFuncSetAttribute(k_near_tma<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));    \
-        k_near_tma<NS><<<g, 128, shm, st>>>(items, ms, R, b.xc.p, X, Y, b.tc_part.p, b.tc_cnt.p, b.wait_ns,       \
+        k_near_tma<NS><<<g, 128, shm, st>>>(items, ms, R, b.xc.p, (size_t)b.ntot * R, X, Y, b.tc_part.p,          \
+                                            b.tc_cnt.p, b.wait_ns,                                                \
                                             b.tc_err.p, skip, mdone);                                             \
         VFD_CUDA(cudaGetLastError());                                                                            \
         return true;                                                                                             \

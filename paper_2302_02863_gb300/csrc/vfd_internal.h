@@ -334,13 +334,14 @@ struct BatchData {
     DBuf<float> fpart;                  // far-field leaf projections (all meshes)
     int max_mt = 0;                     // largest flattened basis width nlev * kp
     DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
-    DBuf<unsigned char> xc;             // x in BF16 for the tcgen05 kernel ([ntot][R])
+    DBuf<unsigned char> xc;             // x for the tcgen05 kernel, BF16 hi then lo ([2][ntot][R])
     DBuf<int> tc_err;                   // set by the tcgen05 kernel when a pipeline wait expires
     DBuf<unsigned char> tc_items;       // TcItem records of the tcgen05 kernel (one per (mesh, leaf))
     int n_tc_items = 0;
     DBuf<float> tc_part;                // split partial tiles of the tcgen05 kernel
     DBuf<int> tc_cnt;                   // per (item, RHS tile) arrival counters (zero between launches)
     long long wait_ns = 1000000000LL;   // bound of the tcgen05 kernel's pipeline waits
+    double ru_drop = 0.03;              // recursive-residual reduction between reliable updates
     // batched refinement solve
     DBuf<float> x, r, p, q, b, red, red2, sc;
     bool fused = false;                 // the captured iteration uses the cooperative vector kernel

@@ -36,7 +36,7 @@ EXPORTS = ["vfd_default_mesh_opts", "vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info"
            "vfd_apply", "vfd_apply_parts", "vfd_apply_noalloc", "vfd_solve", "vfd_precondition", "vfd_grad", "vfd_load",
            "vfd_op_rho", "vfd_op_timings", "vfd_op_far_ranks",
            "vfd_selftest_math", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve", "vfd_batch_tuning",
-           "vfd_batch_set_config", "vfd_batch_set_wait_limit", "vfd_batch_free",
+           "vfd_batch_set_config", "vfd_batch_set_wait_limit", "vfd_batch_set_update_drop", "vfd_batch_free",
            "vfd_free_op", "vfd_free_mesh", "vfd_last_error"]
 
 
@@ -100,6 +100,7 @@ def load():
     L.vfd_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
     L.vfd_batch_set_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     L.vfd_batch_set_wait_limit.argtypes = [vp, C.c_double]
+    L.vfd_batch_set_update_drop.argtypes = [vp, C.c_double]
     L.vfd_batch_free.argtypes = [vp]
     L.vfd_batch_free.restype = None
     L.vfd_free_op.argtypes = [vp]
@@ -109,7 +110,7 @@ def load():
     L.vfd_last_error.restype = C.c_char_p
     for f in ["vfd_mesh", "vfd_mesh_dofs", "vfd_mesh_info", "vfd_assemble", "vfd_apply", "vfd_apply_parts",
               "vfd_apply_noalloc", "vfd_grad", "vfd_batch_create", "vfd_batch_apply", "vfd_batch_solve",
-              "vfd_batch_tuning", "vfd_batch_set_config", "vfd_batch_set_wait_limit",
+              "vfd_batch_tuning", "vfd_batch_set_config", "vfd_batch_set_wait_limit", "vfd_batch_set_update_drop",
               "vfd_solve", "vfd_precondition", "vfd_load", "vfd_op_rho", "vfd_op_timings", "vfd_op_far_ranks",
               "vfd_selftest_math"]:
         getattr(L, f).restype = C.c_int
@@ -368,6 +369,11 @@ def vfd_batch_set_config(batch, cfg):
 def vfd_batch_set_wait_limit(batch, seconds):
     """Bound (seconds) of the tensor-core kernel's device waits; 0 = give up at once."""
     _check(load().vfd_batch_set_wait_limit(batch.handle, float(seconds)))
+
+
+def vfd_batch_set_update_drop(batch, drop):
+    """Recursive-residual reduction (0 < drop < 1) between the batched solve's FP64 reliable updates."""
+    _check(load().vfd_batch_set_update_drop(batch.handle, float(drop)))
 
 
 def vfd_precondition(op, kind=VFD_PREC_TWO_LEVEL, stream=None):

@@ -93,3 +93,33 @@ def test_batch_rejects_mixed_precision():
         vfd.vfd_batch_create([cases[0][5], opb])
     with pytest.raises(vfd.VfdError):
         vfd.vfd_batch_create([cases[0][4]])   # FP64 operator
+
+
+def test_preconditioned_low_precision_on_hard_mesh():
+    """Mesh 13 of the 24-mesh workload (a 21k-DoF disk, s in [0.1, 0.9]):
+    with x rounded once to BF16 before the near-panel product, the
+    preconditioned inner iteration took 1253 BF16 steps (TF32: 80-152); with x
+    carried as hi + lo terms it takes about 40 in both precisions."""
+    i = 13
+    n = int(round(2000 * 65.0 ** (i / 23)))
+    m = synth.disk_mesh_for_dofs(n, R=1.1, jitter=0.2, seed=3000 + i)
+    s = synth.sigmoid_field(synth.random_fourier_field(3000 + i + 100, 1.0), 0.1, 0.9)
+    k = synth.random_fourier_field(3000 + i + 200, 0.5)
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=64, cheb_p=4, lam=0.75, rho_lambda=0.75)
+    op64 = vfd.vfd_assemble(mesh, s, k, 0.9)
+    g = torch.Generator(device="cuda").manual_seed(4013)
+    F = torch.randn(64, mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
+    for prec in (vfd.VFD_BF16, vfd.VFD_FP32):
+        op = vfd.vfd_assemble(mesh, s, k, 0.9, precision=prec)
+        vfd.vfd_precondition(op)
+        batch = vfd.vfd_batch_create([op])
+        for bad in (0.0, 1.0, -0.5, float("nan")):
+            with pytest.raises(vfd.VfdError):
+                vfd.vfd_batch_set_update_drop(batch, bad)
+        vfd.vfd_batch_set_update_drop(batch, 0.03)
+        U = torch.zeros_like(F)
+        st, it, rel = vfd.vfd_batch_solve(batch, [F], [U], rtol=1e-8, max_it=2000)
+        assert st == vfd.VFD_OK and rel.max() <= 1e-8
+        assert it.max() <= 120, (prec, it.max())
+        R = F - vfd.vfd_apply(op64, U, torch.empty_like(U))
+        assert (torch.linalg.norm(R, dim=1) / torch.linalg.norm(F, dim=1)).max().item() <= 1e-8
