@@ -394,13 +394,11 @@ __global__ void k_mr_rows(const MrMesh *__restrict__ ms, const long long *__rest
     ((float4 *)Yall)[tg] = acc;
 }
 
-// the near phase of the apply for candidate c: Y = (near panels + B + M) X.
-// mma.sync candidates: the panel products (partial sums of a split in Y2),
-// then k_mr_rows adds the partials and the B + M rows (or the diagonal, where
-// B + M is folded into the panels); tcgen05 candidates: one kernel
-// (near_tc.cu) with those rows in its epilogue.  Xc: x in BF16 for the
-// tcgen05 kernel (its tensor map is built over that buffer).  false: the
-// candidate does not apply (shared memory, precision, meshes without panels).
+// the near phase of the apply for candidate c: Y = (near panels + B + M) X:
+// the panel products (mma.sync or tcgen05 kernel; partial tiles of a split
+// panel in Y2), then k_mr_rows adds the partials and the B + M rows (or the
+// diagonal, where B + M is folded into the panels).  false: the candidate
+// does not apply (shared memory, precision, meshes without panels).
 template <class T>
 static bool launch_near_phase(BatchData &b, int c, int R, const float *X, float *Y, cudaStream_t st,
                               const int *skip, const int *mdone)
@@ -408,12 +406,12 @@ static bool launch_near_phase(BatchData &b, int c, int R, const float *X, float 
     const NearCfg &f = kNearCfgs[c];
     if (f.tc) {
         if (sizeof(T) != 2 || b.n_tc_items != b.n_near_items) return false;
-        return launch_near_tma(b, f.nstage, f.ksplit, R, X, Y, st, skip, mdone);
-    }
-    if (b.n_near_items > 0 &&
-        !launch_near<T>(c, b.n_near_items, b.max_panel_w, (const NearItem *)b.near_items.p, R, X, Y, b.y2.p,
-                        (size_t)b.ntot * R, st, skip, mdone))
+        if (b.n_tc_items > 0 && !launch_near_tma(b, f.nstage, f.ksplit, R, X, Y, st, skip, mdone)) return false;
+    } else if (b.n_near_items > 0 &&
+               !launch_near<T>(c, b.n_near_items, b.max_panel_w, (const NearItem *)b.near_items.p, R, X, Y, b.y2.p,
+                               (size_t)b.ntot * R, st, skip, mdone)) {
         return false;
+    }
     const MrMesh *ms = (const MrMesh *)b.desc.p;
     k_mr_rows<<<cdiv((long long)b.ntot * (R / 4), 256), 256, 0, st>>>(ms, b.row_off.p, b.nmesh, (long long)b.ntot, R,
                                                                        X, Y, b.y2.p, f.ksplit - 1, skip, mdone);
@@ -563,11 +561,7 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
     for (OpData *op : b.ops) build_batched_panels(*op->m, *op, st);
     b.n_tc_items = 0;
     if (bf) {
-        // tcgen05 near kernel: pre-tiled panels, items, split partials and their counters
-        build_tc_items(b);
-        b.tc_part.alloc((size_t)std::max(b.n_tc_items, 1) * (R / RT) * 4 * 64 * RT);
-        b.tc_cnt.alloc((size_t)std::max(b.n_tc_items, 1) * (R / RT));
-        b.tc_cnt.zero(st);
+        build_tc_items(b);   // tcgen05 near kernel: items over the pre-tiled panels
     }
     std::vector<MrMesh> d(b.nmesh);
     std::vector<int> li, ni;

@@ -16,6 +16,9 @@
 // to TF32) with the rank padded to kp = k rounded up to 8 (zero columns),
 // products run on the tensor cores (mma.sync m16n8k8 TF32, FP32
 // accumulation), vectors are FP32 in the interleaved layout [row][R].
+// Operand tiles reach shared memory by cp.async (matrices in their stored
+// precision, widened when the fragments are read), so every copy of a stage
+// is in flight at once; the coupling double-buffers its blocks per warp group.
 #include <cuda_bf16.h>
 
 #include "batched.cuh"
@@ -26,8 +29,21 @@ namespace {
 
 constexpr int FT = 128;          // threads per CTA (4 warps)
 constexpr int LDB = RT + 8;      // row stride (floats) of [k][64] operand tiles: conflict-free B fragments
-__host__ __device__ constexpr int lda_t(int kp) { return ((kp + 31) & ~31) + 8; }   // transposed A tiles
-__host__ __device__ constexpr int lda_r(int kp) { return ((kp + 31) & ~31) + 4; }   // row-major A tiles
+
+// row strides (elements of T) of the A tiles in shared memory, conflict-free
+// fragment loads: transposed tiles A(m, k) = As[k * lda + m] (rows 8 words
+// apart modulo 32 banks) and row-major tiles A(m, k) = As[m * lda + k] (rows 4
+// words apart)
+template <class T>
+__host__ __device__ constexpr int lda_t(int m)
+{
+    return sizeof(T) == 2 ? ((m + 63) & ~63) + 16 : ((m + 31) & ~31) + 8;
+}
+template <class T>
+__host__ __device__ constexpr int lda_r(int k)
+{
+    return sizeof(T) == 2 ? ((k + 63) & ~63) + 8 : ((k + 31) & ~31) + 4;
+}
 
 __device__ __forceinline__ uint32_t tf32(float x)
 {
@@ -44,87 +60,70 @@ __device__ __forceinline__ void mma_tf32(float *c, const uint32_t *a, const uint
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <class T>
-__device__ __forceinline__ float ld1(const T *p);
-template <>
-__device__ __forceinline__ float ld1<float>(const float *p) { return *p; }
-template <>
-__device__ __forceinline__ float ld1<__nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+// a stored matrix entry as a TF32 operand: BF16 widens exactly, and FP32
+// matrices are stored already rounded to TF32
+__device__ __forceinline__ uint32_t a_op(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint32_t a_op(__nv_bfloat16 v) { return __float_as_uint(__bfloat162float(v)); }
 
-// 16-byte piece of a row: 8 BF16 or 4 FP32 values, widened to FP32
-__device__ __forceinline__ int piece(const __nv_bfloat16 *p, float *v)
+// 16-byte cp.async into shared memory; !valid: the 16 bytes are zero-filled, nothing is read
+__device__ __forceinline__ void cp16(void *smem, const void *gmem, bool valid)
 {
-    const uint4 u = *(const uint4 *)p;
-    const __nv_bfloat162 *h = (const __nv_bfloat162 *)&u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float2 f = __bfloat1622float2(h[j]);
-        v[2 * j] = f.x;
-        v[2 * j + 1] = f.y;
-    }
-    return 8;
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0)
+                 : "memory");
 }
-__device__ __forceinline__ int piece(const float *p, float *v)
-{
-    const float4 u = *(const float4 *)p;
-    v[0] = u.x;
-    v[1] = u.y;
-    v[2] = u.z;
-    v[3] = u.w;
-    return 4;
-}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// rows [0, nrow) of kp columns (kp a multiple of 8) of a row-major global
-// matrix with row stride sstride (default kp) into shared memory (row stride lds, FP32), rows
-// [nrow, npad) zero; 16-byte loads, eight threads per row
+// rows [0, nrow) of ncol columns (ncol * sizeof(T) a multiple of 16 bytes) of a
+// row-major global matrix (row stride ss elements) into shared memory (row
+// stride lds elements), rows [nrow, npad) zero; 16-byte copies, issued by
+// threads t0 .. t0 + nt - 1 (not committed)
 template <class T>
-__device__ __forceinline__ void stage(float *dst, int lds, const T *src, int kp, int nrow, int npad, int sstride = 0)
+__device__ __forceinline__ void stage_async(T *dst, int lds, const T *src, int ncol, int nrow, int npad, int ss,
+                                            int t, int nt)
 {
     constexpr int E = 16 / (int)sizeof(T);
-    const int cpr = kp / E, sub = threadIdx.x & 7, ss = sstride ? sstride : kp;
-    for (int r = threadIdx.x >> 3; r < npad; r += blockDim.x >> 3)
-        for (int c = sub; c < cpr; c += 8) {
-            float v[8];
-            if (r < nrow) piece(src + (size_t)r * ss + c * E, v);
-            else
-#pragma unroll
-                for (int j = 0; j < E; ++j) v[j] = 0.f;
-            float *d = dst + r * lds + c * E;
-#pragma unroll
-            for (int j = 0; j < E; j += 4) *(float4 *)(d + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
-}
-
-// a 64-column FP32 tile [nrow][R-slice] from global (row stride R) into shared memory
-__device__ __forceinline__ void stage_x(float *dst, const float *src, int R, int nrow, int npad)
-{
-    for (int e = threadIdx.x; e < npad * (RT / 4); e += blockDim.x) {
-        const int r = e / (RT / 4), q = e - r * (RT / 4);
-        const float4 v = r < nrow ? __ldcg((const float4 *)(src + (size_t)r * R) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-        *(float4 *)(dst + r * LDB + 4 * q) = v;
+    const int cpr = ncol / E;
+    for (int c = t; c < npad * cpr; c += nt) {
+        const int r = c / cpr, q = c - r * cpr;
+        cp16(dst + r * lds + q * E, r < nrow ? (const void *)(src + (size_t)r * ss + q * E) : (const void *)src,
+             r < nrow);
     }
 }
 
-// Warp w accumulates rows 16w..16w+15 (of M <= 64) x the 64 columns:
-// acc[j] = n8 tile j.  A(m, k) = TRANS ? As[k * lda + m] : As[m * lda + k];
-// B(k, n) = Bs[k * LDB + n]; K a multiple of 8 (operands zero-padded).
-template <bool TRANS>
-__device__ __forceinline__ void cta_gemm(float (&acc)[8][4], const float *As, int lda, const float *Bs, int K)
+// a 64-column FP32 tile [nrow][R-slice] from global (row stride R) into shared
+// memory (row stride LDB), rows [nrow, npad) zero (not committed)
+__device__ __forceinline__ void stage_x_async(float *dst, const float *src, int R, int nrow, int npad, int t, int nt)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int m0 = 16 * warp;
+    for (int e = t; e < npad * (RT / 4); e += nt) {
+        const int r = e / (RT / 4), q = e - r * (RT / 4);
+        cp16(dst + r * LDB + 4 * q, r < nrow ? (const void *)(src + (size_t)r * R + 4 * q) : (const void *)src,
+             r < nrow);
+    }
+}
+
+// One warp accumulates rows m0..m0+15 (of M) x the 64 columns: acc[j] = n8
+// tile j.  A(m, k) = TRANS ? As[k * lda + m] : As[m * lda + k] (stored
+// precision T, taken as TF32 exactly); B(k, n) = Bs[k * LDB + n] (FP32,
+// rounded to TF32); K a multiple of 8 (operands zero-padded).
+template <bool TRANS, class T>
+__device__ __forceinline__ void warp_gemm(float (&acc)[8][4], const T *As, int lda, const float *Bs, int K, int m0)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     for (int k0 = 0; k0 < K; k0 += 8) {
         uint32_t a[4];
         if (TRANS) {
-            a[0] = tf32(As[(k0 + t) * lda + m0 + g]);
-            a[1] = tf32(As[(k0 + t) * lda + m0 + g + 8]);
-            a[2] = tf32(As[(k0 + t + 4) * lda + m0 + g]);
-            a[3] = tf32(As[(k0 + t + 4) * lda + m0 + g + 8]);
+            a[0] = a_op(As[(k0 + t) * lda + m0 + g]);
+            a[1] = a_op(As[(k0 + t) * lda + m0 + g + 8]);
+            a[2] = a_op(As[(k0 + t + 4) * lda + m0 + g]);
+            a[3] = a_op(As[(k0 + t + 4) * lda + m0 + g + 8]);
         } else {
-            a[0] = tf32(As[(m0 + g) * lda + k0 + t]);
-            a[1] = tf32(As[(m0 + g + 8) * lda + k0 + t]);
-            a[2] = tf32(As[(m0 + g) * lda + k0 + t + 4]);
-            a[3] = tf32(As[(m0 + g + 8) * lda + k0 + t + 4]);
+            a[0] = a_op(As[(m0 + g) * lda + k0 + t]);
+            a[1] = a_op(As[(m0 + g + 8) * lda + k0 + t]);
+            a[2] = a_op(As[(m0 + g) * lda + k0 + t + 4]);
+            a[3] = a_op(As[(m0 + g + 8) * lda + k0 + t + 4]);
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -140,13 +139,14 @@ __device__ __forceinline__ void acc_zero(float (&acc)[8][4])
     for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
 }
 
-// the warp's rows of the accumulator to a [rows][R-slice] FP32 tile (global or shared, row stride ld); rows < M
-__device__ __forceinline__ void acc_store(const float (&acc)[8][4], float *dst, size_t ld, int M, bool add)
+// rows m0 + (0..15) of the accumulator to a [rows][R-slice] FP32 tile
+// (global or shared, row stride ld); rows < M
+__device__ __forceinline__ void acc_store(const float (&acc)[8][4], float *dst, size_t ld, int M, bool add, int m0)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int m = 16 * warp + g + 8 * h;
+        const int m = m0 + g + 8 * h;
         if (m >= M) continue;
         float *row = dst + (size_t)m * ld;
 #pragma unroll
@@ -163,33 +163,38 @@ __device__ __forceinline__ void acc_store(const float (&acc)[8][4], float *dst, 
     }
 }
 
-// accumulator += a [rows][R-slice] FP32 tile (global, row stride ld); rows < M
-__device__ __forceinline__ void acc_add(float (&acc)[8][4], const float *src, size_t ld, int M)
+// named barrier over the nthreads threads (a multiple of 32) of one warp group
+__device__ __forceinline__ void group_sync(int id, int nthreads)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int m = 16 * warp + g + 8 * h;
-        if (m >= M) continue;
-        const float *row = src + (size_t)m * ld;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float2 v = __ldcg((const float2 *)(row + 8 * j + 2 * t));
-            acc[j][2 * h] += v.x;
-            acc[j][2 * h + 1] += v.y;
-        }
-    }
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 }  // namespace
 
-// shared memory of the kernels (bytes); mt = nlev * kp, the flattened row width
 // the flattened width is processed in chunks of fb_mc(kp, mt) columns (whole levels)
 __host__ __device__ constexpr int fb_mc(int kp, int mt) { return kp * (kp >= 128 ? 1 : 128 / kp) < mt ? kp * (kp >= 128 ? 1 : 128 / kp) : mt; }
-// host: shared memory for column chunks of at most mcmax = min(128, largest mt) columns
-static size_t fb_smem_proj(int mcmax) { return 4 * ((size_t)64 * LDB + (size_t)64 * lda_t(mcmax)); }
-static size_t fb_smem_couple(int kp) { return 4 * ((size_t)kp * lda_t(kp) + (size_t)kp * LDB); }
-static size_t fb_smem_expand(int mcmax) { return 4 * ((size_t)64 * lda_r(mcmax) + (size_t)mcmax * LDB); }
+// shared memory (bytes) for column chunks of at most mcmax = min(128, largest mt) columns
+template <class T>
+static size_t fb_smem_proj(int mcmax) { return 4 * (size_t)64 * LDB + sizeof(T) * (size_t)64 * lda_t<T>(mcmax); }
+// coupling: per warp group two buffers of S (kp x kp) and xhat (kp x 64), or the group sums
+__host__ __device__ constexpr int fb_groups(int kp) { return 4 / ((kp + 15) / 16); }
+template <class T>
+static size_t fb_smem_couple1(int kp)
+{
+    const size_t buf = sizeof(T) * (size_t)kp * lda_t<T>(kp) + 4 * (size_t)kp * LDB;
+    const size_t stg = (size_t)fb_groups(kp) * 2 * buf, red = (size_t)fb_groups(kp) * 4 * kp * LDB;
+    return stg > red ? stg : red;
+}
+// the meshes of a batch may have different padded ranks (multiples of 8, at most kpmax)
+template <class T>
+static size_t fb_smem_couple(int kpmax)
+{
+    size_t m = 0;
+    for (int kp = 8; kp <= kpmax; kp += 8) m = std::max(m, fb_smem_couple1<T>(kp));
+    return m;
+}
+template <class T>
+static size_t fb_smem_expand(int mcmax) { return sizeof(T) * (size_t)64 * lda_r<T>(mcmax) + 4 * (size_t)mcmax * LDB; }
 
 // ---------------------------------------------------------------------------
 // K1: leaf projections of every level, part[leaf][m][R-slice], m < mt
@@ -199,37 +204,40 @@ __global__ void __launch_bounds__(FT)
 k_fb_proj(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const float *__restrict__ Xall,
           const int *skip, const int *mdone)
 {
-    extern __shared__ __align__(16) float fsm[];
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
     const MrMesh &M = ms[item.x];
     const int mt = M.mt, rt = blockIdx.y * RT, mc = fb_mc(M.kp, mt);
-    const int LA = lda_t(mc);
-    float *Xs = fsm;                 // [64][LDB]   x rows of the leaf
-    float *Us = Xs + 64 * LDB;       // [64][LA]    a column chunk of the leaf's Ulf rows (A transposed)
+    const int LA = lda_t<T>(mc);
+    float *Xs = (float *)fsm_raw;                      // [64][LDB]  x rows of the leaf
+    T *Us = (T *)(fsm_raw + 4 * 64 * LDB);             // [64][LA]   a column chunk of the leaf's Ulf rows (A transposed)
     const int node = M.fl + item.y;
     const int b = M.kb[node], na = M.ke[node] - b;
     const int npad = (na + 7) & ~7;
-    stage_x(Xs, Xall + (size_t)(M.xoff + b) * R + rt, R, na, npad);
+    const int warp = threadIdx.x >> 5;
+    stage_x_async(Xs, Xall + (size_t)(M.xoff + b) * R + rt, R, na, npad, threadIdx.x, FT);
     float *dst = M.part + (size_t)item.y * mt * R + rt;
     for (int c0 = 0; c0 < mt; c0 += mc) {
         const int nc = min(mc, mt - c0);
-        __syncthreads();   // the previous chunk's products are done with Us
-        stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt + c0, nc, na, npad, mt);
+        if (c0 > 0) __syncthreads();   // the previous chunk's products are done with Us
+        stage_async<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt + c0, nc, na, npad, mt, threadIdx.x, FT);
+        cp_commit();
+        cp_wait<0>();
         __syncthreads();
         for (int m0 = 0; m0 < nc; m0 += 64) {
             float acc[8][4];
             acc_zero(acc);
-            if (m0 + 16 * (threadIdx.x >> 5) < nc) cta_gemm<true>(acc, Us + m0, LA, Xs, npad);
-            acc_store(acc, dst + (size_t)(c0 + m0) * R, R, min(64, nc - m0), false);
+            if (m0 + 16 * warp < nc) warp_gemm<true, T>(acc, Us + m0, LA, Xs, npad, 16 * warp);
+            acc_store(acc, dst + (size_t)(c0 + m0) * R, R, min(64, nc - m0), false, 16 * warp);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
 // K1b: node sums xhat[node][a][R-slice] = sum over the node's leaves of their
-// level-(node) slice of part, in leaf order
+// level-(node) slice of part, in leaf order (eight interleaved partial sums)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_fb_nsum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip, const int *mdone)
@@ -244,67 +252,116 @@ k_fb_nsum(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, 
     const int span = 1 << (M.L - l), leaf0 = ((node + 1) << (M.L - l)) - 1 - M.fl;
     const size_t hs = (size_t)kp * R;
     const float *src = M.part + (size_t)leaf0 * mt * R + (size_t)(l - M.lmin) * kp * R + rt;
+    constexpr int U = 8;
     for (int e = threadIdx.x; e < kp * (RT / 4); e += blockDim.x) {
         const int a = e / (RT / 4), q = e % (RT / 4);
-        // four interleaved partial sums (leaves j = 4t + u), combined in a fixed order
-        float4 p[4];
+        // partial sum u takes the leaves j = U t + u; combined in a fixed order
+        float4 p[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) p[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < U; ++u) p[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float *base = src + (size_t)a * R;
         int j = 0;
-        for (; j + 4 <= span; j += 4)
+        for (; j + U <= span; j += U) {
+            float4 w[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) w[u] = __ldcg((const float4 *)(base + (size_t)(j + u) * mt * R) + q);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                p[u].x += w[u].x;
+                p[u].y += w[u].y;
+                p[u].z += w[u].z;
+                p[u].w += w[u].w;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (j + u < span) {
                 const float4 w = __ldcg((const float4 *)(base + (size_t)(j + u) * mt * R) + q);
                 p[u].x += w.x;
                 p[u].y += w.y;
                 p[u].z += w.z;
                 p[u].w += w.w;
             }
-        for (int u = 0; j < span; ++j, ++u) {
-            const float4 w = __ldcg((const float4 *)(base + (size_t)j * mt * R) + q);
-            p[u].x += w.x;
-            p[u].y += w.y;
-            p[u].z += w.z;
-            p[u].w += w.w;
-        }
-        float4 v;
-        v.x = (p[0].x + p[1].x) + (p[2].x + p[3].x);
-        v.y = (p[0].y + p[1].y) + (p[2].y + p[3].y);
-        v.z = (p[0].z + p[1].z) + (p[2].z + p[3].z);
-        v.w = (p[0].w + p[1].w) + (p[2].w + p[3].w);
-        *(float4 *)(M.xhat + (size_t)node * hs + (size_t)a * R + rt + 4 * q) = v;
+#pragma unroll
+        for (int h = U / 2; h >= 1; h /= 2)
+#pragma unroll
+            for (int u = 0; u < h; ++u) {
+                p[u].x += p[u + h].x;
+                p[u].y += p[u + h].y;
+                p[u].z += p[u + h].z;
+                p[u].w += p[u + h].w;
+            }
+        *(float4 *)(M.xhat + (size_t)node * hs + (size_t)a * R + rt + 4 * q) = p[0];
     }
 }
 
 // ---------------------------------------------------------------------------
-// K2: coupling yc_node = sum_e S_e xhat_col(e)   (S_e stored transposed [b][a])
+// K2: coupling yc_node = sum_e S_e xhat_col(e)   (S_e stored transposed [b][a]).
+// The node's blocks are dealt round-robin to warp groups (a group = the
+// ceil(kp / 16) warps covering the kp rows); each group double-buffers its
+// blocks through cp.async and keeps its own accumulator; the group sums are
+// added in group order at the end (deterministic).
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(FT)
 k_fb_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, const int *skip, const int *mdone)
 {
-    extern __shared__ __align__(16) float fsm[];
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
     const MrMesh &M = ms[item.x];
     const int kp = M.kp, rt = blockIdx.y * RT, node = item.y;
-    const int LA = lda_t(kp);
-    float *Ss = fsm;              // [kp][LA]
-    float *Hs = Ss + kp * LA;     // [kp][LDB]
+    const int LA = lda_t<T>(kp);
+    const int mtl = (kp + 15) / 16, ng = 4 / mtl;
+    const int warp = threadIdx.x >> 5, grp = warp / mtl, m0 = 16 * (warp % mtl);
+    const bool in_group = grp < ng;
+    const int gt = threadIdx.x - grp * 32 * mtl, gn = 32 * mtl;   // thread index and size of the group
+    const size_t sbytes = sizeof(T) * (size_t)kp * LA, buf = sbytes + 4 * (size_t)kp * LDB;
+    unsigned char *gbase = fsm_raw + (size_t)grp * 2 * buf;
     const T *S = (const T *)M.S;
     const size_t hs = (size_t)kp * R;
+    const int e0 = M.fptr[node], ne = M.fptr[node + 1] - e0;
+    const int nmine = in_group && grp < ne ? (ne - grp + ng - 1) / ng : 0;   // this group's blocks grp, grp + ng, ...
     float acc[8][4];
     acc_zero(acc);
-    for (int e = M.fptr[node]; e < M.fptr[node + 1]; ++e) {
-        stage<T>(Ss, LA, S + (size_t)e * kp * kp, kp, kp, kp);
-        stage_x(Hs, M.xhat + (size_t)M.fcol[e] * hs + rt, R, kp, kp);
-        __syncthreads();
-        if (16 * (threadIdx.x >> 5) < kp) cta_gemm<true>(acc, Ss, LA, Hs, kp);
-        __syncthreads();
+    auto issue = [&](int i) {
+        const int e = e0 + grp + i * ng;
+        unsigned char *bb = gbase + (size_t)(i & 1) * buf;
+        stage_async<T>((T *)bb, LA, S + (size_t)e * kp * kp, kp, kp, kp, kp, gt, gn);
+        stage_x_async((float *)(bb + sbytes), M.xhat + (size_t)M.fcol[e] * hs + rt, R, kp, kp, gt, gn);
+    };
+    if (nmine > 0) {
+        issue(0);
+        cp_commit();
+        for (int i = 0; i < nmine; ++i) {
+            if (i + 1 < nmine) issue(i + 1);
+            cp_commit();
+            cp_wait<1>();               // this thread's copies of block i have landed
+            group_sync(1 + grp, gn);    // ... and every thread's of the group
+            const unsigned char *bb = gbase + (size_t)(i & 1) * buf;
+            if (m0 < kp) warp_gemm<true, T>(acc, (const T *)bb, LA, (const float *)(bb + sbytes), kp, m0);
+            group_sync(1 + grp, gn);    // buffer i & 1 is free for block i + 2
+        }
     }
-    acc_store(acc, M.yhat + (size_t)node * hs + rt, R, kp, false);
+    cp_wait<0>();
+    __syncthreads();
+    // group sums in shared memory (over the staging buffers), then in group order to yhat
+    float *red = (float *)fsm_raw;   // [ng][kp][LDB]
+    if (in_group) acc_store(acc, red + (size_t)grp * kp * LDB, LDB, kp, false, m0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kp * (RT / 4); e += blockDim.x) {
+        const int a = e / (RT / 4), q = e % (RT / 4);
+        float4 v = *(const float4 *)(red + (size_t)a * LDB + 4 * q);
+        for (int gg = 1; gg < ng; ++gg) {
+            const float4 w = *(const float4 *)(red + ((size_t)gg * kp + a) * LDB + 4 * q);
+            v.x += w.x;
+            v.y += w.y;
+            v.z += w.z;
+            v.w += w.w;
+        }
+        *(float4 *)(M.yhat + (size_t)node * hs + (size_t)a * R + rt + 4 * q) = v;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -315,96 +372,99 @@ __global__ void __launch_bounds__(FT)
 k_fb_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
             const int *skip, const int *mdone)
 {
-    extern __shared__ __align__(16) float fsm[];
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     if (skip && *skip) return;
     const int2 item = items[blockIdx.x];
     if (mdone && mdone[item.x]) return;
     const MrMesh &M = ms[item.x];
     const int kp = M.kp, mt = M.mt, rt = blockIdx.y * RT, L = M.L, lmin = M.lmin, mc = fb_mc(kp, mt);
-    const int LA = lda_r(mc);
-    float *Us = fsm;               // [64][LA]  a column chunk of the leaf's Ulf rows (row-major A)
-    float *Ys = Us + 64 * LA;      // [mc][LDB] the matching levels of the ancestors' yc
+    const int LA = lda_r<T>(mc);
+    T *Us = (T *)fsm_raw;                                               // [64][LA]  a column chunk of the leaf's Ulf rows
+    float *Ys = (float *)(fsm_raw + sizeof(T) * (size_t)64 * LA);       // [mc][LDB] the matching levels of the ancestors' yc
     const size_t hs = (size_t)kp * R;
     const int leafnode = M.fl + item.y;
     const int b = M.kb[leafnode], na = M.ke[leafnode] - b;
     const int npad = (na + 15) & ~15;
+    const int warp = threadIdx.x >> 5;
     float acc[8][4];
     acc_zero(acc);
     for (int c0 = 0; c0 < mt; c0 += mc) {
         const int nc = min(mc, mt - c0);
-        __syncthreads();   // the previous chunk's products are done with Us, Ys
+        if (c0 > 0) __syncthreads();   // the previous chunk's products are done with Us, Ys
         for (int lc = 0; lc < nc / kp; ++lc) {
             const int l = lmin + c0 / kp + lc;
             const int node = ((leafnode + 1) >> (L - l)) - 1;
             float *dst = Ys + (size_t)lc * kp * LDB;
             if (M.fptr[node + 1] > M.fptr[node]) {
-                stage_x(dst, M.yhat + (size_t)node * hs + rt, R, kp, kp);
-            } else {
+                stage_x_async(dst, M.yhat + (size_t)node * hs + rt, R, kp, kp, threadIdx.x, FT);
+            } else {   // a node without admissible blocks has no yc (zero)
                 for (int e = threadIdx.x; e < kp * (RT / 4); e += blockDim.x)
                     *(float4 *)(dst + (e / (RT / 4)) * LDB + 4 * (e % (RT / 4))) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
-        stage<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt + c0, nc, na, npad, mt);
+        stage_async<T>(Us, LA, (const T *)M.Ulf + (size_t)b * mt + c0, nc, na, npad, mt, threadIdx.x, FT);
+        cp_commit();
+        cp_wait<0>();
         __syncthreads();
-        if (16 * (threadIdx.x >> 5) < npad) cta_gemm<false>(acc, Us, LA, Ys, nc);
+        if (16 * warp < npad) warp_gemm<false, T>(acc, Us, LA, Ys, nc, 16 * warp);
     }
-    acc_store(acc, Yall + (size_t)(M.xoff + b) * R + rt, R, na, true);
+    acc_store(acc, Yall + (size_t)(M.xoff + b) * R + rt, R, na, true, 16 * warp);
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// the largest shared memory of the far kernels for padded rank kp and mt = nlev * kp
+// the largest shared memory of the far kernels for padded rank kp and mt = nlev * kp (FP32 tiles: the larger)
 size_t far_batched_smem(int kp, int mt)
 {
     const int mc = std::min(128, mt);
-    return std::max(fb_smem_proj(mc), std::max(fb_smem_couple(kp), fb_smem_expand(mc)));
+    return std::max(fb_smem_proj<float>(mc), std::max(fb_smem_couple<float>(kp), fb_smem_expand<float>(mc)));
 }
 
 template <class T>
 static void far_attrs(int kp, int mt)
 {
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_proj(std::min(128, mt))));
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_couple(kp)));
-    VFD_CUDA(cudaFuncSetAttribute(k_fb_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_expand(std::min(128, mt))));
+    const int mc = std::min(128, mt);
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_proj<T>(mc)));
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_couple<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_couple<T>(kp)));
+    VFD_CUDA(cudaFuncSetAttribute(k_fb_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem_expand<T>(mc)));
+}
+
+template <class T>
+static void launch_far_side_t(BatchData &b, int R, const float *X, cudaStream_t side, const int *skip,
+                              const int *mdone)
+{
+    const MrMesh *ms = (const MrMesh *)b.desc.p;
+    const int kp = b.max_kp, mt = b.max_mt, mc = std::min(128, mt);
+    dim3 gl(b.n_leaf_items, R / RT), gn(b.n_node_items, R / RT);
+    far_attrs<T>(kp, mt);
+    k_fb_proj<T><<<gl, FT, fb_smem_proj<T>(mc), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
+    if (b.n_node_items) {
+        k_fb_nsum<<<gn, 256, 0, side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
+        k_fb_couple<T><<<gn, FT, fb_smem_couple<T>(kp), side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
+    }
+    VFD_CUDA(cudaGetLastError());
 }
 
 // projections, node sums and coupling (K1, K1b, K2) on stream `side`
 void launch_far_side(BatchData &b, int R, const float *X, cudaStream_t side, const int *skip, const int *mdone)
 {
-    const MrMesh *ms = (const MrMesh *)b.desc.p;
-    const int kp = b.max_kp, mt = b.max_mt;
-    dim3 gl(b.n_leaf_items, R / RT), gn(b.n_node_items, R / RT);
-    if (b.precision == VFD_BF16) {
-        far_attrs<__nv_bfloat16>(kp, mt);
-        k_fb_proj<__nv_bfloat16><<<gl, FT, fb_smem_proj(std::min(128, mt)), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip,
-                                                                     mdone);
-    } else {
-        far_attrs<float>(kp, mt);
-        k_fb_proj<float><<<gl, FT, fb_smem_proj(std::min(128, mt)), side>>>(ms, (const int2 *)b.leaf_items.p, R, X, skip, mdone);
-    }
-    if (b.n_node_items) {
-        k_fb_nsum<<<gn, 256, 0, side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
-        if (b.precision == VFD_BF16)
-            k_fb_couple<__nv_bfloat16><<<gn, FT, fb_smem_couple(kp), side>>>(ms, (const int2 *)b.node_items.p, R, skip,
-                                                                             mdone);
-        else
-            k_fb_couple<float><<<gn, FT, fb_smem_couple(kp), side>>>(ms, (const int2 *)b.node_items.p, R, skip, mdone);
-    }
-    VFD_CUDA(cudaGetLastError());
+    if (b.precision == VFD_BF16) launch_far_side_t<__nv_bfloat16>(b, R, X, side, skip, mdone);
+    else launch_far_side_t<float>(b, R, X, side, skip, mdone);
 }
 
 // expansion (K3) on stream `st`, adding into Y
 void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone)
 {
     const MrMesh *ms = (const MrMesh *)b.desc.p;
-    const int mt = b.max_mt;
+    const int mc = std::min(128, b.max_mt);
     dim3 gl(b.n_leaf_items, R / RT);
     if (b.precision == VFD_BF16)
-        k_fb_expand<__nv_bfloat16><<<gl, FT, fb_smem_expand(std::min(128, mt)), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip,
-                                                                       mdone);
+        k_fb_expand<__nv_bfloat16><<<gl, FT, fb_smem_expand<__nv_bfloat16>(mc), st>>>(ms, (const int2 *)b.leaf_items.p, R,
+                                                                                        Y, skip, mdone);
     else
-        k_fb_expand<float><<<gl, FT, fb_smem_expand(std::min(128, mt)), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip, mdone);
+        k_fb_expand<float><<<gl, FT, fb_smem_expand<float>(mc), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip,
+                                                                        mdone);
     VFD_CUDA(cudaGetLastError());
 }
 

@@ -1,6 +1,7 @@
 // Near panels of the batched BF16 apply on the 5th-generation tensor cores,
-// the panel streamed by bulk (TMA-engine) copies, with the B + M rows in the
-// epilogue:  Y[leaf rows][rt .. rt+63] = D_panel Xg + (B + M) X.
+// the panel streamed by bulk (TMA-engine) copies:
+// Y[leaf rows][rt .. rt+63] = D_panel Xg (the B + M rows and the sum of a
+// split panel's partial tiles follow in k_mr_rows, as for the mma.sync kernel).
 //
 // This is the dense inadmissible-leaf product of Sec. 5.2 (eq. e:k-near) for
 // 64 right-hand sides at a time, plus the sparse singular near field and the
@@ -28,11 +29,8 @@
 // Rows na..127 of the M = 128 operand are whatever the shared memory holds;
 // they only produce accumulator rows that are never read.
 // Epilogue: warps 0 and 1 read the accumulator rows of the leaf (tensor
-// memory lanes 0..63) into shared memory; all four warps add the B + M CSR
-// rows (FP32, x in FP32; or only the diagonal where B + M is folded into the
-// panel) and write Y.  With the panel split over P CTAs each
-// CTA writes its partial tile; the last CTA of the item to finish (counter)
-// sums the partials in a fixed order, so the result is deterministic.
+// memory lanes 0..63) into shared memory; all four warps write the tile to Y
+// (part 0 of a split panel) or to partial buffer z - 1 of Y2 (part z > 0).
 //
 // Every mbarrier wait is bounded by the global timer (limit passed in); on
 // expiry the CTA records the error, stops issuing, waits (bounded again) for
@@ -121,9 +119,9 @@ struct TcItem {
 
 template <int NSTAGE>
 __global__ void __launch_bounds__(128, 1)
-k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int R, const void *__restrict__ Xc,
-           size_t xlo, const float *__restrict__ Xall, float *__restrict__ Yall, float *__restrict__ part, int *__restrict__ cnt,
-           long long wait_ns, int *err, const int *skip, const int *mdone)
+k_near_tma(const TcItem *__restrict__ items, int R, const void *__restrict__ Xc, size_t xlo,
+           float *__restrict__ Yall, float *__restrict__ Y2all, size_t pstride, long long wait_ns, int *err,
+           const int *skip, const int *mdone)
 {
     extern __shared__ unsigned char tsm_raw[];
     if (skip && *skip) return;
@@ -134,7 +132,6 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
     uint64_t *bars = (uint64_t *)(tsm + NSTAGE * TC_STAGE_BYTES);   // fullA, fullB, empty [NSTAGE each], done
     uint32_t *tslot = (uint32_t *)(bars + 3 * NSTAGE + 1);
     volatile int *abort_f = (volatile int *)(tslot + 1);
-    int *last_f = (int *)(tslot + 2);
     int *gs = (int *)(tslot + 4);   // gather columns of this CTA's stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rt = blockIdx.y * RT, ksplit = gridDim.z, z = blockIdx.z;
@@ -304,69 +301,13 @@ k_near_tma(const TcItem *__restrict__ items, const MrMesh *__restrict__ ms, int 
     __syncthreads();
     if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(taddr));
 
-    // ---- epilogue: partial tiles, fixed-order sum, B + M rows, Y
-    const int na = it.na, ntile = gridDim.y;
-    const size_t tile = (size_t)blockIdx.x * ntile + blockIdx.y;
-    if (ksplit > 1) {
-        float *mine = part + (tile * ksplit + z) * (size_t)(64 * RT);
-        if (!aborted)
-            for (int e = tid; e < na * (RT / 4); e += 128) {
-                const int row = e / (RT / 4), q = e % (RT / 4);
-                ((float4 *)mine)[e] = *(const float4 *)(acc_s + row * TC_LDS + 4 * q);
-            }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const int prev = atomicAdd(cnt + tile, 1);
-            *last_f = prev == ksplit - 1;
-            if (*last_f) cnt[tile] = 0;   // ready for the next launch
-        }
-        __syncthreads();
-        if (!*last_f) return;
-        __threadfence();
-        if (*(volatile int *)err) return;   // some part timed out: leave Y unwritten
-    } else if (aborted) {
-        return;
-    }
-    const MrMesh &M = ms[it.mesh];
-    const float4 *X4 = (const float4 *)(Xall + (size_t)it.xoff * R + rt);
-    const int R4 = R / 4, i0 = it.row0 - it.xoff;
+    // ---- epilogue: the tile (or this part's partial tile) to Y / Y2
+    if (aborted) return;   // Y unwritten; the host reports the expired wait
+    const int na = it.na;
+    float *Yo = z == 0 ? Yall : Y2all + (size_t)(z - 1) * pstride;
     for (int e = tid; e < na * (RT / 4); e += 128) {
         const int row = e / (RT / 4), q = e % (RT / 4);
-        float4 v;
-        if (ksplit > 1) {
-            const float4 *pp = (const float4 *)(part + tile * ksplit * (size_t)(64 * RT)) + e;
-            v = __ldcg(pp);
-            for (int zz = 1; zz < ksplit; ++zz) {
-                const float4 w = __ldcg(pp + (size_t)zz * (64 * RT / 4));
-                v.x += w.x;
-                v.y += w.y;
-                v.z += w.z;
-                v.w += w.w;
-            }
-        } else {
-            v = *(const float4 *)(acc_s + row * TC_LDS + 4 * q);
-        }
-        const int i = i0 + row;
-        if (M.diag) {   // B + M off the diagonal folded into the panel
-            const float a = M.diag[i];
-            const float4 x = X4[(size_t)i * R4 + q];
-            v.x = fmaf(a, x.x, v.x);
-            v.y = fmaf(a, x.y, v.y);
-            v.z = fmaf(a, x.z, v.z);
-            v.w = fmaf(a, x.w, v.w);
-        } else {        // B + M rows (FP32 CSR)
-#pragma unroll 4
-            for (int c = M.rowptr[i]; c < M.rowptr[i + 1]; ++c) {
-                const float a = M.val[c];
-                const float4 x = X4[(size_t)M.colidx[c] * R4 + q];
-                v.x = fmaf(a, x.x, v.x);
-                v.y = fmaf(a, x.y, v.y);
-                v.z = fmaf(a, x.z, v.z);
-                v.w = fmaf(a, x.w, v.w);
-            }
-        }
-        *(float4 *)(Yall + (size_t)(it.row0 + row) * R + rt + 4 * q) = v;
+        *(float4 *)(Yo + (size_t)(it.row0 + row) * R + rt + 4 * q) = *(const float4 *)(acc_s + row * TC_LDS + 4 * q);
     }
 }
 
@@ -459,17 +400,15 @@ bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X
                      const int *skip, const int *mdone)
 {
     const size_t shm = near_tma_smem(nstage, b.max_panel_w);
+    const size_t pstride = (size_t)b.ntot * R;   // partial tiles of parts 1.. in Y2 (k_mr_rows sums them)
     if (shm > 227 * 1024 || ksplit < 1 || ksplit > 4 || b.n_tc_items == 0) return false;
-    const size_t need = (size_t)b.n_tc_items * (R / RT) * ksplit * 64 * RT;
-    if (ksplit > 1 && b.tc_part.n < need) return false;
+    if (ksplit > 1 && b.y2.n < (size_t)(ksplit - 1) * pstride) return false;
     dim3 g(b.n_tc_items, R / RT, ksplit);
     const TcItem *items = (const TcItem *)b.tc_items.p;
-    const MrMesh *ms = (const MrMesh *)b.desc.p;
 #define VFD_TMA_CASE(NS)                                                                                         \
     if (nstage == NS) {                                                                                          \
         VFD_CUDA(cudaFuncSetAttribute(k_near_tma<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));    \
-        k_near_tma<NS><<<g, 128, shm, st>>>(items, ms, R, b.xc.p, (size_t)b.ntot * R, X, Y, b.tc_part.p,          \
-                                            b.tc_cnt.p, b.wait_ns,                                                \
+        k_near_tma<NS><<<g, 128, shm, st>>>(items, R, b.xc.p, (size_t)b.ntot * R, Y, b.y2.p, pstride, b.wait_ns, \
                                             b.tc_err.p, skip, mdone);                                             \
         VFD_CUDA(cudaGetLastError());                                                                            \
         return true;                                                                                             \

@@ -338,8 +338,6 @@ struct BatchData {
     DBuf<int> tc_err;                   // set by the tcgen05 kernel when a pipeline wait expires
     DBuf<unsigned char> tc_items;       // TcItem records of the tcgen05 kernel (one per (mesh, leaf))
     int n_tc_items = 0;
-    DBuf<float> tc_part;                // split partial tiles of the tcgen05 kernel
-    DBuf<int> tc_cnt;                   // per (item, RHS tile) arrival counters (zero between launches)
     long long wait_ns = 1000000000LL;   // bound of the tcgen05 kernel's pipeline waits
     double ru_drop = 0.03;              // recursive-residual reduction between reliable updates
     // batched refinement solve
