@@ -64,12 +64,6 @@ __device__ __forceinline__ uint32_t f2tf32(float x)
     return r;
 }
 
-template <class T>
-__device__ __forceinline__ T from_f(float v);
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-template <>
-__device__ __forceinline__ float from_f<float>(float v) { return __uint_as_float(f2tf32(v)); }
 
 }  // namespace
 
@@ -80,37 +74,46 @@ __device__ __forceinline__ float from_f<float>(float v) { return __uint_as_float
 // NSTAGE-deep cp.async pipeline:
 //   As[stage][64][LDA]  panel rows (T, as stored: FP32 or BF16), zero-filled
 //                       beyond the leaf's rows and the panel width;
-//   Bs[stage][NK][LDB]  gathered x rows X[gcol[k]][rt .. rt+63] (FP32),
-//                       zero-filled for the padding columns (gcol = -1).
+//   Bs[stage]           gathered x rows X[gcol[k]][rt .. rt+63], zero-filled
+//                       for the padding columns (gcol = -1): FP32 for TF32
+//                       panels, the BF16 hi and lo rows for BF16 panels.
 // The gather indices of the whole panel are staged in shared memory first.
-// A fragments come from ldmatrix (FP32 panels are stored pre-rounded to TF32
-// for this kernel), B fragments from two shared loads, rounded to TF32
-// (cvt.rna) or packed to BF16x2 (cvt.rn).  Rounding to nearest matters:
-// truncation (what the tensor core does with raw FP32 bits) biases the
-// low-precision operator, and the refinement then needed about twice the
-// inner iterations.  x enters as two terms, hi = round(x) and lo =
-// round(x - hi), each multiplied by the panel (twice the MMAs): the panel's
-// own rounding is a fixed perturbation of the operator (its row sums are
-// compensated), but rounding x anew in every apply adds noise of the unit
-// roundoff relative to each entry of x, and for the smooth directions of the
-// preconditioned iteration that noise is larger than A x itself (the inner
-// iteration on one 21k-DoF mesh took 1253 BF16 steps instead of 39).  The panel's chunks are split over gridDim.z CTAs; CTA z
-// writes its partial product to Y (z = 0) or to partial buffer z - 1 of Y2,
-// summed by the CSR kernel.  The stage width NK, the depth NSTAGE and the
-// split are picked per batch by timing the candidates (near_configs).
+// A fragments come from ldmatrix (FP32 panels are stored pre-rounded to
+// TF32 for this kernel); B fragments from two shared loads rounded to TF32
+// (cvt.rna), or for BF16 from ldmatrix.trans of the hi and lo rows (rounded
+// to nearest once per apply).  Rounding to nearest matters: truncation (what
+// the tensor core does with raw FP32 bits) biases the low-precision
+// operator, and the refinement then needed about twice the inner
+// iterations.  x enters as two terms, hi = round(x) and lo = round(x - hi),
+// each multiplied by the panel (twice the MMAs): the panel's own rounding is
+// a fixed perturbation of the operator (its row sums are compensated), but
+// rounding x anew in every apply adds noise of the unit roundoff relative to
+// each entry of x, and for the smooth directions of the preconditioned
+// iteration that noise is larger than A x itself (the inner iteration on
+// one 21k-DoF mesh took 1253 BF16 steps instead of 39).  The panel's chunks
+// are split over gridDim.z CTAs; CTA z writes its partial product to Y (z =
+// 0) or to partial buffer z - 1 of Y2, summed by the CSR kernel.  The stage
+// width NK, the depth NSTAGE and the split are picked per batch by timing
+// the candidates (near_configs).
 // ---------------------------------------------------------------------------
 constexpr int KSPLIT_MAX = 4;
 
+// B tiles: TF32 panels take x in FP32 ([NK][LDB] floats, split at fragment
+// time); BF16 panels take the hi and lo BF16 blocks of x made once per apply
+// ([2][NK][LDB] BF16, hi then lo), read with ldmatrix.trans
 template <class T, int NK>
 struct NearTile {
-    static constexpr int LDA = NK + (sizeof(T) == 2 ? 8 : 4);   // A row stride (elements): conflict-free fragments
-    static constexpr int LDB = RT + (sizeof(T) == 2 ? 4 : 8);   // B row stride (floats)
+    static constexpr bool BF = sizeof(T) == 2;
+    static constexpr int LDA = NK + (BF ? 8 : 4);      // A row stride (elements): conflict-free fragments
+    static constexpr int LDB = RT + 8;                  // B row stride (elements: BF16 or floats)
+    static constexpr int B_ELEM = BF ? 2 : 4;
     static constexpr int A_BYTES = 64 * LDA * (int)sizeof(T);
-    static constexpr int B_BYTES = NK * LDB * 4;
+    static constexpr int B_BYTES = (BF ? 2 : 1) * NK * LDB * B_ELEM;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int A_CHUNKS = 64 * NK * (int)sizeof(T) / 16;   // 16-byte copies per stage
-    static constexpr int B_CHUNKS = NK * RT * 4 / 16;
-    static_assert(A_BYTES % 16 == 0 && B_BYTES % 16 == 0 && (LDA * sizeof(T)) % 16 == 0 && (LDB * 4) % 16 == 0,
+    static constexpr int B_CPR = RT * B_ELEM / 16;                   // 16-byte copies per x row
+    static constexpr int B_CHUNKS = (BF ? 2 : 1) * NK * B_CPR;
+    static_assert(A_BYTES % 16 == 0 && B_BYTES % 16 == 0 && (LDA * sizeof(T)) % 16 == 0 && (LDB * B_ELEM) % 16 == 0,
                   "16-byte aligned rows");
 };
 
@@ -124,6 +127,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t *r, const void *smem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(s));
+}
+
 __device__ __forceinline__ void ldmatrix_x4(uint32_t *r, const void *smem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -132,23 +143,15 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t *r, const void *smem)
                  : "r"(s));
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
-{
-    uint32_t r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-}
-// the two halves of a packed pair as FP32 (exact)
-__device__ __forceinline__ float bf16_lo(uint32_t r) { return __uint_as_float(r << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t r) { return __uint_as_float(r & 0xffff0000u); }
 
 // WARPS = 8: warp tile 16 rows x 32 RHS; WARPS = 4: 32 rows x 32 RHS (two m16
 // tiles share each B fragment).  NACC = 2: even and odd k-steps accumulate
 // into separate registers (twice the independent mma chains), summed at the end.
 template <class T, int NK, int NSTAGE, int WARPS, int NACC>
 __global__ void __launch_bounds__(WARPS * 32)
-k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ Xall, float *__restrict__ Yall,
-          float *__restrict__ Y2all, size_t pstride, const int *skip, const int *mdone)
+k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ Xall,
+          const __nv_bfloat16 *__restrict__ Xc, size_t xlo, float *__restrict__ Yall, float *__restrict__ Y2all,
+          size_t pstride, const int *skip, const int *mdone)
 {
     using TT = NearTile<T, NK>;
     constexpr int NEAR_THREADS = WARPS * 32, MT = 8 / WARPS, RW = 4 / MT;   // m16 tiles per warp, warps per row band
@@ -179,11 +182,22 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
             cp_async16(As + row * TT::LDA + q * EPC, ok ? (const void *)(Dp + (size_t)row * W + col) : (const void *)D,
                        ok);
         }
-        for (int c = threadIdx.x; c < TT::B_CHUNKS; c += NEAR_THREADS) {
-            const int kr = c / (RT / 4), q = c - kr * (RT / 4), col = k0 + kr;
-            const int j = col < W ? gs[col] : -1;
-            cp_async16(Bs + kr * TT::LDB + q * 4, j >= 0 ? (const void *)(X + (size_t)j * R + rt + q * 4) : (const void *)X,
-                       j >= 0);
+        if constexpr (TT::BF) {
+            // hi rows [0, NK), lo rows [NK, 2 NK) of the stage's x tile
+            __nv_bfloat16 *B16 = (__nv_bfloat16 *)Bs;
+            for (int c = threadIdx.x; c < TT::B_CHUNKS; c += NEAR_THREADS) {
+                const int hr = c / TT::B_CPR, q = c - hr * TT::B_CPR, h = hr / NK, kr = hr - h * NK, col = k0 + kr;
+                const int j = col < W ? gs[col] : -1;
+                const __nv_bfloat16 *src = Xc + (size_t)h * xlo + ((size_t)(it.xoff + j) * R + rt + q * 8);
+                cp_async16(B16 + hr * TT::LDB + q * 8, j >= 0 ? (const void *)src : (const void *)Xc, j >= 0);
+            }
+        } else {
+            for (int c = threadIdx.x; c < TT::B_CHUNKS; c += NEAR_THREADS) {
+                const int kr = c / TT::B_CPR, q = c - kr * TT::B_CPR, col = k0 + kr;
+                const int j = col < W ? gs[col] : -1;
+                cp_async16(Bs + kr * TT::LDB + q * 4,
+                           j >= 0 ? (const void *)(X + (size_t)j * R + rt + q * 4) : (const void *)X, j >= 0);
+            }
         }
     };
 
@@ -219,38 +233,46 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
                 const int m = lane >> 3, rr = lane & 7;
                 ldmatrix_x4(a[mt], As + (r0 + 16 * mt + rr + (m & 1) * 8) * TT::LDA + ks + (m >> 1) * (16 / (int)sizeof(T)));
             }
+            if constexpr (TT::BF) {
+                // x = hi + lo, both BF16: the product sees x to ~2^-16 (one BF16
+                // rounding of x alone is noise of 2^-9 relative in every entry,
+                // which swamps A x for the smooth directions of the
+                // preconditioned iteration).  ldmatrix.trans: matrices (k 0-7 |
+                // 8-15) x (n 0-7 | 8-15) of two n8 tiles give b0, b1 of each
+                const __nv_bfloat16 *Bh = (const __nv_bfloat16 *)Bs, *Bl = Bh + NK * TT::LDB;
+                const int brow = ks + (lane & 7) + ((lane >> 3) & 1) * 8, bcol = n0 + ((lane >> 4) & 1) * 8;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = n0 + j * 8 + g;
-                uint32_t bb[2];
-                if constexpr (sizeof(T) == 2) {
-                    // x = hi + lo, both BF16: the product sees x to ~2^-16 (one BF16
-                    // rounding of x alone is noise of 2^-9 relative in every entry,
-                    // which swamps A x for the smooth directions of the
-                    // preconditioned iteration)
-                    const float *B0 = Bs + (ks + 2 * t4) * TT::LDB + n;
-                    const float x0 = B0[0], x1 = B0[TT::LDB], x2 = B0[8 * TT::LDB], x3 = B0[9 * TT::LDB];
-                    bb[0] = pack_bf16x2(x0, x1);
-                    bb[1] = pack_bf16x2(x2, x3);
-                    const uint32_t bl[2] = {pack_bf16x2(x0 - bf16_lo(bb[0]), x1 - bf16_hi(bb[0])),
-                                            pack_bf16x2(x2 - bf16_lo(bb[1]), x3 - bf16_hi(bb[1]))};
+                for (int jp = 0; jp < 2; ++jp) {
+                    uint32_t bh[4], bl[4];
+                    ldmatrix_x4_trans(bh, Bh + brow * TT::LDB + bcol + 16 * jp);
+                    ldmatrix_x4_trans(bl, Bl + brow * TT::LDB + bcol + 16 * jp);
 #pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-                        if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS + 1) % NACC][mt][j], a[mt], bl);
-                } else {
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int j = 2 * jp + jj;
+                        const uint32_t hi[2] = {bh[2 * jj], bh[2 * jj + 1]}, lo[2] = {bl[2 * jj], bl[2 * jj + 1]};
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt)
+                            if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS + 1) % NACC][mt][j], a[mt], lo);
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt)
+                            if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS) % NACC][mt][j], a[mt], hi);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
                     // the same split in TF32: x = hi + lo, both rounded to TF32
-                    const float *B0 = Bs + (ks + t4) * TT::LDB + n;
+                    const float *B0 = Bs + (ks + t4) * TT::LDB + n0 + j * 8 + g;
                     const float x0 = B0[0], x1 = B0[4 * TT::LDB];
-                    bb[0] = f2tf32(x0);
-                    bb[1] = f2tf32(x1);
+                    const uint32_t bb[2] = {f2tf32(x0), f2tf32(x1)};
                     const uint32_t bl[2] = {f2tf32(x0 - __uint_as_float(bb[0])), f2tf32(x1 - __uint_as_float(bb[1]))};
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt)
                         if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS + 1) % NACC][mt][j], a[mt], bl);
-                }
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-                    if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS) % NACC][mt][j], a[mt], bb);
+                    for (int mt = 0; mt < MT; ++mt)
+                        if (r0 + 16 * mt < na) MmaTraits<T>::mma(acc[(ks / KS) % NACC][mt][j], a[mt], bb);
+                }
             }
         }
     }
@@ -270,7 +292,7 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
         }
 }
 
-// x for the tcgen05 near kernel as two BF16 terms: b[i] = hi = BF16(x),
+// x for the BF16 near kernels as two BF16 terms: b[i] = hi = BF16(x),
 // b[n + i] = lo = BF16(x - hi)
 __global__ void k_x_to_bf16(long long n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ b)
 {
@@ -301,29 +323,31 @@ constexpr int kNearCfgCount = (int)(sizeof(kNearCfgs) / sizeof(kNearCfgs[0]));
 
 template <class T, int NK, int NS, int WARPS, int NACC>
 static bool launch_near_cfg(int ksplit, int n_items, int max_panel_w, const NearItem *items, int R, const float *X,
-                            float *Y, float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone)
+                            const __nv_bfloat16 *Xc, size_t xlo, float *Y, float *Y2, size_t pstride, cudaStream_t st,
+                            const int *skip, const int *mdone)
 {
     const size_t shm = near_smem_bytes<T, NK, NS>(max_panel_w);
     if (shm > 227 * 1024) return false;
     VFD_CUDA(cudaFuncSetAttribute(k_mr_near<T, NK, NS, WARPS, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)shm));
     dim3 g(n_items, R / RT, ksplit);
-    k_mr_near<T, NK, NS, WARPS, NACC><<<g, WARPS * 32, shm, st>>>(items, R, X, Y, Y2, pstride, skip, mdone);
+    k_mr_near<T, NK, NS, WARPS, NACC><<<g, WARPS * 32, shm, st>>>(items, R, X, Xc, xlo, Y, Y2, pstride, skip, mdone);
     return true;
 }
 
 // launch configuration c of the mma.sync kernel (near products only); false
 // if it does not fit in shared memory or c is a tcgen05 candidate
 template <class T>
-static bool launch_near(int c, int n_items, int max_panel_w, const NearItem *items, int R, const float *X, float *Y,
-                        float *Y2, size_t pstride, cudaStream_t st, const int *skip, const int *mdone)
+static bool launch_near(int c, int n_items, int max_panel_w, const NearItem *items, int R, const float *X,
+                        const __nv_bfloat16 *Xc, size_t xlo, float *Y, float *Y2, size_t pstride, cudaStream_t st,
+                        const int *skip, const int *mdone)
 {
     const NearCfg &f = kNearCfgs[c];
     if (f.tc) return false;
 #define VFD_NEAR_CASE(NKV, NSV, WV, AV)                                                                          \
     if (f.nk == NKV && f.nstage == NSV && f.warps == WV && f.nacc == AV)                                         \
-        return launch_near_cfg<T, NKV, NSV, WV, AV>(f.ksplit, n_items, max_panel_w, items, R, X, Y, Y2, pstride,   \
-                                                    st, skip, mdone);
+        return launch_near_cfg<T, NKV, NSV, WV, AV>(f.ksplit, n_items, max_panel_w, items, R, X, Xc, xlo, Y, Y2, \
+                                                    pstride, st, skip, mdone);
     VFD_NEAR_CASE(32, 3, 8, 1)
     VFD_NEAR_CASE(16, 4, 8, 1)
     VFD_NEAR_CASE(64, 2, 8, 1)
@@ -408,8 +432,9 @@ static bool launch_near_phase(BatchData &b, int c, int R, const float *X, float 
         if (sizeof(T) != 2 || b.n_tc_items != b.n_near_items) return false;
         if (b.n_tc_items > 0 && !launch_near_tma(b, f.nstage, f.ksplit, R, X, Y, st, skip, mdone)) return false;
     } else if (b.n_near_items > 0 &&
-               !launch_near<T>(c, b.n_near_items, b.max_panel_w, (const NearItem *)b.near_items.p, R, X, Y, b.y2.p,
-                               (size_t)b.ntot * R, st, skip, mdone)) {
+               !launch_near<T>(c, b.n_near_items, b.max_panel_w, (const NearItem *)b.near_items.p, R, X,
+                               (const __nv_bfloat16 *)b.xc.p, (size_t)b.ntot * R, Y, b.y2.p, (size_t)b.ntot * R, st,
+                               skip, mdone)) {
         return false;
     }
     const MrMesh *ms = (const MrMesh *)b.desc.p;
@@ -678,7 +703,7 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
         launch_far_side(b, R, X, b.side, skip, mdone);
         VFD_CUDA(cudaEventRecord(b.ev_join, b.side));
     }
-    if (kNearCfgs[b.near_cfg].tc && !x_bf16_ready) {
+    if (sizeof(T) == 2 && !x_bf16_ready) {   // x as BF16 hi and lo blocks for either near kernel
         const long long n = (long long)b.ntot * R;
         k_x_to_bf16<<<cdiv(n, 256), 256, 0, st>>>(n, X, (__nv_bfloat16 *)b.xc.p);
         VFD_CUDA(cudaGetLastError());
@@ -826,7 +851,7 @@ void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st,
     }
 }
 
-// p (interleaved FP32, R columns) into the tcgen05 kernel's BF16 x block
+// p (interleaved FP32, R columns) into the BF16 hi / lo x blocks of the near kernels
 void batch_x_to_bf16(BatchData &b, const float *X, int R, cudaStream_t st)
 {
     const long long n = (long long)b.ntot * R;
@@ -834,9 +859,9 @@ void batch_x_to_bf16(BatchData &b, const float *X, int R, cudaStream_t st)
     VFD_CUDA(cudaGetLastError());
 }
 
-void *batch_tc_x(BatchData &b)
+void *batch_x16(BatchData &b)
 {
-    return (b.near_cfg >= 0 && kNearCfgs[b.near_cfg].tc) ? (void *)b.xc.p : nullptr;
+    return b.precision == VFD_BF16 ? (void *)b.xc.p : nullptr;
 }
 
 // column-major FP64 <-> interleaved FP32

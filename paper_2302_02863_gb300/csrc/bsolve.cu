@@ -226,9 +226,11 @@ __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float
 }
 
 // p = r + beta p (same block decomposition as the reductions); r is z in the
-// preconditioned iteration; upd (non-null): only the meshes just updated
+// preconditioned iteration; upd (non-null): only the meshes just updated;
+// p16 (non-null): p also as BF16 hi (p16) and lo (p16 + p16lo) for the near kernels
 __global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, float *__restrict__ p,
-                                            const int *__restrict__ upd)
+                                            const int *__restrict__ upd, __nv_bfloat16 *__restrict__ p16,
+                                            long long p16lo)
 {
     if (S.flag[BF_DONE]) return;
     const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
@@ -238,7 +240,13 @@ __global__ void __launch_bounds__(BT) k_b_p(Seg S, const float *__restrict__ r, 
     const size_t base = (size_t)r0 * Rp, n = (size_t)N * Rp;
     for (size_t e = (size_t)j * blockDim.x + threadIdx.x; e < n; e += (size_t)nb * blockDim.x) {
         const int c = (int)(e % Rp);
-        p[base + e] = fmaf(scal(S, C_BE, m, c), p[base + e], r[base + e]);
+        const float v = fmaf(scal(S, C_BE, m, c), p[base + e], r[base + e]);
+        p[base + e] = v;
+        if (p16) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            p16[base + e] = h;
+            p16[p16lo + base + e] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
     }
 }
 
@@ -407,7 +415,7 @@ __device__ __forceinline__ float mesh_sum(const Seg &S, const float *red, int m,
 // one cooperative launch with two grid barriers:
 //   A: p.q (block partials) | alpha = r.p / p.q per column
 //   B: x += alpha p, r -= alpha q, r.r (partials) | beta, convergence
-//   C: p = r + beta p, and p as two BF16 terms for the tensor-core near kernel
+//   C: p = r + beta p, and p as two BF16 terms for the BF16 near kernels
 //      (p16: hi; p16 + p16lo: lo = the rounding error of hi)
 // Same arithmetic and the same fixed summation orders as k_b_pq, k_b_xr and
 // k_b_p.  red2 holds the second partials (the first are still being read).
@@ -864,8 +872,8 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
     batch_apply(b, b.p.p, b.q.p, Rp, st, nullptr, nullptr);
     if (b.exec) return;
     // the fused vector kernel needs every block resident (cooperative launch)
-    // and at most BT columns; p in BF16 goes to the tensor-core kernel's x
-    // block when that kernel is the tuned one
+    // and at most BT columns; in a BF16 batch it also writes p as the BF16 hi
+    // and lo blocks the near kernels read
     {
         int dev = 0, nsm = 0, per = 0, coop = 0;
         VFD_CUDA(cudaGetDevice(&dev));
@@ -873,7 +881,7 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
         VFD_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         VFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_iter, BT, 0));
         b.fused = coop && Rp <= BT && b.nred <= per * nsm && !b.pcg;
-        b.p16_target = batch_tc_x(b) ;
+        b.p16_target = batch_x16(b);
         if (b.fused && !b.gbar.p) {
             b.gbar.alloc(2);
             VFD_CUDA(cudaMemset(b.gbar.p, 0, 2 * sizeof(unsigned)));
@@ -885,10 +893,11 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
     VFD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     try {
         for (int it = 0; it < BCHUNK; ++it) {
-            batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh, b.fused);
+            // p in BF16 hi / lo comes from the vector kernels (BF16 batches)
+            batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh, b.p16_target != nullptr);
             if (b.fused) {
                 // one cooperative launch for the iteration's vector work; p also in
-                // BF16 for the next apply's tensor-core near kernel
+                // BF16 hi / lo for the next apply's near kernel
                 Seg Sv = S;
                 float *red2 = b.red2.p, *xv = b.x.p, *rv = b.r.p, *pv = b.p.p;
                 const float *qv = b.q.p;
@@ -904,11 +913,13 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
                 k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
                 k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, 1);
                 bprec_apply(b, S, 1, nullptr, nullptr, cs);
-                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.z.p, b.p.p, nullptr);
+                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.z.p, b.p.p, nullptr, (__nv_bfloat16 *)b.p16_target,
+                                             (long long)b.ntot * Rp);
             } else {
                 k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
                 k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, 0);
-                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p, nullptr);
+                k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p, nullptr, (__nv_bfloat16 *)b.p16_target,
+                                             (long long)b.ntot * Rp);
             }
         }
     } catch (...) {
@@ -1064,11 +1075,11 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
     VFD_CUDA(cudaGetLastError());
     if (b.pcg) {   // z = M^-1 r, r.p = r.z, p = z
         bprec_apply(b, S, 0, nullptr, nullptr, st);
-        k_b_p<<<b.nred, BT, 0, st>>>(S, b.z.p, b.p.p, nullptr);
+        k_b_p<<<b.nred, BT, 0, st>>>(S, b.z.p, b.p.p, nullptr, nullptr, 0);
     }
     capture_bcg(b, Rp, st);
-    // the captured apply reads p in BF16 from the fused kernel: provide the first one
-    if (b.fused && b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
+    // the captured apply reads p in BF16 hi / lo from the vector kernels: provide the first one
+    if (b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
     const float drop2 = (float)(RU_DROP * RU_DROP);
     int it = 0;
     while (true) {
@@ -1107,11 +1118,11 @@ vfd_status batch_solve(BatchData &b, const double *const *F, double *const *U, c
                                            b.pcg ? b.z.p : nullptr);
         if (b.pcg) {   // z = M^-1 r_true, beta from r.z, p = z + beta (beta_old p_old)
             bprec_apply(b, S, 2, gamma_d.p, upd_d.p, st);
-            k_b_p<<<b.nred, BT, 0, st>>>(S, b.z.p, b.p.p, upd_d.p);
+            k_b_p<<<b.nred, BT, 0, st>>>(S, b.z.p, b.p.p, upd_d.p, nullptr, 0);
         }
         k_b_rp<<<b.nred, BT, 0, st>>>(S, b.r.p, b.p.p, upd_d.p);
         VFD_CUDA(cudaGetLastError());
-        if (b.fused && b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
+        if (b.p16_target) batch_x_to_bf16(b, b.p.p, Rp, st);
     }
     VFD_CUDA(cudaStreamSynchronize(st));
     if (iters)

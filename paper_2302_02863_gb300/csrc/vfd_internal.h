@@ -334,7 +334,7 @@ struct BatchData {
     DBuf<float> fpart;                  // far-field leaf projections (all meshes)
     int max_mt = 0;                     // largest flattened basis width nlev * kp
     DBuf<float> xi, yi;                 // interleaved staging of the column-major apply
-    DBuf<unsigned char> xc;             // x for the tcgen05 kernel, BF16 hi then lo ([2][ntot][R])
+    DBuf<unsigned char> xc;             // x for the BF16 near kernels, BF16 hi then lo ([2][ntot][R])
     DBuf<int> tc_err;                   // set by the tcgen05 kernel when a pipeline wait expires
     DBuf<unsigned char> tc_items;       // TcItem records of the tcgen05 kernel (one per (mesh, leaf))
     int n_tc_items = 0;
@@ -343,7 +343,7 @@ struct BatchData {
     // batched refinement solve
     DBuf<float> x, r, p, q, b, red, red2, sc;
     bool fused = false;                 // the captured iteration uses the cooperative vector kernel
-    void *p16_target = nullptr;         // where that kernel writes p in BF16 (the tcgen05 x block), or null
+    void *p16_target = nullptr;         // where that kernel writes p as BF16 hi / lo (the near kernels' x blocks), or null
     DBuf<unsigned> gbar;                // its grid-barrier counter and generation
     DBuf<int> flag, red_items, red_mesh;
     int nred = 0, sR = 0;
@@ -406,7 +406,7 @@ void batch_check(BatchData &b, cudaStream_t st);
 int batch_set_config(BatchData &b, int cfg);
 void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
                  const int *mdone, bool x_bf16_ready = false);
-void *batch_tc_x(BatchData &b);   // the BF16 x block of the tuned tcgen05 near kernel, or null
+void *batch_x16(BatchData &b);   // the BF16 hi / lo x blocks the near kernels read (BF16 batches), or null
 void batch_x_to_bf16(BatchData &b, const float *X, int R, cudaStream_t st);
 void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,
                           cudaStream_t st);
