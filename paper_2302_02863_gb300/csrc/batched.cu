@@ -318,7 +318,8 @@ static const NearCfg kNearCfgs[] = {{32, 3, 2, 8, 1, 0}, {32, 3, 3, 8, 1, 0}, {1
                                     {64, 2, 2, 8, 1, 0}, {32, 3, 3, 4, 1, 0}, {16, 4, 3, 4, 1, 0},
                                     {32, 3, 2, 8, 2, 0}, {16, 4, 3, 8, 2, 0}, {16, 4, 3, 4, 2, 0},
                                     {64, 4, 1, 4, 1, 1}, {64, 4, 2, 4, 1, 1}, {64, 6, 1, 4, 1, 1},
-                                    {64, 6, 2, 4, 1, 1}, {64, 3, 2, 4, 1, 1}, {64, 3, 3, 4, 1, 1}};
+                                    {64, 6, 2, 4, 1, 1}, {64, 3, 2, 4, 1, 1}, {64, 3, 3, 4, 1, 1},
+                                    {64, 2, 1, 4, 1, 1}, {64, 2, 2, 4, 1, 1}, {64, 2, 3, 4, 1, 1}};
 constexpr int kNearCfgCount = (int)(sizeof(kNearCfgs) / sizeof(kNearCfgs[0]));
 
 template <class T, int NK, int NS, int WARPS, int NACC>

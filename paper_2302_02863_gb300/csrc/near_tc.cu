@@ -413,6 +413,7 @@ bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X
         VFD_CUDA(cudaGetLastError());                                                                            \
         return true;                                                                                             \
     }
+    VFD_TMA_CASE(2)
     VFD_TMA_CASE(3)
     VFD_TMA_CASE(4)
     VFD_TMA_CASE(6)

@@ -143,3 +143,28 @@ def test_inner_order_refinement_reaches_fp64_solution(disk):
         assert st == vfd.VFD_OK and np.all(rel <= 1e-10)
         d = (torch.linalg.norm(U - U64, dim=1) / torch.linalg.norm(U64, dim=1)).max().item()
         assert d < 1e-8, (prec, d)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 6, 8])
+@pytest.mark.parametrize("prec", [vfd.VFD_FP32, vfd.VFD_BF16])
+def test_batched_far_chain_every_padded_rank(disk, p, prec):
+    """The batched far chain at ranks p^2 = 4, 9, 25, 36, 64 (padded to 8, 16,
+    32, 40, 64 columns: coupling blocks dealt to 4, 4, 2, 1, 1 warp groups)
+    against the FP64 operator of the same mesh: within a few units of the
+    panels' rounding (about 1e-4 of ||A x|| with x as hi + lo terms)."""
+    m, s, k = disk
+    mesh = vfd.vfd_mesh(2, m.coords, m.cells, m.cell_is_interior, leaf_m=16, cheb_p=p, lam=0.75, rho_lambda=0.75)
+    assert mesh.info["far_blocks"] > 0 and mesh.info["rank"] == p * p
+    op64 = vfd.vfd_assemble(mesh, s, k, 0.9)
+    opl = vfd.vfd_assemble(mesh, s, k, 0.9, precision=prec)
+    g = torch.Generator(device="cuda").manual_seed(100 + p)
+    X = torch.randn(64, mesh.n_dof, dtype=torch.float64, device="cuda", generator=g)
+    Y64, Yl, K64 = torch.empty_like(X), torch.empty_like(X), torch.empty_like(X)
+    vfd.vfd_apply(op64, X, Y64)
+    vfd.vfd_apply(opl, X, Yl)
+    vfd.vfd_apply_parts(op64, vfd.VFD_PART_KFAR, X, K64)
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(Yl - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)).max().item()
+    far = (torch.linalg.norm(K64) / torch.linalg.norm(Y64)).item()
+    print(f"p {p} prec {prec}: rel err {err:.2e}, far part {far:.2e} of A x")
+    assert err < 5e-4, (err, far)
