@@ -401,14 +401,28 @@ __device__ bool grid_barrier(unsigned *cnt, unsigned *gen, unsigned nblocks, lon
     return ok_s != 0;
 }
 
-// the sum over the blocks of mesh m of the per-column partials red[block][c],
-// in block order (every block of the mesh gets the same value)
-__device__ __forceinline__ float mesh_sum(const Seg &S, const float *red, int m, int c)
+// the sums over the blocks of mesh m of the per-column partials red[block][c],
+// by the whole block in the order of seg_reduce's last block (lane rl takes
+// blocks rl, rl + lanes, ...; the lanes' sums are added in lane order), into
+// out[c] in shared memory; every block of the mesh gets the same values
+__device__ void mesh_sums(const Seg &S, const float *red, int m, float *sh, float *out)
 {
     const int b0 = S.mesh[4 * m], nb = S.mesh[4 * m + 1];
-    float s = 0.f;
-    for (int bI = 0; bI < nb; ++bI) s += __ldcg(red + (size_t)(b0 + bI) * S.Rp + c);
-    return s;
+    const int Rp = S.Rp, Rc = min(Rp, (int)blockDim.x), lanes = blockDim.x / Rc;
+    for (int c0 = 0; c0 < Rp; c0 += Rc) {
+        const int cl = threadIdx.x % Rc, c = c0 + cl, rl = threadIdx.x / Rc;
+        float s = 0.f;
+        if (rl < lanes && c < Rp)
+            for (int bI = rl; bI < nb; bI += lanes) s += __ldcg(red + (size_t)(b0 + bI) * Rp + c);
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        if (rl == 0 && c < Rp) {
+            float tot = 0.f;
+            for (int q = 0; q < lanes; ++q) tot += sh[q * Rc + cl];
+            out[c] = tot;
+        }
+        __syncthreads();
+    }
 }
 
 // One CG iteration's vector work after q = A p, for every (mesh, column), in
@@ -425,7 +439,7 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
                                                long long p16lo, unsigned *gbar, long long wait_ns, int *err)
 {
     __shared__ float sh[BT];
-    __shared__ float al_s[BT], be_s[BT], rr_s[BT];   // per column (Rp <= BT)
+    __shared__ float al_s[BT], be_s[BT], rr_s[BT], sum_s[BT];   // per column (Rp <= BT)
     __shared__ int live_s, done_s;
     if (S.flag[BF_DONE]) return;   // stable during this launch: only written after barrier 1
     const int m = S.items[2 * blockIdx.x], j = S.items[2 * blockIdx.x + 1];
@@ -454,8 +468,9 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
     }
     if (!grid_barrier(gbar, gbar + 1, gridDim.x, wait_ns, err)) return;
     // alpha per column (the exact line search r.p / p.q)
+    mesh_sums(S, S.red, m, sh, sum_s);
     for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
-        const float pq = mesh_sum(S, S.red, m, c);
+        const float pq = sum_s[c];
         const float rr = scal(S, C_RR, m, c), rp = scal(S, C_RP, m, c);
         const bool live = work && rr > scal(S, C_TOL, m, c) && pq > 0.f && rp > 0.f;
         al_s[c] = live ? rp / pq : 0.f;
@@ -493,11 +508,11 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
     if (!grid_barrier(gbar, gbar + 1, gridDim.x, wait_ns, err)) return;
     // beta and convergence per column; every block of a mesh reaches the same decision
     if (threadIdx.x == 0) live_s = 0;
-    __syncthreads();
+    mesh_sums(S, red2, m, sh, sum_s);
     for (int c = threadIdx.x; c < Rp; c += blockDim.x) {
         float be = 0.f;
         if (work) {
-            const float s = mesh_sum(S, red2, m, c), rr = rr_s[c];
+            const float s = sum_s[c], rr = rr_s[c];
             const bool moved = al_s[c] != 0.f;
             if (moved) {
                 be = rr > 0.f ? s / rr : 0.f;
