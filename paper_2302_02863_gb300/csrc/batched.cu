@@ -235,7 +235,7 @@ k_mr_near(const NearItem *__restrict__ items, int R, const float *__restrict__ X
             }
             if constexpr (TT::BF) {
                 // x = hi + lo, both BF16: the product sees x to ~2^-16 (one BF16
-                // rounding of x alone is noise of 2^-9 relative in every entry,
+                // rounding of x alone errs by up to 2^-8 relative in every entry,
                 // which swamps A x for the smooth directions of the
                 // preconditioned iteration).  ldmatrix.trans: matrices (k 0-7 |
                 // 8-15) x (n 0-7 | 8-15) of two n8 tiles give b0, b1 of each
