@@ -200,10 +200,11 @@ vfd_status vfd_assemble(vfd_mesh_t mesh, const vfd_field *s, const vfd_field *lo
  * FP64 operator.  VFD_FP32 / VFD_BF16 operators apply the low-precision
  * operator of the mixed-precision solve: with nrhs a multiple of 64 (and
  * leaves of at most 64 DoFs) the batched path -- near panels on the tensor
- * cores in TF32 (VFD_FP32) or BF16 (VFD_BF16), B + M and the far field in
- * FP32, with the diagonal of B + M compensated on the first batched use so
- * that the rounded operator is exact on constant vectors -- else column by
- * column with K in FP32 and B + M in FP64. */
+ * cores in TF32 (VFD_FP32) or BF16 (VFD_BF16) with x entering as two rounded
+ * terms hi + lo, B + M and the far field in FP32, with the diagonal of B + M
+ * compensated on the first batched use so that the rounded operator is exact
+ * on constant vectors -- else column by column with K in FP32 and B + M in
+ * FP64. */
 vfd_status vfd_apply(vfd_op_t op, const double *X, double *Y, int64_t nrhs, int64_t ld, void *stream);
 
 /* Y = (sum of the selected parts) X; parts is a mask of VFD_PART_*. */
