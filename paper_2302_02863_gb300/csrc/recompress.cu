@@ -179,12 +179,10 @@ __global__ void k_rc_factors(int k, const int *__restrict__ fptr, const double *
     const int n = blockIdx.x;
     if (fptr[n + 1] == fptr[n]) return;
     __shared__ int slot[KMAX];
-    __shared__ double emax;
     const double *e = ev + (size_t)n * k;
     if (threadIdx.x == 0) {
         double mx = 0.0;
         for (int i = 0; i < k; ++i) mx = fmax(mx, e[i]);
-        emax = mx;
         int r = 0;
         for (int i = 0; i < k; ++i) slot[i] = (e[i] > 1e-16 * mx && e[i] > 0.0) ? r++ : -1;
     }
