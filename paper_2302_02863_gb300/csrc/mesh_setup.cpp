@@ -1086,7 +1086,7 @@ double closest_in_simplex(int d, const double *V, const double *x, double *bary)
     const int nvx = d + 1;
     double best = 1e300;
     for (int mask = 1; mask < (1 << nvx); ++mask) {
-        int idx[4], n = 0;
+        int idx[4] = {0, 0, 0, 0}, n = 0;   // mask >= 1: idx[0] is always set below
         for (int a = 0; a < nvx; ++a)
             if (mask >> a & 1) idx[n++] = a;
         const double *v0 = V + (size_t)idx[0] * d;
