@@ -695,13 +695,15 @@ static void ensure_batch(BatchData &b, int R, cudaStream_t st)
 
 template <class T>
 static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
-                             const int *mdone, bool x_bf16_ready)
+                             const int *mdone, bool x_bf16_ready, float *Yfar)
 {
     if (b.any_far) {
-        // upsweep and coupling on the side stream, concurrent with the near panels
+        // projections and coupling on the side stream, concurrent with the near
+        // panels; with Yfar the expansion too (written there)
         VFD_CUDA(cudaEventRecord(b.ev_fork, st));
         VFD_CUDA(cudaStreamWaitEvent(b.side, b.ev_fork, 0));
         launch_far_side(b, R, X, b.side, skip, mdone);
+        if (Yfar) launch_far_down(b, R, Yfar, b.side, skip, mdone, false);
         VFD_CUDA(cudaEventRecord(b.ev_join, b.side));
     }
     if (sizeof(T) == 2 && !x_bf16_ready) {   // x as BF16 hi and lo blocks for either near kernel
@@ -713,7 +715,7 @@ static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cuda
     VFD_REQUIRE(launched, VFD_EUNSUPPORTED, "batched apply: the pinned near-panel configuration does not apply");
     if (b.any_far) {
         VFD_CUDA(cudaStreamWaitEvent(st, b.ev_join, 0));
-        launch_far_down(b, R, Y, st, skip, mdone);
+        if (!Yfar) launch_far_down(b, R, Y, st, skip, mdone, true);
     }
     VFD_CUDA(cudaGetLastError());
 }
@@ -801,7 +803,7 @@ __global__ void k_comp_diag(int N, const double *__restrict__ y64, const float *
 // smooth low modes alone.  The outer FP64 residual is unaffected.
 template <class T>
 static void batch_apply_impl(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
-                             const int *mdone, bool x_bf16_ready);
+                             const int *mdone, bool x_bf16_ready, float *Yfar);
 
 template <class T>
 static void compensate_diag(BatchData &b, cudaStream_t st)
@@ -815,7 +817,7 @@ static void compensate_diag(BatchData &b, cudaStream_t st)
     ones.alloc(n);
     ylow.alloc(n);
     k_fill1f<<<cdiv(n, 256), 256, 0, st>>>(n, ones.p);
-    batch_apply_impl<T>(b, ones.p, ylow.p, R, st, nullptr, nullptr, false);
+    batch_apply_impl<T>(b, ones.p, ylow.p, R, st, nullptr, nullptr, false, nullptr);
     batch_check(b, st);
     for (int i = 0; i < b.nmesh; ++i) {
         OpData &op = *b.ops[i];
@@ -839,16 +841,16 @@ static void compensate_diag(BatchData &b, cudaStream_t st)
 // skip: device flag, nonzero = launch nothing; mdone: per-mesh device flags,
 // nonzero = leave that mesh's rows of Y alone (both may be null)
 void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip, const int *mdone,
-                 bool x_bf16_ready)
+                 bool x_bf16_ready, float *Yfar)
 {
     VFD_REQUIRE(R % RT == 0 && R > 0, VFD_EINVAL, "batched apply needs a multiple of 64 columns");
     ensure_batch(b, R, st);
     if (b.precision == VFD_BF16) {
         compensate_diag<__nv_bfloat16>(b, st);
-        batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone, x_bf16_ready);
+        batch_apply_impl<__nv_bfloat16>(b, X, Y, R, st, skip, mdone, x_bf16_ready, Yfar);
     } else {
         compensate_diag<float>(b, st);
-        batch_apply_impl<float>(b, X, Y, R, st, skip, mdone, x_bf16_ready);
+        batch_apply_impl<float>(b, X, Y, R, st, skip, mdone, x_bf16_ready, Yfar);
     }
 }
 

@@ -158,11 +158,12 @@ __global__ void __launch_bounds__(BT) k_b_init(Seg S, const float *__restrict__ 
 // step rr / pq would overshoot and break r_new . p = 0 for good); alpha = 0
 // for converged columns and for a direction that is not a descent direction
 // (the next p update then restarts the column from p = r)
-__global__ void __launch_bounds__(BT) k_b_pq(Seg S, const float *__restrict__ p, const float *__restrict__ q)
+__global__ void __launch_bounds__(BT) k_b_pq(Seg S, const float *__restrict__ p, const float *__restrict__ q,
+                                             const float *__restrict__ qf)
 {
     if (S.flag[BF_DONE]) return;
     seg_reduce<true>(
-        S, [&](size_t t, int, int) { return p[t] * q[t]; },
+        S, [&](size_t t, int, int) { return p[t] * (qf ? q[t] + qf[t] : q[t]); },
         [&](int m, int c, float s) {
             const float rr = scal(S, C_RR, m, c), rp = scal(S, C_RP, m, c);
             const bool live = rr > scal(S, C_TOL, m, c) && s > 0.f && rp > 0.f;
@@ -174,7 +175,8 @@ __global__ void __launch_bounds__(BT) k_b_pq(Seg S, const float *__restrict__ p,
 // x += alpha p; r -= alpha q; rr_new; beta; convergence of every column
 // (pcg: beta and r.p come from r.z after the preconditioner, k_bp_zr)
 __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float *__restrict__ r,
-                                             const float *__restrict__ p, const float *__restrict__ q, int pcg)
+                                             const float *__restrict__ p, const float *__restrict__ q,
+                                             const float *__restrict__ qf, int pcg)
 {
     if (S.flag[BF_DONE]) return;
     __shared__ int live;
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(BT) k_b_xr(Seg S, float *__restrict__ x, float
         [&](size_t t, int mm, int c) {
             const float al = scal(S, C_AL, mm, c);
             x[t] = fmaf(al, p[t], x[t]);
-            const float rn = fmaf(-al, q[t], r[t]);
+            const float rn = fmaf(-al, qf ? q[t] + qf[t] : q[t], r[t]);
             r[t] = rn;
             return rn * rn;
         },
@@ -435,8 +437,9 @@ __device__ void mesh_sums(const Seg &S, const float *red, int m, float *sh, floa
 // k_b_p.  red2 holds the second partials (the first are still being read).
 __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, float *__restrict__ x,
                                                float *__restrict__ r, float *__restrict__ p,
-                                               const float *__restrict__ q, __nv_bfloat16 *__restrict__ p16,
-                                               long long p16lo, unsigned *gbar, long long wait_ns, int *err)
+                                               const float *__restrict__ q, const float *__restrict__ qf,
+                                               __nv_bfloat16 *__restrict__ p16, long long p16lo, unsigned *gbar,
+                                               long long wait_ns, int *err)
 {
     __shared__ float sh[BT];
     __shared__ float al_s[BT], be_s[BT], rr_s[BT], sum_s[BT];   // per column (Rp <= BT)
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
 #pragma unroll 4
             for (int i = j * lanes + rl; i < N; i += nb * lanes) {
                 const size_t t = (size_t)(r0 + i) * Rp + c;
-                v += p[t] * q[t];
+                v += p[t] * (qf ? q[t] + qf[t] : q[t]);
             }
         sh[threadIdx.x] = v;
         __syncthreads();
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(BT) k_b_iter(Seg S, float *__restrict__ red2, 
             for (int i = j * lanes + rl; i < N; i += nb * lanes) {
                 const size_t t = (size_t)(r0 + i) * Rp + c;
                 x[t] = fmaf(al, p[t], x[t]);
-                const float rn = fmaf(-al, q[t], r[t]);
+                const float rn = fmaf(-al, qf ? q[t] + qf[t] : q[t], r[t]);
                 r[t] = rn;
                 v += rn * rn;
             }
@@ -755,6 +758,8 @@ static void ensure_solve(BatchData &b, int Rp)
     b.r.alloc(nv);
     b.p.alloc(nv);
     b.q.alloc(nv);
+    b.qf.alloc(nv);   // rows of meshes without a far field stay zero
+    VFD_CUDA(cudaMemset(b.qf.p, 0, b.qf.bytes()));
     b.b.alloc(nv);
     b.red.alloc((size_t)nred * Rp);
     b.red2.alloc((size_t)nred * Rp);
@@ -902,6 +907,9 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
             VFD_CUDA(cudaMemset(b.gbar.p, 0, 2 * sizeof(unsigned)));
         }
     }
+    // the far field's expansion runs on the side stream into qf, concurrent with
+    // the near panels; the vector kernels read q + qf
+    float *qf = b.any_far ? b.qf.p : nullptr;
     cudaStream_t cs;
     VFD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph;
@@ -909,30 +917,31 @@ static void capture_bcg(BatchData &b, int Rp, cudaStream_t st)
     try {
         for (int it = 0; it < BCHUNK; ++it) {
             // p in BF16 hi / lo comes from the vector kernels (BF16 batches)
-            batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh, b.p16_target != nullptr);
+            batch_apply(b, b.p.p, b.q.p, Rp, cs, b.flag.p, b.flag.p + FL_CNT + 2 * b.nmesh, b.p16_target != nullptr,
+                        qf);
             if (b.fused) {
                 // one cooperative launch for the iteration's vector work; p also in
                 // BF16 hi / lo for the next apply's near kernel
                 Seg Sv = S;
                 float *red2 = b.red2.p, *xv = b.x.p, *rv = b.r.p, *pv = b.p.p;
-                const float *qv = b.q.p;
+                const float *qv = b.q.p, *qfv = qf;
                 __nv_bfloat16 *p16 = (__nv_bfloat16 *)b.p16_target;
                 long long p16lo = (long long)b.ntot * Rp;
                 unsigned *gb = b.gbar.p;
                 long long wns = b.wait_ns;
                 int *err = b.tc_err.p;
-                void *args[] = {&Sv, &red2, &xv, &rv, &pv, &qv, &p16, &p16lo, &gb, &wns, &err};
+                void *args[] = {&Sv, &red2, &xv, &rv, &pv, &qv, &qfv, &p16, &p16lo, &gb, &wns, &err};
                 VFD_CUDA(cudaLaunchCooperativeKernel((const void *)k_b_iter, b.nred, BT, args, 0, cs));
             } else if (b.pcg) {
                 // preconditioned: p.q, x/r update, z = M^-1 r with r.z and beta, p = z + beta p
-                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
-                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, 1);
+                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p, qf);
+                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, qf, 1);
                 bprec_apply(b, S, 1, nullptr, nullptr, cs);
                 k_b_p<<<b.nred, BT, 0, cs>>>(S, b.z.p, b.p.p, nullptr, (__nv_bfloat16 *)b.p16_target,
                                              (long long)b.ntot * Rp);
             } else {
-                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p);
-                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, 0);
+                k_b_pq<<<b.nred, BT, 0, cs>>>(S, b.p.p, b.q.p, qf);
+                k_b_xr<<<b.nred, BT, 0, cs>>>(S, b.x.p, b.r.p, b.p.p, b.q.p, qf, 0);
                 k_b_p<<<b.nred, BT, 0, cs>>>(S, b.r.p, b.p.p, nullptr, (__nv_bfloat16 *)b.p16_target,
                                              (long long)b.ntot * Rp);
             }

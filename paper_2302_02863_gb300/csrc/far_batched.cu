@@ -370,7 +370,7 @@ k_fb_couple(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R
 template <class T>
 __global__ void __launch_bounds__(FT)
 k_fb_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R, float *__restrict__ Yall,
-            const int *skip, const int *mdone)
+            int add, const int *skip, const int *mdone)
 {
     extern __shared__ __align__(16) unsigned char fsm_raw[];
     if (skip && *skip) return;
@@ -408,7 +408,7 @@ k_fb_expand(const MrMesh *__restrict__ ms, const int2 *__restrict__ items, int R
         __syncthreads();
         if (16 * warp < npad) warp_gemm<false, T>(acc, Us, LA, Ys, nc, 16 * warp);
     }
-    acc_store(acc, Yall + (size_t)(M.xoff + b) * R + rt, R, na, true, 16 * warp);
+    acc_store(acc, Yall + (size_t)(M.xoff + b) * R + rt, R, na, add != 0, 16 * warp);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,18 +453,18 @@ void launch_far_side(BatchData &b, int R, const float *X, cudaStream_t side, con
     else launch_far_side_t<float>(b, R, X, side, skip, mdone);
 }
 
-// expansion (K3) on stream `st`, adding into Y
-void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone)
+// expansion (K3) on stream `st`, adding into Y (add) or writing it
+void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone, bool add)
 {
     const MrMesh *ms = (const MrMesh *)b.desc.p;
     const int mc = std::min(128, b.max_mt);
     dim3 gl(b.n_leaf_items, R / RT);
     if (b.precision == VFD_BF16)
         k_fb_expand<__nv_bfloat16><<<gl, FT, fb_smem_expand<__nv_bfloat16>(mc), st>>>(ms, (const int2 *)b.leaf_items.p, R,
-                                                                                        Y, skip, mdone);
+                                                                                        Y, add ? 1 : 0, skip, mdone);
     else
-        k_fb_expand<float><<<gl, FT, fb_smem_expand<float>(mc), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y, skip,
-                                                                        mdone);
+        k_fb_expand<float><<<gl, FT, fb_smem_expand<float>(mc), st>>>(ms, (const int2 *)b.leaf_items.p, R, Y,
+                                                                        add ? 1 : 0, skip, mdone);
     VFD_CUDA(cudaGetLastError());
 }
 

@@ -342,6 +342,7 @@ struct BatchData {
     double ru_drop = 0.03;              // recursive-residual reduction between reliable updates
     // batched refinement solve
     DBuf<float> x, r, p, q, b, red, red2, sc;
+    DBuf<float> qf;                     // far-field part of q in the captured iteration (added by the vector kernels)
     bool fused = false;                 // the captured iteration uses the cooperative vector kernel
     void *p16_target = nullptr;         // where that kernel writes p as BF16 hi / lo (the near kernels' x blocks), or null
     DBuf<unsigned> gbar;                // its grid-barrier counter and generation
@@ -404,8 +405,10 @@ BatchData *op_batch(OpData &op);   // the op's batch of one (created on first us
 int batch_tuning(const BatchData &b, int *chosen, float *us, int n);
 void batch_check(BatchData &b, cudaStream_t st);
 int batch_set_config(BatchData &b, int cfg);
+// Yfar (non-null): the far field goes to Yfar (written, on the side stream)
+// instead of being added into Y; the caller adds the two
 void batch_apply(BatchData &b, const float *X, float *Y, int R, cudaStream_t st, const int *skip,
-                 const int *mdone, bool x_bf16_ready = false);
+                 const int *mdone, bool x_bf16_ready = false, float *Yfar = nullptr);
 void *batch_x16(BatchData &b);   // the BF16 hi / lo x blocks the near kernels read (BF16 batches), or null
 void batch_x_to_bf16(BatchData &b, const float *X, int R, cudaStream_t st);
 void batch_apply_colmajor(BatchData &b, const double *const *X, double *const *Y, const int64_t *ld, int nrhs,
@@ -423,7 +426,7 @@ bool launch_near_tma(BatchData &b, int nstage, int ksplit, int R, const float *X
 void build_far_lowp(const MeshData &m, OpData &op, cudaStream_t st);
 size_t far_batched_smem(int kp, int mt);
 void launch_far_side(BatchData &b, int R, const float *X, cudaStream_t side, const int *skip, const int *mdone);
-void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone);
+void launch_far_down(BatchData &b, int R, float *Y, cudaStream_t st, const int *skip, const int *mdone, bool add);
 void launch_lowp_csr(const MeshData &m, OpData &op, cudaStream_t st);
 vfd_status cg_solve(const MeshData &m, OpData &op, const double *F, double *U, int nrhs, int64_t ld, double rtol,
                     int max_it, int *iters, double *relres, cudaStream_t st);
